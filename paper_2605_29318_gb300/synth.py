@@ -1,0 +1,191 @@
+"""Seeded synthetic particle clouds (inputs only; none of the method's arithmetic).
+
+Both the CUDA path and the FP64 oracle consume these arrays.  Every generator
+is deterministic in its seed (numpy PCG64) and returns a ``Cloud`` of FP32
+arrays: positions X (N, 3), quadrature volumes v (N,), support radii a (N,),
+and the material (Young's modulus E, Poisson ratio nu; scalars or per particle).
+
+The shapes stand in for the paper's meshes and Gaussian-splat objects
+(Supp. Sec. B "RKPM construction": points sampled inside the object; for 3DGS
+the splat centres themselves).  Support radius a_i = s * h_i with h_i = v_i^(1/3)
+the local spacing, so s = 2 gives "support 2.0x spacing".
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Cloud:
+    X: np.ndarray          # (N, 3) float32 positions
+    v: np.ndarray          # (N,) float32 quadrature volumes
+    a: np.ndarray          # (N,) float32 support radii
+    E: object              # float or (N,) float32 Young's modulus
+    nu: object             # float or (N,) float32 Poisson ratio
+    k: int                 # number of modes asked for (constant mode included)
+    name: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.X.shape[0])
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _finish(X, volume, support, E, nu, k, name):
+    n = X.shape[0]
+    v = np.full(n, volume / n, dtype=np.float64)
+    h = (volume / n) ** (1.0 / 3.0)
+    a = np.full(n, support * h, dtype=np.float64)
+    return Cloud(X.astype(np.float32), v.astype(np.float32), a.astype(np.float32),
+                 E, nu, k, name)
+
+
+def unit_cube(n=2000, seed=1, support=2.0, E=1e5, nu=0.45, k=10):
+    """Uniform random points in [0, 1]^3, equal volumes 1/N."""
+    X = _rng(seed).random((n, 3))
+    return _finish(X, 1.0, support, E, nu, k, f"cube{n}")
+
+
+def _rejection(n, lo, hi, inside, rng, batch=None):
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    out = []
+    got = 0
+    batch = batch or max(1024, 2 * n)
+    while got < n:
+        P = lo + (hi - lo) * rng.random((batch, 3))
+        P = P[inside(P)]
+        out.append(P)
+        got += P.shape[0]
+    return np.concatenate(out)[:n]
+
+
+def torus(n=50000, R=0.5, r=0.2, seed=2, support=2.0, E=1e6, nu=0.4, k=32):
+    """Solid torus (major radius R, minor r), rejection-sampled in its box."""
+    def inside(P):
+        rho = np.sqrt(P[:, 0] ** 2 + P[:, 1] ** 2)
+        return (rho - R) ** 2 + P[:, 2] ** 2 < r * r
+    X = _rejection(n, [-R - r, -R - r, -r], [R + r, R + r, r], inside, _rng(seed))
+    return _finish(X, 2.0 * math.pi ** 2 * R * r * r, support, E, nu, k, f"torus{n}")
+
+
+def _random_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def ellipsoid_union(n=20000, seed=5, n_ell=None, support=2.0, E=1e6, nu=0.4, k=16):
+    """Union of 2-5 overlapping random ellipsoids (a blob-like solid)."""
+    rng = _rng(seed)
+    m = n_ell or int(rng.integers(2, 6))
+    centres = [np.zeros(3)]
+    for _ in range(m - 1):
+        centres.append(centres[-1] + rng.normal(size=3) * 0.25)
+    centres = np.array(centres)
+    axes = 0.2 + 0.3 * rng.random((m, 3))
+    rots = [_random_rotation(rng) for _ in range(m)]
+
+    def inside(P):
+        ok = np.zeros(P.shape[0], bool)
+        for c, ax, Rm in zip(centres, axes, rots):
+            L = (P - c) @ Rm
+            ok |= ((L / ax) ** 2).sum(1) < 1.0
+        return ok
+    lo = (centres - axes.max(1, keepdims=True)).min(0)
+    hi = (centres + axes.max(1, keepdims=True)).max(0)
+    # volume by Monte Carlo on the box (input construction only)
+    probe = lo + (hi - lo) * rng.random((200000, 3))
+    vol = float(np.prod(hi - lo) * inside(probe).mean())
+    X = _rejection(n, lo, hi, inside, rng)
+    return _finish(X, vol, support, E, nu, k, f"ellipsoids{n}")
+
+
+def gaussian_mixture(n=1_000_000, n_comp=64, seed=3, support=2.0, nu=0.45, k=64,
+                     knn=16):
+    """Splat-like cloud: a mixture of anisotropic 3D Gaussians.
+
+    Axis scales log-uniform in [0.02, 0.3], random rotations, equal weights;
+    centres placed by a random walk with step 0.7 x (sum of the two largest
+    scales) so that components overlap; samples truncated at 3 sigma.  The
+    volume of particle i is taken from the local density of its ``knn``
+    nearest neighbours, v_i = (4/3) pi d_i^3 / knn; E is log-uniform in
+    [1e4, 1e7] per component (heterogeneous material)."""
+    from scipy.spatial import cKDTree
+
+    rng = _rng(seed)
+    scales = np.exp(rng.uniform(np.log(0.02), np.log(0.3), size=(n_comp, 3)))
+    rots = [_random_rotation(rng) for _ in range(n_comp)]
+    centres = np.zeros((n_comp, 3))
+    for c in range(1, n_comp):
+        two = np.sort(scales[c - 1])[-2:].sum() + np.sort(scales[c])[-2:].sum()
+        d = rng.normal(size=3)
+        centres[c] = centres[c - 1] + 0.35 * two * d / np.linalg.norm(d)
+    Ecomp = np.exp(rng.uniform(np.log(1e4), np.log(1e7), size=n_comp))
+    comp = rng.integers(0, n_comp, size=n)
+    Z = rng.normal(size=(n, 3))
+    bad = np.abs(Z).max(1) > 3.0
+    while bad.any():
+        Z[bad] = rng.normal(size=(int(bad.sum()), 3))
+        bad = np.abs(Z).max(1) > 3.0
+    X = np.empty((n, 3))
+    for c in range(n_comp):
+        sel = comp == c
+        X[sel] = centres[c] + (Z[sel] * scales[c]) @ rots[c].T
+    X32 = X.astype(np.float32)
+    tree = cKDTree(X32.astype(np.float64))
+    dist, _ = tree.query(X32.astype(np.float64), k=knn + 1)
+    dk = dist[:, -1]
+    v = (4.0 / 3.0) * np.pi * dk ** 3 / knn
+    a = support * np.cbrt(v)
+    E = Ecomp[comp].astype(np.float32)
+    return Cloud(X32, v.astype(np.float32), a.astype(np.float32), E,
+                 np.float32(nu), k, f"splat{n}")
+
+
+def batch(n_objects=256, seed=4, nmin=2000, nmax=200000, kmin=16, kmax=48):
+    """Many objects: cube / torus / ellipsoid union, random scale and rotation,
+    particle counts log-uniform in [nmin, nmax], k uniform in [kmin, kmax]."""
+    rng = _rng(seed)
+    out = []
+    for j in range(n_objects):
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        k = int(rng.integers(kmin, kmax + 1))
+        fam = int(rng.integers(0, 3))
+        s = int(rng.integers(0, 2 ** 31 - 1))
+        if fam == 0:
+            c = unit_cube(n, seed=s, E=1e6, nu=0.4, k=k)
+        elif fam == 1:
+            c = torus(n, seed=s, E=1e6, nu=0.4, k=k)
+        else:
+            c = ellipsoid_union(n, seed=s, E=1e6, nu=0.4, k=k)
+        scale = float(np.exp(rng.uniform(np.log(0.5), np.log(2.0))))
+        Rm = _random_rotation(rng)
+        c.X = ((c.X.astype(np.float64) * scale) @ Rm.T).astype(np.float32)
+        c.v = (c.v.astype(np.float64) * scale ** 3).astype(np.float32)
+        c.a = (c.a.astype(np.float64) * scale).astype(np.float32)
+        c.name = f"obj{j}-{c.name}"
+        out.append(c)
+    return out
+
+
+def random_block(n, k, seed=0):
+    """Seeded N(0, 1) starting block (N x k, float32) for the eigensolver."""
+    return _rng(seed).standard_normal((n, k)).astype(np.float32)
+
+
+CONFIGS = {
+    "cube2k": lambda: unit_cube(2000, seed=1),
+    "torus50k": lambda: torus(50000, seed=2),
+}

@@ -1,0 +1,366 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, index or coefficient, a transposed operand) fails at least one of
+them.  CPU only; sizes keep the whole file to well under a minute.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import assembly, eigen, jacobi, rkpm
+from paper_2605_29318_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cloud(n=400, seed=7, support=2.0):
+    return synth.unit_cube(n, seed=seed, support=support)
+
+
+def _build(c):
+    ptr, idx = rkpm.neighbours(c.X, c.a)
+    phi, dphi, cond = rkpm.shape_functions(c.X, c.a, ptr, idx)
+    return ptr, idx, phi, dphi, cond
+
+
+@pytest.fixture(scope="module")
+def cube400():
+    c = _cloud()
+    return c, _build(c)
+
+
+# ------------------------------------------------------------------ raw kernel
+def test_bspline_golden_values_and_library():
+    rows = [l.split() for l in open(os.path.join(GOLD, "bspline_values.txt"))
+            if l.strip() and not l.startswith("#")]
+    q = np.array([float(r[0]) for r in rows])
+    w = np.array([float(r[1]) for r in rows])
+    np.testing.assert_allclose(rkpm.cubic_bspline(q), w, rtol=0, atol=1e-15)
+    # w(q) is the uniform cubic B-spline on knots -2..2 evaluated at 2q
+    from scipy.interpolate import BSpline
+    b3 = BSpline.basis_element([-2, -1, 0, 1, 2], extrapolate=False)
+    qq = np.linspace(0, 0.999, 257)
+    np.testing.assert_allclose(rkpm.cubic_bspline(qq), np.nan_to_num(b3(2 * qq)), atol=1e-14)
+
+
+def test_bspline_integral_and_derivative():
+    from scipy.integrate import quad
+    # 3D integral: 4 pi int_0^1 w(q) q^2 dq = pi / 12
+    val = 4 * np.pi * (quad(lambda q: rkpm.cubic_bspline(q) * q * q, 0, 0.5)[0]
+                       + quad(lambda q: rkpm.cubic_bspline(q) * q * q, 0.5, 1)[0])
+    assert abs(val - np.pi / 12) < 1e-12
+    # w'(q)/q against a central difference of w
+    q = np.linspace(0.01, 0.99, 99)
+    h = 1e-6
+    fd = (rkpm.cubic_bspline(q + h) - rkpm.cubic_bspline(q - h)) / (2 * h)
+    np.testing.assert_allclose(rkpm.cubic_bspline_dw_over_q(q) * q, fd, atol=1e-8)
+
+
+# ------------------------------------------------------------------ neighbours
+def test_neighbours_against_kdtree():
+    from scipy.spatial import cKDTree
+    c = _cloud(1500, seed=3)
+    ptr, idx = rkpm.neighbours(c.X, c.a)
+    Xd = c.X.astype(np.float64)
+    tree = cKDTree(Xd)
+    a = float(c.a[0])
+    lists = tree.query_ball_point(Xd, r=a)
+    for i in range(c.n):
+        mine = set(idx[ptr[i]:ptr[i + 1]].tolist())
+        ref = set(lists[i])
+        for k in mine ^ ref:      # only pairs within rounding of the radius may differ
+            d = np.linalg.norm(Xd[i] - Xd[k])
+            assert abs(d - a) < 1e-9 * a, (i, k, d, a)
+        assert i in mine
+        row = idx[ptr[i]:ptr[i + 1]]
+        assert np.all(np.diff(row) > 0)
+
+
+def test_neighbour_predicate_is_strict_and_asymmetric():
+    # node 1 has a large support and covers point 0; node 0's small support
+    # does not reach point 1; a point exactly at distance a is excluded.
+    X = np.array([[0, 0, 0], [0.5, 0, 0], [1.5, 0, 0]], np.float32)
+    a = np.array([0.1, 1.0, 1.0], np.float32)
+    ptr, idx = rkpm.neighbours(X, a)
+    rows = [idx[ptr[i]:ptr[i + 1]].tolist() for i in range(3)]
+    assert rows[0] == [0, 1]
+    assert rows[1] == [1]          # |x1 - x2| = 1.0 = a_2: strict, excluded
+    assert rows[2] == [2]
+
+
+# ------------------------------------------------------------------ shape functions
+def test_reproducing_conditions(cube400):
+    c, (ptr, idx, phi, dphi, _) = cube400
+    rows = np.repeat(np.arange(c.n), np.diff(ptr))
+    Xd = c.X.astype(np.float64)
+    assert np.abs(np.bincount(rows, phi) - 1).max() < 1e-10                   # Eq. 8, P = 1
+    for d in range(3):
+        s = np.bincount(rows, phi * Xd[idx, d])
+        assert np.abs(s - Xd[:, d]).max() < 1e-10                              # Eq. 8, P = x
+        assert np.abs(np.bincount(rows, dphi[d], minlength=c.n)).max() < 1e-8  # grad of 1
+        for e in range(3):
+            g = np.bincount(rows, dphi[d] * Xd[idx, e])
+            assert np.abs(g - (d == e)).max() < 1e-8                           # grad of x
+
+
+def test_gradient_against_finite_differences(cube400):
+    c, (ptr, idx, phi, dphi, _) = cube400
+    pts = [0, 17, 123, 399]
+    h = 1e-6
+    for i in pts:
+        x = c.X[i].astype(np.float64)
+        ks = idx[ptr[i]:ptr[i + 1]]
+        g = dphi[:, ptr[i]:ptr[i + 1]]
+        scale = np.abs(g).max()
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = h
+            fp, _ = rkpm.shape_functions_at((x + e)[None], c.X, c.a)
+            fm, _ = rkpm.shape_functions_at((x - e)[None], c.X, c.a)
+            fd = (fp[0, ks] - fm[0, ks]) / (2 * h)
+            assert np.abs(fd - g[d]).max() < 1e-6 * scale
+
+
+def test_shifted_basis_equals_paper_basis(cube400):
+    c, (ptr, idx, phi, dphi, _) = cube400
+    for i in [3, 250]:
+        x = c.X[i].astype(np.float64)[None]
+        p1, g1 = rkpm.shape_functions_at(x, c.X, c.a, literal_basis=True)
+        ks = idx[ptr[i]:ptr[i + 1]]
+        np.testing.assert_allclose(p1[0, ks], phi[ptr[i]:ptr[i + 1]], atol=1e-9)
+        np.testing.assert_allclose(g1[:, 0, ks], dphi[:, ptr[i]:ptr[i + 1]],
+                                   atol=1e-8 * np.abs(g1).max())
+
+
+def test_vectorised_equals_loop_bruteforce():
+    c = _cloud(64, seed=11, support=2.5)
+    ptr, idx, phi, dphi, _ = _build(c)
+    pd, gd = rkpm.shape_functions_at(c.X.astype(np.float64), c.X, c.a,
+                                     scale=c.a.astype(np.float64))
+    rows = np.repeat(np.arange(c.n), np.diff(ptr))
+    np.testing.assert_allclose(pd[rows, idx], phi, atol=1e-12)
+    np.testing.assert_allclose(gd[:, rows, idx], dphi, atol=1e-10)
+    mask = np.zeros((c.n, c.n), bool)
+    mask[rows, idx] = True
+    assert np.all(pd[~mask] == 0)
+
+
+# ------------------------------------------------------------------ Neo-Hookean / Prop. 1
+def _golden_K():
+    lines = [l for l in open(os.path.join(GOLD, "neohookean_rest_hessian.txt"))
+             if l.strip() and not l.startswith("#")]
+    i1 = lines.index("K1\n")
+    i2 = lines.index("K\n")
+    K1 = np.array([[float(v) for v in l.split()] for l in lines[i1 + 1:i2]])
+    K = np.array([[float(v) for v in l.split()] for l in lines[i2 + 1:i2 + 10]])
+    return K1, K
+
+
+def test_golden_K_is_commutation_matrix():
+    _, K = _golden_K()
+    A = np.arange(9.0).reshape(3, 3) + 1
+    np.testing.assert_array_equal(K @ A.reshape(-1), A.T.reshape(-1))
+
+
+def test_neohookean_rest_hessian_and_stress_free():
+    K1, K = _golden_K()
+    lam, mu = assembly.lame(1e5, 0.45)
+    gam = 1 + mu / (lam + mu)
+    ref = mu * np.eye(9) + (lam + mu) * (2 - gam) * K1 - (lam + mu) * (1 - gam) * K
+    h = 1e-4
+
+    def psi(f):
+        return assembly.neo_hookean_psi(f.reshape(1, 3, 3), lam, mu)[0]
+    I = np.eye(3).reshape(-1)
+    assert abs(psi(I)) < 1e-9 * lam
+    Hfd = np.zeros((9, 9))
+    grad = np.zeros(9)
+    for a in range(9):
+        ea = np.zeros(9)
+        ea[a] = h
+        grad[a] = (psi(I + ea) - psi(I - ea)) / (2 * h)
+        for b in range(9):
+            eb = np.zeros(9)
+            eb[b] = h
+            Hfd[a, b] = (psi(I + ea + eb) - psi(I + ea - eb) - psi(I - ea + eb)
+                         + psi(I - ea - eb)) / (4 * h * h)
+    assert np.abs(grad).max() < 1e-6 * lam             # rest state is stress-free
+    assert np.abs(Hfd - ref).max() < 1e-5 * lam
+
+
+def _fd_bilinear(f, u, w, h):
+    """u^T Hess(f) w by central differences with one Richardson step."""
+    def d2(t):
+        return (f(t * (u + w)) - f(t * (u - w)) - f(-t * (u - w)) + f(-t * (u + w))) / (4 * t * t)
+    return (4 * d2(h / 2) - d2(h)) / 3
+
+
+@pytest.mark.parametrize("hetero", [False, True])
+def test_prop1_against_energy_finite_differences(hetero):
+    c = _cloud(64, seed=5, support=2.5)
+    ptr, idx, phi, dphi, _ = _build(c)
+    rng = np.random.default_rng(0)
+    E = rng.uniform(1e4, 1e6, c.n) if hetero else 1e5
+    nu = rng.uniform(0.2, 0.45, c.n) if hetero else 0.45
+    H, _ = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, E, nu, dense=True)
+    lam, mu = assembly.lame(np.broadcast_to(E, (c.n,)), np.broadcast_to(nu, (c.n,)))
+    for trial in range(4):
+        u = rng.standard_normal(c.n)
+        w = rng.standard_normal(c.n)
+        fd_total = 0.0
+        for s in range(3):
+            def f(dvec, s=s):
+                d = np.zeros((c.n, 3))
+                d[:, s] = dvec
+                return assembly.potential(d, c.n, ptr, idx, dphi, c.v, E, nu)
+            fd = _fd_bilinear(f, u, w, 1e-3 * float(c.a[0]))
+            # per-axis block of the proof: (lam + 2 mu) d_s phi d_s phi^T + mu (other two)
+            G = [sp.csr_matrix((dphi[t], idx, ptr), shape=(c.n, c.n)) for t in range(3)]
+            blk = sum(((lam + 2 * mu) if t == s else mu) * c.v * (G[t] @ u) * (G[t] @ w)
+                      for t in range(3)).sum()
+            assert abs(fd - blk) < 1e-6 * (abs(blk) + 1e-300) + 1e-9 * abs(u @ H @ w)
+            fd_total += fd
+        ref = u @ H @ w
+        assert abs(fd_total - ref) < 1e-6 * abs(ref)
+
+
+# ------------------------------------------------------------------ H, M structure
+def test_symmetry_spd_and_null_mode(cube400):
+    c, (ptr, idx, phi, dphi, _) = cube400
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu, dense=True)
+    scale = np.abs(H).max()
+    assert np.abs(H - H.T).max() <= 1e-13 * scale
+    assert np.abs(M - M.T).max() <= 1e-13 * np.abs(M).max()
+    np.linalg.cholesky(M)                                   # M is SPD
+    assert np.abs(H @ np.ones(c.n)).max() <= 1e-12 * scale  # H 1 = 0
+    # partition of unity: 1^T M 1 = sum_i v_i (the total volume)
+    one = np.ones(c.n)
+    assert abs(one @ M @ one - c.v.astype(np.float64).sum()) < 1e-12 * c.v.sum()
+    lam, _ = eigen.eigh_dense(H, M, 4)
+    assert abs(lam[0]) < 1e-9 * lam[1]
+
+
+def test_linear_field_energy(cube400):
+    c, (ptr, idx, phi, dphi, _) = cube400
+    H, _ = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
+    lam, mu = assembly.lame(c.E, c.nu)
+    a = np.array([0.3, -1.1, 0.7])
+    cvec = c.X.astype(np.float64) @ a
+    ref = (lam + 4 * mu) * (a @ a) * c.v.astype(np.float64).sum()
+    assert abs(cvec @ (H @ cvec) - ref) < 1e-9 * ref
+
+
+def test_invariances():
+    c = _cloud(300, seed=9)
+    # snap to a 2^-20 grid so that the exact transforms below stay exact in FP32
+    c.X = (np.round(c.X.astype(np.float64) * 2 ** 20) / 2 ** 20).astype(np.float32)
+    ptr, idx, phi, dphi, _ = _build(c)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu, dense=True)
+    lam0, _ = eigen.eigh_dense(H, M, 6)
+    # exact rotation (axis cycle with a sign flip) and translation
+    Xr = np.stack([-c.X[:, 1], c.X[:, 2], c.X[:, 0]], 1) + np.float32(3.25)
+    c2 = synth.Cloud(Xr.astype(np.float32), c.v, c.a, c.E, c.nu, c.k)
+    p2, i2, f2, g2, _ = _build(c2)
+    H2, M2 = assembly.assemble(c.n, p2, i2, f2, g2, c.v, c.E, c.nu, dense=True)
+    np.testing.assert_allclose(H2, H, atol=1e-9 * np.abs(H).max())
+    np.testing.assert_allclose(M2, M, atol=1e-9 * np.abs(M).max())
+    # general rotation: the FP32 rounding of the rotated inputs perturbs the
+    # cloud by ~1e-7 of its size, so only the spectrum is compared, loosely
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    c3 = synth.Cloud((c.X.astype(np.float64) @ R.T).astype(np.float32), c.v, c.a,
+                     c.E, c.nu, c.k)
+    p3, i3, f3, g3, _ = _build(c3)
+    H3, M3 = assembly.assemble(c.n, p3, i3, f3, g3, c.v, c.E, c.nu, dense=True)
+    lam3, _ = eigen.eigh_dense(H3, M3, 6)
+    np.testing.assert_allclose(lam3[1:], lam0[1:], rtol=1e-4)
+    # uniform scale s: H -> s H, M -> s^3 M, eigenvalues -> eigenvalues / s^2
+    s = 2.0
+    c3 = synth.Cloud(c.X * np.float32(s), c.v * np.float32(s ** 3), c.a * np.float32(s),
+                     c.E, c.nu, c.k)
+    p3, i3, f3, g3, _ = _build(c3)
+    assert np.array_equal(p3, ptr) and np.array_equal(i3, idx)
+    H3, M3 = assembly.assemble(c.n, p3, i3, f3, g3, c3.v, c.E, c.nu, dense=True)
+    np.testing.assert_allclose(H3, s * H, atol=1e-9 * s * np.abs(H).max())
+    np.testing.assert_allclose(M3, s ** 3 * M, atol=1e-9 * s ** 3 * np.abs(M).max())
+    lam3, _ = eigen.eigh_dense(H3, M3, 6)
+    np.testing.assert_allclose(lam3[1:], lam0[1:] / s ** 2, rtol=1e-9)
+    # Young's modulus scaling at fixed nu
+    H4, _ = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, 3 * c.E, c.nu, dense=True)
+    np.testing.assert_allclose(H4, 3 * H, atol=1e-12 * np.abs(H).max())
+    # particle permutation
+    perm = np.random.default_rng(1).permutation(c.n)
+    c5 = synth.Cloud(c.X[perm], c.v[perm], c.a[perm], c.E, c.nu, c.k)
+    p5, i5, f5, g5, _ = _build(c5)
+    H5, M5 = assembly.assemble(c.n, p5, i5, f5, g5, c5.v, c.E, c.nu, dense=True)
+    np.testing.assert_allclose(H5, H[np.ix_(perm, perm)], atol=1e-12 * np.abs(H).max())
+
+
+def test_continuum_sanity_cube2k():
+    """Neumann unit cube: the first non-zero eigenvalue tends to (lam + 4 mu) pi^2
+    (threefold).  At 2,000 particles the discrete value is within a loose band."""
+    c = synth.unit_cube(2000, seed=1)
+    ptr, idx, phi, dphi, _ = _build(c)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
+    lam, _ = eigen.eigh_dense(H, M, 5)
+    lm, mu = assembly.lame(c.E, c.nu)
+    cont = (lm + 4 * mu) * np.pi ** 2
+    assert np.all(np.abs(lam[1:4] / cont - 1) < 0.5)
+    assert lam[4] > lam[3]
+
+
+# ------------------------------------------------------------------ eigensolvers
+def test_dense_eigensolve_against_hand_jacobi():
+    c = _cloud(64, seed=5, support=2.5)
+    ptr, idx, phi, dphi, _ = _build(c)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu, dense=True)
+    lam, C = eigen.eigh_dense(H, M, 8)
+    wj, Cj = jacobi.generalized_jacobi(H, M)
+    np.testing.assert_allclose(lam[1:], wj[1:8], rtol=1e-10)
+    assert abs(lam[0]) < 1e-9 * lam[1] and abs(wj[0]) < 1e-9 * wj[1]
+    np.testing.assert_allclose(C.T @ M @ C, np.eye(8), atol=1e-10)
+    np.testing.assert_allclose(Cj.T @ M @ Cj, np.eye(c.n), atol=1e-9)
+    assert eigen.max_principal_angle(M, C[:, 1:8], Cj[:, 1:8]) < 1e-8
+
+
+def test_sparse_tier_against_dense():
+    c = _cloud(1200, seed=4)
+    ptr, idx, phi, dphi, _ = _build(c)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
+    lam_d, C_d = eigen.eigh_dense(H, M, 10)
+    lam_s, C_s = eigen.eigsh_sparse(H, M, 10)
+    np.testing.assert_allclose(lam_s[1:], lam_d[1:], rtol=1e-9)
+    assert eigen.residuals(H, M, lam_s, C_s)[1:].max() < 1e-8
+    assert eigen.max_principal_angle(M, C_s, C_d) < 1e-6
+
+
+def test_principal_angle_and_residual_helpers():
+    rng = np.random.default_rng(3)
+    n = 50
+    B = rng.standard_normal((n, n))
+    M = B @ B.T + n * np.eye(n)
+    Q = eigen.m_orthonormalise(M, rng.standard_normal((n, 2)))
+    u, v = Q[:, 0], Q[:, 1]
+    for ang in [1e-6, 1e-3, 0.3]:
+        A = np.cos(ang) * u + np.sin(ang) * v
+        assert abs(eigen.max_principal_angle(M, u[:, None], A[:, None]) - ang) < 1e-9
+    Hs = B.T @ B
+    lam, C = eigen.eigh_dense(Hs, M, 3)
+    assert eigen.residuals(Hs, M, lam, C).max() < 1e-10
+    assert eigen.residuals(Hs, M, lam * (1 + 1e-3), C).min() > 5e-4
+
+
+def test_disconnected_clouds_have_one_zero_mode_each():
+    c1 = synth.unit_cube(200, seed=1)
+    c2 = synth.unit_cube(200, seed=2)
+    X = np.concatenate([c1.X, c2.X + np.float32(5)])
+    c = synth.Cloud(X, np.concatenate([c1.v, c2.v]), np.concatenate([c1.a, c2.a]),
+                    1e5, 0.45, 4)
+    ptr, idx, phi, dphi, _ = _build(c)
+    assert rkpm.connected_components(c.n, ptr, idx) == 2
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
+    lam, _ = eigen.eigh_dense(H, M, 3)
+    assert abs(lam[0]) < 1e-8 * lam[2] and abs(lam[1]) < 1e-8 * lam[2]
