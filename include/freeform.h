@@ -1,0 +1,191 @@
+/*
+ * freeform.h -- C ABI of the GB300 (sm_103a) subspace-construction library.
+ *
+ * The library builds the skinning-eigenmode subspace of FreeForm (reduced-order
+ * deformable simulation from particle-based skinning eigenmodes):
+ *
+ *   rkpm_build        support neighbours and corrected RKPM shape functions
+ *                     (Sec. 3.2 "RKPM", Eqs. 6-11)
+ *   assemble_hessian  weight-space Neo-Hookean Hessian H_w (Prop. 1) and the
+ *                     RKPM mass matrix M (Sec. 3.2, Eq. 14)
+ *   eigenmodes        the k lowest generalized eigenpairs of H_w c = lambda M c
+ *                     (Sec. 3.2, Eq. 15; Supp. Sec. B "Eigenanalysis")
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an ff_status; no C++ exception crosses the ABI.  On an
+ *   error ff_last_error() returns a message (for FF_ERR_SINGULAR_MOMENT it names
+ *   the particle, by its index in the caller's input order).
+ * - Array arguments documented "device" are pointers into memory of the
+ *   context's device; the library reads them in stream order on the context's
+ *   stream (e.g. torch tensor.data_ptr() with the stream from
+ *   torch.cuda.current_stream().cuda_stream).  Arguments documented "host" are
+ *   ordinary host memory.  The caller owns every buffer it passes; the context
+ *   owns every internal device buffer and frees them in ff_destroy.
+ * - Calls are state-ordered: rkpm_build, then assemble_hessian, then
+ *   eigenmodes; out of order they return FF_ERR_STATE.  A new rkpm_build
+ *   discards the previous cloud, matrices and modes.
+ * - Calls synchronise the context's stream before returning (results are
+ *   ready on return); host outputs are written before return.
+ * - Particle order: the library reorders particles internally (by spatial
+ *   cell) for locality; every output is returned in the caller's order.
+ */
+#ifndef FREEFORM_H
+#define FREEFORM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ff_ctx ff_ctx;
+
+typedef enum {
+  FF_OK = 0,
+  FF_ERR_INVALID_ARG = 1,     /* bad size, NULL pointer, non-finite or non-positive input */
+  FF_ERR_CUDA = 2,            /* a CUDA runtime call or kernel launch failed */
+  FF_ERR_OOM = 3,             /* device allocation failed */
+  FF_ERR_SINGULAR_MOMENT = 4, /* a moment matrix M(X_i) has rank < 4 (fewer than four
+                                 non-coplanar nodes cover X_i) */
+  FF_ERR_NOT_CONVERGED = 5,   /* eigenmodes hit max_iter; outputs hold the last iterate */
+  FF_ERR_NUMERIC = 6,         /* NaN/Inf or a breakdown the solver could not recover from */
+  FF_ERR_TIMEOUT = 7,         /* the wall-clock budget of ff_eig_opts ran out */
+  FF_ERR_STATE = 8            /* calls out of order */
+} ff_status;
+
+typedef enum {
+  FF_PREC_FP32 = 0,  /* FP32 shape functions (FP64 fallback for ill-conditioned moment
+                        matrices), FP32 matrices and iterates, FP64-accumulated Gram
+                        products, FP32 dense Rayleigh-Ritz */
+  FF_PREC_FP64 = 1   /* FP64 throughout (the preconditioner alone stays FP32) */
+} ff_precision;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `precision` is an
+ * ff_precision.  On success *out receives the context. */
+ff_status ff_create(ff_ctx** out, int device, void* cuda_stream, int precision);
+
+/* Free a context and every device buffer it owns.  NULL is a no-op. */
+void ff_destroy(ff_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none).  The string
+ * stays valid until the next call on the context. */
+const char* ff_last_error(const ff_ctx* ctx);
+
+/* Library version string, e.g. "freeform-gb300 0.1". */
+const char* ff_version(void);
+
+/* ------------------------------------------------------------------ rkpm_build
+ * Supp. Sec. B "RKPM construction" + Sec. 3.2 Eqs. 6-11, nodal discretisation:
+ * every particle is both an RKPM node p_k and a quadrature point X_i with
+ * weight (volume) v_i.  Node k covers X iff ||X - p_k||^2 < a_k^2, the test
+ * evaluated in FP64 on the FP32 inputs as ((dx*dx + dy*dy) + dz*dz) < a_k*a_k
+ * without fused multiply-add (bit-exact with the oracle).  The raw kernel is the
+ * cubic B-spline w(||X - p_k|| / a_k); the correction uses the linear basis.
+ *
+ *   particles  device, float[n][3] row-major positions (x, y, z)
+ *   volumes    device, float[n] quadrature volumes v_i > 0
+ *   support    device, float[n] support radii a_k > 0
+ *   n          number of particles, 1 <= n <= 2^31 - 1
+ *
+ * Errors: FF_ERR_INVALID_ARG on NULL pointers, n out of range, or a non-finite
+ * position / non-positive volume or radius (message names the first one);
+ * FF_ERR_SINGULAR_MOMENT if some moment matrix has rank < 4. */
+ff_status rkpm_build(ff_ctx* ctx, const float* particles, const float* volumes,
+                     const float* support, int64_t n);
+
+/* ------------------------------------------------------------ assemble_hessian
+ * Prop. 1: (H_w)_kl = sum_i v_i (lambda_i + 4 mu_i) grad phi_k(X_i) . grad phi_l(X_i)
+ * Eq. 14:  M_kl     = sum_i v_i phi_k(X_i) phi_l(X_i)
+ * with Lame lambda = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu)) at X_i.  The
+ * diagonal of H_w is set to minus the sum of its row's off-diagonal entries,
+ * so H_w 1 = 0 holds exactly in the stored matrix.
+ *
+ *   E, nu   device, float[n] per-particle Young's modulus and Poisson ratio in
+ *           the caller's order, or NULL to use the uniform E0 / nu0
+ *   E0, nu0 uniform material (used where the array is NULL); E > 0, 0 <= nu < 0.5 */
+ff_status assemble_hessian(ff_ctx* ctx, const float* E, const float* nu, double E0,
+                           double nu0);
+
+/* ------------------------------------------------------------------ eigenmodes */
+typedef struct {
+  double tol;           /* stop when every non-constant mode has
+                           ||H c - lam M c||_2 / (lam ||M c||_2) <= tol   (1e-6) */
+  int max_iter;         /* outer LOBPCG iterations (500) */
+  int guard;            /* extra block vectors beyond the k-1 wanted (8) */
+  int cheb_degree;      /* degree of the Chebyshev preconditioner; 0 = Jacobi (16) */
+  double cheb_ratio;    /* beta / alpha of its interval on D^-1 H (300) */
+  uint64_t seed;        /* seed of the random start block (0) */
+  double time_budget_s; /* wall-clock budget; <= 0 = none (0) */
+  int exclude_constant; /* 1: return k non-constant modes (the paper's m) instead of
+                           k modes with the constant mode at index 0 (0) */
+  int verbose;          /* print per-iteration residuals to stderr (0) */
+} ff_eig_opts;
+
+typedef struct {
+  int iterations;          /* outer iterations run */
+  int converged;           /* modes meeting tol (constant mode counted as converged) */
+  int spmm_calls;          /* (H, M) block products in the outer loop */
+  int precond_spmv_calls;  /* H block products inside the preconditioner */
+  double max_residual;     /* largest relative residual over the non-constant modes */
+  double seconds;          /* wall time of the call */
+  int warm_start_used;     /* 1 if X0 was used, 0 if the random start was used */
+} ff_eig_report;
+
+/* Fill *opts with the defaults listed above. */
+void ff_eig_opts_default(ff_eig_opts* opts);
+
+/* The k lowest generalized eigenpairs, ascending.  Constant mode convention
+ * (Supp. Sec. B: the spectrum always contains the constant mode with
+ * eigenvalue 0): with exclude_constant = 0, index 0 is c0 = 1/sqrt(1^T M 1) * 1
+ * with eigenvalue 0, set analytically and deflated; indices 1..k-1 are the
+ * lowest non-constant modes.  Modes are M-orthonormal: c^T M c = I.
+ *
+ *   k        number of modes, 1 <= k <= 256 and k <= n - 1
+ *   opts     NULL = defaults
+ *   X0       device, optional starting block in the caller's particle order,
+ *            column-major n x (k - 1 + guard) of the context's precision
+ *            (float for FF_PREC_FP32, double for FF_PREC_FP64); NULL = seeded
+ *            random start.  A rank-deficient X0 falls back to the random start.
+ *   eigvals  host, double[k] eigenvalues (ascending)
+ *   modes    device, column-major n x k (leading dimension n) of the context's
+ *            precision, in the caller's particle order; may be NULL
+ *   rep      host, optional report
+ *
+ * Returns FF_ERR_NOT_CONVERGED (outputs filled with the last iterate) when
+ * max_iter is reached, FF_ERR_TIMEOUT when the time budget runs out. */
+ff_status eigenmodes(ff_ctx* ctx, int k, const ff_eig_opts* opts, const void* X0,
+                     double* eigvals, void* modes, ff_eig_report* rep);
+
+/* --------------------------------------------------------- inspection exports
+ * Copies of the internal results, in the caller's particle order, for parity
+ * checks against an independent implementation.  All outputs are host memory. */
+
+/* Sizes after rkpm_build / assemble_hessian: n, n1 = number of (i, k) support
+ * pairs, n2 = stored entries of H_w (= of M), including the diagonal; n2 = 0
+ * before assemble_hessian.  Any pointer may be NULL. */
+ff_status ff_get_sizes(const ff_ctx* ctx, int64_t* n, int64_t* n1, int64_t* n2);
+
+/* Neighbour lists as CSR: ptr int64[n+1], idx int32[n1]; row i lists the nodes
+ * k covering X_i, ascending.  phi double[n1] and dphi double[3*n1] (x block,
+ * then y, then z) are the shape functions phi_k(X_i) and their gradients,
+ * aligned with idx; phi / dphi may be NULL. */
+ff_status ff_export_rkpm(const ff_ctx* ctx, int64_t* ptr, int32_t* idx, double* phi,
+                         double* dphi);
+
+/* H_w and M as CSR with ascending columns: row_ptr int64[n+1], col int32[n2],
+ * H double[n2], M double[n2].  H or M may be NULL. */
+ff_status ff_export_matrices(const ff_ctx* ctx, int64_t* row_ptr, int32_t* col, double* H,
+                             double* M);
+
+/* Apply the assembled operators to a block: Y_H = H_w X, Y_M = M X for X
+ * column-major n x m in the caller's order (device, context precision).
+ * Y_H / Y_M device, same layout; either may be NULL.  1 <= m <= 512. */
+ff_status ff_apply_operators(ff_ctx* ctx, const void* X, int m, void* YH, void* YM);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FREEFORM_H */

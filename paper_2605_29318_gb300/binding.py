@@ -1,0 +1,249 @@
+"""Thin ctypes binding of ``libfreeform.so`` (argument marshalling only).
+
+The names follow the C ABI in ``include/freeform.h``: ``rkpm_build``,
+``assemble_hessian``, ``eigenmodes`` (plus the inspection exports).  Every step
+of the computation runs in the CUDA library; this module only turns torch
+tensors into device pointers and host arrays into ctypes buffers.  It raises
+if the library has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfreeform.so")
+
+FF_OK = 0
+STATUS = {0: "FF_OK", 1: "FF_ERR_INVALID_ARG", 2: "FF_ERR_CUDA", 3: "FF_ERR_OOM",
+          4: "FF_ERR_SINGULAR_MOMENT", 5: "FF_ERR_NOT_CONVERGED", 6: "FF_ERR_NUMERIC",
+          7: "FF_ERR_TIMEOUT", 8: "FF_ERR_STATE"}
+PREC = {"fp32": 0, "fp64": 1}
+
+# every symbol the header declares (checked by the CPU tests)
+EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build",
+           "assemble_hessian", "ff_eig_opts_default", "eigenmodes", "ff_get_sizes",
+           "ff_export_rkpm", "ff_export_matrices", "ff_apply_operators"]
+
+
+class EigOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("guard", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int), ("cheb_ratio", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("time_budget_s", ctypes.c_double),
+                ("exclude_constant", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class EigReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("spmm_calls", ctypes.c_int), ("precond_spmv_calls", ctypes.c_int),
+                ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("warm_start_used", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class FreeformError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfreeform.so and declare its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run `python -m paper_2605_29318_gb300.build`")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.ff_create.argtypes = [ctypes.POINTER(vp), i32, vp, i32]
+    L.ff_destroy.argtypes = [vp]
+    L.ff_destroy.restype = None
+    L.ff_last_error.argtypes = [vp]
+    L.ff_last_error.restype = ctypes.c_char_p
+    L.ff_version.restype = ctypes.c_char_p
+    L.rkpm_build.argtypes = [vp, vp, vp, vp, i64]
+    L.assemble_hessian.argtypes = [vp, vp, vp, dbl, dbl]
+    L.ff_eig_opts_default.argtypes = [ctypes.POINTER(EigOpts)]
+    L.ff_eig_opts_default.restype = None
+    L.eigenmodes.argtypes = [vp, i32, ctypes.POINTER(EigOpts), vp, vp, vp,
+                             ctypes.POINTER(EigReport)]
+    L.ff_get_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.ff_export_rkpm.argtypes = [vp, vp, vp, vp, vp]
+    L.ff_export_matrices.argtypes = [vp, vp, vp, vp, vp]
+    L.ff_apply_operators.argtypes = [vp, vp, i32, vp, vp]
+    for name in EXPORTS:
+        if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def default_opts(**kw) -> EigOpts:
+    o = EigOpts()
+    load_library().ff_eig_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+class Context:
+    """One ff_ctx: a particle cloud, its matrices and eigen-solver workspace."""
+
+    def __init__(self, device: int = 0, precision: str = "fp32", stream=None):
+        import torch
+        self.L = load_library()
+        self.device = device
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self.L.ff_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream),
+                              PREC[precision])
+        if st != FF_OK:
+            raise FreeformError(st, "ff_create failed")
+        self.h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != FF_OK:
+            raise FreeformError(st, self.L.ff_last_error(self.h).decode())
+
+    # ---- the three calls of the paper's pipeline
+    def rkpm_build(self, particles, volumes, support):
+        """particles (n, 3), volumes (n,), support radii (n,): float32 CUDA tensors."""
+        for t in (particles, volumes, support):
+            assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+        self.n = int(particles.shape[0])
+        self._keep = (particles, volumes, support)
+        self._check(self.L.rkpm_build(self.h, _ptr(particles), _ptr(volumes), _ptr(support),
+                                      self.n))
+
+    def assemble_hessian(self, E=None, nu=None, E0: float = 1e5, nu0: float = 0.45):
+        """E, nu: per-particle float32 CUDA tensors or None (uniform E0, nu0)."""
+        self._check(self.L.assemble_hessian(self.h, _ptr(E), _ptr(nu), float(E0), float(nu0)))
+
+    def eigenmodes(self, k: int, opts: Optional[EigOpts] = None, X0=None, want_modes=True,
+                   modes_out=None, check=True):
+        """Returns (eigvals numpy (k,), modes torch (n, k) column-major view, report, status)."""
+        import torch
+        ev = np.zeros(k, dtype=np.float64)
+        modes = modes_out
+        if want_modes and modes is None:
+            modes = torch.empty((k, self.n), dtype=self.dtype, device=f"cuda:{self.device}")
+        rep = EigReport()
+        st = self.L.eigenmodes(self.h, int(k), ctypes.byref(opts) if opts is not None else None,
+                               _ptr(X0), ev.ctypes.data_as(ctypes.c_void_p), _ptr(modes),
+                               ctypes.byref(rep))
+        if check and st not in (FF_OK,):
+            raise FreeformError(st, self.L.ff_last_error(self.h).decode())
+        return ev, (modes.t() if modes is not None else None), rep.as_dict(), st
+
+    # ---- inspection
+    def sizes(self):
+        n, n1, n2 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.L.ff_get_sizes(self.h, ctypes.byref(n), ctypes.byref(n1),
+                                        ctypes.byref(n2)))
+        return n.value, n1.value, n2.value
+
+    def export_rkpm(self):
+        n, n1, _ = self.sizes()
+        ptr = np.zeros(n + 1, np.int64)
+        idx = np.zeros(n1, np.int32)
+        phi = np.zeros(n1, np.float64)
+        dphi = np.zeros(3 * n1, np.float64)
+        self._check(self.L.ff_export_rkpm(self.h, ptr.ctypes.data, idx.ctypes.data,
+                                          phi.ctypes.data, dphi.ctypes.data))
+        return ptr, idx, phi, dphi.reshape(3, n1)
+
+    def export_matrices(self):
+        n, _, n2 = self.sizes()
+        ptr = np.zeros(n + 1, np.int64)
+        col = np.zeros(n2, np.int32)
+        H = np.zeros(n2, np.float64)
+        M = np.zeros(n2, np.float64)
+        self._check(self.L.ff_export_matrices(self.h, ptr.ctypes.data, col.ctypes.data,
+                                              H.ctypes.data, M.ctypes.data))
+        return ptr, col, H, M
+
+    def apply_operators(self, X):
+        """X: (n, m) CUDA tensor of the context dtype -> (H X, M X)."""
+        import torch
+        m = int(X.shape[1])
+        Xc = X.t().contiguous()          # column-major n x m
+        YH = torch.empty_like(Xc)
+        YM = torch.empty_like(Xc)
+        self._check(self.L.ff_apply_operators(self.h, _ptr(Xc), m, _ptr(YH), _ptr(YM)))
+        return YH.t(), YM.t()
+
+
+# module-level names matching the C ABI
+def rkpm_build(ctx: Context, particles, volumes, support):
+    return ctx.rkpm_build(particles, volumes, support)
+
+
+def assemble_hessian(ctx: Context, E=None, nu=None, E0=1e5, nu0=0.45):
+    return ctx.assemble_hessian(E, nu, E0, nu0)
+
+
+def eigenmodes(ctx: Context, k, opts=None, X0=None):
+    return ctx.eigenmodes(k, opts, X0)
+
+
+def subspace_from_host(X, v, a, E, nu, k, precision="fp32", opts=None, device=0, ctx=None):
+    """End-to-end public call on HOST arrays: copy the cloud to the device,
+    build, assemble, solve, and copy eigenvalues and modes back to the host.
+    Returns (eigvals, modes (n, k) numpy, report, bytes_h2d, bytes_d2h)."""
+    import torch
+    own = ctx is None
+    if own:
+        ctx = Context(device, precision)
+    dev = f"cuda:{device}"
+
+    def h2d(x):
+        t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+        return t.pin_memory().to(dev, non_blocking=True)
+    Xd, vd, ad = h2d(X), h2d(v), h2d(a)
+    h2d_bytes = X.nbytes + v.nbytes + a.nbytes
+    Ed = nud = None
+    if np.ndim(E) > 0:
+        Ed = h2d(E)
+        h2d_bytes += np.asarray(E, np.float32).nbytes
+    if np.ndim(nu) > 0:
+        nud = h2d(nu)
+        h2d_bytes += np.asarray(nu, np.float32).nbytes
+    ctx.rkpm_build(Xd, vd, ad)
+    ctx.assemble_hessian(Ed, nud, float(E) if Ed is None else 1.0, float(nu) if nud is None else 0.3)
+    ev, modes, rep, st = ctx.eigenmodes(k, opts, check=False)
+    host = modes.t().contiguous().cpu().numpy().T      # (n, k)
+    d2h_bytes = host.nbytes + ev.nbytes
+    if own:
+        ctx.close()
+    return ev, host, rep, h2d_bytes, d2h_bytes, st

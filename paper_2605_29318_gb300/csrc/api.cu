@@ -1,0 +1,256 @@
+// C ABI of the library: argument checks, error model and inspection exports.
+#include <algorithm>
+#include <numeric>
+
+#include "linalg.cuh"
+
+namespace ff {
+template <class T>
+void gather_block(ff_ctx* c, const T* X0, int m, T* X, int ld);
+template <class T>
+void scatter_block(ff_ctx* c, const T* X, int ld, int m, T* out);
+}  // namespace ff
+
+namespace {
+
+template <class F>
+ff_status guarded(ff_ctx* c, F&& f) {
+  if (!c) return FF_ERR_INVALID_ARG;
+  c->err.clear();
+  try {
+    FF_CUDA(cudaSetDevice(c->device));
+    f();
+    return FF_OK;
+  } catch (const ff::Error& e) {
+    c->err = e.what();
+    (void)cudaGetLastError();
+    return e.code;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return FF_ERR_CUDA;
+  }
+}
+
+}  // namespace
+
+namespace {
+template <class T>
+std::vector<double> to_host_f64(const ff::Buf& b, size_t count) {
+  std::vector<T> tmp(count);
+  if (count) FF_CUDA(cudaMemcpy(tmp.data(), b.p, sizeof(T) * count, cudaMemcpyDeviceToHost));
+  return std::vector<double>(tmp.begin(), tmp.end());
+}
+template <class T>
+std::vector<T> to_host(const ff::Buf& b, size_t count) {
+  std::vector<T> tmp(count);
+  if (count) FF_CUDA(cudaMemcpy(tmp.data(), b.p, sizeof(T) * count, cudaMemcpyDeviceToHost));
+  return tmp;
+}
+
+// internal-order CSR (+ aligned values) -> caller-order CSR with ascending columns
+void remap_csr(const std::vector<int>& perm, const std::vector<int>& iperm,
+               const std::vector<long long>& p, const std::vector<int>& idx,
+               std::vector<const std::vector<double>*> vals, int64_t* optr, int32_t* oidx,
+               std::vector<double*> ovals, const std::vector<size_t>& strides_in,
+               const std::vector<size_t>& strides_out, const std::vector<int>& reps) {
+  const long long n = (long long)perm.size();
+  long long off = 0;
+  std::vector<std::pair<int, long long>> row;
+  for (long long i = 0; i < n; ++i) {
+    const long long j = iperm[i];
+    optr[i] = off;
+    row.clear();
+    for (long long e = p[j]; e < p[j + 1]; ++e) row.emplace_back(perm[idx[e]], e);
+    std::sort(row.begin(), row.end());
+    for (size_t t = 0; t < row.size(); ++t) {
+      oidx[off + t] = row[t].first;
+      for (size_t v = 0; v < vals.size(); ++v) {
+        if (!ovals[v]) continue;
+        for (int r = 0; r < reps[v]; ++r)
+          ovals[v][r * strides_out[v] + off + t] = (*vals[v])[r * strides_in[v] + row[t].second];
+      }
+    }
+    off += (long long)row.size();
+  }
+  optr[n] = off;
+}
+}  // namespace
+
+extern "C" {
+
+const char* ff_version(void) { return "freeform-gb300 0.1"; }
+
+ff_status ff_create(ff_ctx** out, int device, void* cuda_stream, int precision) {
+  if (!out) return FF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (precision != FF_PREC_FP32 && precision != FF_PREC_FP64) return FF_ERR_INVALID_ARG;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    (void)cudaGetLastError();
+    return FF_ERR_CUDA;
+  }
+  ff_ctx* c = new ff_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->prec = precision;
+  ff_status s = guarded(c, [&] {
+    c->flags.ensure(sizeof(ff::DevFlags));
+    void* h = nullptr;
+    FF_CUDA(cudaMallocHost(&h, 64 * 1024));
+    c->hflags = static_cast<ff::DevFlags*>(h);
+  });
+  if (s != FF_OK) {
+    delete c;
+    return s;
+  }
+  *out = c;
+  return FF_OK;
+}
+
+void ff_destroy(ff_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->hflags) cudaFreeHost(c->hflags);
+  delete c;
+}
+
+const char* ff_last_error(const ff_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ff_status rkpm_build(ff_ctx* c, const float* particles, const float* volumes, const float* support,
+                     int64_t n) {
+  return guarded(c, [&] {
+    FF_REQUIRE(particles && volumes && support, FF_ERR_INVALID_ARG, "NULL input pointer");
+    FF_REQUIRE(n >= 1 && n <= 0x7fffffffLL, FF_ERR_INVALID_ARG, "n out of range");
+    c->stage = 0;
+    c->n = n;
+    c->n1 = c->n2 = 0;
+    ff::build_neighbours(c, particles, volumes, support, n);
+    ff::build_shape(c);
+    c->stage = 1;
+  });
+}
+
+ff_status assemble_hessian(ff_ctx* c, const float* E, const float* nu, double E0, double nu0) {
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "assemble_hessian before rkpm_build");
+    if (!E) FF_REQUIRE(E0 > 0 && std::isfinite(E0), FF_ERR_INVALID_ARG, "E0 must be > 0");
+    if (!nu) FF_REQUIRE(nu0 >= 0 && nu0 < 0.5, FF_ERR_INVALID_ARG, "nu0 must be in [0, 0.5)");
+    c->stage = 1;
+    ff::build_matrices(c, E, nu, E0, nu0);
+    c->stage = 2;
+  });
+}
+
+void ff_eig_opts_default(ff_eig_opts* o) {
+  if (!o) return;
+  o->tol = 1e-6;
+  o->max_iter = 500;
+  o->guard = 8;
+  o->cheb_degree = 16;
+  o->cheb_ratio = 300.0;
+  o->seed = 0;
+  o->time_budget_s = 0.0;
+  o->exclude_constant = 0;
+  o->verbose = 0;
+}
+
+ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, double* eigvals,
+                     void* modes, ff_eig_report* rep) {
+  ff_status result = FF_OK;
+  ff_status s = guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 2, FF_ERR_STATE, "eigenmodes before assemble_hessian");
+    FF_REQUIRE(eigvals, FF_ERR_INVALID_ARG, "eigvals must not be NULL");
+    FF_REQUIRE(k >= 1 && k <= 256 && k <= c->n - 1, FF_ERR_INVALID_ARG, "k out of range");
+    ff_eig_opts o;
+    ff_eig_opts_default(&o);
+    if (opts) o = *opts;
+    FF_REQUIRE(o.tol > 0 && o.max_iter >= 0 && o.guard >= 0, FF_ERR_INVALID_ARG, "bad options");
+    if (rep) *rep = ff_eig_report{};
+    result = ff::run_eigenmodes(c, k, o, X0, eigvals, modes, rep);
+    if (result == FF_ERR_NOT_CONVERGED) c->err = "max_iter reached before tol";
+    if (result == FF_ERR_TIMEOUT) c->err = "time budget exhausted";
+    if (result == FF_ERR_NUMERIC) c->err = "non-finite residual";
+  });
+  return s != FF_OK ? s : result;
+}
+
+ff_status ff_get_sizes(const ff_ctx* c, int64_t* n, int64_t* n1, int64_t* n2) {
+  if (!c) return FF_ERR_INVALID_ARG;
+  if (n) *n = c->stage >= 1 ? c->n : 0;
+  if (n1) *n1 = c->stage >= 1 ? c->n1 : 0;
+  if (n2) *n2 = c->stage >= 2 ? c->n2 : 0;
+  return FF_OK;
+}
+
+
+ff_status ff_export_rkpm(const ff_ctx* cc, int64_t* ptr, int32_t* idx, double* phi, double* dphi) {
+  ff_ctx* c = const_cast<ff_ctx*>(cc);
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "no cloud built");
+    FF_REQUIRE(ptr && idx, FF_ERR_INVALID_ARG, "NULL output");
+    FF_CUDA(cudaStreamSynchronize(c->stream));
+    const size_t n = c->n, n1 = c->n1;
+    auto perm = to_host<int>(c->perm, n);
+    auto iperm = to_host<int>(c->iperm, n);
+    auto p = to_host<long long>(c->nbr_ptr, n + 1);
+    auto ix = to_host<int>(c->nbr_idx, n1);
+    std::vector<double> ph, dph;
+    if (c->prec == FF_PREC_FP64) {
+      ph = to_host<double>(c->phi, n1);
+      dph = to_host<double>(c->dphi, 3 * n1);
+    } else {
+      ph = to_host_f64<float>(c->phi, n1);
+      dph = to_host_f64<float>(c->dphi, 3 * n1);
+    }
+    remap_csr(perm, iperm, p, ix, {&ph, &dph}, ptr, idx, {phi, dphi}, {n1, n1}, {n1, n1}, {1, 3});
+  });
+}
+
+ff_status ff_export_matrices(const ff_ctx* cc, int64_t* row_ptr, int32_t* col, double* H,
+                             double* M) {
+  ff_ctx* c = const_cast<ff_ctx*>(cc);
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 2, FF_ERR_STATE, "matrices not assembled");
+    FF_REQUIRE(row_ptr && col, FF_ERR_INVALID_ARG, "NULL output");
+    FF_CUDA(cudaStreamSynchronize(c->stream));
+    const size_t n = c->n, n2 = c->n2;
+    auto perm = to_host<int>(c->perm, n);
+    auto iperm = to_host<int>(c->iperm, n);
+    auto p = to_host<long long>(c->a_ptr, n + 1);
+    auto ix = to_host<int>(c->a_col, n2);
+    std::vector<double> v = c->prec == FF_PREC_FP64 ? to_host<double>(c->a_val, 2 * n2)
+                                                    : to_host_f64<float>(c->a_val, 2 * n2);
+    std::vector<double> hv(n2), mv(n2);
+    for (size_t e = 0; e < n2; ++e) {
+      hv[e] = v[2 * e];
+      mv[e] = v[2 * e + 1];
+    }
+    remap_csr(perm, iperm, p, ix, {&hv, &mv}, row_ptr, col, {H, M}, {0, 0}, {0, 0}, {1, 1});
+  });
+}
+
+ff_status ff_apply_operators(ff_ctx* c, const void* X, int m, void* YH, void* YM) {
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 2, FF_ERR_STATE, "matrices not assembled");
+    FF_REQUIRE(X && m >= 1 && m <= 512, FF_ERR_INVALID_ARG, "bad block");
+    const long long n = c->n;
+    auto run = [&](auto tag) {
+      using T = decltype(tag);
+      T* in = reinterpret_cast<T*>(c->scratch[4].ensure(sizeof(T) * n * m));
+      T* oh = reinterpret_cast<T*>(c->scratch[6].ensure(sizeof(T) * n * m));
+      T* om = reinterpret_cast<T*>(c->scratch[7].ensure(sizeof(T) * n * m));
+      ff::gather_block<T>(c, static_cast<const T*>(X), m, in, m);
+      ff::spmm_hm<T>(c, in, m, oh, om, m, m);
+      if (YH) ff::scatter_block<T>(c, oh, m, m, static_cast<T*>(YH));
+      if (YM) ff::scatter_block<T>(c, om, m, m, static_cast<T*>(YM));
+      FF_CUDA(cudaStreamSynchronize(c->stream));
+    };
+    if (c->prec == FF_PREC_FP64)
+      run(double{});
+    else
+      run(float{});
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations of the freeform-gb300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/freeform.h"
+
+namespace ff {
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+  ff_status code;
+  Error(ff_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define FF_CUDA(x)                                                                     \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) {                                                           \
+      throw ::ff::Error(e_ == cudaErrorMemoryAllocation ? FF_ERR_OOM : FF_ERR_CUDA,    \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));              \
+    }                                                                                  \
+  } while (0)
+
+#define FF_LAUNCH_CHECK() FF_CUDA(cudaGetLastError())
+
+#define FF_REQUIRE(cond, code, msg)            \
+  do {                                         \
+    if (!(cond)) throw ::ff::Error(code, msg); \
+  } while (0)
+
+// ---------------------------------------------------------------- device buffer
+// Owning device allocation (cudaMalloc); grows on demand, never shrinks.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void* ensure(size_t b) {
+    if (b == 0) b = 16;
+    if (b > bytes) {
+      release();
+      cudaError_t e = cudaMalloc(&p, b);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        throw Error(FF_ERR_OOM, "cudaMalloc of " + std::to_string(b) + " bytes failed");
+      }
+      bytes = b;
+    }
+    return p;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Device-side error word written by kernels (never a trap).
+struct DevFlags {
+  int code;          // ff_status of the first error a kernel hit (0 = none)
+  int index;         // particle (internal order) or row that raised it
+  int fallback;      // number of moment solves redone in FP64
+  int max_row;       // largest count seen by a pass that reports one
+  double red[8];     // small reductions returned to the host
+};
+
+// Uniform grid used by the neighbour search.
+struct Grid {
+  double origin[3];
+  double h;          // cell edge
+  int dims[3];       // cells per axis
+  int bdims[3];      // 4x4x4-cell bricks per axis
+  long long ncells;  // bdims product * 64 (key space)
+};
+
+}  // namespace ff
+
+// ---------------------------------------------------------------- context
+struct ff_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int prec = FF_PREC_FP32;
+  std::string err;
+  int stage = 0;  // 0 empty, 1 built, 2 assembled
+  int64_t n = 0, n1 = 0, n2 = 0;
+
+  ff::Grid grid{};
+  // particles in internal (cell) order
+  ff::Buf perm;      // int[n]   internal -> caller index
+  ff::Buf iperm;     // int[n]   caller -> internal index
+  ff::Buf pos;       // float4[n] (x, y, z, a)
+  ff::Buf vol;       // float[n]
+  ff::Buf cell_start;// int[ncells + 1]
+  // neighbours (internal order)
+  ff::Buf nbr_ptr;   // int64[n+1]
+  ff::Buf nbr_idx;   // int[n1]
+  ff::Buf nbrT_ptr;  // int64[n+1]  node k -> rows i it covers
+  ff::Buf nbrT_idx;  // int[n1]     row i
+  ff::Buf nbrT_pos;  // int64[n1]   position of k inside row i
+  // shape functions (context precision), aligned with nbr_idx
+  ff::Buf phi;       // T[n1]
+  ff::Buf dphi;      // T[3 * n1]
+  // matrices (internal order), CSR with the diagonal stored
+  ff::Buf a_ptr;     // int64[n+1]
+  ff::Buf a_col;     // int[n2]
+  ff::Buf a_val;     // T2[n2] interleaved (H, M)
+  ff::Buf h_f32;     // float[n2] H values for the preconditioner
+  ff::Buf hdiag_f32; // float[n] diag(H)
+  ff::Buf wh;        // T[n] v_i (lambda_i + 4 mu_i)
+  // device flags
+  ff::Buf flags;     // DevFlags
+  ff::DevFlags* hflags = nullptr;  // pinned mirror
+  // generic scratch
+  ff::Buf scratch[8];
+  // eigen-solver workspace
+  ff::Buf ws[24];
+};
+
+namespace ff {
+
+// ---------------------------------------------------------------- helpers
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+void reset_flags(ff_ctx* c);
+DevFlags read_flags(ff_ctx* c);
+
+// exclusive scan of int counts -> int64 offsets (out has n+1 entries)
+void scan_counts(const int* in, long long* out, long long n, ff_ctx* c, Buf& tmp);
+// exclusive scan of int -> int (out has n+1 entries)
+void scan_counts_i32(const int* in, int* out, long long n, ff_ctx* c, Buf& tmp);
+
+// stages
+void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a, int64_t n);
+void build_shape(ff_ctx* c);
+void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0);
+
+// operator application on internal-order row-major panels
+template <class T>
+void spmm_hm(ff_ctx* c, const T* X, int ldx, T* YH, T* YM, int ldy, int m);
+
+// eigen solver
+ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
+                         double* eigvals, void* modes, ff_eig_report* rep);
+
+}  // namespace ff

@@ -1,0 +1,256 @@
+// Block kernels of the eigensolver: the fused (H_w, M) block product, the
+// Chebyshev preconditioner steps, tall-skinny Gram products and block updates.
+// Panels are row-major n x ld (row k of a block of m columns is contiguous), so
+// a warp reads one row of a block with unit stride.
+#include "linalg.cuh"
+
+namespace ff {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Y_H = H X, Y_M = M X with H in difference form: (H x)_k = sum_l H_kl (x_l - x_k),
+// exact because every row of the stored H sums to zero (the diagonal term
+// multiplies x_k - x_k = 0).  One warp per row; lanes over block columns.
+template <class T>
+__global__ void k_spmm_hm(const long long* __restrict__ ptr, const int* __restrict__ col,
+                          const T* __restrict__ val, long long n, const T* __restrict__ X, int ldx,
+                          T* __restrict__ YH, T* __restrict__ YM, int ldy, int m) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+    const long long s = ptr[k], e = ptr[k + 1];
+    for (int c0 = 0; c0 < m; c0 += 32) {
+      const int cc = c0 + lane;
+      const bool act = cc < m;
+      const T xk = act ? X[k * ldx + cc] : T(0);
+      T ah = T(0), am = T(0);
+      for (long long e0 = s; e0 < e; e0 += 32) {
+        const int cnt = (int)min((long long)32, e - e0);
+        int l_l = 0;
+        T h_l = T(0), m_l = T(0);
+        if (lane < cnt) {
+          l_l = col[e0 + lane];
+          h_l = val[2 * (e0 + lane)];
+          m_l = val[2 * (e0 + lane) + 1];
+        }
+        for (int j = 0; j < cnt; ++j) {
+          const int l = __shfl_sync(kFull, l_l, j);
+          const T h = __shfl_sync(kFull, h_l, j);
+          const T mm = __shfl_sync(kFull, m_l, j);
+          if (act) {
+            const T xl = X[(long long)l * ldx + cc];
+            ah += h * (xl - xk);
+            am += mm * xl;
+          }
+        }
+      }
+      if (act) {
+        if (YH) YH[k * ldy + cc] = ah;
+        if (YM) YM[k * ldy + cc] = am;
+      }
+    }
+  }
+}
+
+// One Chebyshev step on D^-1 H (FP32):  res -= D^-1 H d_in;  d_out = c1 d_in + c2 res;
+// x += d_out.  (H d)_k in difference form as above.
+__global__ void k_cheb_step(const long long* __restrict__ ptr, const int* __restrict__ col,
+                            const float* __restrict__ hv, const float* __restrict__ hdiag,
+                            long long n, int m, int ld, const float* __restrict__ din,
+                            float* __restrict__ dout, float* __restrict__ x,
+                            float* __restrict__ res, float c1, float c2) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+    const long long s = ptr[k], e = ptr[k + 1];
+    const float dinv = 1.0f / hdiag[k];
+    for (int c0 = 0; c0 < m; c0 += 32) {
+      const int cc = c0 + lane;
+      const bool act = cc < m;
+      const long long o = k * ld + cc;
+      const float dk = act ? din[o] : 0.f;
+      float acc = 0.f;
+      for (long long e0 = s; e0 < e; e0 += 32) {
+        const int cnt = (int)min((long long)32, e - e0);
+        int l_l = 0;
+        float h_l = 0.f;
+        if (lane < cnt) {
+          l_l = col[e0 + lane];
+          h_l = hv[e0 + lane];
+        }
+        for (int j = 0; j < cnt; ++j) {
+          const int l = __shfl_sync(kFull, l_l, j);
+          const float h = __shfl_sync(kFull, h_l, j);
+          if (act) acc += h * (din[(long long)l * ld + cc] - dk);
+        }
+      }
+      if (act) {
+        const float r = res[o] - acc * dinv;
+        const float dn = c1 * dk + c2 * r;
+        res[o] = r;
+        dout[o] = dn;
+        x[o] += dn;
+      }
+    }
+  }
+}
+
+// Gram partials: P[blk][i][j] = sum_{rows in chunk} A[r][ia + i] * B[r][ib + j]
+// (p x q outputs in 32 x 32 tiles; grid.x = row chunks, grid.y = output tiles).
+// Accumulates in T inside the chunk, the cross-chunk sum is FP64 (k_gram_reduce).
+template <class T>
+__global__ void k_gram_partial(const T* __restrict__ A, int lda, int p, const T* __restrict__ B,
+                               int ldb, int q, long long n, long long rows_per_chunk,
+                               double* __restrict__ part) {
+  __shared__ T sa[32][33];
+  __shared__ T sb[32][33];
+  const int tilesq = (q + 31) / 32;
+  const int ti = blockIdx.y / tilesq, tj = blockIdx.y % tilesq;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const long long r0 = (long long)blockIdx.x * rows_per_chunk;
+  const long long r1 = min(n, r0 + rows_per_chunk);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (long long rb = r0; rb < r1; rb += 32) {
+    // load 32 rows x 32 cols of A and B
+    for (int rr = ty; rr < 32; rr += 8) {
+      const long long r = rb + rr;
+      const int ia = ti * 32 + tx, ib = tj * 32 + tx;
+      sa[rr][tx] = (r < r1 && ia < p) ? A[r * lda + ia] : T(0);
+      sb[rr][tx] = (r < r1 && ib < q) ? B[r * ldb + ib] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      const T bv = sb[rr][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += sa[rr][ty + 8 * u] * bv;
+    }
+    __syncthreads();
+  }
+  const int jj = tj * 32 + tx;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int ii = ti * 32 + ty + 8 * u;
+    if (ii < p && jj < q) part[((long long)blockIdx.x * p + ii) * q + jj] = (double)acc[u];
+  }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int pq,
+                              double* __restrict__ out, double alpha, int accumulate) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= pq) return;
+  double s = 0.0;
+  for (int c = 0; c < chunks; ++c) s += part[(long long)c * pq + t];
+  out[t] = accumulate ? out[t] + alpha * s : alpha * s;
+}
+
+// C[r][cmap(j)] = beta * C[...] + sum_i A[r][i] * Y[i][j]; cmap sends columns
+// j < split to C + j and j >= split to C + off2 + (j - split).
+// One warp per row, lanes over 32 columns of the tile; Y tile staged in shared memory.
+template <class T>
+__global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T* __restrict__ Y,
+                               int q, T* __restrict__ C, int ldc, long long n, T beta, int split,
+                               int off2) {
+  extern __shared__ unsigned char smraw[];
+  T* sy = reinterpret_cast<T*>(smraw);  // p x 32
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int j = blockIdx.y * 32 + lane;
+  for (int t = threadIdx.x; t < p * 32; t += blockDim.x) {
+    const int i = t / 32, jj = blockIdx.y * 32 + (t % 32);
+    sy[t] = jj < q ? Y[(long long)i * q + jj] : T(0);
+  }
+  __syncthreads();
+  const int cj = j < split ? j : off2 + (j - split);
+  for (long long r = (long long)blockIdx.x * wpb + wid; r < n; r += (long long)gridDim.x * wpb) {
+    const T* a = A + r * lda;
+    T acc = T(0);
+    int i = 0;
+    for (; i + 4 <= p; i += 4) {
+      acc += a[i] * sy[i * 32 + lane] + a[i + 1] * sy[(i + 1) * 32 + lane] +
+             a[i + 2] * sy[(i + 2) * 32 + lane] + a[i + 3] * sy[(i + 3) * 32 + lane];
+    }
+    for (; i < p; ++i) acc += a[i] * sy[i * 32 + lane];
+    if (j < q) {
+      T* cp = C + r * ldc + cj;
+      *cp = beta == T(0) ? acc : beta * *cp + acc;
+    }
+  }
+}
+
+}  // namespace
+
+template <class T>
+void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T* val, long long n,
+                 const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
+  const int T_ = 256;
+  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
+  k_spmm_hm<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m);
+  FF_LAUNCH_CHECK();
+}
+
+void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const float* hv,
+               const float* hdiag, long long n, int m, int ld, const float* din, float* dout,
+               float* x, float* res, float c1, float c2) {
+  const int T_ = 256;
+  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
+  k_cheb_step<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, hv, hdiag, n, m, ld, din, dout, x, res,
+                                               c1, c2);
+  FF_LAUNCH_CHECK();
+}
+
+template <class T>
+void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int q, long long n,
+          double* out, double alpha, bool accumulate, Buf& part) {
+  if (p <= 0 || q <= 0) return;
+  const int tiles = ((p + 31) / 32) * ((q + 31) / 32);
+  long long chunks = std::max<long long>(1, std::min<long long>((n + 511) / 512, 2048 / tiles + 1));
+  long long rpc = (n + chunks - 1) / chunks;
+  rpc = (rpc + 31) / 32 * 32;
+  chunks = std::max<long long>(1, (n + rpc - 1) / rpc);
+  double* pp = reinterpret_cast<double*>(part.ensure(sizeof(double) * chunks * p * q));
+  dim3 grid((unsigned)chunks, (unsigned)tiles);
+  k_gram_partial<T><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp);
+  FF_LAUNCH_CHECK();
+  k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, p * q, out, alpha,
+                                                    accumulate ? 1 : 0);
+  FF_LAUNCH_CHECK();
+}
+
+template <class T>
+void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q, T* C, int ldc,
+                  long long n, T beta, int split, int off2) {
+  if (q <= 0 || n <= 0) return;
+  if (p <= 0) {
+    // C = beta * C only; p == 0 never happens in the solver
+    return;
+  }
+  const int wpb = 8;
+  size_t smem = sizeof(T) * (size_t)p * 32;
+  static bool attr_set[2] = {false, false};
+  if (smem > 48 * 1024 && !attr_set[sizeof(T) == 8]) {
+    FF_CUDA(cudaFuncSetAttribute(k_block_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    attr_set[sizeof(T) == 8] = true;
+  }
+  dim3 grid((unsigned)std::min<long long>((n + wpb - 1) / wpb, 152LL * 16),
+            (unsigned)((q + 31) / 32));
+  k_block_update<T><<<grid, 32 * wpb, smem, st>>>(A, lda, p, Y, q, C, ldc, n, beta,
+                                                  split < 0 ? q : split, off2);
+  FF_LAUNCH_CHECK();
+}
+
+template void spmm_hm_raw<float>(cudaStream_t, const long long*, const int*, const float*,
+                                 long long, const float*, int, float*, float*, int, int);
+template void spmm_hm_raw<double>(cudaStream_t, const long long*, const int*, const double*,
+                                  long long, const double*, int, double*, double*, int, int);
+template void gram<float>(cudaStream_t, const float*, int, int, const float*, int, int, long long,
+                          double*, double, bool, Buf&);
+template void gram<double>(cudaStream_t, const double*, int, int, const double*, int, int,
+                           long long, double*, double, bool, Buf&);
+template void block_update<float>(cudaStream_t, const float*, int, int, const float*, int, float*,
+                                  int, long long, float, int, int);
+template void block_update<double>(cudaStream_t, const double*, int, int, const double*, int,
+                                   double*, int, long long, double, int, int);
+
+}  // namespace ff

@@ -1,0 +1,37 @@
+// Block linear-algebra launchers used by the eigensolver (internal).
+#pragma once
+
+#include "ff_internal.cuh"
+
+namespace ff {
+
+template <class T>
+void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T* val, long long n,
+                 const T* X, int ldx, T* YH, T* YM, int ldy, int m);
+
+void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const float* hv,
+               const float* hdiag, long long n, int m, int ld, const float* din, float* dout,
+               float* x, float* res, float c1, float c2);
+
+// out (p x q, row-major, FP64) (+)= alpha * A^T B over n rows
+template <class T>
+void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int q, long long n,
+          double* out, double alpha, bool accumulate, Buf& part);
+
+// C (n x q, with the column split described in linalg.cu) = beta C + A Y, Y p x q row-major
+template <class T>
+void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q, T* C, int ldc,
+                  long long n, T beta, int split = -1, int off2 = 0);
+
+// small dense Rayleigh-Ritz (dense.cu)
+struct RRDims {
+  int ns;   // basis columns used (nx + nw + np)
+  int nx;   // columns of X at the front
+  int nb;   // Ritz vectors kept
+  int want_p;  // 1: also build the P coefficients Z
+};
+template <class T>
+void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ,
+                   double* theta, int* dropped, Buf& work, bool fp64);
+
+}  // namespace ff

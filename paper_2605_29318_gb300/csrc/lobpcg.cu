@@ -1,0 +1,508 @@
+// Block eigensolver for the k lowest pairs of H_w c = lambda M c (Sec. 3.2,
+// Eq. 15; Supp. Sec. B "Eigenanalysis" solves the same problem with LOBPCG).
+//
+// Locally optimal block preconditioned conjugate gradient with an explicit
+// M-orthonormal basis [X | W | P]:
+//   * the constant mode c0 = 1 / sqrt(1^T M 1) is set analytically (it is an
+//     exact null vector of the stored H_w) and deflated from every block;
+//   * W = T R, R = H X - M X Theta, with T a Chebyshev polynomial in D^-1 H
+//     (D = diag H) approximating H^+ on [beta / ratio, beta] -- FP32 and
+//     free of reductions; beta from power iteration capped by Gershgorin;
+//   * W is M-projected against X, P and c0 with the blocks M X, M P kept
+//     from earlier products, then (H W, M W) comes from one fused pass;
+//   * Rayleigh-Ritz on the Gram matrices of the basis (dense.cu) returns the
+//     coefficients of the new X and of the new momentum P (already
+//     M-orthonormal and M-orthogonal to X), and one block update forms
+//     X, P, H X, H P, M X, M P from the old panels;
+//   * columns whose relative residual meets tol stop contributing to W.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "linalg.cuh"
+
+namespace ff {
+namespace {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+template <class T>
+__global__ void k_random_block(T* X, int ld, long long n, int m, unsigned long long seed,
+                               const int* perm) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  long long r = t / m;
+  int c = (int)(t % m);
+  unsigned long long h = mix64(seed * 0x100000001b3ULL + (unsigned long long)perm[r] * 1024ULL + c);
+  double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+  X[r * ld + c] = (T)(2.0 * u - 1.0);
+}
+
+template <class T>
+__global__ void k_gather_block(const T* __restrict__ X0, long long n, int m,
+                               const int* __restrict__ perm, T* __restrict__ X, int ld) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  long long r = t / m;
+  int c = (int)(t % m);
+  X[r * ld + c] = X0[(long long)c * n + perm[r]];
+}
+
+template <class T>
+__global__ void k_scatter_block(const T* __restrict__ X, int ld, long long n, int m,
+                                const int* __restrict__ perm, T* __restrict__ out, long long ldo,
+                                int col0) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  long long r = t / m;
+  int c = (int)(t % m);
+  out[(long long)(c + col0) * ldo + perm[r]] = X[r * ld + c];
+}
+
+template <class T>
+__global__ void k_fill(T* x, long long n, T v) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+template <class T>
+__global__ void k_scale(T* x, long long n, const double* s, int mode) {
+  // mode 0: x *= 1/sqrt(s[0]);  mode 1: x *= s[0]
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (T)((double)x[i] * (mode == 0 ? 1.0 / sqrt(s[0]) : s[0]));
+}
+
+template <class T>
+__global__ void k_d2t(const double* in, T* out, int count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = (T)in[i];
+}
+
+// column sums of squares of R = HX - MX theta and of MX (FP64 accumulation)
+template <class T>
+__global__ void k_resid_norms(const T* __restrict__ HX, const T* __restrict__ MX, int ld,
+                              const double* __restrict__ theta, long long n, int m,
+                              double* __restrict__ norms) {
+  const int c = threadIdx.x & 31;
+  const int col = blockIdx.y * 32 + c;
+  double a = 0.0, b = 0.0;
+  if (col < m) {
+    const double th = theta[col];
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n;
+         r += (long long)gridDim.x * (blockDim.x >> 5)) {
+      const double mx = (double)MX[r * ld + col];
+      const double rr = (double)HX[r * ld + col] - th * mx;
+      a += rr * rr;
+      b += mx * mx;
+    }
+  }
+  __shared__ double sa[32][33], sb[32][33];
+  sa[threadIdx.x >> 5][c] = a;
+  sb[threadIdx.x >> 5][c] = b;
+  __syncthreads();
+  if (threadIdx.x < 32 && col < m) {
+    double ta = 0, tb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      ta += sa[w][c];
+      tb += sb[w][c];
+    }
+    atomicAdd(&norms[col], ta);
+    atomicAdd(&norms[m + col], tb);
+  }
+}
+
+// Chebyshev start: b = active * (HX - MX theta) / diag(H); res = b; d = b / theta_c; x = d
+template <class T>
+__global__ void k_cheb_init(const T* __restrict__ HX, const T* __restrict__ MX, int ld,
+                            const double* __restrict__ theta, const int* __restrict__ active,
+                            const float* __restrict__ hdiag, long long n, int m,
+                            float* __restrict__ res, float* __restrict__ d, float* __restrict__ x,
+                            float inv_tc) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  long long r = t / m;
+  int c = (int)(t % m);
+  float b = 0.f;
+  if (active[c]) {
+    double rr = (double)HX[r * ld + c] - theta[c] * (double)MX[r * ld + c];
+    b = (float)(rr / (double)hdiag[r]);
+  }
+  res[t] = b;
+  d[t] = b * inv_tc;
+  x[t] = b * inv_tc;
+}
+
+template <class T>
+__global__ void k_cast_block(const float* __restrict__ x, long long n, int m, T* __restrict__ W,
+                             int ld) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  long long r = t / m;
+  int c = (int)(t % m);
+  W[r * ld + c] = (T)x[t];
+}
+
+__global__ void k_gershgorin(const long long* __restrict__ ptr, const float* __restrict__ hv,
+                             const float* __restrict__ hdiag, long long n, unsigned int* out) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float g = 0.f;
+  if (k < n) {
+    float s = 0.f;
+    for (long long e = ptr[k]; e < ptr[k + 1]; ++e) s += fabsf(hv[e]);
+    g = s / fabsf(hdiag[k]);
+  }
+  for (int o = 16; o; o >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(g));
+}
+
+}  // namespace
+
+template <class T>
+struct Solver {
+  ff_ctx* c;
+  cudaStream_t st;
+  long long n;
+  int nb, kw, ld;
+  bool fp64;
+  T *S[2], *HS[2], *MS[2];
+  T *c0, *Mc0;
+  float *cres, *cd0, *cd1, *cx;
+  double *Ag, *Bg, *G1, *theta_d, *norms_d;
+  T *Gt, *YZ;
+  int *dropped_d, *active_d;
+  double* h_pin;  // pinned: norms (2 nb) | theta (nb) | misc
+  int spmm_calls = 0, spmv_calls = 0;
+
+  T* col(T* panel, int c0_) { return panel + c0_; }
+
+  void alloc() {
+    ld = ((3 * nb + 3) / 4) * 4;
+    for (int b = 0; b < 2; ++b) {
+      S[b] = reinterpret_cast<T*>(c->ws[0 + b].ensure(sizeof(T) * n * ld));
+      HS[b] = reinterpret_cast<T*>(c->ws[2 + b].ensure(sizeof(T) * n * ld));
+      MS[b] = reinterpret_cast<T*>(c->ws[4 + b].ensure(sizeof(T) * n * ld));
+    }
+    c0 = reinterpret_cast<T*>(c->ws[6].ensure(sizeof(T) * n));
+    Mc0 = reinterpret_cast<T*>(c->ws[7].ensure(sizeof(T) * n));
+    cres = reinterpret_cast<float*>(c->ws[8].ensure(sizeof(float) * n * nb));
+    cd0 = reinterpret_cast<float*>(c->ws[9].ensure(sizeof(float) * n * nb));
+    cd1 = reinterpret_cast<float*>(c->ws[10].ensure(sizeof(float) * n * nb));
+    cx = reinterpret_cast<float*>(c->ws[11].ensure(sizeof(float) * n * nb));
+    const int ns = 3 * nb;
+    Ag = reinterpret_cast<double*>(c->ws[12].ensure(sizeof(double) * ns * ns));
+    Bg = reinterpret_cast<double*>(c->ws[13].ensure(sizeof(double) * ns * ns));
+    G1 = reinterpret_cast<double*>(c->ws[14].ensure(sizeof(double) * (2 * nb + 2) * nb));
+    theta_d = reinterpret_cast<double*>(c->ws[15].ensure(sizeof(double) * (nb + 8)));
+    norms_d = reinterpret_cast<double*>(c->ws[16].ensure(sizeof(double) * 2 * nb));
+    Gt = reinterpret_cast<T*>(c->ws[17].ensure(sizeof(T) * (2 * nb + 2) * nb));
+    YZ = reinterpret_cast<T*>(c->ws[18].ensure(sizeof(T) * ns * 2 * nb));
+    dropped_d = reinterpret_cast<int*>(c->ws[19].ensure(sizeof(int) * 4));
+    active_d = reinterpret_cast<int*>(c->ws[20].ensure(sizeof(int) * nb));
+    h_pin = reinterpret_cast<double*>(c->hflags) + 16;  // pinned scratch after the flags
+  }
+
+  void spmm(const T* X, T* YH, T* YM, int m) {
+    spmm_hm_raw<T>(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->a_val.as<T>(), n, X, ld,
+                   YH, YM, ld, m);
+    ++spmm_calls;
+  }
+
+  // C(:, cols) += A (p cols) * G  where G = -coeffs (already negated, FP64 p x q)
+  void apply_coeffs(const T* A, int lda, int p, const double* Gd, int q, T* C, int ldc) {
+    k_d2t<T><<<(p * q + 255) / 256, 256, 0, st>>>(Gd, Gt, p * q);
+    block_update<T>(st, A, lda, p, Gt, q, C, ldc, n, T(1));
+  }
+
+  void deflate(T* X, int m) {
+    // X -= c0 (Mc0^T X)
+    gram<T>(st, Mc0, 1, 1, X, ld, m, n, G1, -1.0, false, c->scratch[0]);
+    apply_coeffs(c0, 1, 1, G1, m, X, ld);
+  }
+};
+
+template <class T>
+ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eigvals, T* modes,
+                ff_eig_report* rep) {
+  using clock = std::chrono::steady_clock;
+  const auto t_start = clock::now();
+  Solver<T> s;
+  s.c = c;
+  s.st = c->stream;
+  s.n = c->n;
+  s.fp64 = c->prec == FF_PREC_FP64;
+  const bool incl_c0 = !o.exclude_constant;
+  s.kw = incl_c0 ? k - 1 : k;
+  s.nb = std::min<long long>(s.kw + std::max(0, o.guard), (s.n - 1) / 3);
+  FF_REQUIRE(s.nb >= s.kw && s.nb >= 1, FF_ERR_INVALID_ARG,
+             "too few particles for the requested number of modes");
+  s.alloc();
+  cudaStream_t st = s.st;
+  const long long n = s.n;
+  const int nb = s.nb, ld = s.ld;
+  const int TB = 256;
+  auto blocks = [&](long long work) { return (unsigned)((work + TB - 1) / TB); };
+
+  // ---- constant mode: c0 = 1 / sqrt(1^T M 1)
+  k_fill<T><<<blocks(n), TB, 0, st>>>(s.c0, n, T(1));
+  spmm_hm_raw<T>(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->a_val.as<T>(), n, s.c0, 1,
+                 nullptr, s.Mc0, 1, 1);
+  gram<T>(st, s.c0, 1, 1, s.Mc0, 1, 1, n, s.G1, 1.0, false, c->scratch[0]);
+  k_scale<T><<<blocks(n), TB, 0, st>>>(s.c0, n, s.G1, 0);
+  k_scale<T><<<blocks(n), TB, 0, st>>>(s.Mc0, n, s.G1, 0);
+  FF_LAUNCH_CHECK();
+
+  // ---- Chebyshev interval on D^-1 H
+  double beta = 0.0, alpha = 0.0;
+  const int deg = std::max(0, o.cheb_degree);
+  if (deg > 1) {
+    unsigned int* gmax = reinterpret_cast<unsigned int*>(s.dropped_d + 2);
+    FF_CUDA(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
+    k_gershgorin<<<blocks(n), TB, 0, st>>>(c->a_ptr.as<long long>(), c->h_f32.as<float>(),
+                                           c->hdiag_f32.as<float>(), n, gmax);
+    // power iteration on one column (reuses the Chebyshev step with res = 0)
+    k_random_block<float><<<blocks(n), TB, 0, st>>>(s.cd0, 1, n, 1, o.seed + 7, c->perm.as<int>());
+    FF_CUDA(cudaMemsetAsync(s.cres, 0, sizeof(float) * n, st));
+    double est = 0.0;
+    float* a = s.cd0;
+    float* b = s.cd1;
+    for (int it = 0; it < 24; ++it) {
+      FF_CUDA(cudaMemsetAsync(s.cres, 0, sizeof(float) * n, st));
+      cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
+                c->hdiag_f32.as<float>(), n, 1, 1, a, b, s.cx, s.cres, 0.f, -1.f);
+      gram<float>(st, a, 1, 1, a, 1, 1, n, s.G1, 1.0, false, c->scratch[0]);
+      gram<float>(st, b, 1, 1, b, 1, 1, n, s.G1 + 1, 1.0, false, c->scratch[0]);
+      gram<float>(st, a, 1, 1, b, 1, 1, n, s.G1 + 2, 1.0, false, c->scratch[0]);
+      // normalise b into a
+      k_scale<float><<<blocks(n), TB, 0, st>>>(b, n, s.G1 + 1, 0);
+      std::swap(a, b);
+    }
+    double hb[3];
+    unsigned int hg = 0;
+    FF_CUDA(cudaMemcpyAsync(hb, s.G1, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    FF_CUDA(cudaMemcpyAsync(&hg, gmax, sizeof(hg), cudaMemcpyDeviceToHost, st));
+    FF_CUDA(cudaStreamSynchronize(st));
+    est = std::sqrt(hb[1] / hb[0]);  // growth of the last power step
+    float gf;
+    memcpy(&gf, &hg, sizeof(gf));
+    beta = std::min(1.2 * est, (double)gf);
+    if (!(beta > 0)) beta = gf;
+    alpha = beta / std::max(2.0, o.cheb_ratio);
+  }
+
+  // ---- starting block
+  int warm = 0;
+  if (X0) {
+    k_gather_block<T><<<blocks(n * nb), TB, 0, st>>>(X0, n, nb, c->perm.as<int>(), s.S[0], ld);
+    warm = 1;
+  } else {
+    k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[0], ld, n, nb, o.seed,
+                                                     c->perm.as<int>());
+  }
+  FF_LAUNCH_CHECK();
+  int cur = 0;
+  RRDims d0{nb, nb, nb, 0};
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    s.deflate(s.S[cur], nb);
+    s.spmm(s.S[cur], s.HS[cur], s.MS[cur], nb);
+    gram<T>(st, s.S[cur], ld, nb, s.HS[cur], ld, nb, n, s.Ag, 1.0, false, c->scratch[0]);
+    gram<T>(st, s.S[cur], ld, nb, s.MS[cur], ld, nb, n, s.Bg, 1.0, false, c->scratch[0]);
+    rayleigh_ritz<T>(st, s.Ag, s.Bg, d0, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.fp64);
+    int dropped = 0;
+    FF_CUDA(cudaMemcpyAsync(&dropped, s.dropped_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FF_CUDA(cudaStreamSynchronize(st));
+    if (dropped == 0 || attempt == 1) break;
+    // rank-deficient warm start: fall back to the seeded random block
+    k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[cur], ld, n, nb, o.seed,
+                                                     c->perm.as<int>());
+    warm = 0;
+  }
+  {
+    const int nxt = 1 - cur;
+    block_update<T>(st, s.S[cur], ld, nb, s.YZ, 2 * nb, s.S[nxt], ld, n, T(0), nb, 2 * nb);
+    block_update<T>(st, s.HS[cur], ld, nb, s.YZ, 2 * nb, s.HS[nxt], ld, n, T(0), nb, 2 * nb);
+    block_update<T>(st, s.MS[cur], ld, nb, s.YZ, 2 * nb, s.MS[nxt], ld, n, T(0), nb, 2 * nb);
+    cur = nxt;
+  }
+
+  // ---- iterations
+  std::vector<int> active(nb, 1);
+  std::vector<double> res(nb, 1.0), theta(nb, 0.0);
+  bool has_p = false;
+  int it = 0;
+  ff_status status = FF_ERR_NOT_CONVERGED;
+  const double th_c = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+  for (;; ++it) {
+    FF_CUDA(cudaMemsetAsync(s.norms_d, 0, sizeof(double) * 2 * nb, st));
+    dim3 gn((unsigned)std::min<long long>((n + 31) / 32, 512), (unsigned)((nb + 31) / 32));
+    k_resid_norms<T><<<gn, 1024, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d, n, nb, s.norms_d);
+    FF_LAUNCH_CHECK();
+    FF_CUDA(cudaMemcpyAsync(s.h_pin, s.norms_d, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, st));
+    FF_CUDA(cudaMemcpyAsync(s.h_pin + 2 * nb, s.theta_d, sizeof(double) * nb,
+                            cudaMemcpyDeviceToHost, st));
+    FF_CUDA(cudaStreamSynchronize(st));
+    int conv = 0;
+    double worst = 0.0;
+    bool bad = false;
+    for (int j = 0; j < nb; ++j) {
+      theta[j] = s.h_pin[2 * nb + j];
+      double r = std::sqrt(s.h_pin[j]) / (std::fabs(theta[j]) * std::sqrt(s.h_pin[nb + j]));
+      if (!std::isfinite(r)) {
+        if (!std::isfinite(theta[j]) || !std::isfinite(s.h_pin[j])) bad = true;
+        r = 1.0;
+      }
+      res[j] = r;
+      active[j] = r > o.tol;
+      if (j < s.kw) {
+        conv += r <= o.tol;
+        worst = std::max(worst, r);
+      }
+    }
+    if (o.verbose)
+      fprintf(stderr, "[eigenmodes] it %d  max res %.3e  converged %d/%d\n", it, worst, conv, s.kw);
+    if (bad) {
+      status = FF_ERR_NUMERIC;
+      break;
+    }
+    if (conv == s.kw) {
+      status = FF_OK;
+      break;
+    }
+    if (it >= o.max_iter) {
+      status = FF_ERR_NOT_CONVERGED;
+      break;
+    }
+    if (o.time_budget_s > 0 &&
+        std::chrono::duration<double>(clock::now() - t_start).count() > o.time_budget_s) {
+      status = FF_ERR_TIMEOUT;
+      break;
+    }
+    FF_CUDA(cudaMemcpyAsync(s.active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+
+    // W = T R  (FP32 Chebyshev polynomial in D^-1 H, or Jacobi when deg <= 1)
+    T* W = s.S[cur] + nb;
+    k_cheb_init<T><<<blocks(n * nb), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d, s.active_d,
+                                                  c->hdiag_f32.as<float>(), n, nb, s.cres, s.cd0,
+                                                  s.cx, deg > 1 ? (float)(1.0 / th_c) : 1.f);
+    FF_LAUNCH_CHECK();
+    if (deg > 1) {
+      const double sigma1 = th_c / delta;
+      double rho = 1.0 / sigma1;
+      float* din = s.cd0;
+      float* dout = s.cd1;
+      for (int j = 1; j < deg; ++j) {
+        const double rn = 1.0 / (2.0 * sigma1 - rho);
+        cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
+                  c->hdiag_f32.as<float>(), n, nb, nb, din, dout, s.cx, s.cres,
+                  (float)(rn * rho), (float)(2.0 * rn / delta));
+        ++s.spmv_calls;
+        rho = rn;
+        std::swap(din, dout);
+      }
+    }
+    k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, n, nb, W, ld);
+    FF_LAUNCH_CHECK();
+    // M-project W against X, P and c0 (with the stored M X, M P, M c0)
+    s.deflate(W, nb);
+    gram<T>(st, s.MS[cur], ld, nb, W, ld, nb, n, s.G1, -1.0, false, c->scratch[0]);
+    s.apply_coeffs(s.S[cur], ld, nb, s.G1, nb, W, ld);
+    if (has_p) {
+      gram<T>(st, s.MS[cur] + 2 * nb, ld, nb, W, ld, nb, n, s.G1, -1.0, false, c->scratch[0]);
+      s.apply_coeffs(s.S[cur] + 2 * nb, ld, nb, s.G1, nb, W, ld);
+    }
+    s.spmm(W, s.HS[cur] + nb, s.MS[cur] + nb, nb);
+    const int ns = has_p ? 3 * nb : 2 * nb;
+    gram<T>(st, s.S[cur], ld, ns, s.HS[cur], ld, ns, n, s.Ag, 1.0, false, c->scratch[0]);
+    gram<T>(st, s.S[cur], ld, ns, s.MS[cur], ld, ns, n, s.Bg, 1.0, false, c->scratch[0]);
+    RRDims dd{ns, nb, nb, 1};
+    rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.fp64);
+    const int nxt = 1 - cur;
+    block_update<T>(st, s.S[cur], ld, ns, s.YZ, 2 * nb, s.S[nxt], ld, n, T(0), nb, 2 * nb);
+    block_update<T>(st, s.HS[cur], ld, ns, s.YZ, 2 * nb, s.HS[nxt], ld, n, T(0), nb, 2 * nb);
+    block_update<T>(st, s.MS[cur], ld, ns, s.YZ, 2 * nb, s.MS[nxt], ld, n, T(0), nb, 2 * nb);
+    cur = nxt;
+    has_p = true;
+  }
+
+  // ---- eigenvalues as Rayleigh quotients of the final block (FP64-accumulated)
+  const int kw = s.kw;
+  std::vector<double> hq(2 * (size_t)kw * kw);
+  gram<T>(st, s.S[cur], ld, kw, s.HS[cur], ld, kw, n, s.Ag, 1.0, false, c->scratch[0]);
+  gram<T>(st, s.S[cur], ld, kw, s.MS[cur], ld, kw, n, s.Bg, 1.0, false, c->scratch[0]);
+  FF_CUDA(cudaMemcpyAsync(hq.data(), s.Ag, sizeof(double) * kw * kw, cudaMemcpyDeviceToHost, st));
+  FF_CUDA(cudaMemcpyAsync(hq.data() + (size_t)kw * kw, s.Bg, sizeof(double) * kw * kw,
+                          cudaMemcpyDeviceToHost, st));
+  FF_CUDA(cudaStreamSynchronize(st));
+  int out = 0;
+  if (incl_c0) eigvals[out++] = 0.0;
+  for (int j = 0; j < kw; ++j)
+    eigvals[out++] = hq[(size_t)j * kw + j] / hq[(size_t)kw * kw + (size_t)j * kw + j];
+  if (modes) {
+    int col0 = 0;
+    if (incl_c0) {
+      k_scatter_block<T><<<blocks(n), TB, 0, st>>>(s.c0, 1, n, 1, c->perm.as<int>(), modes, n, 0);
+      col0 = 1;
+    }
+    k_scatter_block<T><<<blocks(n * kw), TB, 0, st>>>(s.S[cur], ld, n, kw, c->perm.as<int>(),
+                                                      modes, n, col0);
+    FF_LAUNCH_CHECK();
+  }
+  FF_CUDA(cudaStreamSynchronize(st));
+  if (rep) {
+    rep->iterations = it;
+    int conv = incl_c0 ? 1 : 0;
+    double worst = 0.0;
+    for (int j = 0; j < kw; ++j) {
+      conv += res[j] <= o.tol;
+      worst = std::max(worst, res[j]);
+    }
+    rep->converged = conv;
+    rep->spmm_calls = s.spmm_calls;
+    rep->precond_spmv_calls = s.spmv_calls;
+    rep->max_residual = worst;
+    rep->seconds = std::chrono::duration<double>(clock::now() - t_start).count();
+    rep->warm_start_used = warm;
+  }
+  return status;
+}
+
+ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0, double* eigvals,
+                         void* modes, ff_eig_report* rep) {
+  if (c->prec == FF_PREC_FP64)
+    return solve<double>(c, k, o, static_cast<const double*>(X0), eigvals,
+                         static_cast<double*>(modes), rep);
+  return solve<float>(c, k, o, static_cast<const float*>(X0), eigvals, static_cast<float*>(modes),
+                      rep);
+}
+
+template <class T>
+void spmm_hm(ff_ctx* c, const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
+  spmm_hm_raw<T>(c->stream, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->a_val.as<T>(), c->n,
+                 X, ldx, YH, YM, ldy, m);
+}
+template void spmm_hm<float>(ff_ctx*, const float*, int, float*, float*, int, int);
+template void spmm_hm<double>(ff_ctx*, const double*, int, double*, double*, int, int);
+
+// caller-order column-major block <-> internal row-major panel (used by ff_apply_operators)
+template <class T>
+void gather_block(ff_ctx* c, const T* X0, int m, T* X, int ld) {
+  k_gather_block<T><<<(unsigned)((c->n * m + 255) / 256), 256, 0, c->stream>>>(
+      X0, c->n, m, c->perm.as<int>(), X, ld);
+  FF_LAUNCH_CHECK();
+}
+template <class T>
+void scatter_block(ff_ctx* c, const T* X, int ld, int m, T* out) {
+  k_scatter_block<T><<<(unsigned)((c->n * m + 255) / 256), 256, 0, c->stream>>>(
+      X, ld, c->n, m, c->perm.as<int>(), out, c->n, 0);
+  FF_LAUNCH_CHECK();
+}
+template void gather_block<float>(ff_ctx*, const float*, int, float*, int);
+template void gather_block<double>(ff_ctx*, const double*, int, double*, int);
+template void scatter_block<float>(ff_ctx*, const float*, int, int, float*);
+template void scatter_block<double>(ff_ctx*, const double*, int, int, double*);
+
+}  // namespace ff

@@ -1,0 +1,94 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every
+function that include/freeform.h declares; the ctypes structures match the
+header's field lists.  No CUDA call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "freeform.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_29318_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding.load_library()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "defined")))
+
+
+def test_header_declares_the_paper_calls():
+    names = _declared_functions()
+    for n in ("rkpm_build", "assemble_hessian", "eigenmodes"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2605_29318_gb300 import binding
+    names = _declared_functions()
+    assert sorted(binding.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_string(lib):
+    assert lib.ff_version().decode().startswith("freeform-gb300")
+
+
+def _struct_fields(name):
+    text = open(HEADER).read()
+    m = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text)
+    body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+    return [re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*;", l)[0]
+            for l in body.split("\n") if ";" in l]
+
+
+def test_ctypes_structs_match_header():
+    from paper_2605_29318_gb300 import binding
+    assert [f for f, _ in binding.EigOpts._fields_] == _struct_fields("ff_eig_opts")
+    assert [f for f, _ in binding.EigReport._fields_] == _struct_fields("ff_eig_report")
+
+
+def test_default_options_without_gpu(lib):
+    from paper_2605_29318_gb300 import binding
+    o = binding.default_opts()
+    assert o.tol == 1e-6 and o.max_iter == 500 and o.cheb_degree == 16 and o.guard == 8
+
+
+def test_create_without_device_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = lib.ff_create(ctypes.byref(h), 0, None, 0)
+    assert st != 0 and not h.value
+    assert lib.ff_create(None, 0, None, 0) == 1
+    assert lib.ff_create(ctypes.byref(h), 0, None, 7) == 1
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.rkpm_build(None, None, None, None, 10) == 1
+    assert lib.assemble_hessian(None, None, None, 1.0, 0.3) == 1
+    assert lib.eigenmodes(None, 3, None, None, None, None, None) == 1
+    assert lib.ff_get_sizes(None, None, None, None) == 1
+
+
+def test_no_fallback_without_library(tmp_path):
+    from paper_2605_29318_gb300 import binding
+    saved = binding._lib
+    binding._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            binding.load_library(str(tmp_path / "missing.so"))
+    finally:
+        binding._lib = saved

@@ -1,0 +1,225 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (fixed by the method's specification of this build):
+  neighbour lists bit-exact; shape functions 1e-5 relative to the row's
+  max |phi| (FP32); H_w, M entries 1e-5 relative to the row max (FP32);
+  eigenvalues 1e-5 relative (non-constant modes); largest M-principal angle
+  1e-3 rad; FP64 generalized residual 1e-6 in FP64 mode.  FP64 mode is held
+  to 1e-10 where the arithmetic allows it.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import assembly, eigen, rkpm
+from paper_2605_29318_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def _ctx(prec):
+    from paper_2605_29318_gb300 import binding
+    return binding.Context(0, prec)
+
+
+def _oracle(c, dense=False):
+    ptr, idx = rkpm.neighbours(c.X, c.a)
+    phi, dphi, cond = rkpm.shape_functions(c.X, c.a, ptr, idx)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu, dense=dense)
+    return ptr, idx, phi, dphi, H, M
+
+
+def _material(c):
+    E = None if np.ndim(c.E) == 0 else _dev(np.asarray(c.E, np.float32))
+    nu = None if np.ndim(c.nu) == 0 else _dev(np.asarray(c.nu, np.float32))
+    E0 = float(c.E) if np.ndim(c.E) == 0 else 1.0
+    nu0 = float(c.nu) if np.ndim(c.nu) == 0 else 0.3
+    return E, nu, E0, nu0
+
+
+def _run_build(c, prec):
+    ctx = _ctx(prec)
+    ctx.rkpm_build(_dev(c.X), _dev(c.v), _dev(c.a))
+    return ctx
+
+
+CLOUDS = {
+    "cube64": lambda: synth.unit_cube(64, seed=5, support=2.5),
+    "cube2k": lambda: synth.unit_cube(2000, seed=1),
+    "torus4k": lambda: synth.torus(4000, seed=2),
+    "ellipsoids3k": lambda: synth.ellipsoid_union(3000, seed=8),
+}
+
+
+def _hetero_cloud():
+    """Variable support radii and per-particle material (ragged rows)."""
+    c = synth.unit_cube(1500, seed=21)
+    rng = np.random.default_rng(4)
+    c.a = (c.a * rng.uniform(0.9, 1.6, c.n)).astype(np.float32)
+    c.E = rng.uniform(1e4, 1e6, c.n).astype(np.float32)
+    c.nu = rng.uniform(0.2, 0.45, c.n).astype(np.float32)
+    return c
+
+
+CLOUDS["hetero1500"] = _hetero_cloud
+
+
+@pytest.mark.parametrize("name", list(CLOUDS))
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_neighbours_bit_exact_and_shape_functions(name, prec):
+    c = CLOUDS[name]()
+    ptr_o, idx_o = rkpm.neighbours(c.X, c.a)
+    phi_o, dphi_o, _ = rkpm.shape_functions(c.X, c.a, ptr_o, idx_o)
+    ctx = _run_build(c, prec)
+    ptr, idx, phi, dphi = ctx.export_rkpm()
+    assert np.array_equal(ptr, ptr_o)
+    assert np.array_equal(idx, idx_o)
+    rows = np.repeat(np.arange(c.n), np.diff(ptr))
+    scale = np.maximum.reduceat(np.abs(phi_o), ptr_o[:-1])[rows]
+    gscale = np.maximum.reduceat(np.abs(dphi_o).max(0), ptr_o[:-1])[rows]
+    tol = 1e-5 if prec == "fp32" else 1e-10
+    assert np.max(np.abs(phi - phi_o) / scale) < tol
+    assert np.max(np.abs(dphi - dphi_o).max(0) / gscale) < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["cube2k", "torus4k", "hetero1500"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_matrices(name, prec):
+    c = CLOUDS[name]()
+    ptr_o, idx_o, phi_o, dphi_o, H, M = _oracle(c)
+    ctx = _run_build(c, prec)
+    ctx.assemble_hessian(*_material(c))
+    rp, col, Hg, Mg = ctx.export_matrices()
+    assert np.array_equal(rp, H.indptr) and np.array_equal(col, H.indices)
+    assert np.array_equal(rp, M.indptr) and np.array_equal(col, M.indices)
+    rows = np.repeat(np.arange(c.n), np.diff(rp))
+    hs = np.maximum.reduceat(np.abs(H.data), H.indptr[:-1])[rows]
+    ms = np.maximum.reduceat(np.abs(M.data), M.indptr[:-1])[rows]
+    tol = 1e-5 if prec == "fp32" else 1e-10
+    assert np.max(np.abs(Hg - H.data) / hs) < tol
+    assert np.max(np.abs(Mg - M.data) / ms) < tol
+    # the stored H_w has exactly zero row sums up to the rounding of the sum itself
+    Hs = sp.csr_matrix((Hg, col, rp), shape=(c.n, c.n))
+    assert np.abs(Hs @ np.ones(c.n)).max() < (1e-6 if prec == "fp32" else 1e-13) * np.abs(Hg).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_apply_operators(prec):
+    import torch
+    c = CLOUDS["torus4k"]()
+    _, _, _, _, H, M = _oracle(c)
+    ctx = _run_build(c, prec)
+    ctx.assemble_hessian(*_material(c))
+    X = np.random.default_rng(1).standard_normal((c.n, 37))
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    YH, YM = ctx.apply_operators(_dev(X).to(dt))
+    YH = YH.double().cpu().numpy()
+    YM = YM.double().cpu().numpy()
+    tol = 1e-5 if prec == "fp32" else 1e-11
+    assert np.abs(YH - H @ X).max() < tol * np.abs(H @ X).max() * 10
+    assert np.abs(YM - M @ X).max() < tol * np.abs(M @ X).max()
+    ctx.close()
+
+
+def _check_modes(c, H, M, ev, modes, k, prec, tol_res):
+    lam_o, C_o = eigen.eigh_dense(H, M, k) if c.n <= 5000 else eigen.eigsh_sparse(H, M, k)
+    rel = np.abs(ev[1:] - lam_o[1:]) / lam_o[1:]
+    assert rel.max() < 1e-5, (rel, ev, lam_o)
+    Cg = modes.double().cpu().numpy()
+    assert np.allclose(Cg[:, 0], Cg[0, 0]) and Cg[0, 0] > 0          # constant mode first
+    ang = eigen.max_principal_angle(M, Cg[:, 1:], C_o[:, 1:])
+    assert ang < 1e-3, ang
+    res = eigen.residuals(H, M, ev, Cg)[1:]
+    assert res.max() < tol_res, res
+    G = Cg.T @ (M @ Cg)
+    assert np.abs(G - np.eye(k)).max() < (1e-4 if prec == "fp32" else 1e-9)
+    return rel.max(), ang, res.max()
+
+
+def test_eigenmodes_cube2k_fp64():
+    """The 2,000-particle cube in FP64 (k = 10): every mode within the FP64
+    oracle's residual bar."""
+    from paper_2605_29318_gb300 import binding
+    c = CLOUDS["cube2k"]()
+    _, _, _, _, H, M = _oracle(c)
+    ctx = _run_build(c, "fp64")
+    ctx.assemble_hessian(*_material(c))
+    ev, modes, rep, st = ctx.eigenmodes(10, binding.default_opts(tol=1e-8))
+    _check_modes(c, H, M, ev, modes, 10, "fp64", 1e-6)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["cube2k", "torus4k", "hetero1500"])
+def test_eigenmodes_fp32(name):
+    from paper_2605_29318_gb300 import binding
+    c = CLOUDS[name]()
+    _, _, _, _, H, M = _oracle(c)
+    ctx = _run_build(c, "fp32")
+    ctx.assemble_hessian(*_material(c))
+    ev, modes, rep, st = ctx.eigenmodes(12, binding.default_opts(tol=2e-5, max_iter=300),
+                                        check=False)
+    assert st == 0, (st, rep)
+    _check_modes(c, H, M, ev, modes, 12, "fp32", 1e-4)
+    ctx.close()
+
+
+def test_eigenmodes_exclude_constant_and_warm_start():
+    import torch
+    from paper_2605_29318_gb300 import binding
+    c = CLOUDS["cube2k"]()
+    _, _, _, _, H, M = _oracle(c)
+    ctx = _run_build(c, "fp64")
+    ctx.assemble_hessian(*_material(c))
+    o = binding.default_opts(tol=1e-8, exclude_constant=1)
+    ev, modes, rep, st = ctx.eigenmodes(6, o)
+    lam_o, C_o = eigen.eigh_dense(H, M, 7)
+    assert np.abs(ev - lam_o[1:]).max() / lam_o[1] < 1e-7
+    # warm start from the converged modes plus guard columns converges at once
+    nb = 6 + o.guard
+    X0 = torch.zeros((nb, c.n), dtype=torch.float64, device="cuda:0")
+    X0[:6] = modes.t()
+    X0[6:] = torch.randn((nb - 6, c.n), dtype=torch.float64, device="cuda:0")
+    ev2, modes2, rep2, st2 = ctx.eigenmodes(6, o, X0=X0)
+    assert rep2["warm_start_used"] == 1
+    assert rep2["iterations"] < max(3, rep["iterations"] // 2)
+    assert np.abs(ev2 - ev).max() / ev[0] < 1e-7
+    ctx.close()
+
+
+def test_error_paths():
+    import torch
+    from paper_2605_29318_gb300 import binding
+    ctx = _ctx("fp32")
+    c = synth.unit_cube(200, seed=1)
+    X = c.X.copy()
+    X[17, 1] = np.nan
+    with pytest.raises(binding.FreeformError) as e:
+        ctx.rkpm_build(_dev(X), _dev(c.v), _dev(c.a))
+    assert e.value.status == 1 and "17" in str(e.value)
+    with pytest.raises(binding.FreeformError) as e:
+        ctx.assemble_hessian(None, None, 1e5, 0.45)
+    assert e.value.status == 8
+    # a particle far from everything: only itself covers it -> singular moment matrix
+    X = c.X.copy()
+    X[5] = [50.0, 50.0, 50.0]
+    with pytest.raises(binding.FreeformError) as e:
+        ctx.rkpm_build(_dev(X), _dev(c.v), _dev(c.a))
+    assert e.value.status == 4 and "particle 5" in str(e.value)
+    ctx.rkpm_build(_dev(c.X), _dev(c.v), _dev(c.a))
+    with pytest.raises(binding.FreeformError) as e:
+        ctx.assemble_hessian(None, None, 1e5, 0.5)
+    assert e.value.status == 1
+    ctx.assemble_hessian(None, None, 1e5, 0.45)
+    with pytest.raises(binding.FreeformError) as e:
+        ctx.eigenmodes(0)
+    assert e.value.status == 1
+    ev, modes, rep, st = ctx.eigenmodes(5, binding.default_opts(max_iter=1), check=False)
+    assert st == 5 and rep["iterations"] == 1
+    ctx.close()
