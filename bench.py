@@ -1,0 +1,304 @@
+"""Benchmark of the subspace-construction hot path on GB300.
+
+One step = rkpm_build + assemble_hessian + eigenmodes on the seeded solid torus
+(R = 0.5, r = 0.2, 50,000 particles, support 2.0x spacing, E = 1e6, nu = 0.4,
+k = 32 modes with the constant one) with the inputs already resident in HBM.
+The metric is the time to k modes at relative residual 1e-6.  L2 is flushed
+(a 256 MB write) before every timed step; each step is timed with CUDA events
+on the library's stream.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--prec fp64|fp32] [--tol T]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own object
+(replicas; the path has no cross-GPU exchange) and the reported time is the
+maximum over ranks.  `--impl reference` times the FP64 CPU oracle on the host
+cores on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-k-modes at rel. residual 1e-6 (s), warm vs plain; SpMM HBM GB/s"
+WORKLOAD = ("solid torus R=0.5 r=0.2, 50,000 particles rejection-sampled (seed 2), "
+            "cubic B-spline support 2.0x spacing, Neo-Hookean E=1e6 nu=0.4, "
+            "k=32 lowest modes incl. the constant mode")
+SAMPLE_N = 10000  # bounded oracle sample (same torus, 10,000 particles)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic(kernel):
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    return None if e is None else e.get("bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_step(n=SAMPLE_N, k=32):
+    """The FP64 oracle's whole path on the bounded sample: brute-force
+    neighbours, shape functions, sparse H_w and M, shift-invert eigensolve."""
+    from oracle import assembly, eigen, rkpm
+    from paper_2605_29318_gb300 import synth
+    c = synth.torus(n, seed=2)
+    t0 = time.perf_counter()
+    ptr, idx = rkpm.neighbours(c.X, c.a, chunk=64)
+    phi, dphi, _ = rkpm.shape_functions(c.X, c.a, ptr, idx)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
+    lam, C = eigen.eigsh_sparse(H, M, k)
+    dt = time.perf_counter() - t0
+    return dt, float(eigen.residuals(H, M, lam, C)[1:].max())
+
+
+def cpu_baseline_json():
+    dt, res = cpu_oracle_step()
+    return {"value": round(dt, 3), "unit": "s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle",
+            "sample": (f"FP64 oracle (brute-force neighbours, shape functions, scipy sparse "
+                       f"H_w/M, shift-invert eigsh k=32) on the same torus with {SAMPLE_N:,} "
+                       f"particles instead of 50,000; not scaled"),
+            "max_residual": res}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_step()
+    times = []
+    res = None
+    for _ in range(args.steps):
+        dt, res = cpu_oracle_step()
+        times.append(dt)
+    v = sum(times) / len(times)
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * v, 2), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "sample": f"oracle on the same torus with {SAMPLE_N:,} particles"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"torus with {SAMPLE_N:,} particles, k=32"},
+            "e2e": {"value": round(v, 4), "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "max_residual": res}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2605_29318_gb300 import binding, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    c = synth.torus(50000, seed=2 + 1000 * rank)
+    X = torch.from_numpy(c.X).to(dev)
+    v = torch.from_numpy(c.v).to(dev)
+    a = torch.from_numpy(c.a).to(dev)
+    ctx = binding.Context(local, args.prec)
+    opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter)
+    modes = torch.empty((32, c.n), dtype=ctx.dtype, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step():
+        ctx.rkpm_build(X, v, a)
+        ctx.assemble_hessian(None, None, c.E, c.nu)
+        ev, _, rep, status = ctx.eigenmodes(32, opts, modes_out=modes, check=False)
+        return ev, rep, status
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ctx.profile(True)
+    launches0 = binding.launch_count()
+    times, reps = [], []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            ev, rep, status = step()
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            reps.append((rep, status))
+    launches = binding.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    n, n1, n2 = ctx.sizes()
+    ms = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the public call on host buffers (H2D + D2H inside)
+    e2e = []
+    h2d = d2h = 0
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, _, h2d, d2h, _ = binding.subspace_from_host(c.X, c.v, c.a, c.E, c.nu, 32,
+                                                          args.prec, opts, local, ctx)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e) / len(e2e)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = _peaks()
+    # dominant kernel: the Chebyshev preconditioner step (H-only block product)
+    cnt, tot = prof["precond"]
+    m = ((31 + 8 + 3) // 4) * 4
+    esz = 4
+    pre_bytes = n2 * 8 + (n + 1) * 8 + n * 4 + 6 * n * m * esz
+    pre_ms = tot / max(cnt, 1)
+    achieved = pre_bytes / (pre_ms * 1e-3) / 1e9 if cnt else None
+    tr = _traffic("precond")
+    # secondary: fused (H, M) block product
+    scnt, stot = prof["spmm"]
+    t_el = 8 if args.prec == "fp64" else 4
+    spmm_bytes = n2 * (2 * t_el + 4) + (n + 1) * 8 + 3 * n * m * t_el
+    spmm_gbs = spmm_bytes / (stot / max(scnt, 1) * 1e-3) / 1e9 if scnt else None
+    last_rep, last_status = reps[-1]
+    line = {
+        "metric": METRIC, "value": round(ms / 1000.0, 5), "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.prec, "tol": args.tol,
+                   "cheb_degree": args.cheb, "n": n, "n1": n1, "n2": n2,
+                   "l2": "flushed by a 256 MB write before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_cheb_step_vec (Chebyshev preconditioner step)",
+                     "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4) if achieved else None,
+                     "traffic": tr, "algorithmic_bytes_per_launch": pre_bytes,
+                     "avg_launch_ms": round(pre_ms, 5), "launches": cnt},
+        "spmm": {"avg_launch_ms": round(stot / max(scnt, 1), 5), "launches": scnt,
+                 "algorithmic_gbs": round(spmm_gbs, 1) if spmm_gbs else None},
+        "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
+        "solver": {"iterations": last_rep["iterations"], "status": last_status,
+                   "max_residual": last_rep["max_residual"],
+                   "precond_spmv_calls": last_rep["precond_spmv_calls"]},
+        "e2e": {"value": round(e2e_s, 5), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_json()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--cheb", type=int, default=16)
+    ap.add_argument("--max-iter", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

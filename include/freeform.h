@@ -184,6 +184,29 @@ ff_status ff_export_matrices(const ff_ctx* ctx, int64_t* row_ptr, int32_t* col, 
  * Y_H / Y_M device, same layout; either may be NULL.  1 <= m <= 512. */
 ff_status ff_apply_operators(ff_ctx* ctx, const void* X, int m, void* YH, void* YM);
 
+/* --------------------------------------------------------------- profiling
+ * Per-class CUDA-event timing of the library's own launches, recorded on the
+ * context stream (off by default; costs two event records per scope). */
+typedef enum {
+  FF_PROF_PRECOND = 0,        /* Chebyshev preconditioner steps (H-only block products) */
+  FF_PROF_SPMM = 1,           /* fused (H_w, M) block products */
+  FF_PROF_GRAM = 2,           /* tall-skinny Gram products */
+  FF_PROF_RAYLEIGH_RITZ = 3,  /* small dense Rayleigh-Ritz */
+  FF_PROF_UPDATE = 4,         /* block updates */
+  FF_PROF_BUILD = 5,          /* a whole rkpm_build */
+  FF_PROF_ASSEMBLE = 6        /* a whole assemble_hessian */
+} ff_prof_class;
+
+/* on != 0: reset and start recording; on == 0: stop recording. */
+ff_status ff_profile_enable(ff_ctx* ctx, int on);
+
+/* Number of recorded scopes of class `cls` since the last enable and the sum
+ * of their durations in milliseconds (synchronises the context stream). */
+ff_status ff_profile_read(ff_ctx* ctx, int cls, int64_t* launches, double* total_ms);
+
+/* Number of kernel launches the library has issued in this process. */
+int64_t ff_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,10 @@ PREC = {"fp32": 0, "fp64": 1}
 # every symbol the header declares (checked by the CPU tests)
 EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build",
            "assemble_hessian", "ff_eig_opts_default", "eigenmodes", "ff_get_sizes",
-           "ff_export_rkpm", "ff_export_matrices", "ff_apply_operators"]
+           "ff_export_rkpm", "ff_export_matrices", "ff_apply_operators", "ff_profile_enable",
+           "ff_profile_read", "ff_launch_count"]
+PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
+        "assemble": 6}
 
 
 class EigOpts(ctypes.Structure):
@@ -80,11 +83,21 @@ def load_library(path: str = LIB_PATH):
     L.ff_export_rkpm.argtypes = [vp, vp, vp, vp, vp]
     L.ff_export_matrices.argtypes = [vp, vp, vp, vp, vp]
     L.ff_apply_operators.argtypes = [vp, vp, i32, vp, vp]
+    L.ff_profile_enable.argtypes = [vp, i32]
+    L.ff_profile_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+    L.ff_launch_count.argtypes = []
     for name in EXPORTS:
-        if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default"):
+        if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default",
+                        "ff_launch_count"):
             getattr(L, name).restype = ctypes.c_int
+    L.ff_launch_count.restype = ctypes.c_int64
     _lib = L
     return L
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library in this process."""
+    return int(load_library().ff_launch_count())
 
 
 def default_opts(**kw) -> EigOpts:
@@ -165,6 +178,19 @@ class Context:
         if check and st not in (FF_OK,):
             raise FreeformError(st, self.L.ff_last_error(self.h).decode())
         return ev, (modes.t() if modes is not None else None), rep.as_dict(), st
+
+    # ---- profiling
+    def profile(self, on: bool):
+        self._check(self.L.ff_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{class: (scopes, total_ms)} for every profile class."""
+        out = {}
+        for name, cls in PROF.items():
+            cnt, ms = ctypes.c_int64(), ctypes.c_double()
+            self._check(self.L.ff_profile_read(self.h, cls, ctypes.byref(cnt), ctypes.byref(ms)))
+            out[name] = (cnt.value, ms.value)
+        return out
 
     # ---- inspection
     def sizes(self):

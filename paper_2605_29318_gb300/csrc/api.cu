@@ -17,6 +17,10 @@ template <class F>
 ff_status guarded(ff_ctx* c, F&& f) {
   if (!c) return FF_ERR_INVALID_ARG;
   c->err.clear();
+  ff::g_ctx = c;
+  struct Reset {
+    ~Reset() { ff::g_ctx = nullptr; }
+  } reset;
   try {
     FF_CUDA(cudaSetDevice(c->device));
     f();
@@ -111,6 +115,8 @@ void ff_destroy(ff_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  for (auto& v : c->prof.ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   if (c->hflags) cudaFreeHost(c->hflags);
   delete c;
 }
@@ -125,6 +131,7 @@ ff_status rkpm_build(ff_ctx* c, const float* particles, const float* volumes, co
     c->stage = 0;
     c->n = n;
     c->n1 = c->n2 = 0;
+    ff::ProfScope ps(ff::kProfBuild);
     ff::build_neighbours(c, particles, volumes, support, n);
     ff::build_shape(c);
     c->stage = 1;
@@ -137,6 +144,7 @@ ff_status assemble_hessian(ff_ctx* c, const float* E, const float* nu, double E0
     if (!E) FF_REQUIRE(E0 > 0 && std::isfinite(E0), FF_ERR_INVALID_ARG, "E0 must be > 0");
     if (!nu) FF_REQUIRE(nu0 >= 0 && nu0 < 0.5, FF_ERR_INVALID_ARG, "nu0 must be in [0, 0.5)");
     c->stage = 1;
+    ff::ProfScope ps(ff::kProfAssemble);
     ff::build_matrices(c, E, nu, E0, nu0);
     c->stage = 2;
   });
@@ -174,6 +182,31 @@ ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, 
   });
   return s != FF_OK ? s : result;
 }
+
+ff_status ff_profile_enable(ff_ctx* c, int on) {
+  return guarded(c, [&] {
+    FF_CUDA(cudaStreamSynchronize(c->stream));
+    c->prof.on = on != 0;
+    for (int k = 0; k < ff::kProfN; ++k) c->prof.used[k] = 0;
+  });
+}
+
+ff_status ff_profile_read(ff_ctx* c, int cls, int64_t* launches, double* total_ms) {
+  return guarded(c, [&] {
+    FF_REQUIRE(cls >= 0 && cls < ff::kProfN, FF_ERR_INVALID_ARG, "unknown profile class");
+    FF_CUDA(cudaStreamSynchronize(c->stream));
+    double ms = 0.0;
+    for (int i = 0; i < c->prof.used[cls]; ++i) {
+      float t = 0.f;
+      FF_CUDA(cudaEventElapsedTime(&t, c->prof.ev[cls][2 * i], c->prof.ev[cls][2 * i + 1]));
+      ms += t;
+    }
+    if (launches) *launches = c->prof.used[cls];
+    if (total_ms) *total_ms = ms;
+  });
+}
+
+int64_t ff_launch_count(void) { return ff::launch_count(); }
 
 ff_status ff_get_sizes(const ff_ctx* c, int64_t* n, int64_t* n1, int64_t* n2) {
   if (!c) return FF_ERR_INVALID_ARG;

@@ -230,21 +230,21 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   reset_flags(c);
   c->wh.ensure(tb * n);
   if (f64)
-    k_material<double><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
+    (k_material<double><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
                                                     nu, E0, nu0, c->wh.as<double>(),
-                                                    c->flags.as<DevFlags>());
+                                                    c->flags.as<DevFlags>()), ::ff::note_launch());
   else
-    k_material<float><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
+    (k_material<float><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
                                                    nu, E0, nu0, c->wh.as<float>(),
-                                                   c->flags.as<DevFlags>());
+                                                   c->flags.as<DevFlags>()), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   // pass 1: unique columns per row (table of 2048 slots per warp, 4 warps per block)
   const int tsize1 = 2048, wpb1 = 4;
   int* cnt = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (n + 1)));
   int grid1 = (int)std::min<long long>(ceil_div(n, wpb1), 152LL * 16);
-  k_pattern_count<<<grid1, 32 * wpb1, sizeof(int) * tsize1 * wpb1, st>>>(
+  (k_pattern_count<<<grid1, 32 * wpb1, sizeof(int) * tsize1 * wpb1, st>>>(
       c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
-      c->nbrT_idx.as<int>(), n, tsize1, cnt, c->flags.as<DevFlags>());
+      c->nbrT_idx.as<int>(), n, tsize1, cnt, c->flags.as<DevFlags>()), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   DevFlags f = read_flags(c);
   if (f.code == FF_ERR_INVALID_ARG) {
@@ -274,19 +274,19 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   if (f64) {
     FF_CUDA(cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(smem, 48 * 1024)));
-    k_assemble<double><<<grid2, 32 * wpb2, smem, st>>>(
+    (k_assemble<double><<<grid2, 32 * wpb2, smem, st>>>(
         c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
         c->nbrT_idx.as<int>(), c->nbrT_pos.as<long long>(), c->phi.as<double>(),
         c->dphi.as<double>(), n1, c->vol.as<float>(), c->wh.as<double>(), n, tsize2, maxrow, aptr,
-        c->a_col.as<int>(), c->a_val.as<double>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>());
+        c->a_col.as<int>(), c->a_val.as<double>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>()), ::ff::note_launch());
   } else {
     FF_CUDA(cudaFuncSetAttribute(k_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(smem, 48 * 1024)));
-    k_assemble<float><<<grid2, 32 * wpb2, smem, st>>>(
+    (k_assemble<float><<<grid2, 32 * wpb2, smem, st>>>(
         c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
         c->nbrT_idx.as<int>(), c->nbrT_pos.as<long long>(), c->phi.as<float>(),
         c->dphi.as<float>(), n1, c->vol.as<float>(), c->wh.as<float>(), n, tsize2, maxrow, aptr,
-        c->a_col.as<int>(), c->a_val.as<float>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>());
+        c->a_col.as<int>(), c->a_val.as<float>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>()), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
   FF_CUDA(cudaStreamSynchronize(st));

@@ -76,6 +76,28 @@ struct DevFlags {
   double red[8];     // small reductions returned to the host
 };
 
+// Per-class CUDA-event timing of the library's launches (off by default).
+enum ProfClass {
+  kProfPrecond = 0,  // Chebyshev preconditioner steps (H-only block products)
+  kProfSpmm,         // fused (H, M) block products
+  kProfGram,         // tall-skinny Gram products
+  kProfRR,           // small dense Rayleigh-Ritz
+  kProfUpdate,       // block updates
+  kProfBuild,        // rkpm_build (whole stage)
+  kProfAssemble,     // assemble_hessian (whole stage)
+  kProfN
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev[kProfN];  // start/stop pairs
+  int used[kProfN] = {};
+};
+
+// count of kernel launches issued by the library (process-wide)
+void note_launch();
+long long launch_count();
+
 // Uniform grid used by the neighbour search.
 struct Grid {
   double origin[3];
@@ -126,9 +148,21 @@ struct ff_ctx {
   ff::Buf scratch[8];
   // eigen-solver workspace
   ff::Buf ws[24];
+  ff::Profiler prof;
 };
 
 namespace ff {
+
+// context of the C-ABI call running on this thread (profiling hooks)
+extern thread_local ff_ctx* g_ctx;
+
+// records a start/stop event pair around a scope when profiling is on
+struct ProfScope {
+  int cls;
+  cudaEvent_t stop = nullptr;
+  explicit ProfScope(int cls_);
+  ~ProfScope();
+};
 
 // ---------------------------------------------------------------- helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -96,6 +96,179 @@ __global__ void k_cheb_step(const long long* __restrict__ ptr, const int* __rest
   }
 }
 
+// Vectorised variants for blocks whose width m is a multiple of the 16-byte
+// vector (4 floats / 2 doubles) and at most 32 vectors: a group of G = m / VEC
+// lanes reads one neighbour row of the block with 16-byte loads, the warp holds
+// P = 32 / G groups that walk different entries of the matrix row, four
+// entries per group in flight; the groups' partial sums are combined with
+// shuffles at the end of the row.
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+template <class T>
+__device__ __forceinline__ void vload(const T* p, T (&v)[Vec16<T>::n]) {
+  const typename Vec16<T>::type q = *reinterpret_cast<const typename Vec16<T>::type*>(p);
+  if constexpr (Vec16<T>::n == 4) {
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    v[0] = q.x; v[1] = q.y;
+  }
+}
+template <class T>
+__device__ __forceinline__ void vstore(T* p, const T (&v)[Vec16<T>::n]) {
+  typename Vec16<T>::type q;
+  if constexpr (Vec16<T>::n == 4) {
+    q.x = v[0]; q.y = v[1]; q.z = v[2]; q.w = v[3];
+  } else {
+    q.x = v[0]; q.y = v[1];
+  }
+  *reinterpret_cast<typename Vec16<T>::type*>(p) = q;
+}
+
+template <class T>
+__global__ void k_spmm_hm_vec(const long long* __restrict__ ptr, const int* __restrict__ col,
+                              const T* __restrict__ val, long long n, const T* __restrict__ X,
+                              int ldx, T* __restrict__ YH, T* __restrict__ YM, int ldy, int m) {
+  constexpr int VEC = Vec16<T>::n;
+  const int lane = threadIdx.x & 31;
+  const int G = m / VEC, P = 32 / G;
+  const int g = lane / G, cv = (lane % G) * VEC;
+  const bool act = g < P;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+    const long long s = ptr[k], e = ptr[k + 1];
+    T xk[VEC], ah[VEC], am[VEC];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) ah[u] = am[u] = T(0);
+    if (act) vload(X + k * ldx + cv, xk);
+    else
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) xk[u] = T(0);
+    long long e0 = act ? s + g : e;
+    for (; e0 + 3 * P < e; e0 += 4 * P) {
+      int l[4];
+      T h[4], mm[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long t = e0 + q * P;
+        l[q] = col[t];
+        h[q] = val[2 * t];
+        mm[q] = val[2 * t + 1];
+      }
+      T xl[4][VEC];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) vload(X + (long long)l[q] * ldx + cv, xl[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          ah[u] += h[q] * (xl[q][u] - xk[u]);
+          am[u] += mm[q] * xl[q][u];
+        }
+    }
+    for (; e0 < e; e0 += P) {
+      const int l = col[e0];
+      const T h = val[2 * e0], mm = val[2 * e0 + 1];
+      T xl[VEC];
+      vload(X + (long long)l * ldx + cv, xl);
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        ah[u] += h * (xl[u] - xk[u]);
+        am[u] += mm * xl[u];
+      }
+    }
+    for (int q = 1; q < P; ++q) {
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        const T th = __shfl_down_sync(kFull, ah[u], q * G);
+        const T tm = __shfl_down_sync(kFull, am[u], q * G);
+        if (g == 0) {
+          ah[u] += th;
+          am[u] += tm;
+        }
+      }
+    }
+    if (g == 0) {
+      if (YH) vstore(YH + k * ldy + cv, ah);
+      if (YM) vstore(YM + k * ldy + cv, am);
+    }
+  }
+}
+
+__global__ void k_cheb_step_vec(const long long* __restrict__ ptr, const int* __restrict__ col,
+                                const float* __restrict__ hv, const float* __restrict__ hdiag,
+                                long long n, int m, int ld, const float* __restrict__ din,
+                                float* __restrict__ dout, float* __restrict__ x,
+                                float* __restrict__ res, float c1, float c2) {
+  const int lane = threadIdx.x & 31;
+  const int G = m / 4, P = 32 / G;
+  const int g = lane / G, cv = (lane % G) * 4;
+  const bool act = g < P;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+    const long long s = ptr[k], e = ptr[k + 1];
+    float dk[4] = {0, 0, 0, 0}, acc[4] = {0, 0, 0, 0};
+    if (act) vload(din + k * ld + cv, dk);
+    long long e0 = act ? s + g : e;
+    for (; e0 + 3 * P < e; e0 += 4 * P) {
+      int l[4];
+      float h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        l[q] = col[e0 + q * P];
+        h[q] = hv[e0 + q * P];
+      }
+      float dl[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) vload(din + (long long)l[q] * ld + cv, dl[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += h[q] * (dl[q][u] - dk[u]);
+    }
+    for (; e0 < e; e0 += P) {
+      const int l = col[e0];
+      const float h = hv[e0];
+      float dl[4];
+      vload(din + (long long)l * ld + cv, dl);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += h * (dl[u] - dk[u]);
+    }
+    for (int q = 1; q < P; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float t = __shfl_down_sync(kFull, acc[u], q * G);
+        if (g == 0) acc[u] += t;
+      }
+    if (g == 0) {
+      const float dinv = 1.0f / hdiag[k];
+      const long long o = k * ld + cv;
+      float r[4], dn[4], xx[4];
+      vload(res + o, r);
+      vload(x + o, xx);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        r[u] -= acc[u] * dinv;
+        dn[u] = c1 * dk[u] + c2 * r[u];
+        xx[u] += dn[u];
+      }
+      vstore(res + o, r);
+      vstore(dout + o, dn);
+      vstore(x + o, xx);
+    }
+  }
+}
+
 // Gram partials: P[blk][i][j] = sum_{rows in chunk} A[r][ia + i] * B[r][ib + j]
 // (p x q outputs in 32 x 32 tiles; grid.x = row chunks, grid.y = output tiles).
 // Accumulates in T inside the chunk, the cross-chunk sum is FP64 (k_gram_reduce).
@@ -150,15 +323,15 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int p
 // One warp per row, lanes over 32 columns of the tile; Y tile staged in shared memory.
 template <class T>
 __global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T* __restrict__ Y,
-                               int q, T* __restrict__ C, int ldc, long long n, T beta, int split,
-                               int off2) {
+                               int ldy, int q, T* __restrict__ C, int ldc, long long n, T beta,
+                               int split, int off2) {
   extern __shared__ unsigned char smraw[];
   T* sy = reinterpret_cast<T*>(smraw);  // p x 32
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int j = blockIdx.y * 32 + lane;
   for (int t = threadIdx.x; t < p * 32; t += blockDim.x) {
     const int i = t / 32, jj = blockIdx.y * 32 + (t % 32);
-    sy[t] = jj < q ? Y[(long long)i * q + jj] : T(0);
+    sy[t] = jj < q ? Y[(long long)i * ldy + jj] : T(0);
   }
   __syncthreads();
   const int cj = j < split ? j : off2 + (j - split);
@@ -183,19 +356,38 @@ __global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T*
 template <class T>
 void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T* val, long long n,
                  const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
+  ProfScope ps(kProfSpmm);
   const int T_ = 256;
   long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
-  k_spmm_hm<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m);
+  constexpr int VEC = Vec16<T>::n;
+  const bool vec_ok = m % VEC == 0 && m <= 32 * VEC && ldx % VEC == 0 && ldy % VEC == 0 &&
+                      reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
+                      (!YH || reinterpret_cast<uintptr_t>(YH) % 16 == 0) &&
+                      (!YM || reinterpret_cast<uintptr_t>(YM) % 16 == 0);
+  if (vec_ok)
+    (k_spmm_hm_vec<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m), ::ff::note_launch());
+  else
+    (k_spmm_hm<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
 void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const float* hv,
                const float* hdiag, long long n, int m, int ld, const float* din, float* dout,
                float* x, float* res, float c1, float c2) {
+  ProfScope ps(kProfPrecond);
   const int T_ = 256;
   long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
-  k_cheb_step<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, hv, hdiag, n, m, ld, din, dout, x, res,
-                                               c1, c2);
+  const bool vec_ok = m % 4 == 0 && m <= 128 && ld % 4 == 0 &&
+                      reinterpret_cast<uintptr_t>(din) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(dout) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(x) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(res) % 16 == 0;
+  if (vec_ok)
+    (k_cheb_step_vec<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, hv, hdiag, n, m, ld, din, dout, x,
+                                                     res, c1, c2), ::ff::note_launch());
+  else
+    (k_cheb_step<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, hv, hdiag, n, m, ld, din, dout, x, res,
+                                                 c1, c2), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
@@ -203,6 +395,7 @@ template <class T>
 void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int q, long long n,
           double* out, double alpha, bool accumulate, Buf& part) {
   if (p <= 0 || q <= 0) return;
+  ProfScope ps(kProfGram);
   const int tiles = ((p + 31) / 32) * ((q + 31) / 32);
   long long chunks = std::max<long long>(1, std::min<long long>((n + 511) / 512, 2048 / tiles + 1));
   long long rpc = (n + chunks - 1) / chunks;
@@ -210,17 +403,18 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
   chunks = std::max<long long>(1, (n + rpc - 1) / rpc);
   double* pp = reinterpret_cast<double*>(part.ensure(sizeof(double) * chunks * p * q));
   dim3 grid((unsigned)chunks, (unsigned)tiles);
-  k_gram_partial<T><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp);
+  (k_gram_partial<T><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, p * q, out, alpha,
-                                                    accumulate ? 1 : 0);
+  (k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, p * q, out, alpha,
+                                                    accumulate ? 1 : 0), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
 template <class T>
 void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q, T* C, int ldc,
-                  long long n, T beta, int split, int off2) {
+                  long long n, T beta, int split, int off2, int ldy) {
   if (q <= 0 || n <= 0) return;
+  ProfScope ps(kProfUpdate);
   if (p <= 0) {
     // C = beta * C only; p == 0 never happens in the solver
     return;
@@ -230,13 +424,13 @@ void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q
   static bool attr_set[2] = {false, false};
   if (smem > 48 * 1024 && !attr_set[sizeof(T) == 8]) {
     FF_CUDA(cudaFuncSetAttribute(k_block_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
+                                 227 * 1024));
     attr_set[sizeof(T) == 8] = true;
   }
   dim3 grid((unsigned)std::min<long long>((n + wpb - 1) / wpb, 152LL * 16),
             (unsigned)((q + 31) / 32));
-  k_block_update<T><<<grid, 32 * wpb, smem, st>>>(A, lda, p, Y, q, C, ldc, n, beta,
-                                                  split < 0 ? q : split, off2);
+  (k_block_update<T><<<grid, 32 * wpb, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C, ldc, n,
+                                                  beta, split < 0 ? q : split, off2), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
@@ -249,8 +443,8 @@ template void gram<float>(cudaStream_t, const float*, int, int, const float*, in
 template void gram<double>(cudaStream_t, const double*, int, int, const double*, int, int,
                            long long, double*, double, bool, Buf&);
 template void block_update<float>(cudaStream_t, const float*, int, int, const float*, int, float*,
-                                  int, long long, float, int, int);
+                                  int, long long, float, int, int, int);
 template void block_update<double>(cudaStream_t, const double*, int, int, const double*, int,
-                                   double*, int, long long, double, int, int);
+                                   double*, int, long long, double, int, int, int);
 
 }  // namespace ff

@@ -19,16 +19,18 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
           double* out, double alpha, bool accumulate, Buf& part);
 
 // C (n x q, with the column split described in linalg.cu) = beta C + A Y, Y p x q row-major
+// with leading dimension ldy (default q)
 template <class T>
 void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q, T* C, int ldc,
-                  long long n, T beta, int split = -1, int off2 = 0);
+                  long long n, T beta, int split = -1, int off2 = 0, int ldy = -1);
 
 // small dense Rayleigh-Ritz (dense.cu)
 struct RRDims {
-  int ns;   // basis columns used (nx + nw + np)
-  int nx;   // columns of X at the front
-  int nb;   // Ritz vectors kept
+  int ns;      // basis columns used (nx + nw + np)
+  int nx;      // columns of X at the front
+  int nb;      // Ritz vectors kept
   int want_p;  // 1: also build the P coefficients Z
+  int o0, no;  // the block that is not yet M-orthonormal: columns [o0, o0 + no)
 };
 template <class T>
 void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ,

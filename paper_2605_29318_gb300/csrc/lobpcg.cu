@@ -83,36 +83,65 @@ __global__ void k_d2t(const double* in, T* out, int count) {
   if (i < count) out[i] = (T)in[i];
 }
 
-// column sums of squares of R = HX - MX theta and of MX (FP64 accumulation)
+// Per-column statistics of the current block, from the recomputed products:
+// x.Hx, x.Mx, Hx.Hx, Hx.Mx, Mx.Mx (FP64 accumulation of exact products).
+// Partials per row chunk, then a fixed-order reduction (deterministic).
 template <class T>
-__global__ void k_resid_norms(const T* __restrict__ HX, const T* __restrict__ MX, int ld,
-                              const double* __restrict__ theta, long long n, int m,
-                              double* __restrict__ norms) {
-  const int c = threadIdx.x & 31;
-  const int col = blockIdx.y * 32 + c;
-  double a = 0.0, b = 0.0;
-  if (col < m) {
-    const double th = theta[col];
-    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n;
-         r += (long long)gridDim.x * (blockDim.x >> 5)) {
-      const double mx = (double)MX[r * ld + col];
-      const double rr = (double)HX[r * ld + col] - th * mx;
-      a += rr * rr;
-      b += mx * mx;
-    }
+__global__ void k_colstats_partial(const T* __restrict__ X, const T* __restrict__ HX,
+                                   const T* __restrict__ MX, int ld, long long n, int m,
+                                   long long rows_per_block, double* __restrict__ part) {
+  __shared__ double sred[8][5][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r0 = (long long)blockIdx.x * rows_per_block;
+  const long long r1 = min(n, r0 + rows_per_block);
+  for (int c0 = 0; c0 < m; c0 += 32) {
+    const int col = c0 + lane;
+    double a[5] = {0, 0, 0, 0, 0};
+    if (col < m)
+      for (long long r = r0 + w; r < r1; r += 8) {
+        const double x = (double)X[r * ld + col], h = (double)HX[r * ld + col],
+                     mm = (double)MX[r * ld + col];
+        a[0] += x * h;
+        a[1] += x * mm;
+        a[2] += h * h;
+        a[3] += h * mm;
+        a[4] += mm * mm;
+      }
+    for (int q = 0; q < 5; ++q) sred[w][q][lane] = a[q];
+    __syncthreads();
+    if (w == 0 && col < m)
+      for (int q = 0; q < 5; ++q) {
+        double t = 0;
+        for (int ww = 0; ww < 8; ++ww) t += sred[ww][q][lane];
+        part[((long long)blockIdx.x * 5 + q) * m + col] = t;
+      }
+    __syncthreads();
   }
-  __shared__ double sa[32][33], sb[32][33];
-  sa[threadIdx.x >> 5][c] = a;
-  sb[threadIdx.x >> 5][c] = b;
+}
+
+// theta = x.Hx / x.Mx (Rayleigh quotient); ||Hx - theta Mx||^2 expanded in FP64.
+// One block per column, fixed-order tree reduction over the partials.
+__global__ void k_colstats_final(const double* __restrict__ part, int blocks, int m,
+                                 double* __restrict__ theta, double* __restrict__ stats) {
+  __shared__ double sh[5][128];
+  const int col = blockIdx.x;
+  double a[5] = {0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < blocks; b += 128)
+    for (int q = 0; q < 5; ++q) a[q] += part[((long long)b * 5 + q) * m + col];
+  for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = a[q];
   __syncthreads();
-  if (threadIdx.x < 32 && col < m) {
-    double ta = 0, tb = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      ta += sa[w][c];
-      tb += sb[w][c];
-    }
-    atomicAdd(&norms[col], ta);
-    atomicAdd(&norms[m + col], tb);
+  for (int w = 64; w; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double th = sh[0][0] / sh[1][0];
+    const double r2 = fmax(sh[2][0] - 2.0 * th * sh[3][0] + th * th * sh[4][0], 0.0);
+    theta[col] = th;
+    stats[col] = th;
+    stats[m + col] = r2;
+    stats[2 * m + col] = sh[4][0];
   }
 }
 
@@ -175,7 +204,7 @@ struct Solver {
   double *Ag, *Bg, *G1, *theta_d, *norms_d;
   T *Gt, *YZ;
   int *dropped_d, *active_d;
-  double* h_pin;  // pinned: norms (2 nb) | theta (nb) | misc
+  double* h_pin;  // pinned: theta | ||R||^2 | ||MX||^2 (3 nb)
   int spmm_calls = 0, spmv_calls = 0;
 
   T* col(T* panel, int c0_) { return panel + c0_; }
@@ -189,16 +218,16 @@ struct Solver {
     }
     c0 = reinterpret_cast<T*>(c->ws[6].ensure(sizeof(T) * n));
     Mc0 = reinterpret_cast<T*>(c->ws[7].ensure(sizeof(T) * n));
-    cres = reinterpret_cast<float*>(c->ws[8].ensure(sizeof(float) * n * nb));
-    cd0 = reinterpret_cast<float*>(c->ws[9].ensure(sizeof(float) * n * nb));
-    cd1 = reinterpret_cast<float*>(c->ws[10].ensure(sizeof(float) * n * nb));
-    cx = reinterpret_cast<float*>(c->ws[11].ensure(sizeof(float) * n * nb));
+    cres = reinterpret_cast<float*>(c->ws[8].ensure(sizeof(float) * n * std::max(nb, 4)));
+    cd0 = reinterpret_cast<float*>(c->ws[9].ensure(sizeof(float) * n * std::max(nb, 4)));
+    cd1 = reinterpret_cast<float*>(c->ws[10].ensure(sizeof(float) * n * std::max(nb, 4)));
+    cx = reinterpret_cast<float*>(c->ws[11].ensure(sizeof(float) * n * std::max(nb, 4)));
     const int ns = 3 * nb;
     Ag = reinterpret_cast<double*>(c->ws[12].ensure(sizeof(double) * ns * ns));
     Bg = reinterpret_cast<double*>(c->ws[13].ensure(sizeof(double) * ns * ns));
-    G1 = reinterpret_cast<double*>(c->ws[14].ensure(sizeof(double) * (2 * nb + 2) * nb));
+    G1 = reinterpret_cast<double*>(c->ws[14].ensure(sizeof(double) * std::max((2 * nb + 2) * nb, 64)));
     theta_d = reinterpret_cast<double*>(c->ws[15].ensure(sizeof(double) * (nb + 8)));
-    norms_d = reinterpret_cast<double*>(c->ws[16].ensure(sizeof(double) * 2 * nb));
+    norms_d = reinterpret_cast<double*>(c->ws[16].ensure(sizeof(double) * 3 * nb));
     Gt = reinterpret_cast<T*>(c->ws[17].ensure(sizeof(T) * (2 * nb + 2) * nb));
     YZ = reinterpret_cast<T*>(c->ws[18].ensure(sizeof(T) * ns * 2 * nb));
     dropped_d = reinterpret_cast<int*>(c->ws[19].ensure(sizeof(int) * 4));
@@ -214,7 +243,7 @@ struct Solver {
 
   // C(:, cols) += A (p cols) * G  where G = -coeffs (already negated, FP64 p x q)
   void apply_coeffs(const T* A, int lda, int p, const double* Gd, int q, T* C, int ldc) {
-    k_d2t<T><<<(p * q + 255) / 256, 256, 0, st>>>(Gd, Gt, p * q);
+    (k_d2t<T><<<(p * q + 255) / 256, 256, 0, st>>>(Gd, Gt, p * q), ::ff::note_launch());
     block_update<T>(st, A, lda, p, Gt, q, C, ldc, n, T(1));
   }
 
@@ -237,7 +266,10 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   s.fp64 = c->prec == FF_PREC_FP64;
   const bool incl_c0 = !o.exclude_constant;
   s.kw = incl_c0 ? k - 1 : k;
-  s.nb = std::min<long long>(s.kw + std::max(0, o.guard), (s.n - 1) / 3);
+  // block width: the wanted modes plus guard vectors, rounded up to a multiple
+  // of four so that every block starts on a 16-byte boundary
+  s.nb = (s.kw + std::max(0, o.guard) + 3) / 4 * 4;
+  s.nb = std::min<long long>(s.nb, (s.n - 1) / 3);
   FF_REQUIRE(s.nb >= s.kw && s.nb >= 1, FF_ERR_INVALID_ARG,
              "too few particles for the requested number of modes");
   s.alloc();
@@ -248,12 +280,12 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   auto blocks = [&](long long work) { return (unsigned)((work + TB - 1) / TB); };
 
   // ---- constant mode: c0 = 1 / sqrt(1^T M 1)
-  k_fill<T><<<blocks(n), TB, 0, st>>>(s.c0, n, T(1));
+  (k_fill<T><<<blocks(n), TB, 0, st>>>(s.c0, n, T(1)), ::ff::note_launch());
   spmm_hm_raw<T>(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->a_val.as<T>(), n, s.c0, 1,
                  nullptr, s.Mc0, 1, 1);
   gram<T>(st, s.c0, 1, 1, s.Mc0, 1, 1, n, s.G1, 1.0, false, c->scratch[0]);
-  k_scale<T><<<blocks(n), TB, 0, st>>>(s.c0, n, s.G1, 0);
-  k_scale<T><<<blocks(n), TB, 0, st>>>(s.Mc0, n, s.G1, 0);
+  (k_scale<T><<<blocks(n), TB, 0, st>>>(s.c0, n, s.G1, 0), ::ff::note_launch());
+  (k_scale<T><<<blocks(n), TB, 0, st>>>(s.Mc0, n, s.G1, 0), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 
   // ---- Chebyshev interval on D^-1 H
@@ -262,31 +294,29 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   if (deg > 1) {
     unsigned int* gmax = reinterpret_cast<unsigned int*>(s.dropped_d + 2);
     FF_CUDA(cudaMemsetAsync(gmax, 0, sizeof(unsigned int), st));
-    k_gershgorin<<<blocks(n), TB, 0, st>>>(c->a_ptr.as<long long>(), c->h_f32.as<float>(),
-                                           c->hdiag_f32.as<float>(), n, gmax);
-    // power iteration on one column (reuses the Chebyshev step with res = 0)
-    k_random_block<float><<<blocks(n), TB, 0, st>>>(s.cd0, 1, n, 1, o.seed + 7, c->perm.as<int>());
-    FF_CUDA(cudaMemsetAsync(s.cres, 0, sizeof(float) * n, st));
+    (k_gershgorin<<<blocks(n), TB, 0, st>>>(c->a_ptr.as<long long>(), c->h_f32.as<float>(),
+                                           c->hdiag_f32.as<float>(), n, gmax), ::ff::note_launch());
+    // power iteration on a 4-column block (reuses the Chebyshev step with res = 0)
+    (k_random_block<float><<<blocks(4 * n), TB, 0, st>>>(s.cd0, 4, n, 4, o.seed + 7, c->perm.as<int>()), ::ff::note_launch());
     double est = 0.0;
     float* a = s.cd0;
     float* b = s.cd1;
-    for (int it = 0; it < 24; ++it) {
-      FF_CUDA(cudaMemsetAsync(s.cres, 0, sizeof(float) * n, st));
+    for (int it = 0; it < 12; ++it) {
+      FF_CUDA(cudaMemsetAsync(s.cres, 0, sizeof(float) * 4 * n, st));
       cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
-                c->hdiag_f32.as<float>(), n, 1, 1, a, b, s.cx, s.cres, 0.f, -1.f);
-      gram<float>(st, a, 1, 1, a, 1, 1, n, s.G1, 1.0, false, c->scratch[0]);
-      gram<float>(st, b, 1, 1, b, 1, 1, n, s.G1 + 1, 1.0, false, c->scratch[0]);
-      gram<float>(st, a, 1, 1, b, 1, 1, n, s.G1 + 2, 1.0, false, c->scratch[0]);
-      // normalise b into a
-      k_scale<float><<<blocks(n), TB, 0, st>>>(b, n, s.G1 + 1, 0);
+                c->hdiag_f32.as<float>(), n, 4, 4, a, b, s.cx, s.cres, 0.f, -1.f);
+      gram<float>(st, a, 4, 4, a, 4, 4, n, s.G1, 1.0, false, c->scratch[0]);
+      gram<float>(st, b, 4, 4, b, 4, 4, n, s.G1 + 16, 1.0, false, c->scratch[0]);
+      // normalise b (one common factor) and make it the next input
+      (k_scale<float><<<blocks(4 * n), TB, 0, st>>>(b, 4 * n, s.G1 + 16, 0), ::ff::note_launch());
       std::swap(a, b);
     }
-    double hb[3];
+    double hb[32];
     unsigned int hg = 0;
     FF_CUDA(cudaMemcpyAsync(hb, s.G1, sizeof(hb), cudaMemcpyDeviceToHost, st));
     FF_CUDA(cudaMemcpyAsync(&hg, gmax, sizeof(hg), cudaMemcpyDeviceToHost, st));
     FF_CUDA(cudaStreamSynchronize(st));
-    est = std::sqrt(hb[1] / hb[0]);  // growth of the last power step
+    for (int j = 0; j < 4; ++j) est = std::max(est, std::sqrt(hb[16 + 5 * j] / hb[5 * j]));
     float gf;
     memcpy(&gf, &hg, sizeof(gf));
     beta = std::min(1.2 * est, (double)gf);
@@ -297,15 +327,16 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   // ---- starting block
   int warm = 0;
   if (X0) {
-    k_gather_block<T><<<blocks(n * nb), TB, 0, st>>>(X0, n, nb, c->perm.as<int>(), s.S[0], ld);
+    (k_gather_block<T><<<blocks(n * nb), TB, 0, st>>>(X0, n, nb, c->perm.as<int>(), s.S[0], ld), ::ff::note_launch());
     warm = 1;
   } else {
-    k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[0], ld, n, nb, o.seed,
-                                                     c->perm.as<int>());
+    (k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[0], ld, n, nb, o.seed,
+                                                     c->perm.as<int>()), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
   int cur = 0;
-  RRDims d0{nb, nb, nb, 0};
+  // Rayleigh-Ritz on the start block alone (it is the block to orthonormalise)
+  RRDims d0{nb, nb, nb, 0, 0, nb};
   for (int attempt = 0; attempt < 2; ++attempt) {
     s.deflate(s.S[cur], nb);
     s.spmm(s.S[cur], s.HS[cur], s.MS[cur], nb);
@@ -317,15 +348,14 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
     FF_CUDA(cudaStreamSynchronize(st));
     if (dropped == 0 || attempt == 1) break;
     // rank-deficient warm start: fall back to the seeded random block
-    k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[cur], ld, n, nb, o.seed,
-                                                     c->perm.as<int>());
+    (k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[cur], ld, n, nb, o.seed,
+                                                     c->perm.as<int>()), ::ff::note_launch());
     warm = 0;
   }
   {
     const int nxt = 1 - cur;
-    block_update<T>(st, s.S[cur], ld, nb, s.YZ, 2 * nb, s.S[nxt], ld, n, T(0), nb, 2 * nb);
-    block_update<T>(st, s.HS[cur], ld, nb, s.YZ, 2 * nb, s.HS[nxt], ld, n, T(0), nb, 2 * nb);
-    block_update<T>(st, s.MS[cur], ld, nb, s.YZ, 2 * nb, s.MS[nxt], ld, n, T(0), nb, 2 * nb);
+    block_update<T>(st, s.S[cur], ld, nb, s.YZ, nb, s.S[nxt], ld, n, T(0), -1, 0, 2 * nb);
+    s.spmm(s.S[nxt], s.HS[nxt], s.MS[nxt], nb);
     cur = nxt;
   }
 
@@ -336,23 +366,27 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   int it = 0;
   ff_status status = FF_ERR_NOT_CONVERGED;
   const double th_c = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+  const long long rpb = std::max<long long>(256, (n + 511) / 512);
+  const int cs_blocks = (int)((n + rpb - 1) / rpb);
+  double* cs_part = reinterpret_cast<double*>(c->scratch[2].ensure(sizeof(double) * cs_blocks * 5 * nb));
   for (;; ++it) {
-    FF_CUDA(cudaMemsetAsync(s.norms_d, 0, sizeof(double) * 2 * nb, st));
-    dim3 gn((unsigned)std::min<long long>((n + 31) / 32, 512), (unsigned)((nb + 31) / 32));
-    k_resid_norms<T><<<gn, 1024, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d, n, nb, s.norms_d);
+    // Rayleigh quotients and residual norms of the current X (products recomputed)
+    (k_colstats_partial<T><<<cs_blocks, 256, 0, st>>>(s.S[cur], s.HS[cur], s.MS[cur], ld, n, nb,
+                                                     rpb, cs_part), ::ff::note_launch());
+    (k_colstats_final<<<nb, 128, 0, st>>>(cs_part, cs_blocks, nb, s.theta_d, s.norms_d),
+     ::ff::note_launch());
     FF_LAUNCH_CHECK();
-    FF_CUDA(cudaMemcpyAsync(s.h_pin, s.norms_d, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, st));
-    FF_CUDA(cudaMemcpyAsync(s.h_pin + 2 * nb, s.theta_d, sizeof(double) * nb,
-                            cudaMemcpyDeviceToHost, st));
+    FF_CUDA(cudaMemcpyAsync(s.h_pin, s.norms_d, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
+                            st));
     FF_CUDA(cudaStreamSynchronize(st));
     int conv = 0;
     double worst = 0.0;
     bool bad = false;
     for (int j = 0; j < nb; ++j) {
-      theta[j] = s.h_pin[2 * nb + j];
-      double r = std::sqrt(s.h_pin[j]) / (std::fabs(theta[j]) * std::sqrt(s.h_pin[nb + j]));
+      theta[j] = s.h_pin[j];
+      double r = std::sqrt(s.h_pin[nb + j]) / (std::fabs(theta[j]) * std::sqrt(s.h_pin[2 * nb + j]));
       if (!std::isfinite(r)) {
-        if (!std::isfinite(theta[j]) || !std::isfinite(s.h_pin[j])) bad = true;
+        bad = true;
         r = 1.0;
       }
       res[j] = r;
@@ -385,9 +419,9 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
 
     // W = T R  (FP32 Chebyshev polynomial in D^-1 H, or Jacobi when deg <= 1)
     T* W = s.S[cur] + nb;
-    k_cheb_init<T><<<blocks(n * nb), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d, s.active_d,
+    (k_cheb_init<T><<<blocks(n * nb), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d, s.active_d,
                                                   c->hdiag_f32.as<float>(), n, nb, s.cres, s.cd0,
-                                                  s.cx, deg > 1 ? (float)(1.0 / th_c) : 1.f);
+                                                  s.cx, deg > 1 ? (float)(1.0 / th_c) : 1.f), ::ff::note_launch());
     FF_LAUNCH_CHECK();
     if (deg > 1) {
       const double sigma1 = th_c / delta;
@@ -404,7 +438,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
         std::swap(din, dout);
       }
     }
-    k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, n, nb, W, ld);
+    (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, n, nb, W, ld), ::ff::note_launch());
     FF_LAUNCH_CHECK();
     // M-project W against X, P and c0 (with the stored M X, M P, M c0)
     s.deflate(W, nb);
@@ -418,12 +452,18 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
     const int ns = has_p ? 3 * nb : 2 * nb;
     gram<T>(st, s.S[cur], ld, ns, s.HS[cur], ld, ns, n, s.Ag, 1.0, false, c->scratch[0]);
     gram<T>(st, s.S[cur], ld, ns, s.MS[cur], ld, ns, n, s.Bg, 1.0, false, c->scratch[0]);
-    RRDims dd{ns, nb, nb, 1};
+    RRDims dd{ns, nb, nb, 1, nb, nb};
     rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.fp64);
     const int nxt = 1 - cur;
+    // X' = S Y, P' = S Z; H P', M P' from the old products; (H X', M X') recomputed
+    // from X' itself so that the residual seen by the solver is that of the
+    // stored X' (updated products drift from the stored block in FP32)
     block_update<T>(st, s.S[cur], ld, ns, s.YZ, 2 * nb, s.S[nxt], ld, n, T(0), nb, 2 * nb);
-    block_update<T>(st, s.HS[cur], ld, ns, s.YZ, 2 * nb, s.HS[nxt], ld, n, T(0), nb, 2 * nb);
-    block_update<T>(st, s.MS[cur], ld, ns, s.YZ, 2 * nb, s.MS[nxt], ld, n, T(0), nb, 2 * nb);
+    block_update<T>(st, s.HS[cur], ld, ns, s.YZ + nb, nb, s.HS[nxt] + 2 * nb, ld, n, T(0), -1, 0,
+                    2 * nb);
+    block_update<T>(st, s.MS[cur], ld, ns, s.YZ + nb, nb, s.MS[nxt] + 2 * nb, ld, n, T(0), -1, 0,
+                    2 * nb);
+    s.spmm(s.S[nxt], s.HS[nxt], s.MS[nxt], nb);
     cur = nxt;
     has_p = true;
   }
@@ -444,11 +484,11 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   if (modes) {
     int col0 = 0;
     if (incl_c0) {
-      k_scatter_block<T><<<blocks(n), TB, 0, st>>>(s.c0, 1, n, 1, c->perm.as<int>(), modes, n, 0);
+      (k_scatter_block<T><<<blocks(n), TB, 0, st>>>(s.c0, 1, n, 1, c->perm.as<int>(), modes, n, 0), ::ff::note_launch());
       col0 = 1;
     }
-    k_scatter_block<T><<<blocks(n * kw), TB, 0, st>>>(s.S[cur], ld, n, kw, c->perm.as<int>(),
-                                                      modes, n, col0);
+    (k_scatter_block<T><<<blocks(n * kw), TB, 0, st>>>(s.S[cur], ld, n, kw, c->perm.as<int>(),
+                                                      modes, n, col0), ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
   FF_CUDA(cudaStreamSynchronize(st));
@@ -490,14 +530,14 @@ template void spmm_hm<double>(ff_ctx*, const double*, int, double*, double*, int
 // caller-order column-major block <-> internal row-major panel (used by ff_apply_operators)
 template <class T>
 void gather_block(ff_ctx* c, const T* X0, int m, T* X, int ld) {
-  k_gather_block<T><<<(unsigned)((c->n * m + 255) / 256), 256, 0, c->stream>>>(
-      X0, c->n, m, c->perm.as<int>(), X, ld);
+  (k_gather_block<T><<<(unsigned)((c->n * m + 255) / 256), 256, 0, c->stream>>>(
+      X0, c->n, m, c->perm.as<int>(), X, ld), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 template <class T>
 void scatter_block(ff_ctx* c, const T* X, int ld, int m, T* out) {
-  k_scatter_block<T><<<(unsigned)((c->n * m + 255) / 256), 256, 0, c->stream>>>(
-      X, ld, c->n, m, c->perm.as<int>(), out, c->n, 0);
+  (k_scatter_block<T><<<(unsigned)((c->n * m + 255) / 256), 256, 0, c->stream>>>(
+      X, ld, c->n, m, c->perm.as<int>(), out, c->n, 0), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 template void gather_block<float>(ff_ctx*, const float*, int, float*, int);

@@ -266,10 +266,10 @@ void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a,
   unsigned int* red = redb.as<unsigned int>();
   int* bad = reinterpret_cast<int*>(red + 8);
   float* dec = reinterpret_cast<float*>(red + 9);
-  k_init_red<<<1, 1, 0, st>>>(red, bad);
+  (k_init_red<<<1, 1, 0, st>>>(red, bad), ::ff::note_launch());
   int blocks = (int)std::min<long long>(ceil_div(n, T), 152 * 8);
-  k_validate_bbox<<<blocks, T, 0, st>>>(X, v, a, n, red, bad);
-  k_decode_red<<<1, 1, 0, st>>>(red, dec);
+  (k_validate_bbox<<<blocks, T, 0, st>>>(X, v, a, n, red, bad), ::ff::note_launch());
+  (k_decode_red<<<1, 1, 0, st>>>(red, dec), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   struct {
     unsigned int r[9];
@@ -309,24 +309,24 @@ void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a,
   int* cnt = reinterpret_cast<int*>(c->scratch[2].ensure(sizeof(int) * (K + 1)));
   int* cstart = reinterpret_cast<int*>(c->cell_start.ensure(sizeof(int) * (K + 1)));
   FF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (K + 1), st));
-  k_keys<<<ceil_div(n, T), T, 0, st>>>(X, n, gd, key, cnt);
+  (k_keys<<<ceil_div(n, T), T, 0, st>>>(X, n, gd, key, cnt), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   scan_counts_i32(cnt, cstart, K, c, c->scratch[3]);
   FF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (K + 1), st));
   int* tmp = reinterpret_cast<int*>(c->scratch[4].ensure(sizeof(int) * n));
-  k_scatter<<<ceil_div(n, T), T, 0, st>>>(key, n, cstart, cnt, tmp);
+  (k_scatter<<<ceil_div(n, T), T, 0, st>>>(key, n, cstart, cnt, tmp), ::ff::note_launch());
   int* perm = reinterpret_cast<int*>(c->perm.ensure(sizeof(int) * n));
-  k_order_cells<<<ceil_div(K * 32, T), T, 0, st>>>(cstart, K, tmp, perm);
+  (k_order_cells<<<ceil_div(K * 32, T), T, 0, st>>>(cstart, K, tmp, perm), ::ff::note_launch());
   float4* pos = reinterpret_cast<float4*>(c->pos.ensure(sizeof(float4) * n));
   float* vol = reinterpret_cast<float*>(c->vol.ensure(sizeof(float) * n));
   int* iperm = reinterpret_cast<int*>(c->iperm.ensure(sizeof(int) * n));
-  k_gather_particles<<<ceil_div(n, T), T, 0, st>>>(perm, n, X, v, a, pos, vol, iperm);
+  (k_gather_particles<<<ceil_div(n, T), T, 0, st>>>(perm, n, X, v, a, pos, vol, iperm), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 
   // ---- 3-4. scatter search: count, scan, fill, sort rows
   int* rcnt = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (n + 1)));
   FF_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int) * (n + 1), st));
-  k_search<0><<<ceil_div(n, 128), 128, 0, st>>>(pos, n, gd, cstart, rcnt, nullptr, nullptr);
+  (k_search<0><<<ceil_div(n, 128), 128, 0, st>>>(pos, n, gd, cstart, rcnt, nullptr, nullptr), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   long long* rptr = reinterpret_cast<long long*>(c->nbr_ptr.ensure(sizeof(long long) * (n + 1)));
   scan_counts(rcnt, rptr, n, c, c->scratch[3]);
@@ -336,23 +336,23 @@ void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a,
   c->n1 = n1;
   int* ridx = reinterpret_cast<int*>(c->nbr_idx.ensure(sizeof(int) * n1));
   FF_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int) * (n + 1), st));
-  k_search<1><<<ceil_div(n, 128), 128, 0, st>>>(pos, n, gd, cstart, rcnt, rptr, ridx);
+  (k_search<1><<<ceil_div(n, 128), 128, 0, st>>>(pos, n, gd, cstart, rcnt, rptr, ridx), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   int* rtmp = reinterpret_cast<int*>(c->scratch[6].ensure(sizeof(int) * n1));
-  k_sort_rows<<<ceil_div(n * 32, T), T, 0, st>>>(rptr, n, ridx, rtmp);
+  (k_sort_rows<<<ceil_div(n * 32, T), T, 0, st>>>(rptr, n, ridx, rtmp), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 
   // ---- 5. transpose
   FF_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int) * (n + 1), st));
-  k_col_count<<<ceil_div(n1, T), T, 0, st>>>(ridx, n1, rcnt);
+  (k_col_count<<<ceil_div(n1, T), T, 0, st>>>(ridx, n1, rcnt), ::ff::note_launch());
   long long* tptr = reinterpret_cast<long long*>(c->nbrT_ptr.ensure(sizeof(long long) * (n + 1)));
   scan_counts(rcnt, tptr, n, c, c->scratch[3]);
   FF_CUDA(cudaMemsetAsync(rcnt, 0, sizeof(int) * (n + 1), st));
   int* tidx = reinterpret_cast<int*>(c->nbrT_idx.ensure(sizeof(int) * n1));
   long long* tpos = reinterpret_cast<long long*>(c->nbrT_pos.ensure(sizeof(long long) * n1));
-  k_transpose_fill<<<ceil_div(n * 32, T), T, 0, st>>>(rptr, ridx, n, tptr, rcnt, tidx, tpos);
+  (k_transpose_fill<<<ceil_div(n * 32, T), T, 0, st>>>(rptr, ridx, n, tptr, rcnt, tidx, tpos), ::ff::note_launch());
   long long* ptmp = reinterpret_cast<long long*>(c->scratch[7].ensure(sizeof(long long) * n1));
-  k_sort_transposed<<<ceil_div(n * 32, T), T, 0, st>>>(tptr, n, tidx, tpos, rtmp, ptmp);
+  (k_sort_transposed<<<ceil_div(n * 32, T), T, 0, st>>>(tptr, n, tidx, tpos, rtmp, ptmp), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 

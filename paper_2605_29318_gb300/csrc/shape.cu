@@ -217,13 +217,13 @@ void build_shape(ff_ctx* c) {
   c->dphi.ensure(3 * es * n1);
   const double cond_limit = 1e2;
   if (c->prec == FF_PREC_FP64) {
-    k_shape<double><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
+    (k_shape<double><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
         c->pos.as<float4>(), c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), n, n1,
-        c->phi.as<double>(), c->dphi.as<double>(), cond_limit, c->flags.as<DevFlags>());
+        c->phi.as<double>(), c->dphi.as<double>(), cond_limit, c->flags.as<DevFlags>()), ::ff::note_launch());
   } else {
-    k_shape<float><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
+    (k_shape<float><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
         c->pos.as<float4>(), c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), n, n1,
-        c->phi.as<float>(), c->dphi.as<float>(), cond_limit, c->flags.as<DevFlags>());
+        c->phi.as<float>(), c->dphi.as<float>(), cond_limit, c->flags.as<DevFlags>()), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
   DevFlags f = read_flags(c);

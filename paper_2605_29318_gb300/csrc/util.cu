@@ -1,7 +1,40 @@
-// Scans and device-flag helpers shared by the build stages.
+// Scans, device-flag helpers, launch counting and the event profiler.
+#include <atomic>
+
 #include "ff_internal.cuh"
 
 namespace ff {
+
+thread_local ff_ctx* g_ctx = nullptr;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int cls_) : cls(cls_) {
+  ff_ctx* c = g_ctx;
+  if (!c || !c->prof.on) return;
+  Profiler& p = c->prof;
+  const size_t need = 2 * (size_t)(p.used[cls] + 1);
+  while (p.ev[cls].size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
+    p.ev[cls].push_back(e);
+  }
+  cudaEvent_t start = p.ev[cls][2 * p.used[cls]];
+  stop = p.ev[cls][2 * p.used[cls] + 1];
+  p.used[cls]++;
+  cudaEventRecord(start, c->stream);
+}
+
+ProfScope::~ProfScope() {
+  if (stop && g_ctx) cudaEventRecord(stop, g_ctx->stream);
+}
 
 namespace {
 constexpr int kScanThreads = 256;
@@ -75,17 +108,17 @@ void scan_impl(const TI* in, TO* out, long long n, ff_ctx* c, Buf& tmp, size_t t
   FF_REQUIRE(need <= tmp.bytes, FF_ERR_CUDA, "scan workspace too small");
   TO* sums = reinterpret_cast<TO*>(reinterpret_cast<char*>(tmp.p) + tmp_off);
   TO* sums_scan = sums + tiles;
-  k_scan_tile<TI, TO><<<(unsigned)tiles, kScanThreads, 0, c->stream>>>(in, out, sums, n);
+  (k_scan_tile<TI, TO><<<(unsigned)tiles, kScanThreads, 0, c->stream>>>(in, out, sums, n), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (tiles == 1) {
-    k_set_last<TO><<<1, 1, 0, c->stream>>>(out, n, sums);
+    (k_set_last<TO><<<1, 1, 0, c->stream>>>(out, n, sums), ::ff::note_launch());
     FF_LAUNCH_CHECK();
     return;
   }
   scan_impl<TO, TO>(sums, sums_scan, tiles, c, tmp, tmp_off + sizeof(TO) * (size_t)(2 * tiles + 2));
-  k_add_tile_offsets<TO><<<(unsigned)tiles, kScanThreads, 0, c->stream>>>(out, sums_scan, n);
+  (k_add_tile_offsets<TO><<<(unsigned)tiles, kScanThreads, 0, c->stream>>>(out, sums_scan, n), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  k_set_last<TO><<<1, 1, 0, c->stream>>>(out, n, sums_scan + tiles);
+  (k_set_last<TO><<<1, 1, 0, c->stream>>>(out, n, sums_scan + tiles), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
