@@ -34,6 +34,6 @@ struct RRDims {
 };
 template <class T>
 void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ,
-                   double* theta, int* dropped, Buf& work, bool fp64);
+                   double* theta, int* dropped, Buf& work, bool fp64, double* dbg = nullptr);
 
 }  // namespace ff

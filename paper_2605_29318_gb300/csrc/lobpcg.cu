@@ -269,7 +269,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   // block width: the wanted modes plus guard vectors, rounded up to a multiple
   // of four so that every block starts on a 16-byte boundary
   s.nb = (s.kw + std::max(0, o.guard) + 3) / 4 * 4;
-  s.nb = std::min<long long>(s.nb, (s.n - 1) / 3);
+  s.nb = std::min<long long>(std::min(s.nb, 340), (s.n - 1) / 3);
   FF_REQUIRE(s.nb >= s.kw && s.nb >= 1, FF_ERR_INVALID_ARG,
              "too few particles for the requested number of modes");
   s.alloc();
