@@ -184,6 +184,21 @@ ff_status ff_export_matrices(const ff_ctx* ctx, int64_t* row_ptr, int32_t* col, 
  * Y_H / Y_M device, same layout; either may be NULL.  1 <= m <= 512. */
 ff_status ff_apply_operators(ff_ctx* ctx, const void* X, int m, void* YH, void* YM);
 
+/* Allocation-free variant of ff_apply_operators (the paper has no
+ * counterpart; it serves callers that cannot allocate device memory at the
+ * time of the call -- inside CUDA stream capture, in real-time loops that
+ * forbid driver allocations, or when another allocator holds the memory).
+ * Same arguments, results and errors as ff_apply_operators, but the three
+ * staging panels live in a fixed 32 MiB array in the library's device image
+ * (held by every GPU that loads the library until the process exits), and the
+ * call makes no cudaMalloc/cudaFree or other allocation.  Requires
+ * 3 * n * m * (4 for FF_PREC_FP32, 8 for FF_PREC_FP64) bytes <= 32 MiB (each
+ * panel rounded up to 256 bytes); larger blocks return FF_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address and should
+ * come before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller. */
+ff_status ff_apply_operators_noalloc(ff_ctx* ctx, const void* X, int m, void* YH, void* YM);
+
 /* --------------------------------------------------------------- profiling
  * Per-class CUDA-event timing of the library's own launches, recorded on the
  * context stream (off by default; costs two event records per scope). */

@@ -26,8 +26,8 @@ PREC = {"fp32": 0, "fp64": 1}
 # every symbol the header declares (checked by the CPU tests)
 EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build",
            "assemble_hessian", "ff_eig_opts_default", "eigenmodes", "ff_get_sizes",
-           "ff_export_rkpm", "ff_export_matrices", "ff_apply_operators", "ff_profile_enable",
-           "ff_profile_read", "ff_launch_count"]
+           "ff_export_rkpm", "ff_export_matrices", "ff_apply_operators",
+           "ff_apply_operators_noalloc", "ff_profile_enable", "ff_profile_read", "ff_launch_count"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6}
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     L.ff_export_rkpm.argtypes = [vp, vp, vp, vp, vp]
     L.ff_export_matrices.argtypes = [vp, vp, vp, vp, vp]
     L.ff_apply_operators.argtypes = [vp, vp, i32, vp, vp]
+    L.ff_apply_operators_noalloc.argtypes = [vp, vp, i32, vp, vp]
     L.ff_profile_enable.argtypes = [vp, i32]
     L.ff_profile_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
     L.ff_launch_count.argtypes = []
@@ -227,6 +228,17 @@ class Context:
         YH = torch.empty_like(Xc)
         YM = torch.empty_like(Xc)
         self._check(self.L.ff_apply_operators(self.h, _ptr(Xc), m, _ptr(YH), _ptr(YM)))
+        return YH.t(), YM.t()
+
+    def apply_operators_noalloc(self, X, YH=None, YM=None):
+        """Same as apply_operators, through the allocation-free entry point; the
+        caller may pass preallocated column-major outputs (m, n) tensors."""
+        import torch
+        m = int(X.shape[1])
+        Xc = X.t().contiguous()
+        YH = torch.empty_like(Xc) if YH is None else YH
+        YM = torch.empty_like(Xc) if YM is None else YM
+        self._check(self.L.ff_apply_operators_noalloc(self.h, _ptr(Xc), m, _ptr(YH), _ptr(YM)))
         return YH.t(), YM.t()
 
 
