@@ -173,7 +173,8 @@ def run_ours(args):
     v = torch.from_numpy(c.v).to(dev)
     a = torch.from_numpy(c.a).to(dev)
     ctx = binding.Context(local, args.prec)
-    opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter)
+    opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
+                                fp32_phase=args.fp32_phase)
     modes = torch.empty((32, c.n), dtype=ctx.dtype, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
@@ -267,7 +268,8 @@ def run_ours(args):
         "spmm": {"avg_launch_ms": round(stot / max(scnt, 1), 5), "launches": scnt,
                  "algorithmic_gbs": round(spmm_gbs, 1) if spmm_gbs else None},
         "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
-        "solver": {"iterations": last_rep["iterations"], "status": last_status,
+        "solver": {"iterations": last_rep["iterations"],
+                   "fp32_iterations": last_rep["fp32_iterations"], "status": last_status,
                    "max_residual": last_rep["max_residual"],
                    "precond_spmv_calls": last_rep["precond_spmv_calls"]},
         "e2e": {"value": round(e2e_s, 5), "unit": "s", "h2d_bytes_per_step": int(h2d),
@@ -291,6 +293,8 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--cheb", type=int, default=16)
+    ap.add_argument("--fp32-phase", type=int, default=1, choices=[0, 1],
+                    help="FP64 contexts: iterate in FP32 first, then finish in FP64")
     ap.add_argument("--max-iter", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

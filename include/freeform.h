@@ -121,6 +121,10 @@ typedef struct {
   int exclude_constant; /* 1: return k non-constant modes (the paper's m) instead of
                            k modes with the constant mode at index 0 (0) */
   int verbose;          /* print per-iteration residuals to stderr (0) */
+  int fp32_phase;       /* FF_PREC_FP64 contexts: 1 = iterate on FP32 roundings of H_w and M
+                           until the residual reaches fp32_tol or stops falling, then
+                           finish in FP64 from that block; 0 = FP64 throughout (1) */
+  double fp32_tol;      /* residual at which the FP32 phase hands over (1e-4) */
 } ff_eig_opts;
 
 typedef struct {
@@ -131,6 +135,7 @@ typedef struct {
   double max_residual;     /* largest relative residual over the non-constant modes */
   double seconds;          /* wall time of the call */
   int warm_start_used;     /* 1 if X0 was used, 0 if the random start was used */
+  int fp32_iterations;     /* of the iterations, those run in the FP32 phase */
 } ff_eig_report;
 
 /* Fill *opts with the defaults listed above. */
@@ -145,7 +150,8 @@ void ff_eig_opts_default(ff_eig_opts* opts);
  *   k        number of modes, 1 <= k <= 256 and k <= n - 1
  *   opts     NULL = defaults
  *   X0       device, optional starting block in the caller's particle order,
- *            column-major n x (k - 1 + guard) of the context's precision
+ *            column-major n x (m + guard) of the context's precision, m the
+ *            number of non-constant modes (k - 1, or k with exclude_constant)
  *            (float for FF_PREC_FP32, double for FF_PREC_FP64); NULL = seeded
  *            random start.  A rank-deficient X0 falls back to the random start.
  *   eigvals  host, double[k] eigenvalues (ascending)
@@ -153,8 +159,10 @@ void ff_eig_opts_default(ff_eig_opts* opts);
  *            precision, in the caller's particle order; may be NULL
  *   rep      host, optional report
  *
- * Returns FF_ERR_NOT_CONVERGED (outputs filled with the last iterate) when
- * max_iter is reached, FF_ERR_TIMEOUT when the time budget runs out. */
+ * Returns FF_ERR_NOT_CONVERGED when max_iter is reached or the residual has
+ * stopped falling (50 iterations without a new best), FF_ERR_TIMEOUT when the
+ * time budget runs out; the outputs then hold the iterate with the smallest
+ * largest residual seen. */
 ff_status eigenmodes(ff_ctx* ctx, int k, const ff_eig_opts* opts, const void* X0,
                      double* eigvals, void* modes, ff_eig_report* rep);
 

@@ -36,14 +36,15 @@ class EigOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("guard", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("cheb_ratio", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("time_budget_s", ctypes.c_double),
-                ("exclude_constant", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("exclude_constant", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("fp32_phase", ctypes.c_int), ("fp32_tol", ctypes.c_double)]
 
 
 class EigReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("spmm_calls", ctypes.c_int), ("precond_spmv_calls", ctypes.c_int),
                 ("max_residual", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("warm_start_used", ctypes.c_int)]
+                ("warm_start_used", ctypes.c_int), ("fp32_iterations", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -168,6 +169,13 @@ class Context:
                    modes_out=None, check=True):
         """Returns (eigvals numpy (k,), modes torch (n, k) column-major view, report, status)."""
         import torch
+        if X0 is not None:
+            guard = opts.guard if opts is not None else 8
+            kw = k if (opts is not None and opts.exclude_constant) else k - 1
+            if (X0.dtype != self.dtype or not X0.is_contiguous()
+                    or X0.numel() != self.n * (kw + max(0, guard))):
+                raise ValueError(f"X0 must be a contiguous {self.dtype} block of "
+                                 f"(k - 1 + guard) x n = {kw + max(0, guard)} x {self.n} values")
         ev = np.zeros(k, dtype=np.float64)
         modes = modes_out
         if want_modes and modes is None:

@@ -161,6 +161,8 @@ void ff_eig_opts_default(ff_eig_opts* o) {
   o->time_budget_s = 0.0;
   o->exclude_constant = 0;
   o->verbose = 0;
+  o->fp32_phase = 1;
+  o->fp32_tol = 1e-4;
 }
 
 ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, double* eigvals,
@@ -173,10 +175,11 @@ ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, 
     ff_eig_opts o;
     ff_eig_opts_default(&o);
     if (opts) o = *opts;
-    FF_REQUIRE(o.tol > 0 && o.max_iter >= 0 && o.guard >= 0, FF_ERR_INVALID_ARG, "bad options");
+    FF_REQUIRE(o.tol > 0 && o.max_iter >= 0 && o.guard >= 0 && o.fp32_tol > 0, FF_ERR_INVALID_ARG,
+               "bad options");
     if (rep) *rep = ff_eig_report{};
     result = ff::run_eigenmodes(c, k, o, X0, eigvals, modes, rep);
-    if (result == FF_ERR_NOT_CONVERGED) c->err = "max_iter reached before tol";
+    if (result == FF_ERR_NOT_CONVERGED) c->err = "max_iter reached or residual stalled before tol";
     if (result == FF_ERR_TIMEOUT) c->err = "time budget exhausted";
     if (result == FF_ERR_NUMERIC) c->err = "non-finite residual";
   });

@@ -219,6 +219,11 @@ size_t assemble_smem_per_warp(int tsize, int maxrow, size_t tbytes) {
   return (t + 15) & ~size_t(15);
 }
 
+__global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ y, long long m) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) y[t] = (float)x[t];
+}
+
 }  // namespace
 
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0) {
@@ -289,6 +294,13 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
         c->a_col.as<int>(), c->a_val.as<float>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>()), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
+  if (f64) {  // FP32 rounding of (H, M) for the FP32 phase of the eigensolver
+    float* v32 = reinterpret_cast<float*>(c->a_val32.ensure(2 * sizeof(float) * n2));
+    const long long m = 2 * n2;
+    (k_round_f32<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->a_val.as<double>(), v32, m),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
   FF_CUDA(cudaStreamSynchronize(st));
 }
 

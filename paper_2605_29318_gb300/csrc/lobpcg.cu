@@ -176,6 +176,11 @@ __global__ void k_cast_block(const float* __restrict__ x, long long n, int m, T*
   W[r * ld + c] = (T)x[t];
 }
 
+__global__ void k_round_block(const double* __restrict__ x, float* __restrict__ y, long long m) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) y[t] = (float)x[t];
+}
+
 __global__ void k_gershgorin(const long long* __restrict__ ptr, const float* __restrict__ hv,
                              const float* __restrict__ hdiag, long long n, unsigned int* out) {
   long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -195,6 +200,7 @@ template <class T>
 struct Solver {
   ff_ctx* c;
   cudaStream_t st;
+  const T* aval;  // interleaved (H, M) of this phase's precision
   long long n;
   int nb, kw, ld;
   bool fp64;
@@ -236,8 +242,8 @@ struct Solver {
   }
 
   void spmm(const T* X, T* YH, T* YM, int m) {
-    spmm_hm_raw<T>(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->a_val.as<T>(), n, X, ld,
-                   YH, YM, ld, m);
+    spmm_hm_raw<T>(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), aval, n, X, ld, YH, YM, ld,
+                   m);
     ++spmm_calls;
   }
 
@@ -254,16 +260,30 @@ struct Solver {
   }
 };
 
+// One run of the solver at one precision.  A mixed-precision solve runs an
+// FP32 phase (FP32 roundings of H_w and M) that hands its best block to an
+// FP64 phase.
+struct Phase {
+  const void* aval = nullptr;      // interleaved (H, M) of the phase's precision
+  const float* X0_int = nullptr;   // start block from an earlier phase: internal
+                                   // particle order, dense n x nb
+  int stall = 50;                  // stop after this many iterations without progress
+  double gain = 0.999;             // progress = largest residual below gain x the last mark
+  int best_slot = 22;              // workspace slot that keeps the best block (dense n x nb)
+  bool have_best = false;          // out: the best-block slot holds a block
+};
+
 template <class T>
-ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eigvals, T* modes,
-                ff_eig_report* rep) {
+ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
+                double* eigvals, T* modes, ff_eig_report* rep) {
   using clock = std::chrono::steady_clock;
   const auto t_start = clock::now();
   Solver<T> s;
   s.c = c;
   s.st = c->stream;
+  s.aval = static_cast<const T*>(ph.aval);
   s.n = c->n;
-  s.fp64 = c->prec == FF_PREC_FP64;
+  s.fp64 = sizeof(T) == 8;
   const bool incl_c0 = !o.exclude_constant;
   s.kw = incl_c0 ? k - 1 : k;
   // block width: the wanted modes plus guard vectors, rounded up to a multiple
@@ -281,8 +301,8 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
 
   // ---- constant mode: c0 = 1 / sqrt(1^T M 1)
   (k_fill<T><<<blocks(n), TB, 0, st>>>(s.c0, n, T(1)), ::ff::note_launch());
-  spmm_hm_raw<T>(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->a_val.as<T>(), n, s.c0, 1,
-                 nullptr, s.Mc0, 1, 1);
+  spmm_hm_raw<T>(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), s.aval, n, s.c0, 1, nullptr,
+                 s.Mc0, 1, 1);
   gram<T>(st, s.c0, 1, 1, s.Mc0, 1, 1, n, s.G1, 1.0, false, c->scratch[0]);
   (k_scale<T><<<blocks(n), TB, 0, st>>>(s.c0, n, s.G1, 0), ::ff::note_launch());
   (k_scale<T><<<blocks(n), TB, 0, st>>>(s.Mc0, n, s.G1, 0), ::ff::note_launch());
@@ -326,12 +346,18 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
 
   // ---- starting block
   int warm = 0;
-  if (X0) {
-    (k_gather_block<T><<<blocks(n * nb), TB, 0, st>>>(X0, n, nb, c->perm.as<int>(), s.S[0], ld), ::ff::note_launch());
-    warm = 1;
+  if (ph.X0_int) {
+    (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(ph.X0_int, n, nb, s.S[0], ld),
+     ::ff::note_launch());
   } else {
     (k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[0], ld, n, nb, o.seed,
                                                      c->perm.as<int>()), ::ff::note_launch());
+    if (X0) {  // the caller's kw + guard columns; any rounding-up columns stay random
+      const int mu = std::min(nb, s.kw + std::max(0, o.guard));
+      (k_gather_block<T><<<blocks(n * mu), TB, 0, st>>>(X0, n, mu, c->perm.as<int>(), s.S[0], ld),
+       ::ff::note_launch());
+      warm = 1;
+    }
   }
   FF_LAUNCH_CHECK();
   int cur = 0;
@@ -369,6 +395,11 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
   const long long rpb = std::max<long long>(256, (n + 511) / 512);
   const int cs_blocks = (int)((n + rpb - 1) / rpb);
   double* cs_part = reinterpret_cast<double*>(c->scratch[2].ensure(sizeof(double) * cs_blocks * 5 * nb));
+  // the block with the smallest largest residual seen, and the progress mark
+  T* best = reinterpret_cast<T*>(c->ws[ph.best_slot].ensure(sizeof(T) * n * nb));
+  double best_worst = INFINITY, mark = INFINITY, last_worst = INFINITY;
+  int mark_it = 0;
+  std::vector<double> best_res;
   for (;; ++it) {
     // Rayleigh quotients and residual norms of the current X (products recomputed)
     (k_colstats_partial<T><<<cs_blocks, 256, 0, st>>>(s.S[cur], s.HS[cur], s.MS[cur], ld, n, nb,
@@ -398,6 +429,17 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
     }
     if (o.verbose)
       fprintf(stderr, "[eigenmodes] it %d  max res %.3e  converged %d/%d\n", it, worst, conv, s.kw);
+    last_worst = bad ? INFINITY : worst;
+    if (!bad && worst < best_worst) {
+      best_worst = worst;
+      best_res = res;
+      FF_CUDA(cudaMemcpy2DAsync(best, sizeof(T) * nb, s.S[cur], sizeof(T) * ld, sizeof(T) * nb, n,
+                                cudaMemcpyDeviceToDevice, st));
+    }
+    if (!bad && worst < mark * ph.gain) {
+      mark = worst;
+      mark_it = it;
+    }
     if (bad) {
       status = FF_ERR_NUMERIC;
       break;
@@ -406,7 +448,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
       status = FF_OK;
       break;
     }
-    if (it >= o.max_iter) {
+    if (it >= o.max_iter || (ph.stall > 0 && it - mark_it >= ph.stall)) {
       status = FF_ERR_NOT_CONVERGED;
       break;
     }
@@ -468,6 +510,15 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
     has_p = true;
   }
 
+  // ---- without convergence, fall back to the best block seen
+  ph.have_best = !best_res.empty();
+  if (status != FF_OK && !best_res.empty() && !(last_worst <= best_worst)) {
+    FF_CUDA(cudaMemcpy2DAsync(s.S[cur], sizeof(T) * ld, best, sizeof(T) * nb, sizeof(T) * nb, n,
+                              cudaMemcpyDeviceToDevice, st));
+    s.spmm(s.S[cur], s.HS[cur], s.MS[cur], nb);
+    res = best_res;
+  }
+
   // ---- eigenvalues as Rayleigh quotients of the final block (FP64-accumulated)
   const int kw = s.kw;
   std::vector<double> hq(2 * (size_t)kw * kw);
@@ -512,11 +563,61 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, const T* X0, double* eig
 
 ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0, double* eigvals,
                          void* modes, ff_eig_report* rep) {
-  if (c->prec == FF_PREC_FP64)
-    return solve<double>(c, k, o, static_cast<const double*>(X0), eigvals,
+  if (c->prec != FF_PREC_FP64) {
+    Phase ph;
+    ph.aval = c->a_val.as<float>();
+    return solve<float>(c, k, o, ph, static_cast<const float*>(X0), eigvals,
+                        static_cast<float*>(modes), rep);
+  }
+  Phase p64;
+  p64.aval = c->a_val.as<double>();
+  if (!o.fp32_phase)
+    return solve<double>(c, k, o, p64, static_cast<const double*>(X0), eigvals,
                          static_cast<double*>(modes), rep);
-  return solve<float>(c, k, o, static_cast<const float*>(X0), eigvals, static_cast<float*>(modes),
-                      rep);
+  // FP32 phase: to fp32_tol, or until the FP32 residual floor stops it
+  using clock = std::chrono::steady_clock;
+  const auto t0 = clock::now();
+  ff_eig_opts o1 = o;
+  o1.tol = std::max(o.tol, o.fp32_tol);
+  Phase p32;
+  p32.aval = c->a_val32.as<float>();
+  p32.stall = 6;
+  p32.gain = 0.9;
+  p32.best_slot = 21;
+  const float* X0f = nullptr;
+  if (X0) {  // the caller's FP64 start block, rounded
+    const int kw = o.exclude_constant ? k : k - 1;
+    const long long m = (long long)c->n * (kw + std::max(0, o.guard));
+    float* x = reinterpret_cast<float*>(c->ws[23].ensure(sizeof(float) * m));
+    (k_round_block<<<(unsigned)((m + 255) / 256), 256, 0, c->stream>>>(
+         static_cast<const double*>(X0), x, m),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    X0f = x;
+  }
+  std::vector<double> ev1(k);
+  ff_eig_report r1{};
+  const ff_status s1 = solve<float>(c, k, o1, p32, X0f, ev1.data(), nullptr, &r1);
+  // FP64 phase from the FP32 phase's best block
+  ff_eig_opts o2 = o;
+  o2.max_iter = std::max(0, o.max_iter - r1.iterations);
+  if (o.time_budget_s > 0) {
+    const double used = std::chrono::duration<double>(clock::now() - t0).count();
+    o2.time_budget_s = std::max(1e-9, o.time_budget_s - used);
+    if (s1 == FF_ERR_TIMEOUT) o2.max_iter = 0;
+  }
+  if (p32.have_best) p64.X0_int = reinterpret_cast<const float*>(c->ws[21].p);
+  ff_status s2 = solve<double>(c, k, o2, p64, nullptr, eigvals, static_cast<double*>(modes), rep);
+  if (s1 == FF_ERR_TIMEOUT && s2 == FF_ERR_NOT_CONVERGED) s2 = FF_ERR_TIMEOUT;
+  if (rep) {
+    rep->iterations += r1.iterations;
+    rep->fp32_iterations = r1.iterations;
+    rep->spmm_calls += r1.spmm_calls;
+    rep->precond_spmv_calls += r1.precond_spmv_calls;
+    rep->seconds = std::chrono::duration<double>(clock::now() - t0).count();
+    rep->warm_start_used = r1.warm_start_used;
+  }
+  return s2;
 }
 
 template <class T>
