@@ -180,6 +180,34 @@ def batch(n_objects=256, seed=4, nmin=2000, nmax=200000, kmin=16, kmax=48):
     return out
 
 
+def warmstart_shape(seed, nmin=20000, nmax=100000, k=32):
+    """One object of the warm-start corpus: a box with sides in [0.5, 1.5], a
+    torus with R in [0.35, 0.6] and r in [0.12, 0.25], or a union of
+    ellipsoids; random scale in [0.5, 2] and rotation; particle count
+    log-uniform in [nmin, nmax].  Training shapes use seeds 10000 + i, held-out
+    shapes 20000 + i."""
+    rng = _rng(seed)
+    n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+    fam = int(rng.integers(0, 3))
+    s = int(rng.integers(0, 2 ** 31 - 1))
+    if fam == 0:
+        sides = 0.5 + rng.random(3)
+        X = _rng(s).random((n, 3)) * sides
+        c = _finish(X, float(np.prod(sides)), 2.0, 1e6, 0.4, k, f"box{n}")
+    elif fam == 1:
+        c = torus(n, R=float(rng.uniform(0.35, 0.6)), r=float(rng.uniform(0.12, 0.25)), seed=s,
+                  E=1e6, nu=0.4, k=k)
+    else:
+        c = ellipsoid_union(n, seed=s, E=1e6, nu=0.4, k=k)
+    scale = float(np.exp(rng.uniform(np.log(0.5), np.log(2.0))))
+    Rm = _random_rotation(rng)
+    c.X = ((c.X.astype(np.float64) * scale) @ Rm.T).astype(np.float32)
+    c.v = (c.v.astype(np.float64) * scale ** 3).astype(np.float32)
+    c.a = (c.a.astype(np.float64) * scale).astype(np.float32)
+    c.name = f"ws{seed}-{c.name}"
+    return c
+
+
 def random_block(n, k, seed=0):
     """Seeded N(0, 1) starting block (N x k, float32) for the eigensolver."""
     return _rng(seed).standard_normal((n, k)).astype(np.float32)

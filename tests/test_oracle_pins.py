@@ -364,3 +364,124 @@ def test_disconnected_clouds_have_one_zero_mode_each():
     H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
     lam, _ = eigen.eigh_dense(H, M, 3)
     assert abs(lam[0]) < 1e-8 * lam[2] and abs(lam[1]) < 1e-8 * lam[2]
+
+
+# ---------------------------------------------------------------- warm start
+def _ws_cloud(n=300, seed=9):
+    c = synth.ellipsoid_union(n, seed=seed)
+    ptr, idx = rkpm.neighbours(c.X, c.a)
+    return c, ptr, idx
+
+
+def test_warmstart_features_invariant_under_similarity_transforms():
+    from oracle import warmstart
+    c, ptr, idx = _ws_cloud()
+    f0 = warmstart.features(c.X, c.v, c.a, ptr, idx)
+    rng = np.random.default_rng(2)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))          # rotation or reflection
+    for Qm in (Q, Q @ np.diag([1.0, 1.0, -1.0])):
+        sc = 2.5
+        X = (c.X.astype(np.float64) @ Qm.T) * sc + np.array([3.0, -1.0, 0.5])
+        f1 = warmstart.features(X, c.v * sc ** 3, c.a * sc, ptr, idx)
+        np.testing.assert_allclose(f1, f0, atol=1e-9)
+
+
+def test_warmstart_features_on_a_symmetric_lattice():
+    """Interior points of a cubic lattice whose support sees a symmetric
+    neighbourhood have zero neighbour offset and an isotropic spread equal to
+    the lattice sum over the support ball (counted by brute force)."""
+    from oracle import warmstart
+    g = np.arange(9, dtype=np.float64)
+    X = np.stack(np.meshgrid(g * 1.0, g * 1.3, g * 0.8, indexing="ij"), -1).reshape(-1, 3)
+    n = X.shape[0]
+    a = np.full(n, 1.55)
+    ptr, idx = rkpm.neighbours(X.astype(np.float32), a.astype(np.float32))
+    f = warmstart.features(X, np.ones(n), a, ptr, idx)
+    centre = int(np.argmin(((X - X.mean(0)) ** 2).sum(1)))
+    np.testing.assert_allclose(f[centre, 3:6], 0.0, atol=1e-12)
+    offs = [np.array([i * 1.0, j * 1.3, k * 0.8]) for i in range(-2, 3) for j in range(-2, 3)
+            for k in range(-2, 3)]
+    inside = np.array([o for o in offs if o @ o < 1.55 ** 2])
+    var = (inside ** 2).mean(0) / 1.55 ** 2                      # per lattice axis
+    # canonical axes of the box are the lattice axes, longest (y) first
+    np.testing.assert_allclose(np.sort(f[centre, 6:9]), np.sort(var), rtol=1e-12)
+    # variance along each lattice axis of a 9-point uniform grid: (9^2 - 1)/12 h^2
+    mu, R, s2, s = warmstart.canonical_frame(X, np.ones(n))
+    np.testing.assert_allclose(np.sort(s2)[::-1], np.array([1.3, 1.0, 0.8]) ** 2 * 80 / 12,
+                               rtol=1e-12)
+
+
+def test_warmstart_loss_special_cases():
+    from oracle import warmstart
+    rng = np.random.default_rng(5)
+    n, m = 400, 31
+    v = rng.uniform(0.5, 1.5, n)
+    C = rng.standard_normal((n, m))
+    Y = np.concatenate([C @ rng.standard_normal((m, m)), rng.standard_normal((n, 1))], 1)
+    L, _ = warmstart.subspace_loss(Y, v, C)
+    assert abs(L) < 1e-4                       # span(Y) contains span(C)
+    w = v / v.sum()
+    B = rng.standard_normal((n, 32))
+    B -= C @ np.linalg.solve(C.T @ (w[:, None] * C), C.T @ (w[:, None] * B))
+    L, _ = warmstart.subspace_loss(B, v, C)
+    assert abs(L - 1.0) < 1e-9                 # W-orthogonal to span(C)
+    Y = rng.standard_normal((n, 32))
+    L1, _ = warmstart.subspace_loss(Y, v, C)
+    Q, _ = np.linalg.qr(rng.standard_normal((32, 32)))
+    T = Q * rng.uniform(0.5, 2.0, 32)           # well conditioned: the ridge stays ~1e-6
+    L2, _ = warmstart.subspace_loss(Y @ T, v, C)
+    assert abs(L1 - L2) < 1e-5 and 0 < L1 < 1   # depends on the span only
+
+
+def test_warmstart_loss_gradient_by_finite_differences():
+    from oracle import warmstart
+    rng = np.random.default_rng(6)
+    n, m = 200, 31
+    v = rng.uniform(0.5, 1.5, n)
+    C = rng.standard_normal((n, m))
+    Y = rng.standard_normal((n, 32))
+    L, dY = warmstart.subspace_loss(Y, v, C)
+    for _ in range(4):
+        D = rng.standard_normal((n, 32))
+        h = 1e-6
+        fd = (warmstart.subspace_loss(Y + h * D, v, C)[0]
+              - warmstart.subspace_loss(Y - h * D, v, C)[0]) / (2 * h)
+        assert abs(fd - (dY * D).sum()) < 1e-5 * max(1e-3, abs(fd))
+
+
+def test_warmstart_network_gradient_by_finite_differences():
+    from oracle import warmstart
+    c, ptr, idx = _ws_cloud(120, seed=3)
+    f = warmstart.features(c.X, c.v, c.a, ptr, idx)
+    theta = warmstart.init_params(11) * 0.5
+    rng = np.random.default_rng(7)
+    C = rng.standard_normal((c.n, 31))
+    L, g = warmstart.loss_and_grad(theta, f, c.v, C)
+    assert g.shape == (warmstart.n_params(),) == (170784,)
+    off = 0
+    for i, o in warmstart.DIMS:          # one random direction per layer
+        for size in (i * o, o):
+            D = np.zeros_like(theta)
+            D[off:off + size] = rng.standard_normal(size)
+            h = 1e-7
+            fd = (warmstart.loss_and_grad(theta + h * D, f, c.v, C)[0]
+                  - warmstart.loss_and_grad(theta - h * D, f, c.v, C)[0]) / (2 * h)
+            an = g @ D
+            assert abs(fd - an) < 1e-4 * max(abs(an), 1e-3 * np.abs(g).max()), (off, fd, an)
+            off += size
+
+
+def test_adam_step_matches_its_definition_on_a_quadratic():
+    """Adam on f(x) = 0.5 ||x - t||^2 moves every coordinate by lr on its first
+    step (the bias-corrected ratio is sign(g)) and converges to t."""
+    from oracle import warmstart
+    t = np.array([1.0, -2.0, 0.5])
+    x = np.zeros(3)
+    m1 = np.zeros(3)
+    m2 = np.zeros(3)
+    x1, m1, m2 = warmstart.adam_step(x, x - t, m1, m2, 1, 0.1)
+    np.testing.assert_allclose(x1, 0.1 * np.sign(t), rtol=1e-6)
+    x = x1
+    for it in range(2, 3000):
+        x, m1, m2 = warmstart.adam_step(x, x - t, m1, m2, it, 0.01)
+    np.testing.assert_allclose(x, t, atol=1e-3)
