@@ -230,6 +230,87 @@ ff_status ff_profile_read(ff_ctx* ctx, int cls, int64_t* launches, double* total
 /* Number of kernel launches the library has issued in this process. */
 int64_t ff_launch_count(void);
 
+/* --------------------------------------------------------- learned warm start
+ * The paper starts its LOBPCG from a random block (Supp. Sec. B).  This
+ * library can instead start from a block predicted by a small point network
+ * from the particle cloud; the eigenproblem (Sec. 3.2, Eq. 15) and its
+ * tolerances are unchanged, and a start block that turns out rank-deficient
+ * falls back to the random start inside eigenmodes().  The paper has no
+ * counterpart of these calls.
+ *
+ * Features (FF_WS_FEATURES per particle) in the cloud's canonical frame
+ * (volume-weighted centroid mu, principal axes R sorted by descending
+ * variance with each axis signed so that the third moment along it is >= 0,
+ * scale s = sqrt(trace of the covariance)):
+ *   0-2   R^T (X_i - mu) / s
+ *   3-5   R^T (mean of the support neighbours' positions - X_i) / a_i
+ *   6-8   diagonal of R^T C_i R / a_i^2, C_i the neighbours' covariance
+ *   9     neighbour count / mean count     10  a_i / s     11  v_i / mean v
+ *   12-13 sqrt of the 2nd and 3rd principal variances over the 1st
+ *   14    log(n) / 16                      15  1
+ * Network (FF_WS_OUTPUTS outputs, 170,784 parameters; BF16 weights and
+ * activations, FP32 accumulation; flat FP32 order W1 b1 ... W5 b5, every W
+ * row-major [out][in]):
+ *   h1 = relu(W1 f + b1) 16->128,  h2 = relu(W2 h1 + b2) 128->256,
+ *   g = max over particles of h2,  h3 = relu(W3 [h1; g] + b3) 384->256,
+ *   h4 = relu(W4 h3 + b4) 256->128,  y = W5 h4 + b5 128->32.
+ * Training loss for a cloud with m known modes C (W = diag(v) / sum v):
+ *   L = 1 - trace(K^-1 Z^T G^-1 Z) / m,  G = Y^T W Y + eps I,  Z = Y^T W C,
+ *   K = C^T W C,  eps = 1e-6 trace(Y^T W Y) / 32
+ * (0 when span(Y) contains span(C), 1 when the spans are W-orthogonal),
+ * minimised by Adam (beta1 0.9, beta2 0.999, epsilon 1e-8). */
+#define FF_WS_FEATURES 16
+#define FF_WS_OUTPUTS 32
+
+typedef struct ff_net ff_net;
+
+/* Number of network parameters (170784). */
+int64_t ff_net_num_params(void);
+
+/* Create / destroy a network with its Adam state on a device and stream
+ * (NULL stream = the legacy default stream).  Parameters start at zero. */
+ff_status ff_net_create(ff_net** out, int device, void* cuda_stream);
+void ff_net_destroy(ff_net* net);
+/* Message of the last failed call on this network ("" if none). */
+const char* ff_net_last_error(const ff_net* net);
+
+/* He-normal weights and zero biases from a seed; resets the Adam state. */
+ff_status ff_net_init(ff_net* net, uint64_t seed);
+/* Copy the flat FP32 parameters in from / out to host memory; count must be
+ * ff_net_num_params().  Setting resets the Adam state. */
+ff_status ff_net_set_params(ff_net* net, const float* params, int64_t count);
+ff_status ff_net_get_params(ff_net* net, float* params, int64_t count);
+
+/* Features of the context's cloud (after rkpm_build).
+ *   feat  device, float[n * FF_WS_FEATURES], row-major per particle, caller order */
+ff_status ff_warmstart_features(ff_ctx* ctx, float* feat);
+
+/* Network outputs for one cloud.
+ *   feat  device, float[n * FF_WS_FEATURES] (as above);  n >= 1
+ *   out   device, float[n * FF_WS_OUTPUTS], row-major per particle */
+ff_status ff_net_forward(ff_net* net, const float* feat, int64_t n, float* out);
+
+/* Loss and gradient for one cloud without updating the parameters.
+ *   vol    device, float[n] quadrature volumes (caller order)
+ *   modes  device, float column-major n x m known modes, 1 <= m <= 32
+ *   loss   host, double
+ *   grad   host, float[ff_net_num_params()] or NULL */
+ff_status ff_net_loss_grad(ff_net* net, const float* feat, const float* vol, int64_t n,
+                           const float* modes, int m, double* loss, float* grad);
+
+/* One Adam step on one cloud with learning rate lr; *loss (host, may be NULL)
+ * receives the loss before the step. */
+ff_status ff_net_train_step(ff_net* net, const float* feat, const float* vol, int64_t n,
+                            const float* modes, int m, float lr, double* loss);
+
+/* Start block for eigenmodes(ctx, k, opts, X0, ...): features, the network,
+ * and the block's remaining guard columns from opts->seed.
+ *   X0  device, column-major n x (m + guard) in the context's precision and the
+ *       caller's order (m = k - 1, or k with exclude_constant): the layout
+ *       eigenmodes() takes; opts NULL = defaults */
+ff_status ff_warmstart_block(ff_ctx* ctx, ff_net* net, int k, const ff_eig_opts* opts,
+                             void* X0);
+
 #ifdef __cplusplus
 }
 #endif

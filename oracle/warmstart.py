@@ -119,17 +119,28 @@ def features(X, v, a, ptr, idx):
 
 
 # ---------------------------------------------------------------- network
-def forward(theta, f):
-    """Returns (y, cache) for the point network on one cloud."""
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as FP64: the
+    storage format of the CUDA network's weights and activations."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(F64)
+
+
+def forward(theta, f, store=None):
+    """Returns (y, cache) for the point network on one cloud.  ``store``
+    (e.g. ``bf16_round``) is applied to the features and to the activations
+    h1, h3, h4 where a storage format rounds them."""
     (W1, b1), (W2, b2), (W3, b3), (W4, b4), (W5, b5) = unpack(theta)
-    f = np.asarray(f, dtype=F64)
-    h1 = np.maximum(f @ W1.T + b1, 0.0)
+    st = store or (lambda a: a)
+    f = st(np.asarray(f, dtype=F64))
+    h1 = st(np.maximum(f @ W1.T + b1, 0.0))
     h2 = np.maximum(h1 @ W2.T + b2, 0.0)
     arg = np.argmax(h2, axis=0)                 # first maximiser per channel
     g = h2[arg, np.arange(h2.shape[1])]
     z = np.concatenate([h1, np.broadcast_to(g, (h1.shape[0], g.size))], axis=1)
-    h3 = np.maximum(z @ W3.T + b3, 0.0)
-    h4 = np.maximum(h3 @ W4.T + b4, 0.0)
+    h3 = st(np.maximum(z @ W3.T + b3, 0.0))
+    h4 = st(np.maximum(h3 @ W4.T + b4, 0.0))
     y = h4 @ W5.T + b5
     return y, dict(f=f, h1=h1, h2=h2, arg=arg, g=g, z=z, h3=h3, h4=h4)
 
@@ -186,8 +197,8 @@ def backward(theta, cache, dy):
     return pack([(dW1, db1), (dW2, db2), (dW3, db3), (dW4, db4), (dW5, db5)])
 
 
-def loss_and_grad(theta, f, v, C):
-    y, cache = forward(theta, f)
+def loss_and_grad(theta, f, v, C, store=None):
+    y, cache = forward(theta, f, store)
     L, dy = subspace_loss(y, v, C)
     return L, backward(theta, cache, dy)
 

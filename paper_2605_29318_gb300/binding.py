@@ -27,7 +27,10 @@ PREC = {"fp32": 0, "fp64": 1}
 EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build",
            "assemble_hessian", "ff_eig_opts_default", "eigenmodes", "ff_get_sizes",
            "ff_export_rkpm", "ff_export_matrices", "ff_apply_operators",
-           "ff_apply_operators_noalloc", "ff_profile_enable", "ff_profile_read", "ff_launch_count"]
+           "ff_apply_operators_noalloc", "ff_profile_enable", "ff_profile_read", "ff_launch_count",
+           "ff_net_num_params", "ff_net_create", "ff_net_destroy", "ff_net_last_error",
+           "ff_net_init", "ff_net_set_params", "ff_net_get_params", "ff_warmstart_features",
+           "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6}
 
@@ -88,11 +91,29 @@ def load_library(path: str = LIB_PATH):
     L.ff_profile_enable.argtypes = [vp, i32]
     L.ff_profile_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
     L.ff_launch_count.argtypes = []
+    u64, fp = ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)
+    L.ff_net_num_params.argtypes = []
+    L.ff_net_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    L.ff_net_destroy.argtypes = [vp]
+    L.ff_net_init.argtypes = [vp, u64]
+    L.ff_net_set_params.argtypes = [vp, vp, i64]
+    L.ff_net_get_params.argtypes = [vp, vp, i64]
+    L.ff_warmstart_features.argtypes = [vp, vp]
+    L.ff_net_forward.argtypes = [vp, vp, i64, vp]
+    L.ff_net_loss_grad.argtypes = [vp, vp, vp, i64, vp, i32, ctypes.POINTER(dbl), vp]
+    L.ff_net_train_step.argtypes = [vp, vp, vp, i64, vp, i32, ctypes.c_float, ctypes.POINTER(dbl)]
+    L.ff_warmstart_block.argtypes = [vp, vp, i32, ctypes.POINTER(EigOpts), vp]
+    del fp
     for name in EXPORTS:
         if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default",
-                        "ff_launch_count"):
+                        "ff_launch_count", "ff_net_num_params", "ff_net_destroy",
+                        "ff_net_last_error"):
             getattr(L, name).restype = ctypes.c_int
     L.ff_launch_count.restype = ctypes.c_int64
+    L.ff_net_num_params.restype = ctypes.c_int64
+    L.ff_net_destroy.restype = None
+    L.ff_net_last_error.restype = ctypes.c_char_p
+    L.ff_net_last_error.argtypes = [ctypes.c_void_p]
     _lib = L
     return L
 
@@ -187,6 +208,27 @@ class Context:
         if check and st not in (FF_OK,):
             raise FreeformError(st, self.L.ff_last_error(self.h).decode())
         return ev, (modes.t() if modes is not None else None), rep.as_dict(), st
+
+    # ---- learned warm start
+    def warmstart_features(self):
+        """Features of the cloud: float32 CUDA tensor (n, 16), caller order."""
+        import torch
+        f = torch.empty((self.n, 16), dtype=torch.float32, device=f"cuda:{self.device}")
+        self._check(self.L.ff_warmstart_features(self.h, _ptr(f)))
+        return f
+
+    def warmstart_block(self, net: "Net", k: int, opts: Optional[EigOpts] = None):
+        """Start block for eigenmodes(k, opts, X0=...): (m + guard, n) tensor of
+        the context's precision (column-major n x (m + guard))."""
+        import torch
+        guard = opts.guard if opts is not None else 8
+        kw = k if (opts is not None and opts.exclude_constant) else k - 1
+        X0 = torch.empty((kw + max(0, guard), self.n), dtype=self.dtype,
+                         device=f"cuda:{self.device}")
+        self._check(self.L.ff_warmstart_block(self.h, net.h, int(k),
+                                              ctypes.byref(opts) if opts is not None else None,
+                                              _ptr(X0)))
+        return X0
 
     # ---- profiling
     def profile(self, on: bool):
@@ -293,3 +335,79 @@ def subspace_from_host(X, v, a, E, nu, k, precision="fp32", opts=None, device=0,
     if own:
         ctx.close()
     return ev, host, rep, h2d_bytes, d2h_bytes, st
+
+
+class Net:
+    """The warm-start point network (ff_net): parameters, Adam state, kernels."""
+
+    def __init__(self, device: int = 0, stream=None, seed: Optional[int] = None):
+        import torch
+        self.L = load_library()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self.L.ff_net_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        if st != FF_OK:
+            raise FreeformError(st, "ff_net_create failed")
+        self.h = h
+        self.P = int(self.L.ff_net_num_params())
+        if seed is not None:
+            self._check(self.L.ff_net_init(self.h, int(seed)))
+
+    def _check(self, st):
+        if st != FF_OK:
+            raise FreeformError(st, self.L.ff_net_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            self.L.ff_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.P, dtype=np.float32)
+        self._check(self.L.ff_net_get_params(self.h, out.ctypes.data_as(ctypes.c_void_p), self.P))
+        return out
+
+    def set_params(self, theta) -> None:
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        if theta.size != self.P:
+            raise ValueError(f"expected {self.P} parameters")
+        self._check(self.L.ff_net_set_params(self.h, theta.ctypes.data_as(ctypes.c_void_p), self.P))
+
+    def forward(self, feat):
+        import torch
+        n = int(feat.shape[0])
+        out = torch.empty((n, 32), dtype=torch.float32, device=feat.device)
+        self._check(self.L.ff_net_forward(self.h, _ptr(feat), n, _ptr(out)))
+        return out
+
+    @staticmethod
+    def _cloud_args(feat, vol, modes):
+        n = int(feat.shape[0])
+        if modes.dim() != 2 or modes.shape[1] != n or not modes.is_contiguous():
+            raise ValueError("modes must be a contiguous (m, n) tensor (column-major n x m)")
+        return n, int(modes.shape[0])
+
+    def loss_grad(self, feat, vol, modes):
+        """(loss, grad numpy float32) for one cloud; modes is (m, n)."""
+        n, m = self._cloud_args(feat, vol, modes)
+        loss = ctypes.c_double()
+        grad = np.empty(self.P, dtype=np.float32)
+        self._check(self.L.ff_net_loss_grad(self.h, _ptr(feat), _ptr(vol), n, _ptr(modes), m,
+                                            ctypes.byref(loss), grad.ctypes.data_as(ctypes.c_void_p)))
+        return loss.value, grad
+
+    def train_step(self, feat, vol, modes, lr: float) -> float:
+        n, m = self._cloud_args(feat, vol, modes)
+        loss = ctypes.c_double()
+        self._check(self.L.ff_net_train_step(self.h, _ptr(feat), _ptr(vol), n, _ptr(modes), m,
+                                             ctypes.c_float(lr), ctypes.byref(loss)))
+        return loss.value

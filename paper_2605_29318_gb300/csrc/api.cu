@@ -5,6 +5,8 @@
 #include "linalg.cuh"
 
 namespace ff {
+void warmstart_features(ff_ctx* c, float* feat);
+void warmstart_block(ff_ctx* c, ff_net* w, int k, const ff_eig_opts& o, void* X0);
 template <class T>
 void gather_block(ff_ctx* c, const T* X0, int m, T* X, int ld);
 template <class T>
@@ -286,6 +288,29 @@ ff_status ff_apply_operators(ff_ctx* c, const void* X, int m, void* YH, void* YM
       run(double{});
     else
       run(float{});
+  });
+}
+
+ff_status ff_warmstart_features(ff_ctx* c, float* feat) {
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "features before rkpm_build");
+    FF_REQUIRE(feat, FF_ERR_INVALID_ARG, "feat must not be NULL");
+    ff::warmstart_features(c, feat);
+    FF_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+ff_status ff_warmstart_block(ff_ctx* c, ff_net* net, int k, const ff_eig_opts* opts, void* X0) {
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "warm start before rkpm_build");
+    FF_REQUIRE(net && X0, FF_ERR_INVALID_ARG, "net and X0 must not be NULL");
+    FF_REQUIRE(k >= 1 && k <= 256 && k <= c->n - 1, FF_ERR_INVALID_ARG, "k out of range");
+    ff_eig_opts o;
+    ff_eig_opts_default(&o);
+    if (opts) o = *opts;
+    FF_REQUIRE(o.guard >= 0, FF_ERR_INVALID_ARG, "bad options");
+    ff::warmstart_block(c, net, k, o, X0);
+    FF_CUDA(cudaStreamSynchronize(c->stream));
   });
 }
 

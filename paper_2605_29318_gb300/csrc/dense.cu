@@ -99,7 +99,7 @@ __device__ void block_cholesky(double* G, int m, int* keep, double drop_rel) {
 // ------------------------------------------------------------------ 1. tridiagonalise
 __global__ void __launch_bounds__(kThreads)
     k_rr_tridiag(const double* __restrict__ A, const double* __restrict__ B, int n, int o0, int no,
-                 RRWork w, int smem, int do_house) {
+                 RRWork w, int smem, int do_house, double drop) {
   extern __shared__ double dyn[];
   __shared__ double red[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads)
     As[(size_t)j * n + i] = v;
   }
   __syncthreads();
-  block_cholesky(w.L, no, w.keep + o0, kDrop);
+  block_cholesky(w.L, no, w.keep + o0, drop);
   // A <- T^T A T: O rows by L^-1, then O columns
   for (int a = 0; a < no; ++a) {
     const int i = o0 + a;
@@ -841,7 +841,7 @@ void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, 
   // transform (one block); Householder by the cluster when its rows fit
   (k_rr_tridiag<<<1, kThreads, tri_smem ? tri_bytes : 0, st>>>(A, B, d.ns, d.o0, d.no, w,
                                                                tri_smem ? 1 : 0,
-                                                               use_cluster ? 0 : 1),
+                                                               use_cluster ? 0 : 1, d.drop),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {

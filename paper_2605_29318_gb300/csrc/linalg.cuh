@@ -31,6 +31,8 @@ struct RRDims {
   int nb;      // Ritz vectors kept
   int want_p;  // 1: also build the P coefficients Z
   int o0, no;  // the block that is not yet M-orthonormal: columns [o0, o0 + no)
+  double drop = 1e-13;  // O columns whose M-orthogonal remainder has squared
+                        // relative norm below this leave the basis
 };
 template <class T>
 void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ,

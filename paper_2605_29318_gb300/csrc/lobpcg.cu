@@ -269,6 +269,7 @@ struct Phase {
                                    // particle order, dense n x nb
   int stall = 50;                  // stop after this many iterations without progress
   double gain = 0.999;             // progress = largest residual below gain x the last mark
+  double stall_below = INFINITY;   // iterations only count as stalled below this residual
   int best_slot = 22;              // workspace slot that keeps the best block (dense n x nb)
   bool have_best = false;          // out: the best-block slot holds a block
 };
@@ -361,22 +362,32 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   }
   FF_LAUNCH_CHECK();
   int cur = 0;
-  // Rayleigh-Ritz on the start block alone (it is the block to orthonormalise)
-  RRDims d0{nb, nb, nb, 0, 0, nb};
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  // Rayleigh-Ritz on the start block alone (it is the block to orthonormalise).
+  // A warm start is first taken with a loose drop threshold: directions it
+  // hardly adds (nearly dependent predicted columns) leave the basis, the
+  // block is rotated onto its Ritz vectors (the dropped directions come last,
+  // as zero columns) and those columns are refilled from the seeded random
+  // generator.
+  for (int attempt = 0;; ++attempt) {
     s.deflate(s.S[cur], nb);
     s.spmm(s.S[cur], s.HS[cur], s.MS[cur], nb);
     gram<T>(st, s.S[cur], ld, nb, s.HS[cur], ld, nb, n, s.Ag, 1.0, false, c->scratch[0]);
     gram<T>(st, s.S[cur], ld, nb, s.MS[cur], ld, nb, n, s.Bg, 1.0, false, c->scratch[0]);
+    RRDims d0{nb, nb, nb, 0, 0, nb};
+    if (warm && attempt == 0) d0.drop = s.fp64 ? 1e-10 : 1e-6;
     rayleigh_ritz<T>(st, s.Ag, s.Bg, d0, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.fp64);
     int dropped = 0;
     FF_CUDA(cudaMemcpyAsync(&dropped, s.dropped_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     FF_CUDA(cudaStreamSynchronize(st));
-    if (dropped == 0 || attempt == 1) break;
-    // rank-deficient warm start: fall back to the seeded random block
-    (k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[cur], ld, n, nb, o.seed,
-                                                     c->perm.as<int>()), ::ff::note_launch());
-    warm = 0;
+    if (dropped == 0 || attempt == 2) break;
+    const int nxt = 1 - cur;
+    block_update<T>(st, s.S[cur], ld, nb, s.YZ, nb, s.S[nxt], ld, n, T(0), -1, 0, 2 * nb);
+    cur = nxt;
+    const int keep = std::max(0, nb - dropped);
+    (k_random_block<T><<<blocks(n * (nb - keep)), TB, 0, st>>>(
+         s.S[cur] + keep, ld, n, nb - keep, o.seed + 7919ULL * (attempt + 1), c->perm.as<int>()),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
   }
   {
     const int nxt = 1 - cur;
@@ -436,7 +447,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
       FF_CUDA(cudaMemcpy2DAsync(best, sizeof(T) * nb, s.S[cur], sizeof(T) * ld, sizeof(T) * nb, n,
                                 cudaMemcpyDeviceToDevice, st));
     }
-    if (!bad && worst < mark * ph.gain) {
+    if (!bad && (worst < mark * ph.gain || worst >= ph.stall_below)) {
       mark = worst;
       mark_it = it;
     }
@@ -581,8 +592,11 @@ ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
   o1.tol = std::max(o.tol, o.fp32_tol);
   Phase p32;
   p32.aval = c->a_val32.as<float>();
-  p32.stall = 6;
-  p32.gain = 0.9;
+  // hand over once two iterations in a row gain less than 30% (FP32 rounding
+  // of H, M and the block sets a floor near 1e-4 on the 50k torus)
+  p32.stall = 2;
+  p32.gain = 0.7;
+  p32.stall_below = 1e-2;
   p32.best_slot = 21;
   const float* X0f = nullptr;
   if (X0) {  // the caller's FP64 start block, rounded

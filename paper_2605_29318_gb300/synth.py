@@ -87,15 +87,19 @@ def _random_rotation(rng):
 
 
 def ellipsoid_union(n=20000, seed=5, n_ell=None, support=2.0, E=1e6, nu=0.4, k=16):
-    """Union of 2-5 overlapping random ellipsoids (a blob-like solid)."""
+    """Union of 2-5 overlapping random ellipsoids (a connected blob-like solid)."""
     rng = _rng(seed)
     m = n_ell or int(rng.integers(2, 6))
-    centres = [np.zeros(3)]
-    for _ in range(m - 1):
-        centres.append(centres[-1] + rng.normal(size=3) * 0.25)
-    centres = np.array(centres)
     axes = 0.2 + 0.3 * rng.random((m, 3))
     rots = [_random_rotation(rng) for _ in range(m)]
+    # each centre lies inside the previous ellipsoid (within its smallest
+    # semi-axis), so the union is connected
+    centres = [np.zeros(3)]
+    for j in range(1, m):
+        d = rng.normal(size=3)
+        d *= axes[j - 1].min() * rng.uniform(0.3, 0.8) / np.linalg.norm(d)
+        centres.append(centres[-1] + d)
+    centres = np.array(centres)
 
     def inside(P):
         ok = np.zeros(P.shape[0], bool)
@@ -204,16 +208,20 @@ def warmstart_shape(seed, nmin=20000, nmax=100000, k=32):
     c.X = ((c.X.astype(np.float64) * scale) @ Rm.T).astype(np.float32)
     c.v = (c.v.astype(np.float64) * scale ** 3).astype(np.float32)
     c.a = (c.a.astype(np.float64) * scale).astype(np.float32)
+    c.a = support_floor(c.X, c.a)
     c.name = f"ws{seed}-{c.name}"
     return c
 
 
-def random_block(n, k, seed=0):
-    """Seeded N(0, 1) starting block (N x k, float32) for the eigensolver."""
-    return _rng(seed).standard_normal((n, k)).astype(np.float32)
-
-
-CONFIGS = {
-    "cube2k": lambda: unit_cube(2000, seed=1),
-    "torus50k": lambda: torus(50000, seed=2),
-}
+def support_floor(X, a, m=8):
+    """Widen supports so that every particle is covered by its m nearest other
+    particles: a_k <- max(a_k, 1.0001 d(j, k)) over every j that has k among
+    its m nearest (node k covers X_j iff |X_j - p_k| < a_k).  Random sampling
+    otherwise leaves the odd thin spot with too few covering nodes for the
+    moment matrix."""
+    from scipy.spatial import cKDTree
+    P = np.asarray(X, np.float64)
+    d, nb = cKDTree(P).query(P, k=m + 1)
+    out = np.asarray(a, np.float64).copy()
+    np.maximum.at(out, nb[:, 1:].ravel(), 1.0001 * d[:, 1:].ravel())
+    return out.astype(np.float32)

@@ -453,7 +453,16 @@ def test_warmstart_network_gradient_by_finite_differences():
     from oracle import warmstart
     c, ptr, idx = _ws_cloud(120, seed=3)
     f = warmstart.features(c.X, c.v, c.a, ptr, idx)
+    # random layers 1-4 and a last layer that whitens h4 in the volume inner
+    # product: the loss is then well conditioned (G = Y^T W Y ~ I), so central
+    # differences resolve its derivative
     theta = warmstart.init_params(11) * 0.5
+    w = c.v.astype(np.float64) / c.v.sum()
+    _, cache = warmstart.forward(theta, f)
+    _, S, Vt = np.linalg.svd(np.sqrt(w)[:, None] * cache["h4"], full_matrices=False)
+    layers = warmstart.unpack(theta)
+    layers[4] = (Vt[:32] / S[:32, None], np.zeros(32))
+    theta = warmstart.pack(layers)
     rng = np.random.default_rng(7)
     C = rng.standard_normal((c.n, 31))
     L, g = warmstart.loss_and_grad(theta, f, c.v, C)
@@ -485,3 +494,20 @@ def test_adam_step_matches_its_definition_on_a_quadratic():
     for it in range(2, 3000):
         x, m1, m2 = warmstart.adam_step(x, x - t, m1, m2, it, 0.01)
     np.testing.assert_allclose(x, t, atol=1e-3)
+
+
+def test_bf16_rounding_matches_its_definition():
+    """Nearest representable value with 8 significant bits, ties to even."""
+    from oracle import warmstart
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -9, 1.0 + 2 ** -7 + 2 ** -8,
+                  -3.14159, 0.0, 1e-30])
+    r = warmstart.bf16_round(x)                # spacing 2^-7 on [1, 2)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                        # 1 + 2^-8 is the midpoint of 1 and 1 + 2^-7
+    assert r[2] == 1.0 + 2 ** -7              # above the midpoint
+    assert r[3] == 1.0                        # below the midpoint
+    assert r[4] == 1.0 + 2 ** -6              # midpoint of 1 + 2^-7 (odd) and 1 + 2^-6
+    assert abs(r[5] + 3.140625) == 0.0
+    assert r[6] == 0.0
+    m, e = np.frexp(r[np.isfinite(r) & (r != 0)])
+    assert np.all(np.abs(m * 2 ** 8 - np.round(m * 2 ** 8)) == 0)   # 8-bit significand
