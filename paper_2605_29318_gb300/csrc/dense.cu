@@ -44,47 +44,66 @@ namespace {
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr size_t kMaxDynSmem = 200 * 1024;
-constexpr double kDrop = 1e-13;
-constexpr double kEps = 1.1e-16;
+// working-precision constants: unit roundoff, smallest magnitude kept apart
+// from zero, default Cholesky drop, and the exponent at which the Sturm
+// recurrence rescales
+template <class R>
+struct Prec;
+template <>
+struct Prec<double> {
+  static constexpr double eps = 1.1e-16, tiny = 1e-290, drop = 1e-13, hi = 0x1p+600, lo = 0x1p-600;
+};
+template <>
+struct Prec<float> {
+  static constexpr float eps = 6e-8f, tiny = 1e-30f, drop = 1e-6f, hi = 0x1p+60f, lo = 0x1p-60f;
+};
+__device__ __forceinline__ int ilogb_r(double x) { return ilogb(x); }
+__device__ __forceinline__ int ilogb_r(float x) { return ilogbf(x); }
+__device__ __forceinline__ double scalbn_r(double x, int e) { return scalbn(x, e); }
+__device__ __forceinline__ float scalbn_r(float x, int e) { return scalbnf(x, e); }
 
-// global workspace layout (doubles)
+// global workspace layout (working precision R)
+template <class R>
 struct RRWork {
-  double *As, *ref, *L, *dsc, *dg, *e, *e2, *tau, *lam, *V, *Z, *G, *T1, *scr, *C, *U;
+  R *As, *ref, *L, *dsc, *dg, *e, *e2, *tau, *lam, *V, *Z, *G, *T1, *scr, *C, *U;
   int* keep;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class R>
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 // block-wide sum; every thread gets the result
-__device__ double block_sum(double v, double* red) {
+template <class R>
+__device__ R block_sum(R v, R* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v = warp_sum(v);
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+  R t = lane < (int)(blockDim.x >> 5) ? red[lane] : R(0.0);
   return warp_sum(t);
 }
 
 // right-looking Cholesky (lower) of an m x m matrix in place, with drop
-__device__ void block_cholesky(double* G, int m, int* keep, double drop_rel) {
+template <class R>
+__device__ void block_cholesky(R* G, int m, int* keep, R drop_rel) {
   __shared__ int s_keep;
   for (int j = 0; j < m; ++j) {
     if (threadIdx.x == 0) {
-      const double piv = G[j * m + j];
+      const R piv = G[j * m + j];
       const int k = keep[j] && piv > drop_rel;
       keep[j] = k;
-      G[j * m + j] = k ? sqrt(piv) : 1.0;
+      G[j * m + j] = k ? sqrt(piv) : R(1.0);
       s_keep = k;
     }
     __syncthreads();
-    const double ljj = G[j * m + j];
+    const R ljj = G[j * m + j];
     const int kj = s_keep;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) G[i * m + j] = kj ? G[i * m + j] / ljj : 0.0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) G[i * m + j] = kj ? G[i * m + j] / ljj : R(0.0);
     __syncthreads();
     const int r = m - j - 1;
     if (kj)
@@ -96,28 +115,30 @@ __device__ void block_cholesky(double* G, int m, int* keep, double drop_rel) {
   }
 }
 
-// ------------------------------------------------------------------ 1. tridiagonalise
+// ------------------------------------------------------------------ R(1.) tridiagonalise
+template <class R>
 __global__ void __launch_bounds__(kThreads)
     k_rr_tridiag(const double* __restrict__ A, const double* __restrict__ B, int n, int o0, int no,
-                 RRWork w, int smem, int do_house, double drop) {
-  extern __shared__ double dyn[];
-  __shared__ double red[kWarps];
+                 RRWork<R> w, int smem, int do_house, R drop) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* dyn = reinterpret_cast<R*>(dyn_raw);
+  __shared__ R red[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const size_t nn = (size_t)n * n;
-  double* As = smem ? dyn : w.As;
-  double* vt = w.T1;            // n
-  double* pw = w.T1 + n;        // n
+  R* As = smem ? dyn : w.As;
+  R* vt = w.T1;            // n
+  R* pw = w.T1 + n;        // n
   // scaling: O columns by diag(B)^-1/2; other columns must have B_ii ~ 1
   for (int i = tid; i < n; i += kThreads) {
-    const double bii = B[(size_t)i * n + i];
-    double s = 1.0;
+    const R bii = (R)B[(size_t)i * n + i];
+    R s = R(1.0);
     int k = 1;
     if (i >= o0 && i < o0 + no) {
-      k = bii > 1e-280 && isfinite(bii);
-      s = k ? 1.0 / sqrt(bii) : 0.0;
-    } else if (!(bii > 0.25 && bii < 4.0)) {
+      k = bii > Prec<R>::tiny && isfinite(bii);
+      s = k ? R(1.0) / sqrt(bii) : R(0.0);
+    } else if (!(bii > R(0.25) && bii < R(4.0))) {
       k = 0;
-      s = 0.0;
+      s = R(0.0);
     }
     w.keep[i] = k;
     w.dsc[i] = s;
@@ -125,7 +146,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   for (size_t t = tid; t < nn; t += kThreads) {
     const int i = (int)(t / n), j = (int)(t % n);
-    As[t] = 0.5 * (A[t] + A[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j];
+    As[t] = R(0.5) * ((R)A[t] + (R)A[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j];
   }
   // Second projection of the O block against the rest, in coefficient space.
   // The O columns arrive M-projected against the others once, on the
@@ -139,13 +160,13 @@ __global__ void __launch_bounds__(kThreads)
     const int i = t / no, j = o0 + t % no;
     const bool in_o = i >= o0 && i < o1;
     w.C[t] = (!in_o && w.keep[i] && w.keep[j])
-                 ? 0.5 * (B[(size_t)i * n + j] + B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j]
-                 : 0.0;
+                 ? R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j]
+                 : R(0.0);
   }
   __syncthreads();
   for (int t = tid; t < n * no; t += kThreads) {  // U = A_{rest,rest} C
     const int i = t / no, a = t % no;
-    double acc = 0.0;
+    R acc = R(0.0);
     if (i < o0 || i >= o1)
       for (int r = 0; r < n; ++r)
         if (r < o0 || r >= o1) acc += As[(size_t)i * n + r] * w.C[r * no + a];
@@ -154,22 +175,22 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   for (int t = tid; t < no * no; t += kThreads) {
     const int a = t / no, b = t % no, i = o0 + a, j = o0 + b;
-    double cc = 0.0, acc = As[(size_t)i * n + j];
+    R cc = R(0.0), acc = As[(size_t)i * n + j];
     for (int r = 0; r < n; ++r) {
       if (r >= o0 && r < o1) continue;
-      const double ca = w.C[r * no + a], cb = w.C[r * no + b];
+      const R ca = w.C[r * no + a], cb = w.C[r * no + b];
       cc += ca * cb;
       acc += ca * w.U[r * no + b] - ca * As[(size_t)r * n + j] - As[(size_t)i * n + r] * cb;
     }
-    const double v = 0.5 * (B[(size_t)i * n + j] + B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j] - cc;
-    w.L[t] = (w.keep[i] && w.keep[j]) ? v : (a == b ? 1.0 : 0.0);
+    const R v = R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j] - cc;
+    w.L[t] = (w.keep[i] && w.keep[j]) ? v : (a == b ? R(1.0) : R(0.0));
     As[(size_t)i * n + j] = acc;
   }
   __syncthreads();
   for (int t = tid; t < n * no; t += kThreads) {
     const int i = t / no, j = o0 + t % no;
     if (i >= o0 && i < o1) continue;
-    const double v = As[(size_t)i * n + j] - w.U[t];
+    const R v = As[(size_t)i * n + j] - w.U[t];
     As[(size_t)i * n + j] = v;
     As[(size_t)j * n + i] = v;
   }
@@ -178,9 +199,9 @@ __global__ void __launch_bounds__(kThreads)
   // A <- T^T A T: O rows by L^-1, then O columns
   for (int a = 0; a < no; ++a) {
     const int i = o0 + a;
-    const double inv = 1.0 / w.L[a * no + a];
+    const R inv = R(1.0) / w.L[a * no + a];
     for (int c = tid; c < n; c += kThreads) {
-      double acc = As[(size_t)i * n + c];
+      R acc = As[(size_t)i * n + c];
       for (int b = 0; b < a; ++b) acc -= w.L[a * no + b] * As[(size_t)(o0 + b) * n + c];
       As[(size_t)i * n + c] = acc * inv;
     }
@@ -188,9 +209,9 @@ __global__ void __launch_bounds__(kThreads)
   }
   for (int a = 0; a < no; ++a) {
     const int i = o0 + a;
-    const double inv = 1.0 / w.L[a * no + a];
+    const R inv = R(1.0) / w.L[a * no + a];
     for (int r = tid; r < n; r += kThreads) {
-      double acc = As[(size_t)r * n + i];
+      R acc = As[(size_t)r * n + i];
       for (int b = 0; b < a; ++b) acc -= w.L[a * no + b] * As[(size_t)r * n + o0 + b];
       As[(size_t)r * n + i] = acc * inv;
     }
@@ -199,10 +220,10 @@ __global__ void __launch_bounds__(kThreads)
   // symmetrise; dropped columns are decoupled with a diagonal just above the
   // spectrum of the kept part (2 ||A_kept||_inf + 1), which keeps them out of
   // the nb lowest without disturbing the scale of the tridiagonal problem
-  double rmax = 0.0;
+  R rmax = R(0.0);
   for (int i = wid; i < n; i += kWarps) {
     if (!w.keep[i]) continue;
-    double rs = 0.0;
+    R rs = R(0.0);
     for (int j = lane; j < n; j += 32)
       if (w.keep[j]) rs += fabs(As[(size_t)i * n + j]);
     rmax = fmax(rmax, warp_sum(rs));
@@ -211,17 +232,17 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (lane == 0) red[wid] = rmax;
     __syncthreads();
-    double t = lane < kWarps ? red[lane] : 0.0;
+    R t = lane < kWarps ? red[lane] : R(0.0);
 #pragma unroll
     for (int o = 16; o; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
     rmax = t;
     __syncthreads();
   }
-  const double big = 2.0 * rmax + 1.0;
+  const R big = R(2.0) * rmax + R(1.0);
   for (size_t t = tid; t < nn; t += kThreads) {
     const int i = (int)(t / n), j = (int)(t % n);
-    if (!w.keep[i] || !w.keep[j]) As[t] = (i == j) ? big : 0.0;
-    else if (i > j) As[t] = 0.5 * (As[t] + As[(size_t)j * n + i]);
+    if (!w.keep[i] || !w.keep[j]) As[t] = (i == j) ? big : R(0.0);
+    else if (i > j) As[t] = R(0.5) * (As[t] + As[(size_t)j * n + i]);
   }
   __syncthreads();
   for (size_t t = tid; t < nn; t += kThreads) {
@@ -237,29 +258,29 @@ __global__ void __launch_bounds__(kThreads)
   // Householder: reflector j = [1, v] stored in row j of w.ref (entries j+1..n-1)
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
-    double part = 0.0;
+    R part = R(0.0);
     for (int i = tid; i < m; i += kThreads) {
-      const double x = As[(size_t)(j + 1 + i) * n + j];
+      const R x = As[(size_t)(j + 1 + i) * n + j];
       part += x * x;
     }
-    const double ss = block_sum(part, red);
-    const double x0 = As[(size_t)(j + 1) * n + j];
-    const double alpha = sqrt(ss);
+    const R ss = block_sum(part, red);
+    const R x0 = As[(size_t)(j + 1) * n + j];
+    const R alpha = sqrt(ss);
     __syncthreads();
-    if (!(alpha > 1e-290)) {
+    if (!(alpha > Prec<R>::tiny)) {
       if (tid == 0) {
-        w.tau[j] = 0.0;
+        w.tau[j] = R(0.0);
         w.e[j] = x0;
         w.dg[j] = As[(size_t)j * n + j];
       }
       __syncthreads();
       continue;
     }
-    const double beta = x0 >= 0.0 ? -alpha : alpha;
-    const double tj = (beta - x0) / beta;
-    const double scale = 1.0 / (x0 - beta);
+    const R beta = x0 >= R(0.0) ? -alpha : alpha;
+    const R tj = (beta - x0) / beta;
+    const R scale = R(1.0) / (x0 - beta);
     for (int i = tid; i < m; i += kThreads) {
-      const double v = i == 0 ? 1.0 : As[(size_t)(j + 1 + i) * n + j] * scale;
+      const R v = i == 0 ? R(1.0) : As[(size_t)(j + 1 + i) * n + j] * scale;
       vt[i] = v;
       w.ref[(size_t)j * n + j + 1 + i] = v;
     }
@@ -270,22 +291,22 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
     for (int i = wid; i < m; i += kWarps) {  // p = tau A22 v
-      const double* row = As + (size_t)(j + 1 + i) * n + (j + 1);
-      double acc = 0.0;
+      const R* row = As + (size_t)(j + 1 + i) * n + (j + 1);
+      R acc = R(0.0);
       for (int l = lane; l < m; l += 32) acc += row[l] * vt[l];
       acc = warp_sum(acc);
       if (lane == 0) pw[i] = tj * acc;
     }
     __syncthreads();
-    double kp = 0.0;
+    R kp = R(0.0);
     for (int i = tid; i < m; i += kThreads) kp += pw[i] * vt[i];
-    const double K = 0.5 * tj * block_sum(kp, red);
+    const R K = R(0.5) * tj * block_sum(kp, red);
     __syncthreads();
     for (int i = tid; i < m; i += kThreads) pw[i] -= K * vt[i];
     __syncthreads();
     for (int i = wid; i < m; i += kWarps) {  // A22 -= v w^T + w v^T
-      double* row = As + (size_t)(j + 1 + i) * n + (j + 1);
-      const double vi = vt[i], wi = pw[i];
+      R* row = As + (size_t)(j + 1 + i) * n + (j + 1);
+      const R vi = vt[i], wi = pw[i];
       for (int l = lane; l < m; l += 32) row[l] -= vi * pw[l] + wi * vt[l];
     }
     __syncthreads();
@@ -294,36 +315,37 @@ __global__ void __launch_bounds__(kThreads)
     if (n >= 2) {
       w.dg[n - 2] = As[(size_t)(n - 2) * n + (n - 2)];
       w.e[n - 2] = As[(size_t)(n - 1) * n + (n - 2)];
-      w.tau[n - 2] = 0.0;
+      w.tau[n - 2] = R(0.0);
     }
     w.dg[n - 1] = As[(size_t)(n - 1) * n + (n - 1)];
-    w.e[n - 1] = 0.0;
-    w.tau[n - 1] = 0.0;
+    w.e[n - 1] = R(0.0);
+    w.tau[n - 1] = R(0.0);
   }
   __syncthreads();
   for (int i = tid; i < n; i += kThreads) w.e2[i] = w.e[i] * w.e[i];
 }
 
-// ------------------------------------------------------------------ 2. eigenvalues
+// ------------------------------------------------------------------ R(2.) eigenvalues
 // Division-free Sturm count in FP64: sign changes along the leading principal
 // minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{-1} = 1), rescaled by
 // exact powers of two to stay in range.  A zero minor takes the sign opposite
 // to its predecessor.
-__device__ int sturm64(const double* d, const double* e2, int n, double x) {
-  double pm = 1.0, p = d[0] - x;
-  if (p == 0.0) p = -1e-300;
-  int c = p < 0.0;
+template <class R>
+__device__ int sturm(const R* d, const R* e2, int n, R x) {
+  R pm = R(1.0), p = d[0] - x;
+  if (p == R(0.0)) p = -Prec<R>::tiny;
+  int c = p < R(0.0);
   for (int i = 1; i < n; ++i) {
-    double q = fma(d[i] - x, p, -e2[i - 1] * pm);
-    if (q == 0.0) q = p > 0.0 ? -1e-300 : 1e-300;
-    c += (q < 0.0) != (p < 0.0);
+    R q = fma(d[i] - x, p, -e2[i - 1] * pm);
+    if (q == R(0.0)) q = p > R(0.0) ? -Prec<R>::tiny : Prec<R>::tiny;
+    c += (q < R(0.0)) != (p < R(0.0));
     pm = p;
     p = q;
-    const double ap = fabs(p);
-    if (ap > 0x1p+600 || ap < 0x1p-600) {
-      const int ex = ilogb(p);
-      p = scalbn(p, -ex);
-      pm = scalbn(pm, -ex);
+    const R ap = fabs(p);
+    if (ap > Prec<R>::hi || ap < Prec<R>::lo) {
+      const int ex = ilogb_r(p);
+      p = scalbn_r(p, -ex);
+      pm = scalbn_r(pm, -ex);
     }
   }
   return c;
@@ -341,70 +363,73 @@ __device__ int sturm64(const double* d, const double* e2, int n, double x) {
 constexpr int kCS = 8;
 constexpr int kCT = 256;
 
-__device__ double cl_block_sum(double v, double* red) {
+template <class R>
+__device__ R cl_block_sum(R v, R* red) {
   const int lane = threadIdx.x & 31, wdx = threadIdx.x >> 5;
   v = warp_sum(v);
   __syncthreads();
   if (lane == 0) red[wdx] = v;
   __syncthreads();
-  double t = lane < (kCT / 32) ? red[lane] : 0.0;
+  R t = lane < (kCT / 32) ? red[lane] : R(0.0);
   return warp_sum(t);
 }
 
+template <class R>
 __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
-    k_rr_house_cluster(int n, RRWork w) {
+    k_rr_house_cluster(int n, RRWork<R> w) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int kW = kCT / 32;
   const int rpc = (n + kCS - 1) / kCS;
-  extern __shared__ double sm[];
-  double* Ar = sm;                      // rpc x n: row rank + kCS * li
-  double* vf = Ar + (size_t)rpc * n;    // n: column j, then v
-  double* wf = vf + n;                  // n: p, then w
-  double* pubc = wf + n;                // 2 x rpc
-  double* pubp = pubc + 2 * rpc;        // 2 x rpc
-  double* pubs = pubp + 2 * rpc;        // 2
-  __shared__ double red[kW];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  R* sm = reinterpret_cast<R*>(sm_raw);
+  R* Ar = sm;                      // rpc x n: row rank + kCS * li
+  R* vf = Ar + (size_t)rpc * n;    // n: column j, then v
+  R* wf = vf + n;                  // n: p, then w
+  R* pubc = wf + n;                // 2 x rpc
+  R* pubp = pubc + 2 * rpc;        // 2 x rpc
+  R* pubs = pubp + 2 * rpc;        // 2
+  __shared__ R red[kW];
   for (int t = tid; t < rpc * n; t += kCT) {
     const int li = t / n, c = t % n, r = rank + kCS * li;
-    Ar[t] = r < n ? w.As[(size_t)r * n + c] : 0.0;
+    Ar[t] = r < n ? w.As[(size_t)r * n + c] : R(0.0);
   }
   __syncthreads();
   for (int j = 0; j + 2 < n; ++j) {
     const int buf = j & 1;
     for (int li = tid; li < rpc; li += kCT) {
       const int r = rank + kCS * li;
-      pubc[buf * rpc + li] = (r < n && r >= j + 1) ? Ar[(size_t)li * n + j] : 0.0;
+      pubc[buf * rpc + li] = (r < n && r >= j + 1) ? Ar[(size_t)li * n + j] : R(0.0);
     }
     cl.sync();
     for (int r = j + 1 + tid; r < n; r += kCT) {
-      const double* rem = cl.map_shared_rank(pubc + buf * rpc, r % kCS);
+      const R* rem = cl.map_shared_rank(pubc + buf * rpc, r % kCS);
       vf[r] = rem[r / kCS];
     }
     __syncthreads();
-    double part = 0.0;
+    R part = R(0.0);
     for (int r = j + 1 + tid; r < n; r += kCT) part += vf[r] * vf[r];
-    const double ss = cl_block_sum(part, red);
-    const double x0 = vf[j + 1];
-    const double alpha = sqrt(ss);
+    const R ss = cl_block_sum(part, red);
+    const R x0 = vf[j + 1];
+    const R alpha = sqrt(ss);
     const int own_j = (j % kCS) == rank;
-    if (!(alpha > 1e-290)) {
+    if (!(alpha > Prec<R>::tiny)) {
       if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
       if (rank == 0 && tid == 0) {
-        w.tau[j] = 0.0;
+        w.tau[j] = R(0.0);
         w.e[j] = x0;
       }
       __syncthreads();
       continue;
     }
-    const double beta = x0 >= 0.0 ? -alpha : alpha;
-    const double tj = (beta - x0) / beta;
-    const double scale = 1.0 / (x0 - beta);
+    const R beta = x0 >= R(0.0) ? -alpha : alpha;
+    const R tj = (beta - x0) / beta;
+    const R scale = R(1.0) / (x0 - beta);
     __syncthreads();
     for (int r = j + 1 + tid; r < n; r += kCT) {
-      const double v = r == j + 1 ? 1.0 : vf[r] * scale;
+      const R v = r == j + 1 ? R(1.0) : vf[r] * scale;
       vf[r] = v;
       if (rank == 0) w.ref[(size_t)j * n + r] = v;
     }
@@ -415,36 +440,36 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     }
     __syncthreads();
     // p = tau A v for own rows r >= j+1, and this block's share of p^T v
-    double kp = 0.0;
+    R kp = R(0.0);
     for (int li = wid; li < rpc; li += kW) {
       const int r = rank + kCS * li;
-      double acc = 0.0;
+      R acc = R(0.0);
       if (r < n && r >= j + 1) {
-        const double* row = Ar + (size_t)li * n;
+        const R* row = Ar + (size_t)li * n;
         for (int l = j + 1 + lane; l < n; l += 32) acc += row[l] * vf[l];
       }
       acc = warp_sum(acc) * tj;
       if (lane == 0) {
-        pubp[buf * rpc + li] = (r < n && r >= j + 1) ? acc : 0.0;
+        pubp[buf * rpc + li] = (r < n && r >= j + 1) ? acc : R(0.0);
         if (r < n && r >= j + 1) kp += acc * vf[r];
       }
     }
-    const double kpb = cl_block_sum(kp, red);
+    const R kpb = cl_block_sum(kp, red);
     if (tid == 0) pubs[buf] = kpb;
     cl.sync();
-    double K = 0.0;
+    R K = R(0.0);
     for (int q = 0; q < kCS; ++q) K += cl.map_shared_rank(pubs, q)[buf];
-    K *= 0.5 * tj;
+    K *= R(0.5) * tj;
     for (int r = j + 1 + tid; r < n; r += kCT) {
-      const double* rem = cl.map_shared_rank(pubp + buf * rpc, r % kCS);
+      const R* rem = cl.map_shared_rank(pubp + buf * rpc, r % kCS);
       wf[r] = rem[r / kCS] - K * vf[r];
     }
     __syncthreads();
     for (int li = wid; li < rpc; li += kW) {  // A_own -= v w^T + w v^T
       const int r = rank + kCS * li;
       if (r >= n || r < j + 1) continue;
-      double* row = Ar + (size_t)li * n;
-      const double vr = vf[r], wr = wf[r];
+      R* row = Ar + (size_t)li * n;
+      const R vr = vf[r], wr = wf[r];
       for (int l = j + 1 + lane; l < n; l += 32) row[l] -= vr * wf[l] + wr * vf[l];
     }
     __syncthreads();
@@ -453,14 +478,14 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
   if (tid == 0) {
     for (int r = (n >= 2 ? n - 2 : 0); r < n; ++r) {
       if (r % kCS != rank) continue;
-      const double* row = Ar + (size_t)(r / kCS) * n;
+      const R* row = Ar + (size_t)(r / kCS) * n;
       w.dg[r] = row[r];
       if (r == n - 1 && n >= 2) w.e[n - 2] = row[n - 2];
     }
     if (rank == 0) {
-      if (n >= 2) w.tau[n - 2] = 0.0;
-      w.tau[n - 1] = 0.0;
-      w.e[n - 1] = 0.0;
+      if (n >= 2) w.tau[n - 2] = R(0.0);
+      w.tau[n - 1] = R(0.0);
+      w.e[n - 1] = R(0.0);
     }
   }
   __threadfence();
@@ -472,31 +497,32 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
 // ------------------------------------------------------------------ 2b. eigenvalues, one block each
 // FP64 multisection with the division-free Sturm count: one warp per
 // eigenvalue, 32 probes per round (a 33-fold shrink of the bracket per round).
-__global__ void k_rr_eigvals_mc(int n, int nb, RRWork w, double* theta) {
+template <class R>
+__global__ void k_rr_eigvals_mc(int n, int nb, RRWork<R> w, double* theta) {
   const int s = blockIdx.x, lane = threadIdx.x;
-  double lo = 0.0, hi = 0.0;
+  R lo = R(0.0), hi = R(0.0);
   for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(w.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(w.e[i]) : 0.0);
-    const double a = w.dg[i] - r, b = w.dg[i] + r;
+    const R r = (i > 0 ? fabs(w.e[i - 1]) : R(0.0)) + (i + 1 < n ? fabs(w.e[i]) : R(0.0));
+    const R a = w.dg[i] - r, b = w.dg[i] + r;
     if (i == 0 || a < lo) lo = a;
     if (i == 0 || b > hi) hi = b;
   }
-  const double span = fmax(hi - lo, 1e-30);
-  double a = lo - span * 1e-6, b = hi + span * 1e-6;
+  const R span = fmax(hi - lo, R(1e-30));
+  R a = lo - span * R(1e-6), b = hi + span * R(1e-6);
   for (int round = 0; round < 64; ++round) {
-    const double x = a + (b - a) * (double)(lane + 1) / 33.0;
-    const int cnt = sturm64(w.dg, w.e2, n, x);
+    const R x = a + (b - a) * (R)(lane + 1) / R(33.0);
+    const int cnt = sturm(w.dg, w.e2, n, x);
     const unsigned above = __ballot_sync(0xffffffffu, cnt >= s + 1);
     const int first = above ? __ffs(above) - 1 : 32;
-    const double na = first == 0 ? a : a + (b - a) * (double)first / 33.0;
-    const double nbv = first == 32 ? b : a + (b - a) * (double)(first + 1) / 33.0;
+    const R na = first == 0 ? a : a + (b - a) * (R)first / R(33.0);
+    const R nbv = first == 32 ? b : a + (b - a) * (R)(first + 1) / R(33.0);
     a = __shfl_sync(0xffffffffu, na, 0);
     b = __shfl_sync(0xffffffffu, nbv, 0);
-    if (b - a <= 4.0 * kEps * fmax(fabs(a), fabs(b))) break;
+    if (b - a <= R(4.0) * Prec<R>::eps * fmax(fabs(a), fabs(b))) break;
   }
   if (lane == 0) {
-    w.lam[s] = 0.5 * (a + b);
-    theta[s] = 0.5 * (a + b);
+    w.lam[s] = R(0.5) * (a + b);
+    theta[s] = R(0.5) * (a + b);
   }
 }
 
@@ -504,61 +530,63 @@ __global__ void k_rr_eigvals_mc(int n, int nb, RRWork w, double* theta) {
 // kIV threads per block, one vector each, their LU factors in shared memory
 // (one thread per block: the pivoting branches of different vectors diverge)
 constexpr int kIV = 1;
-__global__ void k_rr_invit_sm(int n, int nb, RRWork w) {
-  extern __shared__ double sm[];
+template <class R>
+__global__ void k_rr_invit_sm(int n, int nb, RRWork<R> w) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  R* sm = reinterpret_cast<R*>(sm_raw);
   const int s = blockIdx.x * kIV + threadIdx.x;
-  double* u = sm + (size_t)threadIdx.x * 6 * n;
+  R* u = sm + (size_t)threadIdx.x * 6 * n;
   if (s >= nb) return;
-  double lo = 0.0, hi = 0.0;
+  R lo = R(0.0), hi = R(0.0);
   for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(w.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(w.e[i]) : 0.0);
-    const double a = w.dg[i] - r, b = w.dg[i] + r;
+    const R r = (i > 0 ? fabs(w.e[i - 1]) : R(0.0)) + (i + 1 < n ? fabs(w.e[i]) : R(0.0));
+    const R a = w.dg[i] - r, b = w.dg[i] + r;
     if (i == 0 || a < lo) lo = a;
     if (i == 0 || b > hi) hi = b;
   }
-  const double span = fmax(hi - lo, 1e-30);
-  const double tnorm = fmax(fabs(lo - span * 1e-6), fabs(hi + span * 1e-6));
-  const double pivmin = fmax(1e-290, kEps * tnorm * 1e-6);
-  double* u1 = u + n;
-  double* u2 = u1 + n;
-  double* lm = u2 + n;
-  double* sw = lm + n;
-  double* z = sw + n;
-  const double lam = w.lam[s];
-  const double shift = lam + kEps * fmax(fabs(lam), span * 1e-3) * 4.0;
-  double a_i = w.dg[0] - shift, b_i = n > 1 ? w.e[0] : 0.0, c_i = 0.0;
+  const R span = fmax(hi - lo, R(1e-30));
+  const R tnorm = fmax(fabs(lo - span * R(1e-6)), fabs(hi + span * R(1e-6)));
+  const R pivmin = fmax(Prec<R>::tiny, Prec<R>::eps * tnorm * R(1e-6));
+  R* u1 = u + n;
+  R* u2 = u1 + n;
+  R* lm = u2 + n;
+  R* sw = lm + n;
+  R* z = sw + n;
+  const R lam = w.lam[s];
+  const R shift = lam + Prec<R>::eps * fmax(fabs(lam), span * R(1e-3)) * R(4.0);
+  R a_i = w.dg[0] - shift, b_i = n > 1 ? w.e[0] : R(0.0), c_i = R(0.0);
   for (int i = 0; i < n - 1; ++i) {
-    const double sub = w.e[i];
-    const double d1 = w.dg[i + 1] - shift;
-    const double e1 = i + 2 < n ? w.e[i + 1] : 0.0;
+    const R sub = w.e[i];
+    const R d1 = w.dg[i + 1] - shift;
+    const R e1 = i + 2 < n ? w.e[i + 1] : R(0.0);
     if (fabs(a_i) >= fabs(sub)) {
-      const double pv = fabs(a_i) < pivmin ? (a_i < 0.0 ? -pivmin : pivmin) : a_i;
-      const double l = sub / pv;
-      u[i] = pv; u1[i] = b_i; u2[i] = c_i; lm[i] = l; sw[i] = 0.0;
+      const R pv = fabs(a_i) < pivmin ? (a_i < R(0.0) ? -pivmin : pivmin) : a_i;
+      const R l = sub / pv;
+      u[i] = pv; u1[i] = b_i; u2[i] = c_i; lm[i] = l; sw[i] = R(0.0);
       a_i = d1 - l * b_i;
       b_i = e1 - l * c_i;
-      c_i = 0.0;
+      c_i = R(0.0);
     } else {
-      const double l = a_i / sub;
-      u[i] = sub; u1[i] = d1; u2[i] = e1; lm[i] = l; sw[i] = 1.0;
-      const double na = b_i - l * d1, nc = c_i - l * e1;
+      const R l = a_i / sub;
+      u[i] = sub; u1[i] = d1; u2[i] = e1; lm[i] = l; sw[i] = R(1.0);
+      const R na = b_i - l * d1, nc = c_i - l * e1;
       a_i = na;
       b_i = nc;
-      c_i = 0.0;
+      c_i = R(0.0);
     }
   }
-  u[n - 1] = fabs(a_i) < pivmin ? (a_i < 0.0 ? -pivmin : pivmin) : a_i;
-  u1[n - 1] = 0.0;
-  u2[n - 1] = 0.0;
+  u[n - 1] = fabs(a_i) < pivmin ? (a_i < R(0.0) ? -pivmin : pivmin) : a_i;
+  u1[n - 1] = R(0.0);
+  u2[n - 1] = R(0.0);
   unsigned int h = 2166136261u ^ (unsigned)s * 16777619u;
   for (int i = 0; i < n; ++i) {
     h = h * 1664525u + 1013904223u;
-    z[i] = 0.5 + (double)((h >> 8) & 0xffff) / 65536.0;
+    z[i] = R(0.5) + (R)((h >> 8) & 0xffff) / R(65536.0);
   }
   for (int iter = 0; iter < 3; ++iter) {
     for (int i = 0; i < n - 1; ++i) {
-      if (sw[i] != 0.0) {
-        const double t = z[i];
+      if (sw[i] != R(0.0)) {
+        const R t = z[i];
         z[i] = z[i + 1];
         z[i + 1] = t - lm[i] * z[i];
       } else {
@@ -566,39 +594,40 @@ __global__ void k_rr_invit_sm(int n, int nb, RRWork w) {
       }
     }
     for (int i = n - 1; i >= 0; --i) {
-      double t = z[i];
+      R t = z[i];
       if (i + 1 < n) t -= u1[i] * z[i + 1];
       if (i + 2 < n) t -= u2[i] * z[i + 2];
       z[i] = t / u[i];
     }
-    double nrm = 0.0;
+    R nrm = R(0.0);
     for (int i = 0; i < n; ++i) nrm = fmax(nrm, fabs(z[i]));
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 1.0;
+    const R inv = nrm > R(0.0) ? R(1.0) / nrm : R(1.0);
     for (int i = 0; i < n; ++i) z[i] *= inv;
   }
   for (int i = 0; i < n; ++i) w.V[(size_t)i * nb + s] = z[i];
 }
 
 // ------------------------------------------------------------------ 4a. Cholesky QR (twice) of the tridiagonal eigenvectors
-__global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork w) {
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R> w) {
   __shared__ int keep_nb[512];
-  double* V = w.V;
-  double* G = w.G;
+  R* V = w.V;
+  R* G = w.G;
   for (int pass = 0; pass < 2; ++pass) {
     for (int t = threadIdx.x; t < nb * nb; t += kThreads) {
       const int a = t / nb, b = t % nb;
-      double acc = 0.0;
+      R acc = R(0.0);
       if (b <= a)
         for (int i = 0; i < n; ++i) acc += V[(size_t)i * nb + a] * V[(size_t)i * nb + b];
       G[t] = acc;
     }
     for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
-    block_cholesky(G, nb, keep_nb, 0.0);
+    block_cholesky(G, nb, keep_nb, R(0.0));
     for (int i = threadIdx.x; i < n; i += kThreads) {
-      double* v = V + (size_t)i * nb;
+      R* v = V + (size_t)i * nb;
       for (int s2 = 0; s2 < nb; ++s2) {
-        double acc = v[s2];
+        R acc = v[s2];
         for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * v[p];
         v[s2] = acc / G[s2 * nb + s2];
       }
@@ -608,16 +637,18 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork w)
 }
 
 // ------------------------------------------------------------------ 4b. back-transform, one warp per vector
-__global__ void k_rr_backtransform(int n, int nb, RRWork w) {
-  extern __shared__ double z[];
+template <class R>
+__global__ void k_rr_backtransform(int n, int nb, RRWork<R> w) {
+  extern __shared__ __align__(16) unsigned char z_raw[];
+  R* z = reinterpret_cast<R*>(z_raw);
   const int s = blockIdx.x, lane = threadIdx.x;
   for (int i = lane; i < n; i += 32) z[i] = w.V[(size_t)i * nb + s];
   __syncwarp();
   for (int j = n - 3; j >= 0; --j) {
-    const double tj = w.tau[j];
-    if (tj == 0.0) continue;
-    const double* v = w.ref + (size_t)j * n;
-    double acc = 0.0;
+    const R tj = w.tau[j];
+    if (tj == R(0.0)) continue;
+    const R* v = w.ref + (size_t)j * n;
+    R acc = R(0.0);
     for (int i = j + 1 + lane; i < n; i += 32) acc += v[i] * z[i];
     acc = warp_sum(acc) * tj;
     for (int i = j + 1 + lane; i < n; i += 32) z[i] -= acc * v[i];
@@ -627,52 +658,52 @@ __global__ void k_rr_backtransform(int n, int nb, RRWork w) {
 }
 
 // ------------------------------------------------------------------ 4c. momentum and mapping back
-template <class T>
+template <class R, class T>
 __global__ void __launch_bounds__(kThreads)
-    k_rr_momentum(int n, int o0, int no, int nx, int nb, int want_p, RRWork w,
+    k_rr_momentum(int n, int o0, int no, int nx, int nb, int want_p, RRWork<R> w,
                   T* __restrict__ YZ, int* __restrict__ dropped) {
   __shared__ int keep_nb[512];
   const int tid = threadIdx.x;
-  double* V = w.V;
-  double* Z = w.Z;
-  double* G = w.G;
+  R* V = w.V;
+  R* Z = w.Z;
+  R* G = w.G;
   if (want_p) {
     // G = V^T Zp with Zp = V without its X rows, summed over the W and P rows
     // directly: I - V_X^T V_X would cancel catastrophically once the X rows of
     // V are nearly the identity (a converging block)
     for (int t = tid; t < nb * nb; t += kThreads) {
       const int a = t / nb, b = t % nb;
-      double acc = 0.0;
+      R acc = R(0.0);
       for (int i = nx; i < n; ++i) acc += V[(size_t)i * nb + a] * V[(size_t)i * nb + b];
       G[t] = acc;
     }
     __syncthreads();
     for (int t = tid; t < n * nb; t += kThreads) {  // Z = Zp - V G
       const int i = t / nb, b = t % nb;
-      double acc = i < nx ? 0.0 : V[t];
+      R acc = i < nx ? R(0.0) : V[t];
       for (int a = 0; a < nb; ++a) acc -= V[(size_t)i * nb + a] * G[a * nb + b];
       w.T1[t] = acc;
     }
     __syncthreads();
     for (int t = tid; t < nb * nb; t += kThreads) {  // G = Z^T Z (lower)
       const int a = t / nb, b = t % nb;
-      double acc = 0.0;
+      R acc = R(0.0);
       if (b <= a)
         for (int i = 0; i < n; ++i) acc += w.T1[(size_t)i * nb + a] * w.T1[(size_t)i * nb + b];
       G[t] = acc;
     }
     for (int s2 = tid; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
-    double gref = 0.0;
+    R gref = R(0.0);
     for (int s2 = 0; s2 < nb; ++s2) gref = fmax(gref, G[s2 * nb + s2]);
-    block_cholesky(G, nb, keep_nb, kDrop * fmax(gref, 1e-300));
+    block_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
     for (int i = tid; i < n; i += kThreads) {  // Z <- Z L^-T, dropped columns zero
-      const double* zt = w.T1 + (size_t)i * nb;
-      double* zr = Z + (size_t)i * nb;
+      const R* zt = w.T1 + (size_t)i * nb;
+      R* zr = Z + (size_t)i * nb;
       for (int s2 = 0; s2 < nb; ++s2) {
-        double acc = zt[s2];
+        R acc = zt[s2];
         for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * zr[p];
-        zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : 0.0;
+        zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : R(0.0);
       }
     }
     __syncthreads();
@@ -681,12 +712,12 @@ __global__ void __launch_bounds__(kThreads)
   // y_rest <- y_rest - C y_O, then y <- D y
   for (int a = no - 1; a >= 0; --a) {
     const int i = o0 + a;
-    const double inv = 1.0 / w.L[a * no + a];
+    const R inv = R(1.0) / w.L[a * no + a];
     for (int c = tid; c < 2 * nb; c += kThreads) {
       if (c >= nb && !want_p) continue;
-      double* M_ = c < nb ? V : Z;
+      R* M_ = c < nb ? V : Z;
       const int cc = c < nb ? c : c - nb;
-      double acc = M_[(size_t)i * nb + cc];
+      R acc = M_[(size_t)i * nb + cc];
       for (int b = a + 1; b < no; ++b) acc -= w.L[b * no + a] * M_[(size_t)(o0 + b) * nb + cc];
       M_[(size_t)i * nb + cc] = acc * inv;
     }
@@ -696,16 +727,16 @@ __global__ void __launch_bounds__(kThreads)
   for (int t = tid; t < n * 2 * nb; t += kThreads) {
     const int i = t / (2 * nb), c = t % (2 * nb);
     if ((i >= o0 && i < o0 + no) || (c >= nb && !want_p)) continue;
-    double* M_ = c < nb ? V : Z;
+    R* M_ = c < nb ? V : Z;
     const int cc = c < nb ? c : c - nb;
-    double acc = M_[(size_t)i * nb + cc];
+    R acc = M_[(size_t)i * nb + cc];
     for (int a = 0; a < no; ++a) acc -= w.C[i * no + a] * M_[(size_t)(o0 + a) * nb + cc];
     M_[(size_t)i * nb + cc] = acc;
   }
   __syncthreads();
   for (int t = tid; t < n * nb; t += kThreads) {
     const int i = t / nb, s2 = t % nb;
-    const double d = w.dsc[i];
+    const R d = w.dsc[i];
     YZ[(size_t)i * 2 * nb + s2] = (T)(V[t] * d);
     YZ[(size_t)i * 2 * nb + nb + s2] = want_p ? (T)(Z[t] * d) : T(0);
   }
@@ -716,62 +747,63 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// ------------------------------------------------------------------ 3. inverse iteration
-__global__ void k_rr_invit(int n, int nb, RRWork w) {
+// ------------------------------------------------------------------ R(3.) inverse iteration
+template <class R>
+__global__ void k_rr_invit(int n, int nb, RRWork<R> w) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nb) return;
-  double lo = 0.0, hi = 0.0;
+  R lo = R(0.0), hi = R(0.0);
   for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(w.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(w.e[i]) : 0.0);
-    const double a = w.dg[i] - r, b = w.dg[i] + r;
+    const R r = (i > 0 ? fabs(w.e[i - 1]) : R(0.0)) + (i + 1 < n ? fabs(w.e[i]) : R(0.0));
+    const R a = w.dg[i] - r, b = w.dg[i] + r;
     if (i == 0 || a < lo) lo = a;
     if (i == 0 || b > hi) hi = b;
   }
-  const double span = fmax(hi - lo, 1e-30);
-  const double tnorm = fmax(fabs(lo - span * 1e-6), fabs(hi + span * 1e-6));
-  const double pivmin = fmax(1e-290, kEps * tnorm * 1e-6);
-  double* u = w.scr + (size_t)s * 6 * n;  // U diagonal
-  double* u1 = u + n;                     // first super-diagonal
-  double* u2 = u1 + n;                    // second super-diagonal (pivoting fill)
-  double* lm = u2 + n;                    // multipliers
-  double* sw = lm + n;                    // row-swap flags
-  double* z = sw + n;                     // the vector
-  const double lam = w.lam[s];
+  const R span = fmax(hi - lo, R(1e-30));
+  const R tnorm = fmax(fabs(lo - span * R(1e-6)), fabs(hi + span * R(1e-6)));
+  const R pivmin = fmax(Prec<R>::tiny, Prec<R>::eps * tnorm * R(1e-6));
+  R* u = w.scr + (size_t)s * 6 * n;  // U diagonal
+  R* u1 = u + n;                     // first super-diagonal
+  R* u2 = u1 + n;                    // second super-diagonal (pivoting fill)
+  R* lm = u2 + n;                    // multipliers
+  R* sw = lm + n;                    // row-swap flags
+  R* z = sw + n;                     // the vector
+  const R lam = w.lam[s];
   // a slightly perturbed shift keeps T - shift I from being exactly singular
-  const double shift = lam + kEps * fmax(fabs(lam), span * 1e-3) * 4.0;
-  double a_i = w.dg[0] - shift, b_i = n > 1 ? w.e[0] : 0.0, c_i = 0.0;
+  const R shift = lam + Prec<R>::eps * fmax(fabs(lam), span * R(1e-3)) * R(4.0);
+  R a_i = w.dg[0] - shift, b_i = n > 1 ? w.e[0] : R(0.0), c_i = R(0.0);
   for (int i = 0; i < n - 1; ++i) {
-    const double sub = w.e[i];
-    const double d1 = w.dg[i + 1] - shift;
-    const double e1 = i + 2 < n ? w.e[i + 1] : 0.0;
+    const R sub = w.e[i];
+    const R d1 = w.dg[i + 1] - shift;
+    const R e1 = i + 2 < n ? w.e[i + 1] : R(0.0);
     if (fabs(a_i) >= fabs(sub)) {
-      const double pv = fabs(a_i) < pivmin ? (a_i < 0.0 ? -pivmin : pivmin) : a_i;
-      const double l = sub / pv;
-      u[i] = pv; u1[i] = b_i; u2[i] = c_i; lm[i] = l; sw[i] = 0.0;
+      const R pv = fabs(a_i) < pivmin ? (a_i < R(0.0) ? -pivmin : pivmin) : a_i;
+      const R l = sub / pv;
+      u[i] = pv; u1[i] = b_i; u2[i] = c_i; lm[i] = l; sw[i] = R(0.0);
       a_i = d1 - l * b_i;
       b_i = e1 - l * c_i;
-      c_i = 0.0;
+      c_i = R(0.0);
     } else {
-      const double l = a_i / sub;
-      u[i] = sub; u1[i] = d1; u2[i] = e1; lm[i] = l; sw[i] = 1.0;
-      const double na = b_i - l * d1, nc = c_i - l * e1;
+      const R l = a_i / sub;
+      u[i] = sub; u1[i] = d1; u2[i] = e1; lm[i] = l; sw[i] = R(1.0);
+      const R na = b_i - l * d1, nc = c_i - l * e1;
       a_i = na;
       b_i = nc;
-      c_i = 0.0;
+      c_i = R(0.0);
     }
   }
-  u[n - 1] = fabs(a_i) < pivmin ? (a_i < 0.0 ? -pivmin : pivmin) : a_i;
-  u1[n - 1] = 0.0;
-  u2[n - 1] = 0.0;
+  u[n - 1] = fabs(a_i) < pivmin ? (a_i < R(0.0) ? -pivmin : pivmin) : a_i;
+  u1[n - 1] = R(0.0);
+  u2[n - 1] = R(0.0);
   unsigned int h = 2166136261u ^ (unsigned)s * 16777619u;  // deterministic start vector
   for (int i = 0; i < n; ++i) {
     h = h * 1664525u + 1013904223u;
-    z[i] = 0.5 + (double)((h >> 8) & 0xffff) / 65536.0;
+    z[i] = R(0.5) + (R)((h >> 8) & 0xffff) / R(65536.0);
   }
   for (int iter = 0; iter < 3; ++iter) {
     for (int i = 0; i < n - 1; ++i) {
-      if (sw[i] != 0.0) {
-        const double t = z[i];
+      if (sw[i] != R(0.0)) {
+        const R t = z[i];
         z[i] = z[i + 1];
         z[i + 1] = t - lm[i] * z[i];
       } else {
@@ -779,33 +811,29 @@ __global__ void k_rr_invit(int n, int nb, RRWork w) {
       }
     }
     for (int i = n - 1; i >= 0; --i) {
-      double t = z[i];
+      R t = z[i];
       if (i + 1 < n) t -= u1[i] * z[i + 1];
       if (i + 2 < n) t -= u2[i] * z[i + 2];
       z[i] = t / u[i];
     }
-    double nrm = 0.0;
+    R nrm = R(0.0);
     for (int i = 0; i < n; ++i) nrm = fmax(nrm, fabs(z[i]));
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 1.0;
+    const R inv = nrm > R(0.0) ? R(1.0) / nrm : R(1.0);
     for (int i = 0; i < n; ++i) z[i] *= inv;
   }
   for (int i = 0; i < n; ++i) w.V[(size_t)i * nb + s] = z[i];
 }
 
-}  // namespace
-
-template <class T>
-void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ,
-                   double* theta, int* dropped, Buf& work, bool /*fp64*/, double* /*dbg*/) {
-  ProfScope ps(kProfRR);
-  FF_REQUIRE(d.ns <= 1024 && d.no <= 1024 && d.nb <= 512 && d.o0 + d.no <= d.ns,
-             FF_ERR_INVALID_ARG, "Rayleigh-Ritz basis too large");
+// one Rayleigh-Ritz step in working precision R, output in T
+template <class R, class T>
+void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, double* theta,
+            int* dropped, Buf& work) {
   const size_t n = d.ns, nb = d.nb, no = d.no;
   const size_t t1 = std::max(n * nb, 2 * n);
   const size_t total =
       2 * n * n + no * no + 5 * n + nb + 2 * n * nb + nb * nb + t1 + 6 * n * nb + 2 * n * no;
-  double* p = reinterpret_cast<double*>(work.ensure(sizeof(double) * total + sizeof(int) * n + 256));
-  RRWork w;
+  R* p = reinterpret_cast<R*>(work.ensure(sizeof(R) * total + sizeof(int) * n + 256));
+  RRWork<R> w;
   w.As = p; p += n * n;
   w.ref = p; p += n * n;
   w.L = p; p += no * no;
@@ -825,48 +853,62 @@ void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, 
   w.keep = reinterpret_cast<int*>(p);
   static bool attr = false;
   if (!attr) {
-    FF_CUDA(cudaFuncSetAttribute(k_rr_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FF_CUDA(cudaFuncSetAttribute(k_rr_tridiag<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxDynSmem));
-    FF_CUDA(cudaFuncSetAttribute(k_rr_house_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kMaxDynSmem));
-    FF_CUDA(cudaFuncSetAttribute(k_rr_invit_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FF_CUDA(cudaFuncSetAttribute(k_rr_house_cluster<R>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem));
+    FF_CUDA(cudaFuncSetAttribute(k_rr_invit_sm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxDynSmem));
     attr = true;
   }
-  const size_t tri_bytes = sizeof(double) * n * n;
+  const size_t tri_bytes = sizeof(R) * n * n;
   const bool tri_smem = tri_bytes <= kMaxDynSmem;
   const size_t rpc = (n + kCS - 1) / kCS;
-  const size_t cl_bytes = sizeof(double) * (rpc * n + 2 * n + 4 * rpc + 2);
+  const size_t cl_bytes = sizeof(R) * (rpc * n + 2 * n + 4 * rpc + 2);
   const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
+  const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
   // transform (one block); Householder by the cluster when its rows fit
-  (k_rr_tridiag<<<1, kThreads, tri_smem ? tri_bytes : 0, st>>>(A, B, d.ns, d.o0, d.no, w,
-                                                               tri_smem ? 1 : 0,
-                                                               use_cluster ? 0 : 1, d.drop),
+  (k_rr_tridiag<R><<<1, kThreads, tri_smem ? tri_bytes : 0, st>>>(
+       A, B, d.ns, d.o0, d.no, w, tri_smem ? 1 : 0, use_cluster ? 0 : 1, drop),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
-    (k_rr_house_cluster<<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
+    (k_rr_house_cluster<R><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
-  (k_rr_eigvals_mc<<<(unsigned)nb, 32, 0, st>>>(d.ns, d.nb, w, theta), ::ff::note_launch());
+  (k_rr_eigvals_mc<R><<<(unsigned)nb, 32, 0, st>>>(d.ns, d.nb, w, theta), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  const size_t iv_bytes = sizeof(double) * kIV * 6 * n;
+  const size_t iv_bytes = sizeof(R) * kIV * 6 * n;
   if (iv_bytes <= kMaxDynSmem) {
-    (k_rr_invit_sm<<<(unsigned)((nb + kIV - 1) / kIV), kIV, iv_bytes, st>>>(d.ns, d.nb, w),
+    (k_rr_invit_sm<R><<<(unsigned)((nb + kIV - 1) / kIV), kIV, iv_bytes, st>>>(d.ns, d.nb, w),
      ::ff::note_launch());
   } else {
-    (k_rr_invit<<<(unsigned)((nb + 31) / 32), 32, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
+    (k_rr_invit<R><<<(unsigned)((nb + 31) / 32), 32, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
-  (k_rr_cholqr<<<1, kThreads, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
+  (k_rr_cholqr<R><<<1, kThreads, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  (k_rr_backtransform<<<(unsigned)nb, 32, sizeof(double) * n, st>>>(d.ns, d.nb, w),
+  (k_rr_backtransform<R><<<(unsigned)nb, 32, sizeof(R) * n, st>>>(d.ns, d.nb, w),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  (k_rr_momentum<T><<<1, kThreads, 0, st>>>(d.ns, d.o0, d.no, d.nx, d.nb, d.want_p, w, YZ,
-                                            dropped),
+  (k_rr_momentum<R, T><<<1, kThreads, 0, st>>>(d.ns, d.o0, d.no, d.nx, d.nb, d.want_p, w, YZ,
+                                               dropped),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+template <class T>
+void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ,
+                   double* theta, int* dropped, Buf& work, bool fp64, double* /*dbg*/) {
+  ProfScope ps(kProfRR);
+  FF_REQUIRE(d.ns <= 1024 && d.no <= 1024 && d.nb <= 512 && d.o0 + d.no <= d.ns,
+             FF_ERR_INVALID_ARG, "Rayleigh-Ritz basis too large");
+  if (fp64)
+    rr_run<double, T>(st, A, B, d, YZ, theta, dropped, work);
+  else
+    rr_run<float, T>(st, A, B, d, YZ, theta, dropped, work);
 }
 
 template void rayleigh_ritz<float>(cudaStream_t, const double*, const double*, RRDims, float*,

@@ -203,7 +203,8 @@ struct Solver {
   const T* aval;  // interleaved (H, M) of this phase's precision
   long long n;
   int nb, kw, ld;
-  bool fp64;
+  bool fp64;      // FP64 blocks
+  bool rr64;      // FP64 Rayleigh-Ritz
   T *S[2], *HS[2], *MS[2];
   T *c0, *Mc0;
   float *cres, *cd0, *cd1, *cx;
@@ -271,6 +272,7 @@ struct Phase {
   double gain = 0.999;             // progress = largest residual below gain x the last mark
   double stall_below = INFINITY;   // iterations only count as stalled below this residual
   int best_slot = 22;              // workspace slot that keeps the best block (dense n x nb)
+  bool rr_fp32 = false;            // Rayleigh-Ritz in FP32 (else FP64)
   bool have_best = false;          // out: the best-block slot holds a block
 };
 
@@ -285,6 +287,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   s.aval = static_cast<const T*>(ph.aval);
   s.n = c->n;
   s.fp64 = sizeof(T) == 8;
+  s.rr64 = !ph.rr_fp32;
   const bool incl_c0 = !o.exclude_constant;
   s.kw = incl_c0 ? k - 1 : k;
   // block width: the wanted modes plus guard vectors, rounded up to a multiple
@@ -375,7 +378,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     gram<T>(st, s.S[cur], ld, nb, s.MS[cur], ld, nb, n, s.Bg, 1.0, false, c->scratch[0]);
     RRDims d0{nb, nb, nb, 0, 0, nb};
     if (warm && attempt == 0) d0.drop = s.fp64 ? 1e-10 : 1e-6;
-    rayleigh_ritz<T>(st, s.Ag, s.Bg, d0, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.fp64);
+    rayleigh_ritz<T>(st, s.Ag, s.Bg, d0, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
     int dropped = 0;
     FF_CUDA(cudaMemcpyAsync(&dropped, s.dropped_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     FF_CUDA(cudaStreamSynchronize(st));
@@ -506,7 +509,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     gram<T>(st, s.S[cur], ld, ns, s.HS[cur], ld, ns, n, s.Ag, 1.0, false, c->scratch[0]);
     gram<T>(st, s.S[cur], ld, ns, s.MS[cur], ld, ns, n, s.Bg, 1.0, false, c->scratch[0]);
     RRDims dd{ns, nb, nb, 1, nb, nb};
-    rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.fp64);
+    rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
     const int nxt = 1 - cur;
     // X' = S Y, P' = S Z; H P', M P' from the old products; (H X', M X') recomputed
     // from X' itself so that the residual seen by the solver is that of the
@@ -597,6 +600,7 @@ ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
   p32.stall = 2;
   p32.gain = 0.7;
   p32.stall_below = 1e-2;
+  p32.rr_fp32 = true;
   p32.best_slot = 21;
   const float* X0f = nullptr;
   if (X0) {  // the caller's FP64 start block, rounded
