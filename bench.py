@@ -3,9 +3,11 @@
 One step = rkpm_build + assemble_hessian + eigenmodes on the seeded solid torus
 (R = 0.5, r = 0.2, 50,000 particles, support 2.0x spacing, E = 1e6, nu = 0.4,
 k = 32 modes with the constant one) with the inputs already resident in HBM.
-The metric is the time to k modes at relative residual 1e-6.  L2 is flushed
-(a 256 MB write) before every timed step; each step is timed with CUDA events
-on the library's stream.  Prints one JSON line.
+The metric is the time to k modes at relative residual 1e-6: `value` is the
+plain path (seeded random start block); `warm` times the same step started
+from the trained warm-start network (features and inference included).  L2 is
+flushed (a 256 MB write) before every timed step; each step is timed with CUDA
+events on the library's stream.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--prec fp64|fp32] [--tol T]
@@ -174,16 +176,31 @@ def run_ours(args):
     a = torch.from_numpy(c.a).to(dev)
     ctx = binding.Context(local, args.prec)
     opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
-                                fp32_phase=args.fp32_phase)
+                                fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64)
+    from paper_2605_29318_gb300 import train_warmstart
+    net = binding.Net(local)
+    net.set_params(train_warmstart.load_weights())
     modes = torch.empty((32, c.n), dtype=ctx.dtype, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
 
-    def step():
+    def step(warm=False):
         ctx.rkpm_build(X, v, a)
         ctx.assemble_hessian(None, None, c.E, c.nu)
-        ev, _, rep, status = ctx.eigenmodes(32, opts, modes_out=modes, check=False)
+        X0 = ctx.warmstart_block(net, 32, opts) if warm else None
+        ev, _, rep, status = ctx.eigenmodes(32, opts, X0=X0, modes_out=modes, check=False)
         return ev, rep, status
+
+    def timed(warm):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        ev, rep, status = step(warm)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), rep, status
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -196,25 +213,27 @@ def run_ours(args):
     times, reps = [], []
     with Clocks(local) as clk:
         for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(st)
-            ev, rep, status = step()
-            e1.record(st)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
+            t, rep, status = timed(False)
+            times.append(t)
             reps.append((rep, status))
     launches = binding.launch_count() - launches0
     prof = ctx.profile_read()
     ctx.profile(False)
+    # the same step from the learned warm start
+    for _ in range(args.warmup):
+        timed(True)
+    wtimes, wreps = [], []
+    for _ in range(args.steps):
+        t, rep, status = timed(True)
+        wtimes.append(t)
+        wreps.append((rep, status))
+    wms = sum(wtimes) / len(wtimes)
     n, n1, n2 = ctx.sizes()
     ms = sum(times) / len(times)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
+        t = torch.tensor([ms, wms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, wms = float(t[0].item()), float(t[1].item())
         dist.barrier()
 
     # end to end through the public call on host buffers (H2D + D2H inside)
@@ -256,7 +275,8 @@ def run_ours(args):
         "dtype": "f64" if args.prec == "fp64" else "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.prec, "tol": args.tol,
-                   "cheb_degree": args.cheb, "n": n, "n1": n1, "n2": n2,
+                   "cheb_degree": args.cheb, "cheb_degree_fp64": args.cheb_fp64,
+                   "n": n, "n1": n1, "n2": n2,
                    "l2": "flushed by a 256 MB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_cheb_step_vec (Chebyshev preconditioner step)",
@@ -268,6 +288,12 @@ def run_ours(args):
         "spmm": {"avg_launch_ms": round(stot / max(scnt, 1), 5), "launches": scnt,
                  "algorithmic_gbs": round(spmm_gbs, 1) if spmm_gbs else None},
         "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
+        "warm": {"value": round(wms / 1000.0, 5), "unit": "s",
+                 "plain_over_warm": round(ms / wms, 4),
+                 "iterations": wreps[-1][0]["iterations"],
+                 "fp32_iterations": wreps[-1][0]["fp32_iterations"],
+                 "status": wreps[-1][1], "max_residual": wreps[-1][0]["max_residual"],
+                 "network": "paper_2605_29318_gb300/weights/warmstart_k32.f32"},
         "solver": {"iterations": last_rep["iterations"],
                    "fp32_iterations": last_rep["fp32_iterations"], "status": last_status,
                    "max_residual": last_rep["max_residual"],
@@ -280,6 +306,7 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_json()
     print(json.dumps(line), flush=True)
+    net.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -293,6 +320,7 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--cheb", type=int, default=16)
+    ap.add_argument("--cheb-fp64", type=int, default=64)
     ap.add_argument("--fp32-phase", type=int, default=1, choices=[0, 1],
                     help="FP64 contexts: iterate in FP32 first, then finish in FP64")
     ap.add_argument("--max-iter", type=int, default=500)

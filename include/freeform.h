@@ -125,6 +125,8 @@ typedef struct {
                            until the residual reaches fp32_tol or stops falling, then
                            finish in FP64 from that block; 0 = FP64 throughout (1) */
   double fp32_tol;      /* residual at which the FP32 phase hands over (1e-4) */
+  int cheb_degree_fp64; /* Chebyshev degree of the FP64 phase that follows an FP32 phase;
+                           0 = cheb_degree (64) */
 } ff_eig_opts;
 
 typedef struct {

@@ -165,6 +165,7 @@ void ff_eig_opts_default(ff_eig_opts* o) {
   o->verbose = 0;
   o->fp32_phase = 1;
   o->fp32_tol = 1e-4;
+  o->cheb_degree_fp64 = 64;
 }
 
 ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, double* eigvals,
@@ -177,7 +178,8 @@ ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, 
     ff_eig_opts o;
     ff_eig_opts_default(&o);
     if (opts) o = *opts;
-    FF_REQUIRE(o.tol > 0 && o.max_iter >= 0 && o.guard >= 0 && o.fp32_tol > 0, FF_ERR_INVALID_ARG,
+    FF_REQUIRE(o.tol > 0 && o.max_iter >= 0 && o.guard >= 0 && o.fp32_tol > 0 &&
+                   o.cheb_degree_fp64 >= 0, FF_ERR_INVALID_ARG,
                "bad options");
     if (rep) *rep = ff_eig_report{};
     result = ff::run_eigenmodes(c, k, o, X0, eigvals, modes, rep);

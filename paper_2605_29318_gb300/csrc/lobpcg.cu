@@ -619,6 +619,7 @@ ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
   // FP64 phase from the FP32 phase's best block
   ff_eig_opts o2 = o;
   o2.max_iter = std::max(0, o.max_iter - r1.iterations);
+  if (o.cheb_degree_fp64 > 0) o2.cheb_degree = o.cheb_degree_fp64;
   if (o.time_budget_s > 0) {
     const double used = std::chrono::duration<double>(clock::now() - t0).count();
     o2.time_budget_s = std::max(1e-9, o.time_budget_s - used);
