@@ -309,13 +309,44 @@ __global__ void k_gram_partial(const T* __restrict__ A, int lda, int p, const T*
   }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int pq,
-                              double* __restrict__ out, double alpha, int accumulate) {
+__global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int pq, int q,
+                              double* __restrict__ out, int ldo, double alpha, int accumulate) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= pq) return;
   double s = 0.0;
   for (int c = 0; c < chunks; ++c) s += part[(long long)c * pq + t];
-  out[t] = accumulate ? out[t] + alpha * s : alpha * s;
+  double* o = out + (long long)(t / q) * ldo + t % q;
+  *o = accumulate ? *o + alpha * s : alpha * s;
+}
+
+// out[c * ldo + c] = sum_r A[r][c] B[r][c] for the columns c outside [w0, w1)
+// (one block per column, FP64 sums)
+template <class T>
+__global__ void __launch_bounds__(512)
+    k_gram_diag(const T* __restrict__ A, const T* __restrict__ B, int ld, long long n, int w0,
+                int w1, double* __restrict__ out, int ldo) {
+  const int c = (int)blockIdx.x >= w0 ? (int)blockIdx.x + (w1 - w0) : (int)blockIdx.x;
+  double s = 0.0;
+  for (long long r = threadIdx.x; r < n; r += blockDim.x)
+    s += (double)A[r * ld + c] * (double)B[r * ld + c];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  __shared__ double red[16];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    if (threadIdx.x == 0) out[(long long)c * ldo + c] = t;
+  }
+}
+
+// A: upper block triangle from the lower one; B: W rows from the W columns
+__global__ void k_gram_mirror(double* __restrict__ A, double* __restrict__ B, int ns, int nb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * ns) return;
+  const int i = t / ns, j = t % ns;
+  if (i / nb < j / nb) A[t] = A[(long long)j * ns + i];
+  if (i / nb == 1 && j / nb != 1) B[t] = B[(long long)j * ns + i];
 }
 
 // C[r][cmap(j)] = beta * C[...] + sum_i A[r][i] * Y[i][j]; cmap sends columns
@@ -353,6 +384,84 @@ __global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T*
 
 }  // namespace
 
+// FP64 block product (H x, M x) for m % 4 == 0: each lane owns 4 columns (two
+// 16-byte loads per gathered row), so a 40-column block keeps 30 of 32 lanes
+// busy.  GB300 charges an FP64 warp instruction the same whatever the active
+// lanes, so lane use is FP64 throughput; and H x is accumulated as
+// sum_l h_kl x_l - (sum_l h_kl) x_k (two FMAs per value and nonzero instead of
+// the subtract-and-FMA of the difference form; in FP64 the lost cancellation
+// costs ~1e-12 relative).
+__global__ void k_spmm_hm_f64x4(const long long* __restrict__ ptr, const int* __restrict__ col,
+                                const double* __restrict__ val, long long n,
+                                const double* __restrict__ X, int ldx, double* __restrict__ YH,
+                                double* __restrict__ YM, int ldy, int m) {
+  const int lane = threadIdx.x & 31;
+  const int G = m / 4, P = 32 / G;
+  const int g = lane / G, cv = (lane % G) * 4;
+  const bool act = g < P;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+    const long long s = ptr[k], e = ptr[k + 1];
+    double ah[4] = {0, 0, 0, 0}, am[4] = {0, 0, 0, 0}, hs = 0.0;
+    long long e0 = act ? s + g : e;
+    for (; e0 + P < e; e0 += 2 * P) {
+      const int l0 = col[e0], l1 = col[e0 + P];
+      const double2 hm0 = *reinterpret_cast<const double2*>(val + 2 * e0);
+      const double2 hm1 = *reinterpret_cast<const double2*>(val + 2 * (e0 + P));
+      const double2* p0 = reinterpret_cast<const double2*>(X + (long long)l0 * ldx + cv);
+      const double2* p1 = reinterpret_cast<const double2*>(X + (long long)l1 * ldx + cv);
+      const double2 a0 = __ldg(p0), b0 = __ldg(p0 + 1), a1 = __ldg(p1), b1 = __ldg(p1 + 1);
+      hs += hm0.x + hm1.x;
+      ah[0] = fma(hm0.x, a0.x, ah[0]); ah[1] = fma(hm0.x, a0.y, ah[1]);
+      ah[2] = fma(hm0.x, b0.x, ah[2]); ah[3] = fma(hm0.x, b0.y, ah[3]);
+      am[0] = fma(hm0.y, a0.x, am[0]); am[1] = fma(hm0.y, a0.y, am[1]);
+      am[2] = fma(hm0.y, b0.x, am[2]); am[3] = fma(hm0.y, b0.y, am[3]);
+      ah[0] = fma(hm1.x, a1.x, ah[0]); ah[1] = fma(hm1.x, a1.y, ah[1]);
+      ah[2] = fma(hm1.x, b1.x, ah[2]); ah[3] = fma(hm1.x, b1.y, ah[3]);
+      am[0] = fma(hm1.y, a1.x, am[0]); am[1] = fma(hm1.y, a1.y, am[1]);
+      am[2] = fma(hm1.y, b1.x, am[2]); am[3] = fma(hm1.y, b1.y, am[3]);
+    }
+    for (; e0 < e; e0 += P) {
+      const int l0 = col[e0];
+      const double2 hm0 = *reinterpret_cast<const double2*>(val + 2 * e0);
+      const double2* p0 = reinterpret_cast<const double2*>(X + (long long)l0 * ldx + cv);
+      const double2 a0 = __ldg(p0), b0 = __ldg(p0 + 1);
+      hs += hm0.x;
+      ah[0] = fma(hm0.x, a0.x, ah[0]); ah[1] = fma(hm0.x, a0.y, ah[1]);
+      ah[2] = fma(hm0.x, b0.x, ah[2]); ah[3] = fma(hm0.x, b0.y, ah[3]);
+      am[0] = fma(hm0.y, a0.x, am[0]); am[1] = fma(hm0.y, a0.y, am[1]);
+      am[2] = fma(hm0.y, b0.x, am[2]); am[3] = fma(hm0.y, b0.y, am[3]);
+    }
+    for (int q = 1; q < P; ++q) {  // groups are at most 3 for the 40-column block
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double th = __shfl_down_sync(kFull, ah[u], q * G);
+        const double tm = __shfl_down_sync(kFull, am[u], q * G);
+        if (g == 0) {
+          ah[u] += th;
+          am[u] += tm;
+        }
+      }
+      const double ts = __shfl_down_sync(kFull, hs, q * G);
+      if (g == 0) hs += ts;
+    }
+    if (g == 0) {
+      const double2* pk = reinterpret_cast<const double2*>(X + k * ldx + cv);
+      const double2 xa = pk[0], xb = pk[1];
+      if (YH) {
+        double2* o = reinterpret_cast<double2*>(YH + k * ldy + cv);
+        o[0] = make_double2(fma(-hs, xa.x, ah[0]), fma(-hs, xa.y, ah[1]));
+        o[1] = make_double2(fma(-hs, xb.x, ah[2]), fma(-hs, xb.y, ah[3]));
+      }
+      if (YM) {
+        double2* o = reinterpret_cast<double2*>(YM + k * ldy + cv);
+        o[0] = make_double2(am[0], am[1]);
+        o[1] = make_double2(am[2], am[3]);
+      }
+    }
+  }
+}
+
 template <class T>
 void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T* val, long long n,
                  const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
@@ -364,6 +473,14 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
                       reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
                       (!YH || reinterpret_cast<uintptr_t>(YH) % 16 == 0) &&
                       (!YM || reinterpret_cast<uintptr_t>(YM) % 16 == 0);
+  if constexpr (sizeof(T) == 8) {
+    if (vec_ok && m % 4 == 0 && m <= 128 && reinterpret_cast<uintptr_t>(val) % 16 == 0) {
+      (k_spmm_hm_f64x4<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m),
+       ::ff::note_launch());
+      FF_LAUNCH_CHECK();
+      return;
+    }
+  }
   if (vec_ok)
     (k_spmm_hm_vec<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m), ::ff::note_launch());
   else
@@ -393,7 +510,7 @@ void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const floa
 
 template <class T>
 void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int q, long long n,
-          double* out, double alpha, bool accumulate, Buf& part) {
+          double* out, double alpha, bool accumulate, Buf& part, int ldo) {
   if (p <= 0 || q <= 0) return;
   ProfScope ps(kProfGram);
   const int tiles = ((p + 31) / 32) * ((q + 31) / 32);
@@ -405,8 +522,28 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
   dim3 grid((unsigned)chunks, (unsigned)tiles);
   (k_gram_partial<T><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  (k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, p * q, out, alpha,
+  (k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, p * q, q, out,
+                                                    ldo < 0 ? q : ldo, alpha,
                                                     accumulate ? 1 : 0), ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+}
+
+template <class T>
+void gram_rr(cudaStream_t st, const T* S, const T* HS, const T* MS, int ld, int nb, int nblk,
+             long long n, double* A, double* B, Buf& part) {
+  const int ns = nblk * nb;
+  // lower block triangle: A_ij = S_i^T (H S_j) for block i >= j.  The products
+  // of the smooth, converging blocks (H X) are the accurate ones; W^T (H X)
+  // is taken rather than X^T (H W), whose rounding follows the rough W.
+  for (int j = 0; j < nblk; ++j)
+    gram<T>(st, S + j * nb, ld, ns - j * nb, HS + j * nb, ld, nb, n,
+            A + (long long)j * nb * ns + j * nb, 1.0, false, part, ns);
+  gram<T>(st, S, ld, ns, MS + nb, ld, nb, n, B + nb, 1.0, false, part, ns);
+  ProfScope ps(kProfGram);
+  (k_gram_diag<T><<<(unsigned)(ns - nb), 512, 0, st>>>(S, MS, ld, n, nb, 2 * nb, B, ns),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+  (k_gram_mirror<<<(ns * ns + 255) / 256, 256, 0, st>>>(A, B, ns, nb), ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
@@ -439,9 +576,13 @@ template void spmm_hm_raw<float>(cudaStream_t, const long long*, const int*, con
 template void spmm_hm_raw<double>(cudaStream_t, const long long*, const int*, const double*,
                                   long long, const double*, int, double*, double*, int, int);
 template void gram<float>(cudaStream_t, const float*, int, int, const float*, int, int, long long,
-                          double*, double, bool, Buf&);
+                          double*, double, bool, Buf&, int);
 template void gram<double>(cudaStream_t, const double*, int, int, const double*, int, int,
-                           long long, double*, double, bool, Buf&);
+                           long long, double*, double, bool, Buf&, int);
+template void gram_rr<float>(cudaStream_t, const float*, const float*, const float*, int, int, int,
+                             long long, double*, double*, Buf&);
+template void gram_rr<double>(cudaStream_t, const double*, const double*, const double*, int, int,
+                              int, long long, double*, double*, Buf&);
 template void block_update<float>(cudaStream_t, const float*, int, int, const float*, int, float*,
                                   int, long long, float, int, int, int);
 template void block_update<double>(cudaStream_t, const double*, int, int, const double*, int,

@@ -13,10 +13,20 @@ void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const floa
                const float* hdiag, long long n, int m, int ld, const float* din, float* dout,
                float* x, float* res, float c1, float c2);
 
-// out (p x q, row-major, FP64) (+)= alpha * A^T B over n rows
+// out (p x q, row-major with leading dimension ldo (default q), FP64)
+// (+)= alpha * A^T B over n rows
 template <class T>
 void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int q, long long n,
-          double* out, double alpha, bool accumulate, Buf& part);
+          double* out, double alpha, bool accumulate, Buf& part, int ldo = -1);
+
+// Gram matrices of the Rayleigh-Ritz step on the basis S = [X | W | P] (nblk
+// blocks of nb columns, ns = nblk * nb): A = S^T H S (the block lower triangle,
+// mirrored) and of B = S^T M S the W columns and rows and the diagonal -- the
+// only entries the Rayleigh-Ritz step reads, since X and P are M-orthonormal
+// and M-orthogonal to each other by construction
+template <class T>
+void gram_rr(cudaStream_t st, const T* S, const T* HS, const T* MS, int ld, int nb, int nblk,
+             long long n, double* A, double* B, Buf& part);
 
 // C (n x q, with the column split described in linalg.cu) = beta C + A Y, Y p x q row-major
 // with leading dimension ldy (default q)

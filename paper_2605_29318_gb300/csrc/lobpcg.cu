@@ -506,8 +506,8 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     }
     s.spmm(W, s.HS[cur] + nb, s.MS[cur] + nb, nb);
     const int ns = has_p ? 3 * nb : 2 * nb;
-    gram<T>(st, s.S[cur], ld, ns, s.HS[cur], ld, ns, n, s.Ag, 1.0, false, c->scratch[0]);
-    gram<T>(st, s.S[cur], ld, ns, s.MS[cur], ld, ns, n, s.Bg, 1.0, false, c->scratch[0]);
+    gram_rr<T>(st, s.S[cur], s.HS[cur], s.MS[cur], ld, nb, has_p ? 3 : 2, n, s.Ag, s.Bg,
+               c->scratch[0]);
     RRDims dd{ns, nb, nb, 1, nb, nb};
     rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
     const int nxt = 1 - cur;
