@@ -70,6 +70,42 @@ def assemble(n, ptr, idx, phi, dphi, v, E, nu, dense=False):
     return H, M
 
 
+def rows(ks, X, v, a, E, nu):
+    """Rows ks of H_w (Prop. 1) and M (Eq. 14) for a cloud of any size, from the
+    definition evaluated only where it is non-zero: row k sums over the
+    quadrature points X_i that node k covers, each with the shape functions of
+    its own covering nodes (``rkpm.shape_functions_at`` on that node set).
+    Returns a list of (cols, H_row, M_row), cols ascending, FP64."""
+    from . import rkpm
+    X = np.asarray(X, dtype=np.float32)
+    n = X.shape[0]
+    Xd = X.astype(F64)
+    ad = np.asarray(a, dtype=np.float32).astype(F64)
+    lam, mu = lame(_per_particle(E, n), _per_particle(nu, n))
+    vd = _per_particle(v, n)
+    amax = float(ad.max())
+    out = []
+    for k in ks:
+        # quadrature points node k covers (candidates within the largest radius)
+        near = np.nonzero(((Xd - Xd[k]) ** 2).sum(1) <= (amax * 1.001) ** 2)[0]
+        hs, ms = {}, {}
+        for i in near:
+            cov = rkpm.neighbours_query(X[i:i + 1], X, a)[0]
+            if k not in cov:
+                continue
+            phi, dphi = rkpm.shape_functions_at(X[i:i + 1], X[cov], np.asarray(a)[cov],
+                                                scale=[ad[i]])
+            j = int(np.nonzero(cov == k)[0][0])
+            wh = vd[i] * (lam[i] + 4.0 * mu[i])
+            gk = dphi[:, 0, j]
+            for jj, l in enumerate(cov):
+                hs[l] = hs.get(l, 0.0) + wh * float(gk @ dphi[:, 0, jj])
+                ms[l] = ms.get(l, 0.0) + vd[i] * phi[0, j] * phi[0, jj]
+        cols = np.array(sorted(hs), dtype=np.int64)
+        out.append((cols, np.array([hs[l] for l in cols]), np.array([ms[l] for l in cols])))
+    return out
+
+
 def neo_hookean_psi(F, lam, mu):
     """Psi(F) of Eq. 16 for a batch of 3x3 deformation gradients F (m, 3, 3)."""
     lbar = lam + mu

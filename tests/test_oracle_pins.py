@@ -511,3 +511,19 @@ def test_bf16_rounding_matches_its_definition():
     assert r[6] == 0.0
     m, e = np.frexp(r[np.isfinite(r) & (r != 0)])
     assert np.all(np.abs(m * 2 ** 8 - np.round(m * 2 ** 8)) == 0)   # 8-bit significand
+
+
+def test_single_rows_match_the_full_assembly():
+    """assembly.rows (one row from its covering quadrature points) against the
+    full sparse assembly, on a heterogeneous cloud."""
+    c = synth.unit_cube(500, seed=12)
+    rng = np.random.default_rng(3)
+    E = rng.uniform(1e4, 1e6, c.n)
+    nu = rng.uniform(0.2, 0.45, c.n)
+    ptr, idx, phi, dphi, _ = _build(c)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, E, nu)
+    for k, (cols, h, m) in zip([0, 77, 499], assembly.rows([0, 77, 499], c.X, c.v, c.a, E, nu)):
+        np.testing.assert_array_equal(cols, H[k].indices)
+        np.testing.assert_allclose(h, H[k].data, rtol=1e-9, atol=1e-12 * np.abs(H[k].data).max())
+        np.testing.assert_allclose(m, M[k].toarray()[0, cols], rtol=1e-9,
+                                   atol=1e-12 * np.abs(M[k].data).max())
