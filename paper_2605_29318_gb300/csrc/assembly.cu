@@ -243,19 +243,35 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
                                                    nu, E0, nu0, c->wh.as<float>(),
                                                    c->flags.as<DevFlags>()), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  // pass 1: unique columns per row (table of 2048 slots per warp, 4 warps per block)
-  const int tsize1 = 2048, wpb1 = 4;
+  // pass 1: unique columns per row, in a table of 2048 slots per warp (4 warps
+  // per block); clouds of uneven density (wide supports reaching into dense
+  // regions) retry with 16384 slots per warp (2 warps per block)
   int* cnt = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (n + 1)));
-  int grid1 = (int)std::min<long long>(ceil_div(n, wpb1), 152LL * 16);
-  (k_pattern_count<<<grid1, 32 * wpb1, sizeof(int) * tsize1 * wpb1, st>>>(
-      c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
-      c->nbrT_idx.as<int>(), n, tsize1, cnt, c->flags.as<DevFlags>()), ::ff::note_launch());
-  FF_LAUNCH_CHECK();
-  DevFlags f = read_flags(c);
+  DevFlags f{};
+  int tsize1 = 2048;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    tsize1 = attempt == 0 ? 2048 : 16384;
+    const int wpb1 = attempt == 0 ? 4 : 2;
+    const size_t smem1 = sizeof(int) * tsize1 * wpb1;
+    if (smem1 > 48 * 1024)
+      FF_CUDA(cudaFuncSetAttribute(k_pattern_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem1));
+    if (attempt > 0) reset_flags(c);
+    int grid1 = (int)std::min<long long>(ceil_div(n, wpb1), 152LL * 16);
+    (k_pattern_count<<<grid1, 32 * wpb1, smem1, st>>>(
+        c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
+        c->nbrT_idx.as<int>(), n, tsize1, cnt, c->flags.as<DevFlags>()), ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    f = read_flags(c);
+    const bool overflow =
+        f.code == FF_ERR_INVALID_ARG && f.max_row > 0 && f.max_row * 2 > tsize1;
+    if (!overflow) break;
+  }
   if (f.code == FF_ERR_INVALID_ARG) {
     throw Error(FF_ERR_INVALID_ARG,
-                f.max_row > 0 && f.index >= 0 && f.index < n && f.max_row * 2 > tsize1
-                    ? "a Hessian row has more than 1024 distinct columns (support too large)"
+                f.max_row > 0 && f.max_row * 2 > tsize1
+                    ? "a Hessian row has more than " + std::to_string(tsize1 / 2) +
+                          " distinct columns (support too large)"
                     : "invalid material (need E > 0, 0 <= nu < 0.5) at particle " +
                           std::to_string(f.index));
   }

@@ -125,7 +125,9 @@ def gaussian_mixture(n=1_000_000, n_comp=64, seed=3, support=2.0, nu=0.45, k=64,
     scales) so that components overlap; samples truncated at 3 sigma.  The
     volume of particle i is taken from the local density of its ``knn``
     nearest neighbours, v_i = (4/3) pi d_i^3 / knn; E is log-uniform in
-    [1e4, 1e7] per component (heterogeneous material)."""
+    [1e4, 1e7] per component (heterogeneous material).  Supports get the
+    coverage floor of ``support_floor`` (the thin outskirts of the Gaussians
+    otherwise leave particles covered by fewer than four nodes)."""
     from scipy.spatial import cKDTree
 
     rng = _rng(seed)
@@ -213,15 +215,17 @@ def warmstart_shape(seed, nmin=20000, nmax=100000, k=32):
     return c
 
 
-def support_floor(X, a, m=8):
+def support_floor(X, a, m=8, factor=1.0001):
     """Widen supports so that every particle is covered by its m nearest other
-    particles: a_k <- max(a_k, 1.0001 d(j, k)) over every j that has k among
+    particles: a_k <- max(a_k, factor d(j, k)) over every j that has k among
     its m nearest (node k covers X_j iff |X_j - p_k| < a_k).  Random sampling
     otherwise leaves the odd thin spot with too few covering nodes for the
-    moment matrix."""
+    moment matrix.  With factor near 1 a node reaches such a particle at the
+    edge of its support, where the B-spline weight is ~(4/3)(1 - 1/factor)^3;
+    factor = 1.5 keeps that weight above 0.04."""
     from scipy.spatial import cKDTree
     P = np.asarray(X, np.float64)
     d, nb = cKDTree(P).query(P, k=m + 1)
     out = np.asarray(a, np.float64).copy()
-    np.maximum.at(out, nb[:, 1:].ravel(), 1.0001 * d[:, 1:].ravel())
+    np.maximum.at(out, nb[:, 1:].ravel(), factor * d[:, 1:].ravel())
     return out.astype(np.float32)
