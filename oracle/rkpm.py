@@ -176,7 +176,9 @@ def shape_functions_at(Xq, P, a, literal_basis=False, scale=None):
         if literal_basis:
             o, s = np.zeros(3), 1.0
         else:
-            o, s = x, (scale[j] if scale is not None else 1.0)
+            # FP64 scale: a float32 scalar here would make 1.0 / s below a
+            # float32 (NumPy 2 promotion) and round the e_{1+s}/s term
+            o, s = x, (float(scale[j]) if scale is not None else 1.0)
         Pk = np.concatenate([np.ones((ks.size, 1)), (Pd[ks] - o) / s], axis=1)
         Px = np.concatenate([[1.0], (x - o) / s])
         M = (w[:, None, None] * Pk[:, :, None] * Pk[:, None, :]).sum(0)
