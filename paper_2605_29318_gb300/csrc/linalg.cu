@@ -272,23 +272,30 @@ __global__ void k_cheb_step_vec(const long long* __restrict__ ptr, const int* __
 // Gram partials: P[blk][i][j] = sum_{rows in chunk} A[r][ia + i] * B[r][ib + j]
 // (p x q outputs in 32 x 32 tiles; grid.x = row chunks, grid.y = output tiles).
 // Accumulates in T inside the chunk, the cross-chunk sum is FP64 (k_gram_reduce).
-template <class T>
-__global__ void k_gram_partial(const T* __restrict__ A, int lda, int p, const T* __restrict__ B,
-                               int ldb, int q, long long n, long long rows_per_chunk,
-                               double* __restrict__ part) {
-  __shared__ T sa[32][33];
-  __shared__ T sb[32][33];
-  const int tilesq = (q + 31) / 32;
+// Partial tall-skinny products over a chunk of rows: a TW x TW tile of
+// A^T B per block (TW = 32, or 40 for the 40-wide blocks of a 40-column
+// eigensolver block, so that no lane computes padding -- on GB300 an FP64
+// warp instruction costs the same whatever the active lanes).  Thread
+// (tx, ty) of TW x 8 owns rows ty + 8u of the tile and column tx.
+template <class T, int TW>
+__global__ void __launch_bounds__(TW * 8)
+    k_gram_partial(const T* __restrict__ A, int lda, int p, const T* __restrict__ B, int ldb,
+                   int q, long long n, long long rows_per_chunk, double* __restrict__ part) {
+  constexpr int U = TW / 8;
+  __shared__ T sa[32][TW + 1];
+  __shared__ T sb[32][TW + 1];
+  const int tilesq = (q + TW - 1) / TW;
   const int ti = blockIdx.y / tilesq, tj = blockIdx.y % tilesq;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int tx = threadIdx.x % TW, ty = threadIdx.x / TW;
   const long long r0 = (long long)blockIdx.x * rows_per_chunk;
   const long long r1 = min(n, r0 + rows_per_chunk);
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+  T acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = T(0);
   for (long long rb = r0; rb < r1; rb += 32) {
-    // load 32 rows x 32 cols of A and B
     for (int rr = ty; rr < 32; rr += 8) {
       const long long r = rb + rr;
-      const int ia = ti * 32 + tx, ib = tj * 32 + tx;
+      const int ia = ti * TW + tx, ib = tj * TW + tx;
       sa[rr][tx] = (r < r1 && ia < p) ? A[r * lda + ia] : T(0);
       sb[rr][tx] = (r < r1 && ib < q) ? B[r * ldb + ib] : T(0);
     }
@@ -297,14 +304,14 @@ __global__ void k_gram_partial(const T* __restrict__ A, int lda, int p, const T*
     for (int rr = 0; rr < 32; ++rr) {
       const T bv = sb[rr][tx];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] += sa[rr][ty + 8 * u] * bv;
+      for (int u = 0; u < U; ++u) acc[u] += sa[rr][ty + 8 * u] * bv;
     }
     __syncthreads();
   }
-  const int jj = tj * 32 + tx;
+  const int jj = tj * TW + tx;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int ii = ti * 32 + ty + 8 * u;
+  for (int u = 0; u < U; ++u) {
+    const int ii = ti * TW + ty + 8 * u;
     if (ii < p && jj < q) part[((long long)blockIdx.x * p + ii) * q + jj] = (double)acc[u];
   }
 }
@@ -352,29 +359,33 @@ __global__ void k_gram_mirror(double* __restrict__ A, double* __restrict__ B, in
 // C[r][cmap(j)] = beta * C[...] + sum_i A[r][i] * Y[i][j]; cmap sends columns
 // j < split to C + j and j >= split to C + off2 + (j - split).
 // One warp per row, lanes over 32 columns of the tile; Y tile staged in shared memory.
-template <class T>
+// C = beta C + A Y over all rows: a group of TW threads per row, thread tx
+// owning output column blockIdx.y * TW + tx (TW = 32, or 40 for 40-wide
+// outputs so that no lane computes padding); Y's TW columns staged in shared
+// memory; columns at or past `split` are written at off2 + (j - split).
+template <class T, int TW>
 __global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T* __restrict__ Y,
                                int ldy, int q, T* __restrict__ C, int ldc, long long n, T beta,
                                int split, int off2) {
   extern __shared__ unsigned char smraw[];
-  T* sy = reinterpret_cast<T*>(smraw);  // p x 32
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const int j = blockIdx.y * 32 + lane;
-  for (int t = threadIdx.x; t < p * 32; t += blockDim.x) {
-    const int i = t / 32, jj = blockIdx.y * 32 + (t % 32);
+  T* sy = reinterpret_cast<T*>(smraw);  // p x TW
+  const int tx = threadIdx.x % TW, ry = threadIdx.x / TW, rpb = blockDim.x / TW;
+  const int j = blockIdx.y * TW + tx;
+  for (int t = threadIdx.x; t < p * TW; t += blockDim.x) {
+    const int i = t / TW, jj = blockIdx.y * TW + (t % TW);
     sy[t] = jj < q ? Y[(long long)i * ldy + jj] : T(0);
   }
   __syncthreads();
   const int cj = j < split ? j : off2 + (j - split);
-  for (long long r = (long long)blockIdx.x * wpb + wid; r < n; r += (long long)gridDim.x * wpb) {
+  for (long long r = (long long)blockIdx.x * rpb + ry; r < n; r += (long long)gridDim.x * rpb) {
     const T* a = A + r * lda;
     T acc = T(0);
     int i = 0;
     for (; i + 4 <= p; i += 4) {
-      acc += a[i] * sy[i * 32 + lane] + a[i + 1] * sy[(i + 1) * 32 + lane] +
-             a[i + 2] * sy[(i + 2) * 32 + lane] + a[i + 3] * sy[(i + 3) * 32 + lane];
+      acc += a[i] * sy[i * TW + tx] + a[i + 1] * sy[(i + 1) * TW + tx] +
+             a[i + 2] * sy[(i + 2) * TW + tx] + a[i + 3] * sy[(i + 3) * TW + tx];
     }
-    for (; i < p; ++i) acc += a[i] * sy[i * 32 + lane];
+    for (; i < p; ++i) acc += a[i] * sy[i * TW + tx];
     if (j < q) {
       T* cp = C + r * ldc + cj;
       *cp = beta == T(0) ? acc : beta * *cp + acc;
@@ -513,14 +524,21 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
           double* out, double alpha, bool accumulate, Buf& part, int ldo) {
   if (p <= 0 || q <= 0) return;
   ProfScope ps(kProfGram);
-  const int tiles = ((p + 31) / 32) * ((q + 31) / 32);
+  const bool w40 = p % 40 == 0 && q % 40 == 0;
+  const int TW = w40 ? 40 : 32;
+  const int tiles = ((p + TW - 1) / TW) * ((q + TW - 1) / TW);
   long long chunks = std::max<long long>(1, std::min<long long>((n + 511) / 512, 2048 / tiles + 1));
   long long rpc = (n + chunks - 1) / chunks;
   rpc = (rpc + 31) / 32 * 32;
   chunks = std::max<long long>(1, (n + rpc - 1) / rpc);
   double* pp = reinterpret_cast<double*>(part.ensure(sizeof(double) * chunks * p * q));
   dim3 grid((unsigned)chunks, (unsigned)tiles);
-  (k_gram_partial<T><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp), ::ff::note_launch());
+  if (w40)
+    (k_gram_partial<T, 40><<<grid, 320, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp),
+     ::ff::note_launch());
+  else
+    (k_gram_partial<T, 32><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp),
+     ::ff::note_launch());
   FF_LAUNCH_CHECK();
   (k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, p * q, q, out,
                                                     ldo < 0 ? q : ldo, alpha,
@@ -556,18 +574,30 @@ void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q
     // C = beta * C only; p == 0 never happens in the solver
     return;
   }
-  const int wpb = 8;
-  size_t smem = sizeof(T) * (size_t)p * 32;
-  static bool attr_set[2] = {false, false};
-  if (smem > 48 * 1024 && !attr_set[sizeof(T) == 8]) {
-    FF_CUDA(cudaFuncSetAttribute(k_block_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024));
-    attr_set[sizeof(T) == 8] = true;
+  const int rpb = 8;  // rows per block (one TW-thread group each)
+  const bool w40 = q % 40 == 0;
+  const int TW = w40 ? 40 : 32;
+  size_t smem = sizeof(T) * (size_t)p * TW;
+  static bool attr_set[2][2] = {{false, false}, {false, false}};
+  if (smem > 48 * 1024 && !attr_set[sizeof(T) == 8][w40]) {
+    if (w40)
+      FF_CUDA(cudaFuncSetAttribute(k_block_update<T, 40>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    else
+      FF_CUDA(cudaFuncSetAttribute(k_block_update<T, 32>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_set[sizeof(T) == 8][w40] = true;
   }
-  dim3 grid((unsigned)std::min<long long>((n + wpb - 1) / wpb, 152LL * 16),
-            (unsigned)((q + 31) / 32));
-  (k_block_update<T><<<grid, 32 * wpb, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C, ldc, n,
-                                                  beta, split < 0 ? q : split, off2), ::ff::note_launch());
+  dim3 grid((unsigned)std::min<long long>((n + rpb - 1) / rpb, 152LL * 16),
+            (unsigned)((q + TW - 1) / TW));
+  if (w40)
+    (k_block_update<T, 40><<<grid, 40 * rpb, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C,
+                                                        ldc, n, beta, split < 0 ? q : split, off2),
+     ::ff::note_launch());
+  else
+    (k_block_update<T, 32><<<grid, 32 * rpb, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C,
+                                                        ldc, n, beta, split < 0 ? q : split, off2),
+     ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
