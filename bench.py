@@ -45,13 +45,16 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic(kernel):
+def _traffic(cls, kernel):
+    """DRAM bytes per launch from the committed ncu capture, if it was taken on
+    this kernel (null once the kernel has changed)."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    e = d.get(kernel)
-    return None if e is None else e.get("bytes_per_launch")
+    e = json.load(open(p)).get(cls)
+    if e is None or e.get("kernel") != kernel:
+        return None
+    return e.get("bytes_per_launch")
 
 
 class Clocks:
@@ -254,14 +257,16 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     peak, peak_kind = _peaks()
-    # dominant kernel: the Chebyshev preconditioner step (H-only block product)
+    # dominant kernel: the Chebyshev preconditioner step (H-only block product
+    # on the 40-column block, BF16 directions): H values and columns, row
+    # pointers and diagonal, read d_in (2 B), write d_out (2 B), read and
+    # write res and x (FP32): 20 B per block element
     cnt, tot = prof["precond"]
     m = ((31 + 8 + 3) // 4) * 4
-    esz = 4
-    pre_bytes = n2 * 8 + (n + 1) * 8 + n * 4 + 6 * n * m * esz
+    pre_bytes = n2 * 8 + (n + 1) * 8 + n * 4 + 20 * n * m
     pre_ms = tot / max(cnt, 1)
     achieved = pre_bytes / (pre_ms * 1e-3) / 1e9 if cnt else None
-    tr = _traffic("precond")
+    tr = _traffic("precond", "k_cheb_step_b16")
     # secondary: fused (H, M) block product
     scnt, stot = prof["spmm"]
     t_el = 8 if args.prec == "fp64" else 4
@@ -279,7 +284,7 @@ def run_ours(args):
                    "n": n, "n1": n1, "n2": n2,
                    "l2": "flushed by a 256 MB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_cheb_step_vec (Chebyshev preconditioner step)",
+        "roofline": {"kernel": "k_cheb_step_b16 (Chebyshev preconditioner step, BF16 directions)",
                      "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4) if achieved else None,

@@ -219,7 +219,9 @@ typedef enum {
   FF_PROF_RAYLEIGH_RITZ = 3,  /* small dense Rayleigh-Ritz */
   FF_PROF_UPDATE = 4,         /* block updates */
   FF_PROF_BUILD = 5,          /* a whole rkpm_build */
-  FF_PROF_ASSEMBLE = 6        /* a whole assemble_hessian */
+  FF_PROF_ASSEMBLE = 6,       /* a whole assemble_hessian */
+  FF_PROF_SETUP = 7           /* eigensolver set-up: power iteration for the
+                                 preconditioner interval */
 } ff_prof_class;
 
 /* on != 0: reset and start recording; on == 0: stop recording. */

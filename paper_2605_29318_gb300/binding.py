@@ -32,7 +32,7 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_net_init", "ff_net_set_params", "ff_net_get_params", "ff_warmstart_features",
            "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
-        "assemble": 6}
+        "assemble": 6, "setup": 7}
 
 
 class EigOpts(ctypes.Structure):

@@ -18,8 +18,9 @@
 //                       thread-block cluster, rows spread over the blocks'
 //                       shared memory;
 //   k_rr_eigvals_mc     the nb smallest eigenvalues of the tridiagonal matrix,
-//                       one warp each: FP64 multisection on a division-free
-//                       Sturm count;
+//                       one 4-warp block each: FP32 multisection brackets,
+//                       then multisection in the working precision on a
+//                       division-free Sturm count;
 //   k_rr_invit_sm       their eigenvectors by inverse iteration on the
 //                       tridiagonal (LU with partial pivoting), one block each;
 //   k_rr_cholqr         Cholesky QR (twice) of those vectors;
@@ -497,30 +498,141 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
 // ------------------------------------------------------------------ 2b. eigenvalues, one block each
 // FP64 multisection with the division-free Sturm count: one warp per
 // eigenvalue, 32 probes per round (a 33-fold shrink of the bracket per round).
+// Sturm count with the sign and range tests on the bit patterns (integer
+// instructions): per step three floating-point instructions, which matters in
+// FP64 on GB300 (64 cycles per FP64 warp instruction).
+__device__ __forceinline__ long long bits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ int bits(float v) { return __float_as_int(v); }
 template <class R>
-__global__ void k_rr_eigvals_mc(int n, int nb, RRWork<R> w, double* theta) {
-  const int s = blockIdx.x, lane = threadIdx.x;
+__device__ int sturm_bits(const R* d, const R* e2, int n, R x) {
+  using I = decltype(bits(R(0)));
+  constexpr int kSign = 8 * (int)sizeof(R) - 1;
+  constexpr int kMant = sizeof(R) == 8 ? 52 : 23;
+  constexpr int kBias = sizeof(R) == 8 ? 1023 : 127;
+  constexpr int kMask = sizeof(R) == 8 ? 0x7ff : 0xff;
+  constexpr int kSpan = sizeof(R) == 8 ? 600 : 60;
+  R pm = R(1.0), p = d[0] - x;
+  I bp = bits(p);
+  if ((bp << 1) == 0) {
+    p = -Prec<R>::tiny;
+    bp = bits(p);
+  }
+  int c = (int)((unsigned long long)(bp >> kSign) & 1ull);
+  for (int i = 1; i < n; ++i) {
+    R q = fma(d[i] - x, p, -e2[i - 1] * pm);
+    I bq = bits(q);
+    if ((bq << 1) == 0) {  // a zero minor takes the sign opposite to its predecessor
+      q = bp < 0 ? Prec<R>::tiny : -Prec<R>::tiny;
+      bq = bits(q);
+    }
+    c += (int)((unsigned long long)((bq ^ bp) >> kSign) & 1ull);
+    pm = p;
+    p = q;
+    bp = bq;
+    const int ex = (int)((bq >> kMant) & kMask) - kBias;
+    if (ex > kSpan || ex < -kSpan) {
+      p = scalbn_r(p, -ex);
+      pm = scalbn_r(pm, -ex);
+      bp = bits(p);
+    }
+  }
+  return c;
+}
+
+// One block of kEW warps per eigenvalue s: multisection with 32 kEW probes a
+// round, first on FP32 copies of the tridiagonal (cheap bracketing to FP32
+// resolution), then in the working precision from the FP32 bracket widened by
+// its error bound and checked by working-precision counts.
+constexpr int kEW = 4;
+template <class R>
+__device__ void multisection(const R* d, const R* e2, int n, int s, R& a, R& b, int max_rounds,
+                             R rel, int* sfirst) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NP = 32 * kEW;
+  for (int round = 0; round < max_rounds; ++round) {
+    const R x = a + (b - a) * (R)(threadIdx.x + 1) / (R)(NP + 1);
+    const int cnt = sturm_bits<R>(d, e2, n, x);
+    const unsigned above = __ballot_sync(0xffffffffu, cnt >= s + 1);
+    if (lane == 0) sfirst[wid] = above ? 32 * wid + __ffs(above) - 1 : NP;
+    __syncthreads();
+    int first = NP;
+    for (int q = 0; q < kEW; ++q) first = min(first, sfirst[q]);
+    const R na = first == 0 ? a : a + (b - a) * (R)first / (R)(NP + 1);
+    const R nbv = first == NP ? b : a + (b - a) * (R)(first + 1) / (R)(NP + 1);
+    a = na;
+    b = nbv;
+    __syncthreads();
+    if (b - a <= rel * fmax(fabs(a), fabs(b))) break;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(32 * kEW)
+    k_rr_eigvals_mc(int n, int nb, RRWork<R> w, double* theta) {
+  extern __shared__ __align__(16) unsigned char ev_raw[];
+  R* d = reinterpret_cast<R*>(ev_raw);
+  R* e2 = d + n;
+  float* d32 = reinterpret_cast<float*>(e2 + n);
+  float* e32 = d32 + n;
+  __shared__ int sfirst[kEW];
+  __shared__ R red[2 * kEW];
+  const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   R lo = R(0.0), hi = R(0.0);
-  for (int i = 0; i < n; ++i) {
+  bool any = false;
+  for (int i = tid; i < n; i += blockDim.x) {
+    d[i] = w.dg[i];
+    e2[i] = w.e2[i];
+    d32[i] = (float)w.dg[i];
+    e32[i] = (float)w.e2[i];
     const R r = (i > 0 ? fabs(w.e[i - 1]) : R(0.0)) + (i + 1 < n ? fabs(w.e[i]) : R(0.0));
     const R a = w.dg[i] - r, b = w.dg[i] + r;
-    if (i == 0 || a < lo) lo = a;
-    if (i == 0 || b > hi) hi = b;
+    lo = any ? fmin(lo, a) : a;
+    hi = any ? fmax(hi, b) : b;
+    any = true;
   }
-  const R span = fmax(hi - lo, R(1e-30));
-  R a = lo - span * R(1e-6), b = hi + span * R(1e-6);
-  for (int round = 0; round < 64; ++round) {
-    const R x = a + (b - a) * (R)(lane + 1) / R(33.0);
-    const int cnt = sturm(w.dg, w.e2, n, x);
-    const unsigned above = __ballot_sync(0xffffffffu, cnt >= s + 1);
-    const int first = above ? __ffs(above) - 1 : 32;
-    const R na = first == 0 ? a : a + (b - a) * (R)first / R(33.0);
-    const R nbv = first == 32 ? b : a + (b - a) * (R)(first + 1) / R(33.0);
-    a = __shfl_sync(0xffffffffu, na, 0);
-    b = __shfl_sync(0xffffffffu, nbv, 0);
-    if (b - a <= R(4.0) * Prec<R>::eps * fmax(fabs(a), fabs(b))) break;
+  if (!any) {
+    lo = R(1e30);
+    hi = R(-1e30);
+  }
+  for (int o = 16; o; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
   if (lane == 0) {
+    red[wid] = lo;
+    red[kEW + wid] = hi;
+  }
+  __syncthreads();
+  lo = red[0];
+  hi = red[kEW];
+  for (int q = 1; q < kEW; ++q) {
+    lo = fmin(lo, red[q]);
+    hi = fmax(hi, red[kEW + q]);
+  }
+  const R span = fmax(hi - lo, R(1e-30));
+  lo -= span * R(1e-6);
+  hi += span * R(1e-6);
+  R a = lo, b = hi;
+  if (sizeof(R) == 8) {
+    // FP32 bracket, then widened by the FP32 count's error bound
+    float a32 = (float)lo, b32 = (float)hi;
+    multisection<float>(d32, e32, n, s, a32, b32, 16, 4.f * Prec<float>::eps, sfirst);
+    const R tnorm = fmax(fabs(lo), fabs(hi));
+    const R pad = R(64.0) * R(6e-8) * tnorm;
+    a = fmax(lo, (R)a32 - pad);
+    b = fmin(hi, (R)b32 + pad);
+    // keep the bracket only if working-precision counts confirm it
+    if (tid == 0) {
+      sfirst[0] = sturm_bits<R>(d, e2, n, a) <= s;
+      sfirst[1] = sturm_bits<R>(d, e2, n, b) >= s + 1;
+    }
+    __syncthreads();
+    if (!sfirst[0]) a = lo;
+    if (!sfirst[1]) b = hi;
+    __syncthreads();
+  }
+  multisection<R>(d, e2, n, s, a, b, 64, R(4.0) * Prec<R>::eps, sfirst);
+  if (tid == 0) {
     w.lam[s] = R(0.5) * (a + b);
     theta[s] = R(0.5) * (a + b);
   }
@@ -876,7 +988,9 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
     (k_rr_house_cluster<R><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
-  (k_rr_eigvals_mc<R><<<(unsigned)nb, 32, 0, st>>>(d.ns, d.nb, w, theta), ::ff::note_launch());
+  (k_rr_eigvals_mc<R><<<(unsigned)nb, 32 * kEW, (sizeof(R) + sizeof(float)) * 2 * n, st>>>(
+       d.ns, d.nb, w, theta),
+   ::ff::note_launch());
   FF_LAUNCH_CHECK();
   const size_t iv_bytes = sizeof(R) * kIV * 6 * n;
   if (iv_bytes <= kMaxDynSmem) {

@@ -85,6 +85,7 @@ enum ProfClass {
   kProfUpdate,       // block updates
   kProfBuild,        // rkpm_build (whole stage)
   kProfAssemble,     // assemble_hessian (whole stage)
+  kProfSetup,        // eigensolver set-up (power iteration)
   kProfN
 };
 
@@ -148,7 +149,7 @@ struct ff_ctx {
   // generic scratch
   ff::Buf scratch[8];
   // eigen-solver workspace
-  ff::Buf ws[24];
+  ff::Buf ws[28];
   ff::Profiler prof;
 };
 

@@ -1,3 +1,4 @@
+#include <cuda_bf16.h>
 // Block kernels of the eigensolver: the fused (H_w, M) block product, the
 // Chebyshev preconditioner steps, tall-skinny Gram products and block updates.
 // Panels are row-major n x ld (row k of a block of m columns is contiguous), so
@@ -499,10 +500,119 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
   FF_LAUNCH_CHECK();
 }
 
+// One warp per row; lanes form groups of G = m / 8 lanes, each lane owning 8
+// consecutive columns (one 16-byte load of 8 BF16 values per gathered row);
+// the P = 32 / G groups take P nonzeros of the row at a time.
+__device__ __forceinline__ void bf8_load(const __nv_bfloat16* p, float (&v)[8]) {
+  const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float2 f = __bfloat1622float2(h[u]);
+    v[2 * u] = f.x;
+    v[2 * u + 1] = f.y;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_cheb_step_b16(const long long* __restrict__ ptr, const int* __restrict__ col,
+                    const float* __restrict__ hv, const float* __restrict__ hdiag, long long n,
+                    int m, const __nv_bfloat16* __restrict__ din, __nv_bfloat16* __restrict__ dout,
+                    float* __restrict__ x, float* __restrict__ res, float c1, float c2) {
+  const int lane = threadIdx.x & 31;
+  const int G = m / 8, P = 32 / G;
+  const int g = lane / G, cv = (lane % G) * 8;
+  const bool act = g < P;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
+    const long long s = ptr[k], e = ptr[k + 1];
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, hs = 0.f;
+    long long e0 = act ? s + g : e;
+    for (; e0 + 3 * P < e; e0 += 4 * P) {
+      int l[4];
+      float h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        l[q] = col[e0 + q * P];
+        h[q] = hv[e0 + q * P];
+      }
+      float dl[4][8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bf8_load(din + (long long)l[q] * m + cv, dl[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        hs += h[q];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = fmaf(h[q], dl[q][u], acc[u]);
+      }
+    }
+    for (; e0 < e; e0 += P) {
+      float dl[8];
+      const float h = hv[e0];
+      bf8_load(din + (long long)col[e0] * m + cv, dl);
+      hs += h;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = fmaf(h, dl[u], acc[u]);
+    }
+    for (int off = G; off < 32; off <<= 1) {  // tree over the groups
+      const bool in = lane + off < 32;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float t = __shfl_down_sync(kFull, acc[u], off);
+        if (in) acc[u] += t;
+      }
+      const float t = __shfl_down_sync(kFull, hs, off);
+      if (in) hs += t;
+    }
+    if (g == 0) {
+      const float dinv = 1.0f / hdiag[k];
+      const long long o = k * m + cv;
+      float dk[8];
+      bf8_load(din + o, dk);
+      float4* rp = reinterpret_cast<float4*>(res + o);
+      float4* xp = reinterpret_cast<float4*>(x + o);
+      const float4 r0 = rp[0], r1 = rp[1], x0 = xp[0], x1 = xp[1];
+      float r[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+      float xx[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      __align__(16) __nv_bfloat16 dn[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        r[u] -= (acc[u] - hs * dk[u]) * dinv;
+        const __nv_bfloat16 q = __float2bfloat16(c1 * dk[u] + c2 * r[u]);
+        dn[u] = q;
+        xx[u] += __bfloat162float(q);
+      }
+      rp[0] = make_float4(r[0], r[1], r[2], r[3]);
+      rp[1] = make_float4(r[4], r[5], r[6], r[7]);
+      xp[0] = make_float4(xx[0], xx[1], xx[2], xx[3]);
+      xp[1] = make_float4(xx[4], xx[5], xx[6], xx[7]);
+      *reinterpret_cast<uint4*>(dout + o) = *reinterpret_cast<const uint4*>(dn);
+    }
+  }
+}
+
+void cheb_step_b16(cudaStream_t st, const long long* ptr, const int* col, const float* hv,
+                   const float* hdiag, long long n, int m, const void* din, void* dout, float* x,
+                   float* res, float c1, float c2) {
+  ProfScope ps(kProfPrecond);
+  FF_REQUIRE(m % 8 == 0 && m <= 256 && reinterpret_cast<uintptr_t>(din) % 16 == 0 &&
+                 reinterpret_cast<uintptr_t>(dout) % 16 == 0 &&
+                 reinterpret_cast<uintptr_t>(x) % 16 == 0 &&
+                 reinterpret_cast<uintptr_t>(res) % 16 == 0,
+             FF_ERR_INVALID_ARG, "BF16 preconditioner step needs m % 8 == 0 and aligned blocks");
+  const int T_ = 256;
+  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
+  (k_cheb_step_b16<<<(unsigned)blocks, T_, 0, st>>>(
+       ptr, col, hv, hdiag, n, m, static_cast<const __nv_bfloat16*>(din),
+       static_cast<__nv_bfloat16*>(dout), x, res, c1, c2),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+}
+
 void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const float* hv,
                const float* hdiag, long long n, int m, int ld, const float* din, float* dout,
-               float* x, float* res, float c1, float c2) {
-  ProfScope ps(kProfPrecond);
+               float* x, float* res, float c1, float c2, int prof) {
+  ProfScope ps(prof);
   const int T_ = 256;
   long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
   const bool vec_ok = m % 4 == 0 && m <= 128 && ld % 4 == 0 &&

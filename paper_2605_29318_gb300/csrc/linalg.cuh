@@ -11,7 +11,14 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
 
 void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const float* hv,
                const float* hdiag, long long n, int m, int ld, const float* din, float* dout,
-               float* x, float* res, float c1, float c2);
+               float* x, float* res, float c1, float c2, int prof = kProfPrecond);
+
+// The same step with the direction vectors d stored in BF16 (m % 8 == 0):
+// each gathered row is half the bytes; the residual and the accumulated x stay
+// FP32, and x accumulates the rounded directions that H is applied to.
+void cheb_step_b16(cudaStream_t st, const long long* ptr, const int* col, const float* hv,
+                   const float* hdiag, long long n, int m, const void* din, void* dout, float* x,
+                   float* res, float c1, float c2);
 
 // out (p x q, row-major with leading dimension ldo (default q), FP64)
 // (+)= alpha * A^T B over n rows

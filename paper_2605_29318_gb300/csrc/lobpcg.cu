@@ -15,6 +15,8 @@
 //     M-orthonormal and M-orthogonal to X), and one block update forms
 //     X, P, H X, H P, M X, M P from the old panels;
 //   * columns whose relative residual meets tol stop contributing to W.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -151,7 +153,7 @@ __global__ void k_cheb_init(const T* __restrict__ HX, const T* __restrict__ MX, 
                             const double* __restrict__ theta, const int* __restrict__ active,
                             const float* __restrict__ hdiag, long long n, int m,
                             float* __restrict__ res, float* __restrict__ d, float* __restrict__ x,
-                            float inv_tc) {
+                            float inv_tc, __nv_bfloat16* __restrict__ d16) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * m) return;
   long long r = t / m;
@@ -162,8 +164,14 @@ __global__ void k_cheb_init(const T* __restrict__ HX, const T* __restrict__ MX, 
     b = (float)(rr / (double)hdiag[r]);
   }
   res[t] = b;
-  d[t] = b * inv_tc;
-  x[t] = b * inv_tc;
+  if (d16) {  // BF16 directions: x starts from the rounded one
+    const __nv_bfloat16 q = __float2bfloat16(b * inv_tc);
+    d16[t] = q;
+    x[t] = __bfloat162float(q);
+  } else {
+    d[t] = b * inv_tc;
+    x[t] = b * inv_tc;
+  }
 }
 
 template <class T>
@@ -208,6 +216,7 @@ struct Solver {
   T *S[2], *HS[2], *MS[2];
   T *c0, *Mc0;
   float *cres, *cd0, *cd1, *cx;
+  __nv_bfloat16 *cb0, *cb1;  // BF16 direction vectors of the preconditioner
   double *Ag, *Bg, *G1, *theta_d, *norms_d;
   T *Gt, *YZ;
   int *dropped_d, *active_d;
@@ -228,6 +237,8 @@ struct Solver {
     cres = reinterpret_cast<float*>(c->ws[8].ensure(sizeof(float) * n * std::max(nb, 4)));
     cd0 = reinterpret_cast<float*>(c->ws[9].ensure(sizeof(float) * n * std::max(nb, 4)));
     cd1 = reinterpret_cast<float*>(c->ws[10].ensure(sizeof(float) * n * std::max(nb, 4)));
+    cb0 = reinterpret_cast<__nv_bfloat16*>(c->ws[24].ensure(sizeof(__nv_bfloat16) * n * nb + 16));
+    cb1 = reinterpret_cast<__nv_bfloat16*>(c->ws[25].ensure(sizeof(__nv_bfloat16) * n * nb + 16));
     cx = reinterpret_cast<float*>(c->ws[11].ensure(sizeof(float) * n * std::max(nb, 4)));
     const int ns = 3 * nb;
     Ag = reinterpret_cast<double*>(c->ws[12].ensure(sizeof(double) * ns * ns));
@@ -328,7 +339,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     for (int it = 0; it < 12; ++it) {
       FF_CUDA(cudaMemsetAsync(s.cres, 0, sizeof(float) * 4 * n, st));
       cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
-                c->hdiag_f32.as<float>(), n, 4, 4, a, b, s.cx, s.cres, 0.f, -1.f);
+                c->hdiag_f32.as<float>(), n, 4, 4, a, b, s.cx, s.cres, 0.f, -1.f, kProfSetup);
       gram<float>(st, a, 4, 4, a, 4, 4, n, s.G1, 1.0, false, c->scratch[0]);
       gram<float>(st, b, 4, 4, b, 4, 4, n, s.G1 + 16, 1.0, false, c->scratch[0]);
       // normalise b (one common factor) and make it the next input
@@ -475,23 +486,34 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
 
     // W = T R  (FP32 Chebyshev polynomial in D^-1 H, or Jacobi when deg <= 1)
     T* W = s.S[cur] + nb;
+    // BF16 directions halve the bytes each preconditioner step gathers
+    const bool b16 = deg > 1 && nb % 8 == 0;
     (k_cheb_init<T><<<blocks(n * nb), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d, s.active_d,
                                                   c->hdiag_f32.as<float>(), n, nb, s.cres, s.cd0,
-                                                  s.cx, deg > 1 ? (float)(1.0 / th_c) : 1.f), ::ff::note_launch());
+                                                  s.cx, deg > 1 ? (float)(1.0 / th_c) : 1.f,
+                                                  b16 ? s.cb0 : nullptr), ::ff::note_launch());
     FF_LAUNCH_CHECK();
     if (deg > 1) {
       const double sigma1 = th_c / delta;
       double rho = 1.0 / sigma1;
       float* din = s.cd0;
       float* dout = s.cd1;
+      __nv_bfloat16* bin = s.cb0;
+      __nv_bfloat16* bout = s.cb1;
       for (int j = 1; j < deg; ++j) {
         const double rn = 1.0 / (2.0 * sigma1 - rho);
-        cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
-                  c->hdiag_f32.as<float>(), n, nb, nb, din, dout, s.cx, s.cres,
-                  (float)(rn * rho), (float)(2.0 * rn / delta));
+        if (b16)
+          cheb_step_b16(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
+                        c->hdiag_f32.as<float>(), n, nb, bin, bout, s.cx, s.cres,
+                        (float)(rn * rho), (float)(2.0 * rn / delta));
+        else
+          cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
+                    c->hdiag_f32.as<float>(), n, nb, nb, din, dout, s.cx, s.cres,
+                    (float)(rn * rho), (float)(2.0 * rn / delta));
         ++s.spmv_calls;
         rho = rn;
         std::swap(din, dout);
+        std::swap(bin, bout);
       }
     }
     (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, n, nb, W, ld), ::ff::note_launch());
