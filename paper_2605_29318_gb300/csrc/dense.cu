@@ -835,27 +835,34 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
   }
-  // undo the coefficient-space projection: rest rows -= C y_O
-  for (int t = tid; t < n * 2 * nb; t += kThreads) {
-    const int i = t / (2 * nb), c = t % (2 * nb);
-    if ((i >= o0 && i < o0 + no) || (c >= nb && !want_p)) continue;
-    R* M_ = c < nb ? V : Z;
-    const int cc = c < nb ? c : c - nb;
-    R acc = M_[(size_t)i * nb + cc];
-    for (int a = 0; a < no; ++a) acc -= w.C[i * no + a] * M_[(size_t)(o0 + a) * nb + cc];
-    M_[(size_t)i * nb + cc] = acc;
-  }
-  __syncthreads();
-  for (int t = tid; t < n * nb; t += kThreads) {
-    const int i = t / nb, s2 = t % nb;
-    const R d = w.dsc[i];
-    YZ[(size_t)i * 2 * nb + s2] = (T)(V[t] * d);
-    YZ[(size_t)i * 2 * nb + nb + s2] = want_p ? (T)(Z[t] * d) : T(0);
-  }
   if (tid == 0) {
     int dc = 0;
     for (int a = 0; a < n; ++a) dc += !w.keep[a];
     *dropped = dc;
+  }
+}
+
+// Output, one block per row i: undo the coefficient-space projection
+// (y_i -= sum_a C_ia y_{o0+a} for rows outside O) and scale, for the Ritz
+// vectors V and the momentum coefficients Z.
+template <class R, class T>
+__global__ void k_rr_output(int n, int o0, int no, int nb, int want_p, RRWork<R> w,
+                            T* __restrict__ YZ) {
+  const int i = blockIdx.x;
+  const bool in_o = i >= o0 && i < o0 + no;
+  const R d = w.dsc[i];
+  for (int c = threadIdx.x; c < 2 * nb; c += blockDim.x) {
+    T* out = YZ + (size_t)i * 2 * nb + c;
+    if (c >= nb && !want_p) {
+      *out = T(0);
+      continue;
+    }
+    const R* M_ = c < nb ? w.V : w.Z;
+    const int cc = c < nb ? c : c - nb;
+    R acc = M_[(size_t)i * nb + cc];
+    if (!in_o)
+      for (int a = 0; a < no; ++a) acc -= w.C[i * no + a] * M_[(size_t)(o0 + a) * nb + cc];
+    *out = (T)(acc * d);
   }
 }
 
@@ -1007,6 +1014,9 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   FF_LAUNCH_CHECK();
   (k_rr_momentum<R, T><<<1, kThreads, 0, st>>>(d.ns, d.o0, d.no, d.nx, d.nb, d.want_p, w, YZ,
                                                dropped),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+  (k_rr_output<R, T><<<(unsigned)n, 128, 0, st>>>(d.ns, d.o0, d.no, d.nb, d.want_p, w, YZ),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }

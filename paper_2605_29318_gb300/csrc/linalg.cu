@@ -327,6 +327,20 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int p
   *o = accumulate ? *o + alpha * s : alpha * s;
 }
 
+// p == 1: part[chunk][j] = sum over the chunk's rows of a[r] B[r][j] (one
+// thread per column j, FP64 sums)
+template <class T>
+__global__ void k_gram_row(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
+                           int q, long long n, long long rows_per_chunk, double* __restrict__ part) {
+  const long long r0 = (long long)blockIdx.x * rows_per_chunk;
+  const long long r1 = min(n, r0 + rows_per_chunk);
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    double s = 0.0;
+    for (long long r = r0; r < r1; ++r) s += (double)A[r * lda] * (double)B[r * ldb + j];
+    part[(long long)blockIdx.x * q + j] = s;
+  }
+}
+
 // out[c * ldo + c] = sum_r A[r][c] B[r][c] for the columns c outside [w0, w1)
 // (one block per column, FP64 sums)
 template <class T>
@@ -634,6 +648,20 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
           double* out, double alpha, bool accumulate, Buf& part, int ldo) {
   if (p <= 0 || q <= 0) return;
   ProfScope ps(kProfGram);
+  if (p == 1 && q <= 256) {  // a row vector times a block: no tile of padding
+    const long long chunks = std::max<long long>(1, std::min<long long>((n + 255) / 256, 608));
+    const long long rpc = (n + chunks - 1) / chunks;
+    double* pp = reinterpret_cast<double*>(part.ensure(sizeof(double) * chunks * q));
+    (k_gram_row<T><<<(unsigned)chunks, ((q + 31) / 32) * 32, 0, st>>>(A, lda, B, ldb, q, n, rpc,
+                                                                      pp),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    (k_gram_reduce<<<(q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, q, q, out, ldo < 0 ? q : ldo,
+                                                  alpha, accumulate ? 1 : 0),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    return;
+  }
   const bool w40 = p % 40 == 0 && q % 40 == 0;
   const int TW = w40 ? 40 : 32;
   const int tiles = ((p + TW - 1) / TW) * ((q + TW - 1) / TW);
