@@ -516,43 +516,51 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
 
 // One warp per row; lanes form groups of G = m / 8 lanes, each lane owning 8
 // consecutive columns (one 16-byte load of 8 BF16 values per gathered row);
-// the P = 32 / G groups take P nonzeros of the row at a time.
+// the P = 32 / G groups take P nonzeros of the row at a time.  GT > 0 fixes G
+// at compile time (the block widths the solver uses), GT = 0 reads it from m.
+// Offsets within a row and into the direction block are 32-bit (the host
+// checks n * m < 2^31).
 __device__ __forceinline__ void bf8_load(const __nv_bfloat16* p, float (&v)[8]) {
   const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
-  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+  const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const float2 f = __bfloat1622float2(h[u]);
-    v[2 * u] = f.x;
-    v[2 * u + 1] = f.y;
+  for (int u = 0; u < 4; ++u) {  // a BF16 value is the top half of an FP32 one
+    v[2 * u] = __uint_as_float(w[u] << 16);
+    v[2 * u + 1] = __uint_as_float(w[u] & 0xffff0000u);
   }
 }
 
+template <int GT>
 __global__ void __launch_bounds__(256)
     k_cheb_step_b16(const long long* __restrict__ ptr, const int* __restrict__ col,
-                    const float* __restrict__ hv, const float* __restrict__ hdiag, long long n,
-                    int m, const __nv_bfloat16* __restrict__ din, __nv_bfloat16* __restrict__ dout,
+                    const float* __restrict__ hv, const float* __restrict__ hdiag, int n, int m_,
+                    const __nv_bfloat16* __restrict__ din, __nv_bfloat16* __restrict__ dout,
                     float* __restrict__ x, float* __restrict__ res, float c1, float c2) {
+  const int G = GT > 0 ? GT : m_ / 8;
+  const int m = 8 * G, P = 32 / G;
   const int lane = threadIdx.x & 31;
-  const int G = m / 8, P = 32 / G;
   const int g = lane / G, cv = (lane % G) * 8;
   const bool act = g < P;
-  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += warps) {
-    const long long s = ptr[k], e = ptr[k + 1];
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  const __nv_bfloat16* dc = din + cv;
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < n; k += warps) {
+    const long long s = ptr[k];
+    const int cnt = (int)(ptr[k + 1] - s);
+    const int* cr = col + s;
+    const float* hr = hv + s;
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, hs = 0.f;
-    long long e0 = act ? s + g : e;
-    for (; e0 + 3 * P < e; e0 += 4 * P) {
+    int e = act ? g : cnt;
+    for (; e + 3 * P < cnt; e += 4 * P) {
       int l[4];
       float h[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        l[q] = col[e0 + q * P];
-        h[q] = hv[e0 + q * P];
+        l[q] = __ldg(cr + e + q * P);
+        h[q] = __ldg(hr + e + q * P);
       }
       float dl[4][8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) bf8_load(din + (long long)l[q] * m + cv, dl[q]);
+      for (int q = 0; q < 4; ++q) bf8_load(dc + l[q] * m, dl[q]);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         hs += h[q];
@@ -560,14 +568,15 @@ __global__ void __launch_bounds__(256)
         for (int u = 0; u < 8; ++u) acc[u] = fmaf(h[q], dl[q][u], acc[u]);
       }
     }
-    for (; e0 < e; e0 += P) {
+    for (; e < cnt; e += P) {
       float dl[8];
-      const float h = hv[e0];
-      bf8_load(din + (long long)col[e0] * m + cv, dl);
+      const float h = __ldg(hr + e);
+      bf8_load(dc + __ldg(cr + e) * m, dl);
       hs += h;
 #pragma unroll
       for (int u = 0; u < 8; ++u) acc[u] = fmaf(h, dl[u], acc[u]);
     }
+#pragma unroll
     for (int off = G; off < 32; off <<= 1) {  // tree over the groups
       const bool in = lane + off < 32;
 #pragma unroll
@@ -580,7 +589,7 @@ __global__ void __launch_bounds__(256)
     }
     if (g == 0) {
       const float dinv = 1.0f / hdiag[k];
-      const long long o = k * m + cv;
+      const int o = k * m + cv;
       float dk[8];
       bf8_load(din + o, dk);
       float4* rp = reinterpret_cast<float4*>(res + o);
@@ -614,12 +623,24 @@ void cheb_step_b16(cudaStream_t st, const long long* ptr, const int* col, const 
                  reinterpret_cast<uintptr_t>(x) % 16 == 0 &&
                  reinterpret_cast<uintptr_t>(res) % 16 == 0,
              FF_ERR_INVALID_ARG, "BF16 preconditioner step needs m % 8 == 0 and aligned blocks");
+  FF_REQUIRE(n * m < (1LL << 31), FF_ERR_INVALID_ARG, "BF16 preconditioner step: n * m >= 2^31");
   const int T_ = 256;
   long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
-  (k_cheb_step_b16<<<(unsigned)blocks, T_, 0, st>>>(
-       ptr, col, hv, hdiag, n, m, static_cast<const __nv_bfloat16*>(din),
-       static_cast<__nv_bfloat16*>(dout), x, res, c1, c2),
-   ::ff::note_launch());
+  const auto* bi = static_cast<const __nv_bfloat16*>(din);
+  auto* bo = static_cast<__nv_bfloat16*>(dout);
+  const int ni = (int)n;
+#define FF_CHEB16(GT)                                                                     \
+  (k_cheb_step_b16<GT><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, hv, hdiag, ni, m, bi, bo, x, \
+                                                        res, c1, c2),                     \
+   ::ff::note_launch())
+  switch (m / 8) {
+    case 4: FF_CHEB16(4); break;
+    case 5: FF_CHEB16(5); break;
+    case 6: FF_CHEB16(6); break;
+    case 8: FF_CHEB16(8); break;
+    default: FF_CHEB16(0); break;
+  }
+#undef FF_CHEB16
   FF_LAUNCH_CHECK();
 }
 
