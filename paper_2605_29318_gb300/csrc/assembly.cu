@@ -224,6 +224,15 @@ __global__ void k_round_f32(const double* __restrict__ x, float* __restrict__ y,
   if (t < m) y[t] = (float)x[t];
 }
 
+// x = h + l with h = fl32(x), l = fl32(x - h): the double-float split
+__global__ void k_split_df(const double* __restrict__ x, float2* __restrict__ y, long long m) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) {
+    const float h = (float)x[t];
+    y[t] = make_float2(h, (float)(x[t] - (double)h));
+  }
+}
+
 }  // namespace
 
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0) {
@@ -314,6 +323,11 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
     float* v32 = reinterpret_cast<float*>(c->a_val32.ensure(2 * sizeof(float) * n2));
     const long long m = 2 * n2;
     (k_round_f32<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->a_val.as<double>(), v32, m),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    // and the double-float split for its FP64 phase
+    float2* vdf = reinterpret_cast<float2*>(c->a_valdf.ensure(2 * sizeof(float2) * n2));
+    (k_split_df<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->a_val.as<double>(), vdf, m),
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }

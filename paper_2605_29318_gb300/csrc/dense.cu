@@ -1039,5 +1039,7 @@ template void rayleigh_ritz<float>(cudaStream_t, const double*, const double*, R
                                    double*, int*, Buf&, bool, double*);
 template void rayleigh_ritz<double>(cudaStream_t, const double*, const double*, RRDims, double*,
                                     double*, int*, Buf&, bool, double*);
+template void rayleigh_ritz<dfloat>(cudaStream_t, const double*, const double*, RRDims, dfloat*,
+                                    double*, int*, Buf&, bool, double*);
 
 }  // namespace ff

@@ -140,6 +140,8 @@ struct ff_ctx {
   ff::Buf a_col;     // int[n2]
   ff::Buf a_val;     // T2[n2] interleaved (H, M)
   ff::Buf a_val32;   // float2[n2] (H, M) rounded from a_val (FP64 contexts)
+  ff::Buf a_valdf;   // float4[n2] (H.h, H.l, M.h, M.l) double-float split of a_val
+                     // (FP64 contexts)
   ff::Buf h_f32;     // float[n2] H values for the preconditioner
   ff::Buf hdiag_f32; // float[n] diag(H)
   ff::Buf wh;        // T[n] v_i (lambda_i + 4 mu_i)

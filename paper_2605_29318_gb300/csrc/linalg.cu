@@ -3,6 +3,8 @@
 // Chebyshev preconditioner steps, tall-skinny Gram products and block updates.
 // Panels are row-major n x ld (row k of a block of m columns is contiguous), so
 // a warp reads one row of a block with unit stride.
+#include <type_traits>
+
 #include "linalg.cuh"
 
 namespace ff {
@@ -305,7 +307,12 @@ __global__ void __launch_bounds__(TW * 8)
     for (int rr = 0; rr < 32; ++rr) {
       const T bv = sb[rr][tx];
 #pragma unroll
-      for (int u = 0; u < U; ++u) acc[u] += sa[rr][ty + 8 * u] * bv;
+      for (int u = 0; u < U; ++u) {
+        if constexpr (std::is_same_v<T, dfloat>)
+          df_mac(acc[u], sa[rr][ty + 8 * u], bv);
+        else
+          acc[u] += sa[rr][ty + 8 * u] * bv;
+      }
     }
     __syncthreads();
   }
@@ -327,17 +334,35 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int p
   *o = accumulate ? *o + alpha * s : alpha * s;
 }
 
+// Sums of products for the reductions below: FP64 for FP32 and FP64 blocks,
+// double-float for double-float blocks
+template <class T>
+struct SumOf {
+  using type = double;
+};
+template <>
+struct SumOf<dfloat> {
+  using type = dfloat;
+};
+__device__ __forceinline__ void add_prod(double& s, float a, float b) {
+  s += (double)a * (double)b;
+}
+__device__ __forceinline__ void add_prod(double& s, double a, double b) { s += a * b; }
+__device__ __forceinline__ void add_prod(dfloat& s, dfloat a, dfloat b) { df_mac(s, a, b); }
+__device__ __forceinline__ void add_sum(double& s, double a) { s += a; }
+__device__ __forceinline__ void add_sum(dfloat& s, dfloat a) { df_acc(s, a); }
+
 // p == 1: part[chunk][j] = sum over the chunk's rows of a[r] B[r][j] (one
-// thread per column j, FP64 sums)
+// thread per column j)
 template <class T>
 __global__ void k_gram_row(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
                            int q, long long n, long long rows_per_chunk, double* __restrict__ part) {
   const long long r0 = (long long)blockIdx.x * rows_per_chunk;
   const long long r1 = min(n, r0 + rows_per_chunk);
   for (int j = threadIdx.x; j < q; j += blockDim.x) {
-    double s = 0.0;
-    for (long long r = r0; r < r1; ++r) s += (double)A[r * lda] * (double)B[r * ldb + j];
-    part[(long long)blockIdx.x * q + j] = s;
+    typename SumOf<T>::type s(0);
+    for (long long r = r0; r < r1; ++r) add_prod(s, A[r * lda], B[r * ldb + j]);
+    part[(long long)blockIdx.x * q + j] = (double)s;
   }
 }
 
@@ -348,9 +373,9 @@ __global__ void __launch_bounds__(512)
     k_gram_diag(const T* __restrict__ A, const T* __restrict__ B, int ld, long long n, int w0,
                 int w1, double* __restrict__ out, int ldo) {
   const int c = (int)blockIdx.x >= w0 ? (int)blockIdx.x + (w1 - w0) : (int)blockIdx.x;
-  double s = 0.0;
-  for (long long r = threadIdx.x; r < n; r += blockDim.x)
-    s += (double)A[r * ld + c] * (double)B[r * ld + c];
+  typename SumOf<T>::type sp(0);
+  for (long long r = threadIdx.x; r < n; r += blockDim.x) add_prod(sp, A[r * ld + c], B[r * ld + c]);
+  double s = (double)sp;
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
   __shared__ double red[16];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -392,6 +417,19 @@ __global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T*
   }
   __syncthreads();
   const int cj = j < split ? j : off2 + (j - split);
+  if constexpr (std::is_same_v<T, dfloat>) {
+    for (long long r = (long long)blockIdx.x * rpb + ry; r < n; r += (long long)gridDim.x * rpb) {
+      const T* a = A + r * lda;
+      T acc(0);
+#pragma unroll 4
+      for (int i = 0; i < p; ++i) df_mac(acc, a[i], sy[i * TW + tx]);
+      if (j < q) {
+        T* cp = C + r * ldc + cj;
+        if (!(beta == T(0))) df_mac(acc, beta, *cp);
+        *cp = df_norm(acc);
+      }
+    }
+  } else {
   for (long long r = (long long)blockIdx.x * rpb + ry; r < n; r += (long long)gridDim.x * rpb) {
     const T* a = A + r * lda;
     T acc = T(0);
@@ -405,6 +443,7 @@ __global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T*
       T* cp = C + r * ldc + cj;
       *cp = beta == T(0) ? acc : beta * *cp + acc;
     }
+  }
   }
 }
 
@@ -488,30 +527,151 @@ __global__ void k_spmm_hm_f64x4(const long long* __restrict__ ptr, const int* __
   }
 }
 
+// Double-float block product (H x, M x) for m % 4 == 0: the values of a
+// nonzero are (H.h, H.l, M.h, M.l), one 16-byte load; each lane owns 4
+// columns (two 16-byte loads per gathered row); H x accumulated as
+// sum_l h_kl x_l - (sum_l h_kl) x_k, as in the FP64 kernel, with unnormalised
+// double-float accumulators.
+__global__ void __launch_bounds__(256)
+    k_spmm_hm_df(const long long* __restrict__ ptr, const int* __restrict__ col,
+                 const float4* __restrict__ val, int n, const dfloat* __restrict__ X, int ldx,
+                 dfloat* __restrict__ YH, dfloat* __restrict__ YM, int ldy, int m) {
+  const int lane = threadIdx.x & 31;
+  const int G = m / 4, P = 32 / G;
+  const int g = lane / G, cv = (lane % G) * 4;
+  const bool act = g < P;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < n; k += warps) {
+    const long long s = ptr[k];
+    const int cnt = (int)(ptr[k + 1] - s);
+    const int* cr = col + s;
+    const float4* vr = val + s;
+    dfloat ah[4], am[4], hs(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ah[u] = am[u] = dfloat(0);
+    int e = act ? g : cnt;
+    for (; e + P < cnt; e += 2 * P) {
+      const int l0 = __ldg(cr + e), l1 = __ldg(cr + e + P);
+      const float4 v0 = __ldg(vr + e), v1 = __ldg(vr + e + P);
+      const float4* p0 = reinterpret_cast<const float4*>(X + (long long)l0 * ldx + cv);
+      const float4* p1 = reinterpret_cast<const float4*>(X + (long long)l1 * ldx + cv);
+      const float4 a0 = __ldg(p0), b0 = __ldg(p0 + 1), a1 = __ldg(p1), b1 = __ldg(p1 + 1);
+      const dfloat x0[4] = {dfloat(a0.x, a0.y), dfloat(a0.z, a0.w), dfloat(b0.x, b0.y),
+                            dfloat(b0.z, b0.w)};
+      const dfloat x1[4] = {dfloat(a1.x, a1.y), dfloat(a1.z, a1.w), dfloat(b1.x, b1.y),
+                            dfloat(b1.z, b1.w)};
+      const dfloat h0(v0.x, v0.y), m0(v0.z, v0.w), h1(v1.x, v1.y), m1(v1.z, v1.w);
+      df_acc(hs, h0);
+      df_acc(hs, h1);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        df_mac(ah[u], h0, x0[u]);
+        df_mac(am[u], m0, x0[u]);
+        df_mac(ah[u], h1, x1[u]);
+        df_mac(am[u], m1, x1[u]);
+      }
+    }
+    for (; e < cnt; e += P) {
+      const int l0 = __ldg(cr + e);
+      const float4 v0 = __ldg(vr + e);
+      const float4* p0 = reinterpret_cast<const float4*>(X + (long long)l0 * ldx + cv);
+      const float4 a0 = __ldg(p0), b0 = __ldg(p0 + 1);
+      const dfloat x0[4] = {dfloat(a0.x, a0.y), dfloat(a0.z, a0.w), dfloat(b0.x, b0.y),
+                            dfloat(b0.z, b0.w)};
+      const dfloat h0(v0.x, v0.y), m0(v0.z, v0.w);
+      df_acc(hs, h0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        df_mac(ah[u], h0, x0[u]);
+        df_mac(am[u], m0, x0[u]);
+      }
+    }
+    for (int q = 1; q < P; ++q) {  // groups are at most 3 for the 40-column block
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const dfloat th = __shfl_down_sync(kFull, ah[u], q * G);
+        const dfloat tm = __shfl_down_sync(kFull, am[u], q * G);
+        if (g == 0) {
+          df_acc(ah[u], th);
+          df_acc(am[u], tm);
+        }
+      }
+      const dfloat ts = __shfl_down_sync(kFull, hs, q * G);
+      if (g == 0) df_acc(hs, ts);
+    }
+    if (g == 0) {
+      const long long o = (long long)k * ldy + cv;
+      if (YH) {
+        const float4* pk = reinterpret_cast<const float4*>(X + (long long)k * ldx + cv);
+        const float4 xa = pk[0], xb = pk[1];
+        const dfloat xk[4] = {dfloat(xa.x, xa.y), dfloat(xa.z, xa.w), dfloat(xb.x, xb.y),
+                              dfloat(xb.z, xb.w)};
+        dfloat r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          df_mac(ah[u], -hs, xk[u]);
+          r[u] = df_norm(ah[u]);
+        }
+        float4* out = reinterpret_cast<float4*>(YH + o);
+        out[0] = make_float4(r[0].h, r[0].l, r[1].h, r[1].l);
+        out[1] = make_float4(r[2].h, r[2].l, r[3].h, r[3].l);
+      }
+      if (YM) {
+        dfloat r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = df_norm(am[u]);
+        float4* out = reinterpret_cast<float4*>(YM + o);
+        out[0] = make_float4(r[0].h, r[0].l, r[1].h, r[1].l);
+        out[1] = make_float4(r[2].h, r[2].l, r[3].h, r[3].l);
+      }
+    }
+  }
+}
+
 template <class T>
 void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T* val, long long n,
                  const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
   ProfScope ps(kProfSpmm);
   const int T_ = 256;
   long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
-  constexpr int VEC = Vec16<T>::n;
-  const bool vec_ok = m % VEC == 0 && m <= 32 * VEC && ldx % VEC == 0 && ldy % VEC == 0 &&
-                      reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
-                      (!YH || reinterpret_cast<uintptr_t>(YH) % 16 == 0) &&
-                      (!YM || reinterpret_cast<uintptr_t>(YM) % 16 == 0);
-  if constexpr (sizeof(T) == 8) {
-    if (vec_ok && m % 4 == 0 && m <= 128 && reinterpret_cast<uintptr_t>(val) % 16 == 0) {
-      (k_spmm_hm_f64x4<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m),
+  if constexpr (std::is_same_v<T, dfloat>) {
+    const bool df_ok = m % 4 == 0 && m <= 128 && ldx % 2 == 0 && ldy % 2 == 0 &&
+                       n * (long long)std::max(ldx, ldy) < (1LL << 31) &&
+                       reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
+                       reinterpret_cast<uintptr_t>(val) % 16 == 0 &&
+                       (!YH || reinterpret_cast<uintptr_t>(YH) % 16 == 0) &&
+                       (!YM || reinterpret_cast<uintptr_t>(YM) % 16 == 0);
+    if (df_ok)
+      (k_spmm_hm_df<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, reinterpret_cast<const float4*>(val),
+                                                     (int)n, X, ldx, YH, YM, ldy, m),
        ::ff::note_launch());
-      FF_LAUNCH_CHECK();
-      return;
+    else
+      (k_spmm_hm<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m),
+       ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  } else {
+    constexpr int VEC = Vec16<T>::n;
+    const bool vec_ok = m % VEC == 0 && m <= 32 * VEC && ldx % VEC == 0 && ldy % VEC == 0 &&
+                        reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
+                        (!YH || reinterpret_cast<uintptr_t>(YH) % 16 == 0) &&
+                        (!YM || reinterpret_cast<uintptr_t>(YM) % 16 == 0);
+    if constexpr (std::is_same_v<T, double>) {
+      if (vec_ok && m % 4 == 0 && m <= 128 && reinterpret_cast<uintptr_t>(val) % 16 == 0) {
+        (k_spmm_hm_f64x4<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy,
+                                                         m),
+         ::ff::note_launch());
+        FF_LAUNCH_CHECK();
+        return;
+      }
     }
+    if (vec_ok)
+      (k_spmm_hm_vec<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m),
+       ::ff::note_launch());
+    else
+      (k_spmm_hm<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m),
+       ::ff::note_launch());
+    FF_LAUNCH_CHECK();
   }
-  if (vec_ok)
-    (k_spmm_hm_vec<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m), ::ff::note_launch());
-  else
-    (k_spmm_hm<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m), ::ff::note_launch());
-  FF_LAUNCH_CHECK();
 }
 
 // One warp per row; lanes form groups of G = m / 8 lanes, each lane owning 8
@@ -776,5 +936,13 @@ template void block_update<float>(cudaStream_t, const float*, int, int, const fl
                                   int, long long, float, int, int, int);
 template void block_update<double>(cudaStream_t, const double*, int, int, const double*, int,
                                    double*, int, long long, double, int, int, int);
+template void spmm_hm_raw<dfloat>(cudaStream_t, const long long*, const int*, const dfloat*,
+                                  long long, const dfloat*, int, dfloat*, dfloat*, int, int);
+template void gram<dfloat>(cudaStream_t, const dfloat*, int, int, const dfloat*, int, int,
+                           long long, double*, double, bool, Buf&, int);
+template void gram_rr<dfloat>(cudaStream_t, const dfloat*, const dfloat*, const dfloat*, int, int,
+                              int, long long, double*, double*, Buf&);
+template void block_update<dfloat>(cudaStream_t, const dfloat*, int, int, const dfloat*, int,
+                                   dfloat*, int, long long, dfloat, int, int, int);
 
 }  // namespace ff

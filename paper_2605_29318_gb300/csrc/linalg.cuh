@@ -1,6 +1,7 @@
 // Block linear-algebra launchers used by the eigensolver (internal).
 #pragma once
 
+#include "dfloat.cuh"
 #include "ff_internal.cuh"
 
 namespace ff {

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 
 #include "linalg.cuh"
 
@@ -55,15 +56,15 @@ __global__ void k_gather_block(const T* __restrict__ X0, long long n, int m,
   X[r * ld + c] = X0[(long long)c * n + perm[r]];
 }
 
-template <class T>
+template <class T, class To = T>
 __global__ void k_scatter_block(const T* __restrict__ X, int ld, long long n, int m,
-                                const int* __restrict__ perm, T* __restrict__ out, long long ldo,
+                                const int* __restrict__ perm, To* __restrict__ out, long long ldo,
                                 int col0) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * m) return;
   long long r = t / m;
   int c = (int)(t % m);
-  out[(long long)(c + col0) * ldo + perm[r]] = X[r * ld + c];
+  out[(long long)(c + col0) * ldo + perm[r]] = (To)X[r * ld + c];
 }
 
 template <class T>
@@ -121,10 +122,61 @@ __global__ void k_colstats_partial(const T* __restrict__ X, const T* __restrict_
   }
 }
 
-// theta = x.Hx / x.Mx (Rayleigh quotient); ||Hx - theta Mx||^2 expanded in FP64.
+// The same statistics for double-float blocks: x.Hx and x.Mx in double-float
+// (slots 0, 1), and the residual norm taken directly, ||Hx - sigma Mx||^2 with
+// sigma the Ritz values of the last Rayleigh-Ritz step (slot 2; the residual
+// vector in double-float, its squares summed in FP32 within a thread), and
+// ||Mx||^2 (slot 4).  Expanding the norm would need the three sums to ~1e-13
+// relative for a 1e-6 residual, beyond double-float sums over n rows; sigma
+// differs from the Rayleigh quotient of the stored block by ~1e-9 relative,
+// which moves the residual norm by as much.
+__global__ void k_colstats_partial_df(const dfloat* __restrict__ X, const dfloat* __restrict__ HX,
+                                      const dfloat* __restrict__ MX, int ld, long long n, int m,
+                                      long long rows_per_block, const double* __restrict__ sigma,
+                                      double* __restrict__ part) {
+  __shared__ double sred[8][5][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r0 = (long long)blockIdx.x * rows_per_block;
+  const long long r1 = min(n, r0 + rows_per_block);
+  for (int c0 = 0; c0 < m; c0 += 32) {
+    const int col = c0 + lane;
+    dfloat xh(0), xm(0);
+    float rr = 0.f, mm2 = 0.f;
+    if (col < m) {
+      const dfloat ns(-sigma[col]);
+      for (long long r = r0 + w; r < r1; r += 8) {
+        const dfloat x = X[r * ld + col], h = HX[r * ld + col], mm = MX[r * ld + col];
+        df_mac(xh, x, h);
+        df_mac(xm, x, mm);
+        dfloat res = h;
+        df_mac(res, ns, mm);
+        const float rf = (float)df_norm(res), mf = (float)mm;
+        rr = fmaf(rf, rf, rr);
+        mm2 = fmaf(mf, mf, mm2);
+      }
+    }
+    sred[w][0][lane] = (double)xh;
+    sred[w][1][lane] = (double)xm;
+    sred[w][2][lane] = rr;
+    sred[w][3][lane] = 0.0;
+    sred[w][4][lane] = mm2;
+    __syncthreads();
+    if (w == 0 && col < m)
+      for (int q = 0; q < 5; ++q) {
+        double t = 0;
+        for (int ww = 0; ww < 8; ++ww) t += sred[ww][q][lane];
+        part[((long long)blockIdx.x * 5 + q) * m + col] = t;
+      }
+    __syncthreads();
+  }
+}
+
+// theta = x.Hx / x.Mx (Rayleigh quotient); ||Hx - theta Mx||^2 expanded in
+// FP64, or (direct) the norm summed by the partial kernel.
 // One block per column, fixed-order tree reduction over the partials.
 __global__ void k_colstats_final(const double* __restrict__ part, int blocks, int m,
-                                 double* __restrict__ theta, double* __restrict__ stats) {
+                                 double* __restrict__ theta, double* __restrict__ stats,
+                                 int direct) {
   __shared__ double sh[5][128];
   const int col = blockIdx.x;
   double a[5] = {0, 0, 0, 0, 0};
@@ -139,7 +191,8 @@ __global__ void k_colstats_final(const double* __restrict__ part, int blocks, in
   }
   if (threadIdx.x == 0) {
     const double th = sh[0][0] / sh[1][0];
-    const double r2 = fmax(sh[2][0] - 2.0 * th * sh[3][0] + th * th * sh[4][0], 0.0);
+    const double r2 =
+        direct ? sh[2][0] : fmax(sh[2][0] - 2.0 * th * sh[3][0] + th * th * sh[4][0], 0.0);
     theta[col] = th;
     stats[col] = th;
     stats[m + col] = r2;
@@ -160,8 +213,14 @@ __global__ void k_cheb_init(const T* __restrict__ HX, const T* __restrict__ MX, 
   int c = (int)(t % m);
   float b = 0.f;
   if (active[c]) {
-    double rr = (double)HX[r * ld + c] - theta[c] * (double)MX[r * ld + c];
-    b = (float)(rr / (double)hdiag[r]);
+    if constexpr (std::is_same_v<T, dfloat>) {  // the residual in double-float
+      dfloat rr = HX[r * ld + c];
+      df_mac(rr, dfloat(-theta[c]), MX[r * ld + c]);
+      b = (float)df_norm(rr) / hdiag[r];
+    } else {
+      double rr = (double)HX[r * ld + c] - theta[c] * (double)MX[r * ld + c];
+      b = (float)(rr / (double)hdiag[r]);
+    }
   }
   res[t] = b;
   if (d16) {  // BF16 directions: x starts from the rounded one
@@ -287,9 +346,13 @@ struct Phase {
   bool have_best = false;          // out: the best-block slot holds a block
 };
 
+// the caller's precision of the modes: FP64 for a double-float phase
+template <class T>
+using OutOf = std::conditional_t<std::is_same_v<T, dfloat>, double, T>;
+
 template <class T>
 ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
-                double* eigvals, T* modes, ff_eig_report* rep) {
+                double* eigvals, OutOf<T>* modes, ff_eig_report* rep) {
   using clock = std::chrono::steady_clock;
   const auto t_start = clock::now();
   Solver<T> s;
@@ -427,9 +490,16 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   std::vector<double> best_res;
   for (;; ++it) {
     // Rayleigh quotients and residual norms of the current X (products recomputed)
-    (k_colstats_partial<T><<<cs_blocks, 256, 0, st>>>(s.S[cur], s.HS[cur], s.MS[cur], ld, n, nb,
-                                                     rpb, cs_part), ::ff::note_launch());
-    (k_colstats_final<<<nb, 128, 0, st>>>(cs_part, cs_blocks, nb, s.theta_d, s.norms_d),
+    if constexpr (std::is_same_v<T, dfloat>)
+      (k_colstats_partial_df<<<cs_blocks, 256, 0, st>>>(s.S[cur], s.HS[cur], s.MS[cur], ld, n, nb,
+                                                        rpb, s.theta_d, cs_part),
+       ::ff::note_launch());
+    else
+      (k_colstats_partial<T><<<cs_blocks, 256, 0, st>>>(s.S[cur], s.HS[cur], s.MS[cur], ld, n,
+                                                       nb, rpb, cs_part),
+       ::ff::note_launch());
+    (k_colstats_final<<<nb, 128, 0, st>>>(cs_part, cs_blocks, nb, s.theta_d, s.norms_d,
+                                          std::is_same_v<T, dfloat> ? 1 : 0),
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
     FF_CUDA(cudaMemcpyAsync(s.h_pin, s.norms_d, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
@@ -571,11 +641,14 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   if (modes) {
     int col0 = 0;
     if (incl_c0) {
-      (k_scatter_block<T><<<blocks(n), TB, 0, st>>>(s.c0, 1, n, 1, c->perm.as<int>(), modes, n, 0), ::ff::note_launch());
+      (k_scatter_block<T, OutOf<T>><<<blocks(n), TB, 0, st>>>(s.c0, 1, n, 1, c->perm.as<int>(),
+                                                               modes, n, 0),
+       ::ff::note_launch());
       col0 = 1;
     }
-    (k_scatter_block<T><<<blocks(n * kw), TB, 0, st>>>(s.S[cur], ld, n, kw, c->perm.as<int>(),
-                                                      modes, n, col0), ::ff::note_launch());
+    (k_scatter_block<T, OutOf<T>><<<blocks(n * kw), TB, 0, st>>>(
+         s.S[cur], ld, n, kw, c->perm.as<int>(), modes, n, col0),
+     ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
   FF_CUDA(cudaStreamSynchronize(st));
@@ -647,8 +720,10 @@ ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
     o2.time_budget_s = std::max(1e-9, o.time_budget_s - used);
     if (s1 == FF_ERR_TIMEOUT) o2.max_iter = 0;
   }
+  // in double-float arithmetic (H, M split into FP32 pairs, ~48-bit significands)
   if (p32.have_best) p64.X0_int = reinterpret_cast<const float*>(c->ws[21].p);
-  ff_status s2 = solve<double>(c, k, o2, p64, nullptr, eigvals, static_cast<double*>(modes), rep);
+  p64.aval = c->a_valdf.p;
+  ff_status s2 = solve<dfloat>(c, k, o2, p64, nullptr, eigvals, static_cast<double*>(modes), rep);
   if (s1 == FF_ERR_TIMEOUT && s2 == FF_ERR_NOT_CONVERGED) s2 = FF_ERR_TIMEOUT;
   if (rep) {
     rep->iterations += r1.iterations;
