@@ -277,7 +277,8 @@ def run_ours(args):
         "metric": METRIC, "value": round(ms / 1000.0, 5), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.prec == "fp64" else "f32",
+        "dtype": (("f32+bf16, then f32x2 double-float; f64 Rayleigh-Ritz" if args.fp32_phase
+                   else "f64") if args.prec == "fp64" else "f32+bf16"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.prec, "tol": args.tol,
                    "cheb_degree": args.cheb, "cheb_degree_fp64": args.cheb_fp64,
@@ -291,7 +292,9 @@ def run_ours(args):
                      "traffic": tr, "algorithmic_bytes_per_launch": pre_bytes,
                      "avg_launch_ms": round(pre_ms, 5), "launches": cnt},
         "spmm": {"avg_launch_ms": round(stot / max(scnt, 1), 5), "launches": scnt,
-                 "algorithmic_gbs": round(spmm_gbs, 1) if spmm_gbs else None},
+                 "algorithmic_gbs": round(spmm_gbs, 1) if spmm_gbs else None,
+                 "note": "average over both phases' launches, bytes counted at the second "
+                         "phase's 8-byte elements"},
         "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in prof.items()},
         "warm": {"value": round(wms / 1000.0, 5), "unit": "s",
                  "plain_over_warm": round(ms / wms, 4),
