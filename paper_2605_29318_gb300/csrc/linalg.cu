@@ -352,17 +352,29 @@ __device__ __forceinline__ void add_prod(dfloat& s, dfloat a, dfloat b) { df_mac
 __device__ __forceinline__ void add_sum(double& s, double a) { s += a; }
 __device__ __forceinline__ void add_sum(dfloat& s, dfloat a) { df_acc(s, a); }
 
-// p == 1: part[chunk][j] = sum over the chunk's rows of a[r] B[r][j] (one
-// thread per column j)
+// p == 1: part[chunk][j] = sum over the chunk's rows of a[r] B[r][j]; the 8
+// warps of a block take interleaved rows, lanes take columns
 template <class T>
-__global__ void k_gram_row(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb,
-                           int q, long long n, long long rows_per_chunk, double* __restrict__ part) {
+__global__ void __launch_bounds__(256)
+    k_gram_row(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb, int q,
+               long long n, long long rows_per_chunk, double* __restrict__ part) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long r0 = (long long)blockIdx.x * rows_per_chunk;
   const long long r1 = min(n, r0 + rows_per_chunk);
-  for (int j = threadIdx.x; j < q; j += blockDim.x) {
-    typename SumOf<T>::type s(0);
-    for (long long r = r0; r < r1; ++r) add_prod(s, A[r * lda], B[r * ldb + j]);
-    part[(long long)blockIdx.x * q + j] = (double)s;
+  for (int j0 = 0; j0 < q; j0 += 32) {
+    const int j = j0 + lane;
+    typename SumOf<T>::type sp(0);
+    if (j < q)
+      for (long long r = r0 + w; r < r1; r += 8) add_prod(sp, A[r * lda], B[r * ldb + j]);
+    red[w][lane] = (double)sp;
+    __syncthreads();
+    if (w == 0 && j < q) {
+      double t = 0.0;
+      for (int ww = 0; ww < 8; ++ww) t += red[ww][lane];
+      part[(long long)blockIdx.x * q + j] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -444,6 +456,234 @@ __global__ void k_block_update(const T* __restrict__ A, int lda, int p, const T*
       *cp = beta == T(0) ? acc : beta * *cp + acc;
     }
   }
+  }
+}
+
+// ------------------------------------------------------------- register-tiled kernels
+// A Gram tile: operand panels (first column of the tile in each), destination
+// of entry (0, 0) and the valid rows and columns (multiples of 4)
+struct GramTile {
+  const void* a;
+  const void* b;
+  double* out;
+  int pi, qj;
+  int diag_only;
+};
+constexpr int kMaxGramTiles = 32;
+struct GramTiles {
+  GramTile t[kMaxGramTiles];
+  int count;
+};
+
+// Four consecutive values of a row (16-byte aligned): one 16-byte load for
+// FP32, two for FP64 and double-float.
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const dfloat* p, dfloat (&v)[4]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0];
+  const float4 b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = dfloat(a.x, a.y); v[1] = dfloat(a.z, a.w); v[2] = dfloat(b.x, b.y);
+  v[3] = dfloat(b.z, b.w);
+}
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void store4(dfloat* p, const dfloat (&v)[4]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0].h, v[0].l, v[1].h, v[1].l);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[2].h, v[2].l, v[3].h, v[3].l);
+}
+
+// 16-byte asynchronous copy global -> shared; bytes = 0 fills zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// Several Gram tiles in one launch, each with its own operand panels and
+// destination: part[chunk][tile][i][j] = sum over the chunk's rows of
+// a[r][i] b[r][j] for a TW x TW tile.  The block streams its rows through
+// shared memory in 32-row slabs of both panels' TW columns (16-byte
+// asynchronous copies, two slabs in flight; rows past the chunk and columns
+// past the tile's valid width are zero-filled).  A group of TD x TD threads
+// (TD = TW / 4) covers the tile, each thread a 4 x 4 register block; GR
+// groups take interleaved rows of a slab and are summed in shared memory at
+// the end.  Sums in T within a thread (double-float for double-float panels),
+// FP64 from there on.
+template <class T, int TW>
+__global__ void __launch_bounds__(256)
+    k_gram_tiles(GramTiles tiles, int lda, int ldb, long long n, long long rows_per_chunk,
+                 double* __restrict__ part) {
+  constexpr int TD = TW / 4, TT = TD * TD, GR = 256 / TT, NT = TT * GR;
+  constexpr int SL = 32, EPC = 16 / (int)sizeof(T), CPR = TW / EPC;
+  constexpr int kSlab = 2 * 2 * SL * TW * (int)sizeof(T);
+  constexpr int kRed = (GR - 1) * TT * 16 * 8;
+  __shared__ __align__(16) unsigned char sm[kSlab > kRed ? kSlab : kRed];
+  T* slab = reinterpret_cast<T*>(sm);  // [buf][panel][row][TW]
+  const int tid = threadIdx.x, grp = tid / TT, lt = tid % TT;
+  const int ti = lt / TD, tj = lt % TD;
+  const GramTile tl = tiles.t[blockIdx.y];
+  const T* pa = static_cast<const T*>(tl.a);
+  const T* pb = static_cast<const T*>(tl.b);
+  const bool live = grp < GR && 4 * ti < tl.pi && 4 * tj < tl.qj;
+  const long long r0 = (long long)blockIdx.x * rows_per_chunk;
+  const long long r1 = min(n, r0 + rows_per_chunk);
+  const int nslab = (int)((r1 - r0 + SL - 1) / SL);
+  auto issue = [&](int buf, long long rs) {
+    for (int t = tid; t < 2 * SL * CPR; t += NT) {
+      const int pan = t / (SL * CPR), w = t % (SL * CPR), rr = w / CPR, cc = (w % CPR) * EPC;
+      const long long r = rs + rr;
+      const bool ok = r < r1 && cc < (pan == 0 ? tl.pi : tl.qj);
+      const T* src = pan == 0 ? pa + (ok ? r * lda + cc : r0 * lda) : pb + (ok ? r * ldb + cc : r0 * ldb);
+      cp_async16(slab + ((buf * 2 + pan) * SL + rr) * TW + cc, src, ok ? 16 : 0);
+    }
+  };
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+  if (nslab > 0) issue(0, r0);
+  cp_async_commit();
+  for (int sl = 0; sl < nslab; ++sl) {
+    if (sl + 1 < nslab) issue((sl + 1) & 1, r0 + (long long)(sl + 1) * SL);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    if (live) {
+      const T* sa = slab + ((sl & 1) * 2 + 0) * SL * TW + 4 * ti;
+      const T* sb = slab + ((sl & 1) * 2 + 1) * SL * TW + 4 * tj;
+#pragma unroll 4
+      for (int rr = grp; rr < SL; rr += GR) {
+        T x[4], y[4];
+        load4(sa + rr * TW, x);
+        load4(sb + rr * TW, y);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) mac(acc[u][v], x[u], y[v]);
+      }
+    }
+    __syncthreads();
+  }
+  double* red = reinterpret_cast<double*>(sm);  // [GR - 1][TT][16]
+  if (grp > 0 && grp < GR)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) red[((grp - 1) * TT + lt) * 16 + 4 * u + v] = (double)acc[u][v];
+  __syncthreads();
+  if (grp == 0 && live) {
+    double* o = part + ((long long)blockIdx.x * tiles.count + blockIdx.y) * (TW * TW);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double t = (double)acc[u][v];
+        for (int g = 1; g < GR; ++g) t += red[((g - 1) * TT + lt) * 16 + 4 * u + v];
+        o[(4 * ti + u) * TW + 4 * tj + v] = t;
+      }
+  }
+}
+
+// out = alpha * (sum over chunks) (+ out), per tile entry; tiles marked
+// diag_only write their diagonal alone
+template <int TW>
+__global__ void k_gram_tiles_reduce(GramTiles tiles, int chunks, int ldo, double alpha,
+                                    int accumulate, const double* __restrict__ part) {
+  const int t = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= TW * TW) return;
+  const int i = e / TW, j = e % TW;
+  const GramTile tl = tiles.t[t];
+  if (i >= tl.pi || j >= tl.qj || (tl.diag_only && i != j)) return;
+  double s = 0.0;
+  for (int c = 0; c < chunks; ++c) s += part[((long long)c * tiles.count + t) * (TW * TW) + e];
+  double* o = tl.out + (long long)i * ldo + j;
+  *o = accumulate ? *o + alpha * s : alpha * s;
+}
+
+// C = beta C + A Y for blocks with p, q, lda, ldc, split, off2 multiples of 4:
+// each thread computes a 4 x 4 register block (4 consecutive rows, 4
+// consecutive output columns) from 16-byte row loads of A and of the Y tile
+// staged in shared memory; TD = TW / 4 threads span a TW-column tile and
+// RG = 256 / TD row groups share a block.  Columns at or past `split` are
+// written at off2 + (j - split).
+template <class T, int TW>
+__global__ void __launch_bounds__(256)
+    k_block_update_rt(const T* __restrict__ A, int lda, int p, const T* __restrict__ Y, int ldy,
+                      int q, T* __restrict__ C, int ldc, long long n, T beta, int split,
+                      int off2) {
+  constexpr int TD = TW / 4, RG = 256 / TD, RR = 4;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sy = reinterpret_cast<T*>(smraw);  // p x TW
+  const int c0 = blockIdx.y * TW;
+  for (int t = threadIdx.x; t < p * TW; t += blockDim.x) {
+    const int i = t / TW, jj = c0 + (t % TW);
+    sy[t] = jj < q ? Y[(long long)i * ldy + jj] : T(0);
+  }
+  __syncthreads();
+  const int tc = threadIdx.x % TD, rg = threadIdx.x / TD;
+  const int j0 = c0 + 4 * tc;
+  if (rg >= RG || j0 >= q) return;
+  const int cj = j0 < split ? j0 : off2 + (j0 - split);
+  const T* yb = sy + 4 * tc;
+  for (long long rb = ((long long)blockIdx.x * RG + rg) * RR; rb < n;
+       rb += (long long)gridDim.x * RG * RR) {
+    const T* ar[RR];
+#pragma unroll
+    for (int rr = 0; rr < RR; ++rr) ar[rr] = A + min(rb + rr, n - 1) * lda;  // tail rows clamped
+    T acc[RR][4];
+#pragma unroll
+    for (int rr = 0; rr < RR; ++rr)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[rr][v] = T(0);
+    for (int i = 0; i < p; i += 4) {
+      T y[4][4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) load4(yb + (i + kk) * TW, y[kk]);
+#pragma unroll
+      for (int rr = 0; rr < RR; ++rr) {
+        T x[4];
+        load4(ar[rr] + i, x);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) mac(acc[rr][v], x[kk], y[kk][v]);
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RR; ++rr) {
+      if (rb + rr >= n) break;
+      T* cp = C + (rb + rr) * ldc + cj;
+      if (!(beta == T(0))) {
+        T old[4];
+        load4(cp, old);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) mac(acc[rr][v], beta, old[v]);
+      }
+      T o4[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) o4[v] = finish(acc[rr][v]);
+      store4(cp, o4);
+    }
   }
 }
 
@@ -824,17 +1064,73 @@ void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const floa
   FF_LAUNCH_CHECK();
 }
 
+namespace {
+
+bool al16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
+// append the TW x TW tiles of a (p x q) product A^T B written at out (row
+// stride ldo); false when the list would overflow
+template <class T>
+bool add_tiles(GramTiles& g, int TW, const T* A, int p, const T* B, int q, double* out, int ldo,
+               int diag_only = 0) {
+  for (int i0 = 0; i0 < p; i0 += TW)
+    for (int j0 = 0; j0 < q; j0 += TW) {
+      if (diag_only && i0 != j0) continue;
+      if (g.count == kMaxGramTiles) return false;
+      g.t[g.count++] = GramTile{A + i0, B + j0, out + (long long)i0 * ldo + j0,
+                                std::min(TW, p - i0), std::min(TW, q - j0), diag_only};
+    }
+  return true;
+}
+
+template <class T>
+void launch_tiles(cudaStream_t st, const GramTiles& g, int TW, int lda, int ldb, long long n,
+                  int ldo, double alpha, bool accumulate, Buf& part) {
+  // about four blocks per SM in all, at least 64 rows per chunk
+  long long chunks = std::max<long long>(1, (152LL * 4) / g.count);
+  chunks = std::max<long long>(1, std::min(chunks, (n + 63) / 64));
+  const long long rpc = (n + chunks - 1) / chunks;
+  chunks = (n + rpc - 1) / rpc;
+  double* pp = reinterpret_cast<double*>(part.ensure(sizeof(double) * chunks * g.count * TW * TW));
+  dim3 grid((unsigned)chunks, (unsigned)g.count);
+  dim3 rgrid((unsigned)((TW * TW + 255) / 256), (unsigned)g.count);
+  if (TW == 40) {
+    (k_gram_tiles<T, 40><<<grid, 200, 0, st>>>(g, lda, ldb, n, rpc, pp), ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    (k_gram_tiles_reduce<40><<<rgrid, 256, 0, st>>>(g, (int)chunks, ldo, alpha, accumulate ? 1 : 0,
+                                                   pp),
+     ::ff::note_launch());
+  } else {
+    (k_gram_tiles<T, 32><<<grid, 256, 0, st>>>(g, lda, ldb, n, rpc, pp), ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    (k_gram_tiles_reduce<32><<<rgrid, 256, 0, st>>>(g, (int)chunks, ldo, alpha, accumulate ? 1 : 0,
+                                                   pp),
+     ::ff::note_launch());
+  }
+  FF_LAUNCH_CHECK();
+}
+
+}  // namespace
+
 template <class T>
 void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int q, long long n,
           double* out, double alpha, bool accumulate, Buf& part, int ldo) {
   if (p <= 0 || q <= 0) return;
   ProfScope ps(kProfGram);
+  if (p % 4 == 0 && q % 4 == 0 && lda % 4 == 0 && ldb % 4 == 0 && al16(A) && al16(B)) {
+    const int TW = p % 40 == 0 && q % 40 == 0 ? 40 : 32;
+    GramTiles g;
+    g.count = 0;
+    if (add_tiles(g, TW, A, p, B, q, out, ldo < 0 ? q : ldo)) {
+      launch_tiles<T>(st, g, TW, lda, ldb, n, ldo < 0 ? q : ldo, alpha, accumulate, part);
+      return;
+    }
+  }
   if (p == 1 && q <= 256) {  // a row vector times a block: no tile of padding
     const long long chunks = std::max<long long>(1, std::min<long long>((n + 255) / 256, 608));
     const long long rpc = (n + chunks - 1) / chunks;
     double* pp = reinterpret_cast<double*>(part.ensure(sizeof(double) * chunks * q));
-    (k_gram_row<T><<<(unsigned)chunks, ((q + 31) / 32) * 32, 0, st>>>(A, lda, B, ldb, q, n, rpc,
-                                                                      pp),
+    (k_gram_row<T><<<(unsigned)chunks, 256, 0, st>>>(A, lda, B, ldb, q, n, rpc, pp),
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
     (k_gram_reduce<<<(q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, q, q, out, ldo < 0 ? q : ldo,
@@ -869,6 +1165,31 @@ template <class T>
 void gram_rr(cudaStream_t st, const T* S, const T* HS, const T* MS, int ld, int nb, int nblk,
              long long n, double* A, double* B, Buf& part) {
   const int ns = nblk * nb;
+  if (nb % 4 == 0 && ld % 4 == 0 && al16(S) && al16(HS) && al16(MS)) {
+    // all tiles in one launch: the lower block triangle of A, the W columns
+    // of B and the diagonals of B's X and P blocks
+    const int TW = nb % 40 == 0 ? 40 : 32;
+    GramTiles g;
+    g.count = 0;
+    bool ok = true;
+    for (int j = 0; j < nblk && ok; ++j)
+      for (int i = j; i < nblk && ok; ++i)
+        ok = add_tiles(g, TW, S + i * nb, nb, HS + j * nb, nb, A + (long long)i * nb * ns + j * nb,
+                       ns);
+    for (int i = 0; i < nblk && ok; ++i)
+      ok = add_tiles(g, TW, S + i * nb, nb, MS + nb, nb, B + (long long)i * nb * ns + nb, ns);
+    for (int i = 0; i < nblk && ok; ++i)
+      if (i != 1)
+        ok = add_tiles(g, TW, S + i * nb, nb, MS + i * nb, nb,
+                       B + (long long)i * nb * ns + i * nb, ns, 1);
+    if (ok) {
+      ProfScope ps(kProfGram);
+      launch_tiles<T>(st, g, TW, ld, ld, n, ns, 1.0, false, part);
+      (k_gram_mirror<<<(ns * ns + 255) / 256, 256, 0, st>>>(A, B, ns, nb), ::ff::note_launch());
+      FF_LAUNCH_CHECK();
+      return;
+    }
+  }
   // lower block triangle: A_ij = S_i^T (H S_j) for block i >= j.  The products
   // of the smooth, converging blocks (H X) are the accurate ones; W^T (H X)
   // is taken rather than X^T (H W), whose rounding follows the rough W.
@@ -893,19 +1214,49 @@ void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q
     // C = beta * C only; p == 0 never happens in the solver
     return;
   }
-  const int rpb = 8;  // rows per block (one TW-thread group each)
   const bool w40 = q % 40 == 0;
   const int TW = w40 ? 40 : 32;
   size_t smem = sizeof(T) * (size_t)p * TW;
-  static bool attr_set[2][2] = {{false, false}, {false, false}};
-  if (smem > 48 * 1024 && !attr_set[sizeof(T) == 8][w40]) {
+  const int sp = split < 0 ? q : split;
+  if (p % 4 == 0 && q % 4 == 0 && lda % 4 == 0 && ldc % 4 == 0 && sp % 4 == 0 && off2 % 4 == 0 &&
+      al16(A) && al16(C) && smem <= 200 * 1024) {
+    static bool rt_attr[3][2] = {};
+    const int ti = std::is_same_v<T, float> ? 0 : std::is_same_v<T, double> ? 1 : 2;
+    if (smem > 48 * 1024 && !rt_attr[ti][w40]) {
+      if (w40)
+        FF_CUDA(cudaFuncSetAttribute(k_block_update_rt<T, 40>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      else
+        FF_CUDA(cudaFuncSetAttribute(k_block_update_rt<T, 32>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      rt_attr[ti][w40] = true;
+    }
+    const int TD = TW / 4, RG = 256 / TD;
+    const long long rows_per_block = (long long)RG * 4;
+    dim3 grid((unsigned)std::min<long long>((n + rows_per_block - 1) / rows_per_block, 152LL * 8),
+              (unsigned)((q + TW - 1) / TW));
+    if (w40)
+      (k_block_update_rt<T, 40><<<grid, TD * RG, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C,
+                                                            ldc, n, beta, sp, off2),
+       ::ff::note_launch());
+    else
+      (k_block_update_rt<T, 32><<<grid, TD * RG, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C,
+                                                            ldc, n, beta, sp, off2),
+       ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    return;
+  }
+  const int rpb = 8;  // rows per block (one TW-thread group each)
+  static bool attr_set[3][2] = {};
+  const int tix = std::is_same_v<T, float> ? 0 : std::is_same_v<T, double> ? 1 : 2;
+  if (smem > 48 * 1024 && !attr_set[tix][w40]) {
     if (w40)
       FF_CUDA(cudaFuncSetAttribute(k_block_update<T, 40>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     else
       FF_CUDA(cudaFuncSetAttribute(k_block_update<T, 32>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set[sizeof(T) == 8][w40] = true;
+    attr_set[tix][w40] = true;
   }
   dim3 grid((unsigned)std::min<long long>((n + rpb - 1) / rpb, 152LL * 16),
             (unsigned)((q + TW - 1) / TW));
