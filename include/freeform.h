@@ -127,6 +127,9 @@ typedef struct {
   double fp32_tol;      /* residual at which the FP32 phase hands over (1e-4) */
   int cheb_degree_fp64; /* Chebyshev degree of the FP64 phase that follows an FP32 phase;
                            0 = cheb_degree (64) */
+  int precond_tc;       /* 1: the preconditioner's H products on tensor cores, with H in
+                           BF16 dense tiles of 16-row blocks (block widths 8..64 in steps
+                           of 8); 0: sparse FP32 H on CUDA cores (1) */
 } ff_eig_opts;
 
 typedef struct {

@@ -16,6 +16,7 @@
 // the off-diagonal entries of its row, which makes H_w 1 = 0 exact in storage
 // (the constant mode of Supp. Sec. B is an exact null vector).
 #include "ff_internal.cuh"
+#include "linalg.cuh"
 
 namespace ff {
 namespace {
@@ -331,6 +332,7 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
+  cheb_tc_build(c);
   FF_CUDA(cudaStreamSynchronize(st));
 }
 

@@ -143,6 +143,14 @@ struct ff_ctx {
   ff::Buf a_valdf;   // float4[n2] (H.h, H.l, M.h, M.l) double-float split of a_val
                      // (FP64 contexts)
   ff::Buf h_f32;     // float[n2] H values for the preconditioner
+  // the same H in 16-row blocks, each a dense BF16 tile over the union of its
+  // rows' columns in mma.m16n8k16 A-fragment order (tensor-core
+  // preconditioner step); tc_ksteps = 0 when not built
+  ff::Buf tc_kofs;   // int[nblk + 1] first k-step (16 union columns) of each block
+  ff::Buf tc_ucol;   // int[16 * ksteps] union columns
+  ff::Buf tc_tile;   // uint4[32 * ksteps] A fragments
+  ff::Buf tc_hs;     // float[n] row sums of the rounded entries
+  long long tc_ksteps = 0;
   ff::Buf hdiag_f32; // float[n] diag(H)
   ff::Buf wh;        // T[n] v_i (lambda_i + 4 mu_i)
   // device flags

@@ -572,14 +572,17 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
       __nv_bfloat16* bout = s.cb1;
       for (int j = 1; j < deg; ++j) {
         const double rn = 1.0 / (2.0 * sigma1 - rho);
-        if (b16)
+        const float c1 = (float)(rn * rho), c2 = (float)(2.0 * rn / delta);
+        // the tensor-core step when its tiles exist, else the CUDA-core ones
+        const bool tc =
+            b16 && o.precond_tc && cheb_step_tc(st, c, nb, bin, bout, s.cx, s.cres, c1, c2);
+        if (!tc && b16) {
           cheb_step_b16(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
-                        c->hdiag_f32.as<float>(), n, nb, bin, bout, s.cx, s.cres,
-                        (float)(rn * rho), (float)(2.0 * rn / delta));
-        else
+                        c->hdiag_f32.as<float>(), n, nb, bin, bout, s.cx, s.cres, c1, c2);
+        } else if (!tc) {
           cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
-                    c->hdiag_f32.as<float>(), n, nb, nb, din, dout, s.cx, s.cres,
-                    (float)(rn * rho), (float)(2.0 * rn / delta));
+                    c->hdiag_f32.as<float>(), n, nb, nb, din, dout, s.cx, s.cres, c1, c2);
+        }
         ++s.spmv_calls;
         rho = rn;
         std::swap(din, dout);
