@@ -258,15 +258,26 @@ def run_ours(args):
         return
     peak, peak_kind = _peaks()
     # dominant kernel: the Chebyshev preconditioner step (H-only block product
-    # on the 40-column block, BF16 directions): H values and columns, row
-    # pointers and diagonal, read d_in (2 B), write d_out (2 B), read and
-    # write res and x (FP32): 20 B per block element
+    # on the 40-column block, BF16 directions).  Tensor-core form: per 16-column
+    # k-step a 512 B BF16 tile and 16 int32 union columns, per 16-row block an
+    # int32 offset, per row the rounded row sum and the diagonal (FP32); read
+    # d_in (2 B), write d_out (2 B), read and write res and x (FP32): 20 B per
+    # block element.  (Sparse CUDA-core form when the tiles are not built: H
+    # values and columns, row pointers, diagonal.)
     cnt, tot = prof["precond"]
     m = ((31 + 8 + 3) // 4) * 4
-    pre_bytes = n2 * 8 + (n + 1) * 8 + n * 4 + 20 * n * m
+    row_blocks, ksteps = ctx.precond_layout()
+    if ksteps:
+        pre_kernel = "k_cheb_step_tc"
+        pre_desc = "k_cheb_step_tc (Chebyshev preconditioner step, BF16 tiles on tensor cores)"
+        pre_bytes = ksteps * (512 + 64) + (row_blocks + 1) * 4 + n * 8 + 20 * n * m
+    else:
+        pre_kernel = "k_cheb_step_b16"
+        pre_desc = "k_cheb_step_b16 (Chebyshev preconditioner step, BF16 directions)"
+        pre_bytes = n2 * 8 + (n + 1) * 8 + n * 4 + 20 * n * m
     pre_ms = tot / max(cnt, 1)
     achieved = pre_bytes / (pre_ms * 1e-3) / 1e9 if cnt else None
-    tr = _traffic("precond", "k_cheb_step_b16")
+    tr = _traffic("precond", pre_kernel)
     # secondary: fused (H, M) block product
     scnt, stot = prof["spmm"]
     t_el = 8 if args.prec == "fp64" else 4
@@ -285,7 +296,7 @@ def run_ours(args):
                    "n": n, "n1": n1, "n2": n2,
                    "l2": "flushed by a 256 MB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"kernel": "k_cheb_step_b16 (Chebyshev preconditioner step, BF16 directions)",
+        "roofline": {"kernel": pre_desc,
                      "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4) if achieved else None,

@@ -180,6 +180,14 @@ ff_status eigenmodes(ff_ctx* ctx, int k, const ff_eig_opts* opts, const void* X0
  * before assemble_hessian.  Any pointer may be NULL. */
 ff_status ff_get_sizes(const ff_ctx* ctx, int64_t* n, int64_t* n1, int64_t* n2);
 
+/* Layout of the preconditioner's tensor-core copy of H_w (built by
+ * assemble_hessian): row_blocks = ceil(n / 16) blocks of 16 rows, ksteps = the
+ * 16-column steps over all blocks' column unions (each step: a 16 x 16 BF16
+ * tile of 512 bytes and 16 int32 column indices).  ksteps = 0 when that copy
+ * was not built (a block's columns span more than 262144 indices) and the
+ * preconditioner runs on the sparse FP32 values.  Any pointer may be NULL. */
+ff_status ff_get_precond_layout(const ff_ctx* ctx, int64_t* row_blocks, int64_t* ksteps);
+
 /* Neighbour lists as CSR: ptr int64[n+1], idx int32[n1]; row i lists the nodes
  * k covering X_i, ascending.  phi double[n1] and dphi double[3*n1] (x block,
  * then y, then z) are the shape functions phi_k(X_i) and their gradients,

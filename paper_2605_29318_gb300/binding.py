@@ -25,7 +25,7 @@ PREC = {"fp32": 0, "fp64": 1}
 
 # every symbol the header declares (checked by the CPU tests)
 EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build",
-           "assemble_hessian", "ff_eig_opts_default", "eigenmodes", "ff_get_sizes",
+           "assemble_hessian", "ff_eig_opts_default", "eigenmodes", "ff_get_sizes", "ff_get_precond_layout",
            "ff_export_rkpm", "ff_export_matrices", "ff_apply_operators",
            "ff_apply_operators_noalloc", "ff_profile_enable", "ff_profile_read", "ff_launch_count",
            "ff_net_num_params", "ff_net_create", "ff_net_destroy", "ff_net_last_error",
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
     L.eigenmodes.argtypes = [vp, i32, ctypes.POINTER(EigOpts), vp, vp, vp,
                              ctypes.POINTER(EigReport)]
     L.ff_get_sizes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.ff_get_precond_layout.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.ff_export_rkpm.argtypes = [vp, vp, vp, vp, vp]
     L.ff_export_matrices.argtypes = [vp, vp, vp, vp, vp]
     L.ff_apply_operators.argtypes = [vp, vp, i32, vp, vp]
@@ -250,6 +251,13 @@ class Context:
         self._check(self.L.ff_get_sizes(self.h, ctypes.byref(n), ctypes.byref(n1),
                                         ctypes.byref(n2)))
         return n.value, n1.value, n2.value
+
+    def precond_layout(self):
+        """(row_blocks, ksteps) of the preconditioner's tensor-core tiles; (0, 0)
+        when they were not built."""
+        rb, ks = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.L.ff_get_precond_layout(self.h, ctypes.byref(rb), ctypes.byref(ks)))
+        return rb.value, ks.value
 
     def export_rkpm(self):
         n, n1, _ = self.sizes()

@@ -224,6 +224,14 @@ ff_status ff_get_sizes(const ff_ctx* c, int64_t* n, int64_t* n1, int64_t* n2) {
   return FF_OK;
 }
 
+ff_status ff_get_precond_layout(const ff_ctx* c, int64_t* row_blocks, int64_t* ksteps) {
+  if (!c) return FF_ERR_INVALID_ARG;
+  const bool built = c->stage >= 2 && c->tc_ksteps > 0;
+  if (row_blocks) *row_blocks = built ? (c->n + 15) / 16 : 0;
+  if (ksteps) *ksteps = built ? c->tc_ksteps : 0;
+  return FF_OK;
+}
+
 
 ff_status ff_export_rkpm(const ff_ctx* cc, int64_t* ptr, int32_t* idx, double* phi, double* dphi) {
   ff_ctx* c = const_cast<ff_ctx*>(cc);

@@ -6,9 +6,9 @@
 // and column).  Rows in the internal (cell) order are spatially local, so 16
 // consecutive rows share most of their columns: per block of 16 rows the H
 // entries are laid out as a dense 16 x K BF16 tile over the sorted union of the
-// block's columns (K rounded up to 16; ~20% of the tile is nonzero on the 50k
-// torus), stored in the A-fragment order of mma.m16n8k16 so that a k-step is
-// one 16-byte load per lane.  A step gathers the 16 union rows of the
+// block's columns (K rounded up to 16; on the 50k torus K averages ~450 and
+// ~35% of the tile is nonzero), stored in the A-fragment order of
+// mma.m16n8k16 so that a k-step is one 16-byte load per lane.  A step gathers the 16 union rows of the
 // direction block into shared memory once (16-byte asynchronous copies),
 // forms the B fragments with ldmatrix.trans and accumulates in FP32.
 //
@@ -164,7 +164,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint4& a, unsigned b0, unsigned b1) {
@@ -176,10 +176,11 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint4& a, unsigned
 }
 
 // One block of 4 warps per 16-row block; warp w takes the block's k-steps
-// w, w + 4, ...: the union rows of step s + 4 are copied while step s is
-// multiplied, its union columns loaded a step earlier still.  The warps'
-// partial 16 x m products are summed in shared memory and warp 0 finishes the
-// step: res -= D^-1 (H d), d' = c1 d + c2 res (BF16), x += d'.
+// w, w + 4, ...: three staging buffers per warp keep the union rows of two
+// later steps in flight while a step is multiplied (their union columns and
+// A fragments loaded earlier still).  The warps' partial 16 x m products are
+// summed through the same shared memory and each warp finishes a share of the
+// column tiles: res -= D^-1 (H d), d' = c1 d + c2 res (BF16), x += d'.
 template <int NT>
 __global__ void __launch_bounds__(128)
     k_cheb_step_tc(const int* __restrict__ kofs, const int* __restrict__ ucol,
@@ -187,17 +188,23 @@ __global__ void __launch_bounds__(128)
                    const float* __restrict__ hdiag, int n, const __nv_bfloat16* __restrict__ din,
                    __nv_bfloat16* __restrict__ dout, float* __restrict__ x,
                    float* __restrict__ res, float c1, float c2) {
-  constexpr int m = 8 * NT, PIECES = kTcRows * NT, ITERS = (PIECES + 31) / 32;
-  __shared__ __align__(16) __nv_bfloat16 stage[4][2][kTcRows * m];
-  __shared__ float red[3][32][4 * NT];
+  constexpr int m = 8 * NT, PIECES = kTcRows * NT, ITERS = (PIECES + 31) / 32, NB = 3;
+  constexpr int kStage = 4 * NB * kTcRows * m * 2, kRed = 4 * 32 * 4 * NT * 4;
+  __shared__ __align__(16) unsigned char smem[kStage > kRed ? kStage : kRed];
   const int b = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem) + w * NB * kTcRows * m;
   const int s0 = kofs[b], ns = kofs[b + 1] - s0;
   float acc[NT][4];
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  auto ucol_of = [&](int s) { return (s < ns && lane < 16) ? __ldg(ucol + (long long)(s0 + s) * 16 + lane) : 0; };
+  auto ucol_of = [&](int s) {
+    return (s < ns && lane < 16) ? __ldg(ucol + (long long)(s0 + s) * 16 + lane) : 0;
+  };
+  auto tile_of = [&](int s, const uint4& dflt) {
+    return s < ns ? __ldg(tile + (long long)(s0 + s) * 32 + lane) : dflt;
+  };
   auto stage_step = [&](int buf, int u) {  // u: lane r < 16 holds the step's union column r
-    __nv_bfloat16* dst = stage[w][buf];
+    __nv_bfloat16* dst = stage + buf * kTcRows * m;
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
       const int p = it * 32 + lane;
@@ -206,22 +213,25 @@ __global__ void __launch_bounds__(128)
       if (p < PIECES) cp_async16(dst + rr * m + pc * 8, din + (long long)row * m + pc * 8);
     }
   };
+  // Registers rotate without moves (a move would wait for its load): A[p]
+  // holds the fragments of the step multiplied in phase p, U[p] the union
+  // columns of the step staged in phase p; each is reloaded right after use
+  // for the step three phases on.
   int s = w;
-  int u_cur = ucol_of(s);
-  int u_nxt = ucol_of(s + 4);
-  if (s < ns) stage_step(0, u_cur);
+  if (s < ns) stage_step(0, ucol_of(s));
   cp_commit();
-  uint4 a_cur = s < ns ? __ldg(tile + (long long)(s0 + s) * 32 + lane) : make_uint4(0u, 0u, 0u, 0u);
-  int buf = 0;
-  for (; s < ns; s += 4) {
-    const int sn = s + 4;
-    const int u_nn = ucol_of(sn + 4);
-    if (sn < ns) stage_step(buf ^ 1, u_nxt);
+  if (s + 4 < ns) stage_step(1, ucol_of(s + 4));
+  cp_commit();
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 A[3] = {tile_of(s, zero4), tile_of(s + 4, zero4), tile_of(s + 8, zero4)};
+  int U[3] = {ucol_of(s + 8), ucol_of(s + 12), ucol_of(s + 16)};
+  auto phase = [&](const int p) {
+    if (s + 8 < ns) stage_step((p + 2) % 3, U[p]);
     cp_commit();
-    const uint4 a_nxt = sn < ns ? __ldg(tile + (long long)(s0 + sn) * 32 + lane) : a_cur;
-    cp_wait1();
+    U[p] = ucol_of(s + 20);
+    cp_wait2();
     __syncwarp();
-    const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage[w][buf]);
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage + p * kTcRows * m);
     const int mat = lane >> 3, krow = (mat & 1) * 8 + (lane & 7);
 #pragma unroll
     for (int j = 0; j + 1 < NT; j += 2) {
@@ -230,50 +240,58 @@ __global__ void __launch_bounds__(128)
       asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                    : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                    : "r"(addr));
-      mma_bf16(acc[j], a_cur, r0, r1);
-      mma_bf16(acc[j + 1], a_cur, r2, r3);
+      mma_bf16(acc[j], A[p], r0, r1);
+      mma_bf16(acc[j + 1], A[p], r2, r3);
     }
     if (NT & 1) {
       constexpr int j = NT - 1;
       unsigned r0, r1;
-      const unsigned addr = sbase + (unsigned)(((lane >> 3) & 1) * 8 * m * 2 + (lane & 7) * m * 2 + j * 16);
+      const unsigned addr =
+          sbase + (unsigned)(((lane >> 3) & 1) * 8 * m * 2 + (lane & 7) * m * 2 + j * 16);
       asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
                    : "=r"(r0), "=r"(r1)
                    : "r"(addr));
-      mma_bf16(acc[j], a_cur, r0, r1);
+      mma_bf16(acc[j], A[p], r0, r1);
     }
     __syncwarp();
-    a_cur = a_nxt;
-    u_nxt = u_nn;
-    buf ^= 1;
+    A[p] = tile_of(s + 12, zero4);
+    s += 4;
+  };
+  while (s < ns) {
+    phase(0);
+    if (s >= ns) break;
+    phase(1);
+    if (s >= ns) break;
+    phase(2);
   }
   cp_wait0();
-  if (w > 0)
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) red[w - 1][lane][4 * j + q] = acc[j][q];
-  __syncthreads();
-  if (w != 0) return;
+  __syncthreads();  // every warp is done with its staging buffers
+  float* red = reinterpret_cast<float*>(smem);  // [4][32][4 NT]
 #pragma unroll
   for (int j = 0; j < NT; ++j)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[j][q] += red[0][lane][4 * j + q] + red[1][lane][4 * j + q] + red[2][lane][4 * j + q];
+    for (int q = 0; q < 4; ++q) red[(w * 32 + lane) * 4 * NT + 4 * j + q] = acc[j][q];
+  __syncthreads();
+  // warp w finishes the column tiles j = w, w + 4, ...
   const int g = lane >> 2, t = lane & 3;
+  for (int j = w; j < NT; j += 4) {
+    float c[4];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int k = b * kTcRows + g + 8 * h;
-    if (k >= n) continue;
-    const float dinv = 1.0f / hdiag[k], hsk = hs[k];
+    for (int q = 0; q < 4; ++q)
+      c[q] = red[(0 * 32 + lane) * 4 * NT + 4 * j + q] + red[(1 * 32 + lane) * 4 * NT + 4 * j + q] +
+             red[(2 * 32 + lane) * 4 * NT + 4 * j + q] + red[(3 * 32 + lane) * 4 * NT + 4 * j + q];
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
+    for (int h = 0; h < 2; ++h) {
+      const int k = b * kTcRows + g + 8 * h;
+      if (k >= n) continue;
+      const float dinv = 1.0f / hdiag[k], hsk = hs[k];
       const long long o = (long long)k * m + 8 * j + 2 * t;
       const __nv_bfloat162 dk2 = *reinterpret_cast<const __nv_bfloat162*>(din + o);
       const float2 dk = __bfloat1622float2(dk2);
       float2 r = *reinterpret_cast<const float2*>(res + o);
       float2 xx = *reinterpret_cast<const float2*>(x + o);
-      r.x -= (acc[j][2 * h] - hsk * dk.x) * dinv;
-      r.y -= (acc[j][2 * h + 1] - hsk * dk.y) * dinv;
+      r.x -= (c[2 * h] - hsk * dk.x) * dinv;
+      r.y -= (c[2 * h + 1] - hsk * dk.y) * dinv;
       const __nv_bfloat16 q0 = __float2bfloat16(c1 * dk.x + c2 * r.x);
       const __nv_bfloat16 q1 = __float2bfloat16(c1 * dk.y + c2 * r.y);
       xx.x += __bfloat162float(q0);

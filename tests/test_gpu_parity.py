@@ -161,6 +161,32 @@ def test_eigenmodes_cube2k_fp64(fp32_phase):
     ctx.close()
 
 
+def test_preconditioner_tensor_core_tiles_and_sparse_step():
+    """The preconditioner's H products run on tensor cores from BF16 dense tiles
+    of 16-row blocks, or on the sparse FP32 values: the tile layout holds every
+    entry of H_w (each 16 x 16 tile has 256 slots; each block's union has at
+    most its entries' count of columns), and both forms solve the torus to the
+    FP64 residual bar with the same eigenvalues."""
+    from paper_2605_29318_gb300 import binding
+    c = CLOUDS["torus4k"]()
+    _, _, _, _, H, M = _oracle(c)
+    ctx = _run_build(c, "fp64")
+    ctx.assemble_hessian(*_material(c))
+    n, _, n2 = ctx.sizes()
+    rb, ks = ctx.precond_layout()
+    assert rb == (n + 15) // 16 and ks > 0
+    assert 256 * ks >= n2 and 16 * ks <= n2 + 15 * rb
+    out = {}
+    for tc in (1, 0):
+        o = binding.default_opts(tol=1e-7, precond_tc=tc)
+        ev, modes, rep, st = ctx.eigenmodes(12, o)
+        assert st == 0 and rep["max_residual"] <= 1e-7, rep
+        _check_modes(c, H, M, ev, modes, 12, "fp64", 1e-6)
+        out[tc] = ev
+    assert np.abs(out[1][1:] - out[0][1:]).max() / out[0][1] < 1e-8
+    ctx.close()
+
+
 @pytest.mark.parametrize("name", ["cube2k", "torus4k", "hetero1500"])
 def test_eigenmodes_fp32(name):
     from paper_2605_29318_gb300 import binding
