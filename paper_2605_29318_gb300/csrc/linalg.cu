@@ -324,12 +324,26 @@ __global__ void __launch_bounds__(TW * 8)
   }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int chunks, int pq, int q,
-                              double* __restrict__ out, int ldo, double alpha, int accumulate) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= pq) return;
+// Cross-chunk sums of Gram partials: a block of kRedWarps warps per 32
+// consecutive entries, warp w summing chunks w, w + kRedWarps, ... and warp 0
+// adding the warps' sums in order (a fixed order: results do not depend on
+// timing).
+constexpr int kRedWarps = 16;
+__global__ void __launch_bounds__(32 * kRedWarps)
+    k_gram_reduce(const double* __restrict__ part, int chunks, int pq, int q,
+                  double* __restrict__ out, int ldo, double alpha, int accumulate) {
+  __shared__ double red[kRedWarps][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += part[(long long)c * pq + t];
+  if (t < pq)
+#pragma unroll 4
+    for (int c = w; c < chunks; c += kRedWarps) s += part[(long long)c * pq + t];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w != 0 || t >= pq) return;
+  s = 0.0;
+  for (int q2 = 0; q2 < kRedWarps; ++q2) s += red[q2][lane];
   double* o = out + (long long)(t / q) * ldo + t % q;
   *o = accumulate ? *o + alpha * s : alpha * s;
 }
@@ -604,18 +618,29 @@ __global__ void __launch_bounds__(256)
 }
 
 // out = alpha * (sum over chunks) (+ out), per tile entry; tiles marked
-// diag_only write their diagonal alone
+// diag_only write their diagonal alone.  Chunks split over the block's warps
+// as in k_gram_reduce.
 template <int TW>
-__global__ void k_gram_tiles_reduce(GramTiles tiles, int chunks, int ldo, double alpha,
-                                    int accumulate, const double* __restrict__ part) {
+__global__ void __launch_bounds__(32 * kRedWarps)
+    k_gram_tiles_reduce(GramTiles tiles, int chunks, int ldo, double alpha, int accumulate,
+                        const double* __restrict__ part) {
+  __shared__ double red[kRedWarps][33];
   const int t = blockIdx.y;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= TW * TW) return;
-  const int i = e / TW, j = e % TW;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
   const GramTile tl = tiles.t[t];
-  if (i >= tl.pi || j >= tl.qj || (tl.diag_only && i != j)) return;
+  const int i = e / TW, j = e % TW;
+  const bool want = e < TW * TW && i < tl.pi && j < tl.qj && !(tl.diag_only && i != j);
   double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += part[((long long)c * tiles.count + t) * (TW * TW) + e];
+  if (want)
+#pragma unroll 4
+    for (int c = w; c < chunks; c += kRedWarps)
+      s += part[((long long)c * tiles.count + t) * (TW * TW) + e];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w != 0 || !want) return;
+  s = 0.0;
+  for (int q = 0; q < kRedWarps; ++q) s += red[q][lane];
   double* o = tl.out + (long long)i * ldo + j;
   *o = accumulate ? *o + alpha * s : alpha * s;
 }
@@ -1093,18 +1118,18 @@ void launch_tiles(cudaStream_t st, const GramTiles& g, int TW, int lda, int ldb,
   chunks = (n + rpc - 1) / rpc;
   double* pp = reinterpret_cast<double*>(part.ensure(sizeof(double) * chunks * g.count * TW * TW));
   dim3 grid((unsigned)chunks, (unsigned)g.count);
-  dim3 rgrid((unsigned)((TW * TW + 255) / 256), (unsigned)g.count);
+  dim3 rgrid((unsigned)((TW * TW + 31) / 32), (unsigned)g.count);
   if (TW == 40) {
     (k_gram_tiles<T, 40><<<grid, 200, 0, st>>>(g, lda, ldb, n, rpc, pp), ::ff::note_launch());
     FF_LAUNCH_CHECK();
-    (k_gram_tiles_reduce<40><<<rgrid, 256, 0, st>>>(g, (int)chunks, ldo, alpha, accumulate ? 1 : 0,
-                                                   pp),
+    (k_gram_tiles_reduce<40><<<rgrid, 32 * kRedWarps, 0, st>>>(g, (int)chunks, ldo, alpha,
+                                                                accumulate ? 1 : 0, pp),
      ::ff::note_launch());
   } else {
     (k_gram_tiles<T, 32><<<grid, 256, 0, st>>>(g, lda, ldb, n, rpc, pp), ::ff::note_launch());
     FF_LAUNCH_CHECK();
-    (k_gram_tiles_reduce<32><<<rgrid, 256, 0, st>>>(g, (int)chunks, ldo, alpha, accumulate ? 1 : 0,
-                                                   pp),
+    (k_gram_tiles_reduce<32><<<rgrid, 32 * kRedWarps, 0, st>>>(g, (int)chunks, ldo, alpha,
+                                                                accumulate ? 1 : 0, pp),
      ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
@@ -1133,8 +1158,8 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
     (k_gram_row<T><<<(unsigned)chunks, 256, 0, st>>>(A, lda, B, ldb, q, n, rpc, pp),
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
-    (k_gram_reduce<<<(q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, q, q, out, ldo < 0 ? q : ldo,
-                                                  alpha, accumulate ? 1 : 0),
+    (k_gram_reduce<<<(q + 31) / 32, 32 * kRedWarps, 0, st>>>(
+         pp, (int)chunks, q, q, out, ldo < 0 ? q : ldo, alpha, accumulate ? 1 : 0),
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
     return;
@@ -1155,9 +1180,9 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
     (k_gram_partial<T, 32><<<grid, 256, 0, st>>>(A, lda, p, B, ldb, q, n, rpc, pp),
      ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  (k_gram_reduce<<<(p * q + 255) / 256, 256, 0, st>>>(pp, (int)chunks, p * q, q, out,
-                                                    ldo < 0 ? q : ldo, alpha,
-                                                    accumulate ? 1 : 0), ::ff::note_launch());
+  (k_gram_reduce<<<(p * q + 31) / 32, 32 * kRedWarps, 0, st>>>(
+       pp, (int)chunks, p * q, q, out, ldo < 0 ? q : ldo, alpha, accumulate ? 1 : 0),
+   ::ff::note_launch());
   FF_LAUNCH_CHECK();
 }
 
