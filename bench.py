@@ -179,7 +179,8 @@ def run_ours(args):
     a = torch.from_numpy(c.a).to(dev)
     ctx = binding.Context(local, args.prec)
     opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
-                                fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64)
+                                fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64,
+                                precond_tc=args.precond_tc)
     from paper_2605_29318_gb300 import train_warmstart
     net = binding.Net(local)
     net.set_params(train_warmstart.load_weights())
@@ -293,6 +294,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.prec, "tol": args.tol,
                    "cheb_degree": args.cheb, "cheb_degree_fp64": args.cheb_fp64,
+                   "precond_tc": args.precond_tc,
                    "n": n, "n1": n1, "n2": n2,
                    "l2": "flushed by a 256 MB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -343,6 +345,8 @@ def main():
     ap.add_argument("--fp32-phase", type=int, default=1, choices=[0, 1],
                     help="FP64 contexts: iterate in FP32 first, then finish in FP64")
     ap.add_argument("--max-iter", type=int, default=500)
+    ap.add_argument("--precond-tc", type=int, default=1, choices=[0, 1],
+                    help="preconditioner steps on tensor cores (BF16 tiles) or on CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -28,6 +28,7 @@ namespace ff {
 namespace {
 
 constexpr int kTcRows = 16;            // rows per block (the M of the MMA)
+constexpr int kWB = 4;                 // warps per block of the step kernel
 constexpr int kTcMaxWords = 8192;      // bitmap words: column spans up to 262144
 constexpr unsigned kFullMask = 0xffffffffu;
 
@@ -175,21 +176,21 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint4& a, unsigned
       : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
-// One block of 4 warps per 16-row block; warp w takes the block's k-steps
-// w, w + 4, ...: three staging buffers per warp keep the union rows of two
+// One block of kWB warps per 16-row block; warp w takes the block's k-steps
+// w, w + kWB, ...: three staging buffers per warp keep the union rows of two
 // later steps in flight while a step is multiplied (their union columns and
 // A fragments loaded earlier still).  The warps' partial 16 x m products are
 // summed through the same shared memory and each warp finishes a share of the
 // column tiles: res -= D^-1 (H d), d' = c1 d + c2 res (BF16), x += d'.
 template <int NT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32 * kWB)
     k_cheb_step_tc(const int* __restrict__ kofs, const int* __restrict__ ucol,
                    const uint4* __restrict__ tile, const float* __restrict__ hs,
                    const float* __restrict__ hdiag, int n, const __nv_bfloat16* __restrict__ din,
                    __nv_bfloat16* __restrict__ dout, float* __restrict__ x,
                    float* __restrict__ res, float c1, float c2) {
   constexpr int m = 8 * NT, PIECES = kTcRows * NT, ITERS = (PIECES + 31) / 32, NB = 3;
-  constexpr int kStage = 4 * NB * kTcRows * m * 2, kRed = 4 * 32 * 4 * NT * 4;
+  constexpr int kStage = kWB * NB * kTcRows * m * 2, kRed = kWB * 32 * 4 * NT * 4;
   __shared__ __align__(16) unsigned char smem[kStage > kRed ? kStage : kRed];
   const int b = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem) + w * NB * kTcRows * m;
@@ -220,15 +221,15 @@ __global__ void __launch_bounds__(128)
   int s = w;
   if (s < ns) stage_step(0, ucol_of(s));
   cp_commit();
-  if (s + 4 < ns) stage_step(1, ucol_of(s + 4));
+  if (s + kWB < ns) stage_step(1, ucol_of(s + kWB));
   cp_commit();
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  uint4 A[3] = {tile_of(s, zero4), tile_of(s + 4, zero4), tile_of(s + 8, zero4)};
-  int U[3] = {ucol_of(s + 8), ucol_of(s + 12), ucol_of(s + 16)};
+  uint4 A[3] = {tile_of(s, zero4), tile_of(s + kWB, zero4), tile_of(s + 2 * kWB, zero4)};
+  int U[3] = {ucol_of(s + 2 * kWB), ucol_of(s + 3 * kWB), ucol_of(s + 4 * kWB)};
   auto phase = [&](const int p) {
-    if (s + 8 < ns) stage_step((p + 2) % 3, U[p]);
+    if (s + 2 * kWB < ns) stage_step((p + 2) % 3, U[p]);
     cp_commit();
-    U[p] = ucol_of(s + 20);
+    U[p] = ucol_of(s + 5 * kWB);
     cp_wait2();
     __syncwarp();
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(stage + p * kTcRows * m);
@@ -254,8 +255,8 @@ __global__ void __launch_bounds__(128)
       mma_bf16(acc[j], A[p], r0, r1);
     }
     __syncwarp();
-    A[p] = tile_of(s + 12, zero4);
-    s += 4;
+    A[p] = tile_of(s + 3 * kWB, zero4);
+    s += kWB;
   };
   while (s < ns) {
     phase(0);
@@ -266,20 +267,22 @@ __global__ void __launch_bounds__(128)
   }
   cp_wait0();
   __syncthreads();  // every warp is done with its staging buffers
-  float* red = reinterpret_cast<float*>(smem);  // [4][32][4 NT]
+  float* red = reinterpret_cast<float*>(smem);  // [kWB][32][4 NT]
 #pragma unroll
   for (int j = 0; j < NT; ++j)
 #pragma unroll
     for (int q = 0; q < 4; ++q) red[(w * 32 + lane) * 4 * NT + 4 * j + q] = acc[j][q];
   __syncthreads();
-  // warp w finishes the column tiles j = w, w + 4, ...
+  // warp w finishes the column tiles j = w, w + kWB, ...
   const int g = lane >> 2, t = lane & 3;
-  for (int j = w; j < NT; j += 4) {
+  for (int j = w; j < NT; j += kWB) {
     float c[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      c[q] = red[(0 * 32 + lane) * 4 * NT + 4 * j + q] + red[(1 * 32 + lane) * 4 * NT + 4 * j + q] +
-             red[(2 * 32 + lane) * 4 * NT + 4 * j + q] + red[(3 * 32 + lane) * 4 * NT + 4 * j + q];
+    for (int q = 0; q < 4; ++q) {
+      float t = 0.f;
+      for (int v = 0; v < kWB; ++v) t += red[(v * 32 + lane) * 4 * NT + 4 * j + q];
+      c[q] = t;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int k = b * kTcRows + g + 8 * h;
@@ -362,7 +365,7 @@ bool cheb_step_tc(cudaStream_t st, const ff_ctx* c, int m, const void* din, void
   const auto* bi = static_cast<const __nv_bfloat16*>(din);
   auto* bo = static_cast<__nv_bfloat16*>(dout);
 #define FF_TC(NT)                                                                              \
-  (k_cheb_step_tc<NT><<<nblk, 128, 0, st>>>(c->tc_kofs.as<int>(), c->tc_ucol.as<int>(),        \
+  (k_cheb_step_tc<NT><<<nblk, 32 * kWB, 0, st>>>(c->tc_kofs.as<int>(), c->tc_ucol.as<int>(),        \
                                              reinterpret_cast<const uint4*>(c->tc_tile.p),     \
                                              c->tc_hs.as<float>(), c->hdiag_f32.as<float>(),   \
                                              (int)c->n, bi, bo, x, res, c1, c2),               \
