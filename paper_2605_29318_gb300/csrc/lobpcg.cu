@@ -200,19 +200,20 @@ __global__ void k_colstats_final(const double* __restrict__ part, int blocks, in
   }
 }
 
-// Chebyshev start: b = active * (HX - MX theta) / diag(H); res = b; d = b / theta_c; x = d
+// Chebyshev start: b = active * (HX - MX theta) / diag(H); res = b; d = b / theta_c; x = d.
+// The iteration's arrays are n x mc (mc >= m): columns m..mc-1 are zero.
 template <class T>
 __global__ void k_cheb_init(const T* __restrict__ HX, const T* __restrict__ MX, int ld,
                             const double* __restrict__ theta, const int* __restrict__ active,
-                            const float* __restrict__ hdiag, long long n, int m,
+                            const float* __restrict__ hdiag, long long n, int m, int mc,
                             float* __restrict__ res, float* __restrict__ d, float* __restrict__ x,
                             float inv_tc, __nv_bfloat16* __restrict__ d16) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * m) return;
-  long long r = t / m;
-  int c = (int)(t % m);
+  if (t >= n * mc) return;
+  long long r = t / mc;
+  int c = (int)(t % mc);
   float b = 0.f;
-  if (active[c]) {
+  if (c < m && active[c]) {
     if constexpr (std::is_same_v<T, dfloat>) {  // the residual in double-float
       dfloat rr = HX[r * ld + c];
       df_mac(rr, dfloat(-theta[c]), MX[r * ld + c]);
@@ -233,14 +234,15 @@ __global__ void k_cheb_init(const T* __restrict__ HX, const T* __restrict__ MX, 
   }
 }
 
+// W (n x m of a panel) = x (n x m of a dense array with row stride ldx)
 template <class T>
-__global__ void k_cast_block(const float* __restrict__ x, long long n, int m, T* __restrict__ W,
-                             int ld) {
+__global__ void k_cast_block(const float* __restrict__ x, int ldx, long long n, int m,
+                             T* __restrict__ W, int ld) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * m) return;
   long long r = t / m;
   int c = (int)(t % m);
-  W[r * ld + c] = (T)x[t];
+  W[r * ld + c] = (T)x[r * ldx + c];
 }
 
 __global__ void k_round_block(const double* __restrict__ x, float* __restrict__ y, long long m) {
@@ -270,6 +272,8 @@ struct Solver {
   const T* aval;  // interleaved (H, M) of this phase's precision
   long long n;
   int nb, kw, ld;
+  int mc;         // columns of the Chebyshev iteration's arrays (nb, or nb
+                  // rounded up to 8 for the BF16 / tensor-core steps)
   bool fp64;      // FP64 blocks
   bool rr64;      // FP64 Rayleigh-Ritz
   T *S[2], *HS[2], *MS[2];
@@ -293,12 +297,13 @@ struct Solver {
     }
     c0 = reinterpret_cast<T*>(c->ws[6].ensure(sizeof(T) * n));
     Mc0 = reinterpret_cast<T*>(c->ws[7].ensure(sizeof(T) * n));
-    cres = reinterpret_cast<float*>(c->ws[8].ensure(sizeof(float) * n * std::max(nb, 4)));
-    cd0 = reinterpret_cast<float*>(c->ws[9].ensure(sizeof(float) * n * std::max(nb, 4)));
-    cd1 = reinterpret_cast<float*>(c->ws[10].ensure(sizeof(float) * n * std::max(nb, 4)));
-    cb0 = reinterpret_cast<__nv_bfloat16*>(c->ws[24].ensure(sizeof(__nv_bfloat16) * n * nb + 16));
-    cb1 = reinterpret_cast<__nv_bfloat16*>(c->ws[25].ensure(sizeof(__nv_bfloat16) * n * nb + 16));
-    cx = reinterpret_cast<float*>(c->ws[11].ensure(sizeof(float) * n * std::max(nb, 4)));
+    const int mw = std::max({nb, mc, 4});
+    cres = reinterpret_cast<float*>(c->ws[8].ensure(sizeof(float) * n * mw));
+    cd0 = reinterpret_cast<float*>(c->ws[9].ensure(sizeof(float) * n * mw));
+    cd1 = reinterpret_cast<float*>(c->ws[10].ensure(sizeof(float) * n * mw));
+    cb0 = reinterpret_cast<__nv_bfloat16*>(c->ws[24].ensure(sizeof(__nv_bfloat16) * n * mw + 16));
+    cb1 = reinterpret_cast<__nv_bfloat16*>(c->ws[25].ensure(sizeof(__nv_bfloat16) * n * mw + 16));
+    cx = reinterpret_cast<float*>(c->ws[11].ensure(sizeof(float) * n * mw));
     const int ns = 3 * nb;
     Ag = reinterpret_cast<double*>(c->ws[12].ensure(sizeof(double) * ns * ns));
     Bg = reinterpret_cast<double*>(c->ws[13].ensure(sizeof(double) * ns * ns));
@@ -370,6 +375,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   s.nb = std::min<long long>(std::min(s.nb, 340), (s.n - 1) / 3);
   FF_REQUIRE(s.nb >= s.kw && s.nb >= 1, FF_ERR_INVALID_ARG,
              "too few particles for the requested number of modes");
+  s.mc = (s.nb + 7) / 8 * 8 <= 256 ? (s.nb + 7) / 8 * 8 : s.nb;
   s.alloc();
   cudaStream_t st = s.st;
   const long long n = s.n;
@@ -425,7 +431,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   // ---- starting block
   int warm = 0;
   if (ph.X0_int) {
-    (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(ph.X0_int, n, nb, s.S[0], ld),
+    (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(ph.X0_int, nb, n, nb, s.S[0], ld),
      ::ff::note_launch());
   } else {
     (k_random_block<T><<<blocks(n * nb), TB, 0, st>>>(s.S[0], ld, n, nb, o.seed,
@@ -556,11 +562,14 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
 
     // W = T R  (FP32 Chebyshev polynomial in D^-1 H, or Jacobi when deg <= 1)
     T* W = s.S[cur] + nb;
-    // BF16 directions halve the bytes each preconditioner step gathers
-    const bool b16 = deg > 1 && nb % 8 == 0;
-    (k_cheb_init<T><<<blocks(n * nb), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d, s.active_d,
-                                                  c->hdiag_f32.as<float>(), n, nb, s.cres, s.cd0,
-                                                  s.cx, deg > 1 ? (float)(1.0 / th_c) : 1.f,
+    // BF16 directions halve the bytes each preconditioner step gathers; their
+    // steps take widths in multiples of 8, the padding columns stay zero
+    const bool b16 = deg > 1 && s.mc % 8 == 0;
+    const int mc = s.mc;
+    (k_cheb_init<T><<<blocks(n * mc), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d,
+                                                  s.active_d, c->hdiag_f32.as<float>(), n, nb, mc,
+                                                  s.cres, s.cd0, s.cx,
+                                                  deg > 1 ? (float)(1.0 / th_c) : 1.f,
                                                   b16 ? s.cb0 : nullptr), ::ff::note_launch());
     FF_LAUNCH_CHECK();
     if (deg > 1) {
@@ -575,13 +584,13 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
         const float c1 = (float)(rn * rho), c2 = (float)(2.0 * rn / delta);
         // the tensor-core step when its tiles exist, else the CUDA-core ones
         const bool tc =
-            b16 && o.precond_tc && cheb_step_tc(st, c, nb, bin, bout, s.cx, s.cres, c1, c2);
+            b16 && o.precond_tc && cheb_step_tc(st, c, mc, bin, bout, s.cx, s.cres, c1, c2);
         if (!tc && b16) {
           cheb_step_b16(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
-                        c->hdiag_f32.as<float>(), n, nb, bin, bout, s.cx, s.cres, c1, c2);
+                        c->hdiag_f32.as<float>(), n, mc, bin, bout, s.cx, s.cres, c1, c2);
         } else if (!tc) {
           cheb_step(st, c->a_ptr.as<long long>(), c->a_col.as<int>(), c->h_f32.as<float>(),
-                    c->hdiag_f32.as<float>(), n, nb, nb, din, dout, s.cx, s.cres, c1, c2);
+                    c->hdiag_f32.as<float>(), n, mc, mc, din, dout, s.cx, s.cres, c1, c2);
         }
         ++s.spmv_calls;
         rho = rn;
@@ -589,7 +598,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
         std::swap(bin, bout);
       }
     }
-    (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, n, nb, W, ld), ::ff::note_launch());
+    (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, mc, n, nb, W, ld), ::ff::note_launch());
     FF_LAUNCH_CHECK();
     // M-project W against X, P and c0 (with the stored M X, M P, M c0)
     s.deflate(W, nb);

@@ -178,6 +178,8 @@ def test_preconditioner_tensor_core_tiles_and_sparse_step():
     assert 256 * ks >= n2 and 16 * ks <= n2 + 15 * rb
     out = {}
     for tc in (1, 0):
+        # k = 12: a 20-column block, the preconditioner's arrays padded to 24
+        # columns (three column tiles of the MMA, an odd count)
         o = binding.default_opts(tol=1e-7, precond_tc=tc)
         ev, modes, rep, st = ctx.eigenmodes(12, o)
         assert st == 0 and rep["max_residual"] <= 1e-7, rep
