@@ -138,13 +138,14 @@ __device__ __forceinline__ void vstore(T* p, const T (&v)[Vec16<T>::n]) {
   *reinterpret_cast<typename Vec16<T>::type*>(p) = q;
 }
 
-template <class T>
+// GT > 0 fixes the group width G at compile time (the solver's block widths).
+template <class T, int GT = 0>
 __global__ void k_spmm_hm_vec(const long long* __restrict__ ptr, const int* __restrict__ col,
                               const T* __restrict__ val, long long n, const T* __restrict__ X,
                               int ldx, T* __restrict__ YH, T* __restrict__ YM, int ldy, int m) {
   constexpr int VEC = Vec16<T>::n;
   const int lane = threadIdx.x & 31;
-  const int G = m / VEC, P = 32 / G;
+  const int G = GT > 0 ? GT : m / VEC, P = 32 / G;
   const int g = lane / G, cv = (lane % G) * VEC;
   const bool act = g < P;
   const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -157,16 +158,22 @@ __global__ void k_spmm_hm_vec(const long long* __restrict__ ptr, const int* __re
     else
 #pragma unroll
       for (int u = 0; u < VEC; ++u) xk[u] = T(0);
-    long long e0 = act ? s + g : e;
-    for (; e0 + 3 * P < e; e0 += 4 * P) {
+    // offsets within the row are 32-bit; (H, M) of a nonzero is one 2-vector load
+    using T2 = typename std::conditional<std::is_same_v<T, float>, float2, double2>::type;
+    const int cnt = (int)(e - s);
+    const int* cr = col + s;
+    const T2* vr = reinterpret_cast<const T2*>(val) + s;
+    int e0 = act ? g : cnt;
+    for (; e0 + 3 * P < cnt; e0 += 4 * P) {
       int l[4];
       T h[4], mm[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const long long t = e0 + q * P;
-        l[q] = col[t];
-        h[q] = val[2 * t];
-        mm[q] = val[2 * t + 1];
+        const int t = e0 + q * P;
+        l[q] = __ldg(cr + t);
+        const T2 hm = vr[t];
+        h[q] = hm.x;
+        mm[q] = hm.y;
       }
       T xl[4][VEC];
 #pragma unroll
@@ -179,9 +186,10 @@ __global__ void k_spmm_hm_vec(const long long* __restrict__ ptr, const int* __re
           am[u] += mm[q] * xl[q][u];
         }
     }
-    for (; e0 < e; e0 += P) {
-      const int l = col[e0];
-      const T h = val[2 * e0], mm = val[2 * e0 + 1];
+    for (; e0 < cnt; e0 += P) {
+      const int l = __ldg(cr + e0);
+      const T2 hm = vr[e0];
+      const T h = hm.x, mm = hm.y;
       T xl[VEC];
       vload(X + (long long)l * ldx + cv, xl);
 #pragma unroll
@@ -929,7 +937,11 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
         return;
       }
     }
-    if (vec_ok)
+    if (vec_ok && std::is_same_v<T, float> && m == 40)  // the solver's 40-column blocks
+      (k_spmm_hm_vec<T, 10><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM,
+                                                              ldy, m),
+       ::ff::note_launch());
+    else if (vec_ok)
       (k_spmm_hm_vec<T><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM, ldy, m),
        ::ff::note_launch());
     else

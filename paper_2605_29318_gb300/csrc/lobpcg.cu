@@ -100,16 +100,36 @@ __global__ void k_colstats_partial(const T* __restrict__ X, const T* __restrict_
   for (int c0 = 0; c0 < m; c0 += 32) {
     const int col = c0 + lane;
     double a[5] = {0, 0, 0, 0, 0};
-    if (col < m)
-      for (long long r = r0 + w; r < r1; r += 8) {
-        const double x = (double)X[r * ld + col], h = (double)HX[r * ld + col],
-                     mm = (double)MX[r * ld + col];
-        a[0] += x * h;
-        a[1] += x * mm;
-        a[2] += h * h;
-        a[3] += h * mm;
-        a[4] += mm * mm;
-      }
+    if constexpr (std::is_same_v<T, float>) {
+      // FP32 blocks: each product exact as a double-float (FMA TwoProduct),
+      // summed in double-float -- FP64-grade sums without FP64 arithmetic
+      dfloat s5[5] = {dfloat(0), dfloat(0), dfloat(0), dfloat(0), dfloat(0)};
+      auto tp = [](float u, float v) {
+        const float p = __fmul_rn(u, v);
+        return dfloat(p, __fmaf_rn(u, v, -p));
+      };
+      if (col < m)
+        for (long long r = r0 + w; r < r1; r += 8) {
+          const float x = X[r * ld + col], h = HX[r * ld + col], mm = MX[r * ld + col];
+          df_acc(s5[0], tp(x, h));
+          df_acc(s5[1], tp(x, mm));
+          df_acc(s5[2], tp(h, h));
+          df_acc(s5[3], tp(h, mm));
+          df_acc(s5[4], tp(mm, mm));
+        }
+      for (int q = 0; q < 5; ++q) a[q] = (double)s5[q];
+    } else {
+      if (col < m)
+        for (long long r = r0 + w; r < r1; r += 8) {
+          const double x = (double)X[r * ld + col], h = (double)HX[r * ld + col],
+                       mm = (double)MX[r * ld + col];
+          a[0] += x * h;
+          a[1] += x * mm;
+          a[2] += h * h;
+          a[3] += h * mm;
+          a[4] += mm * mm;
+        }
+    }
     for (int q = 0; q < 5; ++q) sred[w][q][lane] = a[q];
     __syncthreads();
     if (w == 0 && col < m)
@@ -122,35 +142,40 @@ __global__ void k_colstats_partial(const T* __restrict__ X, const T* __restrict_
   }
 }
 
-// The same statistics for double-float blocks: x.Hx and x.Mx in double-float
-// (slots 0, 1), and the residual norm taken directly, ||Hx - sigma Mx||^2 with
-// sigma the Ritz values of the last Rayleigh-Ritz step (slot 2; the residual
-// vector in double-float, its squares summed in FP32 within a thread), and
-// ||Mx||^2 (slot 4).  Expanding the norm would need the three sums to ~1e-13
-// relative for a 1e-6 residual, beyond double-float sums over n rows; sigma
-// differs from the Rayleigh quotient of the stored block by ~1e-9 relative,
-// which moves the residual norm by as much.
-__global__ void k_colstats_partial_df(const dfloat* __restrict__ X, const dfloat* __restrict__ HX,
-                                      const dfloat* __restrict__ MX, int ld, long long n, int m,
-                                      long long rows_per_block, const double* __restrict__ sigma,
-                                      double* __restrict__ part) {
+// The same statistics for double-float blocks with the residual norm taken
+// directly: x.Hx and x.Mx in double-float (slots 0, 1), ||Hx - sigma Mx||^2
+// with sigma the Ritz values of the last (FP64) Rayleigh-Ritz step (slot 2;
+// the residual vector in double-float, its squares summed in FP32 within a
+// thread) and ||Mx||^2 (slot 4).  Expanding the norm would need the three sums
+// to ~1e-13 relative for a 1e-6 residual, beyond double-float sums over n
+// rows; sigma differs from the Rayleigh quotient of the stored block by ~1e-9
+// relative, which moves the residual norm by as much.  (FP32 Ritz values are
+// far less accurate for the small modes, so FP32 blocks keep the expanded
+// form, with exact products and double-float sums.)
+template <class T>
+__global__ void k_colstats_partial_direct(const T* __restrict__ X, const T* __restrict__ HX,
+                                          const T* __restrict__ MX, int ld, long long n, int m,
+                                          long long rows_per_block,
+                                          const double* __restrict__ sigma,
+                                          double* __restrict__ part) {
   __shared__ double sred[8][5][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long r0 = (long long)blockIdx.x * rows_per_block;
   const long long r1 = min(n, r0 + rows_per_block);
   for (int c0 = 0; c0 < m; c0 += 32) {
     const int col = c0 + lane;
-    dfloat xh(0), xm(0);
+    T xh(0), xm(0);
     float rr = 0.f, mm2 = 0.f;
     if (col < m) {
-      const dfloat ns(-sigma[col]);
+      const T ns(-sigma[col]);
       for (long long r = r0 + w; r < r1; r += 8) {
-        const dfloat x = X[r * ld + col], h = HX[r * ld + col], mm = MX[r * ld + col];
+        const T x = X[r * ld + col], h = HX[r * ld + col], mm = MX[r * ld + col];
         df_mac(xh, x, h);
         df_mac(xm, x, mm);
         dfloat res = h;
         df_mac(res, ns, mm);
-        const float rf = (float)df_norm(res), mf = (float)mm;
+        const float rf = (float)df_norm(res);
+        const float mf = (float)mm;
         rr = fmaf(rf, rf, rr);
         mm2 = fmaf(mf, mf, mm2);
       }
@@ -218,6 +243,8 @@ __global__ void k_cheb_init(const T* __restrict__ HX, const T* __restrict__ MX, 
       dfloat rr = HX[r * ld + c];
       df_mac(rr, dfloat(-theta[c]), MX[r * ld + c]);
       b = (float)df_norm(rr) / hdiag[r];
+    } else if constexpr (std::is_same_v<T, float>) {  // FP32 blocks: in FP32
+      b = fmaf(-(float)theta[c], MX[r * ld + c], HX[r * ld + c]) / hdiag[r];
     } else {
       double rr = (double)HX[r * ld + c] - theta[c] * (double)MX[r * ld + c];
       b = (float)(rr / (double)hdiag[r]);
@@ -496,16 +523,17 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   std::vector<double> best_res;
   for (;; ++it) {
     // Rayleigh quotients and residual norms of the current X (products recomputed)
-    if constexpr (std::is_same_v<T, dfloat>)
-      (k_colstats_partial_df<<<cs_blocks, 256, 0, st>>>(s.S[cur], s.HS[cur], s.MS[cur], ld, n, nb,
-                                                        rpb, s.theta_d, cs_part),
+    constexpr bool direct = std::is_same_v<T, dfloat>;
+    if constexpr (direct)
+      (k_colstats_partial_direct<T><<<cs_blocks, 256, 0, st>>>(
+           s.S[cur], s.HS[cur], s.MS[cur], ld, n, nb, rpb, s.theta_d, cs_part),
        ::ff::note_launch());
     else
       (k_colstats_partial<T><<<cs_blocks, 256, 0, st>>>(s.S[cur], s.HS[cur], s.MS[cur], ld, n,
                                                        nb, rpb, cs_part),
        ::ff::note_launch());
     (k_colstats_final<<<nb, 128, 0, st>>>(cs_part, cs_blocks, nb, s.theta_d, s.norms_d,
-                                          std::is_same_v<T, dfloat> ? 1 : 0),
+                                          direct ? 1 : 0),
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
     FF_CUDA(cudaMemcpyAsync(s.h_pin, s.norms_d, sizeof(double) * 3 * nb, cudaMemcpyDeviceToHost,
