@@ -180,7 +180,7 @@ def run_ours(args):
     ctx = binding.Context(local, args.prec)
     opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
                                 fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64,
-                                precond_tc=args.precond_tc)
+                                precond_tc=args.precond_tc, fp32_tol=args.fp32_tol)
     from paper_2605_29318_gb300 import train_warmstart
     net = binding.Net(local)
     net.set_params(train_warmstart.load_weights())
@@ -289,12 +289,12 @@ def run_ours(args):
         "metric": METRIC, "value": round(ms / 1000.0, 5), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": (("f32+bf16, then f32x2 double-float; f64 Rayleigh-Ritz" if args.fp32_phase
+        "dtype": (("f32+bf16, then f32x2 double-float" if args.fp32_phase
                    else "f64") if args.prec == "fp64" else "f32+bf16"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": args.prec, "tol": args.tol,
                    "cheb_degree": args.cheb, "cheb_degree_fp64": args.cheb_fp64,
-                   "precond_tc": args.precond_tc,
+                   "precond_tc": args.precond_tc, "fp32_tol": args.fp32_tol,
                    "n": n, "n1": n1, "n2": n2,
                    "l2": "flushed by a 256 MB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -345,6 +345,8 @@ def main():
     ap.add_argument("--fp32-phase", type=int, default=1, choices=[0, 1],
                     help="FP64 contexts: iterate in FP32 first, then finish in FP64")
     ap.add_argument("--max-iter", type=int, default=500)
+    ap.add_argument("--fp32-tol", type=float, default=1e-4,
+                    help="residual at which the FP32 phase hands over")
     ap.add_argument("--precond-tc", type=int, default=1, choices=[0, 1],
                     help="preconditioner steps on tensor cores (BF16 tiles) or on CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -37,6 +37,8 @@
 // accuracy.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "linalg.cuh"
 
 namespace ff {
@@ -58,10 +60,20 @@ template <>
 struct Prec<float> {
   static constexpr float eps = 6e-8f, tiny = 1e-30f, drop = 1e-6f, hi = 0x1p+60f, lo = 0x1p-60f;
 };
+// double-float: ~2^-47 unit roundoff at the FP32 exponent range
+template <>
+struct Prec<dfloat> {
+  static constexpr dfloat eps = dfloat(1.5e-14), tiny = dfloat(1e-30), drop = dfloat(1e-12),
+                          hi = dfloat(0x1p+60), lo = dfloat(0x1p-60);
+};
 __device__ __forceinline__ int ilogb_r(double x) { return ilogb(x); }
 __device__ __forceinline__ int ilogb_r(float x) { return ilogbf(x); }
 __device__ __forceinline__ double scalbn_r(double x, int e) { return scalbn(x, e); }
 __device__ __forceinline__ float scalbn_r(float x, int e) { return scalbnf(x, e); }
+__device__ __forceinline__ int ilogb_r(dfloat x) { return ilogbf(x.h); }
+__device__ __forceinline__ dfloat scalbn_r(dfloat x, int e) {
+  return dfloat(scalbnf(x.h, e), scalbnf(x.l, e));
+}
 
 // global workspace layout (working precision R)
 template <class R>
@@ -539,6 +551,27 @@ __device__ int sturm_bits(const R* d, const R* e2, int n, R x) {
   return c;
 }
 
+// Double-float: the sign, zero and exponent tests on the (normalised) head.
+template <>
+__device__ int sturm_bits<dfloat>(const dfloat* d, const dfloat* e2, int n, dfloat x) {
+  dfloat pm(1.0f), p = d[0] - x;
+  if (p.h == 0.f) p = -Prec<dfloat>::tiny;
+  int c = p.h < 0.f;
+  for (int i = 1; i < n; ++i) {
+    dfloat q = df_add(df_mul(d[i] - x, p), -df_mul(e2[i - 1], pm));
+    if (q.h == 0.f) q = p.h < 0.f ? Prec<dfloat>::tiny : -Prec<dfloat>::tiny;
+    c += (q.h < 0.f) != (p.h < 0.f);
+    pm = p;
+    p = q;
+    const int ex = ilogbf(p.h);
+    if (ex > 60 || ex < -60) {
+      p = scalbn_r(p, -ex);
+      pm = scalbn_r(pm, -ex);
+    }
+  }
+  return c;
+}
+
 // One block of kEW warps per eigenvalue s: multisection with 32 kEW probes a
 // round, first on FP32 copies of the tridiagonal (cheap bracketing to FP32
 // resolution), then in the working precision from the FP32 bracket widened by
@@ -634,7 +667,7 @@ __global__ void __launch_bounds__(32 * kEW)
   multisection<R>(d, e2, n, s, a, b, 64, R(4.0) * Prec<R>::eps, sfirst);
   if (tid == 0) {
     w.lam[s] = R(0.5) * (a + b);
-    theta[s] = R(0.5) * (a + b);
+    theta[s] = (double)(R(0.5) * (a + b));
   }
 }
 
@@ -1029,10 +1062,16 @@ void rayleigh_ritz(cudaStream_t st, const double* A, const double* B, RRDims d, 
   ProfScope ps(kProfRR);
   FF_REQUIRE(d.ns <= 1024 && d.no <= 1024 && d.nb <= 512 && d.o0 + d.no <= d.ns,
              FF_ERR_INVALID_ARG, "Rayleigh-Ritz basis too large");
-  if (fp64)
-    rr_run<double, T>(st, A, B, d, YZ, theta, dropped, work);
-  else
+  if (fp64) {
+    // double-float blocks: the dense step in double-float too (GB300's FP64
+    // rate holds the FP64 step to a fraction of the FP32 pipes)
+    if constexpr (std::is_same_v<T, dfloat>)
+      rr_run<dfloat, T>(st, A, B, d, YZ, theta, dropped, work);
+    else
+      rr_run<double, T>(st, A, B, d, YZ, theta, dropped, work);
+  } else {
     rr_run<float, T>(st, A, B, d, YZ, theta, dropped, work);
+  }
 }
 
 template void rayleigh_ritz<float>(cudaStream_t, const double*, const double*, RRDims, float*,

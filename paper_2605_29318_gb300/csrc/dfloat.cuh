@@ -23,12 +23,13 @@ struct __align__(8) dfloat {
   float h, l;
   dfloat() = default;
   __host__ __device__ constexpr dfloat(float a, float b) : h(a), l(b) {}
-  __host__ __device__ explicit dfloat(float a) : h(a), l(0.f) {}
-  __host__ __device__ explicit dfloat(int a) : h((float)a), l(0.f) {}
-  __host__ __device__ explicit dfloat(double d) {
-    h = (float)d;
-    l = (float)(d - (double)h);
-  }
+  __host__ __device__ constexpr explicit dfloat(float a) : h(a), l(0.f) {}
+  __host__ __device__ constexpr explicit dfloat(int a) : h((float)a), l(0.f) {}
+  __host__ __device__ constexpr explicit dfloat(unsigned a)
+      : h((float)a), l((float)((double)a - (double)(float)a)) {}
+  // exact split of a double into a rounded head and its remainder
+  __host__ __device__ constexpr explicit dfloat(double d)
+      : h((float)d), l((float)(d - (double)(float)d)) {}
   __host__ __device__ explicit operator double() const { return (double)h + (double)l; }
   __host__ __device__ explicit operator float() const { return h + l; }
 };
@@ -91,12 +92,49 @@ __device__ __forceinline__ void df_acc(dfloat& acc, dfloat a) {
   acc.l = __fadd_rn(acc.l, __fadd_rn(t, a.l));
 }
 
+// a / b: the FP32 quotient of the heads, corrected twice from the exact
+// remainder a - q b
+__device__ __forceinline__ dfloat df_div(dfloat a, dfloat b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const dfloat b1 = df_mul(b, dfloat(q1));
+  dfloat r = df_add(a, dfloat(-b1.h, -b1.l));
+  const float q2 = __fdiv_rn(r.h, b.h);
+  const dfloat b2 = df_mul(b, dfloat(q2));
+  r = df_add(r, dfloat(-b2.h, -b2.l));
+  const float q3 = __fdiv_rn(r.h, b.h);
+  dfloat q;
+  fast_two_sum(q1, q2, q.h, q.l);
+  return df_add(q, dfloat(q3));
+}
+
+// sqrt(a), a >= 0: the FP32 root y of the head, then y + (a - y^2) / (2 y)
+__device__ __forceinline__ dfloat df_sqrt(dfloat a) {
+  if (!(a.h > 0.f)) return dfloat(0.f, 0.f);
+  const float y = __fsqrt_rn(a.h);
+  const float p = __fmul_rn(y, y);
+  const dfloat e = df_add(a, dfloat(-p, -__fmaf_rn(y, y, -p)));
+  dfloat r;
+  fast_two_sum(y, __fdiv_rn(e.h, __fmul_rn(2.f, y)), r.h, r.l);
+  return r;
+}
+
 __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) { return df_add(a, b); }
 __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.h, -a.l); }
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return df_add(a, -b); }
 __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) { return df_mul(a, b); }
+__device__ __forceinline__ dfloat operator/(dfloat a, dfloat b) { return df_div(a, b); }
 __device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = df_add(a, b); }
+__device__ __forceinline__ dfloat& operator-=(dfloat& a, dfloat b) { return a = df_add(a, -b); }
+__device__ __forceinline__ dfloat& operator*=(dfloat& a, dfloat b) { return a = df_mul(a, b); }
+// comparisons of normalised values: heads first, then tails
 __device__ __forceinline__ bool operator==(dfloat a, dfloat b) { return a.h == b.h && a.l == b.l; }
+__device__ __forceinline__ bool operator!=(dfloat a, dfloat b) { return !(a == b); }
+__device__ __forceinline__ bool operator<(dfloat a, dfloat b) {
+  return a.h < b.h || (a.h == b.h && a.l < b.l);
+}
+__device__ __forceinline__ bool operator>(dfloat a, dfloat b) { return b < a; }
+__device__ __forceinline__ bool operator<=(dfloat a, dfloat b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(dfloat a, dfloat b) { return !(a < b); }
 
 // Generic multiply-accumulate and finishing step for the block kernels:
 // FMA for float and double, df_mac (unnormalised) for dfloat.
@@ -109,10 +147,24 @@ __device__ __forceinline__ dfloat finish(dfloat a) { return df_norm(a); }
 
 }  // namespace ff
 
+// the math functions the dense Rayleigh-Ritz kernels call, for double-float
+// arguments (global overloads beside CUDA's, so unqualified calls resolve)
+__device__ __forceinline__ ff::dfloat sqrt(ff::dfloat a) { return ff::df_sqrt(a); }
+__device__ __forceinline__ ff::dfloat fabs(ff::dfloat a) { return a.h < 0.f ? -a : a; }
+__device__ __forceinline__ ff::dfloat fmax(ff::dfloat a, ff::dfloat b) { return a < b ? b : a; }
+__device__ __forceinline__ ff::dfloat fmin(ff::dfloat a, ff::dfloat b) { return b < a ? b : a; }
+__device__ __forceinline__ ff::dfloat fma(ff::dfloat a, ff::dfloat b, ff::dfloat c) {
+  return ff::df_add(ff::df_mul(a, b), c);
+}
+__device__ __forceinline__ bool isfinite(ff::dfloat a) { return isfinite(a.h) && isfinite(a.l); }
+
 // shuffles of a dfloat move both halves
 __device__ __forceinline__ ff::dfloat __shfl_down_sync(unsigned mask, ff::dfloat v, unsigned d) {
   return ff::dfloat(__shfl_down_sync(mask, v.h, d), __shfl_down_sync(mask, v.l, d));
 }
 __device__ __forceinline__ ff::dfloat __shfl_sync(unsigned mask, ff::dfloat v, int src) {
   return ff::dfloat(__shfl_sync(mask, v.h, src), __shfl_sync(mask, v.l, src));
+}
+__device__ __forceinline__ ff::dfloat __shfl_xor_sync(unsigned mask, ff::dfloat v, int lm) {
+  return ff::dfloat(__shfl_xor_sync(mask, v.h, lm), __shfl_xor_sync(mask, v.l, lm));
 }
