@@ -13,7 +13,9 @@
 // of M and the 30 of d M; a butterfly reduction gives every lane the sums; every
 // lane then solves the 4x4 system (Cholesky) and writes phi / grad phi for its
 // own neighbours.  In FP32 mode a row whose moment matrix has a 1-norm condition
-// number above `cond_fp64` is recomputed entirely in FP64.
+// number above `cond_fp64` is recomputed entirely in FP64.  FP64 mode computes
+// in double-float (pairs of FP32 values, ~2^-47 relative) and writes FP64.
+#include "dfloat.cuh"
 #include "ff_internal.cuh"
 
 namespace ff {
@@ -130,12 +132,12 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
   if (!chol4<C>(m, L, C(1e-12))) return 1;
   if (check_cond) {
     // 1-norm condition number from the explicit inverse
-    C inv_norm = 0, m_norm = 0;
+    C inv_norm = C(0), m_norm = C(0);
     for (int col = 0; col < 4; ++col) {
-      C ecol[4] = {0, 0, 0, 0}, x[4];
+      C ecol[4] = {C(0), C(0), C(0), C(0)}, x[4];
       ecol[col] = C(1);
       chol4_solve<C>(L, ecol, x);
-      C a1 = 0, a2 = 0;
+      C a1 = C(0), a2 = C(0);
       for (int r = 0; r < 4; ++r) {
         a1 += fabs(x[r]);
         a2 += fabs(m[sidx(r, col)]);
@@ -199,7 +201,9 @@ __global__ void k_shape(const float4* __restrict__ pos, const long long* __restr
       if (lane == 0 && st == 0) atomicAdd(&flags->fallback, 1);
     }
   } else {
-    st = shape_row<double, T>(pos, s, e, idx, Xi, phi, dphi, n1, 0.0, false);
+    // FP64 outputs computed in double-float (~2^-47 relative; GB300's FP64
+    // rate made this kernel FP64-bound)
+    st = shape_row<dfloat, T>(pos, s, e, idx, Xi, phi, dphi, n1, 0.0, false);
   }
   if (st == 1 && lane == 0) {
     if (atomicCAS(&flags->code, 0, (int)FF_ERR_SINGULAR_MOMENT) == 0) flags->index = (int)i;
