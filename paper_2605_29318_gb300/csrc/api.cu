@@ -46,6 +46,14 @@ std::vector<double> to_host_f64(const ff::Buf& b, size_t count) {
   if (count) FF_CUDA(cudaMemcpy(tmp.data(), b.p, sizeof(T) * count, cudaMemcpyDeviceToHost));
   return std::vector<double>(tmp.begin(), tmp.end());
 }
+// double-float pairs (head, tail) to FP64: head + tail
+std::vector<double> to_host_df(const ff::Buf& b, size_t count) {
+  std::vector<float> tmp(2 * count);
+  if (count) FF_CUDA(cudaMemcpy(tmp.data(), b.p, sizeof(float) * 2 * count, cudaMemcpyDeviceToHost));
+  std::vector<double> out(count);
+  for (size_t i = 0; i < count; ++i) out[i] = (double)tmp[2 * i] + (double)tmp[2 * i + 1];
+  return out;
+}
 template <class T>
 std::vector<T> to_host(const ff::Buf& b, size_t count) {
   std::vector<T> tmp(count);
@@ -246,8 +254,8 @@ ff_status ff_export_rkpm(const ff_ctx* cc, int64_t* ptr, int32_t* idx, double* p
     auto ix = to_host<int>(c->nbr_idx, n1);
     std::vector<double> ph, dph;
     if (c->prec == FF_PREC_FP64) {
-      ph = to_host<double>(c->phi, n1);
-      dph = to_host<double>(c->dphi, 3 * n1);
+      ph = to_host_df(c->phi, n1);
+      dph = to_host_df(c->dphi, 3 * n1);
     } else {
       ph = to_host_f64<float>(c->phi, n1);
       dph = to_host_f64<float>(c->dphi, 3 * n1);

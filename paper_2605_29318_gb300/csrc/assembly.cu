@@ -15,6 +15,8 @@
 // accumulates the values.  The diagonal of H_w is replaced by minus the sum of
 // the off-diagonal entries of its row, which makes H_w 1 = 0 exact in storage
 // (the constant mode of Supp. Sec. B is an exact null vector).
+#include <type_traits>
+
 #include "ff_internal.cuh"
 #include "linalg.cuh"
 
@@ -117,14 +119,16 @@ __global__ void k_pattern_count(const long long* __restrict__ ptr, const int* __
 }
 
 // pass 2: sorted columns and values
-template <class T>
+// T: shape functions, material weights and sums (double-float for FP64
+// contexts); TO: the stored matrix values
+template <class T, class TO = T>
 __global__ void k_assemble(const long long* __restrict__ ptr, const int* __restrict__ idx,
                            const long long* __restrict__ tptr, const int* __restrict__ tidx,
                            const long long* __restrict__ tpos, const T* __restrict__ phi,
                            const T* __restrict__ dphi, long long n1, const float* __restrict__ vol,
                            const T* __restrict__ wh, long long n, int tsize, int maxrow,
                            const long long* __restrict__ aptr, int* __restrict__ acol,
-                           T* __restrict__ aval, float* __restrict__ hf32,
+                           TO* __restrict__ aval, float* __restrict__ hf32,
                            float* __restrict__ hdiag) {
   extern __shared__ unsigned char sm_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -183,8 +187,15 @@ __global__ void k_assemble(const long long* __restrict__ ptr, const int* __restr
       T cH0 = wi * gk0, cH1 = wi * gk1, cH2 = wi * gk2, cM = vi * fk;
       for (long long e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
         int r = rnk[hset_find(tab, tsize, idx[e])];
-        vh[r] += cH0 * dphi[e] + cH1 * dphi[n1 + e] + cH2 * dphi[2 * n1 + e];
-        vm[r] += cM * phi[e];
+        if constexpr (std::is_same_v<T, dfloat>) {  // unnormalised sums, normalised below
+          df_mac(vh[r], cH0, dphi[e]);
+          df_mac(vh[r], cH1, dphi[n1 + e]);
+          df_mac(vh[r], cH2, dphi[2 * n1 + e]);
+          df_mac(vm[r], cM, phi[e]);
+        } else {
+          vh[r] += cH0 * dphi[e] + cH1 * dphi[n1 + e] + cH2 * dphi[2 * n1 + e];
+          vm[r] += cM * phi[e];
+        }
       }
       __syncwarp();
     }
@@ -196,19 +207,19 @@ __global__ void k_assemble(const long long* __restrict__ ptr, const int* __restr
     __syncwarp();
     T off = T(0);
     for (int r = lane; r < m; r += 32)
-      if (skeys[r] != (int)k) off += vh[r];
+      if (skeys[r] != (int)k) off += finish(vh[r]);
 #pragma unroll
     for (int o = 16; o; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
     const long long row0 = aptr[k];
     for (int r = lane; r < m; r += 32) {
       int col = skeys[r];
-      T h = (col == (int)k) ? -off : vh[r];
+      const TO h = (col == (int)k) ? (TO)(-off) : (TO)finish(vh[r]);
       acol[row0 + r] = col;
       aval[2 * (row0 + r)] = h;
-      aval[2 * (row0 + r) + 1] = vm[r];
+      aval[2 * (row0 + r) + 1] = (TO)finish(vm[r]);
       hf32[row0 + r] = (float)h;
     }
-    if (lane == 0) hdiag[k] = (float)(-off);
+    if (lane == 0) hdiag[k] = (float)(TO)(-off);
     __syncwarp();
   }
 }
@@ -244,9 +255,9 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   const size_t tb = f64 ? 8 : 4;
   reset_flags(c);
   c->wh.ensure(tb * n);
-  if (f64)
-    (k_material<double><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
-                                                    nu, E0, nu0, c->wh.as<double>(),
+  if (f64)  // FP64 contexts: material weights in double-float, like the shape functions
+    (k_material<dfloat><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
+                                                    nu, E0, nu0, c->wh.as<dfloat>(),
                                                     c->flags.as<DevFlags>()), ::ff::note_launch());
   else
     (k_material<float><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
@@ -303,12 +314,12 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   size_t smem = pw * wpb2;
   int grid2 = (int)std::min<long long>(ceil_div(n, wpb2), 152LL * 32);
   if (f64) {
-    FF_CUDA(cudaFuncSetAttribute(k_assemble<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FF_CUDA(cudaFuncSetAttribute(k_assemble<dfloat, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(smem, 48 * 1024)));
-    (k_assemble<double><<<grid2, 32 * wpb2, smem, st>>>(
+    (k_assemble<dfloat, double><<<grid2, 32 * wpb2, smem, st>>>(
         c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
-        c->nbrT_idx.as<int>(), c->nbrT_pos.as<long long>(), c->phi.as<double>(),
-        c->dphi.as<double>(), n1, c->vol.as<float>(), c->wh.as<double>(), n, tsize2, maxrow, aptr,
+        c->nbrT_idx.as<int>(), c->nbrT_pos.as<long long>(), c->phi.as<dfloat>(),
+        c->dphi.as<dfloat>(), n1, c->vol.as<float>(), c->wh.as<dfloat>(), n, tsize2, maxrow, aptr,
         c->a_col.as<int>(), c->a_val.as<double>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>()), ::ff::note_launch());
   } else {
     FF_CUDA(cudaFuncSetAttribute(k_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -14,7 +14,7 @@
 // lane then solves the 4x4 system (Cholesky) and writes phi / grad phi for its
 // own neighbours.  In FP32 mode a row whose moment matrix has a 1-norm condition
 // number above `cond_fp64` is recomputed entirely in FP64.  FP64 mode computes
-// in double-float (pairs of FP32 values, ~2^-47 relative) and writes FP64.
+// and stores double-float pairs (FP32 head and tail, ~2^-47 relative).
 #include "dfloat.cuh"
 #include "ff_internal.cuh"
 
@@ -220,10 +220,10 @@ void build_shape(ff_ctx* c) {
   c->phi.ensure(es * n1);
   c->dphi.ensure(3 * es * n1);
   const double cond_limit = 1e2;
-  if (c->prec == FF_PREC_FP64) {
-    (k_shape<double><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
+  if (c->prec == FF_PREC_FP64) {  // stored as double-float pairs for the assembly
+    (k_shape<dfloat><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
         c->pos.as<float4>(), c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), n, n1,
-        c->phi.as<double>(), c->dphi.as<double>(), cond_limit, c->flags.as<DevFlags>()), ::ff::note_launch());
+        c->phi.as<dfloat>(), c->dphi.as<dfloat>(), cond_limit, c->flags.as<DevFlags>()), ::ff::note_launch());
   } else {
     (k_shape<float><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
         c->pos.as<float4>(), c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), n, n1,
