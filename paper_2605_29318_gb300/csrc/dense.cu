@@ -367,12 +367,14 @@ __device__ int sturm(const R* d, const R* e2, int n, R x) {
 // ------------------------------------------------------------------ 1b. cluster Householder
 // Householder tridiagonalisation of the transformed n x n matrix (w.As) by a
 // cluster of kCS thread blocks: row r lives in block r % kCS (distributed
-// shared memory), so the O(n^3) FP64 work is spread over kCS SMs.  Per step j
-// each block publishes its entries of column j, every block gathers the whole
-// column and forms the same reflector; each block computes p = tau A v for its
-// rows and publishes them with its share of p^T v; every block gathers p, forms
-// w = p - K v and updates its rows.  Two cluster barriers per step; the
-// published buffers alternate between steps so no barrier guards their reuse.
+// shared memory), so the O(n^3) work is spread over kCS SMs.  Every block
+// holds column j of the current matrix and forms the same reflector v; each
+// block computes p = tau A v for its rows and publishes it with its share of
+// p^T v and its rows' entries of column j+1 (before the update); after one
+// cluster barrier every block gathers p, forms w = p - K v, updates its rows
+// and forms the updated column j+1 of all rows itself from the published
+// entries -- one cluster barrier per step.  The published buffers alternate
+// between steps, so no barrier guards their reuse.
 constexpr int kCS = 8;
 constexpr int kCT = 256;
 
@@ -401,7 +403,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
   R* Ar = sm;                      // rpc x n: row rank + kCS * li
   R* vf = Ar + (size_t)rpc * n;    // n: column j, then v
   R* wf = vf + n;                  // n: p, then w
-  R* pubc = wf + n;                // 2 x rpc
+  R* cf = wf + n;                  // n: column j of the current matrix
+  R* pubc = cf + n;                // 2 x rpc: own rows' entries of the next column
   R* pubp = pubc + 2 * rpc;        // 2 x rpc
   R* pubs = pubp + 2 * rpc;        // 2
   __shared__ R red[kW];
@@ -410,17 +413,27 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     Ar[t] = r < n ? w.As[(size_t)r * n + c] : R(0.0);
   }
   __syncthreads();
-  for (int j = 0; j + 2 < n; ++j) {
-    const int buf = j & 1;
+  // own rows' entries of column c (rows >= c + 1) into pubc[b], then every
+  // block gathers the column into cf
+  auto publish_col = [&](int c, int b) {
     for (int li = tid; li < rpc; li += kCT) {
       const int r = rank + kCS * li;
-      pubc[buf * rpc + li] = (r < n && r >= j + 1) ? Ar[(size_t)li * n + j] : R(0.0);
+      pubc[b * rpc + li] = (r < n && r >= c + 1) ? Ar[(size_t)li * n + c] : R(0.0);
     }
-    cl.sync();
-    for (int r = j + 1 + tid; r < n; r += kCT) {
-      const R* rem = cl.map_shared_rank(pubc + buf * rpc, r % kCS);
-      vf[r] = rem[r / kCS];
+  };
+  auto gather_col = [&](int c, int b) {
+    for (int r = c + 1 + tid; r < n; r += kCT) {
+      const R* rem = cl.map_shared_rank(pubc + b * rpc, r % kCS);
+      cf[r] = rem[r / kCS];
     }
+  };
+  publish_col(0, 0);
+  cl.sync();
+  gather_col(0, 0);
+  __syncthreads();
+  for (int j = 0; j + 2 < n; ++j) {
+    const int buf = j & 1;
+    for (int r = j + 1 + tid; r < n; r += kCT) vf[r] = cf[r];
     __syncthreads();
     R part = R(0.0);
     for (int r = j + 1 + tid; r < n; r += kCT) part += vf[r] * vf[r];
@@ -428,12 +441,15 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     const R x0 = vf[j + 1];
     const R alpha = sqrt(ss);
     const int own_j = (j % kCS) == rank;
-    if (!(alpha > Prec<R>::tiny)) {
+    if (!(alpha > Prec<R>::tiny)) {  // nothing to reflect: the next column as it stands
       if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
       if (rank == 0 && tid == 0) {
         w.tau[j] = R(0.0);
         w.e[j] = x0;
       }
+      publish_col(j + 1, buf ^ 1);
+      cl.sync();
+      gather_col(j + 1, buf ^ 1);
       __syncthreads();
       continue;
     }
@@ -452,7 +468,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
       w.e[j] = beta;
     }
     __syncthreads();
-    // p = tau A v for own rows r >= j+1, and this block's share of p^T v
+    // p = tau A v for own rows r >= j+1, this block's share of p^T v, and the
+    // own rows' entries of column j+1 before the update
     R kp = R(0.0);
     for (int li = wid; li < rpc; li += kW) {
       const int r = rank + kCS * li;
@@ -467,6 +484,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
         if (r < n && r >= j + 1) kp += acc * vf[r];
       }
     }
+    publish_col(j + 1, buf ^ 1);
     const R kpb = cl_block_sum(kp, red);
     if (tid == 0) pubs[buf] = kpb;
     cl.sync();
@@ -478,6 +496,12 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
       wf[r] = rem[r / kCS] - K * vf[r];
     }
     __syncthreads();
+    // the updated column j+1 of every row: a_r,j+1 - v_r w_j+1 - w_r v_j+1
+    const R vn = vf[j + 1], wn = wf[j + 1];
+    for (int r = j + 2 + tid; r < n; r += kCT) {
+      const R* rem = cl.map_shared_rank(pubc + (buf ^ 1) * rpc, r % kCS);
+      cf[r] = rem[r / kCS] - (vf[r] * wn + wf[r] * vn);
+    }
     for (int li = wid; li < rpc; li += kW) {  // A_own -= v w^T + w v^T
       const int r = rank + kCS * li;
       if (r >= n || r < j + 1) continue;
@@ -1016,7 +1040,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   const size_t tri_bytes = sizeof(R) * n * n;
   const bool tri_smem = tri_bytes <= kMaxDynSmem;
   const size_t rpc = (n + kCS - 1) / kCS;
-  const size_t cl_bytes = sizeof(R) * (rpc * n + 2 * n + 4 * rpc + 2);
+  const size_t cl_bytes = sizeof(R) * (rpc * n + 3 * n + 4 * rpc + 2);
   const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
   const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
   // transform (one block); Householder by the cluster when its rows fit
