@@ -209,27 +209,25 @@ __global__ void __launch_bounds__(kThreads)
   }
   __syncthreads();
   block_cholesky(w.L, no, w.keep + o0, drop);
-  // A <- T^T A T: O rows by L^-1, then O columns
-  for (int a = 0; a < no; ++a) {
-    const int i = o0 + a;
-    const R inv = R(1.0) / w.L[a * no + a];
-    for (int c = tid; c < n; c += kThreads) {
+  // A <- T^T A T: O rows by L^-1, then O columns.  A thread's forward
+  // substitution reads only the entries of its own column (row) that it wrote
+  // itself, so the whole substitution runs without barriers.
+  for (int c = tid; c < n; c += kThreads)
+    for (int a = 0; a < no; ++a) {
+      const int i = o0 + a;
       R acc = As[(size_t)i * n + c];
       for (int b = 0; b < a; ++b) acc -= w.L[a * no + b] * As[(size_t)(o0 + b) * n + c];
-      As[(size_t)i * n + c] = acc * inv;
+      As[(size_t)i * n + c] = acc / w.L[a * no + a];
     }
-    __syncthreads();
-  }
-  for (int a = 0; a < no; ++a) {
-    const int i = o0 + a;
-    const R inv = R(1.0) / w.L[a * no + a];
-    for (int r = tid; r < n; r += kThreads) {
+  __syncthreads();
+  for (int r = tid; r < n; r += kThreads)
+    for (int a = 0; a < no; ++a) {
+      const int i = o0 + a;
       R acc = As[(size_t)r * n + i];
       for (int b = 0; b < a; ++b) acc -= w.L[a * no + b] * As[(size_t)r * n + o0 + b];
-      As[(size_t)r * n + i] = acc * inv;
+      As[(size_t)r * n + i] = acc / w.L[a * no + a];
     }
-    __syncthreads();
-  }
+  __syncthreads();
   // symmetrise; dropped columns are decoupled with a diagonal just above the
   // spectrum of the kept part (2 ||A_kept||_inf + 1), which keeps them out of
   // the nb lowest without disturbing the scale of the tridiagonal problem
@@ -488,8 +486,12 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     const R kpb = cl_block_sum(kp, red);
     if (tid == 0) pubs[buf] = kpb;
     cl.sync();
+    R kq[kCS];  // the blocks' shares, loaded together (remote loads in flight at once)
+#pragma unroll
+    for (int q = 0; q < kCS; ++q) kq[q] = cl.map_shared_rank(pubs, q)[buf];
     R K = R(0.0);
-    for (int q = 0; q < kCS; ++q) K += cl.map_shared_rank(pubs, q)[buf];
+#pragma unroll
+    for (int q = 0; q < kCS; ++q) K += kq[q];
     K *= R(0.5) * tj;
     for (int r = j + 1 + tid; r < n; r += kCT) {
       const R* rem = cl.map_shared_rank(pubp + buf * rpc, r % kCS);
@@ -877,21 +879,21 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
   }
-  // back to the coefficients of the original basis: y_O <- L^-T y_O, then
-  // y_rest <- y_rest - C y_O, then y <- D y
-  for (int a = no - 1; a >= 0; --a) {
-    const int i = o0 + a;
-    const R inv = R(1.0) / w.L[a * no + a];
-    for (int c = tid; c < 2 * nb; c += kThreads) {
-      if (c >= nb && !want_p) continue;
-      R* M_ = c < nb ? V : Z;
-      const int cc = c < nb ? c : c - nb;
+  // back to the coefficients of the original basis: y_O <- L^-T y_O (a
+  // thread per column, its back substitution reading only entries it wrote:
+  // no barriers), then y_rest <- y_rest - C y_O and y <- D y (k_rr_output)
+  for (int c = tid; c < 2 * nb; c += kThreads) {
+    if (c >= nb && !want_p) continue;
+    R* M_ = c < nb ? V : Z;
+    const int cc = c < nb ? c : c - nb;
+    for (int a = no - 1; a >= 0; --a) {
+      const int i = o0 + a;
       R acc = M_[(size_t)i * nb + cc];
       for (int b = a + 1; b < no; ++b) acc -= w.L[b * no + a] * M_[(size_t)(o0 + b) * nb + cc];
-      M_[(size_t)i * nb + cc] = acc * inv;
+      M_[(size_t)i * nb + cc] = acc / w.L[a * no + a];
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (tid == 0) {
     int dc = 0;
     for (int a = 0; a < n; ++a) dc += !w.keep[a];
