@@ -779,11 +779,18 @@ __global__ void k_rr_invit_sm(int n, int nb, RRWork<R> w) {
 }
 
 // ------------------------------------------------------------------ 4a. Cholesky QR (twice) of the tridiagonal eigenvectors
-template <class R>
+// SM: V (n x nb) and G staged in shared memory (dynamic), else worked on in
+// the global workspace
+template <class R, bool SM>
 __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R> w) {
   __shared__ int keep_nb[512];
-  R* V = w.V;
-  R* G = w.G;
+  extern __shared__ __align__(16) unsigned char cq_raw[];
+  R* V = SM ? reinterpret_cast<R*>(cq_raw) : w.V;
+  R* G = SM ? V + (size_t)n * nb : w.G;
+  if (SM) {
+    for (int t = threadIdx.x; t < n * nb; t += kThreads) V[t] = w.V[t];
+    __syncthreads();
+  }
   for (int pass = 0; pass < 2; ++pass) {
     for (int t = threadIdx.x; t < nb * nb; t += kThreads) {
       const int a = t / nb, b = t % nb;
@@ -805,6 +812,8 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
     }
     __syncthreads();
   }
+  if (SM)
+    for (int t = threadIdx.x; t < n * nb; t += kThreads) w.V[t] = V[t];
 }
 
 // ------------------------------------------------------------------ 4b. back-transform, one warp per vector
@@ -1037,6 +1046,8 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem));
     FF_CUDA(cudaFuncSetAttribute(k_rr_invit_sm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxDynSmem));
+    FF_CUDA(cudaFuncSetAttribute(k_rr_cholqr<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMaxDynSmem));
     attr = true;
   }
   const size_t tri_bytes = sizeof(R) * n * n;
@@ -1066,7 +1077,11 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
     (k_rr_invit<R><<<(unsigned)((nb + 31) / 32), 32, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
-  (k_rr_cholqr<R><<<1, kThreads, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
+  const size_t cq_bytes = sizeof(R) * (n * nb + nb * nb);
+  if (cq_bytes <= kMaxDynSmem)
+    (k_rr_cholqr<R, true><<<1, kThreads, cq_bytes, st>>>(d.ns, d.nb, w), ::ff::note_launch());
+  else
+    (k_rr_cholqr<R, false><<<1, kThreads, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   (k_rr_backtransform<R><<<(unsigned)nb, 32, sizeof(R) * n, st>>>(d.ns, d.nb, w),
    ::ff::note_launch());

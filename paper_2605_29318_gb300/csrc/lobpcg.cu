@@ -513,7 +513,9 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   int it = 0;
   ff_status status = FF_ERR_NOT_CONVERGED;
   const double th_c = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
-  const long long rpb = std::max<long long>(256, (n + 511) / 512);
+  // column statistics: chunks of 64 rows (8 per warp), enough blocks in flight
+  // to cover the loads' latency
+  const long long rpb = std::max<long long>(64, (n + 2047) / 2048);
   const int cs_blocks = (int)((n + rpb - 1) / rpb);
   double* cs_part = reinterpret_cast<double*>(c->scratch[2].ensure(sizeof(double) * cs_blocks * 5 * nb));
   // the block with the smallest largest residual seen, and the progress mark
