@@ -838,15 +838,22 @@ __global__ void k_rr_backtransform(int n, int nb, RRWork<R> w) {
 }
 
 // ------------------------------------------------------------------ 4c. momentum and mapping back
-template <class R, class T>
+template <class R, class T, bool SM>
 __global__ void __launch_bounds__(kThreads)
     k_rr_momentum(int n, int o0, int no, int nx, int nb, int want_p, RRWork<R> w,
                   T* __restrict__ YZ, int* __restrict__ dropped) {
   __shared__ int keep_nb[512];
   const int tid = threadIdx.x;
-  R* V = w.V;
-  R* Z = w.Z;
-  R* G = w.G;
+  // SM: V, Z, T1 (n x nb each) and G staged in shared memory (dynamic)
+  extern __shared__ __align__(16) unsigned char mo_raw[];
+  R* V = SM ? reinterpret_cast<R*>(mo_raw) : w.V;
+  R* Z = SM ? V + (size_t)n * nb : w.Z;
+  R* T1 = SM ? Z + (size_t)n * nb : w.T1;
+  R* G = SM ? T1 + (size_t)n * nb : w.G;
+  if (SM) {
+    for (int t = tid; t < n * nb; t += kThreads) V[t] = w.V[t];
+    __syncthreads();
+  }
   if (want_p) {
     // G = V^T Zp with Zp = V without its X rows, summed over the W and P rows
     // directly: I - V_X^T V_X would cancel catastrophically once the X rows of
@@ -862,14 +869,14 @@ __global__ void __launch_bounds__(kThreads)
       const int i = t / nb, b = t % nb;
       R acc = i < nx ? R(0.0) : V[t];
       for (int a = 0; a < nb; ++a) acc -= V[(size_t)i * nb + a] * G[a * nb + b];
-      w.T1[t] = acc;
+      T1[t] = acc;
     }
     __syncthreads();
     for (int t = tid; t < nb * nb; t += kThreads) {  // G = Z^T Z (lower)
       const int a = t / nb, b = t % nb;
       R acc = R(0.0);
       if (b <= a)
-        for (int i = 0; i < n; ++i) acc += w.T1[(size_t)i * nb + a] * w.T1[(size_t)i * nb + b];
+        for (int i = 0; i < n; ++i) acc += T1[(size_t)i * nb + a] * T1[(size_t)i * nb + b];
       G[t] = acc;
     }
     for (int s2 = tid; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
@@ -878,7 +885,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int s2 = 0; s2 < nb; ++s2) gref = fmax(gref, G[s2 * nb + s2]);
     block_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
     for (int i = tid; i < n; i += kThreads) {  // Z <- Z L^-T, dropped columns zero
-      const R* zt = w.T1 + (size_t)i * nb;
+      const R* zt = T1 + (size_t)i * nb;
       R* zr = Z + (size_t)i * nb;
       for (int s2 = 0; s2 < nb; ++s2) {
         R acc = zt[s2];
@@ -903,6 +910,11 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   __syncthreads();
+  if (SM) {
+    for (int t = tid; t < n * nb; t += kThreads) w.V[t] = V[t];
+    if (want_p)
+      for (int t = tid; t < n * nb; t += kThreads) w.Z[t] = Z[t];
+  }
   if (tid == 0) {
     int dc = 0;
     for (int a = 0; a < n; ++a) dc += !w.keep[a];
@@ -1038,6 +1050,12 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.C = p; p += n * no;
   w.U = p; p += n * no;
   w.keep = reinterpret_cast<int*>(p);
+  static bool attr_mo = false;
+  if (!attr_mo) {
+    FF_CUDA(cudaFuncSetAttribute(k_rr_momentum<R, T, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem));
+    attr_mo = true;
+  }
   static bool attr = false;
   if (!attr) {
     FF_CUDA(cudaFuncSetAttribute(k_rr_tridiag<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1086,9 +1104,15 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   (k_rr_backtransform<R><<<(unsigned)nb, 32, sizeof(R) * n, st>>>(d.ns, d.nb, w),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  (k_rr_momentum<R, T><<<1, kThreads, 0, st>>>(d.ns, d.o0, d.no, d.nx, d.nb, d.want_p, w, YZ,
-                                               dropped),
-   ::ff::note_launch());
+  const size_t mo_bytes = sizeof(R) * (3 * n * nb + nb * nb);
+  if (mo_bytes <= kMaxDynSmem)
+    (k_rr_momentum<R, T, true><<<1, kThreads, mo_bytes, st>>>(d.ns, d.o0, d.no, d.nx, d.nb,
+                                                               d.want_p, w, YZ, dropped),
+     ::ff::note_launch());
+  else
+    (k_rr_momentum<R, T, false><<<1, kThreads, 0, st>>>(d.ns, d.o0, d.no, d.nx, d.nb, d.want_p,
+                                                         w, YZ, dropped),
+     ::ff::note_launch());
   FF_LAUNCH_CHECK();
   (k_rr_output<R, T><<<(unsigned)n, 128, 0, st>>>(d.ns, d.o0, d.no, d.nb, d.want_p, w, YZ),
    ::ff::note_launch());
