@@ -817,17 +817,30 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
 }
 
 // ------------------------------------------------------------------ 4b. back-transform, one warp per vector
-template <class R>
-__global__ void k_rr_backtransform(int n, int nb, RRWork<R> w) {
+// kBW vectors (warps) per block; SM: the reflectors and tau staged in shared
+// memory once per block (the reflector loop is a dependent chain per vector)
+constexpr int kBW = 8;
+template <class R, bool SM>
+__global__ void __launch_bounds__(32 * kBW) k_rr_backtransform(int n, int nb, RRWork<R> w) {
   extern __shared__ __align__(16) unsigned char z_raw[];
-  R* z = reinterpret_cast<R*>(z_raw);
-  const int s = blockIdx.x, lane = threadIdx.x;
+  R* zall = reinterpret_cast<R*>(z_raw);               // kBW x n
+  R* ref = SM ? zall + (size_t)kBW * n : w.ref;       // n x n
+  R* tau = SM ? ref + (size_t)n * n : w.tau;          // n
+  const int wv = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kBW + wv;
+  if (SM) {
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) ref[t] = w.ref[t];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tau[t] = w.tau[t];
+    __syncthreads();
+  }
+  if (s >= nb) return;
+  R* z = zall + (size_t)wv * n;
   for (int i = lane; i < n; i += 32) z[i] = w.V[(size_t)i * nb + s];
   __syncwarp();
   for (int j = n - 3; j >= 0; --j) {
-    const R tj = w.tau[j];
+    const R tj = tau[j];
     if (tj == R(0.0)) continue;
-    const R* v = w.ref + (size_t)j * n;
+    const R* v = ref + (size_t)j * n;
     R acc = R(0.0);
     for (int i = j + 1 + lane; i < n; i += 32) acc += v[i] * z[i];
     acc = warp_sum(acc) * tj;
@@ -1066,6 +1079,8 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
                                  (int)kMaxDynSmem));
     FF_CUDA(cudaFuncSetAttribute(k_rr_cholqr<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kMaxDynSmem));
+    FF_CUDA(cudaFuncSetAttribute(k_rr_backtransform<R, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem));
     attr = true;
   }
   const size_t tri_bytes = sizeof(R) * n * n;
@@ -1101,8 +1116,15 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   else
     (k_rr_cholqr<R, false><<<1, kThreads, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  (k_rr_backtransform<R><<<(unsigned)nb, 32, sizeof(R) * n, st>>>(d.ns, d.nb, w),
-   ::ff::note_launch());
+  const size_t bt_bytes = sizeof(R) * (kBW * n + n * n + n);
+  if (bt_bytes <= kMaxDynSmem)
+    (k_rr_backtransform<R, true><<<(unsigned)((nb + kBW - 1) / kBW), 32 * kBW, bt_bytes, st>>>(
+         d.ns, d.nb, w),
+     ::ff::note_launch());
+  else
+    (k_rr_backtransform<R, false><<<(unsigned)((nb + kBW - 1) / kBW), 32 * kBW,
+                                    sizeof(R) * kBW * n, st>>>(d.ns, d.nb, w),
+     ::ff::note_launch());
   FF_LAUNCH_CHECK();
   const size_t mo_bytes = sizeof(R) * (3 * n * nb + nb * nb);
   if (mo_bytes <= kMaxDynSmem)
