@@ -58,7 +58,10 @@ typedef enum {
   FF_PREC_FP32 = 0,  /* FP32 shape functions (FP64 fallback for ill-conditioned moment
                         matrices), FP32 matrices and iterates, FP64-accumulated Gram
                         products, FP32 dense Rayleigh-Ritz */
-  FF_PREC_FP64 = 1   /* FP64 throughout (the preconditioner alone stays FP32) */
+  FF_PREC_FP64 = 1   /* FP64 matrices and results: shape functions and assembly sums in
+                        double-float (FP32 pairs, ~2^-47 relative), H_w and M stored in
+                        FP64; the eigensolver as set by ff_eig_opts.fp32_phase (the
+                        preconditioner stays FP32 / BF16) */
 } ff_precision;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
@@ -123,9 +126,11 @@ typedef struct {
   int verbose;          /* print per-iteration residuals to stderr (0) */
   int fp32_phase;       /* FF_PREC_FP64 contexts: 1 = iterate on FP32 roundings of H_w and M
                            until the residual reaches fp32_tol or stops falling, then
-                           finish in FP64 from that block; 0 = FP64 throughout (1) */
+                           finish from that block in double-float arithmetic (FP32 pairs,
+                           ~2^-47 relative; residuals to tol against the FP64 matrices);
+                           0 = FP64 blocks and Rayleigh-Ritz throughout (1) */
   double fp32_tol;      /* residual at which the FP32 phase hands over (1e-4) */
-  int cheb_degree_fp64; /* Chebyshev degree of the FP64 phase that follows an FP32 phase;
+  int cheb_degree_fp64; /* Chebyshev degree of the second phase that follows an FP32 phase;
                            0 = cheb_degree (64) */
   int precond_tc;       /* 1: the preconditioner's H products on tensor cores, with H in
                            BF16 dense tiles of 16-row blocks (block widths 8..64 in steps

@@ -337,7 +337,7 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
     (k_round_f32<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->a_val.as<double>(), v32, m),
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
-    // and the double-float split for its FP64 phase
+    // and the double-float split for its second phase
     float2* vdf = reinterpret_cast<float2*>(c->a_valdf.ensure(2 * sizeof(float2) * n2));
     (k_split_df<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(c->a_val.as<double>(), vdf, m),
      ::ff::note_launch());

@@ -32,9 +32,11 @@
 //                       M-orthonormal and M-orthogonal to the next X), and the
 //                       O rows mapped back through L^-T and the scaling.
 // Output YZ = [Y | Z] (n x 2 nb, row-major, context precision) and the Ritz
-// values theta (nb).  FP64 throughout: the spectrum of A spans the whole range
-// of the basis' Rayleigh quotients and the small eigenvalues need relative
-// accuracy.
+// values theta (nb).  Instantiated in FP64 (FP64 blocks), in double-float
+// (the double-float phase of the mixed solve) and in FP32 (the FP32 phase):
+// the spectrum of A spans the whole range of the basis' Rayleigh quotients and
+// the small eigenvalues need relative accuracy, so every phase that must reach
+// the FP64 residual bar runs it in FP64 or double-float.
 #include <cooperative_groups.h>
 
 #include <type_traits>

@@ -364,8 +364,8 @@ struct Solver {
 };
 
 // One run of the solver at one precision.  A mixed-precision solve runs an
-// FP32 phase (FP32 roundings of H_w and M) that hands its best block to an
-// FP64 phase.
+// FP32 phase (FP32 roundings of H_w and M) that hands its best block to a
+// double-float phase.
 struct Phase {
   const void* aval = nullptr;      // interleaved (H, M) of the phase's precision
   const float* X0_int = nullptr;   // start block from an earlier phase: internal
@@ -753,7 +753,7 @@ ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
   std::vector<double> ev1(k);
   ff_eig_report r1{};
   const ff_status s1 = solve<float>(c, k, o1, p32, X0f, ev1.data(), nullptr, &r1);
-  // FP64 phase from the FP32 phase's best block
+  // second phase from the FP32 phase's best block
   ff_eig_opts o2 = o;
   o2.max_iter = std::max(0, o.max_iter - r1.iterations);
   if (o.cheb_degree_fp64 > 0) o2.cheb_degree = o.cheb_degree_fp64;
