@@ -48,7 +48,7 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr size_t kMaxDynSmem = 200 * 1024;
+constexpr size_t kMaxDynSmem = 220 * 1024;  // opt-in limit less room for static shared memory
 // working-precision constants: unit roundoff, smallest magnitude kept apart
 // from zero, default Cholesky drop, and the exponent at which the Sturm
 // recurrence rescales
@@ -140,7 +140,11 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ R red[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const size_t nn = (size_t)n * n;
+  // smem = 1: A in shared memory; smem = 2: also C, U (n x no) and L (no x no)
   R* As = smem ? dyn : w.As;
+  R* Cw = smem == 2 ? As + nn : w.C;
+  R* Uw = smem == 2 ? Cw + (size_t)n * no : w.U;
+  R* Lw = smem == 2 ? Uw + (size_t)n * no : w.L;
   R* vt = w.T1;            // n
   R* pw = w.T1 + n;        // n
   // scaling: O columns by diag(B)^-1/2; other columns must have B_ii ~ 1
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int t = tid; t < n * no; t += kThreads) {
     const int i = t / no, j = o0 + t % no;
     const bool in_o = i >= o0 && i < o1;
-    w.C[t] = (!in_o && w.keep[i] && w.keep[j])
+    Cw[t] = (!in_o && w.keep[i] && w.keep[j])
                  ? R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j]
                  : R(0.0);
   }
@@ -184,8 +188,8 @@ __global__ void __launch_bounds__(kThreads)
     R acc = R(0.0);
     if (i < o0 || i >= o1)
       for (int r = 0; r < n; ++r)
-        if (r < o0 || r >= o1) acc += As[(size_t)i * n + r] * w.C[r * no + a];
-    w.U[t] = acc;
+        if (r < o0 || r >= o1) acc += As[(size_t)i * n + r] * Cw[r * no + a];
+    Uw[t] = acc;
   }
   __syncthreads();
   for (int t = tid; t < no * no; t += kThreads) {
@@ -193,24 +197,24 @@ __global__ void __launch_bounds__(kThreads)
     R cc = R(0.0), acc = As[(size_t)i * n + j];
     for (int r = 0; r < n; ++r) {
       if (r >= o0 && r < o1) continue;
-      const R ca = w.C[r * no + a], cb = w.C[r * no + b];
+      const R ca = Cw[r * no + a], cb = Cw[r * no + b];
       cc += ca * cb;
-      acc += ca * w.U[r * no + b] - ca * As[(size_t)r * n + j] - As[(size_t)i * n + r] * cb;
+      acc += ca * Uw[r * no + b] - ca * As[(size_t)r * n + j] - As[(size_t)i * n + r] * cb;
     }
     const R v = R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j] - cc;
-    w.L[t] = (w.keep[i] && w.keep[j]) ? v : (a == b ? R(1.0) : R(0.0));
+    Lw[t] = (w.keep[i] && w.keep[j]) ? v : (a == b ? R(1.0) : R(0.0));
     As[(size_t)i * n + j] = acc;
   }
   __syncthreads();
   for (int t = tid; t < n * no; t += kThreads) {
     const int i = t / no, j = o0 + t % no;
     if (i >= o0 && i < o1) continue;
-    const R v = As[(size_t)i * n + j] - w.U[t];
+    const R v = As[(size_t)i * n + j] - Uw[t];
     As[(size_t)i * n + j] = v;
     As[(size_t)j * n + i] = v;
   }
   __syncthreads();
-  block_cholesky(w.L, no, w.keep + o0, drop);
+  block_cholesky(Lw, no, w.keep + o0, drop);
   // A <- T^T A T: O rows by L^-1, then O columns.  A thread's forward
   // substitution reads only the entries of its own column (row) that it wrote
   // itself, so the whole substitution runs without barriers.
@@ -218,16 +222,16 @@ __global__ void __launch_bounds__(kThreads)
     for (int a = 0; a < no; ++a) {
       const int i = o0 + a;
       R acc = As[(size_t)i * n + c];
-      for (int b = 0; b < a; ++b) acc -= w.L[a * no + b] * As[(size_t)(o0 + b) * n + c];
-      As[(size_t)i * n + c] = acc / w.L[a * no + a];
+      for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)(o0 + b) * n + c];
+      As[(size_t)i * n + c] = acc / Lw[a * no + a];
     }
   __syncthreads();
   for (int r = tid; r < n; r += kThreads)
     for (int a = 0; a < no; ++a) {
       const int i = o0 + a;
       R acc = As[(size_t)r * n + i];
-      for (int b = 0; b < a; ++b) acc -= w.L[a * no + b] * As[(size_t)r * n + o0 + b];
-      As[(size_t)r * n + i] = acc / w.L[a * no + a];
+      for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)r * n + o0 + b];
+      As[(size_t)r * n + i] = acc / Lw[a * no + a];
     }
   __syncthreads();
   // symmetrise; dropped columns are decoupled with a diagonal just above the
@@ -263,6 +267,10 @@ __global__ void __launch_bounds__(kThreads)
     if (i < j) As[t] = As[(size_t)j * n + i];
   }
   __syncthreads();
+  if (smem == 2) {  // L and C are read by the later kernels
+    for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
+    for (int t = tid; t < n * no; t += kThreads) w.C[t] = Cw[t];
+  }
   if (!do_house) {  // hand the transformed matrix to the cluster reduction
     if (smem)
       for (size_t t = tid; t < nn; t += kThreads) w.As[t] = As[t];
@@ -1086,14 +1094,15 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
     attr = true;
   }
   const size_t tri_bytes = sizeof(R) * n * n;
-  const bool tri_smem = tri_bytes <= kMaxDynSmem;
+  const size_t tri2_bytes = sizeof(R) * (n * n + 2 * n * no + no * no);
+  const int tri_smem = tri2_bytes <= kMaxDynSmem ? 2 : tri_bytes <= kMaxDynSmem ? 1 : 0;
   const size_t rpc = (n + kCS - 1) / kCS;
   const size_t cl_bytes = sizeof(R) * (rpc * n + 3 * n + 4 * rpc + 2);
   const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
   const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
   // transform (one block); Householder by the cluster when its rows fit
-  (k_rr_tridiag<R><<<1, kThreads, tri_smem ? tri_bytes : 0, st>>>(
-       A, B, d.ns, d.o0, d.no, w, tri_smem ? 1 : 0, use_cluster ? 0 : 1, drop),
+  (k_rr_tridiag<R><<<1, kThreads, tri_smem == 2 ? tri2_bytes : tri_smem ? tri_bytes : 0, st>>>(
+       A, B, d.ns, d.o0, d.no, w, tri_smem, use_cluster ? 0 : 1, drop),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
