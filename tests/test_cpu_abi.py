@@ -63,6 +63,8 @@ def test_default_options_without_gpu(lib):
     from paper_2605_29318_gb300 import binding
     o = binding.default_opts()
     assert o.tol == 1e-6 and o.max_iter == 500 and o.cheb_degree == 16 and o.guard == 8
+    assert o.fp32_phase == 1 and o.fp32_tol == 1e-4 and o.cheb_degree_fp64 == 64
+    assert o.precond_tc == 1
 
 
 def test_create_without_device_fails_cleanly(lib):
@@ -81,6 +83,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.assemble_hessian(None, None, None, 1.0, 0.3) == 1
     assert lib.eigenmodes(None, 3, None, None, None, None, None) == 1
     assert lib.ff_get_sizes(None, None, None, None) == 1
+    assert lib.ff_get_precond_layout(None, None, None) == 1
 
 
 def test_no_fallback_without_library(tmp_path):
