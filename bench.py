@@ -253,6 +253,25 @@ def run_ours(args):
             e2e.append(time.perf_counter() - t0)
     e2e_s = sum(e2e) / len(e2e)
 
+    # the consumer of the modes: their skinning weight fields at every particle
+    # and a linear blend skinning of them (Sec. 3.2, Eq. 1), wall time per call
+    Zs = (0.01 * torch.randn((32, 3, 4), generator=torch.Generator().manual_seed(5))).to(
+        dev, ctx.dtype)
+    sk_w, sk_l = [], []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Wsk = ctx.skinning_weights(X, modes.t())
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.lbs(X, Wsk, Zs)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if i >= args.warmup:
+            sk_w.append(t1 - t0)
+            sk_l.append(t2 - t1)
+    sk_w_ms, sk_l_ms = 1000 * sum(sk_w) / len(sk_w), 1000 * sum(sk_l) / len(sk_l)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -304,6 +323,9 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4) if achieved else None,
                      "traffic": tr, "algorithmic_bytes_per_launch": pre_bytes,
                      "avg_launch_ms": round(pre_ms, 5), "launches": cnt},
+        "skinning": {"points": n, "modes": 32, "weights_ms": round(sk_w_ms, 3),
+                     "lbs_ms": round(sk_l_ms, 4),
+                     "weights_points_per_s": round(n / (sk_w_ms * 1e-3))},
         "spmm": {"avg_launch_ms": round(stot / max(scnt, 1), 5), "launches": scnt,
                  "algorithmic_gbs": round(spmm_gbs, 1) if spmm_gbs else None,
                  "note": "average over both phases' launches, bytes counted at the second "

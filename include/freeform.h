@@ -185,6 +185,31 @@ ff_status eigenmodes(ff_ctx* ctx, int k, const ff_eig_opts* opts, const void* X0
  * before assemble_hessian.  Any pointer may be NULL. */
 ff_status ff_get_sizes(const ff_ctx* ctx, int64_t* n, int64_t* n1, int64_t* n2);
 
+/* ------------------------------------------------------------------ skinning weights and LBS */
+/* Skinning weight fields at arbitrary points (Sec. 3.2): W^j(X) = sum_k phi_k(X) c_k^j, with
+ * phi_k the corrected RKPM shape functions of the built cloud (the kernel, supports and
+ * linear basis of rkpm_build, Eqs. 6-11) evaluated at X, and c the nodal values of the
+ * fields -- typically the modes eigenmodes returned.
+ *   Q    device float[nq * 3] query points, x y z interleaved (any positions the
+ *        cloud's supports cover; the particles themselves included)
+ *   C    device, context precision, column-major n x m: column j = the nodal values of
+ *        field j in the caller's particle order (the layout eigenmodes writes)
+ *   W    device, context precision, row-major nq x m output: W[q * m + j] = W^j(Q_q)
+ * Needs rkpm_build.  A query point covered by fewer than four non-coplanar nodes (or by
+ * none) returns FF_ERR_SINGULAR_MOMENT naming it; m in 1..4096, nq < 2^26. */
+ff_status ff_skinning_weights(ff_ctx* ctx, const float* Q, int64_t nq, const void* C, int m,
+                              void* W);
+
+/* Linear blend skinning, Eq. 1: x_q = X_q + sum_j W_q^j Z_j [X_q; 1].
+ *   Q  device float[nq * 3] rest positions X_q
+ *   W  device, context precision, row-major nq x m weights (ff_skinning_weights)
+ *   Z  device, context precision, m affine transforms Z_j in R^{3x4}, row-major
+ *      (Z[12 j + 4 r + c] = row r, column c of Z_j)
+ *   x  device, context precision, nq x 3 output positions
+ * Needs a context (any stage); m in 1..4096, nq < 2^26. */
+ff_status ff_lbs_deform(ff_ctx* ctx, const float* Q, int64_t nq, const void* W, int m,
+                        const void* Z, void* x);
+
 /* Layout of the preconditioner's tensor-core copy of H_w (built by
  * assemble_hessian): row_blocks = ceil(n / 16) blocks of 16 rows, ksteps = the
  * 16-column steps over all blocks' column unions (each step: a 16 x 16 BF16

@@ -30,7 +30,8 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_apply_operators_noalloc", "ff_profile_enable", "ff_profile_read", "ff_launch_count",
            "ff_net_num_params", "ff_net_create", "ff_net_destroy", "ff_net_last_error",
            "ff_net_init", "ff_net_set_params", "ff_net_get_params", "ff_warmstart_features",
-           "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block"]
+           "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block",
+           "ff_skinning_weights", "ff_lbs_deform"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6, "setup": 7}
 
@@ -105,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     L.ff_net_loss_grad.argtypes = [vp, vp, vp, i64, vp, i32, ctypes.POINTER(dbl), vp]
     L.ff_net_train_step.argtypes = [vp, vp, vp, i64, vp, i32, ctypes.c_float, ctypes.POINTER(dbl)]
     L.ff_warmstart_block.argtypes = [vp, vp, i32, ctypes.POINTER(EigOpts), vp]
+    L.ff_skinning_weights.argtypes = [vp, vp, i64, vp, i32, vp]
+    L.ff_lbs_deform.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     del fp
     for name in EXPORTS:
         if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default",
@@ -299,6 +302,29 @@ class Context:
         YM = torch.empty_like(Xc) if YM is None else YM
         self._check(self.L.ff_apply_operators_noalloc(self.h, _ptr(Xc), m, _ptr(YH), _ptr(YM)))
         return YH.t(), YM.t()
+
+    # ---- skinning weights and linear blend skinning (Sec. 3.2, Eq. 1)
+    def skinning_weights(self, Q, C):
+        """W (nq, m) with W[q, j] = sum_k phi_k(Q_q) C[k, j]: Q a (nq, 3) float32 CUDA
+        tensor, C the (n, m) nodal values in the context dtype and the caller's
+        particle order (e.g. the modes eigenmodes returns)."""
+        import torch
+        Q = Q.contiguous()
+        Ct = C.t().contiguous()          # column-major n x m
+        nq, m = int(Q.shape[0]), int(Ct.shape[0])
+        W = torch.empty((nq, m), dtype=self.dtype, device=Q.device)
+        self._check(self.L.ff_skinning_weights(self.h, _ptr(Q), nq, _ptr(Ct), m, _ptr(W)))
+        return W
+
+    def lbs(self, Q, W, Z):
+        """x = X + sum_j W[:, j] Z_j [X; 1] (Eq. 1) for rest positions Q (nq, 3) float32,
+        weights W (nq, m) and affine transforms Z (m, 3, 4), both in the context dtype."""
+        import torch
+        Q, W, Z = Q.contiguous(), W.contiguous(), Z.contiguous()
+        nq, m = int(Q.shape[0]), int(W.shape[1])
+        x = torch.empty((nq, 3), dtype=self.dtype, device=Q.device)
+        self._check(self.L.ff_lbs_deform(self.h, _ptr(Q), nq, _ptr(W), m, _ptr(Z), _ptr(x)))
+        return x
 
 
 # module-level names matching the C ABI

@@ -232,6 +232,27 @@ ff_status ff_get_sizes(const ff_ctx* c, int64_t* n, int64_t* n1, int64_t* n2) {
   return FF_OK;
 }
 
+ff_status ff_skinning_weights(ff_ctx* c, const float* Q, int64_t nq, const void* C, int m,
+                              void* W) {
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "no cloud built");
+    FF_REQUIRE(nq >= 0 && nq < (1LL << 26) && m >= 1 && m <= 4096, FF_ERR_INVALID_ARG,
+               "bad sizes");
+    FF_REQUIRE(nq == 0 || (Q && C && W), FF_ERR_INVALID_ARG, "NULL array");
+    ff::skinning_weights(c, Q, nq, C, m, W);
+  });
+}
+
+ff_status ff_lbs_deform(ff_ctx* c, const float* Q, int64_t nq, const void* W, int m,
+                        const void* Z, void* x) {
+  return guarded(c, [&] {
+    FF_REQUIRE(nq >= 0 && nq < (1LL << 26) && m >= 1 && m <= 4096, FF_ERR_INVALID_ARG,
+               "bad sizes");
+    FF_REQUIRE(nq == 0 || (Q && W && Z && x), FF_ERR_INVALID_ARG, "NULL array");
+    ff::lbs_deform(c, Q, nq, W, m, Z, x);
+  });
+}
+
 ff_status ff_get_precond_layout(const ff_ctx* c, int64_t* row_blocks, int64_t* ksteps) {
   if (!c) return FF_ERR_INVALID_ARG;
   const bool built = c->stage >= 2 && c->tc_ksteps > 0;

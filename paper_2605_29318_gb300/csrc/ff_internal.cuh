@@ -152,6 +152,11 @@ struct ff_ctx {
   ff::Buf tc_hs;     // float[n] row sums of the rounded entries
   long long tc_ksteps = 0;
   ff::Buf hdiag_f32; // float[n] diag(H)
+  // skinning weights at query points (scratch of the last call)
+  ff::Buf sk_cnt;    // int[nq + 1]
+  ff::Buf sk_ptr;    // int64[nq + 1]
+  ff::Buf sk_idx;    // int[nq1]  covering nodes (internal order)
+  ff::Buf sk_phi;    // T[4 * nq1] shape functions and gradients
   ff::Buf wh;        // T[n] v_i (lambda_i + 4 mu_i)
   // device flags
   ff::Buf flags;     // DevFlags
@@ -191,6 +196,11 @@ void scan_counts_i32(const int* in, int* out, long long n, ff_ctx* c, Buf& tmp);
 void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a, int64_t n);
 void build_shape(ff_ctx* c);
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0);
+
+// skinning weight fields and linear blend skinning at query points (skinning.cu)
+void skinning_weights(ff_ctx* c, const float* Q, long long nq, const void* C, int m, void* W);
+void lbs_deform(ff_ctx* c, const float* Q, long long nq, const void* W, int m, const void* Z,
+                void* x);
 
 // operator application on internal-order row-major panels
 template <class T>

@@ -18,6 +18,7 @@
 //   4. scan, fill (atomic cursor per row), sort each row ascending
 //   5. transpose lists (node k -> rows i it covers, with the position of k in row i)
 #include "ff_internal.cuh"
+#include "grid.cuh"
 
 namespace ff {
 namespace {
@@ -84,26 +85,6 @@ __global__ void k_decode_red(const unsigned int* red, float* out) {
   for (int d = 0; d < 7; ++d) out[d] = ord2f(red[d]);
 }
 
-struct GridDev {
-  double o0, o1, o2, h;
-  int d0, d1, d2, b0, b1, b2;
-};
-
-__device__ __forceinline__ int cell_coord(float x, double o, double h, int dim) {
-  int c = (int)floor(((double)x - o) / h);
-  return min(max(c, 0), dim - 1);
-}
-
-__device__ __forceinline__ unsigned int spread3(unsigned int v) {  // 2 bits -> positions 0, 3
-  return (v & 1u) | ((v & 2u) << 2);
-}
-
-__device__ __forceinline__ long long cell_key(const GridDev& g, int cx, int cy, int cz) {
-  long long brick = ((long long)(cz >> 2) * g.b1 + (cy >> 2)) * g.b0 + (cx >> 2);
-  unsigned int m = spread3(cx & 3) | (spread3(cy & 3) << 1) | (spread3(cz & 3) << 2);
-  return brick * 64 + m;
-}
-
 __global__ void k_keys(const float* __restrict__ X, long long n, GridDev g,
                        int* __restrict__ key, int* __restrict__ cnt) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,20 +131,6 @@ __global__ void k_gather_particles(const int* __restrict__ perm, long long n,
   pos[j] = make_float4(X[3LL * i], X[3LL * i + 1], X[3LL * i + 2], a[i]);
   vol[j] = v[i];
   iperm[i] = (int)j;
-}
-
-// the coverage predicate: FP32 with a margin, FP64 (no FMA) inside the margin
-__device__ __forceinline__ bool covers(float4 X, float4 p) {
-  float dx = __fsub_rn(X.x, p.x), dy = __fsub_rn(X.y, p.y), dz = __fsub_rn(X.z, p.z);
-  float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-  float a2 = __fmul_rn(p.w, p.w);
-  if (d2 < a2 * 0.99999f) return true;
-  if (d2 > a2 * 1.00001f) return false;
-  double ex = __dsub_rn((double)X.x, (double)p.x);
-  double ey = __dsub_rn((double)X.y, (double)p.y);
-  double ez = __dsub_rn((double)X.z, (double)p.z);
-  double e2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-  return e2 < __dmul_rn((double)p.w, (double)p.w);
 }
 
 // MODE 0: count per row (atomic); MODE 1: fill rows through an atomic cursor

@@ -1,0 +1,176 @@
+// Device routines of the corrected RKPM shape functions at one evaluation point
+// (internal; shared by the cloud's own shape functions and by the skinning
+// weights at query points).  Sec. 3.2, Eqs. 7, 9-10; the basis written about
+// the evaluation point (see shape.cu).
+#pragma once
+
+#include "dfloat.cuh"
+#include "ff_internal.cuh"
+
+namespace ff {
+namespace rkpm {
+
+template <class C>
+__device__ __forceinline__ void bspline(C q, C& w, C& dwq) {
+  if (q <= C(0.5)) {
+    w = C(2.0 / 3.0) - C(4) * q * q + C(4) * q * q * q;
+    dwq = C(-8) + C(12) * q;
+  } else if (q <= C(1)) {
+    C t = C(1) - q;
+    w = C(4.0 / 3.0) * t * t * t;
+    dwq = C(-4) * t * t / q;
+  } else {
+    w = C(0);
+    dwq = C(0);
+  }
+}
+
+template <class C>
+__device__ __forceinline__ C warp_sum(C v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// symmetric 4x4 packed upper triangle: (0,0)(0,1)(0,2)(0,3)(1,1)(1,2)(1,3)(2,2)(2,3)(3,3)
+__device__ __forceinline__ int sidx(int r, int c) {
+  if (r > c) { int t = r; r = c; c = t; }
+  const int base[4] = {0, 4, 7, 9};
+  return base[r] + (c - r);
+}
+
+// Cholesky of a 4x4 SPD matrix (packed), returns false if a pivot is not
+// positive relative to the trace.  L stored dense row-major lower.
+template <class C>
+__device__ __forceinline__ bool chol4(const C* m, C* L, C rel_tol) {
+  C tr = m[0] + m[4] + m[7] + m[9];
+  for (int j = 0; j < 4; ++j) {
+    C s = m[sidx(j, j)];
+    for (int p = 0; p < j; ++p) s -= L[j * 4 + p] * L[j * 4 + p];
+    if (!(s > rel_tol * tr)) return false;
+    C d = sqrt(s);
+    L[j * 4 + j] = d;
+    for (int i = j + 1; i < 4; ++i) {
+      C t = m[sidx(i, j)];
+      for (int p = 0; p < j; ++p) t -= L[i * 4 + p] * L[j * 4 + p];
+      L[i * 4 + j] = t / d;
+    }
+    for (int i = 0; i < j; ++i) L[i * 4 + j] = C(0);
+  }
+  return true;
+}
+
+template <class C>
+__device__ __forceinline__ void chol4_solve(const C* L, const C* b, C* x) {
+  C y[4];
+  for (int i = 0; i < 4; ++i) {
+    C t = b[i];
+    for (int p = 0; p < i; ++p) t -= L[i * 4 + p] * y[p];
+    y[i] = t / L[i * 4 + i];
+  }
+  for (int i = 3; i >= 0; --i) {
+    C t = y[i];
+    for (int p = i + 1; p < 4; ++p) t -= L[p * 4 + i] * x[p];
+    x[i] = t / L[i * 4 + i];
+  }
+}
+
+// Evaluate one row in compute precision C, writing outputs of precision T.
+// Returns 0 ok, 1 singular, 2 ill-conditioned (only when check_cond).
+template <class C, class T>
+__device__ int shape_row(const float4* __restrict__ pos, long long s, long long e,
+                         const int* __restrict__ idx, float4 Xi, T* __restrict__ phi,
+                         T* __restrict__ dphi, long long n1, double cond_limit, bool check_cond) {
+  const int lane = threadIdx.x & 31;
+  const C xi = (C)Xi.x, yi = (C)Xi.y, zi = (C)Xi.z, si = (C)Xi.w;
+  C m[10], dm[3][10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    m[q] = C(0);
+    dm[0][q] = dm[1][q] = dm[2][q] = C(0);
+  }
+  for (long long t = s + lane; t < e; t += 32) {
+    float4 p = pos[idx[t]];
+    C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi, ak = (C)p.w;
+    C dist = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    C w, dwq;
+    bspline<C>(dist / ak, w, dwq);
+    C gs = -dwq / (ak * ak);  // grad_X varphi = gs * r
+    C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
+    C g[3] = {gs * r0, gs * r1, gs * r2};
+    int q = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b, ++q) {
+        C pp = P[a] * P[b];
+        m[q] += w * pp;
+        dm[0][q] += g[0] * pp;
+        dm[1][q] += g[1] * pp;
+        dm[2][q] += g[2] * pp;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    m[q] = warp_sum(m[q]);
+    dm[0][q] = warp_sum(dm[0][q]);
+    dm[1][q] = warp_sum(dm[1][q]);
+    dm[2][q] = warp_sum(dm[2][q]);
+  }
+  C L[16];
+  if (!chol4<C>(m, L, C(1e-12))) return 1;
+  if (check_cond) {
+    // 1-norm condition number from the explicit inverse
+    C inv_norm = C(0), m_norm = C(0);
+    for (int col = 0; col < 4; ++col) {
+      C ecol[4] = {C(0), C(0), C(0), C(0)}, x[4];
+      ecol[col] = C(1);
+      chol4_solve<C>(L, ecol, x);
+      C a1 = C(0), a2 = C(0);
+      for (int r = 0; r < 4; ++r) {
+        a1 += fabs(x[r]);
+        a2 += fabs(m[sidx(r, col)]);
+      }
+      inv_norm = fmax(inv_norm, a1);
+      m_norm = fmax(m_norm, a2);
+    }
+    if ((double)(inv_norm * m_norm) > cond_limit) return 2;
+  }
+  C Cv[4], dC[3][4];
+  {
+    C e0[4] = {C(1), C(0), C(0), C(0)};
+    chol4_solve<C>(L, e0, Cv);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    C rhs[4];
+    for (int r = 0; r < 4; ++r) {
+      C t = C(0);
+      for (int cc = 0; cc < 4; ++cc) t += dm[d][sidx(r, cc)] * Cv[cc];
+      rhs[r] = -t;
+    }
+    rhs[1 + d] += C(1) / si;
+    chol4_solve<C>(L, rhs, dC[d]);
+  }
+  for (long long t = s + lane; t < e; t += 32) {
+    float4 p = pos[idx[t]];
+    C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi, ak = (C)p.w;
+    C dist = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+    C w, dwq;
+    bspline<C>(dist / ak, w, dwq);
+    C gs = -dwq / (ak * ak);
+    C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
+    C PC = P[0] * Cv[0] + P[1] * Cv[1] + P[2] * Cv[2] + P[3] * Cv[3];
+    phi[t] = (T)(w * PC);
+    C g[3] = {gs * r0, gs * r1, gs * r2};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      C PdC = P[0] * dC[d][0] + P[1] * dC[d][1] + P[2] * dC[d][2] + P[3] * dC[d][3];
+      dphi[d * n1 + t] = (T)(g[d] * PC + w * PdC);
+    }
+  }
+  return 0;
+}
+
+}  // namespace rkpm
+}  // namespace ff

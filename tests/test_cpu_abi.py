@@ -84,6 +84,8 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.eigenmodes(None, 3, None, None, None, None, None) == 1
     assert lib.ff_get_sizes(None, None, None, None) == 1
     assert lib.ff_get_precond_layout(None, None, None) == 1
+    assert lib.ff_skinning_weights(None, None, 1, None, 1, None) == 1
+    assert lib.ff_lbs_deform(None, None, 1, None, 1, None, None) == 1
 
 
 def test_no_fallback_without_library(tmp_path):

@@ -527,3 +527,51 @@ def test_single_rows_match_the_full_assembly():
         np.testing.assert_allclose(h, H[k].data, rtol=1e-9, atol=1e-12 * np.abs(H[k].data).max())
         np.testing.assert_allclose(m, M[k].toarray()[0, cols], rtol=1e-9,
                                    atol=1e-12 * np.abs(M[k].data).max())
+
+
+# ---------------------------------------------------------------- skinning weights, LBS (Sec. 3.2, Eq. 1)
+def _query_points(c, count, seed):
+    """Particles of the cloud moved by up to a tenth of their support: points
+    every support rule still covers."""
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(c.n, count, replace=False)
+    Q = c.X[pick].astype(np.float64) + 0.1 * c.a[pick, None] * rng.uniform(-1, 1, (count, 3))
+    return Q.astype(np.float32)
+
+
+def test_skinning_weights_reproduce_constant_and_linear_fields():
+    """W of constant nodal values is constant (partition of unity, Eq. 8) and W
+    of the nodes' coordinates is the query point itself (linear reproduction):
+    the skinning fields inherit RKPM's consistency at arbitrary points."""
+    from oracle import skinning
+    c = synth.unit_cube(300, seed=11)
+    Q = _query_points(c, 40, 3)
+    W1 = skinning.weights(Q, c.X, c.a, np.ones((c.n, 1)))
+    assert np.abs(W1 - 1.0).max() < 1e-12
+    WX = skinning.weights(Q, c.X, c.a, c.X.astype(np.float32).astype(np.float64))
+    assert np.abs(WX - Q.astype(np.float64)).max() < 1e-12
+    # and the fields are linear in their nodal values
+    rng = np.random.default_rng(4)
+    C1, C2 = rng.standard_normal((c.n, 2)), rng.standard_normal((c.n, 2))
+    lhs = skinning.weights(Q, c.X, c.a, 2.0 * C1 - 3.0 * C2)
+    rhs = 2.0 * skinning.weights(Q, c.X, c.a, C1) - 3.0 * skinning.weights(Q, c.X, c.a, C2)
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(lhs).max()
+
+
+def test_lbs_closed_forms():
+    """Eq. 1 on closed forms: zero transforms leave X; a unit-weight field with
+    Z = [A | t] moves X to X + A X + t; two fields blend their transforms."""
+    from oracle import skinning
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (25, 3))
+    W = rng.uniform(0, 1, (25, 2))
+    assert np.array_equal(skinning.lbs(X, W, np.zeros((2, 3, 4))), X)
+    A, t = rng.standard_normal((3, 3)), rng.standard_normal(3)
+    Z = np.concatenate([A, t[:, None]], axis=1)[None]
+    x = skinning.lbs(X, np.ones((25, 1)), Z)
+    assert np.abs(x - (X + X @ A.T + t)).max() < 1e-13
+    t2 = rng.standard_normal(3)
+    Z2 = np.zeros((2, 3, 4))
+    Z2[0, :, 3], Z2[1, :, 3] = t, t2
+    x2 = skinning.lbs(X, W, Z2)
+    assert np.abs(x2 - (X + W[:, :1] * t + W[:, 1:] * t2)).max() < 1e-13
