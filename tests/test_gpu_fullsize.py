@@ -81,3 +81,23 @@ def test_modes_meet_the_residual_bar(torus50k):
     assert np.allclose(C[:, 0], C[0, 0]) and C[0, 0] > 0
     G = C.T @ MC
     assert np.abs(G - np.eye(32)).max() < 1e-9
+
+
+def test_sampled_skinning_weights(torus50k):
+    """The weight fields of the 32 full-size modes at sampled points between the
+    particles, against the oracle's shape functions at those points; and their
+    partition of unity with the constant mode (1e-10 of max |W|)."""
+    import torch
+    from oracle import skinning
+    c, ctx = torus50k["c"], torus50k["ctx"]
+    rng = np.random.default_rng(9)
+    pick = SAMPLE[:30]
+    Q = (c.X[pick].astype(np.float64)
+         + 0.1 * c.a[pick, None] * rng.uniform(-1, 1, (pick.size, 3))).astype(np.float32)
+    C = torus50k["modes"]
+    Wg = ctx.skinning_weights(torch.from_numpy(Q).cuda(),
+                              torch.from_numpy(np.ascontiguousarray(C)).cuda()).cpu().numpy()
+    Wo = skinning.weights(Q, c.X, c.a, C)
+    assert np.abs(Wg - Wo).max() <= 1e-10 * np.abs(Wo).max()
+    # the constant mode's field is constant
+    assert np.abs(Wg[:, 0] - C[0, 0]).max() <= 1e-10 * abs(C[0, 0])
