@@ -320,14 +320,8 @@ bool cheb_tc_build(ff_ctx* c) {
   int* nks = reinterpret_cast<int*>(c->scratch[4].ensure(sizeof(int) * 3 * (size_t)nblk));
   int* lo = nks + nblk;
   int* words = lo + nblk;
-  static bool attr = false;
-  if (!attr) {
-    FF_CUDA(cudaFuncSetAttribute(k_tc_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(unsigned) * kTcMaxWords)));
-    FF_CUDA(cudaFuncSetAttribute(k_tc_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * sizeof(unsigned) * kTcMaxWords)));
-    attr = true;
-  }
+  set_max_dyn_smem((const void*)k_tc_count, (int)(sizeof(unsigned) * kTcMaxWords));
+  set_max_dyn_smem((const void*)k_tc_fill, (int)(2 * sizeof(unsigned) * kTcMaxWords));
   (k_tc_count<<<nblk, 256, sizeof(unsigned) * kTcMaxWords, st>>>(
        c->a_ptr.as<long long>(), c->a_col.as<int>(), (int)n, nks, lo, words),
    ::ff::note_launch());

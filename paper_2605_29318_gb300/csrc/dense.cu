@@ -1073,26 +1073,10 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.C = p; p += n * no;
   w.U = p; p += n * no;
   w.keep = reinterpret_cast<int*>(p);
-  static bool attr_mo = false;
-  if (!attr_mo) {
-    FF_CUDA(cudaFuncSetAttribute(k_rr_momentum<R, T, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem));
-    attr_mo = true;
-  }
-  static bool attr = false;
-  if (!attr) {
-    FF_CUDA(cudaFuncSetAttribute(k_rr_tridiag<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kMaxDynSmem));
-    FF_CUDA(cudaFuncSetAttribute(k_rr_house_cluster<R>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem));
-    FF_CUDA(cudaFuncSetAttribute(k_rr_invit_sm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kMaxDynSmem));
-    FF_CUDA(cudaFuncSetAttribute(k_rr_cholqr<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kMaxDynSmem));
-    FF_CUDA(cudaFuncSetAttribute(k_rr_backtransform<R, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynSmem));
-    attr = true;
-  }
+  for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
+                         (const void*)k_rr_house_cluster<R>, (const void*)k_rr_invit_sm<R>,
+                         (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>})
+    set_max_dyn_smem(fn, (int)kMaxDynSmem);
   const size_t tri_bytes = sizeof(R) * n * n;
   const size_t tri2_bytes = sizeof(R) * (n * n + 2 * n * no + no * no);
   const int tri_smem = tri2_bytes <= kMaxDynSmem ? 2 : tri_bytes <= kMaxDynSmem ? 1 : 0;

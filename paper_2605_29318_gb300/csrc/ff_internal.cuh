@@ -184,6 +184,10 @@ struct ProfScope {
 // ---------------------------------------------------------------- helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// raise a kernel's dynamic shared-memory limit on the current device (once per
+// kernel, device and size; the attribute belongs to the device's context)
+void set_max_dyn_smem(const void* fn, int bytes);
+
 void reset_flags(ff_ctx* c);
 DevFlags read_flags(ff_ctx* c);
 

@@ -1257,17 +1257,10 @@ void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q
   const int sp = split < 0 ? q : split;
   if (p % 4 == 0 && q % 4 == 0 && lda % 4 == 0 && ldc % 4 == 0 && sp % 4 == 0 && off2 % 4 == 0 &&
       al16(A) && al16(C) && smem <= 200 * 1024) {
-    static bool rt_attr[3][2] = {};
-    const int ti = std::is_same_v<T, float> ? 0 : std::is_same_v<T, double> ? 1 : 2;
-    if (smem > 48 * 1024 && !rt_attr[ti][w40]) {
-      if (w40)
-        FF_CUDA(cudaFuncSetAttribute(k_block_update_rt<T, 40>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      else
-        FF_CUDA(cudaFuncSetAttribute(k_block_update_rt<T, 32>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      rt_attr[ti][w40] = true;
-    }
+    if (smem > 48 * 1024)
+      set_max_dyn_smem(w40 ? (const void*)k_block_update_rt<T, 40>
+                           : (const void*)k_block_update_rt<T, 32>,
+                       200 * 1024);
     const int TD = TW / 4, RG = 256 / TD;
     const long long rows_per_block = (long long)RG * 4;
     dim3 grid((unsigned)std::min<long long>((n + rows_per_block - 1) / rows_per_block, 152LL * 8),
@@ -1284,17 +1277,9 @@ void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q
     return;
   }
   const int rpb = 8;  // rows per block (one TW-thread group each)
-  static bool attr_set[3][2] = {};
-  const int tix = std::is_same_v<T, float> ? 0 : std::is_same_v<T, double> ? 1 : 2;
-  if (smem > 48 * 1024 && !attr_set[tix][w40]) {
-    if (w40)
-      FF_CUDA(cudaFuncSetAttribute(k_block_update<T, 40>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    else
-      FF_CUDA(cudaFuncSetAttribute(k_block_update<T, 32>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_set[tix][w40] = true;
-  }
+  if (smem > 48 * 1024)
+    set_max_dyn_smem(w40 ? (const void*)k_block_update<T, 40> : (const void*)k_block_update<T, 32>,
+                     227 * 1024);
   dim3 grid((unsigned)std::min<long long>((n + rpb - 1) / rpb, 152LL * 16),
             (unsigned)((q + TW - 1) / TW));
   if (w40)

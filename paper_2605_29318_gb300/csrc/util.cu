@@ -1,9 +1,24 @@
 // Scans, device-flag helpers, launch counting and the event profiler.
 #include <atomic>
+#include <mutex>
+#include <set>
+#include <tuple>
 
 #include "ff_internal.cuh"
 
 namespace ff {
+
+void set_max_dyn_smem(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;
+  int dev = 0;
+  FF_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(fn, dev, bytes);
+  if (done.count(key)) return;
+  FF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert(key);
+}
 
 thread_local ff_ctx* g_ctx = nullptr;
 
