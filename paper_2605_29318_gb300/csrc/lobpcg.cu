@@ -375,6 +375,9 @@ struct Phase {
   double stall_below = INFINITY;   // iterations only count as stalled below this residual
   int best_slot = 22;              // workspace slot that keeps the best block (dense n x nb)
   bool rr_fp32 = false;            // Rayleigh-Ritz in FP32 (else FP64)
+  bool update_products = false;    // H X', M X' by the block update instead of a
+                                   // fresh block product (a phase that hands over
+                                   // well above its rounding floor)
   bool have_best = false;          // out: the best-block slot holds a block
 };
 
@@ -647,13 +650,19 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     const int nxt = 1 - cur;
     // X' = S Y, P' = S Z; H P', M P' from the old products; (H X', M X') recomputed
     // from X' itself so that the residual seen by the solver is that of the
-    // stored X' (updated products drift from the stored block in FP32)
+    // stored X' (updated products drift from the stored block in FP32) -- or,
+    // in a phase that hands over well above that drift, updated as well
     block_update<T>(st, s.S[cur], ld, ns, s.YZ, 2 * nb, s.S[nxt], ld, n, T(0), nb, 2 * nb);
-    block_update<T>(st, s.HS[cur], ld, ns, s.YZ + nb, nb, s.HS[nxt] + 2 * nb, ld, n, T(0), -1, 0,
-                    2 * nb);
-    block_update<T>(st, s.MS[cur], ld, ns, s.YZ + nb, nb, s.MS[nxt] + 2 * nb, ld, n, T(0), -1, 0,
-                    2 * nb);
-    s.spmm(s.S[nxt], s.HS[nxt], s.MS[nxt], nb);
+    if (ph.update_products) {
+      block_update<T>(st, s.HS[cur], ld, ns, s.YZ, 2 * nb, s.HS[nxt], ld, n, T(0), nb, 2 * nb);
+      block_update<T>(st, s.MS[cur], ld, ns, s.YZ, 2 * nb, s.MS[nxt], ld, n, T(0), nb, 2 * nb);
+    } else {
+      block_update<T>(st, s.HS[cur], ld, ns, s.YZ + nb, nb, s.HS[nxt] + 2 * nb, ld, n, T(0), -1,
+                      0, 2 * nb);
+      block_update<T>(st, s.MS[cur], ld, ns, s.YZ + nb, nb, s.MS[nxt] + 2 * nb, ld, n, T(0), -1,
+                      0, 2 * nb);
+      s.spmm(s.S[nxt], s.HS[nxt], s.MS[nxt], nb);
+    }
     cur = nxt;
     has_p = true;
   }
@@ -738,6 +747,7 @@ ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
   p32.gain = 0.7;
   p32.stall_below = 1e-2;
   p32.rr_fp32 = true;
+  p32.update_products = true;
   p32.best_slot = 21;
   const float* X0f = nullptr;
   if (X0) {  // the caller's FP64 start block, rounded
