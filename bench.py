@@ -132,6 +132,16 @@ def cpu_baseline_json():
             "max_residual": res}
 
 
+def max_over_ranks(values, device):
+    """The largest of each value over all ranks of the process group (the step
+    time of a replica run is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -235,9 +245,7 @@ def run_ours(args):
     n, n1, n2 = ctx.sizes()
     ms = sum(times) / len(times)
     if world > 1:
-        t = torch.tensor([ms, wms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, wms = float(t[0].item()), float(t[1].item())
+        ms, wms = max_over_ranks([ms, wms], dev)
         dist.barrier()
 
     # end to end through the public call on host buffers (H2D + D2H inside)
