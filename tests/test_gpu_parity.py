@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (fixed by the method's specification of this build):
+Tolerances (fixed by the method's specification):
   neighbour lists bit-exact; shape functions 1e-5 relative to the row's
   max |phi| (FP32); H_w, M entries 1e-5 relative to the row max (FP32);
   eigenvalues 1e-5 relative (non-constant modes); largest M-principal angle
