@@ -7,10 +7,15 @@ The metric is the time to k modes at relative residual 1e-6: `value` is the
 plain path (seeded random start block); `warm` times the same step started
 from the trained warm-start network (features and inference included).  L2 is
 flushed (a 256 MB write) before every timed step; each step is timed with CUDA
-events on the library's stream.  Prints one JSON line.
+events on the library's stream.  The line also reports the end-to-end time
+from host arrays (`e2e`), the roofline of the preconditioner step, the stage
+split, and the evaluation of the modes' skinning weight fields at every
+particle with a linear blend skinning of them (`skinning`).  Prints one JSON
+line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--prec fp64|fp32] [--tol T]
+                  [--prec fp64|fp32] [--tol T] [--cheb D] [--cheb-fp64 D]
+                  [--fp32-phase 0|1] [--fp32-tol T] [--precond-tc 0|1]
 
 With N > 1 (torchrun, one process per GPU) every rank solves its own object
 (replicas; the path has no cross-GPU exchange) and the reported time is the
