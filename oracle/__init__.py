@@ -15,6 +15,11 @@ What it computes, in plain FP64 (citations are to the FreeForm paper):
                    (Sec. 3.2, Eq. 14), plus the Neo-Hookean potential of
                    Eq. 16 evaluated through the deformation gradient of the
                    proof of Prop. 1 (Supp. Sec. C) for finite-difference pins.
+* ``twoset``    -- the paper's own two-set discretisation (Supp. Sec. B "RKPM
+                   construction"): farthest-point kernel centres chosen from
+                   grid quadrature points, radii reaching two other centres,
+                   Gaussian-kernel shape functions at the quadrature points
+                   and the K x K H_w and M.
 * ``eigen``     -- the lowest-k generalized eigenpairs of H_w c = lambda M c
                    (Sec. 3.2, Eq. 15; Supp. Sec. B "Eigenanalysis") by a dense
                    LAPACK solve, a sparse shift-invert tier, residuals and
@@ -22,7 +27,8 @@ What it computes, in plain FP64 (citations are to the FreeForm paper):
 * ``jacobi``    -- a hand-written cyclic Jacobi eigensolver used only to pin the
                    LAPACK call on tiny inputs.
 
-Every function here is pinned by ``tests/test_oracle_pins.py`` against facts
+Every function here is pinned by ``tests/test_oracle_pins.py`` (``twoset`` by
+``tests/test_oracle_twoset.py``) against facts
 the paper and the mathematics fix (reproducing conditions, finite differences
 of the energy, invariances, brute force).  Equation numbers follow the order in
 which LaTeX numbers the paper's displayed equations (Eq. 1 = the LBS map).

@@ -75,6 +75,35 @@ def torus(n=50000, R=0.5, r=0.2, seed=2, support=2.0, E=1e6, nu=0.4, k=32):
     return _finish(X, 2.0 * math.pi ** 2 * R * r * r, support, E, nu, k, f"torus{n}")
 
 
+def inside_grid(lo, hi, h, inside):
+    """Quadrature points of the paper's two-set construction: the centres of a
+    uniform grid of spacing h over the box [lo, hi], those outside the solid
+    dropped, each with volume h^3 (Supp. Sec. B samples the object's bounding
+    box on a grid and rejects outside points).  Returns (X float32 (n, 3),
+    v float32 (n,)); points ordered x fastest, then y, then z."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    m = np.maximum(np.ceil((hi - lo) / h - 1e-9).astype(np.int64), 1)
+    axes = [lo[d] + (np.arange(m[d]) + 0.5) * h for d in range(3)]
+    Z, Y, Xg = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    P = np.stack([Xg.ravel(), Y.ravel(), Z.ravel()], 1)
+    P = P[inside(P)]
+    return P.astype(np.float32), np.full(P.shape[0], h ** 3, dtype=np.float32)
+
+
+def cube_grid(m=16):
+    """The unit cube's quadrature grid: m^3 cell centres, volume 1/m^3 each."""
+    return inside_grid([0, 0, 0], [1, 1, 1], 1.0 / m, lambda P: np.ones(P.shape[0], bool))
+
+
+def torus_grid(h=0.02, R=0.5, r=0.2):
+    """Inside grid of the solid torus of ``torus`` (exact volume 2 pi^2 R r^2)."""
+    def inside(P):
+        rho = np.sqrt(P[:, 0] ** 2 + P[:, 1] ** 2)
+        return (rho - R) ** 2 + P[:, 2] ** 2 < r * r
+    return inside_grid([-R - r, -R - r, -r], [R + r, R + r, r], h, inside)
+
+
 def _random_rotation(rng):
     q = rng.normal(size=4)
     q /= np.linalg.norm(q)
