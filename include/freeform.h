@@ -6,6 +6,9 @@
  *
  *   rkpm_build        support neighbours and corrected RKPM shape functions
  *                     (Sec. 3.2 "RKPM", Eqs. 6-11)
+ *   rkpm_build_twoset the same for the paper's two-set construction: kernel
+ *                     centres chosen from quadrature points by farthest-point
+ *                     sampling, Gaussian kernels (Supp. Sec. B "RKPM construction")
  *   assemble_hessian  weight-space Neo-Hookean Hessian H_w (Prop. 1) and the
  *                     RKPM mass matrix M (Sec. 3.2, Eq. 14)
  *   eigenmodes        the k lowest generalized eigenpairs of H_w c = lambda M c
@@ -22,9 +25,9 @@
  *   torch.cuda.current_stream().cuda_stream).  Arguments documented "host" are
  *   ordinary host memory.  The caller owns every buffer it passes; the context
  *   owns every internal device buffer and frees them in ff_destroy.
- * - Calls are state-ordered: rkpm_build, then assemble_hessian, then
- *   eigenmodes; out of order they return FF_ERR_STATE.  A new rkpm_build
- *   discards the previous cloud, matrices and modes.
+ * - Calls are state-ordered: rkpm_build (or rkpm_build_twoset), then
+ *   assemble_hessian, then eigenmodes; out of order they return FF_ERR_STATE.
+ *   A new build discards the previous cloud, matrices and modes.
  * - Calls synchronise the context's stream before returning (results are
  *   ready on return); host outputs are written before return.
  * - Particle order: the library reorders particles internally (by spatial
@@ -98,6 +101,45 @@ const char* ff_version(void);
 ff_status rkpm_build(ff_ctx* ctx, const float* particles, const float* volumes,
                      const float* support, int64_t n);
 
+/* ----------------------------------------------------------- rkpm_build_twoset
+ * Supp. Sec. B "RKPM construction" with the kernel of Sec. 3.2: two point sets.
+ * The n given points are quadrature points X_i with volumes v_i (an inside grid
+ * of the object, or its own points).  K kernel centres p_k are chosen among
+ * them by farthest-point sampling: the first is point `start`, each next one
+ * the point farthest from those chosen, ties to the lowest index.  Centre k has
+ * radius r_k = distance to its second-nearest other centre, raw kernel
+ * exp(-||X - p_k||^2 / r_k^2) and covers X iff ||X - p_k||^2 < trunc^2 r_k^2
+ * (every X when trunc = 0).  Squared distances, their comparisons and r_k are
+ * the FP64 values of ((dx*dx + dy*dy) + dz*dz) on the FP32 inputs without fused
+ * multiply-add, r_k = sqrt in FP64 (bit-exact with the oracle).  The shape
+ * functions (corrected, linear basis, Eqs. 7, 9-10) are evaluated at the
+ * quadrature points.  Afterwards the unknowns are the K centres: assemble_hessian
+ * takes per-point materials of length n, eigenmodes returns K x k modes in
+ * the centres' order of choice, and ff_skinning_weights evaluates the fields
+ * with these Gaussian shape functions.  The warm start takes nodal clouds only.
+ *
+ *   points   device, float[n][3] row-major quadrature points
+ *   volumes  device, float[n] quadrature volumes v_i > 0
+ *   n        number of points, 4 <= n <= 2^31 - 1
+ *   K        number of centres, 4 <= K <= n
+ *   trunc    cut radius in units of r_k (> 0), or 0 for the untruncated Gaussian
+ *            (every centre at every point: n K pairs)
+ *   start    index of the first centre, 0 <= start < n
+ *
+ * Errors: FF_ERR_INVALID_ARG on NULL pointers, sizes out of range, a
+ * non-finite position or non-positive volume (message names the first), or
+ * fewer than K distinct positions; FF_ERR_SINGULAR_MOMENT if fewer than four
+ * non-coplanar centres cover some quadrature point (message names it). */
+ff_status rkpm_build_twoset(ff_ctx* ctx, const float* points, const float* volumes, int64_t n,
+                            int32_t K, double trunc, int64_t start);
+
+/* The two-set cloud: n_points quadrature points, K centres, centres int64[K]
+ * the index of the point chosen as centre k (in the order of choice), radii
+ * double[K] the r_k.  Host outputs, any may be NULL; FF_ERR_STATE without a
+ * two-set cloud. */
+ff_status ff_get_twoset(const ff_ctx* ctx, int64_t* n_points, int32_t* K, int64_t* centres,
+                        double* radii);
+
 /* ------------------------------------------------------------ assemble_hessian
  * Prop. 1: (H_w)_kl = sum_i v_i (lambda_i + 4 mu_i) grad phi_k(X_i) . grad phi_l(X_i)
  * Eq. 14:  M_kl     = sum_i v_i phi_k(X_i) phi_l(X_i)
@@ -105,8 +147,9 @@ ff_status rkpm_build(ff_ctx* ctx, const float* particles, const float* volumes,
  * diagonal of H_w is set to minus the sum of its row's off-diagonal entries,
  * so H_w 1 = 0 holds exactly in the stored matrix.
  *
- *   E, nu   device, float[n] per-particle Young's modulus and Poisson ratio in
- *           the caller's order, or NULL to use the uniform E0 / nu0
+ *   E, nu   device, float[n] per-particle (two-set: per quadrature point)
+ *           Young's modulus and Poisson ratio in the caller's order, or NULL to
+ *           use the uniform E0 / nu0
  *   E0, nu0 uniform material (used where the array is NULL); E > 0, 0 <= nu < 0.5 */
 ff_status assemble_hessian(ff_ctx* ctx, const float* E, const float* nu, double E0,
                            double nu0);
@@ -180,9 +223,10 @@ ff_status eigenmodes(ff_ctx* ctx, int k, const ff_eig_opts* opts, const void* X0
  * Copies of the internal results, in the caller's particle order, for parity
  * checks against an independent implementation.  All outputs are host memory. */
 
-/* Sizes after rkpm_build / assemble_hessian: n, n1 = number of (i, k) support
- * pairs, n2 = stored entries of H_w (= of M), including the diagonal; n2 = 0
- * before assemble_hessian.  Any pointer may be NULL. */
+/* Sizes after rkpm_build / assemble_hessian: n = unknowns (particles, or the K
+ * centres of a two-set cloud), n1 = number of (i, k) support pairs, n2 = stored
+ * entries of H_w (= of M), including the diagonal; n2 = 0 before
+ * assemble_hessian.  Any pointer may be NULL. */
 ff_status ff_get_sizes(const ff_ctx* ctx, int64_t* n, int64_t* n1, int64_t* n2);
 
 /* ------------------------------------------------------------------ skinning weights and LBS */
@@ -218,8 +262,9 @@ ff_status ff_lbs_deform(ff_ctx* ctx, const float* Q, int64_t nq, const void* W, 
  * preconditioner runs on the sparse FP32 values.  Any pointer may be NULL. */
 ff_status ff_get_precond_layout(const ff_ctx* ctx, int64_t* row_blocks, int64_t* ksteps);
 
-/* Neighbour lists as CSR: ptr int64[n+1], idx int32[n1]; row i lists the nodes
- * k covering X_i, ascending.  phi double[n1] and dphi double[3*n1] (x block,
+/* Neighbour lists as CSR: ptr int64[rows+1], idx int32[n1] with rows = n (or
+ * the n_points quadrature points of a two-set cloud); row i lists the nodes
+ * (centres) k covering X_i, ascending.  phi double[n1] and dphi double[3*n1] (x block,
  * then y, then z) are the shape functions phi_k(X_i) and their gradients,
  * aligned with idx; phi / dphi may be NULL. */
 ff_status ff_export_rkpm(const ff_ctx* ctx, int64_t* ptr, int32_t* idx, double* phi,

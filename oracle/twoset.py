@@ -54,7 +54,8 @@ def farthest_point_sampling(X, K, start=0):
     """Indices of K points of X chosen greedily: each next point is the one
     farthest from those already chosen (Supp. Sec. B).  Returns int64 (K,) in
     the order of choice.  Ties go to the lowest index (``np.argmax`` returns
-    the first maximum)."""
+    the first maximum).  Raises ValueError when the points hold fewer than K
+    distinct positions (the farthest remaining point is at distance zero)."""
     Xd = np.asarray(X, dtype=np.float32).astype(F64)
     n = Xd.shape[0]
     if not 0 < K <= n:
@@ -64,6 +65,8 @@ def farthest_point_sampling(X, K, start=0):
     dist = _d2(Xd, Xd[start])                  # squared distance to the chosen set
     for j in range(1, K):
         nxt = int(np.argmax(dist))
+        if dist[nxt] == 0.0:
+            raise ValueError("fewer than K distinct points")
         chosen[j] = nxt
         dist = np.minimum(dist, _d2(Xd, Xd[nxt]))
     return chosen
@@ -109,7 +112,9 @@ def covering(Xq, P, r, trunc):
     if trunc is None:
         ptr = np.arange(n + 1, dtype=np.int64) * K
         return ptr, np.tile(np.arange(K, dtype=np.int32), n)
-    lim = (float(trunc) ** 2) * np.asarray(r, F64) ** 2
+    t = float(trunc)
+    rr = np.asarray(r, F64)
+    lim = (t * t) * (rr * rr)
     cols = [np.nonzero(_d2(Pd, x) < lim)[0].astype(np.int32) for x in Xd]
     ptr = np.zeros(n + 1, dtype=np.int64)
     ptr[1:] = np.cumsum([c.size for c in cols])

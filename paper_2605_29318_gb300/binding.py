@@ -31,7 +31,7 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_net_num_params", "ff_net_create", "ff_net_destroy", "ff_net_last_error",
            "ff_net_init", "ff_net_set_params", "ff_net_get_params", "ff_warmstart_features",
            "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block",
-           "ff_skinning_weights", "ff_lbs_deform"]
+           "ff_skinning_weights", "ff_lbs_deform", "rkpm_build_twoset", "ff_get_twoset"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6, "setup": 7}
 
@@ -108,6 +108,8 @@ def load_library(path: str = LIB_PATH):
     L.ff_warmstart_block.argtypes = [vp, vp, i32, ctypes.POINTER(EigOpts), vp]
     L.ff_skinning_weights.argtypes = [vp, vp, i64, vp, i32, vp]
     L.ff_lbs_deform.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+    L.rkpm_build_twoset.argtypes = [vp, vp, vp, i64, i32, dbl, i64]
+    L.ff_get_twoset.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), vp, vp]
     del fp
     for name in EXPORTS:
         if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default",
@@ -187,6 +189,27 @@ class Context:
         self._check(self.L.rkpm_build(self.h, _ptr(particles), _ptr(volumes), _ptr(support),
                                       self.n))
 
+    def rkpm_build_twoset(self, points, volumes, K: int, trunc: float = 3.0, start: int = 0):
+        """The two-set construction: quadrature points (n, 3) and volumes (n,), float32
+        CUDA tensors; K farthest-point centres from point ``start``; Gaussian kernels
+        cut at ``trunc`` r_k (0: untruncated).  The unknowns are then the K centres."""
+        for t in (points, volumes):
+            assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+        self._keep = (points, volumes)
+        self._check(self.L.rkpm_build_twoset(self.h, _ptr(points), _ptr(volumes),
+                                             int(points.shape[0]), int(K), float(trunc),
+                                             int(start)))
+        self.n = int(K)
+
+    def twoset(self):
+        """(n_points, centres int64 (K,), radii float64 (K,)) of a two-set cloud."""
+        npt, K = ctypes.c_int64(), ctypes.c_int32()
+        self._check(self.L.ff_get_twoset(self.h, ctypes.byref(npt), ctypes.byref(K), None, None))
+        cen = np.zeros(K.value, np.int64)
+        rad = np.zeros(K.value, np.float64)
+        self._check(self.L.ff_get_twoset(self.h, None, None, cen.ctypes.data, rad.ctypes.data))
+        return npt.value, cen, rad
+
     def assemble_hessian(self, E=None, nu=None, E0: float = 1e5, nu0: float = 0.45):
         """E, nu: per-particle float32 CUDA tensors or None (uniform E0, nu0)."""
         self._check(self.L.assemble_hessian(self.h, _ptr(E), _ptr(nu), float(E0), float(nu0)))
@@ -264,6 +287,9 @@ class Context:
 
     def export_rkpm(self):
         n, n1, _ = self.sizes()
+        npt = ctypes.c_int64()
+        if self.L.ff_get_twoset(self.h, ctypes.byref(npt), None, None, None) == FF_OK:
+            n = npt.value                # rows: the quadrature points
         ptr = np.zeros(n + 1, np.int64)
         idx = np.zeros(n1, np.int32)
         phi = np.zeros(n1, np.float64)
@@ -330,6 +356,10 @@ class Context:
 # module-level names matching the C ABI
 def rkpm_build(ctx: Context, particles, volumes, support):
     return ctx.rkpm_build(particles, volumes, support)
+
+
+def rkpm_build_twoset(ctx: Context, points, volumes, K, trunc=3.0, start=0):
+    return ctx.rkpm_build_twoset(points, volumes, K, trunc, start)
 
 
 def assemble_hessian(ctx: Context, E=None, nu=None, E0=1e5, nu0=0.45):

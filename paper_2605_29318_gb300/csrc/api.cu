@@ -140,10 +140,29 @@ ff_status rkpm_build(ff_ctx* c, const float* particles, const float* volumes, co
     FF_REQUIRE(n >= 1 && n <= 0x7fffffffLL, FF_ERR_INVALID_ARG, "n out of range");
     c->stage = 0;
     c->n = n;
+    c->nq = n;
+    c->twoset = false;
     c->n1 = c->n2 = 0;
     ff::ProfScope ps(ff::kProfBuild);
     ff::build_neighbours(c, particles, volumes, support, n);
     ff::build_shape(c);
+    c->stage = 1;
+  });
+}
+
+ff_status rkpm_build_twoset(ff_ctx* c, const float* points, const float* volumes, int64_t n,
+                            int32_t K, double trunc, int64_t start) {
+  return guarded(c, [&] {
+    FF_REQUIRE(points && volumes, FF_ERR_INVALID_ARG, "NULL input pointer");
+    FF_REQUIRE(n >= 4 && n <= 0x7fffffffLL, FF_ERR_INVALID_ARG, "n out of range");
+    FF_REQUIRE(K >= 4 && (int64_t)K <= n, FF_ERR_INVALID_ARG, "K must lie in 4..n");
+    FF_REQUIRE(std::isfinite(trunc) && trunc >= 0.0, FF_ERR_INVALID_ARG,
+               "trunc must be finite and >= 0 (0: untruncated)");
+    FF_REQUIRE(start >= 0 && start < n, FF_ERR_INVALID_ARG, "start out of range");
+    c->stage = 0;
+    c->n1 = c->n2 = 0;
+    ff::ProfScope ps(ff::kProfBuild);
+    ff::build_twoset(c, points, volumes, n, K, trunc, start);
     c->stage = 1;
   });
 }
@@ -232,6 +251,21 @@ ff_status ff_get_sizes(const ff_ctx* c, int64_t* n, int64_t* n1, int64_t* n2) {
   return FF_OK;
 }
 
+ff_status ff_get_twoset(const ff_ctx* cc, int64_t* n_points, int32_t* K, int64_t* centres,
+                        double* radii) {
+  ff_ctx* c = const_cast<ff_ctx*>(cc);
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1 && c->twoset, FF_ERR_STATE, "no two-set cloud built");
+    if (n_points) *n_points = c->nq;
+    if (K) *K = (int32_t)c->n;
+    FF_CUDA(cudaStreamSynchronize(c->stream));
+    if (centres)
+      FF_CUDA(cudaMemcpy(centres, c->centre_idx.p, sizeof(int64_t) * c->n,
+                         cudaMemcpyDeviceToHost));
+    if (radii) FF_CUDA(cudaMemcpy(radii, c->crad.p, sizeof(double) * c->n, cudaMemcpyDeviceToHost));
+  });
+}
+
 ff_status ff_skinning_weights(ff_ctx* c, const float* Q, int64_t nq, const void* C, int m,
                               void* W) {
   return guarded(c, [&] {
@@ -268,10 +302,8 @@ ff_status ff_export_rkpm(const ff_ctx* cc, int64_t* ptr, int32_t* idx, double* p
     FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "no cloud built");
     FF_REQUIRE(ptr && idx, FF_ERR_INVALID_ARG, "NULL output");
     FF_CUDA(cudaStreamSynchronize(c->stream));
-    const size_t n = c->n, n1 = c->n1;
-    auto perm = to_host<int>(c->perm, n);
-    auto iperm = to_host<int>(c->iperm, n);
-    auto p = to_host<long long>(c->nbr_ptr, n + 1);
+    const size_t n = c->n, n1 = c->n1, nq = c->nq;
+    auto p = to_host<long long>(c->nbr_ptr, nq + 1);
     auto ix = to_host<int>(c->nbr_idx, n1);
     std::vector<double> ph, dph;
     if (c->prec == FF_PREC_FP64) {
@@ -281,6 +313,15 @@ ff_status ff_export_rkpm(const ff_ctx* cc, int64_t* ptr, int32_t* idx, double* p
       ph = to_host_f64<float>(c->phi, n1);
       dph = to_host_f64<float>(c->dphi, 3 * n1);
     }
+    if (c->twoset) {  // rows and centres are already in the caller's order
+      std::copy(p.begin(), p.end(), ptr);
+      std::copy(ix.begin(), ix.end(), idx);
+      if (phi) std::copy(ph.begin(), ph.end(), phi);
+      if (dphi) std::copy(dph.begin(), dph.end(), dphi);
+      return;
+    }
+    auto perm = to_host<int>(c->perm, n);
+    auto iperm = to_host<int>(c->iperm, n);
     remap_csr(perm, iperm, p, ix, {&ph, &dph}, ptr, idx, {phi, dphi}, {n1, n1}, {n1, n1}, {1, 3});
   });
 }
@@ -334,6 +375,7 @@ ff_status ff_apply_operators(ff_ctx* c, const void* X, int m, void* YH, void* YM
 ff_status ff_warmstart_features(ff_ctx* c, float* feat) {
   return guarded(c, [&] {
     FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "features before rkpm_build");
+    FF_REQUIRE(!c->twoset, FF_ERR_STATE, "the warm start takes a nodal cloud (rkpm_build)");
     FF_REQUIRE(feat, FF_ERR_INVALID_ARG, "feat must not be NULL");
     ff::warmstart_features(c, feat);
     FF_CUDA(cudaStreamSynchronize(c->stream));
@@ -343,6 +385,7 @@ ff_status ff_warmstart_features(ff_ctx* c, float* feat) {
 ff_status ff_warmstart_block(ff_ctx* c, ff_net* net, int k, const ff_eig_opts* opts, void* X0) {
   return guarded(c, [&] {
     FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "warm start before rkpm_build");
+    FF_REQUIRE(!c->twoset, FF_ERR_STATE, "the warm start takes a nodal cloud (rkpm_build)");
     FF_REQUIRE(net && X0, FF_ERR_INVALID_ARG, "net and X0 must not be NULL");
     FF_REQUIRE(k >= 1 && k <= 256 && k <= c->n - 1, FF_ERR_INVALID_ARG, "k out of range");
     ff_eig_opts o;

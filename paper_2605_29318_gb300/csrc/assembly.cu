@@ -70,7 +70,7 @@ __global__ void k_material(const int* __restrict__ perm, long long n, const floa
                            double nu0, T* __restrict__ wh, DevFlags* flags) {
   long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  int i = perm[j];
+  int i = perm ? perm[j] : (int)j;  // caller index of quadrature point j
   double e = E ? (double)E[i] : E0;
   double p = nu ? (double)nu[i] : nu0;
   if (!(e > 0.0) || !(p >= 0.0) || !(p < 0.5) || !isfinite(e)) {
@@ -249,20 +249,23 @@ __global__ void k_split_df(const double* __restrict__ x, float2* __restrict__ y,
 
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0) {
   cudaStream_t st = c->stream;
-  const long long n = c->n, n1 = c->n1;
+  const long long n = c->n, n1 = c->n1, nq = c->nq;
   const int T = 256;
   const bool f64 = c->prec == FF_PREC_FP64;
   const size_t tb = f64 ? 8 : 4;
   reset_flags(c);
-  c->wh.ensure(tb * n);
+  // material weights per quadrature point (the nodal points are in cell
+  // order, the two-set quadrature points in the caller's)
+  c->wh.ensure(tb * nq);
+  const int* qperm = c->twoset ? nullptr : c->perm.as<int>();
   if (f64)  // FP64 contexts: material weights in double-float, like the shape functions
-    (k_material<dfloat><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
-                                                    nu, E0, nu0, c->wh.as<dfloat>(),
-                                                    c->flags.as<DevFlags>()), ::ff::note_launch());
+    (k_material<dfloat><<<ceil_div(nq, T), T, 0, st>>>(qperm, nq, c->vol.as<float>(), E, nu, E0,
+                                                     nu0, c->wh.as<dfloat>(),
+                                                     c->flags.as<DevFlags>()), ::ff::note_launch());
   else
-    (k_material<float><<<ceil_div(n, T), T, 0, st>>>(c->perm.as<int>(), n, c->vol.as<float>(), E,
-                                                   nu, E0, nu0, c->wh.as<float>(),
-                                                   c->flags.as<DevFlags>()), ::ff::note_launch());
+    (k_material<float><<<ceil_div(nq, T), T, 0, st>>>(qperm, nq, c->vol.as<float>(), E, nu, E0,
+                                                    nu0, c->wh.as<float>(),
+                                                    c->flags.as<DevFlags>()), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   // pass 1: unique columns per row, in a table of 2048 slots per warp (4 warps
   // per block); clouds of uneven density (wide supports reaching into dense
@@ -293,7 +296,7 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
                 f.max_row > 0 && f.max_row * 2 > tsize1
                     ? "a Hessian row has more than " + std::to_string(tsize1 / 2) +
                           " distinct columns (support too large)"
-                    : "invalid material (need E > 0, 0 <= nu < 0.5) at particle " +
+                    : "invalid material (need E > 0, 0 <= nu < 0.5) at point " +
                           std::to_string(f.index));
   }
   const int maxrow = std::max(f.max_row, 1);

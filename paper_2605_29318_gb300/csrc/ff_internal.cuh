@@ -117,17 +117,29 @@ struct ff_ctx {
   int prec = FF_PREC_FP32;
   std::string err;
   int stage = 0;  // 0 empty, 1 built, 2 assembled
-  int64_t n = 0, n1 = 0, n2 = 0;
+  int64_t n = 0, n1 = 0, n2 = 0;  // unknowns (nodes or centres), shape pairs, matrix entries
+  // quadrature points (rows of the shape-function lists): n for the nodal
+  // discretisation, the given points for the two-set one
+  int64_t nq = 0;
+  bool twoset = false;  // two-set discretisation: farthest-point centres, Gaussian kernel
+  double trunc = 0.0;   // its cut radius in units of r_k (0: untruncated)
+  float qscale = 1.f;   // its basis scale
 
   ff::Grid grid{};
   // particles in internal (cell) order
+  // (two-set: the centres in their farthest-point order, pos.w = fl32(r_k))
   ff::Buf perm;      // int[n]   internal -> caller index
   ff::Buf iperm;     // int[n]   caller -> internal index
   ff::Buf pos;       // float4[n] (x, y, z, a)
-  ff::Buf vol;       // float[n]
+  ff::Buf vol;       // float[nq] quadrature volumes
   ff::Buf cell_start;// int[ncells + 1]
+  // two-set centres
+  ff::Buf centre_idx;// int64[K]  quadrature point chosen as centre k
+  ff::Buf crad;      // double[K] r_k
+  ff::Buf clim;      // double[K] t^2 r_k^2 (+inf untruncated)
+  ff::Buf clim32;    // float[K]  its FP32 rounding (filter)
   // neighbours (internal order)
-  ff::Buf nbr_ptr;   // int64[n+1]
+  ff::Buf nbr_ptr;   // int64[nq+1]
   ff::Buf nbr_idx;   // int[n1]
   ff::Buf nbrT_ptr;  // int64[n+1]  node k -> rows i it covers
   ff::Buf nbrT_idx;  // int[n1]     row i
@@ -157,7 +169,7 @@ struct ff_ctx {
   ff::Buf sk_ptr;    // int64[nq + 1]
   ff::Buf sk_idx;    // int[nq1]  covering nodes (internal order)
   ff::Buf sk_phi;    // T[4 * nq1] shape functions and gradients
-  ff::Buf wh;        // T[n] v_i (lambda_i + 4 mu_i)
+  ff::Buf wh;        // T[nq] v_i (lambda_i + 4 mu_i)
   // device flags
   ff::Buf flags;     // DevFlags
   ff::DevFlags* hflags = nullptr;  // pinned mirror
@@ -200,6 +212,16 @@ void scan_counts_i32(const int* in, int* out, long long n, ff_ctx* c, Buf& tmp);
 void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a, int64_t n);
 void build_shape(ff_ctx* c);
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0);
+
+// the two-set discretisation (twoset.cu): centres, radii, covering lists and
+// shape functions at the quadrature points
+void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int K, double trunc,
+                  long long start);
+// covering lists of arbitrary points over the centres (returns the pair count)
+// and the Gaussian shape functions there (returns the pass's flags)
+long long twoset_cover(ff_ctx* c, const float* Q, long long nq, Buf& ptrb, Buf& idxb, Buf& cntb);
+DevFlags twoset_shape(ff_ctx* c, const float* Q, long long nq, const long long* ptr,
+                      const int* idx, long long n1, void* phi, void* dphi, bool fp64_out);
 
 // skinning weight fields and linear blend skinning at query points (skinning.cu)
 void skinning_weights(ff_ctx* c, const float* Q, long long nq, const void* C, int m, void* W);

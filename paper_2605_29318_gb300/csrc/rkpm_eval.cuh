@@ -1,7 +1,7 @@
 // Device routines of the corrected RKPM shape functions at one evaluation point
-// (internal; shared by the cloud's own shape functions and by the skinning
-// weights at query points).  Sec. 3.2, Eqs. 7, 9-10; the basis written about
-// the evaluation point (see shape.cu).
+// (internal; shared by the cloud's own shape functions, the two-set
+// construction and the skinning weights at query points).  Sec. 3.2,
+// Eqs. 7, 9-10; the basis written about the evaluation point (see shape.cu).
 #pragma once
 
 #include "dfloat.cuh"
@@ -24,6 +24,42 @@ __device__ __forceinline__ void bspline(C q, C& w, C& dwq) {
     dwq = C(0);
   }
 }
+
+// Raw kernels varphi_k as functors: from the squared distance d2 = |X - p_k|^2
+// they give w = varphi_k(X) and gs with grad_X varphi_k = gs (p_k - X).
+// BSpline: the cubic B-spline of radius a_k = p.w (the nodal discretisation).
+struct BSpline {
+  template <class C>
+  __device__ __forceinline__ void eval(int, float4 p, C d2, C& w, C& gs) const {
+    const C ak = (C)p.w;
+    C dwq;
+    bspline<C>(sqrt(d2) / ak, w, dwq);
+    gs = -dwq / (ak * ak);
+  }
+};
+
+__device__ __forceinline__ float gauss_exp(float x) { return expf(x); }
+__device__ __forceinline__ double gauss_exp(double x) { return exp(x); }
+__device__ __forceinline__ dfloat gauss_exp(dfloat x) { return dfloat(exp((double)x)); }
+
+template <class C>
+__device__ __forceinline__ C from_f64(double x) { return (C)x; }
+template <>
+__device__ __forceinline__ dfloat from_f64<dfloat>(double x) { return dfloat(x); }
+
+// Gauss: exp(-|X - p_k|^2 / r_k^2) (Sec. 3.2) with the FP64 radii r_k of the
+// two-set construction; grad_X = (2 w / r_k^2)(p_k - X).  In double-float the
+// exponential is CUDA's FP64 exp of the argument, split into a pair.
+struct Gauss {
+  const double* rad;
+  template <class C>
+  __device__ __forceinline__ void eval(int k, float4, C d2, C& w, C& gs) const {
+    const C rk = from_f64<C>(rad[k]);
+    const C rk2 = rk * rk;
+    w = gauss_exp(-(d2 / rk2));
+    gs = C(2) * w / rk2;
+  }
+};
 
 template <class C>
 __device__ __forceinline__ C warp_sum(C v) {
@@ -77,10 +113,11 @@ __device__ __forceinline__ void chol4_solve(const C* L, const C* b, C* x) {
 
 // Evaluate one row in compute precision C, writing outputs of precision T.
 // Returns 0 ok, 1 singular, 2 ill-conditioned (only when check_cond).
-template <class C, class T>
+template <class C, class T, class Kern = BSpline>
 __device__ int shape_row(const float4* __restrict__ pos, long long s, long long e,
                          const int* __restrict__ idx, float4 Xi, T* __restrict__ phi,
-                         T* __restrict__ dphi, long long n1, double cond_limit, bool check_cond) {
+                         T* __restrict__ dphi, long long n1, double cond_limit, bool check_cond,
+                         const Kern& kern = Kern()) {
   const int lane = threadIdx.x & 31;
   const C xi = (C)Xi.x, yi = (C)Xi.y, zi = (C)Xi.z, si = (C)Xi.w;
   C m[10], dm[3][10];
@@ -90,12 +127,11 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
     dm[0][q] = dm[1][q] = dm[2][q] = C(0);
   }
   for (long long t = s + lane; t < e; t += 32) {
-    float4 p = pos[idx[t]];
-    C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi, ak = (C)p.w;
-    C dist = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-    C w, dwq;
-    bspline<C>(dist / ak, w, dwq);
-    C gs = -dwq / (ak * ak);  // grad_X varphi = gs * r
+    const int k = idx[t];
+    float4 p = pos[k];
+    C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi;
+    C w, gs;  // grad_X varphi = gs * r
+    kern.template eval<C>(k, p, r0 * r0 + r1 * r1 + r2 * r2, w, gs);
     C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
     C g[3] = {gs * r0, gs * r1, gs * r2};
     int q = 0;
@@ -153,12 +189,11 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
     chol4_solve<C>(L, rhs, dC[d]);
   }
   for (long long t = s + lane; t < e; t += 32) {
-    float4 p = pos[idx[t]];
-    C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi, ak = (C)p.w;
-    C dist = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-    C w, dwq;
-    bspline<C>(dist / ak, w, dwq);
-    C gs = -dwq / (ak * ak);
+    const int k = idx[t];
+    float4 p = pos[k];
+    C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi;
+    C w, gs;
+    kern.template eval<C>(k, p, r0 * r0 + r1 * r1 + r2 * r2, w, gs);
     C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
     C PC = P[0] * Cv[0] + P[1] * Cv[1] + P[2] * Cv[2] + P[3] * Cv[3];
     phi[t] = (T)(w * PC);

@@ -13,7 +13,9 @@
 // cells, which still hold every node within one support of them), the moment
 // solve and shape functions per query point (one warp each; double-float in
 // FP64 contexts, FP32 with the FP64 redo of ill-conditioned points in FP32
-// ones), and the weights as one warp per point over the modes.
+// ones), and the weights as one warp per point over the modes.  Clouds of the
+// two-set discretisation take its own covering test over the K centres and
+// its Gaussian shape functions (twoset.cu).
 #include "grid.cuh"
 #include "rkpm_eval.cuh"
 
@@ -121,6 +123,23 @@ template <class T>
 void weights_t(ff_ctx* c, const float* Q, long long nq, const T* C, int m, T* W) {
   cudaStream_t st = c->stream;
   const int TB = 256;
+  if (c->twoset) {
+    const long long nq1 = twoset_cover(c, Q, nq, c->sk_ptr, c->sk_idx, c->sk_cnt);
+    const long long* qptr = c->sk_ptr.as<long long>();
+    const int* qidx = c->sk_idx.as<int>();
+    T* phi = reinterpret_cast<T*>(c->sk_phi.ensure(sizeof(T) * 4 * std::max(nq1, 1LL)));
+    const DevFlags f = twoset_shape(c, Q, nq, qptr, qidx, nq1, phi, phi + nq1, true);
+    if (f.code == FF_ERR_SINGULAR_MOMENT)
+      throw Error(FF_ERR_SINGULAR_MOMENT,
+                  "query point " + std::to_string(f.index) +
+                      " is covered by fewer than four non-coplanar centres");
+    (k_query_weights<T><<<ceil_div(nq * 32, TB), TB, 0, st>>>(qptr, qidx, phi, nq,
+                                                              c->perm.as<int>(), C, c->n, m, W),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    FF_CUDA(cudaStreamSynchronize(st));
+    return;
+  }
   const Grid& g = c->grid;
   const GridDev gd{g.origin[0], g.origin[1], g.origin[2], g.h, g.dims[0], g.dims[1], g.dims[2],
                    g.bdims[0], g.bdims[1], g.bdims[2]};

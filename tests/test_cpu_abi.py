@@ -86,6 +86,8 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.ff_get_precond_layout(None, None, None) == 1
     assert lib.ff_skinning_weights(None, None, 1, None, 1, None) == 1
     assert lib.ff_lbs_deform(None, None, 1, None, 1, None, None) == 1
+    assert lib.rkpm_build_twoset(None, None, None, 100, 10, 3.0, 0) == 1
+    assert lib.ff_get_twoset(None, None, None, None, None) == 1
 
 
 def test_no_fallback_without_library(tmp_path):

@@ -52,6 +52,13 @@ def test_fps_is_a_two_approximation_of_the_k_centre_optimum():
         assert sep >= cov - 1e-12
 
 
+def test_fps_refuses_more_centres_than_distinct_points():
+    X = _line([0, 1, 1, 0, 2])
+    assert twoset.farthest_point_sampling(X, 3).tolist() == [0, 4, 1]
+    with pytest.raises(ValueError):
+        twoset.farthest_point_sampling(X, 4)
+
+
 def test_fps_follows_a_permutation_of_the_points():
     rng = np.random.default_rng(5)
     X = rng.random((300, 3)).astype(np.float32)
