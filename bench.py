@@ -16,6 +16,12 @@ line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--prec fp64|fp32] [--tol T] [--cheb D] [--cheb-fp64 D]
                   [--fp32-phase 0|1] [--fp32-tol T] [--precond-tc 0|1]
+                  [--workload nodal|twoset]
+
+`--workload twoset` times the paper's own two-set construction instead: the
+same torus as 49,584 grid quadrature points (h = 0.02), K = 1,000
+farthest-point centres with Gaussian kernels cut at 3 r_k, the same material
+and k; one step = rkpm_build_twoset + assemble_hessian + eigenmodes.
 
 With N > 1 (torchrun, one process per GPU) every rank solves its own object
 (replicas; the path has no cross-GPU exchange) and the reported time is the
@@ -135,6 +141,119 @@ def cpu_baseline_json():
                        f"H_w/M, shift-invert eigsh k=32) on the same torus with {SAMPLE_N:,} "
                        f"particles instead of 50,000; not scaled"),
             "max_residual": res}
+
+
+TWOSET_WORKLOAD = ("solid torus R=0.5 r=0.2 as 49,584 inside-grid quadrature points "
+                   "(h=0.02), K=1,000 farthest-point centres, Gaussian kernels with "
+                   "r_k = 2nd-nearest-centre distance cut at 3 r_k, Neo-Hookean E=1e6 "
+                   "nu=0.4, k=32 lowest modes incl. the constant mode")
+def cpu_twoset_step(h=0.02, K=1000, k=32):
+    """The FP64 oracle's two-set path on the whole workload (a few seconds):
+    farthest-point centres, radii, Gaussian shape functions, dense H_w and M,
+    dense eigensolve."""
+    from oracle import eigen, twoset
+    from paper_2605_29318_gb300 import synth
+    X, v = synth.torus_grid(h)
+    t0 = time.perf_counter()
+    _, _, H, M = twoset.build(X, v, K, 1e6, 0.4, trunc=3.0)
+    lam, C = eigen.eigh_dense(H, M, k)
+    dt = time.perf_counter() - t0
+    return dt, float(eigen.residuals(H, M, lam, C)[1:].max()), X.shape[0]
+
+
+def run_twoset(args):
+    """One GPU, the two-set workload: device-timed steps (L2 flushed), the
+    stage split, and the end-to-end step from host arrays."""
+    import numpy as np
+    import torch
+
+    from paper_2605_29318_gb300 import binding, synth
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    Xh, vh = synth.torus_grid(0.02)
+    K, k = 1000, 32
+    X = torch.from_numpy(Xh).to(dev)
+    v = torch.from_numpy(vh).to(dev)
+    ctx = binding.Context(0, args.prec)
+    opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
+                                fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64,
+                                precond_tc=args.precond_tc, fp32_tol=args.fp32_tol)
+    modes = torch.empty((k, K), dtype=ctx.dtype, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step(Xd, vd):
+        ctx.rkpm_build_twoset(Xd, vd, K, 3.0, 0)
+        ctx.assemble_hessian(None, None, 1e6, 0.4)
+        return ctx.eigenmodes(k, opts, modes_out=modes, check=False)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(X, v)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    launches0 = binding.launch_count()
+    times = []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            _, _, rep, status = step(X, v)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    launches = binding.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = sum(times) / len(times)
+    # end to end: pinned host inputs copied in, the modes read back, per step
+    Xp, vp = torch.from_numpy(Xh).pin_memory(), torch.from_numpy(vh).pin_memory()
+    host_modes = torch.empty((k, K), dtype=ctx.dtype).pin_memory()
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd, vd = Xp.to(dev, non_blocking=True), vp.to(dev, non_blocking=True)
+        step(Xd, vd)
+        host_modes.copy_(modes)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e) / len(e2e)
+    n, n1, n2 = ctx.sizes()
+    line = {
+        "metric": METRIC, "value": round(ms / 1000.0, 5), "unit": "s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": (("f32+bf16, then f32x2 double-float" if args.fp32_phase
+                   else "f64") if args.prec == "fp64" else "f32+bf16"),
+        "data": "synthetic",
+        "config": {"workload": TWOSET_WORKLOAD, "precision": args.prec, "tol": args.tol,
+                   "quadrature_points": int(Xh.shape[0]), "K": n, "n1": n1, "n2": n2,
+                   "l2": "flushed by a 256 MB write before every timed step",
+                   "parallelism": "single GPU"},
+        "stage_ms_per_step": {kk: round(vv[1] / args.steps, 3) for kk, vv in prof.items()},
+        "solver": {"iterations": rep["iterations"], "status": status,
+                   "max_residual": rep["max_residual"]},
+        "e2e": {"value": round(e2e_s, 5), "unit": "s",
+                "h2d_bytes_per_step": int(Xh.nbytes + vh.nbytes),
+                "d2h_bytes_per_step": int(host_modes.numel() * host_modes.element_size())},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        dt, res, npts = cpu_twoset_step()
+        line["cpu_baseline"] = {
+            "value": round(dt, 3), "unit": "s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "max_residual": res,
+            "sample": (f"FP64 two-set oracle (farthest-point centres, radii, Gaussian shape "
+                       f"functions, dense H_w/M, dense eigensolve) on the whole workload "
+                       f"({npts:,} points, K=1,000)")}
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def max_over_ranks(values, device):
@@ -385,9 +504,13 @@ def main():
     ap.add_argument("--precond-tc", type=int, default=1, choices=[0, 1],
                     help="preconditioner steps on tensor cores (BF16 tiles) or on CUDA cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="nodal", choices=["nodal", "twoset"],
+                    help="the nodal torus (default) or the paper's two-set construction")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "twoset":
+        run_twoset(args)
     else:
         run_ours(args)
 
