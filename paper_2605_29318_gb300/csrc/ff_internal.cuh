@@ -127,7 +127,8 @@ struct ff_ctx {
 
   ff::Grid grid{};
   // particles in internal (cell) order
-  // (two-set: the centres in their farthest-point order, pos.w = fl32(r_k))
+  // (two-set: the centres in their farthest-point order, pos.w = 0; the radii
+  // are kept in FP64 in crad)
   ff::Buf perm;      // int[n]   internal -> caller index
   ff::Buf iperm;     // int[n]   caller -> internal index
   ff::Buf pos;       // float4[n] (x, y, z, a)

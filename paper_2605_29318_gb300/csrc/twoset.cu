@@ -224,8 +224,8 @@ __global__ void k_gather_centres(const float* __restrict__ X, const long long* _
 
 // ------------------------------------------------------------------ radii
 // r_k = sqrt(second-smallest squared distance to the other centres); lim_k =
-// (t*t) * (r_k*r_k) or +inf without a cut.  pos.w receives fl32(r_k).
-__global__ void k_radii(float4* __restrict__ cpos, int K, double tt, double* __restrict__ rad,
+// (t*t) * (r_k*r_k) or +inf without a cut.
+__global__ void k_radii(const float4* __restrict__ cpos, int K, double tt, double* __restrict__ rad,
                         double* __restrict__ lim, float* __restrict__ lim32,
                         DevFlags* __restrict__ flags) {
   const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -259,7 +259,6 @@ __global__ void k_radii(float4* __restrict__ cpos, int K, double tt, double* __r
     const double L = tt > 0.0 ? __dmul_rn(tt, __dmul_rn(r, r)) : (double)INFINITY;
     lim[k] = L;
     lim32[k] = (float)L;
-    cpos[k].w = (float)r;
     if (!(r > 0.0) || !isfinite(r))
       if (atomicCAS(&flags->code, 0, (int)FF_ERR_INVALID_ARG) == 0) flags->index = k;
   }
