@@ -101,16 +101,18 @@ def test_no_fallback_without_library(tmp_path):
         binding._lib = saved
 
 
-def test_reference_arm_prints_the_contract_line():
+@pytest.mark.parametrize("workload", ["nodal", "twoset"])
+def test_reference_arm_prints_the_contract_line(workload):
     """bench.py --impl reference times the FP64 oracle on the host cores and
-    prints one JSON line with the contract's keys (no GPU needed)."""
+    prints one JSON line with the contract's keys (no GPU needed), for both
+    workloads."""
     import json
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], cwd=root, capture_output=True, text=True,
-                         timeout=600)
+                          "--warmup", "0", "--workload", workload], cwd=root,
+                         capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
@@ -121,6 +123,7 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["max_residual"] < 1e-6
+    assert ("K=1,000" in line["config"]["workload"]) == (workload == "twoset")
 
 
 def _replica_worker(rank, world, port, q):
