@@ -8,7 +8,7 @@ Paper: Sec. 3.2 "RKPM", Eqs. 6-11.  A field is u(X) = sum_k phi_k(X) c_k with
     P(X) = [1, x, y, z]^T (linear basis, D = 1).
 The reproducing condition sum_k phi_k(X) P(p_k) = P(X) (Eq. 8) is the pin.
 
-Readings taken where the paper is silent (each is listed in the design doc):
+Readings taken where the paper is silent:
 * raw kernel varphi_k: the cubic B-spline of radius a_k (unnormalised) instead
   of the paper's Gaussian (the workloads ask for it);
 * neighbour rule: node k contributes at X iff ||X - p_k||^2 < a_k^2, tested in

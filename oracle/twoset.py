@@ -17,7 +17,7 @@ kernel of Sec. 3.2) keeps two point sets apart:
 The corrected shape functions are those of Eqs. 7, 9-10 with the linear basis,
 evaluated at the quadrature points; H_w (Prop. 1) and M (Eq. 14) are K x K.
 
-Readings taken where the paper is silent (each is listed in the design doc):
+Readings taken where the paper is silent:
 * farthest-point sampling starts from the first point in the order given and
   breaks ties in distance towards the lowest index; distances are compared
   squared, in FP64, from the FP32-stored points, as ((dx*dx + dy*dy) + dz*dz)
