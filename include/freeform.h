@@ -13,6 +13,7 @@
  *                     RKPM mass matrix M (Sec. 3.2, Eq. 14)
  *   eigenmodes        the k lowest generalized eigenpairs of H_w c = lambda M c
  *                     (Sec. 3.2, Eq. 15; Supp. Sec. B "Eigenanalysis")
+ *   eigenmodes_batched the three calls for many objects, overlapped on one GPU
  *
  * Conventions shared by every call
  * --------------------------------
@@ -218,6 +219,49 @@ void ff_eig_opts_default(ff_eig_opts* opts);
  * largest residual seen. */
 ff_status eigenmodes(ff_ctx* ctx, int k, const ff_eig_opts* opts, const void* X0,
                      double* eigvals, void* modes, ff_eig_report* rep);
+
+/* ---------------------------------------------------------- eigenmodes_batched
+ * Many objects in one call: for every item, rkpm_build + assemble_hessian +
+ * eigenmodes exactly as the single-object calls do them (same kernels, same
+ * arithmetic, so each item's results equal those of the three calls on their
+ * own).  `workers` host threads (0: min(count, 8)) each drive their own
+ * context on their own non-blocking CUDA stream of `device`, taking the
+ * objects largest first from a shared counter, so the latency-bound solves of
+ * several objects overlap on the GPU.  The call synchronises the device before
+ * it starts (the inputs must be ready on any stream) and returns when every
+ * item is done.
+ *
+ *   device, precision  as for ff_create
+ *   items     host array of count items; inputs as for rkpm_build and
+ *             assemble_hessian, outputs as for eigenmodes (modes may be NULL,
+ *             report may be NULL); status and error are written for every item
+ *             (error: the item's ff_last_error message, empty when FF_OK)
+ *   opts      NULL = defaults; the same options for every item
+ *
+ * Returns FF_OK when every item succeeded, else the status of the first failed
+ * item in array order; FF_ERR_INVALID_ARG on NULL items with count > 0, count
+ * < 0, a bad precision or a bad workers count; FF_ERR_CUDA when the device is
+ * not usable.  Items no worker could start (every worker failed to create its
+ * context) keep FF_ERR_CUDA. */
+typedef struct {
+  const float* particles;  /* device, float[n][3] */
+  const float* volumes;    /* device, float[n] */
+  const float* support;    /* device, float[n] */
+  int64_t n;
+  const float* E;          /* device float[n] or NULL (uniform E0) */
+  const float* nu;         /* device float[n] or NULL (uniform nu0) */
+  double E0;
+  double nu0;
+  int k;                   /* modes wanted, as for eigenmodes */
+  double* eigvals;         /* host, double[k] */
+  void* modes;             /* device, column-major n x k of the precision, or NULL */
+  ff_eig_report* report;   /* host, or NULL */
+  ff_status status;        /* out */
+  char error[192];         /* out */
+} ff_batch_item;
+
+ff_status eigenmodes_batched(int device, int precision, ff_batch_item* items, int count,
+                             const ff_eig_opts* opts, int workers);
 
 /* --------------------------------------------------------- inspection exports
  * Copies of the internal results, in the caller's particle order, for parity

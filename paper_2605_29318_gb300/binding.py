@@ -31,7 +31,8 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_net_num_params", "ff_net_create", "ff_net_destroy", "ff_net_last_error",
            "ff_net_init", "ff_net_set_params", "ff_net_get_params", "ff_warmstart_features",
            "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block",
-           "ff_skinning_weights", "ff_lbs_deform", "rkpm_build_twoset", "ff_get_twoset"]
+           "ff_skinning_weights", "ff_lbs_deform", "rkpm_build_twoset", "ff_get_twoset",
+           "eigenmodes_batched"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6, "setup": 7}
 
@@ -53,6 +54,16 @@ class EigReport(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("particles", ctypes.c_void_p), ("volumes", ctypes.c_void_p),
+                ("support", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("E", ctypes.c_void_p), ("nu", ctypes.c_void_p),
+                ("E0", ctypes.c_double), ("nu0", ctypes.c_double), ("k", ctypes.c_int),
+                ("eigvals", ctypes.c_void_p), ("modes", ctypes.c_void_p),
+                ("report", ctypes.c_void_p), ("status", ctypes.c_int),
+                ("error", ctypes.c_char * 192)]
 
 
 class FreeformError(RuntimeError):
@@ -110,6 +121,8 @@ def load_library(path: str = LIB_PATH):
     L.ff_lbs_deform.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     L.rkpm_build_twoset.argtypes = [vp, vp, vp, i64, i32, dbl, i64]
     L.ff_get_twoset.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), vp, vp]
+    L.eigenmodes_batched.argtypes = [i32, i32, ctypes.POINTER(BatchItem), i32,
+                                     ctypes.POINTER(EigOpts), i32]
     del fp
     for name in EXPORTS:
         if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default",
@@ -356,6 +369,42 @@ class Context:
 # module-level names matching the C ABI
 def rkpm_build(ctx: Context, particles, volumes, support):
     return ctx.rkpm_build(particles, volumes, support)
+
+
+def eigenmodes_batched(objects, precision="fp64", opts: Optional[EigOpts] = None,
+                       workers: int = 0, device: int = 0):
+    """The three calls for many objects in one call, overlapped on one GPU.
+
+    objects: list of dicts with float32 CUDA tensors X (n, 3), v (n,), a (n,),
+    optional per-particle E and nu tensors (else the scalars E0, nu0) and k.
+    Returns (status, results) with one (eigvals numpy (k,), modes torch (n, k)
+    column-major view, report dict, status, error message) per object."""
+    import torch
+    L = load_library()
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    items = (BatchItem * max(len(objects), 1))()
+    keep, outs = [], []
+    for it, o in zip(items, objects):
+        for t in (o["X"], o["v"], o["a"]):
+            assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+        n, k = int(o["X"].shape[0]), int(o["k"])
+        ev = np.zeros(k, np.float64)
+        modes = torch.empty((k, n), dtype=dtype, device=f"cuda:{device}")
+        rep = EigReport()
+        it.particles, it.volumes, it.support = _ptr(o["X"]), _ptr(o["v"]), _ptr(o["a"])
+        it.n, it.k = n, k
+        it.E, it.nu = _ptr(o.get("E")), _ptr(o.get("nu"))
+        it.E0, it.nu0 = float(o.get("E0", 1e5)), float(o.get("nu0", 0.45))
+        it.eigvals = ev.ctypes.data
+        it.modes = _ptr(modes)
+        it.report = ctypes.addressof(rep)
+        keep.append(o)
+        outs.append((ev, modes, rep))
+    st = L.eigenmodes_batched(device, PREC[precision], items, len(objects),
+                              ctypes.byref(opts) if opts is not None else None, int(workers))
+    res = [(ev, modes.t(), rep.as_dict(), it.status, it.error.decode())
+           for (ev, modes, rep), it in zip(outs, items)]
+    return st, res
 
 
 def rkpm_build_twoset(ctx: Context, points, volumes, K, trunc=3.0, start=0):

@@ -277,9 +277,7 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
     tsize1 = attempt == 0 ? 2048 : 16384;
     const int wpb1 = attempt == 0 ? 4 : 2;
     const size_t smem1 = sizeof(int) * tsize1 * wpb1;
-    if (smem1 > 48 * 1024)
-      FF_CUDA(cudaFuncSetAttribute(k_pattern_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem1));
+    if (smem1 > 48 * 1024) set_max_dyn_smem((const void*)k_pattern_count, (int)smem1);
     if (attempt > 0) reset_flags(c);
     int grid1 = (int)std::min<long long>(ceil_div(n, wpb1), 152LL * 16);
     (k_pattern_count<<<grid1, 32 * wpb1, smem1, st>>>(
@@ -317,16 +315,15 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   size_t smem = pw * wpb2;
   int grid2 = (int)std::min<long long>(ceil_div(n, wpb2), 152LL * 32);
   if (f64) {
-    FF_CUDA(cudaFuncSetAttribute(k_assemble<dfloat, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)std::max<size_t>(smem, 48 * 1024)));
+    set_max_dyn_smem((const void*)k_assemble<dfloat, double>,
+                     (int)std::max<size_t>(smem, 48 * 1024));
     (k_assemble<dfloat, double><<<grid2, 32 * wpb2, smem, st>>>(
         c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
         c->nbrT_idx.as<int>(), c->nbrT_pos.as<long long>(), c->phi.as<dfloat>(),
         c->dphi.as<dfloat>(), n1, c->vol.as<float>(), c->wh.as<dfloat>(), n, tsize2, maxrow, aptr,
         c->a_col.as<int>(), c->a_val.as<double>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>()), ::ff::note_launch());
   } else {
-    FF_CUDA(cudaFuncSetAttribute(k_assemble<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)std::max<size_t>(smem, 48 * 1024)));
+    set_max_dyn_smem((const void*)k_assemble<float>, (int)std::max<size_t>(smem, 48 * 1024));
     (k_assemble<float><<<grid2, 32 * wpb2, smem, st>>>(
         c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
         c->nbrT_idx.as<int>(), c->nbrT_pos.as<long long>(), c->phi.as<float>(),

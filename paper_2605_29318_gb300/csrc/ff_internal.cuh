@@ -197,8 +197,9 @@ struct ProfScope {
 // ---------------------------------------------------------------- helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-// raise a kernel's dynamic shared-memory limit on the current device (once per
-// kernel, device and size; the attribute belongs to the device's context)
+// raise a kernel's dynamic shared-memory limit on the current device (only
+// ever raised, per kernel and device; thread-safe; the attribute belongs to
+// the device's context)
 void set_max_dyn_smem(const void* fn, int bytes);
 
 void reset_flags(ff_ctx* c);

@@ -1,23 +1,26 @@
 // Scans, device-flag helpers, launch counting and the event profiler.
 #include <atomic>
+#include <map>
 #include <mutex>
-#include <set>
-#include <tuple>
+#include <utility>
 
 #include "ff_internal.cuh"
 
 namespace ff {
 
+// The limit only grows: contexts driven from several host threads may launch
+// the same kernel with different sizes, and a larger limit never affects a
+// smaller launch (the attribute is an upper bound, not an allocation).
 void set_max_dyn_smem(const void* fn, int bytes) {
   static std::mutex mu;
-  static std::set<std::tuple<const void*, int, int>> done;
+  static std::map<std::pair<const void*, int>, int> limit;
   int dev = 0;
   FF_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
-  const auto key = std::make_tuple(fn, dev, bytes);
-  if (done.count(key)) return;
+  int& cur = limit[std::make_pair(fn, dev)];
+  if (bytes <= cur) return;
   FF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  done.insert(key);
+  cur = bytes;
 }
 
 thread_local ff_ctx* g_ctx = nullptr;

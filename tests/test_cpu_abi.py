@@ -49,7 +49,7 @@ def _struct_fields(name):
     text = open(HEADER).read()
     m = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text)
     body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
-    return [re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*;", l)[0]
+    return [re.findall(r"([A-Za-z_][A-Za-z0-9_]*)\s*(?:\[[^\]]*\])?\s*;", l)[0]
             for l in body.split("\n") if ";" in l]
 
 
@@ -57,6 +57,7 @@ def test_ctypes_structs_match_header():
     from paper_2605_29318_gb300 import binding
     assert [f for f, _ in binding.EigOpts._fields_] == _struct_fields("ff_eig_opts")
     assert [f for f, _ in binding.EigReport._fields_] == _struct_fields("ff_eig_report")
+    assert [f for f, _ in binding.BatchItem._fields_] == _struct_fields("ff_batch_item")
 
 
 def test_default_options_without_gpu(lib):
@@ -88,6 +89,12 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.ff_lbs_deform(None, None, 1, None, 1, None, None) == 1
     assert lib.rkpm_build_twoset(None, None, None, 100, 10, 3.0, 0) == 1
     assert lib.ff_get_twoset(None, None, None, None, None) == 1
+    # batched call: argument checks come before any device use
+    assert lib.eigenmodes_batched(0, 1, None, 3, None, 0) == 1
+    assert lib.eigenmodes_batched(0, 1, None, -1, None, 0) == 1
+    assert lib.eigenmodes_batched(0, 7, None, 0, None, 0) == 1
+    assert lib.eigenmodes_batched(0, 1, None, 0, None, -2) == 1
+    assert lib.eigenmodes_batched(0, 1, None, 0, None, 0) == 0
 
 
 def test_no_fallback_without_library(tmp_path):

@@ -17,9 +17,9 @@ from oracle import assembly, eigen, twoset
 from paper_2605_29318_gb300 import synth
 
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("FF_TWOSET_GPU_TESTS") != "1",
+              pytest.mark.skipif(os.environ.get("FF_PENDING_GPU_TESTS") != "1",
                                  reason="the two-set path awaits its first GB300 run "
-                                        "(FF_TWOSET_GPU_TESTS=1 runs it)")]
+                                        "(FF_PENDING_GPU_TESTS=1 runs it)")]
 
 TOL_SHAPE = {"fp64": 1e-10, "fp32": 2e-5}
 TOL_MAT = {"fp64": 1e-10, "fp32": 1e-4}
