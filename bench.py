@@ -16,7 +16,7 @@ line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--prec fp64|fp32] [--tol T] [--cheb D] [--cheb-fp64 D]
                   [--fp32-phase 0|1] [--fp32-tol T] [--precond-tc 0|1]
-                  [--workload nodal|twoset]
+                  [--precond-compact 0|1] [--workload nodal|twoset]
 
 `--workload twoset` times the paper's own two-set construction instead: the
 same torus as 49,584 grid quadrature points (h = 0.02), K = 1,000
@@ -177,7 +177,8 @@ def run_twoset(args):
     ctx = binding.Context(0, args.prec)
     opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
                                 fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64,
-                                precond_tc=args.precond_tc, fp32_tol=args.fp32_tol)
+                                precond_tc=args.precond_tc, fp32_tol=args.fp32_tol,
+                                precond_compact=args.precond_compact)
     modes = torch.empty((k, K), dtype=ctx.dtype, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
@@ -319,7 +320,8 @@ def run_ours(args):
     ctx = binding.Context(local, args.prec)
     opts = binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
                                 fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64,
-                                precond_tc=args.precond_tc, fp32_tol=args.fp32_tol)
+                                precond_tc=args.precond_tc, fp32_tol=args.fp32_tol,
+                                precond_compact=args.precond_compact)
     from paper_2605_29318_gb300 import train_warmstart
     net = binding.Net(local)
     net.set_params(train_warmstart.load_weights())
@@ -451,6 +453,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "precision": args.prec, "tol": args.tol,
                    "cheb_degree": args.cheb, "cheb_degree_fp64": args.cheb_fp64,
                    "precond_tc": args.precond_tc, "fp32_tol": args.fp32_tol,
+                   "precond_compact": args.precond_compact,
                    "n": n, "n1": n1, "n2": n2,
                    "l2": "flushed by a 256 MB write before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -508,6 +511,8 @@ def main():
                     help="residual at which the FP32 phase hands over")
     ap.add_argument("--precond-tc", type=int, default=1, choices=[0, 1],
                     help="preconditioner steps on tensor cores (BF16 tiles) or on CUDA cores")
+    ap.add_argument("--precond-compact", type=int, default=0, choices=[0, 1],
+                    help="preconditioner steps on the unconverged columns only, packed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="nodal", choices=["nodal", "twoset"],
                     help="the nodal torus (default) or the paper's two-set construction")

@@ -179,6 +179,9 @@ typedef struct {
   int precond_tc;       /* 1: the preconditioner's H products on tensor cores, with H in
                            BF16 dense tiles of 16-row blocks (block widths 8..64 in steps
                            of 8); 0: sparse FP32 H on CUDA cores (1) */
+  int precond_compact;  /* 1: the preconditioner runs on the columns still above tol only,
+                           packed to a multiple of 8 (the others are zero either way, so
+                           the results are the same); 0: on the whole block (0) */
 } ff_eig_opts;
 
 typedef struct {

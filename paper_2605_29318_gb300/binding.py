@@ -43,7 +43,8 @@ class EigOpts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("time_budget_s", ctypes.c_double),
                 ("exclude_constant", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("fp32_phase", ctypes.c_int), ("fp32_tol", ctypes.c_double),
-                ("cheb_degree_fp64", ctypes.c_int), ("precond_tc", ctypes.c_int)]
+                ("cheb_degree_fp64", ctypes.c_int), ("precond_tc", ctypes.c_int),
+                ("precond_compact", ctypes.c_int)]
 
 
 class EigReport(ctypes.Structure):

@@ -194,6 +194,7 @@ void ff_eig_opts_default(ff_eig_opts* o) {
   o->fp32_tol = 1e-4;
   o->cheb_degree_fp64 = 64;
   o->precond_tc = 1;
+  o->precond_compact = 0;
 }
 
 ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, double* eigvals,

@@ -272,6 +272,51 @@ __global__ void k_cast_block(const float* __restrict__ x, int ldx, long long n, 
   W[r * ld + c] = (T)x[r * ldx + c];
 }
 
+// Packed Chebyshev start: the same b as k_cheb_init for the columns still
+// above tol only, column q of the n x w arrays taken from block column cmap[q]
+// (cmap[q] < 0: a padding column, zero).
+template <class T>
+__global__ void k_cheb_init_packed(const T* __restrict__ HX, const T* __restrict__ MX, int ld,
+                                   const double* __restrict__ theta, const int* __restrict__ cmap,
+                                   const float* __restrict__ hdiag, long long n, int w,
+                                   float* __restrict__ res, float* __restrict__ x, float inv_tc,
+                                   __nv_bfloat16* __restrict__ d16) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * w) return;
+  long long r = t / w;
+  const int c = cmap[(int)(t % w)];
+  float b = 0.f;
+  if (c >= 0) {
+    if constexpr (std::is_same_v<T, dfloat>) {
+      dfloat rr = HX[r * ld + c];
+      df_mac(rr, dfloat(-theta[c]), MX[r * ld + c]);
+      b = (float)df_norm(rr) / hdiag[r];
+    } else if constexpr (std::is_same_v<T, float>) {
+      b = fmaf(-(float)theta[c], MX[r * ld + c], HX[r * ld + c]) / hdiag[r];
+    } else {
+      double rr = (double)HX[r * ld + c] - theta[c] * (double)MX[r * ld + c];
+      b = (float)(rr / (double)hdiag[r]);
+    }
+  }
+  res[t] = b;
+  const __nv_bfloat16 q = __float2bfloat16(b * inv_tc);
+  d16[t] = q;
+  x[t] = __bfloat162float(q);
+}
+
+// W (n x m of a panel) from the packed n x w result: block column c takes
+// packed column cinv[c], or zero when it was not preconditioned
+template <class T>
+__global__ void k_cast_packed(const float* __restrict__ x, int w, const int* __restrict__ cinv,
+                              long long n, int m, T* __restrict__ W, int ld) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * m) return;
+  long long r = t / m;
+  int c = (int)(t % m);
+  const int q = cinv[c];
+  W[r * ld + c] = q >= 0 ? (T)x[r * w + q] : T(0);
+}
+
 __global__ void k_round_block(const double* __restrict__ x, float* __restrict__ y, long long m) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) y[t] = (float)x[t];
@@ -340,7 +385,8 @@ struct Solver {
     Gt = reinterpret_cast<T*>(c->ws[17].ensure(sizeof(T) * (2 * nb + 2) * nb));
     YZ = reinterpret_cast<T*>(c->ws[18].ensure(sizeof(T) * ns * 2 * nb));
     dropped_d = reinterpret_cast<int*>(c->ws[19].ensure(sizeof(int) * 4));
-    active_d = reinterpret_cast<int*>(c->ws[20].ensure(sizeof(int) * nb));
+    // active flags, then the packing maps of the preconditioner: cmap (mc), cinv (nb)
+    active_d = reinterpret_cast<int*>(c->ws[20].ensure(sizeof(int) * (2 * nb + mc + 8)));
     h_pin = reinterpret_cast<double*>(c->hflags) + 16;  // pinned scratch after the flags
   }
 
@@ -510,7 +556,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   }
 
   // ---- iterations
-  std::vector<int> active(nb, 1);
+  std::vector<int> active(nb, 1), pack;
   std::vector<double> res(nb, 1.0), theta(nb, 0.0);
   bool has_p = false;
   int it = 0;
@@ -591,19 +637,41 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
       status = FF_ERR_TIMEOUT;
       break;
     }
-    FF_CUDA(cudaMemcpyAsync(s.active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
-
     // W = T R  (FP32 Chebyshev polynomial in D^-1 H, or Jacobi when deg <= 1)
     T* W = s.S[cur] + nb;
     // BF16 directions halve the bytes each preconditioner step gathers; their
     // steps take widths in multiples of 8, the padding columns stay zero
     const bool b16 = deg > 1 && s.mc % 8 == 0;
-    const int mc = s.mc;
-    (k_cheb_init<T><<<blocks(n * mc), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d,
-                                                  s.active_d, c->hdiag_f32.as<float>(), n, nb, mc,
-                                                  s.cres, s.cd0, s.cx,
-                                                  deg > 1 ? (float)(1.0 / th_c) : 1.f,
-                                                  b16 ? s.cb0 : nullptr), ::ff::note_launch());
+    // packed: only the columns above tol enter the steps, w of them rounded up
+    // to 8 (the steps treat every column alone, so W is the same either way)
+    const bool packed = b16 && o.precond_compact;
+    int mc = s.mc;
+    if (packed) {
+      int nact = 0;
+      for (int j = 0; j < nb; ++j) nact += active[j] != 0;
+      mc = std::max(8, (nact + 7) / 8 * 8);
+      pack.assign(2 * nb + s.mc, -1);
+      std::copy(active.begin(), active.end(), pack.begin());
+      for (int j = 0, q = 0; j < nb; ++j)
+        if (active[j]) {
+          pack[nb + q] = j;           // cmap[q] = j
+          pack[nb + s.mc + j] = q++;  // cinv[j] = q
+        }
+      FF_CUDA(cudaMemcpyAsync(s.active_d, pack.data(), sizeof(int) * pack.size(),
+                              cudaMemcpyHostToDevice, st));
+      (k_cheb_init_packed<T><<<blocks(n * mc), TB, 0, st>>>(
+           s.HS[cur], s.MS[cur], ld, s.theta_d, s.active_d + nb, c->hdiag_f32.as<float>(), n, mc,
+           s.cres, s.cx, (float)(1.0 / th_c), s.cb0),
+       ::ff::note_launch());
+    } else {
+      FF_CUDA(cudaMemcpyAsync(s.active_d, active.data(), sizeof(int) * nb, cudaMemcpyHostToDevice,
+                              st));
+      (k_cheb_init<T><<<blocks(n * mc), TB, 0, st>>>(s.HS[cur], s.MS[cur], ld, s.theta_d,
+                                                    s.active_d, c->hdiag_f32.as<float>(), n, nb,
+                                                    mc, s.cres, s.cd0, s.cx,
+                                                    deg > 1 ? (float)(1.0 / th_c) : 1.f,
+                                                    b16 ? s.cb0 : nullptr), ::ff::note_launch());
+    }
     FF_LAUNCH_CHECK();
     if (deg > 1) {
       const double sigma1 = th_c / delta;
@@ -631,7 +699,12 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
         std::swap(bin, bout);
       }
     }
-    (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, mc, n, nb, W, ld), ::ff::note_launch());
+    if (packed)
+      (k_cast_packed<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, mc, s.active_d + nb + s.mc, n, nb,
+                                                       W, ld), ::ff::note_launch());
+    else
+      (k_cast_block<T><<<blocks(n * nb), TB, 0, st>>>(s.cx, mc, n, nb, W, ld),
+       ::ff::note_launch());
     FF_LAUNCH_CHECK();
     // M-project W against X, P and c0 (with the stored M X, M P, M c0)
     s.deflate(W, nb);
