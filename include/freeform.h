@@ -180,8 +180,10 @@ typedef struct {
                            BF16 dense tiles of 16-row blocks (block widths 8..64 in steps
                            of 8); 0: sparse FP32 H on CUDA cores (1) */
   int precond_compact;  /* 1: the preconditioner runs on the columns still above tol only,
-                           packed to a multiple of 8 (the others are zero either way, so
-                           the results are the same); 0: on the whole block (0) */
+                           packed to a multiple of 8 (the others are zero either way: the
+                           same results, bit for bit on tensor cores, to FP32 rounding of
+                           the preconditioned block on CUDA cores); 0: on the whole
+                           block (0) */
 } ff_eig_opts;
 
 typedef struct {

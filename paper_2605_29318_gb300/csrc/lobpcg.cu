@@ -643,7 +643,9 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     // steps take widths in multiples of 8, the padding columns stay zero
     const bool b16 = deg > 1 && s.mc % 8 == 0;
     // packed: only the columns above tol enter the steps, w of them rounded up
-    // to 8 (the steps treat every column alone, so W is the same either way)
+    // to 8 (the others are zero either way; on tensor cores W is bit-identical,
+    // the CUDA-core step's lane split follows the width, so there W changes at
+    // FP32 rounding)
     const bool packed = b16 && o.precond_compact;
     int mc = s.mc;
     if (packed) {
