@@ -274,3 +274,17 @@ def test_torus_grid_volume():
     exact = 2 * math.pi ** 2 * 0.5 * 0.2 ** 2
     assert abs(vols[1] - exact) < 0.01 * exact
     assert abs(vols[1] - exact) < abs(vols[0] - exact) + 1e-3 * exact
+
+
+def test_batch_generator_covers_every_particle():
+    """The batch generator's support floor: every particle is covered (strict
+    predicate |X_i - p_k| < a_k) by at least nine nodes, itself and its eight
+    nearest, so no moment matrix of the batch lacks support."""
+    from scipy.spatial import cKDTree
+    for c in synth.batch(6, seed=11, nmin=2000, nmax=6000):
+        X = c.X.astype(np.float64)
+        a = c.a.astype(np.float64)
+        cand = cKDTree(X).query_ball_point(X, float(a.max()))
+        cover = [int(np.sum(np.linalg.norm(X[cd] - X[i], axis=1) < a[cd]))
+                 for i, cd in enumerate(cand)]
+        assert min(cover) >= 9, c.name
