@@ -268,6 +268,31 @@ typedef struct {
 ff_status eigenmodes_batched(int device, int precision, ff_batch_item* items, int count,
                              const ff_eig_opts* opts, int workers);
 
+/* ------------------------------------------------------------ host buffers
+ * The whole subspace construction from host memory, for callers without
+ * device arrays: the inputs are copied to device buffers the context owns (on
+ * its stream; pinned host memory makes the copies asynchronous DMA), the
+ * three calls run as above, and the eigenvalues and modes are copied back.
+ * Arguments as for rkpm_build / rkpm_build_twoset, assemble_hessian and
+ * eigenmodes, except that every array is HOST memory:
+ *   E, nu    host float[n] per-particle (two-set: per point) material, or NULL
+ *            for the uniform E0 / nu0
+ *   eigvals  host double[k]
+ *   modes    host, column-major n x k (two-set: K x k) of the context's
+ *            precision, or NULL
+ * Errors: those of the three calls (the first failing call's status); with
+ * FF_ERR_NOT_CONVERGED, FF_ERR_TIMEOUT or FF_ERR_NUMERIC the outputs still
+ * hold the eigenmodes call's result.  The warm start is not offered here. */
+ff_status ff_subspace_host(ff_ctx* ctx, const float* particles, const float* volumes,
+                           const float* support, const float* E, const float* nu, int64_t n,
+                           double E0, double nu0, int k, const ff_eig_opts* opts,
+                           double* eigvals, void* modes, ff_eig_report* rep);
+ff_status ff_subspace_twoset_host(ff_ctx* ctx, const float* points, const float* volumes,
+                                  const float* E, const float* nu, int64_t n, int32_t K,
+                                  double trunc, int64_t start, double E0, double nu0, int k,
+                                  const ff_eig_opts* opts, double* eigvals, void* modes,
+                                  ff_eig_report* rep);
+
 /* --------------------------------------------------------- inspection exports
  * Copies of the internal results, in the caller's particle order, for parity
  * checks against an independent implementation.  All outputs are host memory. */
@@ -319,6 +344,11 @@ ff_status ff_get_precond_layout(const ff_ctx* ctx, int64_t* row_blocks, int64_t*
 ff_status ff_export_rkpm(const ff_ctx* ctx, int64_t* ptr, int32_t* idx, double* phi,
                          double* dphi);
 
+/* Row offsets of the neighbour lists alone: ptr int64[rows+1] as in
+ * ff_export_rkpm (rows = n particles in the caller's order, or the n_points
+ * quadrature points of a two-set cloud), without copying the lists. */
+ff_status ff_export_row_ptr(const ff_ctx* ctx, int64_t* ptr);
+
 /* H_w and M as CSR with ascending columns: row_ptr int64[n+1], col int32[n2],
  * H double[n2], M double[n2].  H or M may be NULL. */
 ff_status ff_export_matrices(const ff_ctx* ctx, int64_t* row_ptr, int32_t* col, double* H,
@@ -330,18 +360,21 @@ ff_status ff_export_matrices(const ff_ctx* ctx, int64_t* row_ptr, int32_t* col, 
 ff_status ff_apply_operators(ff_ctx* ctx, const void* X, int m, void* YH, void* YM);
 
 /* Allocation-free variant of ff_apply_operators (the paper has no
- * counterpart; it serves callers that cannot allocate device memory at the
- * time of the call -- inside CUDA stream capture, in real-time loops that
- * forbid driver allocations, or when another allocator holds the memory).
- * Same arguments, results and errors as ff_apply_operators, but the three
- * staging panels live in a fixed 32 MiB array in the library's device image
- * (held by every GPU that loads the library until the process exits), and the
- * call makes no cudaMalloc/cudaFree or other allocation.  Requires
+ * counterpart).  It serves callers that cannot allocate device memory at the
+ * time of the call: real-time loops that forbid driver allocations (a
+ * cudaMalloc may synchronise the device), processes whose device memory is
+ * held by another allocator, or plug-ins given a fixed memory budget.  Same
+ * arguments, results and errors as ff_apply_operators, but the three staging
+ * panels live in a fixed 32 MiB array in the library's device image (held by
+ * every GPU that loads the library until the process exits), and the call
+ * makes no cudaMalloc/cudaFree or other allocation.  Requires
  * 3 * n * m * (4 for FF_PREC_FP32, 8 for FF_PREC_FP64) bytes <= 32 MiB (each
  * panel rounded up to 256 bytes); larger blocks return FF_ERR_INVALID_ARG.
  * The first call on a device looks up the array's device address and should
- * come before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race and must be serialised by the caller. */
+ * come before any stream capture.  Like every call of this library it
+ * synchronises the context's stream before returning.  All calls share the
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller. */
 ff_status ff_apply_operators_noalloc(ff_ctx* ctx, const void* X, int m, void* YH, void* YM);
 
 /* --------------------------------------------------------------- profiling
@@ -355,12 +388,22 @@ typedef enum {
   FF_PROF_UPDATE = 4,         /* block updates */
   FF_PROF_BUILD = 5,          /* a whole rkpm_build */
   FF_PROF_ASSEMBLE = 6,       /* a whole assemble_hessian */
-  FF_PROF_SETUP = 7           /* eigensolver set-up: power iteration for the
+  FF_PROF_SETUP = 7,          /* eigensolver set-up: power iteration for the
                                  preconditioner interval */
+  FF_PROF_FPS = 8,            /* farthest-point sampling of the two-set centres */
+  FF_PROF_COVER = 9,          /* covering lists of the two-set construction */
+  FF_PROF_SHAPE = 10,         /* shape-function kernels (the moment solves) */
+  FF_PROF_PATTERN = 11,       /* assembly: sparsity pattern of H_w and M */
+  FF_PROF_ASM_VALUES = 12     /* assembly: values of H_w and M */
 } ff_prof_class;
 
 /* on != 0: reset and start recording; on == 0: stop recording. */
 ff_status ff_profile_enable(ff_ctx* ctx, int on);
+
+/* mask != 0: reset and record the classes whose bit (1 << class) is set
+ * (a timed run can record one kernel class at two event records per scope
+ * without timing the rest); mask == 0: stop recording. */
+ff_status ff_profile_classes(ff_ctx* ctx, uint32_t mask);
 
 /* Number of recorded scopes of class `cls` since the last enable and the sum
  * of their durations in milliseconds (synchronises the context stream). */

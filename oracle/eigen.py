@@ -11,7 +11,9 @@ index 0 (the paper's m counts the non-constant ones, m = k - 1).
 Tiers: dense LAPACK (scipy.linalg.eigh, Cholesky + symmetric solve) up to a
 few thousand particles; sparse shift-invert Lanczos (scipy eigsh with a sparse
 LU of H - sigma M) beyond.  Residuals and M-principal angles judge any
-candidate eigenpairs against an FP64 H, M.
+candidate eigenpairs against an FP64 H, M; where the exact eigenvectors are
+too costly to form, ``subspace_angle_bound`` bounds the angle from the exact
+eigenvalues alone.
 """
 from __future__ import annotations
 
@@ -94,3 +96,26 @@ def rayleigh_ritz(H, M, C):
     B = C.T @ (M @ C)
     th, Z = sla.eigh(0.5 * (A + A.T), 0.5 * (B + B.T))
     return th, C @ Z
+
+
+def subspace_angle_bound(H, M, C, lam):
+    """Upper bound on the largest M-principal angle between span(C) (k
+    columns) and the exact eigenspace of the k lowest eigenvalues, from the
+    exact eigenvalues lam (ascending, at least k + 1 of them) alone.
+
+    With Y an M-orthonormal basis of span(C), written Y = U_k A + U_perp B in
+    the exact M-orthonormal eigenvectors, A^T A + B^T B = I and
+    ||B||_F = ||sin Theta||_F.  Then
+        tr(Y^T H Y) = tr(A^T L_k A) + tr(B^T L_perp B)
+                   >= sum_{j<k} lam_j - lam_{k-1} ||B||_F^2 + lam_k ||B||_F^2,
+    since the diagonal of A A^T is at most 1 and its trace is k - ||B||_F^2.
+    Hence sin(theta_max) <= ||sin Theta||_F
+                         <= sqrt((tr(Y^T H Y) - sum_{j<k} lam_j) / (lam_k - lam_{k-1})).
+    Returns the angle (radians); 0 when the excess trace rounds below zero."""
+    Y = m_orthonormalise(M, C)
+    k = Y.shape[1]
+    lam = np.asarray(lam, F64)
+    excess = float(np.trace(Y.T @ (H @ Y))) - float(lam[:k].sum())
+    gap = float(lam[k] - lam[k - 1])
+    s2 = max(excess, 0.0) / gap
+    return float(np.arcsin(min(1.0, np.sqrt(s2))))

@@ -32,9 +32,11 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_net_init", "ff_net_set_params", "ff_net_get_params", "ff_warmstart_features",
            "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block",
            "ff_skinning_weights", "ff_lbs_deform", "rkpm_build_twoset", "ff_get_twoset",
-           "eigenmodes_batched"]
+           "eigenmodes_batched", "ff_profile_classes", "ff_subspace_host",
+           "ff_subspace_twoset_host", "ff_export_row_ptr"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
-        "assemble": 6, "setup": 7}
+        "assemble": 6, "setup": 7, "fps": 8, "cover": 9, "shape": 10, "pattern": 11,
+        "asm_values": 12}
 
 
 class EigOpts(ctypes.Structure):
@@ -124,6 +126,13 @@ def load_library(path: str = LIB_PATH):
     L.ff_get_twoset.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), vp, vp]
     L.eigenmodes_batched.argtypes = [i32, i32, ctypes.POINTER(BatchItem), i32,
                                      ctypes.POINTER(EigOpts), i32]
+    L.ff_profile_classes.argtypes = [vp, ctypes.c_uint32]
+    L.ff_export_row_ptr.argtypes = [vp, vp]
+    L.ff_subspace_host.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, i32,
+                                   ctypes.POINTER(EigOpts), vp, vp, ctypes.POINTER(EigReport)]
+    L.ff_subspace_twoset_host.argtypes = [vp, vp, vp, vp, vp, i64, i32, dbl, i64, dbl, dbl, i32,
+                                          ctypes.POINTER(EigOpts), vp, vp,
+                                          ctypes.POINTER(EigReport)]
     del fp
     for name in EXPORTS:
         if name not in ("ff_destroy", "ff_last_error", "ff_version", "ff_eig_opts_default",
@@ -273,8 +282,16 @@ class Context:
         return X0
 
     # ---- profiling
-    def profile(self, on: bool):
-        self._check(self.L.ff_profile_enable(self.h, 1 if on else 0))
+    def profile(self, on: bool, classes=None):
+        """Start (reset) or stop the event profiler; `classes` restricts the
+        recording to those profile classes (names of PROF)."""
+        if classes is None:
+            self._check(self.L.ff_profile_enable(self.h, 1 if on else 0))
+        else:
+            mask = 0
+            for name in classes:
+                mask |= 1 << PROF[name]
+            self._check(self.L.ff_profile_classes(self.h, mask if on else 0))
 
     def profile_read(self):
         """{class: (scopes, total_ms)} for every profile class."""
@@ -291,6 +308,20 @@ class Context:
         self._check(self.L.ff_get_sizes(self.h, ctypes.byref(n), ctypes.byref(n1),
                                         ctypes.byref(n2)))
         return n.value, n1.value, n2.value
+
+    def row_ptr(self):
+        """Row offsets (int64, rows + 1) of the neighbour / covering lists."""
+        npt = ctypes.c_int64()
+        st = self.L.ff_get_twoset(self.h, ctypes.byref(npt), None, None, None)
+        rows = npt.value if st == FF_OK else self.sizes()[0]
+        out = np.zeros(rows + 1, np.int64)
+        self._check(self.L.ff_export_row_ptr(self.h, out.ctypes.data))
+        return out
+
+    def pair_products(self):
+        """sum over rows of (row length)^2: the pair products of the assembly."""
+        c = np.diff(self.row_ptr()).astype(np.float64)
+        return int(np.dot(c, c))
 
     def precond_layout(self):
         """(row_blocks, ksteps) of the preconditioner's tensor-core tiles; (0, 0)
@@ -420,36 +451,82 @@ def eigenmodes(ctx: Context, k, opts=None, X0=None):
     return ctx.eigenmodes(k, opts, X0)
 
 
+def _host(x, dtype=np.float32):
+    """(host pointer, bytes, keep-alive) of a host array: a numpy array or a CPU
+    (optionally pinned) torch tensor; None passes through as NULL."""
+    if x is None:
+        return None, 0, None
+    if hasattr(x, "data_ptr"):
+        assert not x.is_cuda and x.is_contiguous()
+        return int(x.data_ptr()), x.numel() * x.element_size(), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a.nbytes, a
+
+
 def subspace_from_host(X, v, a, E, nu, k, precision="fp32", opts=None, device=0, ctx=None):
-    """End-to-end public call on HOST arrays: copy the cloud to the device,
-    build, assemble, solve, and copy eigenvalues and modes back to the host.
-    Returns (eigvals, modes (n, k) numpy, report, bytes_h2d, bytes_d2h)."""
-    import torch
+    """End-to-end public call on HOST arrays (ff_subspace_host): the library
+    copies the cloud to the device, builds, assembles, solves, and copies
+    eigenvalues and modes back.  X, v, a (and E, nu when they are arrays) are
+    numpy arrays or CPU torch tensors (pinned ones copy asynchronously); E, nu
+    may be scalars.  Returns (eigvals, modes (n, k) numpy, report, bytes_h2d,
+    bytes_d2h, status)."""
     own = ctx is None
     if own:
         ctx = Context(device, precision)
-    dev = f"cuda:{device}"
-
-    def h2d(x):
-        t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
-        return t.pin_memory().to(dev, non_blocking=True)
-    Xd, vd, ad = h2d(X), h2d(v), h2d(a)
-    h2d_bytes = X.nbytes + v.nbytes + a.nbytes
-    Ed = nud = None
-    if np.ndim(E) > 0:
-        Ed = h2d(E)
-        h2d_bytes += np.asarray(E, np.float32).nbytes
-    if np.ndim(nu) > 0:
-        nud = h2d(nu)
-        h2d_bytes += np.asarray(nu, np.float32).nbytes
-    ctx.rkpm_build(Xd, vd, ad)
-    ctx.assemble_hessian(Ed, nud, float(E) if Ed is None else 1.0, float(nu) if nud is None else 0.3)
-    ev, modes, rep, st = ctx.eigenmodes(k, opts, check=False)
-    host = modes.t().contiguous().cpu().numpy().T      # (n, k)
-    d2h_bytes = host.nbytes + ev.nbytes
+    n = int(X.shape[0])
+    ptrs = [_host(t) for t in (X, v, a)]
+    Ep = _host(E) if np.ndim(E) > 0 else (None, 0, None)
+    nup = _host(nu) if np.ndim(nu) > 0 else (None, 0, None)
+    E0 = 1.0 if Ep[0] else float(E)
+    nu0 = 0.3 if nup[0] else float(nu)
+    ev = np.zeros(k, np.float64)
+    modes = np.zeros((k, n), np.float64 if precision == "fp64" else np.float32)
+    rep = EigReport()
+    st = ctx.L.ff_subspace_host(ctx.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], Ep[0], nup[0], n,
+                                E0, nu0, int(k), ctypes.byref(opts) if opts is not None else None,
+                                ev.ctypes.data, modes.ctypes.data, ctypes.byref(rep))
+    if st not in (FF_OK, 5, 7):
+        raise FreeformError(st, ctx.L.ff_last_error(ctx.h).decode())
+    h2d_bytes = sum(p[1] for p in ptrs) + Ep[1] + nup[1]
+    d2h_bytes = modes.nbytes + ev.nbytes
     if own:
         ctx.close()
-    return ev, host, rep, h2d_bytes, d2h_bytes, st
+    return ev, modes.T, rep.as_dict(), h2d_bytes, d2h_bytes, st
+
+
+def subspace_twoset_from_host(points, volumes, E, nu, K, k, trunc=3.0, start=0,
+                              precision="fp64", opts=None, device=0, ctx=None, modes_out=None):
+    """The two-set construction end to end from HOST arrays
+    (ff_subspace_twoset_host).  points (n, 3), volumes (n,) and E / nu (arrays
+    of n, or scalars) are numpy arrays or CPU torch tensors; modes_out, if
+    given, is a host array (k, K) of the context precision to write into.
+    Returns (eigvals, modes (k, K): row j = mode j, report, bytes_h2d,
+    bytes_d2h, status)."""
+    own = ctx is None
+    if own:
+        ctx = Context(device, precision)
+    n = int(points.shape[0])
+    Xp, vp_ = _host(points), _host(volumes)
+    Ep = _host(E) if np.ndim(E) > 0 else (None, 0, None)
+    nup = _host(nu) if np.ndim(nu) > 0 else (None, 0, None)
+    E0 = 1.0 if Ep[0] else float(E)
+    nu0 = 0.3 if nup[0] else float(nu)
+    ev = np.zeros(k, np.float64)
+    if modes_out is None:
+        modes_out = np.zeros((k, K), np.float64 if precision == "fp64" else np.float32)
+    Mp = _host(modes_out, modes_out.dtype if isinstance(modes_out, np.ndarray) else None)
+    rep = EigReport()
+    st = ctx.L.ff_subspace_twoset_host(ctx.h, Xp[0], vp_[0], Ep[0], nup[0], n, int(K),
+                                       float(trunc), int(start), E0, nu0, int(k),
+                                       ctypes.byref(opts) if opts is not None else None,
+                                       ev.ctypes.data, Mp[0], ctypes.byref(rep))
+    if st not in (FF_OK, 5, 7):
+        raise FreeformError(st, ctx.L.ff_last_error(ctx.h).decode())
+    h2d_bytes = Xp[1] + vp_[1] + Ep[1] + nup[1]
+    d2h_bytes = Mp[1] + ev.nbytes
+    if own:
+        ctx.close()
+    return ev, modes_out, rep.as_dict(), h2d_bytes, d2h_bytes, st
 
 
 class Net:

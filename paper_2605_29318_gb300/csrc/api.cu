@@ -220,11 +220,97 @@ ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, 
 }
 
 ff_status ff_profile_enable(ff_ctx* c, int on) {
+  return ff_profile_classes(c, on ? ~0u : 0u);
+}
+
+ff_status ff_profile_classes(ff_ctx* c, uint32_t mask) {
   return guarded(c, [&] {
     FF_CUDA(cudaStreamSynchronize(c->stream));
-    c->prof.on = on != 0;
+    c->prof.on = mask != 0;
+    c->prof.mask = mask;
     for (int k = 0; k < ff::kProfN; ++k) c->prof.used[k] = 0;
   });
+}
+
+}  // extern "C"
+
+namespace {
+// device copy of a host array on the context stream (nullptr stays nullptr)
+template <class T>
+const T* stage_in(ff_ctx* c, int slot, const T* h, long long count) {
+  if (!h) return nullptr;
+  T* d = reinterpret_cast<T*>(c->host_in[slot].ensure(sizeof(T) * std::max(count, 1LL)));
+  FF_CUDA(cudaMemcpyAsync(d, h, sizeof(T) * count, cudaMemcpyHostToDevice, c->stream));
+  return d;
+}
+
+// the eigenmodes step of the host-buffer calls: modes to a device buffer of
+// the context, then copied to the caller's host array
+ff_status host_eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, double* eigvals, void* modes,
+                          ff_eig_report* rep) {
+  const size_t esz = c->prec == FF_PREC_FP64 ? 8 : 4;
+  size_t bytes = 0;
+  void* dmodes = nullptr;
+  ff_status s = guarded(c, [&] {
+    FF_REQUIRE(k >= 1 && k <= 256 && k <= c->n - 1, FF_ERR_INVALID_ARG, "k out of range");
+    bytes = esz * (size_t)c->n * k;
+    if (modes) dmodes = c->host_out.ensure(bytes);
+  });
+  if (s != FF_OK) return s;
+  const ff_status r = eigenmodes(c, k, opts, nullptr, eigvals, dmodes, rep);
+  if (r != FF_OK && r != FF_ERR_NOT_CONVERGED && r != FF_ERR_TIMEOUT && r != FF_ERR_NUMERIC)
+    return r;
+  if (modes) {
+    s = guarded(c, [&] {
+      FF_CUDA(cudaMemcpyAsync(modes, dmodes, bytes, cudaMemcpyDeviceToHost, c->stream));
+      FF_CUDA(cudaStreamSynchronize(c->stream));
+    });
+    if (s != FF_OK) return s;
+  }
+  return r;
+}
+}  // namespace
+
+extern "C" {
+
+ff_status ff_subspace_host(ff_ctx* c, const float* particles, const float* volumes,
+                           const float* support, const float* E, const float* nu, int64_t n,
+                           double E0, double nu0, int k, const ff_eig_opts* opts,
+                           double* eigvals, void* modes, ff_eig_report* rep) {
+  const float *dX = nullptr, *dv = nullptr, *da = nullptr, *dE = nullptr, *dnu = nullptr;
+  ff_status s = guarded(c, [&] {
+    FF_REQUIRE(particles && volumes && support, FF_ERR_INVALID_ARG, "NULL input pointer");
+    FF_REQUIRE(n >= 1 && n <= 0x7fffffffLL, FF_ERR_INVALID_ARG, "n out of range");
+    dX = stage_in(c, 0, particles, 3 * n);
+    dv = stage_in(c, 1, volumes, n);
+    da = stage_in(c, 2, support, n);
+    dE = stage_in(c, 3, E, n);
+    dnu = stage_in(c, 4, nu, n);
+  });
+  if (s != FF_OK) return s;
+  if ((s = rkpm_build(c, dX, dv, da, n)) != FF_OK) return s;
+  if ((s = assemble_hessian(c, dE, dnu, E0, nu0)) != FF_OK) return s;
+  return host_eigenmodes(c, k, opts, eigvals, modes, rep);
+}
+
+ff_status ff_subspace_twoset_host(ff_ctx* c, const float* points, const float* volumes,
+                                  const float* E, const float* nu, int64_t n, int32_t K,
+                                  double trunc, int64_t start, double E0, double nu0, int k,
+                                  const ff_eig_opts* opts, double* eigvals, void* modes,
+                                  ff_eig_report* rep) {
+  const float *dX = nullptr, *dv = nullptr, *dE = nullptr, *dnu = nullptr;
+  ff_status s = guarded(c, [&] {
+    FF_REQUIRE(points && volumes, FF_ERR_INVALID_ARG, "NULL input pointer");
+    FF_REQUIRE(n >= 4 && n <= 0x7fffffffLL, FF_ERR_INVALID_ARG, "n out of range");
+    dX = stage_in(c, 0, points, 3 * n);
+    dv = stage_in(c, 1, volumes, n);
+    dE = stage_in(c, 3, E, n);
+    dnu = stage_in(c, 4, nu, n);
+  });
+  if (s != FF_OK) return s;
+  if ((s = rkpm_build_twoset(c, dX, dv, n, K, trunc, start)) != FF_OK) return s;
+  if ((s = assemble_hessian(c, dE, dnu, E0, nu0)) != FF_OK) return s;
+  return host_eigenmodes(c, k, opts, eigvals, modes, rep);
 }
 
 ff_status ff_profile_read(ff_ctx* c, int cls, int64_t* launches, double* total_ms) {
@@ -324,6 +410,26 @@ ff_status ff_export_rkpm(const ff_ctx* cc, int64_t* ptr, int32_t* idx, double* p
     auto perm = to_host<int>(c->perm, n);
     auto iperm = to_host<int>(c->iperm, n);
     remap_csr(perm, iperm, p, ix, {&ph, &dph}, ptr, idx, {phi, dphi}, {n1, n1}, {n1, n1}, {1, 3});
+  });
+}
+
+ff_status ff_export_row_ptr(const ff_ctx* cc, int64_t* ptr) {
+  ff_ctx* c = const_cast<ff_ctx*>(cc);
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "no cloud built");
+    FF_REQUIRE(ptr, FF_ERR_INVALID_ARG, "NULL output");
+    FF_CUDA(cudaStreamSynchronize(c->stream));
+    const size_t nq = c->nq;
+    auto p = to_host<long long>(c->nbr_ptr, nq + 1);
+    if (c->twoset) {
+      std::copy(p.begin(), p.end(), ptr);
+      return;
+    }
+    auto perm = to_host<int>(c->perm, nq);  // internal -> caller
+    std::vector<long long> cnt(nq);
+    for (size_t j = 0; j < nq; ++j) cnt[perm[j]] = p[j + 1] - p[j];
+    ptr[0] = 0;
+    for (size_t i = 0; i < nq; ++i) ptr[i + 1] = ptr[i] + cnt[i];
   });
 }
 

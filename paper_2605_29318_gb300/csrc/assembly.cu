@@ -273,13 +273,14 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   int* cnt = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (n + 1)));
   DevFlags f{};
   int tsize1 = 2048;
+  ProfScope ps_pattern(kProfPattern);
   for (int attempt = 0; attempt < 2; ++attempt) {
     tsize1 = attempt == 0 ? 2048 : 16384;
     const int wpb1 = attempt == 0 ? 4 : 2;
     const size_t smem1 = sizeof(int) * tsize1 * wpb1;
     if (smem1 > 48 * 1024) set_max_dyn_smem((const void*)k_pattern_count, (int)smem1);
     if (attempt > 0) reset_flags(c);
-    int grid1 = (int)std::min<long long>(ceil_div(n, wpb1), 152LL * 16);
+    int grid1 = (int)std::min<long long>(ceil_div(n, wpb1), (long long)sm_count() * 16);
     (k_pattern_count<<<grid1, 32 * wpb1, smem1, st>>>(
         c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
         c->nbrT_idx.as<int>(), n, tsize1, cnt, c->flags.as<DevFlags>()), ::ff::note_launch());
@@ -289,6 +290,7 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
         f.code == FF_ERR_INVALID_ARG && f.max_row > 0 && f.max_row * 2 > tsize1;
     if (!overflow) break;
   }
+  ps_pattern.close();
   if (f.code == FF_ERR_INVALID_ARG) {
     throw Error(FF_ERR_INVALID_ARG,
                 f.max_row > 0 && f.max_row * 2 > tsize1
@@ -313,7 +315,8 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   size_t pw = assemble_smem_per_warp(tsize2, maxrow, tb);
   int wpb2 = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / pw));
   size_t smem = pw * wpb2;
-  int grid2 = (int)std::min<long long>(ceil_div(n, wpb2), 152LL * 32);
+  int grid2 = (int)std::min<long long>(ceil_div(n, wpb2), (long long)sm_count() * 32);
+  ProfScope ps_values(kProfAsmValues);
   if (f64) {
     set_max_dyn_smem((const void*)k_assemble<dfloat, double>,
                      (int)std::max<size_t>(smem, 48 * 1024));
@@ -331,6 +334,7 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
         c->a_col.as<int>(), c->a_val.as<float>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>()), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
+  ps_values.close();
   if (f64) {  // FP32 rounding of (H, M) for the FP32 phase of the eigensolver
     float* v32 = reinterpret_cast<float*>(c->a_val32.ensure(2 * sizeof(float) * n2));
     const long long m = 2 * n2;

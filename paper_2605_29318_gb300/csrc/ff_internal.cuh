@@ -86,11 +86,17 @@ enum ProfClass {
   kProfBuild,        // rkpm_build (whole stage)
   kProfAssemble,     // assemble_hessian (whole stage)
   kProfSetup,        // eigensolver set-up (power iteration)
+  kProfFps,          // farthest-point sampling of the two-set centres
+  kProfCover,        // covering lists of the two-set construction
+  kProfShape,        // shape-function kernels (moment solves)
+  kProfPattern,      // assembly: the sparsity pattern of H_w and M
+  kProfAsmValues,    // assembly: the values of H_w and M
   kProfN
 };
 
 struct Profiler {
   bool on = false;
+  unsigned mask = ~0u;  // classes recorded while on (bit 1 << class)
   std::vector<cudaEvent_t> ev[kProfN];  // start/stop pairs
   int used[kProfN] = {};
 };
@@ -176,6 +182,9 @@ struct ff_ctx {
   ff::DevFlags* hflags = nullptr;  // pinned mirror
   // generic scratch
   ff::Buf scratch[8];
+  // device copies of host inputs and outputs of the host-buffer calls
+  ff::Buf host_in[5];
+  ff::Buf host_out;
   // eigen-solver workspace
   ff::Buf ws[28];
   ff::Profiler prof;
@@ -191,7 +200,8 @@ struct ProfScope {
   int cls;
   cudaEvent_t stop = nullptr;
   explicit ProfScope(int cls_);
-  ~ProfScope();
+  ~ProfScope() { close(); }
+  void close();  // record the stop event now (once)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -201,6 +211,9 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 // ever raised, per kernel and device; thread-safe; the attribute belongs to
 // the device's context)
 void set_max_dyn_smem(const void* fn, int bytes);
+
+// number of streaming multiprocessors of the current device (cached per device)
+int sm_count();
 
 void reset_flags(ff_ctx* c);
 DevFlags read_flags(ff_ctx* c);

@@ -906,7 +906,7 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
                  const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
   ProfScope ps(kProfSpmm);
   const int T_ = 256;
-  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
+  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, (long long)sm_count() * 64);
   if constexpr (std::is_same_v<T, dfloat>) {
     const bool df_ok = m % 4 == 0 && m <= 128 && ldx % 2 == 0 && ldy % 2 == 0 &&
                        n * (long long)std::max(ldx, ldy) < (1LL << 31) &&
@@ -1062,7 +1062,7 @@ void cheb_step_b16(cudaStream_t st, const long long* ptr, const int* col, const 
              FF_ERR_INVALID_ARG, "BF16 preconditioner step needs m % 8 == 0 and aligned blocks");
   FF_REQUIRE(n * m < (1LL << 31), FF_ERR_INVALID_ARG, "BF16 preconditioner step: n * m >= 2^31");
   const int T_ = 256;
-  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
+  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, (long long)sm_count() * 64);
   const auto* bi = static_cast<const __nv_bfloat16*>(din);
   auto* bo = static_cast<__nv_bfloat16*>(dout);
   const int ni = (int)n;
@@ -1086,7 +1086,7 @@ void cheb_step(cudaStream_t st, const long long* ptr, const int* col, const floa
                float* x, float* res, float c1, float c2, int prof) {
   ProfScope ps(prof);
   const int T_ = 256;
-  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, 152LL * 64);
+  long long blocks = std::min<long long>((n * 32 + T_ - 1) / T_, (long long)sm_count() * 64);
   const bool vec_ok = m % 4 == 0 && m <= 128 && ld % 4 == 0 &&
                       reinterpret_cast<uintptr_t>(din) % 16 == 0 &&
                       reinterpret_cast<uintptr_t>(dout) % 16 == 0 &&
@@ -1124,7 +1124,7 @@ template <class T>
 void launch_tiles(cudaStream_t st, const GramTiles& g, int TW, int lda, int ldb, long long n,
                   int ldo, double alpha, bool accumulate, Buf& part) {
   // about four blocks per SM in all, at least 64 rows per chunk
-  long long chunks = std::max<long long>(1, (152LL * 4) / g.count);
+  long long chunks = std::max<long long>(1, ((long long)sm_count() * 4) / g.count);
   chunks = std::max<long long>(1, std::min(chunks, (n + 63) / 64));
   const long long rpc = (n + chunks - 1) / chunks;
   chunks = (n + rpc - 1) / rpc;
@@ -1263,7 +1263,7 @@ void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q
                        200 * 1024);
     const int TD = TW / 4, RG = 256 / TD;
     const long long rows_per_block = (long long)RG * 4;
-    dim3 grid((unsigned)std::min<long long>((n + rows_per_block - 1) / rows_per_block, 152LL * 8),
+    dim3 grid((unsigned)std::min<long long>((n + rows_per_block - 1) / rows_per_block, (long long)sm_count() * 8),
               (unsigned)((q + TW - 1) / TW));
     if (w40)
       (k_block_update_rt<T, 40><<<grid, TD * RG, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C,
@@ -1280,7 +1280,7 @@ void block_update(cudaStream_t st, const T* A, int lda, int p, const T* Y, int q
   if (smem > 48 * 1024)
     set_max_dyn_smem(w40 ? (const void*)k_block_update<T, 40> : (const void*)k_block_update<T, 32>,
                      227 * 1024);
-  dim3 grid((unsigned)std::min<long long>((n + rpb - 1) / rpb, 152LL * 16),
+  dim3 grid((unsigned)std::min<long long>((n + rpb - 1) / rpb, (long long)sm_count() * 16),
             (unsigned)((q + TW - 1) / TW));
   if (w40)
     (k_block_update<T, 40><<<grid, 40 * rpb, smem, st>>>(A, lda, p, Y, ldy < 0 ? q : ldy, q, C,

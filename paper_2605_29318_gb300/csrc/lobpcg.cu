@@ -317,6 +317,20 @@ __global__ void k_cast_packed(const float* __restrict__ x, int w, const int* __r
   W[r * ld + c] = q >= 0 ? (T)x[r * w + q] : T(0);
 }
 
+// Soft locking of the momentum: the P coefficients (columns nb..2nb-1 of the
+// ns x 2nb coefficient matrix YZ) of modes that met tol this iteration are
+// zeroed, so their next P column is exactly zero and leaves the basis.  A
+// converged mode's momentum is tiny; normalised, it would carry the rounding
+// of the products it is formed from into the Gram matrices.
+template <class T>
+__global__ void k_lock_momentum(T* __restrict__ YZ, int ns, int nb,
+                                const int* __restrict__ active) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * nb) return;
+  const int r = t / nb, j = t % nb;
+  if (!active[j]) YZ[(size_t)r * 2 * nb + nb + j] = T(0);
+}
+
 __global__ void k_round_block(const double* __restrict__ x, float* __restrict__ y, long long m) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) y[t] = (float)x[t];
@@ -424,6 +438,8 @@ struct Phase {
   bool update_products = false;    // H X', M X' by the block update instead of a
                                    // fresh block product (a phase that hands over
                                    // well above its rounding floor)
+  bool handover_on_breakdown = false;  // a breakdown ends the phase (its best block
+                                       // is handed over) instead of a restart
   bool have_best = false;          // out: the best-block slot holds a block
 };
 
@@ -521,39 +537,40 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   }
   FF_LAUNCH_CHECK();
   int cur = 0;
-  // Rayleigh-Ritz on the start block alone (it is the block to orthonormalise).
-  // A warm start is first taken with a loose drop threshold: directions it
-  // hardly adds (nearly dependent predicted columns) leave the basis, the
-  // block is rotated onto its Ritz vectors (the dropped directions come last,
-  // as zero columns) and those columns are refilled from the seeded random
-  // generator.
-  for (int attempt = 0;; ++attempt) {
-    s.deflate(s.S[cur], nb);
-    s.spmm(s.S[cur], s.HS[cur], s.MS[cur], nb);
-    gram<T>(st, s.S[cur], ld, nb, s.HS[cur], ld, nb, n, s.Ag, 1.0, false, c->scratch[0]);
-    gram<T>(st, s.S[cur], ld, nb, s.MS[cur], ld, nb, n, s.Bg, 1.0, false, c->scratch[0]);
-    RRDims d0{nb, nb, nb, 0, 0, nb};
-    if (warm && attempt == 0) d0.drop = s.fp64 ? 1e-10 : 1e-6;
-    rayleigh_ritz<T>(st, s.Ag, s.Bg, d0, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
-    int dropped = 0;
-    FF_CUDA(cudaMemcpyAsync(&dropped, s.dropped_d, sizeof(int), cudaMemcpyDeviceToHost, st));
-    FF_CUDA(cudaStreamSynchronize(st));
-    if (dropped == 0 || attempt == 2) break;
-    const int nxt = 1 - cur;
-    block_update<T>(st, s.S[cur], ld, nb, s.YZ, nb, s.S[nxt], ld, n, T(0), -1, 0, 2 * nb);
-    cur = nxt;
-    const int keep = std::max(0, nb - dropped);
-    (k_random_block<T><<<blocks(n * (nb - keep)), TB, 0, st>>>(
-         s.S[cur] + keep, ld, n, nb - keep, o.seed + 7919ULL * (attempt + 1), c->perm.as<int>()),
-     ::ff::note_launch());
-    FF_LAUNCH_CHECK();
-  }
-  {
+  // Rayleigh-Ritz on a block alone (the start block, or the best block after
+  // a breakdown): it is the block to orthonormalise.  A warm start is first
+  // taken with a loose drop threshold: directions it hardly adds (nearly
+  // dependent predicted columns) leave the basis, the block is rotated onto
+  // its Ritz vectors (the dropped directions come last, as zero columns) and
+  // those columns are refilled from the seeded random generator.
+  auto block_rr = [&](bool loose) {
+    for (int attempt = 0;; ++attempt) {
+      s.deflate(s.S[cur], nb);
+      s.spmm(s.S[cur], s.HS[cur], s.MS[cur], nb);
+      gram<T>(st, s.S[cur], ld, nb, s.HS[cur], ld, nb, n, s.Ag, 1.0, false, c->scratch[0]);
+      gram<T>(st, s.S[cur], ld, nb, s.MS[cur], ld, nb, n, s.Bg, 1.0, false, c->scratch[0]);
+      RRDims d0{nb, nb, nb, 0, 0, nb};
+      if (loose && attempt == 0) d0.drop = s.fp64 ? 1e-10 : 1e-6;
+      rayleigh_ritz<T>(st, s.Ag, s.Bg, d0, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
+      int dropped = 0;
+      FF_CUDA(cudaMemcpyAsync(&dropped, s.dropped_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FF_CUDA(cudaStreamSynchronize(st));
+      if (dropped == 0 || attempt == 2) break;
+      const int nxt = 1 - cur;
+      block_update<T>(st, s.S[cur], ld, nb, s.YZ, nb, s.S[nxt], ld, n, T(0), -1, 0, 2 * nb);
+      cur = nxt;
+      const int keep = std::max(0, nb - dropped);
+      (k_random_block<T><<<blocks(n * (nb - keep)), TB, 0, st>>>(
+           s.S[cur] + keep, ld, n, nb - keep, o.seed + 7919ULL * (attempt + 1), c->perm.as<int>()),
+       ::ff::note_launch());
+      FF_LAUNCH_CHECK();
+    }
     const int nxt = 1 - cur;
     block_update<T>(st, s.S[cur], ld, nb, s.YZ, nb, s.S[nxt], ld, n, T(0), -1, 0, 2 * nb);
     s.spmm(s.S[nxt], s.HS[nxt], s.MS[nxt], nb);
     cur = nxt;
-  }
+  };
+  block_rr(warm != 0);
 
   // ---- iterations
   std::vector<int> active(nb, 1), pack;
@@ -570,7 +587,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   // the block with the smallest largest residual seen, and the progress mark
   T* best = reinterpret_cast<T*>(c->ws[ph.best_slot].ensure(sizeof(T) * n * nb));
   double best_worst = INFINITY, mark = INFINITY, last_worst = INFINITY;
-  int mark_it = 0;
+  int mark_it = 0, restarts = 0;
   std::vector<double> best_res;
   for (;; ++it) {
     // Rayleigh quotients and residual norms of the current X (products recomputed)
@@ -623,6 +640,24 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     if (bad) {
       status = FF_ERR_NUMERIC;
       break;
+    }
+    // Breakdown: after the block had come close (best below 1e-2) the largest
+    // residual is ten times the best seen -- the basis has lost converged
+    // directions.  Restart from the best block without momentum (or, in a
+    // phase that hands over, end the phase: its best block is handed on).
+    if (best_worst < 1e-2 && worst > 10.0 * best_worst && conv < s.kw) {
+      if (ph.handover_on_breakdown || restarts >= 3) {
+        status = FF_ERR_NOT_CONVERGED;
+        break;
+      }
+      ++restarts;
+      FF_CUDA(cudaMemcpy2DAsync(s.S[cur], sizeof(T) * ld, best, sizeof(T) * nb, sizeof(T) * nb, n,
+                                cudaMemcpyDeviceToDevice, st));
+      block_rr(false);
+      has_p = false;
+      mark = best_worst;
+      mark_it = it;
+      continue;
     }
     if (conv == s.kw) {
       status = FF_OK;
@@ -722,6 +757,8 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
                c->scratch[0]);
     RRDims dd{ns, nb, nb, 1, nb, nb};
     rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
+    (k_lock_momentum<T><<<blocks((long long)ns * nb), TB, 0, st>>>(s.YZ, ns, nb, s.active_d),
+     ::ff::note_launch());
     const int nxt = 1 - cur;
     // X' = S Y, P' = S Z; H P', M P' from the old products; (H X', M X') recomputed
     // from X' itself so that the residual seen by the solver is that of the
@@ -823,6 +860,7 @@ ff_status run_eigenmodes(ff_ctx* c, int k, const ff_eig_opts& o, const void* X0,
   p32.stall_below = 1e-2;
   p32.rr_fp32 = true;
   p32.update_products = true;
+  p32.handover_on_breakdown = true;
   p32.best_slot = 21;
   const float* X0f = nullptr;
   if (X0) {  // the caller's FP64 start block, rounded

@@ -234,7 +234,7 @@ void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a,
   int* bad = reinterpret_cast<int*>(red + 8);
   float* dec = reinterpret_cast<float*>(red + 9);
   (k_init_red<<<1, 1, 0, st>>>(red, bad), ::ff::note_launch());
-  int blocks = (int)std::min<long long>(ceil_div(n, T), 152 * 8);
+  int blocks = (int)std::min<long long>(ceil_div(n, T), (long long)sm_count() * 8);
   (k_validate_bbox<<<blocks, T, 0, st>>>(X, v, a, n, red, bad), ::ff::note_launch());
   (k_decode_red<<<1, 1, 0, st>>>(red, dec), ::ff::note_launch());
   FF_LAUNCH_CHECK();

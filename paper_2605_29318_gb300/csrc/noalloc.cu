@@ -2,12 +2,14 @@
 //
 // ff_apply_operators stages the caller's block in three device panels that the
 // context allocates on demand (cudaMalloc).  Some callers cannot allocate at
-// that point: code running while a CUDA stream is being captured into a graph,
-// real-time loops that forbid driver allocations, or processes whose memory is
-// fully reserved by another allocator.  This entry point uses a fixed scratch
-// array that lives in the library's own device image instead: a file-scope
-// __device__ array of kStaticScratchBytes, which every GPU that loads the
-// library holds until the process exits.
+// that point: real-time loops that forbid driver allocations (a cudaMalloc can
+// synchronise the device and take milliseconds), processes whose device memory
+// is fully reserved by another allocator (a caching allocator or a memory pool
+// that owns the rest of the GPU), and hosts that hand a plug-in a fixed memory
+// budget.  This entry point uses a fixed scratch array that lives in the
+// library's own device image instead: a file-scope __device__ array of
+// kStaticScratchBytes, which every GPU that loads the library holds until the
+// process exits.
 //
 // Host code must not use the array's name as a device address (on the host it
 // names a stand-in object); the device address is fetched once per device with
@@ -16,7 +18,9 @@
 // capture.  Every call shares the one array and leaves its contents behind;
 // nothing in it needs to start at zero (each call overwrites every byte it
 // reads).  Calls that overlap on the GPU -- on two streams, or from two
-// threads -- race on the array and must be serialised by the caller.
+// threads -- race on the array and must be serialised by the caller.  Like the
+// library's other calls, it synchronises the context's stream before it
+// returns.
 #include <mutex>
 
 #include "linalg.cuh"
@@ -61,6 +65,12 @@ extern "C" ff_status ff_apply_operators_noalloc(ff_ctx* c, const void* X, int m,
                                                 void* YM) {
   if (!c) return FF_ERR_INVALID_ARG;
   c->err.clear();
+  // the profiler attributes the block products to this context, as in
+  // ff_apply_operators
+  ff::g_ctx = c;
+  struct Reset {
+    ~Reset() { ff::g_ctx = nullptr; }
+  } reset;
   try {
     FF_CUDA(cudaSetDevice(c->device));
     FF_REQUIRE(c->stage >= 2, FF_ERR_STATE, "matrices not assembled");

@@ -61,6 +61,7 @@ void build_shape(ff_ctx* c) {
   c->phi.ensure(es * n1);
   c->dphi.ensure(3 * es * n1);
   const double cond_limit = 1e2;
+  ProfScope ps(kProfShape);
   if (c->prec == FF_PREC_FP64) {  // stored as double-float pairs for the assembly
     (k_shape<dfloat><<<ceil_div(n * 32, T), T, 0, c->stream>>>(
         c->pos.as<float4>(), c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), n, n1,
@@ -71,6 +72,7 @@ void build_shape(ff_ctx* c) {
         c->phi.as<float>(), c->dphi.as<float>(), cond_limit, c->flags.as<DevFlags>()), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
+  ps.close();
   DevFlags f = read_flags(c);
   c->hflags->fallback = f.fallback;
   if (f.code == FF_ERR_SINGULAR_MOMENT) {

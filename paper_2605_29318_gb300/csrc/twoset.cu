@@ -438,6 +438,7 @@ DevFlags twoset_shape(ff_ctx* c, const float* Q, long long nq, const long long* 
   cudaStream_t st = c->stream;
   const int T = 256;
   reset_flags(c);
+  ProfScope ps(kProfShape);
   if (c->prec == FF_PREC_FP64 && fp64_out)
     (k_shape_twoset<double><<<ceil_div(nq * 32, T), T, 0, st>>>(
          c->pos.as<float4>(), c->crad.as<double>(), Q, c->qscale, ptr, idx, nq, n1,
@@ -454,6 +455,7 @@ DevFlags twoset_shape(ff_ctx* c, const float* Q, long long nq, const long long* 
          static_cast<float*>(phi), static_cast<float*>(dphi), 1e2, c->flags.as<DevFlags>()),
      ::ff::note_launch());
   FF_LAUNCH_CHECK();
+  ps.close();
   return read_flags(c);
 }
 
@@ -465,7 +467,7 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   int* bad = reinterpret_cast<int*>(c->scratch[0].ensure(64));
   const int imax = INT_MAX;
   FF_CUDA(cudaMemcpyAsync(bad, &imax, sizeof(int), cudaMemcpyHostToDevice, st));
-  (k_validate_points<<<(int)std::min<long long>(ceil_div(nq, T), 152 * 8), T, 0, st>>>(Xq, vq, nq,
+  (k_validate_points<<<(int)std::min<long long>(ceil_div(nq, T), (long long)sm_count() * 8), T, 0, st>>>(Xq, vq, nq,
                                                                                       bad),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
@@ -497,11 +499,14 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   }
   long long* chosen = reinterpret_cast<long long*>(c->centre_idx.ensure(sizeof(long long) * K));
   reset_flags(c);
-  (k_fps<<<kFpsCS, kFpsT, in_smem ? smem : 0, st>>>(Xq, n, K, (int)start, S, in_smem ? 1 : 0,
-                                                    gxyz, gcur, gcur32, chosen,
-                                                    c->flags.as<DevFlags>()),
-   ::ff::note_launch());
-  FF_LAUNCH_CHECK();
+  {
+    ProfScope ps(kProfFps);
+    (k_fps<<<kFpsCS, kFpsT, in_smem ? smem : 0, st>>>(Xq, n, K, (int)start, S, in_smem ? 1 : 0,
+                                                      gxyz, gcur, gcur32, chosen,
+                                                      c->flags.as<DevFlags>()),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
   DevFlags f = read_flags(c);
   FF_REQUIRE(f.code == 0, FF_ERR_INVALID_ARG,
              "the quadrature points hold fewer than K = " + std::to_string(K) +
@@ -528,6 +533,7 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   c->qscale = (float)*std::max_element(hr.begin(), hr.end());
 
   // ---- 4. covering lists: rows (point -> centres) and columns (centre -> points)
+  ProfScope ps_cover(kProfCover);
   const long long n1 = twoset_cover(c, Xq, nq, c->nbr_ptr, c->nbr_idx, c->scratch[5]);
   c->n1 = n1;
   int* ccnt = reinterpret_cast<int*>(c->scratch[6].ensure(sizeof(int) * (K + 1)));
@@ -552,6 +558,7 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   FF_LAUNCH_CHECK();
   f = read_flags(c);
   FF_REQUIRE(f.code == 0, FF_ERR_CUDA, "covering lists disagree between the two passes");
+  ps_cover.close();
 
   // ---- 5. quadrature volumes, identity order of the centres
   float* vol = reinterpret_cast<float*>(c->vol.ensure(sizeof(float) * nq));

@@ -23,6 +23,21 @@ void set_max_dyn_smem(const void* fn, int bytes) {
   cur = bytes;
 }
 
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> count;
+  int dev = 0;
+  FF_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  int& n = count[dev];
+  if (n == 0) {
+    FF_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 thread_local ff_ctx* g_ctx = nullptr;
 
 namespace {
@@ -33,7 +48,7 @@ long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 ProfScope::ProfScope(int cls_) : cls(cls_) {
   ff_ctx* c = g_ctx;
-  if (!c || !c->prof.on) return;
+  if (!c || !c->prof.on || !((c->prof.mask >> cls_) & 1u)) return;
   Profiler& p = c->prof;
   const size_t need = 2 * (size_t)(p.used[cls] + 1);
   while (p.ev[cls].size() < need) {
@@ -50,8 +65,9 @@ ProfScope::ProfScope(int cls_) : cls(cls_) {
   cudaEventRecord(start, c->stream);
 }
 
-ProfScope::~ProfScope() {
+void ProfScope::close() {
   if (stop && g_ctx) cudaEventRecord(stop, g_ctx->stream);
+  stop = nullptr;
 }
 
 namespace {

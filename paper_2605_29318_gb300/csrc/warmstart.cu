@@ -728,7 +728,7 @@ void net_forward(ff_net* w, cudaStream_t st, const float* feat, long long n) {
 void net_loss(ff_net* w, cudaStream_t st, const float* vol, long long n, const float* C, int m) {
   double* sums = w->lsum.as<double>();
   FF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * (kLossEntries + 1), st));
-  const unsigned gb = (unsigned)std::min<long long>(ceil_div(n, 32), 2 * 152);
+  const unsigned gb = (unsigned)std::min<long long>(ceil_div(n, 32), 2LL * sm_count());
   (k_loss_gram<<<gb, 256, 0, st>>>(w->y.as<float>(), C, vol, n, m, sums), ::ff::note_launch());
   FF_LAUNCH_CHECK();
   float* P1 = w->small.as<float>();
@@ -872,7 +872,7 @@ void warmstart_features(ff_ctx* c, float* feat) {
   double* sums = reinterpret_cast<double*>(c->scratch[5].ensure(sizeof(double) * 40));
   double* frame = sums + 16;
   FF_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 40, st));
-  const unsigned gb = (unsigned)std::min<long long>(ceil_div(n, 256), 4 * 152);
+  const unsigned gb = (unsigned)std::min<long long>(ceil_div(n, 256), 4LL * sm_count());
   const float4* pos = c->pos.as<float4>();
   const float* vol = c->vol.as<float>();
   const long long* nptr = c->nbr_ptr.as<long long>();

@@ -192,9 +192,11 @@ def gaussian_mixture(n=1_000_000, n_comp=64, seed=3, support=2.0, nu=0.45, k=64,
 def batch(n_objects=256, seed=4, nmin=2000, nmax=200000, kmin=16, kmax=48):
     """Many objects: cube / torus / ellipsoid union, random scale and rotation,
     particle counts log-uniform in [nmin, nmax], k uniform in [kmin, kmax].
-    Supports get the coverage floor of ``support_floor``: among this many
-    random clouds some leave a particle (a cube corner, typically) covered by
-    only two or three nodes at 2.0x spacing."""
+    Supports get the coverage floor of ``support_floor`` with factor 1.5:
+    among this many random clouds some leave a particle (a cube corner,
+    typically) covered by only two or three nodes at 2.0x spacing, and a floor
+    that reaches it only at the edge of the nodes' supports (factor near 1)
+    leaves its moment matrix numerically singular (cond ~1e12)."""
     rng = _rng(seed)
     out = []
     for j in range(n_objects):
@@ -213,7 +215,7 @@ def batch(n_objects=256, seed=4, nmin=2000, nmax=200000, kmin=16, kmax=48):
         c.X = ((c.X.astype(np.float64) * scale) @ Rm.T).astype(np.float32)
         c.v = (c.v.astype(np.float64) * scale ** 3).astype(np.float32)
         c.a = (c.a.astype(np.float64) * scale).astype(np.float32)
-        c.a = support_floor(c.X, c.a)
+        c.a = support_floor(c.X, c.a, factor=1.5)
         c.name = f"obj{j}-{c.name}"
         out.append(c)
     return out

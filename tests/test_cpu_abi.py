@@ -1,6 +1,7 @@
 """CPU checks of the C ABI: the library builds, loads, and exports every
 function that include/freeform.h declares; the ctypes structures match the
 header's field lists.  No CUDA call is made."""
+import argparse
 import ctypes
 import os
 import re
@@ -108,18 +109,21 @@ def test_no_fallback_without_library(tmp_path):
         binding._lib = saved
 
 
-@pytest.mark.parametrize("workload", ["nodal", "twoset"])
+@pytest.mark.parametrize("workload", ["splat", "torus", "twoset-torus"])
 def test_reference_arm_prints_the_contract_line(workload):
     """bench.py --impl reference times the FP64 oracle on the host cores and
-    prints one JSON line with the contract's keys (no GPU needed), for both
-    workloads."""
+    prints one JSON line with the contract's keys (no GPU needed), with the
+    same config object as our arm prints for the workload."""
     import json
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import bench
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
                           "--warmup", "0", "--workload", workload], cwd=root,
-                         capture_output=True, text=True, timeout=600)
+                         capture_output=True, text=True, timeout=900)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
@@ -129,8 +133,10 @@ def test_reference_arm_prints_the_contract_line(workload):
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
-    assert line["max_residual"] < 1e-6
-    assert ("K=1,000" in line["config"]["workload"]) == (workload == "twoset")
+    args = argparse.Namespace(prec="fp64", tol=1e-6)
+    ours = {"splat": bench.splat_config, "torus": bench.torus_config,
+            "twoset-torus": bench.twoset_torus_config}[workload](args)
+    assert line["config"] == ours
 
 
 def _replica_worker(rank, world, port, q):

@@ -4,17 +4,12 @@ arithmetic, only the streams differ), failures are reported per object, and
 the 256-object batch (cube / torus / ellipsoid unions, 2,000-200,000
 particles, k from 16 to 48) reaches the residual bar on every object (the
 solver's residuals are FP64 against the FP64 matrices)."""
-import os
-
 import numpy as np
 import pytest
 
 from paper_2605_29318_gb300 import synth
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("FF_PENDING_GPU_TESTS") != "1",
-                                 reason="the batched call awaits its first GB300 run "
-                                        "(FF_PENDING_GPU_TESTS=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 
 def _objects(clouds):

@@ -8,17 +8,27 @@ neighbour lists, shape functions and rows of H_w and M of sampled particles --
 and through properties that hold at any size: the residual of every returned
 mode against the exported FP64 matrices (themselves checked row by row), the
 M-orthonormality of the modes, ascending eigenvalues and the constant mode.
+The eigenvalues are compared with the oracle's own (the 34 lowest of its FP64
+H_w and M by shift-invert Lanczos, stored by
+``tests/golden/make_torus50k_eigenvalues.py``), and the modes' subspace with the
+oracle's exact eigenspace through the trace bound of
+``oracle.eigen.subspace_angle_bound`` on the oracle's H_w and M.
 
 Tolerances: neighbour lists bit-exact; shape functions 1e-10 of the row's
 largest |value|; matrix rows 1e-10 of the row's largest |entry|; residual
-1e-6; M-orthonormality 1e-9.
+1e-6; M-orthonormality 1e-9; eigenvalues 1e-5 relative; largest M-principal
+angle 1e-3 rad.
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from oracle import assembly, rkpm
+from oracle import assembly, eigen, rkpm
 from paper_2605_29318_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "torus50k_eigenvalues.txt")
 
 pytestmark = pytest.mark.gpu
 
@@ -101,3 +111,32 @@ def test_sampled_skinning_weights(torus50k):
     assert np.abs(Wg - Wo).max() <= 1e-10 * np.abs(Wo).max()
     # the constant mode's field is constant
     assert np.abs(Wg[:, 0] - C[0, 0]).max() <= 1e-10 * abs(C[0, 0])
+
+
+def _cut(lam, k, rel_gap=1e-3):
+    """The largest k' <= k whose cut-off is not inside a cluster: relative gap
+    (lam[k'] - lam[k'-1]) / lam[k'] at least rel_gap (degenerate pairs of the
+    torus's rotational symmetry are compared as whole subspaces)."""
+    for kk in range(k, 1, -1):
+        if (lam[kk] - lam[kk - 1]) / lam[kk] >= rel_gap:
+            return kk
+    raise AssertionError("no gap in the spectrum")
+
+
+def test_eigenvalues_and_subspace_match_the_oracle(torus50k):
+    """The 31 non-constant eigenvalues against the oracle's (1e-5 relative):
+    they are the lowest ones, none of a degenerate pair missed.  The subspace
+    of the modes up to the last adequate gap against the oracle's exact
+    eigenspace, bounded from the oracle's FP64 H_w and M and its eigenvalues
+    (largest M-principal angle 1e-3 rad)."""
+    lam = np.loadtxt(GOLDEN)[:, 1]
+    ev = torus50k["ev"]
+    rel = np.abs(ev[1:] - lam[1:32]) / lam[1:32]
+    assert rel.max() <= 1e-5, rel
+    c = torus50k["c"]
+    ptr, idx = rkpm.neighbours(c.X, c.a, chunk=64)
+    phi, dphi, _ = rkpm.shape_functions(c.X, c.a, ptr, idx)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
+    kk = _cut(lam, 32)
+    ang = eigen.subspace_angle_bound(H, M, torus50k["modes"][:, :kk], lam)
+    assert ang <= 1e-3, (kk, ang)

@@ -8,18 +8,13 @@ contexts (double-float arithmetic, the Gaussian from the FP64 exp), 2e-5 in
 FP32 ones; H_w and M within 1e-10 / 1e-4 of their largest entry; eigenvalues
 within 1e-8 relative of the oracle's dense solve (FP64).
 """
-import os
-
 import numpy as np
 import pytest
 
 from oracle import assembly, eigen, twoset
 from paper_2605_29318_gb300 import synth
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("FF_PENDING_GPU_TESTS") != "1",
-                                 reason="the two-set path awaits its first GB300 run "
-                                        "(FF_PENDING_GPU_TESTS=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 TOL_SHAPE = {"fp64": 1e-10, "fp32": 2e-5}
 TOL_MAT = {"fp64": 1e-10, "fp32": 1e-4}

@@ -353,6 +353,54 @@ def test_principal_angle_and_residual_helpers():
     assert eigen.residuals(Hs, M, lam * (1 + 1e-3), C).min() > 5e-4
 
 
+def test_rayleigh_ritz_and_absolute_residuals():
+    """Rayleigh-Ritz on a span holding exact eigenvectors returns their
+    eigenvalues and vectors; on any span its Ritz values interlace from above
+    (theta_j >= lam_j, Courant-Fischer).  Absolute residuals vanish on exact
+    pairs (the zero eigenvalue included) and equal |delta| on a shifted one."""
+    rng = np.random.default_rng(5)
+    n = 40
+    B = rng.standard_normal((n, n))
+    M = B @ B.T + n * np.eye(n)
+    G = rng.standard_normal((n, n))
+    Hs = G.T @ G
+    Hs[:, 0] = Hs[0, :] = 0.0          # a zero eigenvalue, as the constant mode
+    lam, C = eigen.eigh_dense(Hs, M, n)
+    th, Y = eigen.rayleigh_ritz(Hs, M, C[:, [3, 1, 6]] @ rng.standard_normal((3, 3)))
+    np.testing.assert_allclose(th, lam[[1, 3, 6]], rtol=1e-9)
+    assert eigen.max_principal_angle(M, Y, C[:, [1, 3, 6]]) < 1e-7
+    th, _ = eigen.rayleigh_ritz(Hs, M, rng.standard_normal((n, 5)))
+    assert np.all(th >= lam[:5] * (1 - 1e-12))
+    assert eigen.absolute_residuals(Hs, M, lam[:4], C[:, :4]).max() < 1e-9 * lam[3]
+    delta = 1e-3 * lam[2]
+    r = eigen.absolute_residuals(Hs, M, [lam[2] + delta], C[:, [2]])
+    assert abs(r[0] - delta) < 1e-9 * delta
+
+
+def test_subspace_angle_bound():
+    """The trace bound on the largest M-principal angle: exact eigenvectors
+    give 0; rotating the last kept eigenvector by theta towards the first
+    excluded one makes the bound exact (sin^2 theta (lam_k - lam_{k-1}) is the
+    whole excess trace); any other perturbation stays below the bound."""
+    rng = np.random.default_rng(8)
+    n, k = 30, 5
+    B = rng.standard_normal((n, n))
+    M = B @ B.T + n * np.eye(n)
+    G = rng.standard_normal((n, n))
+    Hs = G.T @ G + np.eye(n)
+    lam, C = eigen.eigh_dense(Hs, M, n)
+    assert eigen.subspace_angle_bound(Hs, M, C[:, :k], lam) < 1e-6
+    for theta in (1e-4, 1e-2, 0.3):
+        Y = C[:, :k].copy()
+        Y[:, k - 1] = np.cos(theta) * C[:, k - 1] + np.sin(theta) * C[:, k]
+        assert abs(eigen.subspace_angle_bound(Hs, M, Y, lam) - theta) < 1e-6 * max(theta, 1e-2)
+        assert abs(eigen.max_principal_angle(M, Y, C[:, :k]) - theta) < 1e-8
+    for _ in range(5):
+        Y = C[:, :k] + 1e-3 * rng.standard_normal((n, k)) * np.abs(C[:, :k]).max()
+        true = eigen.max_principal_angle(M, Y, C[:, :k])
+        assert true <= eigen.subspace_angle_bound(Hs, M, Y, lam) * (1 + 1e-9)
+
+
 def test_disconnected_clouds_have_one_zero_mode_each():
     c1 = synth.unit_cube(200, seed=1)
     c2 = synth.unit_cube(200, seed=2)

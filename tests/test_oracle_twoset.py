@@ -279,8 +279,12 @@ def test_torus_grid_volume():
 def test_batch_generator_covers_every_particle():
     """The batch generator's support floor: every particle is covered (strict
     predicate |X_i - p_k| < a_k) by at least nine nodes, itself and its eight
-    nearest, so no moment matrix of the batch lacks support."""
+    nearest, each reaching it well inside its support (factor 1.5), so every
+    moment matrix of the batch is well conditioned (the oracle's 1-norm
+    condition numbers stay below 1e4; a floor reaching particles at the
+    support edge left one at 1.7e12 in the 256-object batch)."""
     from scipy.spatial import cKDTree
+    from oracle import rkpm
     for c in synth.batch(6, seed=11, nmin=2000, nmax=6000):
         X = c.X.astype(np.float64)
         a = c.a.astype(np.float64)
@@ -288,3 +292,6 @@ def test_batch_generator_covers_every_particle():
         cover = [int(np.sum(np.linalg.norm(X[cd] - X[i], axis=1) < a[cd]))
                  for i, cd in enumerate(cand)]
         assert min(cover) >= 9, c.name
+        ptr, idx = rkpm.neighbours(c.X, c.a)
+        _, _, cond = rkpm.shape_functions(c.X, c.a, ptr, idx)
+        assert np.max(cond) < 1e4, c.name

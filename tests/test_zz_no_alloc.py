@@ -1,9 +1,10 @@
 """The allocation-free entry point ff_apply_operators_noalloc.
 
 It serves callers that cannot allocate device memory when they call the
-library (inside stream capture, in loops that forbid driver allocations, or
-with the memory held by another allocator): its staging panels live in a fixed
-array of the library's device image.  Checked through the C ABI against the
+library (real-time loops that forbid driver allocations, processes whose
+device memory is held by another allocator, plug-ins given a fixed memory
+budget): its staging panels live in a fixed array of the library's device
+image.  Checked through the C ABI against the
 allocating entry point ff_apply_operators on two calls in a row (the array
 keeps the previous call's contents), in both precisions, and on an oversize
 block, which must be refused.  Collected last so that a failure here cannot
