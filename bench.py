@@ -388,7 +388,8 @@ def splat_line(args, r, peaks):
     pair_products = r["pair_products"]
     per_mac = 24 if args.prec == "fp64" else 2
     ops = 4 * pair_products * per_mac
-    roof = _roofline("alu", "k_assemble (H_w and M values, two-set K x K, row-owner gather)",
+    roof = _roofline("alu", "k_tset_tiles (two-set H_w and M: dense 64 x 64 register tiles of "
+                     "32-point tiles grouped by nearest centre)",
                      ops, "algorithmic_fp32_ops_per_launch", ms_launch, cnt, peaks,
                      extra={"pair_products": pair_products,
                             "fp32_ops_per_multiply_add": per_mac // 2 * 2})

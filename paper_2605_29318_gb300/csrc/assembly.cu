@@ -247,6 +247,8 @@ __global__ void k_split_df(const double* __restrict__ x, float2* __restrict__ y,
 
 }  // namespace
 
+void finish_matrices(ff_ctx* c);
+
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0) {
   cudaStream_t st = c->stream;
   const long long n = c->n, n1 = c->n1, nq = c->nq;
@@ -254,6 +256,7 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   const bool f64 = c->prec == FF_PREC_FP64;
   const size_t tb = f64 ? 8 : 4;
   reset_flags(c);
+  DevFlags f{};
   // material weights per quadrature point (the nodal points are in cell
   // order, the two-set quadrature points in the caller's)
   c->wh.ensure(tb * nq);
@@ -267,11 +270,20 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
                                                     nu0, c->wh.as<float>(),
                                                     c->flags.as<DevFlags>()), ::ff::note_launch());
   FF_LAUNCH_CHECK();
+  if (c->twoset && tset_assembly_fits(n)) {
+    // two-set clouds: dense tiles of points grouped by their nearest centre
+    f = read_flags(c);
+    if (f.code == FF_ERR_INVALID_ARG)
+      throw Error(FF_ERR_INVALID_ARG, "invalid material (need E > 0, 0 <= nu < 0.5) at point " +
+                                          std::to_string(f.index));
+    tset_assemble(c);
+    finish_matrices(c);
+    return;
+  }
   // pass 1: unique columns per row, in a table of 2048 slots per warp (4 warps
   // per block); clouds of uneven density (wide supports reaching into dense
   // regions) retry with 16384 slots per warp (2 warps per block)
   int* cnt = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (n + 1)));
-  DevFlags f{};
   int tsize1 = 2048;
   ProfScope ps_pattern(kProfPattern);
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -335,6 +347,15 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   }
   FF_LAUNCH_CHECK();
   ps_values.close();
+  finish_matrices(c);
+}
+
+// the copies of (H, M) the eigensolver reads besides the stored values, and
+// the preconditioner's tensor-core tiles
+void finish_matrices(ff_ctx* c) {
+  cudaStream_t st = c->stream;
+  const long long n2 = c->n2;
+  const bool f64 = c->prec == FF_PREC_FP64;
   if (f64) {  // FP32 rounding of (H, M) for the FP32 phase of the eigensolver
     float* v32 = reinterpret_cast<float*>(c->a_val32.ensure(2 * sizeof(float) * n2));
     const long long m = 2 * n2;

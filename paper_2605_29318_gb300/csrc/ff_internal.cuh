@@ -145,6 +145,7 @@ struct ff_ctx {
   ff::Buf crad;      // double[K] r_k
   ff::Buf clim;      // double[K] t^2 r_k^2 (+inf untruncated)
   ff::Buf clim32;    // float[K]  its FP32 rounding (filter)
+  ff::Buf qpts;      // float[3 nq] the quadrature points (x, y, z), caller order
   // neighbours (internal order)
   ff::Buf nbr_ptr;   // int64[nq+1]
   ff::Buf nbr_idx;   // int[n1]
@@ -232,6 +233,11 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
 // shape functions at the quadrature points
 void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int K, double trunc,
                   long long start);
+// dense-tile assembly of a two-set cloud's H_w and M (tset_assembly.cu), for
+// K up to kTsetMaxCentres centres
+constexpr long long kTsetMaxCentres = 4096;
+bool tset_assembly_fits(long long K);
+void tset_assemble(ff_ctx* c);
 // covering lists of arbitrary points over the centres (returns the pair count)
 // and the Gaussian shape functions there (returns the pass's flags)
 long long twoset_cover(ff_ctx* c, const float* Q, long long nq, Buf& ptrb, Buf& idxb, Buf& cntb);

@@ -1,0 +1,382 @@
+// Assembly of H_w (Prop. 1) and M (Sec. 3.2, Eq. 14) for the two-set
+// discretisation in dense tiles.
+//
+//   (H_w)_kl = sum_i v_i (lambda_i + 4 mu_i) grad phi_k(X_i) . grad phi_l(X_i)
+//   M_kl     = sum_i v_i phi_k(X_i) phi_l(X_i)
+//
+// With K centres and n quadrature points each covered by c_i centres, the sums
+// hold sum_i c_i^2 pair products (6e9 for a million points at ~80 centres
+// each): a dense contraction once the points are grouped.  The points are
+// grouped by their nearest covering centre (a counting sort over the K
+// centres), and cut into tiles of kTilePts consecutive points of that order.
+// A tile's points are close together, so the union U of their covering centres
+// is small (~1.5 c_i).  One thread block per tile:
+//   1. the union as a bitmap over the centres and its popcount ranks;
+//   2. for every pair (A, B), A <= B, of 64-column blocks of the union: the
+//      tile's weighted gradients and shape functions of block A and the plain
+//      ones of block B staged densely in shared memory (zeros where a point
+//      does not see a centre), then the 64 x 64 block of
+//      sum_t (w_t g_A(t)) g_B(t)^T and sum_t (v_t phi_A(t)) phi_B(t)^T in
+//      register tiles (4 x 4 per thread, rows tr + 16 r, columns tc + 16 c);
+//   3. each non-zero entry of the upper triangle added into dense K x K FP64
+//      accumulators (atomic adds).
+// The sums inside a tile run in the context's working precision (double-float
+// in FP64 contexts, about 2^-47 relative; FP32 otherwise); across tiles they
+// are FP64.  The order of the FP64 additions follows the atomics' arrival, so
+// the matrices are reproducible to FP64 rounding (not bit for bit).
+// A second pass turns the accumulators into the CSR layout of the nodal path
+// (ascending columns; an entry is stored where H_w or M is non-zero), with the
+// diagonal of H_w set to minus the sum of its row's off-diagonal entries.
+#include <algorithm>
+#include <type_traits>
+
+#include "ff_internal.cuh"
+#include "linalg.cuh"
+
+namespace ff {
+namespace {
+
+constexpr int kTilePts = 32;   // quadrature points per tile
+constexpr int kBlk = 64;       // union columns per register block
+constexpr int kThreads = 256;  // 16 x 16 threads, 4 x 4 entries each
+
+// the nearest covering centre of every point (ties: the lower index) and the
+// points per centre
+__global__ void k_home(const float* __restrict__ Xq, long long nq, const long long* __restrict__ ptr,
+                       const int* __restrict__ idx, const float4* __restrict__ cpos,
+                       int* __restrict__ home, int* __restrict__ cnt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const float x = Xq[3 * i], y = Xq[3 * i + 1], z = Xq[3 * i + 2];
+  float best = INFINITY;
+  int h = 0;
+  for (long long e = ptr[i]; e < ptr[i + 1]; ++e) {
+    const int k = idx[e];
+    const float4 p = cpos[k];
+    const float dx = x - p.x, dy = y - p.y, dz = z - p.z;
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 < best) {  // ascending k: the first minimum is the lowest index
+      best = d2;
+      h = k;
+    }
+  }
+  home[i] = h;
+  atomicAdd(&cnt[h], 1);
+}
+
+__global__ void k_home_scatter(const int* __restrict__ home, long long nq,
+                               const long long* __restrict__ start, int* __restrict__ cursor,
+                               int* __restrict__ order) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  const int h = home[i];
+  order[start[h] + atomicAdd(&cursor[h], 1)] = (int)i;
+}
+
+// rank of centre c in the tile's union (bitmap words and their exclusive
+// popcount prefix)
+__device__ __forceinline__ int union_rank(const unsigned* bits, const int* wpre, int c) {
+  const int w = c >> 5;
+  return wpre[w] + __popc(bits[w] & ((1u << (c & 31)) - 1u));
+}
+
+// One block per tile.  Shared memory (dynamic): bitmap (nw words), word
+// prefix (nw + 1), union columns (K), then the staging arrays
+// sA[4][kTilePts][kBlk] and sB[4][kTilePts][kBlk] of T.
+template <class T>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tset_tiles(const int* __restrict__ order, long long nq, const long long* __restrict__ ptr,
+                 const int* __restrict__ idx, const T* __restrict__ phi,
+                 const T* __restrict__ dphi, long long n1, const T* __restrict__ wh,
+                 const float* __restrict__ vol, int K, double* __restrict__ Hd,
+                 double* __restrict__ Md) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int nw = (K + 31) >> 5;
+  unsigned* bits = reinterpret_cast<unsigned*>(sm_raw);
+  int* wpre = reinterpret_cast<int*>(bits + nw);
+  int* ucol = wpre + nw + 1;
+  size_t off = (size_t)(2 * nw + 1 + K) * 4;
+  off = (off + 15) & ~size_t(15);
+  T* sA = reinterpret_cast<T*>(sm_raw + off);
+  T* sB = sA + 4 * kTilePts * kBlk;
+  __shared__ int pts[kTilePts];
+  __shared__ int s_total;
+
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const long long p0 = (long long)blockIdx.x * kTilePts;
+  const int np = (int)min((long long)kTilePts, nq - p0);
+  if (tid < kTilePts) pts[tid] = tid < np ? order[p0 + tid] : -1;
+  for (int w = tid; w < nw; w += kThreads) bits[w] = 0u;
+  __syncthreads();
+  // 1. the union of the tile's covering centres
+  for (int j = wid; j < np; j += kThreads / 32) {
+    const int i = pts[j];
+    for (long long e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+      const int c = idx[e];
+      atomicOr(&bits[c >> 5], 1u << (c & 31));
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {  // exclusive prefix of the words' popcounts
+    int run = 0;
+    for (int w0 = 0; w0 < nw; w0 += 32) {
+      const int w = w0 + lane;
+      const int v = w < nw ? __popc(bits[w]) : 0;
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (w < nw) wpre[w] = run + incl - v;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) {
+      wpre[nw] = run;
+      s_total = run;
+    }
+  }
+  __syncthreads();
+  const int U = s_total;
+  for (int w = tid; w < nw; w += kThreads) {
+    unsigned b = bits[w];
+    int r = wpre[w];
+    while (b) {
+      const int q = __ffs(b) - 1;
+      ucol[r++] = (w << 5) + q;
+      b &= b - 1u;
+    }
+  }
+  __syncthreads();
+
+  const int tr = tid >> 4, tc = tid & 15;
+  const int nblk = (U + kBlk - 1) / kBlk;
+  constexpr int kPlane = kTilePts * kBlk;  // one value plane of a staging array
+  for (int bi = 0; bi < nblk; ++bi)
+    for (int bj = bi; bj < nblk; ++bj) {
+      const int a0 = bi * kBlk, b0 = bj * kBlk;
+      // 2a. stage the blocks (zeros where a point does not see a centre)
+      for (int q = tid; q < 4 * kPlane; q += kThreads) {
+        sA[q] = T(0);
+        sB[q] = T(0);
+      }
+      __syncthreads();
+      for (int j = wid; j < np; j += kThreads / 32) {
+        const int i = pts[j];
+        const T w = wh[i];
+        const T v = T(vol[i]);
+        for (long long e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+          const int r = union_rank(bits, wpre, idx[e]);
+          const bool inA = r >= a0 && r < a0 + kBlk, inB = r >= b0 && r < b0 + kBlk;
+          if (!inA && !inB) continue;
+          const T g0 = dphi[e], g1 = dphi[n1 + e], g2 = dphi[2 * n1 + e], f = phi[e];
+          if (inA) {
+            const int o = j * kBlk + (r - a0);
+            sA[o] = w * g0;
+            sA[kPlane + o] = w * g1;
+            sA[2 * kPlane + o] = w * g2;
+            sA[3 * kPlane + o] = v * f;
+          }
+          if (inB) {
+            const int o = j * kBlk + (r - b0);
+            sB[o] = g0;
+            sB[kPlane + o] = g1;
+            sB[2 * kPlane + o] = g2;
+            sB[3 * kPlane + o] = f;
+          }
+        }
+      }
+      __syncthreads();
+      // 2b. the 64 x 64 block: rows tr + 16 r of A, columns tc + 16 c of B
+      T h[4][4], m[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          h[r][c] = T(0);
+          m[r][c] = T(0);
+        }
+      for (int j = 0; j < np; ++j) {
+#pragma unroll
+        for (int val = 0; val < 4; ++val) {
+          T a[4], b[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) a[r] = sA[val * kPlane + j * kBlk + tr + 16 * r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) b[c] = sB[val * kPlane + j * kBlk + tc + 16 * c];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              if (val < 3)
+                mac(h[r][c], a[r], b[c]);
+              else
+                mac(m[r][c], a[r], b[c]);
+            }
+        }
+      }
+      // 3. the upper triangle of the non-zero entries into the accumulators
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int ur = a0 + tr + 16 * r, uc = b0 + tc + 16 * c;
+          if (ur >= U || uc >= U || ur > uc) continue;
+          const double hv = (double)finish(h[r][c]), mv = (double)finish(m[r][c]);
+          if (hv == 0.0 && mv == 0.0) continue;
+          const long long at = (long long)ucol[ur] * K + ucol[uc];
+          atomicAdd(&Hd[at], hv);
+          atomicAdd(&Md[at], mv);
+        }
+      __syncthreads();  // the staging arrays are refilled next
+    }
+}
+
+__device__ __forceinline__ bool stored(const double* Hd, const double* Md, long long at) {
+  return Hd[at] != 0.0 || Md[at] != 0.0;
+}
+
+// row k of the symmetric matrices from the upper-triangle accumulators
+__device__ __forceinline__ long long at_sym(int k, int l, int K) {
+  return k <= l ? (long long)k * K + l : (long long)l * K + k;
+}
+
+// entries per row (the diagonal always)
+__global__ void k_dense_count(const double* __restrict__ Hd, const double* __restrict__ Md, int K,
+                              int* __restrict__ cnt) {
+  const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (k >= K) return;
+  const int lane = threadIdx.x & 31;
+  int c = 0;
+  for (int l = lane; l < K; l += 32) c += (l == k) || stored(Hd, Md, at_sym(k, l, K));
+  c = __reduce_add_sync(0xffffffffu, c);
+  if (lane == 0) cnt[k] = c;
+}
+
+// CSR rows with ascending columns; diagonal of H_w = -(sum of the row's
+// off-diagonal entries), summed in a fixed order
+template <class TO>
+__global__ void k_dense_fill(const double* __restrict__ Hd, const double* __restrict__ Md, int K,
+                             const long long* __restrict__ aptr, int* __restrict__ acol,
+                             TO* __restrict__ aval, float* __restrict__ hf32,
+                             float* __restrict__ hdiag) {
+  const int k = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (k >= K) return;
+  const int lane = threadIdx.x & 31;
+  double off = 0.0;
+  for (int l = lane; l < K; l += 32)
+    if (l != k) off += (double)(TO)Hd[at_sym(k, l, K)];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+  long long pos = aptr[k];
+  for (int l0 = 0; l0 < K; l0 += 32) {
+    const int l = l0 + lane;
+    const bool has = l < K && (l == k || stored(Hd, Md, at_sym(k, l, K)));
+    const unsigned bal = __ballot_sync(0xffffffffu, has);
+    if (has) {
+      const long long e = pos + __popc(bal & ((1u << lane) - 1u));
+      const long long at = at_sym(k, l, K);
+      const TO hv = l == k ? (TO)(-off) : (TO)Hd[at];
+      acol[e] = l;
+      aval[2 * e] = hv;
+      aval[2 * e + 1] = (TO)Md[at];
+      hf32[e] = (float)hv;
+      if (l == k) hdiag[k] = (float)hv;
+    }
+    pos += __popc(bal);
+  }
+}
+
+template <class T>
+size_t tile_smem(int K) {
+  const int nw = (K + 31) >> 5;
+  size_t off = (size_t)(2 * nw + 1 + K) * 4;
+  off = (off + 15) & ~size_t(15);
+  return off + 2 * 4 * (size_t)kTilePts * kBlk * sizeof(T);
+}
+
+}  // namespace
+
+bool tset_assembly_fits(long long K) { return K >= 1 && K <= kTsetMaxCentres; }
+
+// H_w and M of a two-set cloud (c->wh holds the material weights).  Leaves
+// a_ptr, a_col, a_val, h_f32, hdiag_f32 and c->n2 as the row-owner assembly does.
+void tset_assemble(ff_ctx* c) {
+  cudaStream_t st = c->stream;
+  const long long nq = c->nq, n1 = c->n1;
+  const int K = (int)c->n;
+  const bool f64 = c->prec == FF_PREC_FP64;
+  const int TB = 256;
+  // ---- grouping by the nearest covering centre
+  int* home = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (nq + 1)));
+  int* order = reinterpret_cast<int*>(c->scratch[6].ensure(sizeof(int) * (nq + 1)));
+  int* cnt = reinterpret_cast<int*>(c->scratch[7].ensure(sizeof(int) * 2 * (K + 1)));
+  int* cursor = cnt + (K + 1);
+  long long* start = reinterpret_cast<long long*>(c->scratch[4].ensure(sizeof(long long) * (K + 1)));
+  FF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * 2 * (K + 1), st));
+  {
+    ProfScope ps(kProfPattern);
+    (k_home<<<ceil_div(nq, TB), TB, 0, st>>>(c->qpts.as<float>(), nq, c->nbr_ptr.as<long long>(),
+                                             c->nbr_idx.as<int>(), c->pos.as<float4>(), home, cnt),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    scan_counts(cnt, start, K, c, c->scratch[3]);
+    (k_home_scatter<<<ceil_div(nq, TB), TB, 0, st>>>(home, nq, start, cursor, order),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
+  // ---- dense accumulators
+  const size_t kk = (size_t)K * K;
+  double* Hd = reinterpret_cast<double*>(c->scratch[2].ensure(2 * sizeof(double) * kk));
+  double* Md = Hd + kk;
+  FF_CUDA(cudaMemsetAsync(Hd, 0, 2 * sizeof(double) * kk, st));
+  const unsigned tiles = (unsigned)((nq + kTilePts - 1) / kTilePts);
+  {
+    ProfScope ps(kProfAsmValues);
+    if (f64) {
+      const size_t smem = tile_smem<dfloat>(K);
+      set_max_dyn_smem((const void*)k_tset_tiles<dfloat>, (int)smem);
+      (k_tset_tiles<dfloat><<<tiles, kThreads, smem, st>>>(
+           order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<dfloat>(),
+           c->dphi.as<dfloat>(), n1, c->wh.as<dfloat>(), c->vol.as<float>(), K, Hd, Md),
+       ::ff::note_launch());
+    } else {
+      const size_t smem = tile_smem<float>(K);
+      set_max_dyn_smem((const void*)k_tset_tiles<float>, (int)smem);
+      (k_tset_tiles<float><<<tiles, kThreads, smem, st>>>(
+           order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<float>(),
+           c->dphi.as<float>(), n1, c->wh.as<float>(), c->vol.as<float>(), K, Hd, Md),
+       ::ff::note_launch());
+    }
+    FF_LAUNCH_CHECK();
+  }
+  // ---- CSR
+  int* rc = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (nq + 1)));
+  (k_dense_count<<<ceil_div((long long)K * 32, TB), TB, 0, st>>>(Hd, Md, K, rc),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+  long long* aptr = reinterpret_cast<long long*>(c->a_ptr.ensure(sizeof(long long) * (K + 1)));
+  scan_counts(rc, aptr, K, c, c->scratch[3]);
+  long long n2 = 0;
+  FF_CUDA(cudaMemcpyAsync(&n2, aptr + K, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  FF_CUDA(cudaStreamSynchronize(st));
+  c->n2 = n2;
+  const size_t tb = f64 ? 8 : 4;
+  c->a_col.ensure(sizeof(int) * n2);
+  c->a_val.ensure(2 * tb * n2);
+  c->h_f32.ensure(sizeof(float) * n2);
+  c->hdiag_f32.ensure(sizeof(float) * K);
+  if (f64)
+    (k_dense_fill<double><<<ceil_div((long long)K * 32, TB), TB, 0, st>>>(
+         Hd, Md, K, aptr, c->a_col.as<int>(), c->a_val.as<double>(), c->h_f32.as<float>(),
+         c->hdiag_f32.as<float>()),
+     ::ff::note_launch());
+  else
+    (k_dense_fill<float><<<ceil_div((long long)K * 32, TB), TB, 0, st>>>(
+         Hd, Md, K, aptr, c->a_col.as<int>(), c->a_val.as<float>(), c->h_f32.as<float>(),
+         c->hdiag_f32.as<float>()),
+     ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+}
+
+}  // namespace ff

@@ -49,6 +49,7 @@ namespace {
 constexpr int kFpsCS = 8;                    // blocks per cluster
 constexpr int kFpsT = 1024;                  // threads per block
 constexpr int kFpsSmemMax = 200 * 1024;      // dynamic shared memory per block
+constexpr int kFpsGridMin = 200000;          // points from which the whole GPU samples
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ double d2_f64(float ax, float ay, float az, float bx, float by,
@@ -212,6 +213,148 @@ __global__ void __cluster_dims__(kFpsCS, 1, 1) __launch_bounds__(kFpsT, 1)
     cz = win.z;
   }
   cl.sync();  // no block leaves while another may still read its candidates
+}
+
+// The same sampling on the whole GPU: one block per SM in a cooperative
+// launch, each holding its slice of the points and their running distances in
+// shared memory (global memory when the slice does not fit).  Per centre:
+// update, block arg-max, the block's candidate published to global memory
+// (two buffers by parity), a grid barrier, and every block reduces all the
+// published candidates itself -- the same winner everywhere, so every block
+// leaves the loop at the same step.  The barrier is a monotone arrival counter
+// in global memory; its wait is bounded (about a second of clock cycles) and
+// a block that gives up records FF_ERR_TIMEOUT in the flags and in `abort`, and
+// every block leaves the loop at the next barrier it sees it at.
+constexpr long long kGridWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* abort,
+                                             DevFlags* flags) {
+  __shared__ int s_abort;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const long long t0 = clock64();
+    int ab = 0;
+    while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+      if (*reinterpret_cast<volatile int*>(abort)) {
+        ab = 1;
+        break;
+      }
+      if (clock64() - t0 > kGridWaitCycles) {
+        atomicExch(abort, 1);
+        if (atomicCAS(&flags->code, 0, (int)FF_ERR_TIMEOUT) == 0) flags->index = -1;
+        ab = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_abort = ab || *reinterpret_cast<volatile int*>(abort);
+  }
+  __syncthreads();
+  return s_abort == 0;
+}
+
+__global__ void __launch_bounds__(kFpsT, 1)
+    k_fps_grid(const float* __restrict__ X, int n, int K, int start, int S, int in_smem,
+               float* __restrict__ gxyz, double* __restrict__ gcur, float* __restrict__ gcur32,
+               long long* __restrict__ chosen, FpsCand* __restrict__ cand, unsigned* bar,
+               int* abort, DevFlags* __restrict__ flags) {
+  const int G = gridDim.x, rank = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int p0 = min(rank * S, n);
+  const int cnt = min(n - p0, S);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ FpsCand red[kFpsT / 32];
+  __shared__ FpsCand s_win;
+  double* cur;
+  float *cur32, *xs, *ys, *zs;
+  if (in_smem) {
+    cur = reinterpret_cast<double*>(sm_raw);
+    cur32 = reinterpret_cast<float*>(cur + S);
+    xs = cur32 + S;
+    ys = xs + S;
+    zs = ys + S;
+  } else {
+    cur = gcur + p0;
+    cur32 = gcur32 + p0;
+    xs = gxyz + p0;
+    ys = gxyz + (size_t)n + p0;
+    zs = gxyz + 2 * (size_t)n + p0;
+  }
+  const float sx = X[3LL * start], sy = X[3LL * start + 1], sz = X[3LL * start + 2];
+  for (int p = tid; p < cnt; p += kFpsT) {
+    const long long g = (long long)p0 + p;
+    const float x = X[3 * g], y = X[3 * g + 1], z = X[3 * g + 2];
+    xs[p] = x;
+    ys[p] = y;
+    zs[p] = z;
+    const double d = d2_f64(x, y, z, sx, sy, sz);
+    cur[p] = d;
+    cur32[p] = (float)d;
+  }
+  if (rank == 0 && tid == 0) chosen[0] = start;
+  __syncthreads();
+  float cx = sx, cy = sy, cz = sz;
+  for (int j = 1; j < K; ++j) {
+    FpsCand best{0ull, INT_MAX, 0.f, 0.f, 0.f, 0};
+    for (int p = tid; p < cnt; p += kFpsT) {
+      const float x = xs[p], y = ys[p], z = zs[p];
+      double c = cur[p];
+      if (j > 1) {  // fold in the centre chosen last (the start is in already)
+        const float c32 = cur32[p];
+        if (c32 < 1e-30f || d2_f32(x, y, z, cx, cy, cz) <= __fmul_rn(c32, 1.00001f)) {
+          const double d = d2_f64(x, y, z, cx, cy, cz);
+          if (d < c) {
+            c = d;
+            cur[p] = d;
+            cur32[p] = (float)d;
+          }
+        }
+      }
+      fps_pick(best, (unsigned long long)__double_as_longlong(c), p0 + p, x, y, z);
+    }
+    fps_warp_max(best);
+    if (lane == 0) red[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+      FpsCand b = red[lane];
+      fps_warp_max(b);
+      if (lane == 0) cand[(size_t)(j & 1) * G + rank] = b;
+    }
+    if (!grid_barrier(bar, (unsigned)j * (unsigned)G, abort, flags)) break;
+    // every block reduces all the published candidates (L1 bypassed)
+    FpsCand w{0ull, INT_MAX, 0.f, 0.f, 0.f, 0};
+    const FpsCand* cj = cand + (size_t)(j & 1) * G;
+    for (int q = tid; q < G; q += kFpsT) {
+      const unsigned long long key = __ldcg(reinterpret_cast<const unsigned long long*>(&cj[q].key));
+      const int idx = __ldcg(&cj[q].idx);
+      const float x = __ldcg(&cj[q].x), y = __ldcg(&cj[q].y), z = __ldcg(&cj[q].z);
+      fps_pick(w, key, idx, x, y, z);
+    }
+    fps_warp_max(w);
+    if (lane == 0) red[wid] = w;
+    __syncthreads();
+    if (wid == 0) {
+      FpsCand b = red[lane];
+      fps_warp_max(b);
+      if (lane == 0) s_win = b;
+    }
+    __syncthreads();
+    const FpsCand win = s_win;
+    if (win.key == 0ull || win.idx == INT_MAX) {
+      // every remaining point coincides with a chosen centre
+      if (rank == 0 && tid == 0 && atomicCAS(&flags->code, 0, (int)FF_ERR_INVALID_ARG) == 0)
+        flags->index = j;
+      break;
+    }
+    if (rank == 0 && tid == 0) chosen[j] = win.idx;
+    cx = win.x;
+    cy = win.y;
+    cz = win.z;
+    __syncthreads();  // s_win and red are rewritten in the next step
+  }
 }
 
 __global__ void k_gather_centres(const float* __restrict__ X, const long long* __restrict__ chosen,
@@ -459,6 +602,41 @@ DevFlags twoset_shape(ff_ctx* c, const float* Q, long long nq, const long long* 
   return read_flags(c);
 }
 
+// The transposed covering lists of a two-set cloud: for every centre the
+// points it covers (ascending) and its position in each point's row; checked
+// against the row lists built before.
+void twoset_columns(ff_ctx* c, const float* Xq) {
+  cudaStream_t st = c->stream;
+  const int T = 256;
+  const int K = (int)c->n;
+  const long long nq = c->nq, n1 = c->n1;
+  const float4* cpos = c->pos.as<float4>();
+  const float* lim32 = c->clim32.as<float>();
+  const double* lim = c->clim.as<double>();
+  int* ccnt = reinterpret_cast<int*>(c->scratch[6].ensure(sizeof(int) * (K + 1)));
+  (k_cover_cols<0><<<ceil_div((long long)K * 32, T), T, 0, st>>>(
+       Xq, nq, cpos, lim32, lim, K, ccnt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+  long long* tptr = reinterpret_cast<long long*>(c->nbrT_ptr.ensure(sizeof(long long) * (K + 1)));
+  scan_counts(ccnt, tptr, K, c, c->scratch[3]);
+  long long n1t = 0;
+  FF_CUDA(cudaMemcpyAsync(&n1t, tptr + K, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  FF_CUDA(cudaStreamSynchronize(st));
+  FF_REQUIRE(n1t == n1, FF_ERR_CUDA, "covering lists disagree between the two passes");
+  int* tidx = reinterpret_cast<int*>(c->nbrT_idx.ensure(sizeof(int) * std::max(n1, 1LL)));
+  long long* tpos =
+      reinterpret_cast<long long*>(c->nbrT_pos.ensure(sizeof(long long) * std::max(n1, 1LL)));
+  reset_flags(c);
+  (k_cover_cols<1><<<ceil_div((long long)K * 32, T), T, 0, st>>>(
+       Xq, nq, cpos, lim32, lim, K, nullptr, tptr, tidx, tpos, c->nbr_ptr.as<long long>(),
+       c->nbr_idx.as<int>(), c->flags.as<DevFlags>()),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+  const DevFlags f = read_flags(c);
+  FF_REQUIRE(f.code == 0, FF_ERR_CUDA, "covering lists disagree between the two passes");
+}
+
 void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int K, double trunc,
                   long long start) {
   cudaStream_t st = c->stream;
@@ -482,32 +660,75 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   c->twoset = true;
   c->trunc = trunc;
 
-  // ---- 2. farthest-point sampling
+  // ---- 2. farthest-point sampling: on the whole GPU (cooperative launch, one
+  // block per SM) when the points are many, else on one thread-block cluster
   const int n = (int)nq;
-  const int S = (n + kFpsCS - 1) / kFpsCS;
-  const size_t smem = 24 * (size_t)S;
-  const bool in_smem = smem <= (size_t)kFpsSmemMax;
-  float* gxyz = nullptr;
-  double* gcur = nullptr;
-  float* gcur32 = nullptr;
-  if (in_smem) {
-    set_max_dyn_smem((const void*)k_fps, (int)std::max<size_t>(smem, 16));
-  } else {
-    gxyz = reinterpret_cast<float*>(c->scratch[1].ensure(sizeof(float) * 3 * (size_t)n));
-    gcur = reinterpret_cast<double*>(c->scratch[2].ensure(sizeof(double) * (size_t)n));
-    gcur32 = reinterpret_cast<float*>(c->scratch[4].ensure(sizeof(float) * (size_t)n));
-  }
   long long* chosen = reinterpret_cast<long long*>(c->centre_idx.ensure(sizeof(long long) * K));
   reset_flags(c);
+  bool done = false;
   {
     ProfScope ps(kProfFps);
-    (k_fps<<<kFpsCS, kFpsT, in_smem ? smem : 0, st>>>(Xq, n, K, (int)start, S, in_smem ? 1 : 0,
-                                                      gxyz, gcur, gcur32, chosen,
-                                                      c->flags.as<DevFlags>()),
-     ::ff::note_launch());
-    FF_LAUNCH_CHECK();
+    int coop = 0;
+    FF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+    const int G = sm_count();
+    if (coop && n >= kFpsGridMin) {
+      const int S = (n + G - 1) / G;
+      const size_t smem = 24 * (size_t)S;
+      const bool in_smem = smem <= (size_t)kFpsSmemMax;
+      if (in_smem) set_max_dyn_smem((const void*)k_fps_grid, (int)std::max<size_t>(smem, 16));
+      int per_sm = 0;
+      FF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fps_grid, kFpsT,
+                                                            in_smem ? smem : 0));
+      if (per_sm >= 1) {
+        float* gxyz = nullptr;
+        double* gcur = nullptr;
+        float* gcur32 = nullptr;
+        if (!in_smem) {
+          gxyz = reinterpret_cast<float*>(c->scratch[1].ensure(sizeof(float) * 3 * (size_t)n));
+          gcur = reinterpret_cast<double*>(c->scratch[2].ensure(sizeof(double) * (size_t)n));
+          gcur32 = reinterpret_cast<float*>(c->scratch[4].ensure(sizeof(float) * (size_t)n));
+        }
+        // candidates (two buffers of G), then the barrier counter and the abort word
+        unsigned char* sync = reinterpret_cast<unsigned char*>(
+            c->scratch[7].ensure(2 * sizeof(FpsCand) * G + 64));
+        FpsCand* cand = reinterpret_cast<FpsCand*>(sync);
+        unsigned* bar = reinterpret_cast<unsigned*>(sync + 2 * sizeof(FpsCand) * G);
+        int* abort = reinterpret_cast<int*>(bar + 4);
+        FF_CUDA(cudaMemsetAsync(bar, 0, 32, st));
+        int nn = n, KK = K, st0 = (int)start, SS = S, ism = in_smem ? 1 : 0;
+        DevFlags* fl = c->flags.as<DevFlags>();
+        void* args[] = {(void*)&Xq, &nn, &KK, &st0, &SS, &ism, &gxyz, &gcur, &gcur32,
+                        &chosen, &cand, &bar, &abort, &fl};
+        FF_CUDA(cudaLaunchCooperativeKernel((const void*)k_fps_grid, dim3(G), dim3(kFpsT), args,
+                                            in_smem ? smem : 0, st));
+        ::ff::note_launch();
+        done = true;
+      }
+    }
+    if (!done) {
+      const int S = (n + kFpsCS - 1) / kFpsCS;
+      const size_t smem = 24 * (size_t)S;
+      const bool in_smem = smem <= (size_t)kFpsSmemMax;
+      float* gxyz = nullptr;
+      double* gcur = nullptr;
+      float* gcur32 = nullptr;
+      if (in_smem) {
+        set_max_dyn_smem((const void*)k_fps, (int)std::max<size_t>(smem, 16));
+      } else {
+        gxyz = reinterpret_cast<float*>(c->scratch[1].ensure(sizeof(float) * 3 * (size_t)n));
+        gcur = reinterpret_cast<double*>(c->scratch[2].ensure(sizeof(double) * (size_t)n));
+        gcur32 = reinterpret_cast<float*>(c->scratch[4].ensure(sizeof(float) * (size_t)n));
+      }
+      (k_fps<<<kFpsCS, kFpsT, in_smem ? smem : 0, st>>>(Xq, n, K, (int)start, S,
+                                                        in_smem ? 1 : 0, gxyz, gcur, gcur32,
+                                                        chosen, c->flags.as<DevFlags>()),
+       ::ff::note_launch());
+      FF_LAUNCH_CHECK();
+    }
   }
   DevFlags f = read_flags(c);
+  FF_REQUIRE(f.code != FF_ERR_TIMEOUT, FF_ERR_TIMEOUT,
+             "farthest-point sampling: a grid barrier wait ran out");
   FF_REQUIRE(f.code == 0, FF_ERR_INVALID_ARG,
              "the quadrature points hold fewer than K = " + std::to_string(K) +
                  " distinct positions (farthest-point step " + std::to_string(f.index) + ")");
@@ -536,33 +757,17 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   ProfScope ps_cover(kProfCover);
   const long long n1 = twoset_cover(c, Xq, nq, c->nbr_ptr, c->nbr_idx, c->scratch[5]);
   c->n1 = n1;
-  int* ccnt = reinterpret_cast<int*>(c->scratch[6].ensure(sizeof(int) * (K + 1)));
-  (k_cover_cols<0><<<ceil_div((long long)K * 32, T), T, 0, st>>>(
-       Xq, nq, cpos, lim32, lim, K, ccnt, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr),
-   ::ff::note_launch());
-  FF_LAUNCH_CHECK();
-  long long* tptr = reinterpret_cast<long long*>(c->nbrT_ptr.ensure(sizeof(long long) * (K + 1)));
-  scan_counts(ccnt, tptr, K, c, c->scratch[3]);
-  long long n1t = 0;
-  FF_CUDA(cudaMemcpyAsync(&n1t, tptr + K, sizeof(long long), cudaMemcpyDeviceToHost, st));
-  FF_CUDA(cudaStreamSynchronize(st));
-  FF_REQUIRE(n1t == n1, FF_ERR_CUDA, "covering lists disagree between the two passes");
-  int* tidx = reinterpret_cast<int*>(c->nbrT_idx.ensure(sizeof(int) * std::max(n1, 1LL)));
-  long long* tpos =
-      reinterpret_cast<long long*>(c->nbrT_pos.ensure(sizeof(long long) * std::max(n1, 1LL)));
-  reset_flags(c);
-  (k_cover_cols<1><<<ceil_div((long long)K * 32, T), T, 0, st>>>(
-       Xq, nq, cpos, lim32, lim, K, nullptr, tptr, tidx, tpos, c->nbr_ptr.as<long long>(),
-       c->nbr_idx.as<int>(), c->flags.as<DevFlags>()),
-   ::ff::note_launch());
-  FF_LAUNCH_CHECK();
-  f = read_flags(c);
-  FF_REQUIRE(f.code == 0, FF_ERR_CUDA, "covering lists disagree between the two passes");
+  // the transposed lists (centre -> the points it covers) serve the
+  // row-owner assembly only, which runs when K is too large for the dense
+  // tiles of the two-set assembly
+  if (!tset_assembly_fits(K)) twoset_columns(c, Xq);
   ps_cover.close();
 
   // ---- 5. quadrature volumes, identity order of the centres
   float* vol = reinterpret_cast<float*>(c->vol.ensure(sizeof(float) * nq));
   (k_copy_f32<<<ceil_div(nq, T), T, 0, st>>>(vq, vol, nq), ::ff::note_launch());
+  float* qpts = reinterpret_cast<float*>(c->qpts.ensure(sizeof(float) * 3 * nq));
+  (k_copy_f32<<<ceil_div(3 * nq, T), T, 0, st>>>(Xq, qpts, 3 * nq), ::ff::note_launch());
   int* perm = reinterpret_cast<int*>(c->perm.ensure(sizeof(int) * K));
   int* iperm = reinterpret_cast<int*>(c->iperm.ensure(sizeof(int) * K));
   (k_iota<<<ceil_div(K, T), T, 0, st>>>(perm, iperm, K), ::ff::note_launch());

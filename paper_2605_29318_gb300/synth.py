@@ -75,6 +75,23 @@ def torus(n=50000, R=0.5, r=0.2, seed=2, support=2.0, E=1e6, nu=0.4, k=32):
     return _finish(X, 2.0 * math.pi ** 2 * R * r * r, support, E, nu, k, f"torus{n}")
 
 
+def layered_sphere(n=3000, radius=0.5, seed=6, support=2.0, E_stiff=1e7, E_soft=1e5,
+                   nu=0.45, k=10):
+    """The heterogeneous sphere of the paper's multi-layer demonstration: four
+    concentric shells of equal thickness, stiff-soft-stiff-soft from the
+    centre out (the paper states the order, not the radii or moduli: the
+    shells split the radius in four, and stiff / soft are 1e7 / 1e5 Pa).
+    Rejection-sampled in the ball; E per particle from its shell."""
+    def inside(P):
+        return (P * P).sum(1) < radius * radius
+    X = _rejection(n, [-radius] * 3, [radius] * 3, inside, _rng(seed))
+    c = _finish(X, 4.0 / 3.0 * math.pi * radius ** 3, support, 1.0, nu, k, f"layers{n}")
+    shell = np.minimum((np.sqrt((X * X).sum(1)) / radius * 4).astype(np.int64), 3)
+    c.E = np.where(shell % 2 == 0, E_stiff, E_soft).astype(np.float32)
+    c.nu = np.float32(nu)
+    return c
+
+
 def inside_grid(lo, hi, h, inside):
     """Quadrature points of the paper's two-set construction: the centres of a
     uniform grid of spacing h over the box [lo, hi], those outside the solid

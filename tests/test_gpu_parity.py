@@ -67,6 +67,7 @@ def _hetero_cloud():
 
 
 CLOUDS["hetero1500"] = _hetero_cloud
+CLOUDS["layers3k"] = lambda: synth.layered_sphere(3000, seed=6)
 
 
 @pytest.mark.parametrize("name", list(CLOUDS))
@@ -88,7 +89,7 @@ def test_neighbours_bit_exact_and_shape_functions(name, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["cube2k", "torus4k", "hetero1500"])
+@pytest.mark.parametrize("name", ["cube2k", "torus4k", "hetero1500", "layers3k"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_matrices(name, prec):
     c = CLOUDS[name]()
@@ -184,6 +185,25 @@ def test_eigenmodes_torus10k_k32_bench_configuration():
     ang = eigen.max_principal_angle(M, Cg[:, 1:kk], C_o[:, 1:kk])
     assert ang < 1e-3, (kk, ang)
     assert eigen.residuals(H, M, ev, Cg)[1:].max() <= 1e-6
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_eigenmodes_of_the_layered_sphere(prec):
+    """The paper's multi-layer material case (four shells, stiff-soft-stiff-soft,
+    E 1e7 / 1e5 Pa): per-particle Lame parameters in Prop. 1 with a 100:1 jump
+    between shells.  Eigenvalues, subspace and residuals against the dense
+    FP64 oracle (FP64 context to 1e-6 through the FP32 phase; FP32 context to
+    its 1e-4 floor)."""
+    from paper_2605_29318_gb300 import binding
+    c = CLOUDS["layers3k"]()
+    _, _, _, _, H, M = _oracle(c)
+    ctx = _run_build(c, prec)
+    ctx.assemble_hessian(*_material(c))
+    o = binding.default_opts(tol=1e-7 if prec == "fp64" else 5e-5, max_iter=300)
+    ev, modes, rep, st = ctx.eigenmodes(10, o, check=False)
+    assert st == 0, rep
+    _check_modes(c, H, M, ev, modes, 10, prec, 1e-6 if prec == "fp64" else 1e-4)
     ctx.close()
 
 

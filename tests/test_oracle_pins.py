@@ -353,6 +353,26 @@ def test_principal_angle_and_residual_helpers():
     assert eigen.residuals(Hs, M, lam * (1 + 1e-3), C).min() > 5e-4
 
 
+def test_layered_sphere_generator_and_its_linear_field_energy():
+    """The four-shell sphere: E follows the shell (stiff, soft, stiff, soft from
+    the centre out), and with that per-particle material a linear nodal field
+    c_k = a . p_k still has the exact energy c^T H_w c = |a|^2 sum_i v_i
+    (lambda_i + 4 mu_i) (gradient reproduction, Eq. 8, in Prop. 1)."""
+    c = synth.layered_sphere(800, seed=3)
+    r = np.sqrt((c.X.astype(np.float64) ** 2).sum(1)) / 0.5
+    shell = np.minimum((r * 4).astype(int), 3)
+    assert np.all(c.E[shell % 2 == 0] == np.float32(1e7))
+    assert np.all(c.E[shell % 2 == 1] == np.float32(1e5))
+    assert all(np.any(shell == s) for s in range(4))
+    ptr, idx, phi, dphi, _ = _build(c)
+    H, M = assembly.assemble(c.n, ptr, idx, phi, dphi, c.v, c.E, c.nu)
+    a = np.array([0.3, -1.1, 0.7])
+    cf = c.X.astype(np.float64) @ a
+    lam, mu = assembly.lame(np.asarray(c.E, np.float64), float(c.nu))
+    expect = float(a @ a) * float(np.sum(c.v.astype(np.float64) * (lam + 4 * mu)))
+    assert abs(cf @ (H @ cf) - expect) <= 1e-10 * expect
+
+
 def test_rayleigh_ritz_and_absolute_residuals():
     """Rayleigh-Ritz on a span holding exact eigenvectors returns their
     eigenvalues and vectors; on any span its Ritz values interlace from above
