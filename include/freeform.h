@@ -177,7 +177,7 @@ typedef struct {
   int cheb_degree_fp64; /* Chebyshev degree of the second phase that follows an FP32 phase;
                            0 = cheb_degree (64) */
   int precond_tc;       /* 1: the preconditioner's H products on tensor cores, with H in
-                           BF16 dense tiles of 16-row blocks (block widths 8..64 in steps
+                           BF16 dense tiles of 16-row blocks (block widths 8..120 in steps
                            of 8); 0: sparse FP32 H on CUDA cores (1) */
   int precond_compact;  /* 1: the preconditioner runs on the columns still above tol only,
                            packed to a multiple of 8 (the others are zero either way: the

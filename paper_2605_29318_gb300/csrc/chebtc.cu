@@ -353,7 +353,8 @@ bool cheb_tc_build(ff_ctx* c) {
 
 bool cheb_step_tc(cudaStream_t st, const ff_ctx* c, int m, const void* din, void* dout, float* x,
                   float* res, float c1, float c2) {
-  if (c->tc_ksteps <= 0 || m % 8 != 0 || m < 8 || m > 64 || c->n * m >= (1LL << 31)) return false;
+  // widths 8..120 in steps of 8 (the staging buffers stay in static shared memory)
+  if (c->tc_ksteps <= 0 || m % 8 != 0 || m < 8 || m > 120 || c->n * m >= (1LL << 31)) return false;
   ProfScope ps(kProfPrecond);
   const int nblk = (int)((c->n + kTcRows - 1) / kTcRows);
   const auto* bi = static_cast<const __nv_bfloat16*>(din);
@@ -372,7 +373,14 @@ bool cheb_step_tc(cudaStream_t st, const ff_ctx* c, int m, const void* din, void
     case 5: FF_TC(5); break;
     case 6: FF_TC(6); break;
     case 7: FF_TC(7); break;
-    default: FF_TC(8); break;
+    case 8: FF_TC(8); break;
+    case 9: FF_TC(9); break;
+    case 10: FF_TC(10); break;
+    case 11: FF_TC(11); break;
+    case 12: FF_TC(12); break;
+    case 13: FF_TC(13); break;
+    case 14: FF_TC(14); break;
+    default: FF_TC(15); break;
   }
 #undef FF_TC
   FF_LAUNCH_CHECK();

@@ -24,7 +24,7 @@ void cheb_step_b16(cudaStream_t st, const long long* ptr, const int* col, const 
 // Tensor-core form of the BF16 step (chebtc.cu): cheb_tc_build lays out the
 // block-dense tiles after assembly (false: spans too wide, the CUDA-core step
 // stays in use); cheb_step_tc runs one step (false: not built or m outside
-// 8..64 in steps of 8 -- nothing launched).
+// 8..120 in steps of 8 -- nothing launched).
 bool cheb_tc_build(ff_ctx* c);
 bool cheb_step_tc(cudaStream_t st, const ff_ctx* c, int m, const void* din, void* dout, float* x,
                   float* res, float c1, float c2);

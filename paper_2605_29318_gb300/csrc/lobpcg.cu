@@ -331,6 +331,27 @@ __global__ void k_lock_momentum(T* __restrict__ YZ, int ns, int nb,
   if (!active[j]) YZ[(size_t)r * 2 * nb + nb + j] = T(0);
 }
 
+// Soft locking of the basis: the Gram matrices restricted to the kept
+// columns (out[i][j] = in[keep[i]][keep[j]], ns x ns -> m x m) ...
+__global__ void k_gather_sq(const double* __restrict__ in, int ns, const int* __restrict__ keep,
+                            int m, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * m) return;
+  const int i = t / m, j = t % m;
+  out[t] = in[(size_t)keep[i] * ns + keep[j]];
+}
+
+// ... and the Rayleigh-Ritz coefficients (m x q rows) placed back on the full
+// basis (ns x q rows; the rows of the columns left out are zeroed first)
+template <class T>
+__global__ void k_place_rows(const T* __restrict__ in, int m, int q, const int* __restrict__ keep,
+                             T* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * q) return;
+  const int i = t / q, j = t % q;
+  out[(size_t)keep[i] * q + j] = in[t];
+}
+
 __global__ void k_round_block(const double* __restrict__ x, float* __restrict__ y, long long m) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) y[t] = (float)x[t];
@@ -369,6 +390,9 @@ struct Solver {
   double *Ag, *Bg, *G1, *theta_d, *norms_d;
   T *Gt, *YZ;
   int *dropped_d, *active_d;
+  double *Ac, *Bc;  // Gram matrices restricted to the kept columns (soft locking)
+  T* YZc;           // their Rayleigh-Ritz coefficients
+  int* keep_d;      // kept columns
   double* h_pin;  // pinned: theta | ||R||^2 | ||MX||^2 (3 nb)
   int spmm_calls = 0, spmv_calls = 0;
 
@@ -402,6 +426,12 @@ struct Solver {
     // active flags, then the packing maps of the preconditioner: cmap (mc), cinv (nb)
     active_d = reinterpret_cast<int*>(c->ws[20].ensure(sizeof(int) * (2 * nb + mc + 8)));
     h_pin = reinterpret_cast<double*>(c->hflags) + 16;  // pinned scratch after the flags
+    Ac = reinterpret_cast<double*>(c->ws[26].ensure(sizeof(double) * 2 * ns * ns));
+    Bc = Ac + (size_t)ns * ns;
+    unsigned char* yk = reinterpret_cast<unsigned char*>(
+        c->ws[27].ensure(sizeof(T) * ns * 2 * nb + sizeof(int) * (ns + 4) + 64));
+    YZc = reinterpret_cast<T*>(yk);
+    keep_d = reinterpret_cast<int*>(yk + ((sizeof(T) * ns * 2 * nb + 63) / 64) * 64);
   }
 
   void spmm(const T* X, T* YH, T* YM, int m) {
@@ -573,7 +603,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
   block_rr(warm != 0);
 
   // ---- iterations
-  std::vector<int> active(nb, 1), pack;
+  std::vector<int> active(nb, 1), pack, keep, pact(nb, 1);
   std::vector<double> res(nb, 1.0), theta(nb, 0.0);
   bool has_p = false;
   int it = 0;
@@ -655,6 +685,7 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
                                 cudaMemcpyDeviceToDevice, st));
       block_rr(false);
       has_p = false;
+      std::fill(pact.begin(), pact.end(), 1);
       mark = best_worst;
       mark_it = it;
       continue;
@@ -755,8 +786,44 @@ ff_status solve(ff_ctx* c, int k, const ff_eig_opts& o, Phase& ph, const T* X0,
     const int ns = has_p ? 3 * nb : 2 * nb;
     gram_rr<T>(st, s.S[cur], s.HS[cur], s.MS[cur], ld, nb, has_p ? 3 : 2, n, s.Ag, s.Bg,
                c->scratch[0]);
-    RRDims dd{ns, nb, nb, 1, nb, nb};
-    rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
+    // Soft locking: the Rayleigh-Ritz step keeps X, the W columns of the modes
+    // still above tol and the P columns that carry momentum (those of the
+    // modes active in the previous iteration); the others are zero and would
+    // only be dropped inside it.  Its cost falls from (3 nb)^3 towards
+    // (nb + 2 n_active)^3 as the modes converge.
+    keep.clear();
+    int na = 0;
+    for (int j = 0; j < nb; ++j) keep.push_back(j);
+    for (int j = 0; j < nb; ++j)
+      if (active[j]) {
+        keep.push_back(nb + j);
+        ++na;
+      }
+    if (has_p)
+      for (int j = 0; j < nb; ++j)
+        if (pact[j]) keep.push_back(2 * nb + j);
+    const int nsc = (int)keep.size();
+    if (nsc < ns && na > 0) {
+      FF_CUDA(cudaMemcpyAsync(s.keep_d, keep.data(), sizeof(int) * nsc, cudaMemcpyHostToDevice,
+                              st));
+      (k_gather_sq<<<blocks((long long)nsc * nsc), TB, 0, st>>>(s.Ag, ns, s.keep_d, nsc, s.Ac),
+       ::ff::note_launch());
+      (k_gather_sq<<<blocks((long long)nsc * nsc), TB, 0, st>>>(s.Bg, ns, s.keep_d, nsc, s.Bc),
+       ::ff::note_launch());
+      FF_LAUNCH_CHECK();
+      RRDims dc{nsc, nb, nb, 1, nb, na};
+      rayleigh_ritz<T>(st, s.Ac, s.Bc, dc, s.YZc, s.theta_d, s.dropped_d, c->scratch[1],
+                       s.rr64);
+      FF_CUDA(cudaMemsetAsync(s.YZ, 0, sizeof(T) * (size_t)ns * 2 * nb, st));
+      (k_place_rows<T><<<blocks((long long)nsc * 2 * nb), TB, 0, st>>>(s.YZc, nsc, 2 * nb,
+                                                                      s.keep_d, s.YZ),
+       ::ff::note_launch());
+      FF_LAUNCH_CHECK();
+    } else {
+      RRDims dd{ns, nb, nb, 1, nb, nb};
+      rayleigh_ritz<T>(st, s.Ag, s.Bg, dd, s.YZ, s.theta_d, s.dropped_d, c->scratch[1], s.rr64);
+    }
+    pact = active;
     (k_lock_momentum<T><<<blocks((long long)ns * nb), TB, 0, st>>>(s.YZ, ns, nb, s.active_d),
      ::ff::note_launch());
     const int nxt = 1 - cur;

@@ -40,7 +40,7 @@ struct BSpline {
 
 __device__ __forceinline__ float gauss_exp(float x) { return expf(x); }
 __device__ __forceinline__ double gauss_exp(double x) { return exp(x); }
-__device__ __forceinline__ dfloat gauss_exp(dfloat x) { return dfloat(exp((double)x)); }
+__device__ __forceinline__ dfloat gauss_exp(dfloat x) { return df_exp(x); }
 
 template <class C>
 __device__ __forceinline__ C from_f64(double x) { return (C)x; }
@@ -49,7 +49,8 @@ __device__ __forceinline__ dfloat from_f64<dfloat>(double x) { return dfloat(x);
 
 // Gauss: exp(-|X - p_k|^2 / r_k^2) (Sec. 3.2) with the FP64 radii r_k of the
 // two-set construction; grad_X = (2 w / r_k^2)(p_k - X).  In double-float the
-// exponential is CUDA's FP64 exp of the argument, split into a pair.
+// exponential is df_exp (reduction by ln 2 and a Taylor polynomial on the FP32
+// pipes).
 struct Gauss {
   const double* rad;
   template <class C>
@@ -126,24 +127,35 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
     m[q] = C(0);
     dm[0][q] = dm[1][q] = dm[2][q] = C(0);
   }
-  for (long long t = s + lane; t < e; t += 32) {
+  // the raw kernel of a lane's first kCache entries is kept for the second
+  // pass (the Gaussian's exponential is the costliest step of a pair)
+  constexpr int kCache = 4;
+  C cw[kCache], cg[kCache];
+  int q = 0;
+  for (long long t = s + lane; t < e; t += 32, ++q) {
     const int k = idx[t];
     float4 p = pos[k];
     C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi;
     C w, gs;  // grad_X varphi = gs * r
     kern.template eval<C>(k, p, r0 * r0 + r1 * r1 + r2 * r2, w, gs);
+#pragma unroll
+    for (int u = 0; u < kCache; ++u)
+      if (q == u) {
+        cw[u] = w;
+        cg[u] = gs;
+      }
     C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
     C g[3] = {gs * r0, gs * r1, gs * r2};
-    int q = 0;
+    int o = 0;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = a; b < 4; ++b, ++q) {
+      for (int b = a; b < 4; ++b, ++o) {
         C pp = P[a] * P[b];
-        m[q] += w * pp;
-        dm[0][q] += g[0] * pp;
-        dm[1][q] += g[1] * pp;
-        dm[2][q] += g[2] * pp;
+        m[o] += w * pp;
+        dm[0][o] += g[0] * pp;
+        dm[1][o] += g[1] * pp;
+        dm[2][o] += g[2] * pp;
       }
   }
 #pragma unroll
@@ -188,12 +200,22 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
     rhs[1 + d] += C(1) / si;
     chol4_solve<C>(L, rhs, dC[d]);
   }
-  for (long long t = s + lane; t < e; t += 32) {
+  q = 0;
+  for (long long t = s + lane; t < e; t += 32, ++q) {
     const int k = idx[t];
     float4 p = pos[k];
     C r0 = (C)p.x - xi, r1 = (C)p.y - yi, r2 = (C)p.z - zi;
     C w, gs;
-    kern.template eval<C>(k, p, r0 * r0 + r1 * r1 + r2 * r2, w, gs);
+    if (q < kCache) {
+#pragma unroll
+      for (int u = 0; u < kCache; ++u)
+        if (q == u) {
+          w = cw[u];
+          gs = cg[u];
+        }
+    } else {
+      kern.template eval<C>(k, p, r0 * r0 + r1 * r1 + r2 * r2, w, gs);
+    }
     C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
     C PC = P[0] * Cv[0] + P[1] * Cv[1] + P[2] * Cv[2] + P[3] * Cv[3];
     phi[t] = (T)(w * PC);

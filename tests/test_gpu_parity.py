@@ -222,16 +222,18 @@ def test_preconditioner_tensor_core_tiles_and_sparse_step():
     rb, ks = ctx.precond_layout()
     assert rb == (n + 15) // 16 and ks > 0
     assert 256 * ks >= n2 and 16 * ks <= n2 + 15 * rb
-    out = {}
-    for tc in (1, 0):
+    for k in (12, 80):
         # k = 12: a 20-column block, the preconditioner's arrays padded to 24
-        # columns (three column tiles of the MMA, an odd count)
-        o = binding.default_opts(tol=1e-7, precond_tc=tc)
-        ev, modes, rep, st = ctx.eigenmodes(12, o)
-        assert st == 0 and rep["max_residual"] <= 1e-7, rep
-        _check_modes(c, H, M, ev, modes, 12, "fp64", 1e-6)
-        out[tc] = ev
-    assert np.abs(out[1][1:] - out[0][1:]).max() / out[0][1] < 1e-8
+        # columns (three column tiles of the MMA, an odd count); k = 80: 88
+        # columns (eleven tiles, beyond the 64 of the torus benchmark)
+        out = {}
+        for tc in (1, 0):
+            o = binding.default_opts(tol=1e-7, precond_tc=tc)
+            ev, modes, rep, st = ctx.eigenmodes(k, o)
+            assert st == 0 and rep["max_residual"] <= 1e-7, rep
+            _check_modes(c, H, M, ev, modes, k, "fp64", 1e-6)
+            out[tc] = ev
+        assert np.abs(out[1][1:] - out[0][1:]).max() / out[0][1] < 1e-8
     ctx.close()
 
 

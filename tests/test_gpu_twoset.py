@@ -156,6 +156,19 @@ def test_farthest_points_beyond_shared_memory():
     ctx.close()
 
 
+def test_farthest_points_on_the_whole_gpu():
+    """From 200,000 points on, the sampling runs on every SM at once (one block
+    per SM, a grid barrier per centre): a 228,000-point torus grid, K = 300,
+    matches the oracle exactly, as does the cluster form below that size."""
+    X, v = synth.torus_grid(0.012)
+    assert X.shape[0] > 200000
+    ctx = _build(X, v, 300, 3.0)
+    _, cen, rad = ctx.twoset()
+    ocen, _, orad = _oracle(X, 300, 3.0)
+    assert np.array_equal(cen, ocen) and np.array_equal(rad, orad)
+    ctx.close()
+
+
 def test_errors_are_reported():
     from paper_2605_29318_gb300 import binding
     # six distinct positions, K = 7
