@@ -359,6 +359,25 @@ ff_status ff_export_matrices(const ff_ctx* ctx, int64_t* row_ptr, int32_t* col, 
  * Y_H / Y_M device, same layout; either may be NULL.  1 <= m <= 512. */
 ff_status ff_apply_operators(ff_ctx* ctx, const void* X, int m, void* YH, void* YM);
 
+/* Matrix-free application (Prop. 1 and Eq. 14 without assembly): Y_H = H_w X
+ * and Y_M = M X computed from the shape-function tables of the built cloud
+ * as sum_s G_s^T D G_s X and Phi^T V Phi X, with (G_s)_ik = d_s phi_k(X_i),
+ * Phi_ik = phi_k(X_i), D = diag(v_i (lambda_i + 4 mu_i)), V = diag(v_i): one
+ * pass per quadrature point (G_s X, Phi X) and one per node over the points it
+ * covers (no atomics, fixed summation order).  Needs rkpm_build or
+ * rkpm_build_twoset only; the material is given here as for assemble_hessian.
+ * It reads the tables instead of the assembled matrices (fewer bytes where a
+ * cloud has many more matrix entries than support pairs).  H_w's diagonal is
+ * not replaced here: H_w 1 = 0 holds to the rounding of the tables.  FP64
+ * sums in FP64 contexts, FP32 otherwise.  A two-set cloud builds its
+ * centre -> points lists on the first call (a pass over all points per centre).
+ *   E, nu    device float[n] per-particle (two-set: per point) material, or NULL
+ *   E0, nu0  uniform material where the arrays are NULL
+ *   X        device, column-major n x m in the caller's order, context precision
+ *   YH, YM   device, same layout; either may be NULL.  1 <= m <= 512. */
+ff_status ff_apply_operators_matfree(ff_ctx* ctx, const float* E, const float* nu, double E0,
+                                     double nu0, const void* X, int m, void* YH, void* YM);
+
 /* Allocation-free variant of ff_apply_operators (the paper has no
  * counterpart).  It serves callers that cannot allocate device memory at the
  * time of the call: real-time loops that forbid driver allocations (a

@@ -33,7 +33,7 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block",
            "ff_skinning_weights", "ff_lbs_deform", "rkpm_build_twoset", "ff_get_twoset",
            "eigenmodes_batched", "ff_profile_classes", "ff_subspace_host",
-           "ff_subspace_twoset_host", "ff_export_row_ptr"]
+           "ff_subspace_twoset_host", "ff_export_row_ptr", "ff_apply_operators_matfree"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6, "setup": 7, "fps": 8, "cover": 9, "shape": 10, "pattern": 11,
         "asm_values": 12}
@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(EigOpts), i32]
     L.ff_profile_classes.argtypes = [vp, ctypes.c_uint32]
     L.ff_export_row_ptr.argtypes = [vp, vp]
+    L.ff_apply_operators_matfree.argtypes = [vp, vp, vp, dbl, dbl, vp, i32, vp, vp]
     L.ff_subspace_host.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, i32,
                                    ctypes.POINTER(EigOpts), vp, vp, ctypes.POINTER(EigReport)]
     L.ff_subspace_twoset_host.argtypes = [vp, vp, vp, vp, vp, i64, i32, dbl, i64, dbl, dbl, i32,
@@ -361,6 +362,20 @@ class Context:
         YH = torch.empty_like(Xc)
         YM = torch.empty_like(Xc)
         self._check(self.L.ff_apply_operators(self.h, _ptr(Xc), m, _ptr(YH), _ptr(YM)))
+        return YH.t(), YM.t()
+
+    def apply_operators_matfree(self, X, E=None, nu=None, E0=1e5, nu0=0.45):
+        """(H X, M X) from the shape-function tables without assembled matrices;
+        the material as for assemble_hessian (E, nu per-particle float32 CUDA
+        tensors or None for the uniform E0, nu0)."""
+        import torch
+        m = int(X.shape[1])
+        Xc = X.t().contiguous()
+        YH = torch.empty_like(Xc)
+        YM = torch.empty_like(Xc)
+        self._check(self.L.ff_apply_operators_matfree(self.h, _ptr(E), _ptr(nu), float(E0),
+                                                      float(nu0), _ptr(Xc), m, _ptr(YH),
+                                                      _ptr(YM)))
         return YH.t(), YM.t()
 
     def apply_operators_noalloc(self, X, YH=None, YM=None):

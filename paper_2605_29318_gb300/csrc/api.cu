@@ -479,6 +479,17 @@ ff_status ff_apply_operators(ff_ctx* c, const void* X, int m, void* YH, void* YM
   });
 }
 
+ff_status ff_apply_operators_matfree(ff_ctx* c, const float* E, const float* nu, double E0,
+                                     double nu0, const void* X, int m, void* YH, void* YM) {
+  return guarded(c, [&] {
+    FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "no cloud built");
+    FF_REQUIRE(X && m >= 1 && m <= 512, FF_ERR_INVALID_ARG, "bad block");
+    if (!E) FF_REQUIRE(E0 > 0 && std::isfinite(E0), FF_ERR_INVALID_ARG, "E0 must be > 0");
+    if (!nu) FF_REQUIRE(nu0 >= 0 && nu0 < 0.5, FF_ERR_INVALID_ARG, "nu0 must be in [0, 0.5)");
+    ff::apply_matfree(c, E, nu, E0, nu0, X, m, YH, YM);
+  });
+}
+
 ff_status ff_warmstart_features(ff_ctx* c, float* feat) {
   return guarded(c, [&] {
     FF_REQUIRE(c->stage >= 1, FF_ERR_STATE, "features before rkpm_build");

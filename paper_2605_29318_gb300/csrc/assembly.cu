@@ -249,6 +249,32 @@ __global__ void k_split_df(const double* __restrict__ x, float2* __restrict__ y,
 
 void finish_matrices(ff_ctx* c);
 
+// v_i (lambda_i + 4 mu_i) per quadrature point into wh (double-float pairs in
+// FP64 contexts, FP32 otherwise); throws FF_ERR_INVALID_ARG on a bad material
+void material_weights(ff_ctx* c, const float* E, const float* nu, double E0, double nu0,
+                      void* wh) {
+  cudaStream_t st = c->stream;
+  const long long nq = c->nq;
+  const int T = 256;
+  const int* qperm = c->twoset ? nullptr : c->perm.as<int>();
+  reset_flags(c);
+  if (c->prec == FF_PREC_FP64)
+    (k_material<dfloat><<<ceil_div(nq, T), T, 0, st>>>(qperm, nq, c->vol.as<float>(), E, nu, E0,
+                                                     nu0, static_cast<dfloat*>(wh),
+                                                     c->flags.as<DevFlags>()),
+     ::ff::note_launch());
+  else
+    (k_material<float><<<ceil_div(nq, T), T, 0, st>>>(qperm, nq, c->vol.as<float>(), E, nu, E0,
+                                                    nu0, static_cast<float*>(wh),
+                                                    c->flags.as<DevFlags>()),
+     ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+  const DevFlags f = read_flags(c);
+  if (f.code == FF_ERR_INVALID_ARG)
+    throw Error(FF_ERR_INVALID_ARG, "invalid material (need E > 0, 0 <= nu < 0.5) at point " +
+                                        std::to_string(f.index));
+}
+
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0) {
   cudaStream_t st = c->stream;
   const long long n = c->n, n1 = c->n1, nq = c->nq;

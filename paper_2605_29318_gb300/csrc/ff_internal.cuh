@@ -146,6 +146,7 @@ struct ff_ctx {
   ff::Buf clim;      // double[K] t^2 r_k^2 (+inf untruncated)
   ff::Buf clim32;    // float[K]  its FP32 rounding (filter)
   ff::Buf qpts;      // float[3 nq] the quadrature points (x, y, z), caller order
+  bool has_cols = false;  // the transposed lists nbrT_* are built
   // neighbours (internal order)
   ff::Buf nbr_ptr;   // int64[nq+1]
   ff::Buf nbr_idx;   // int[n1]
@@ -228,6 +229,14 @@ void scan_counts_i32(const int* in, int* out, long long n, ff_ctx* c, Buf& tmp);
 void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a, int64_t n);
 void build_shape(ff_ctx* c);
 void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, double nu0);
+// v_i (lambda_i + 4 mu_i) per quadrature point (context precision) into wh
+void material_weights(ff_ctx* c, const float* E, const float* nu, double E0, double nu0,
+                      void* wh);
+// the transposed lists of a two-set cloud (built on demand)
+void twoset_columns(ff_ctx* c, const float* Xq);
+// H_w X and M X from the shape-function tables (matfree.cu)
+void apply_matfree(ff_ctx* c, const float* E, const float* nu, double E0, double nu0,
+                   const void* X, int m, void* YH, void* YM);
 
 // the two-set discretisation (twoset.cu): centres, radii, covering lists and
 // shape functions at the quadrature points

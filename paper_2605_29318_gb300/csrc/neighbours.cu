@@ -321,6 +321,7 @@ void build_neighbours(ff_ctx* c, const float* X, const float* v, const float* a,
   long long* ptmp = reinterpret_cast<long long*>(c->scratch[7].ensure(sizeof(long long) * n1));
   (k_sort_transposed<<<ceil_div(n * 32, T), T, 0, st>>>(tptr, n, tidx, tpos, rtmp, ptmp), ::ff::note_launch());
   FF_LAUNCH_CHECK();
+  c->has_cols = true;
 }
 
 }  // namespace ff

@@ -121,6 +121,7 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
                          const Kern& kern = Kern()) {
   const int lane = threadIdx.x & 31;
   const C xi = (C)Xi.x, yi = (C)Xi.y, zi = (C)Xi.z, si = (C)Xi.w;
+  const C isi = C(1) / si;  // the basis scale's reciprocal, once per row
   C m[10], dm[3][10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
@@ -144,26 +145,26 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
         cw[u] = w;
         cg[u] = gs;
       }
-    C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
+    C P[4] = {C(1), r0 * isi, r1 * isi, r2 * isi};
     C g[3] = {gs * r0, gs * r1, gs * r2};
     int o = 0;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = a; b < 4; ++b, ++o) {
-        C pp = P[a] * P[b];
-        m[o] += w * pp;
-        dm[0][o] += g[0] * pp;
-        dm[1][o] += g[1] * pp;
-        dm[2][o] += g[2] * pp;
+        const C pp = P[a] * P[b];
+        mac(m[o], w, pp);  // fused (unnormalised in double-float), finished below
+        mac(dm[0][o], g[0], pp);
+        mac(dm[1][o], g[1], pp);
+        mac(dm[2][o], g[2], pp);
       }
   }
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
-    m[q] = warp_sum(m[q]);
-    dm[0][q] = warp_sum(dm[0][q]);
-    dm[1][q] = warp_sum(dm[1][q]);
-    dm[2][q] = warp_sum(dm[2][q]);
+    m[q] = warp_sum(finish(m[q]));
+    dm[0][q] = warp_sum(finish(dm[0][q]));
+    dm[1][q] = warp_sum(finish(dm[1][q]));
+    dm[2][q] = warp_sum(finish(dm[2][q]));
   }
   C L[16];
   if (!chol4<C>(m, L, C(1e-12))) return 1;
@@ -197,7 +198,7 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
       for (int cc = 0; cc < 4; ++cc) t += dm[d][sidx(r, cc)] * Cv[cc];
       rhs[r] = -t;
     }
-    rhs[1 + d] += C(1) / si;
+    rhs[1 + d] += isi;
     chol4_solve<C>(L, rhs, dC[d]);
   }
   q = 0;
@@ -216,13 +217,19 @@ __device__ int shape_row(const float4* __restrict__ pos, long long s, long long 
     } else {
       kern.template eval<C>(k, p, r0 * r0 + r1 * r1 + r2 * r2, w, gs);
     }
-    C P[4] = {C(1), r0 / si, r1 / si, r2 / si};
-    C PC = P[0] * Cv[0] + P[1] * Cv[1] + P[2] * Cv[2] + P[3] * Cv[3];
+    C P[4] = {C(1), r0 * isi, r1 * isi, r2 * isi};
+    C PC = Cv[0];
+#pragma unroll
+    for (int a = 1; a < 4; ++a) mac(PC, P[a], Cv[a]);
+    PC = finish(PC);
     phi[t] = (T)(w * PC);
     C g[3] = {gs * r0, gs * r1, gs * r2};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      C PdC = P[0] * dC[d][0] + P[1] * dC[d][1] + P[2] * dC[d][2] + P[3] * dC[d][3];
+      C PdC = dC[d][0];
+#pragma unroll
+      for (int a = 1; a < 4; ++a) mac(PdC, P[a], dC[d][a]);
+      PdC = finish(PdC);
       dphi[d * n1 + t] = (T)(g[d] * PC + w * PdC);
     }
   }

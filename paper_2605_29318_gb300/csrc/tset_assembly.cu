@@ -12,12 +12,16 @@
 // A tile's points are close together, so the union U of their covering centres
 // is small (~1.5 c_i).  One thread block per tile:
 //   1. the union as a bitmap over the centres and its popcount ranks;
-//   2. for every pair (A, B), A <= B, of 64-column blocks of the union: the
-//      tile's weighted gradients and shape functions of block A and the plain
-//      ones of block B staged densely in shared memory (zeros where a point
-//      does not see a centre), then the 64 x 64 block of
-//      sum_t (w_t g_A(t)) g_B(t)^T and sum_t (v_t phi_A(t)) phi_B(t)^T in
-//      register tiles (4 x 4 per thread, rows tr + 16 r, columns tc + 16 c);
+//   2. for every pair of 64-column blocks of the union, rows from block
+//      A = bj and columns from block B = bi <= bj: the tile's weighted
+//      gradients and shape functions of A and the plain ones of B staged
+//      densely in shared memory (zeros where a point does not see a centre),
+//      then the 64 x 64 block of sum_t (w_t g_A(t)) g_B(t)^T and
+//      sum_t (v_t phi_A(t)) phi_B(t)^T in register tiles (4 x 4 per thread,
+//      rows 4 tr + r, columns tc + 16 c: broadcast reads of A, conflict-free
+//      reads of B).  The last block of the union is usually narrow; it always
+//      falls on the row side, where the warps whose rows lie past the union
+//      skip the products;
 //   3. each non-zero entry of the upper triangle added into dense K x K FP64
 //      accumulators (atomic adds).
 // The sums inside a tile run in the context's working precision (double-float
@@ -154,7 +158,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kPlane = kTilePts * kBlk;  // one value plane of a staging array
   for (int bi = 0; bi < nblk; ++bi)
     for (int bj = bi; bj < nblk; ++bj) {
-      const int a0 = bi * kBlk, b0 = bj * kBlk;
+      const int a0 = bj * kBlk, b0 = bi * kBlk;  // rows: block bj, columns: block bi
+      const bool live = 4 * tr < U - a0;         // the thread has a row in the union
       // 2a. stage the blocks (zeros where a point does not see a centre)
       for (int q = tid; q < 4 * kPlane; q += kThreads) {
         sA[q] = T(0);
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       __syncthreads();
-      // 2b. the 64 x 64 block: rows tr + 16 r of A, columns tc + 16 c of B
+      // 2b. the 64 x 64 block: rows 4 tr + r of A, columns tc + 16 c of B
       T h[4][4], m[4][4];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -196,12 +201,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           h[r][c] = T(0);
           m[r][c] = T(0);
         }
-      for (int j = 0; j < np; ++j) {
+      for (int j = 0; j < (live ? np : 0); ++j) {
 #pragma unroll
         for (int val = 0; val < 4; ++val) {
           T a[4], b[4];
 #pragma unroll
-          for (int r = 0; r < 4; ++r) a[r] = sA[val * kPlane + j * kBlk + tr + 16 * r];
+          for (int r = 0; r < 4; ++r) a[r] = sA[val * kPlane + j * kBlk + 4 * tr + r];
 #pragma unroll
           for (int c = 0; c < 4; ++c) b[c] = sB[val * kPlane + j * kBlk + tc + 16 * c];
 #pragma unroll
@@ -220,11 +225,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const int ur = a0 + tr + 16 * r, uc = b0 + tc + 16 * c;
-          if (ur >= U || uc >= U || ur > uc) continue;
+          const int ur = a0 + 4 * tr + r, uc = b0 + tc + 16 * c;
+          if (!live || ur >= U || uc >= U || ur < uc) continue;
           const double hv = (double)finish(h[r][c]), mv = (double)finish(m[r][c]);
           if (hv == 0.0 && mv == 0.0) continue;
-          const long long at = (long long)ucol[ur] * K + ucol[uc];
+          const long long at = (long long)ucol[uc] * K + ucol[ur];  // upper triangle
           atomicAdd(&Hd[at], hv);
           atomicAdd(&Md[at], mv);
         }

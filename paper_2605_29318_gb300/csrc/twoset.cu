@@ -503,7 +503,7 @@ __global__ void k_cover_cols(const float* __restrict__ Xq, long long nq,
 
 // ------------------------------------------------------------------ shape functions
 template <class T>
-__global__ void k_shape_twoset(const float4* __restrict__ cpos, const double* __restrict__ rad,
+__global__ void __launch_bounds__(256, 2) k_shape_twoset(const float4* __restrict__ cpos, const double* __restrict__ rad,
                                const float* __restrict__ Xq, float scale,
                                const long long* __restrict__ ptr, const int* __restrict__ idx,
                                long long nq, long long n1, T* __restrict__ phi,
@@ -635,6 +635,7 @@ void twoset_columns(ff_ctx* c, const float* Xq) {
   FF_LAUNCH_CHECK();
   const DevFlags f = read_flags(c);
   FF_REQUIRE(f.code == 0, FF_ERR_CUDA, "covering lists disagree between the two passes");
+  c->has_cols = true;
 }
 
 void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int K, double trunc,
@@ -757,10 +758,6 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   ProfScope ps_cover(kProfCover);
   const long long n1 = twoset_cover(c, Xq, nq, c->nbr_ptr, c->nbr_idx, c->scratch[5]);
   c->n1 = n1;
-  // the transposed lists (centre -> the points it covers) serve the
-  // row-owner assembly only, which runs when K is too large for the dense
-  // tiles of the two-set assembly
-  if (!tset_assembly_fits(K)) twoset_columns(c, Xq);
   ps_cover.close();
 
   // ---- 5. quadrature volumes, identity order of the centres
@@ -768,6 +765,11 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   (k_copy_f32<<<ceil_div(nq, T), T, 0, st>>>(vq, vol, nq), ::ff::note_launch());
   float* qpts = reinterpret_cast<float*>(c->qpts.ensure(sizeof(float) * 3 * nq));
   (k_copy_f32<<<ceil_div(3 * nq, T), T, 0, st>>>(Xq, qpts, 3 * nq), ::ff::note_launch());
+  // the transposed lists (centre -> the points it covers) serve the row-owner
+  // assembly, which runs when K is too large for the dense tiles of the
+  // two-set assembly, and the matrix-free operator (built on demand there)
+  c->has_cols = false;
+  if (!tset_assembly_fits(K)) twoset_columns(c, qpts);
   int* perm = reinterpret_cast<int*>(c->perm.ensure(sizeof(int) * K));
   int* iperm = reinterpret_cast<int*>(c->iperm.ensure(sizeof(int) * K));
   (k_iota<<<ceil_div(K, T), T, 0, st>>>(perm, iperm, K), ::ff::note_launch());
