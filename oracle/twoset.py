@@ -206,6 +206,40 @@ def assemble(n, K, ptr, idx, phi, dphi, v, E, nu, dense=False):
     return H, M
 
 
+def rows(ks, Xq, v, P, r, trunc, E, nu, scale):
+    """Rows ks of H_w (Prop. 1) and M (Eq. 14) of a two-set cloud of any size,
+    from the definition evaluated only where it is non-zero: row k sums over
+    the quadrature points centre k covers, each with the shape functions of
+    all its covering centres.  E, nu scalars or per point.  Returns a list of
+    (cols, H_row, M_row), cols ascending, FP64."""
+    Xq = np.asarray(Xq, dtype=np.float32)
+    n = Xq.shape[0]
+    Xd = Xq.astype(F64)
+    Pd = np.asarray(P, dtype=np.float32).astype(F64)
+    rd = np.asarray(r, F64)
+    lam, mu = lame(np.broadcast_to(np.asarray(E, F64), (n,)),
+                   np.broadcast_to(np.asarray(nu, F64), (n,)))
+    vd = np.broadcast_to(np.asarray(v, F64), (n,))
+    out = []
+    for k in ks:
+        d2 = _d2(Xd, Pd[k])
+        sel = np.nonzero(d2 < (float(trunc) ** 2) * (rd[k] * rd[k]))[0] if trunc else np.arange(n)
+        ptr, idx, phi, dphi, _ = shape_functions(Xq[sel], P, r, trunc, scale=scale)
+        rowof = np.repeat(np.arange(sel.size), np.diff(ptr))
+        at_k = np.nonzero(idx == k)[0]          # one entry per selected point
+        assert np.array_equal(rowof[at_k], np.arange(sel.size))
+        wh = vd[sel] * (lam[sel] + 4.0 * mu[sel])
+        gk = dphi[:, at_k]                      # (3, points)
+        fk = phi[at_k]
+        h = np.zeros(P.shape[0])
+        m = np.zeros(P.shape[0])
+        np.add.at(h, idx, (wh[rowof] * (gk[:, rowof] * dphi).sum(0)))
+        np.add.at(m, idx, vd[sel][rowof] * fk[rowof] * phi)
+        cols = np.unique(idx)
+        out.append((cols, h[cols], m[cols]))
+    return out
+
+
 def build(Xq, v, K, E, nu, trunc=None, start=0, dense=True):
     """The whole construction in the paper's order: centres by farthest-point
     sampling of the quadrature points, radii, shape functions at the

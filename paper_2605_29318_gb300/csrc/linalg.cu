@@ -1198,10 +1198,18 @@ void gram(cudaStream_t st, const T* A, int lda, int p, const T* B, int ldb, int 
   FF_LAUNCH_CHECK();
 }
 
+void gram_mirror(cudaStream_t st, double* A, double* B, int ns, int nb) {
+  (k_gram_mirror<<<(ns * ns + 255) / 256, 256, 0, st>>>(A, B, ns, nb), ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+}
+
 template <class T>
 void gram_rr(cudaStream_t st, const T* S, const T* HS, const T* MS, int ld, int nb, int nblk,
              long long n, double* A, double* B, Buf& part) {
   const int ns = nblk * nb;
+  // FP32 blocks: split-BF16 x 3 products on the tensor cores when the basis fits
+  if constexpr (std::is_same_v<T, float>)
+    if (gram_tc_enabled() && gram_rr_tc(st, S, HS, MS, ld, nb, nblk, n, A, B, part)) return;
   if (nb % 4 == 0 && ld % 4 == 0 && al16(S) && al16(HS) && al16(MS)) {
     // all tiles in one launch: the lower block triangle of A, the W columns
     // of B and the diagonals of B's X and P blocks

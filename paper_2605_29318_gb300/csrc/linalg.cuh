@@ -44,6 +44,17 @@ template <class T>
 void gram_rr(cudaStream_t st, const T* S, const T* HS, const T* MS, int ld, int nb, int nblk,
              long long n, double* A, double* B, Buf& part);
 
+// the same Gram matrices for FP32 blocks on the tensor cores (gram_tc.cu):
+// split-BF16 x 3 tcgen05 products with FP32 accumulation in TMEM, FP64 sums
+// across row ranges; false (nothing launched) when ns > 256 or n < 2048
+bool gram_rr_tc(cudaStream_t st, const float* S, const float* HS, const float* MS, int ld, int nb,
+                int nblk, long long n, double* A, double* B, Buf& part);
+// whether gram_rr takes the tensor-core path for FP32 blocks (default on;
+// the environment variable FF_GRAM_TC=0 turns it off for comparisons)
+bool gram_tc_enabled();
+// A: upper block triangle from the lower one; B: the W rows from the W columns
+void gram_mirror(cudaStream_t st, double* A, double* B, int ns, int nb);
+
 // C (n x q, with the column split described in linalg.cu) = beta C + A Y, Y p x q row-major
 // with leading dimension ldy (default q)
 template <class T>

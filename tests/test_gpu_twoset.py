@@ -8,6 +8,8 @@ contexts (double-float arithmetic, the Gaussian from the FP64 exp), 2e-5 in
 FP32 ones; H_w and M within 1e-10 / 1e-4 of their largest entry; eigenvalues
 within 1e-8 relative of the oracle's dense solve (FP64).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -197,11 +199,17 @@ def test_errors_are_reported():
 def test_splat_of_a_million_points():
     """The splat-like cloud (1,000,000 points from 64 anisotropic Gaussians,
     volumes from local density, E per Gaussian) through the paper's own route
-    for splats: the points themselves as quadrature points, K = 1,000
-    farthest-point centres, k = 64.  Centres and radii bit-exact against the
-    oracle's farthest-point sampling of all million points; the weight fields
-    at sampled points against the oracle's shape functions; every residual
-    recomputed in FP64 from the exported K x K matrices."""
+    for splats, in the benchmark's configuration: the points themselves as
+    quadrature points, K = 1,000 farthest-point centres, k = 64, FP64 context,
+    default options.  Centres and radii bit-exact against the oracle's
+    farthest-point sampling of all million points; sampled rows of H_w and M
+    against the oracle's rows (1e-10 of the row's largest entry); the 63
+    non-constant eigenvalues against the oracle's dense solve of its own
+    matrices (stored by tests/golden/make_splat_eigenvalues.py; 1e-5
+    relative); every residual recomputed in FP64 from the exported K x K
+    matrices; the modes' subspace within 1e-3 rad of the exact eigenspace of
+    those matrices (trace bound with the oracle's eigenvalues); the weight
+    fields at sampled points against the oracle's shape functions."""
     import scipy.sparse as sp
     import torch
     from paper_2605_29318_gb300 import binding
@@ -219,6 +227,21 @@ def test_splat_of_a_million_points():
     Ms = sp.csr_matrix((M, col, ptr), shape=(K, K))
     C = modes.double().cpu().numpy()
     assert eigen.residuals(Hs, Ms, ev, C)[1:].max() <= 2e-6
+    scale = float(np.float32(orad.max()))
+    for kk, (cols, h, m) in zip([5, 500, 999], twoset.rows([5, 500, 999], c.X, c.v, P, orad, 3.0,
+                                                           c.E, c.nu, scale)):
+        s = slice(ptr[kk], ptr[kk + 1])
+        np.testing.assert_array_equal(col[s], cols)
+        # the stored diagonal of H_w is minus the row's off-diagonal sum
+        off = col[s] != kk
+        assert np.abs(H[s][off] - h[off]).max() <= 1e-10 * np.abs(h).max()
+        assert abs(-H[s][off].sum() - h[~off][0]) <= 1e-9 * np.abs(h).max()
+        assert np.abs(M[s] - m).max() <= 1e-10 * np.abs(m).max()
+    lam = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden",
+                                  "splat_eigenvalues.txt"))[:, 1]
+    rel = np.abs(ev[1:] - lam[1:k]) / lam[1:k]
+    assert rel.max() <= 1e-5, rel
+    assert eigen.subspace_angle_bound(Hs, Ms, C, lam) <= 1e-3
     rng = np.random.default_rng(6)
     Q = c.X[rng.choice(c.n, 300, replace=False)]
     Cw = rng.standard_normal((K, 4))

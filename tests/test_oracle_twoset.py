@@ -295,3 +295,25 @@ def test_batch_generator_covers_every_particle():
         ptr, idx = rkpm.neighbours(c.X, c.a)
         _, _, cond = rkpm.shape_functions(c.X, c.a, ptr, idx)
         assert np.max(cond) < 1e4, c.name
+
+
+def test_single_rows_match_the_full_assembly():
+    """twoset.rows (one row from the quadrature points its centre covers)
+    against the full assembly, with per-point material."""
+    X, v = synth.cube_grid(10)
+    K = 80
+    cen = twoset.farthest_point_sampling(X, K)
+    P = X[cen]
+    r = twoset.radii(P)
+    rng = np.random.default_rng(2)
+    E = rng.uniform(1e4, 1e6, X.shape[0])
+    nu = 0.4
+    scale = float(np.float32(r.max()))
+    ptr, idx, phi, dphi, _ = twoset.shape_functions(X, P, r, 3.0, scale=scale)
+    H, M = twoset.assemble(X.shape[0], K, ptr, idx, phi, dphi, v, E, nu)
+    for k, (cols, h, m) in zip([0, 33, 79], twoset.rows([0, 33, 79], X, v, P, r, 3.0, E, nu,
+                                                        scale)):
+        np.testing.assert_array_equal(cols, H[k].indices)
+        np.testing.assert_allclose(h, H[k].data, rtol=1e-9, atol=1e-12 * np.abs(H[k].data).max())
+        np.testing.assert_allclose(m, M[k].toarray()[0, cols], rtol=1e-9,
+                                   atol=1e-12 * np.abs(M[k].data).max())
