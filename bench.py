@@ -26,14 +26,16 @@ learned warm start, with the roofline of its preconditioner step, its fused
 (H, M) block product and the skinning weight fields of its modes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload splat|torus|twoset-torus] [--prec fp64|fp32]
+                  [--workload splat|torus|twoset-torus|batch] [--prec fp64|fp32]
                   [--tol T] [--cheb D] [--cheb-fp64 D] [--fp32-phase 0|1]
                   [--fp32-tol T] [--precond-tc 0|1] [--precond-compact 0|1]
                   [--no-cpu-baseline] [--no-torus]
 
 `--workload torus` prints the torus line on its own (the nodal path alone);
 `--workload twoset-torus` times the two-set construction on the torus as
-49,584 inside-grid quadrature points (h = 0.02), K = 1,000, k = 32.
+49,584 inside-grid quadrature points (h = 0.02), K = 1,000, k = 32;
+`--workload batch` times one eigenmodes_batched call on 32 objects of
+2,000-200,000 particles per step (objects/s, particles/s).
 
 With N > 1 (torchrun, one process per GPU) every rank solves its own object
 (replicas: the path has no cross-GPU exchange; weak scaling) and the reported
@@ -391,6 +393,7 @@ def splat_line(args, r, peaks):
     roof = _roofline("alu", "k_tset_tiles (two-set H_w and M: dense 64 x 64 register tiles of "
                      "32-point tiles grouped by nearest centre)",
                      ops, "algorithmic_fp32_ops_per_launch", ms_launch, cnt, peaks,
+                     traffic=_traffic("asm_values", "k_tset_tiles"),
                      extra={"pair_products": pair_products,
                             "fp32_ops_per_multiply_add": per_mac // 2 * 2})
     line = {
@@ -633,6 +636,62 @@ def run_twoset_torus(args, ctx, dev, local):
     return line
 
 
+BATCH_OBJECTS = 32
+BATCH_WORKLOAD = ("batch of 32 objects (cube / torus / ellipsoid unions, seed 4, random scale "
+                  "and rotation), particle counts log-uniform 2,000-200,000, k uniform 16-48, "
+                  "cubic B-spline support 2.0x spacing floored at 1.5x the 8-nearest "
+                  "distance, E=1e6 nu=0.4; one eigenmodes_batched call per step")
+
+
+def batch_config(args):
+    return {"workload": BATCH_WORKLOAD, "precision": args.prec, "tol": args.tol,
+            "objects": BATCH_OBJECTS, "l2": L2_NOTE, "parallelism": "single GPU"}
+
+
+def run_batch(args, dev, local):
+    """Config 4 in miniature: one eigenmodes_batched call on 32 objects per
+    step (a pool of host threads, one context and stream each, on one GPU);
+    seconds per batch, objects/s and particles/s."""
+    import torch
+
+    from paper_2605_29318_gb300 import binding, synth
+    clouds = synth.batch(BATCH_OBJECTS, seed=4)
+    objs = [{"X": torch.from_numpy(c.X).to(dev), "v": torch.from_numpy(c.v).to(dev),
+             "a": torch.from_numpy(c.a).to(dev), "E0": c.E, "nu0": c.nu, "k": c.k}
+            for c in clouds]
+    opts = _opts(args)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step():
+        return binding.eigenmodes_batched(objs, args.prec, opts, device=local)
+
+    for _ in range(args.warmup):
+        _timed(step, st, flush)
+    launches0 = binding.launch_count()
+    times = []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            t, (status, res) = _timed(step, st, flush)
+            times.append(t)
+    launches = binding.launch_count() - launches0
+    ms = sum(times) / len(times)
+    npart = sum(c.n for c in clouds)
+    return {
+        "metric": METRIC, "value": round(ms / 1000.0, 5), "unit": "s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": _dtype_name(args), "data": "synthetic", "config": batch_config(args),
+        "batch": {"objects": len(clouds), "particles": int(npart),
+                  "objects_per_s": round(len(clouds) / (ms * 1e-3), 2),
+                  "particles_per_s": round(npart / (ms * 1e-3)),
+                  "status": int(status),
+                  "max_residual": max(r[2]["max_residual"] for r in res),
+                  "iterations_max": max(r[2]["iterations"] for r in res)},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -652,6 +711,12 @@ def run_ours(args):
     # FP32 pipe peak from the unit counts: SMs x 128 FP32 lanes x 2 (FMA) x max clock
     peaks["fp32_tflops"] = round(props.multi_processor_count * 128 * 2 * peaks["sm_max_mhz"]
                                  * 1e-6, 2)
+    if args.workload == "batch":
+        line = run_batch(args, dev, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        ctx.close()
+        return
     if args.workload == "twoset-torus":
         line = run_twoset_torus(args, ctx, dev, local)
         if rank == 0:
@@ -722,6 +787,11 @@ def run_reference(args):
     elif args.workload == "twoset-torus":
         one, config = oracle_twoset_torus_step, twoset_torus_config(args)
         sample = "FP64 two-set oracle on the whole workload"
+    elif args.workload == "batch":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the batch workload has no oracle arm (its objects are checked "
+                          "one by one against the single-object calls)"}), flush=True)
+        return
     else:
         one, config = oracle_torus_step, torus_config(args)
         sample = "FP64 oracle on the same torus with 10,000 particles instead of 50,000"
@@ -746,8 +816,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="splat", choices=["splat", "torus", "twoset-torus"],
-                    help="the splat-like cloud (default), the nodal torus, or the two-set torus")
+    ap.add_argument("--workload", default="splat",
+                    choices=["splat", "torus", "twoset-torus", "batch"],
+                    help="the splat-like cloud (default), the nodal torus, the two-set torus, "
+                         "or a 32-object batch")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--cheb", type=int, default=16)

@@ -431,6 +431,19 @@ ff_status ff_profile_read(ff_ctx* ctx, int cls, int64_t* launches, double* total
 /* Number of kernel launches the library has issued in this process. */
 int64_t ff_launch_count(void);
 
+/* Self-check of the library's bounded device-side waits (the paper has no
+ * counterpart).  The only kernels of the library that wait on other blocks
+ * are the farthest-point sampling on the whole GPU (a grid barrier per
+ * centre) and the tensor-core Gram (mbarriers); every such wait gives up after
+ * a bounded number of clock cycles and reports FF_ERR_TIMEOUT instead of
+ * hanging.  This call runs that grid barrier with one arrival missing, so
+ * that its wait can only end by running out after wait_cycles SM clock cycles
+ * (1e6 .. 4e9; about 2e9 a second at GB300's clock).  Returns FF_ERR_TIMEOUT
+ * when the wait ran out and the kernel returned (the expected outcome; the
+ * device stays usable), FF_ERR_CUDA when the device has no cooperative launch
+ * or a CUDA call failed, FF_ERR_INVALID_ARG on a bad device or wait. */
+ff_status ff_selftest_device_wait(int device, int64_t wait_cycles);
+
 /* --------------------------------------------------------- learned warm start
  * The paper starts its LOBPCG from a random block (Supp. Sec. B).  This
  * library can instead start from a block predicted by a small point network

@@ -33,7 +33,8 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_net_forward", "ff_net_loss_grad", "ff_net_train_step", "ff_warmstart_block",
            "ff_skinning_weights", "ff_lbs_deform", "rkpm_build_twoset", "ff_get_twoset",
            "eigenmodes_batched", "ff_profile_classes", "ff_subspace_host",
-           "ff_subspace_twoset_host", "ff_export_row_ptr", "ff_apply_operators_matfree"]
+           "ff_subspace_twoset_host", "ff_export_row_ptr", "ff_apply_operators_matfree",
+           "ff_selftest_device_wait"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6, "setup": 7, "fps": 8, "cover": 9, "shape": 10, "pattern": 11,
         "asm_values": 12}
@@ -128,6 +129,7 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(EigOpts), i32]
     L.ff_profile_classes.argtypes = [vp, ctypes.c_uint32]
     L.ff_export_row_ptr.argtypes = [vp, vp]
+    L.ff_selftest_device_wait.argtypes = [i32, i64]
     L.ff_apply_operators_matfree.argtypes = [vp, vp, vp, dbl, dbl, vp, i32, vp, vp]
     L.ff_subspace_host.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, i32,
                                    ctypes.POINTER(EigOpts), vp, vp, ctypes.POINTER(EigReport)]
@@ -147,6 +149,12 @@ def load_library(path: str = LIB_PATH):
     L.ff_net_last_error.argtypes = [ctypes.c_void_p]
     _lib = L
     return L
+
+
+def selftest_device_wait(device: int = 0, wait_cycles: int = 200_000_000) -> int:
+    """Run the library's grid barrier with one arrival missing: its bounded
+    wait runs out; returns the status (FF_ERR_TIMEOUT = 7 expected)."""
+    return int(load_library().ff_selftest_device_wait(int(device), int(wait_cycles)))
 
 
 def launch_count() -> int:

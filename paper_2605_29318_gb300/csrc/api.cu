@@ -330,6 +330,23 @@ ff_status ff_profile_read(ff_ctx* c, int cls, int64_t* launches, double* total_m
 
 int64_t ff_launch_count(void) { return ff::launch_count(); }
 
+ff_status ff_selftest_device_wait(int device, int64_t wait_cycles) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    (void)cudaGetLastError();
+    return FF_ERR_CUDA;
+  }
+  if (wait_cycles < 1000000 || wait_cycles > 4000000000LL) return FF_ERR_INVALID_ARG;
+  try {
+    return ff::selftest_device_wait(device, wait_cycles);
+  } catch (const ff::Error& e) {
+    (void)cudaGetLastError();
+    return e.code;
+  } catch (...) {
+    return FF_ERR_CUDA;
+  }
+}
+
 ff_status ff_get_sizes(const ff_ctx* c, int64_t* n, int64_t* n1, int64_t* n2) {
   if (!c) return FF_ERR_INVALID_ARG;
   if (n) *n = c->stage >= 1 ? c->n : 0;

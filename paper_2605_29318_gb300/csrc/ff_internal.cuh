@@ -232,6 +232,8 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
 // v_i (lambda_i + 4 mu_i) per quadrature point (context precision) into wh
 void material_weights(ff_ctx* c, const float* E, const float* nu, double E0, double nu0,
                       void* wh);
+// the grid barrier's bounded wait run out on purpose (one arrival missing)
+ff_status selftest_device_wait(int device, long long wait_cycles);
 // the transposed lists of a two-set cloud (built on demand)
 void twoset_columns(ff_ctx* c, const float* Xq);
 // H_w X and M X from the shape-function tables (matfree.cu)

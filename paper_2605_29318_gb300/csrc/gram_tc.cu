@@ -23,9 +23,11 @@
 //     commits them to the stage's mbarrier, which frees the stage for the
 //     chunk after next;
 //   * the epilogue reads the accumulators back with tcgen05.ld (warp w owns
-//     TMEM lanes 32 w .. 32 w + 31, i.e. output rows) into an FP32 partial per
+//     TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, i.e. output rows, and every
+//     fourth 16-column group from 16 (w / 4) on) into an FP32 partial per
 //     CTA; a second kernel sums the partials of all CTAs in a fixed order in
-//     FP64 and writes the entries the Rayleigh-Ritz step reads.
+//     FP64 and writes the entries the Rayleigh-Ritz step reads.  16 warps
+//     share the conversion of the chunks (4 per scheduler).
 // Waits on the mbarriers are bounded; a wait that runs out (a fault of the
 // hardware, not of the data) poisons the partial with NaN, which the solver
 // reports as a non-finite residual.
@@ -40,7 +42,7 @@
 namespace ff {
 namespace {
 
-constexpr int kGT = 128;        // threads: 4 warps = the 128 TMEM lanes of the tile
+constexpr int kGT = 512;        // threads: 16 warps, four per set of 32 TMEM lanes
 constexpr int kKC = 32;         // rows per chunk (two K = 16 slices)
 constexpr int kMT = 128;        // output rows per tile (the M of the MMA)
 constexpr long long kSpin = 1LL << 26;
@@ -238,15 +240,16 @@ __global__ void __launch_bounds__(kGT, 1)
   if (tid == 0 && nchunk > 0) commit(su32(&mbar[2]));
   if (nchunk > 0) ok = ok && wait_parity(su32(&mbar[2]), 0u);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // epilogue: row m0 + 32 warp + lane of CA and CB into this CTA's partial
-  const int row = 32 * warp + lane;
+  // epilogue: row m0 + 32 (warp % 4) + lane of CA and CB into this CTA's partial
+  const int lw = warp & 3;
+  const int row = 32 * lw + lane;
   float* pa = part + ((long long)(mt * G + g) * 2) * kMT * npad;
   float* pb = pa + (long long)kMT * npad;
-  for (int c0 = 0; c0 < npad; c0 += 16) {
+  for (int c0 = 16 * (warp >> 2); c0 < npad; c0 += 64) {
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
       unsigned r[16];
-      const unsigned addr = tbase + ((unsigned)(32 * warp) << 16) + (unsigned)(which * 256 + c0);
+      const unsigned addr = tbase + ((unsigned)(32 * lw) << 16) + (unsigned)(which * 256 + c0);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
           "%14,%15}, [%16];\n"

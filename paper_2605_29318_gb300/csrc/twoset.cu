@@ -228,7 +228,8 @@ __global__ void __cluster_dims__(kFpsCS, 1, 1) __launch_bounds__(kFpsT, 1)
 constexpr long long kGridWaitCycles = 2000000000LL;
 
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* abort,
-                                             DevFlags* flags) {
+                                             DevFlags* flags,
+                                             long long limit = kGridWaitCycles) {
   __shared__ int s_abort;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -241,7 +242,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int
         ab = 1;
         break;
       }
-      if (clock64() - t0 > kGridWaitCycles) {
+      if (clock64() - t0 > limit) {
         atomicExch(abort, 1);
         if (atomicCAS(&flags->code, 0, (int)FF_ERR_TIMEOUT) == 0) flags->index = -1;
         ab = 1;
@@ -355,6 +356,13 @@ __global__ void __launch_bounds__(kFpsT, 1)
     cz = win.z;
     __syncthreads();  // s_win and red are rewritten in the next step
   }
+}
+
+// Self-check of the bounded wait: every block arrives once at a barrier that
+// waits for one arrival more than the grid has, so the wait can only end by
+// running out (FF_ERR_TIMEOUT in the flags) or through the abort word.
+__global__ void k_wait_check(unsigned* bar, int* abort, DevFlags* flags, long long limit) {
+  grid_barrier(bar, gridDim.x + 1u, abort, flags, limit);
 }
 
 __global__ void k_gather_centres(const float* __restrict__ X, const long long* __restrict__ chosen,
@@ -636,6 +644,38 @@ void twoset_columns(ff_ctx* c, const float* Xq) {
   const DevFlags f = read_flags(c);
   FF_REQUIRE(f.code == 0, FF_ERR_CUDA, "covering lists disagree between the two passes");
   c->has_cols = true;
+}
+
+// The grid barrier of the farthest-point sampling with one arrival missing:
+// the status the host reads once the bounded wait has run out.
+ff_status selftest_device_wait(int device, long long wait_cycles) {
+  int coop = 0;
+  FF_CUDA(cudaSetDevice(device));
+  FF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+  FF_REQUIRE(coop, FF_ERR_CUDA, "the device has no cooperative launch");
+  unsigned char* mem = nullptr;
+  FF_CUDA(cudaMalloc(&mem, 256));
+  ff_status out = FF_ERR_CUDA;
+  try {
+    unsigned* bar = reinterpret_cast<unsigned*>(mem);
+    int* abort = reinterpret_cast<int*>(mem + 16);
+    DevFlags* flags = reinterpret_cast<DevFlags*>(mem + 64);
+    FF_CUDA(cudaMemset(mem, 0, 256));
+    long long limit = wait_cycles;
+    void* args[] = {&bar, &abort, &flags, &limit};
+    FF_CUDA(cudaLaunchCooperativeKernel((const void*)k_wait_check, dim3(sm_count()), dim3(32),
+                                        args, 0, nullptr));
+    ::ff::note_launch();
+    FF_CUDA(cudaDeviceSynchronize());
+    DevFlags h{};
+    FF_CUDA(cudaMemcpy(&h, flags, sizeof(h), cudaMemcpyDeviceToHost));
+    out = h.code == FF_ERR_TIMEOUT ? FF_ERR_TIMEOUT : h.code == 0 ? FF_OK : (ff_status)h.code;
+  } catch (...) {
+    cudaFree(mem);
+    throw;
+  }
+  cudaFree(mem);
+  return out;
 }
 
 void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int K, double trunc,

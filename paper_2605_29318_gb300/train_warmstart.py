@@ -2,6 +2,8 @@
 
     python -m paper_2605_29318_gb300.train_warmstart [--train 96] [--heldout 16]
         [--nmin 8000] [--nmax 30000] [--epochs 60] [--out DIR]
+    python -m paper_2605_29318_gb300.train_warmstart --eval-only --heldout 100 \
+        --nmin 20000 --nmax 100000
 
 Labels are the 31 lowest non-constant modes (k = 32) of each training shape,
 computed by this library's own plain eigensolver path (FP32 context, random
@@ -76,6 +78,66 @@ def solve_time(c, net=None, k=32, tol=1e-6):
     return dt, rep, st
 
 
+def evaluate(n_heldout=100, nmin=20000, nmax=100000, path=None, k=32, tol=1e-6, repeats=2):
+    """The trained network against the random start on held-out shapes (seeds
+    20000 + i, particle counts log-uniform in [nmin, nmax]): per shape one
+    context, a warm-up solve, then the best of `repeats` device-timed steps
+    (rkpm_build + assemble_hessian [+ features and inference] + eigenmodes to
+    relative residual tol, FP64 context) from each start.  Returns the
+    per-shape records and the distribution of iterations, times and their
+    ratios."""
+    import torch
+    net = binding.Net(0)
+    net.set_params(load_weights() if path is None else load_weights(path))
+    recs = []
+    st = torch.cuda.current_stream()
+    for i in range(n_heldout):
+        c = synth.warmstart_shape(20000 + i, nmin, nmax, k)
+        X, v, a = _cloud_tensors(c)
+        ctx = binding.Context(0, "fp64")
+        o = binding.default_opts(tol=tol)
+
+        def step(warm):
+            ctx.rkpm_build(X, v, a)
+            ctx.assemble_hessian(None, None, c.E, c.nu)
+            X0 = ctx.warmstart_block(net, k, o) if warm else None
+            return ctx.eigenmodes(k, o, X0=X0, check=False)
+
+        out = {}
+        for warm in (False, True):
+            step(warm)
+            best, rep, status = math.inf, None, None
+            for _ in range(repeats):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(st)
+                _, _, rep, status = step(warm)
+                e1.record(st)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1000.0)
+            out[warm] = (best, rep, status)
+        recs.append(dict(name=c.name, n=c.n, plain_s=out[False][0], warm_s=out[True][0],
+                         plain_iters=out[False][1]["iterations"],
+                         warm_iters=out[True][1]["iterations"],
+                         plain_status=out[False][2], warm_status=out[True][2]))
+        print(json.dumps(recs[-1]), flush=True)
+        ctx.close()
+    net.close()
+    ratio = np.array([r["plain_s"] / r["warm_s"] for r in recs])
+    dit = np.array([r["plain_iters"] - r["warm_iters"] for r in recs])
+    q = [10, 50, 90]
+    summary = dict(
+        shapes=len(recs), nmin=nmin, nmax=nmax, tol=tol,
+        plain_over_warm_time=dict(zip(["p10", "p50", "p90"], np.percentile(ratio, q).tolist()),
+                                  mean=float(ratio.mean())),
+        iterations_saved=dict(zip(["p10", "p50", "p90"], np.percentile(dit, q).tolist()),
+                              mean=float(dit.mean())),
+        plain_s_mean=float(np.mean([r["plain_s"] for r in recs])),
+        warm_s_mean=float(np.mean([r["warm_s"] for r in recs])),
+        all_converged=bool(all(r["plain_status"] == 0 and r["warm_status"] == 0 for r in recs)))
+    return recs, summary
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--train", type=int, default=96)
@@ -86,8 +148,17 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default=os.path.dirname(WEIGHTS))
+    ap.add_argument("--eval-only", action="store_true",
+                    help="evaluate the stored network on --heldout shapes of --nmin..--nmax "
+                         "particles and write DIR/warmstart_k32_eval.json")
     args = ap.parse_args(argv)
     import torch
+    if args.eval_only:
+        recs, summary = evaluate(args.heldout, args.nmin, args.nmax)
+        with open(os.path.join(args.out, "warmstart_k32_eval.json"), "w") as fh:
+            json.dump(dict(summary=summary, shapes=recs), fh, indent=1)
+        print(json.dumps(summary), flush=True)
+        return
 
     t0 = time.perf_counter()
     data = []
