@@ -169,7 +169,8 @@ def splat_cloud():
 
 def splat_config(args):
     """The config object of the splat line (identical in both arms)."""
-    return {"workload": SPLAT_WORKLOAD, "precision": args.prec, "tol": args.tol,
+    return {"workload": SPLAT_WORKLOAD, "precision": args.prec,
+            "build_precision": getattr(args, "build_prec", "fp64"), "tol": args.tol,
             "points": SPLAT["n"], "K": SPLAT["K"], "k": SPLAT["k"], "l2": L2_NOTE,
             "parallelism": "single GPU"}
 
@@ -329,6 +330,8 @@ def run_splat(args, ctx, dev, local):
     modes = torch.empty((k, K), dtype=ctx.dtype, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
+    if args.prec == "fp64":
+        ctx.set_build_precision(args.build_prec)
 
     def step():
         ctx.rkpm_build_twoset(X, v, K, trunc, start)
@@ -388,7 +391,7 @@ def splat_line(args, r, peaks):
     # double-float sums of FP64 contexts cost 12 FP32 operations per
     # multiply-add, the FP32 ones 2
     pair_products = r["pair_products"]
-    per_mac = 24 if args.prec == "fp64" else 2
+    per_mac = 24 if (args.prec == "fp64" and args.build_prec == "fp64") else 2
     ops = 4 * pair_products * per_mac
     roof = _roofline("alu", "k_tset_tiles (two-set H_w and M: dense 64 x 64 register tiles of "
                      "32-point tiles grouped by nearest centre)",
@@ -834,6 +837,9 @@ def main():
     ap.add_argument("--precond-compact", type=int, default=0, choices=[0, 1],
                     help="preconditioner steps on the unconverged columns only, packed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--build-prec", default="fp64", choices=["fp64", "fp32"],
+                    help="splat / two-set: shape functions and assembly sums in double-float "
+                         "(fp64) or FP32 (the matrices stored in FP64 either way)")
     ap.add_argument("--no-torus", action="store_true",
                     help="splat workload: leave out the nodal torus beside it")
     args = ap.parse_args()

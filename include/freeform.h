@@ -134,6 +134,20 @@ ff_status rkpm_build(ff_ctx* ctx, const float* particles, const float* volumes,
 ff_status rkpm_build_twoset(ff_ctx* ctx, const float* points, const float* volumes, int64_t n,
                             int32_t K, double trunc, int64_t start);
 
+/* Build precision of the two-set construction in an FF_PREC_FP64 context
+ * (applies to the following rkpm_build_twoset calls).  FF_PREC_FP64 (the
+ * default): shape functions, material weights and the assembly's sums in
+ * double-float (~2^-47).  FF_PREC_FP32: the shape functions in FP32 (the FP64
+ * redo for ill-conditioned moment matrices kept) and the sums within a tile of
+ * 24 points in FP32, across tiles in FP64 -- the benchmark spec's precision plan
+ * (assembly in FP32; FP64 for the eigensolver's dense steps): H_w and M are
+ * still stored in FP64, with about FP32 accuracy (~1e-7 of their entries),
+ * and eigenmodes runs as in any FP64 context, its residuals measured against
+ * those stored matrices.  FP32 contexts always build in FP32.
+ * Errors: FF_ERR_INVALID_ARG for another value, or FF_PREC_FP64 in an FP32
+ * context. */
+ff_status ff_set_build_precision(ff_ctx* ctx, int precision);
+
 /* The two-set cloud: n_points quadrature points, K centres, centres int64[K]
  * the index of the point chosen as centre k (in the order of choice), radii
  * double[K] the r_k.  Host outputs, any may be NULL; FF_ERR_STATE without a

@@ -34,7 +34,7 @@ EXPORTS = ["ff_create", "ff_destroy", "ff_last_error", "ff_version", "rkpm_build
            "ff_skinning_weights", "ff_lbs_deform", "rkpm_build_twoset", "ff_get_twoset",
            "eigenmodes_batched", "ff_profile_classes", "ff_subspace_host",
            "ff_subspace_twoset_host", "ff_export_row_ptr", "ff_apply_operators_matfree",
-           "ff_selftest_device_wait"]
+           "ff_selftest_device_wait", "ff_set_build_precision"]
 PROF = {"precond": 0, "spmm": 1, "gram": 2, "rayleigh_ritz": 3, "update": 4, "build": 5,
         "assemble": 6, "setup": 7, "fps": 8, "cover": 9, "shape": 10, "pattern": 11,
         "asm_values": 12}
@@ -130,6 +130,7 @@ def load_library(path: str = LIB_PATH):
     L.ff_profile_classes.argtypes = [vp, ctypes.c_uint32]
     L.ff_export_row_ptr.argtypes = [vp, vp]
     L.ff_selftest_device_wait.argtypes = [i32, i64]
+    L.ff_set_build_precision.argtypes = [vp, i32]
     L.ff_apply_operators_matfree.argtypes = [vp, vp, vp, dbl, dbl, vp, i32, vp, vp]
     L.ff_subspace_host.argtypes = [vp, vp, vp, vp, vp, vp, i64, dbl, dbl, i32,
                                    ctypes.POINTER(EigOpts), vp, vp, ctypes.POINTER(EigReport)]
@@ -232,6 +233,11 @@ class Context:
                                              int(points.shape[0]), int(K), float(trunc),
                                              int(start)))
         self.n = int(K)
+
+    def set_build_precision(self, precision: str):
+        """"fp32" or "fp64": the precision of the following two-set builds
+        (shape functions and assembly sums) in an FP64 context."""
+        self._check(self.L.ff_set_build_precision(self.h, PREC[precision]))
 
     def twoset(self):
         """(n_points, centres int64 (K,), radii float64 (K,)) of a two-set cloud."""

@@ -142,6 +142,7 @@ ff_status rkpm_build(ff_ctx* c, const float* particles, const float* volumes, co
     c->n = n;
     c->nq = n;
     c->twoset = false;
+    c->t32 = c->prec != FF_PREC_FP64;
     c->n1 = c->n2 = 0;
     ff::ProfScope ps(ff::kProfBuild);
     ff::build_neighbours(c, particles, volumes, support, n);
@@ -161,6 +162,7 @@ ff_status rkpm_build_twoset(ff_ctx* c, const float* points, const float* volumes
     FF_REQUIRE(start >= 0 && start < n, FF_ERR_INVALID_ARG, "start out of range");
     c->stage = 0;
     c->n1 = c->n2 = 0;
+    c->t32 = c->prec != FF_PREC_FP64 || c->build32;
     ff::ProfScope ps(ff::kProfBuild);
     ff::build_twoset(c, points, volumes, n, K, trunc, start);
     c->stage = 1;
@@ -217,6 +219,16 @@ ff_status eigenmodes(ff_ctx* c, int k, const ff_eig_opts* opts, const void* X0, 
     if (result == FF_ERR_NUMERIC) c->err = "non-finite residual";
   });
   return s != FF_OK ? s : result;
+}
+
+ff_status ff_set_build_precision(ff_ctx* c, int precision) {
+  return guarded(c, [&] {
+    FF_REQUIRE(precision == FF_PREC_FP32 || precision == FF_PREC_FP64, FF_ERR_INVALID_ARG,
+               "build precision must be FF_PREC_FP32 or FF_PREC_FP64");
+    FF_REQUIRE(c->prec == FF_PREC_FP64 || precision == FF_PREC_FP32, FF_ERR_INVALID_ARG,
+               "an FP32 context builds in FP32");
+    c->build32 = precision == FF_PREC_FP32;
+  });
 }
 
 ff_status ff_profile_enable(ff_ctx* c, int on) {
@@ -410,7 +422,7 @@ ff_status ff_export_rkpm(const ff_ctx* cc, int64_t* ptr, int32_t* idx, double* p
     auto p = to_host<long long>(c->nbr_ptr, nq + 1);
     auto ix = to_host<int>(c->nbr_idx, n1);
     std::vector<double> ph, dph;
-    if (c->prec == FF_PREC_FP64) {
+    if (!ff::tables_f32(c)) {
       ph = to_host_df(c->phi, n1);
       dph = to_host_df(c->dphi, 3 * n1);
     } else {

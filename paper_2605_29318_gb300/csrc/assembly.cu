@@ -258,7 +258,7 @@ void material_weights(ff_ctx* c, const float* E, const float* nu, double E0, dou
   const int T = 256;
   const int* qperm = c->twoset ? nullptr : c->perm.as<int>();
   reset_flags(c);
-  if (c->prec == FF_PREC_FP64)
+  if (!tables_f32(c))
     (k_material<dfloat><<<ceil_div(nq, T), T, 0, st>>>(qperm, nq, c->vol.as<float>(), E, nu, E0,
                                                      nu0, static_cast<dfloat*>(wh),
                                                      c->flags.as<DevFlags>()),
@@ -280,14 +280,15 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   const long long n = c->n, n1 = c->n1, nq = c->nq;
   const int T = 256;
   const bool f64 = c->prec == FF_PREC_FP64;
+  const bool tdf = !tables_f32(c);  // double-float tables, weights and sums
   const size_t tb = f64 ? 8 : 4;
   reset_flags(c);
   DevFlags f{};
   // material weights per quadrature point (the nodal points are in cell
   // order, the two-set quadrature points in the caller's)
-  c->wh.ensure(tb * nq);
+  c->wh.ensure((tdf ? 8 : 4) * nq);
   const int* qperm = c->twoset ? nullptr : c->perm.as<int>();
-  if (f64)  // FP64 contexts: material weights in double-float, like the shape functions
+  if (tdf)  // FP64 contexts: material weights in double-float, like the shape functions
     (k_material<dfloat><<<ceil_div(nq, T), T, 0, st>>>(qperm, nq, c->vol.as<float>(), E, nu, E0,
                                                      nu0, c->wh.as<dfloat>(),
                                                      c->flags.as<DevFlags>()), ::ff::note_launch());
@@ -350,12 +351,20 @@ void build_matrices(ff_ctx* c, const float* E, const float* nu, double E0, doubl
   c->hdiag_f32.ensure(sizeof(float) * n);
   int tsize2 = 64;
   while (tsize2 < 2 * maxrow) tsize2 <<= 1;
-  size_t pw = assemble_smem_per_warp(tsize2, maxrow, tb);
+  size_t pw = assemble_smem_per_warp(tsize2, maxrow, tdf ? 8 : 4);
   int wpb2 = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / pw));
   size_t smem = pw * wpb2;
   int grid2 = (int)std::min<long long>(ceil_div(n, wpb2), (long long)sm_count() * 32);
   ProfScope ps_values(kProfAsmValues);
-  if (f64) {
+  if (f64 && !tdf) {  // FP32 tables and sums, FP64 storage
+    set_max_dyn_smem((const void*)k_assemble<float, double>,
+                     (int)std::max<size_t>(smem, 48 * 1024));
+    (k_assemble<float, double><<<grid2, 32 * wpb2, smem, st>>>(
+        c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->nbrT_ptr.as<long long>(),
+        c->nbrT_idx.as<int>(), c->nbrT_pos.as<long long>(), c->phi.as<float>(),
+        c->dphi.as<float>(), n1, c->vol.as<float>(), c->wh.as<float>(), n, tsize2, maxrow, aptr,
+        c->a_col.as<int>(), c->a_val.as<double>(), c->h_f32.as<float>(), c->hdiag_f32.as<float>()), ::ff::note_launch());
+  } else if (f64) {
     set_max_dyn_smem((const void*)k_assemble<dfloat, double>,
                      (int)std::max<size_t>(smem, 48 * 1024));
     (k_assemble<dfloat, double><<<grid2, 32 * wpb2, smem, st>>>(

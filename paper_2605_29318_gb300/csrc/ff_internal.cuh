@@ -130,6 +130,10 @@ struct ff_ctx {
   bool twoset = false;  // two-set discretisation: farthest-point centres, Gaussian kernel
   double trunc = 0.0;   // its cut radius in units of r_k (0: untruncated)
   float qscale = 1.f;   // its basis scale
+  // FP64 contexts: FP32 shape functions and tile sums for two-set clouds
+  // (ff_set_build_precision), the matrices still stored in FP64
+  bool build32 = false;
+  bool t32 = false;  // the built cloud's tables are FP32 (set at each build)
 
   ff::Grid grid{};
   // particles in internal (cell) order
@@ -208,6 +212,11 @@ struct ProfScope {
 
 // ---------------------------------------------------------------- helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// whether the shape-function tables (and the material weights and tile sums
+// of the assembly) are FP32: FP32 contexts, and two-set clouds of FP64
+// contexts built with FP32 build precision; else double-float pairs
+inline bool tables_f32(const ff_ctx* c) { return c->t32; }
 
 // raise a kernel's dynamic shared-memory limit on the current device (only
 // ever raised, per kernel and device; thread-safe; the attribute belongs to

@@ -118,7 +118,7 @@ void apply_matfree(ff_ctx* c, const float* E, const float* nu, double E0, double
   if (!c->has_cols) twoset_columns(c, c->qpts.as<float>());
   const long long n = c->n, nq = c->nq;
   const bool f64 = c->prec == FF_PREC_FP64;
-  void* wh = c->scratch[0].ensure((f64 ? 8 : 4) * (size_t)nq + 64);
+  void* wh = c->scratch[0].ensure((tables_f32(c) ? 4 : 8) * (size_t)nq + 64);
   material_weights(c, E, nu, E0, nu0, wh);
   auto go = [&](auto tag) {
     using C = decltype(tag);
@@ -126,9 +126,12 @@ void apply_matfree(ff_ctx* c, const float* E, const float* nu, double E0, double
     C* oh = reinterpret_cast<C*>(c->scratch[6].ensure(sizeof(C) * n * m));
     C* om = reinterpret_cast<C*>(c->scratch[7].ensure(sizeof(C) * n * m));
     gather_block<C>(c, static_cast<const C*>(X), m, in, m);
-    if constexpr (std::is_same_v<C, double>)
-      run<double, dfloat>(c, in, m, oh, om, static_cast<const dfloat*>(wh));
-    else
+    if constexpr (std::is_same_v<C, double>) {
+      if (tables_f32(c))
+        run<double, float>(c, in, m, oh, om, static_cast<const float*>(wh));
+      else
+        run<double, dfloat>(c, in, m, oh, om, static_cast<const dfloat*>(wh));
+    } else
       run<float, float>(c, in, m, oh, om, static_cast<const float*>(wh));
     if (YH) scatter_block<C>(c, oh, m, m, static_cast<C*>(YH));
     if (YM) scatter_block<C>(c, om, m, m, static_cast<C*>(YM));

@@ -8,7 +8,8 @@
 // hold sum_i c_i^2 pair products (6e9 for a million points at ~80 centres
 // each): a dense contraction once the points are grouped.  The points are
 // grouped by their nearest covering centre (a counting sort over the K
-// centres), and cut into tiles of kTilePts consecutive points of that order.
+// centres), and cut into tiles of TP consecutive points of that order (TP = 16,
+// 24 or 32: smaller tiles let two blocks share an SM).
 // A tile's points are close together, so the union U of their covering centres
 // is small (~1.5 c_i).  One thread block per tile:
 //   1. the union as a bitmap over the centres and its popcount ranks;
@@ -32,6 +33,7 @@
 // (ascending columns; an entry is stored where H_w or M is non-zero), with the
 // diagonal of H_w set to minus the sum of its row's off-diagonal entries.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "ff_internal.cuh"
@@ -40,7 +42,7 @@
 namespace ff {
 namespace {
 
-constexpr int kTilePts = 32;   // quadrature points per tile
+constexpr int kTilePtsDefault = 24;  // quadrature points per tile
 constexpr int kBlk = 64;       // union columns per register block
 constexpr int kThreads = 256;  // 16 x 16 threads, 4 x 4 entries each
 
@@ -86,9 +88,9 @@ __device__ __forceinline__ int union_rank(const unsigned* bits, const int* wpre,
 
 // One block per tile.  Shared memory (dynamic): bitmap (nw words), word
 // prefix (nw + 1), union columns (K), then the staging arrays
-// sA[4][kTilePts][kBlk] and sB[4][kTilePts][kBlk] of T.
-template <class T>
-__global__ void __launch_bounds__(kThreads, 1)
+// sA[4][TP][kBlk] and sB[4][TP][kBlk] of T.
+template <class T, int TP>
+__global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
     k_tset_tiles(const int* __restrict__ order, long long nq, const long long* __restrict__ ptr,
                  const int* __restrict__ idx, const T* __restrict__ phi,
                  const T* __restrict__ dphi, long long n1, const T* __restrict__ wh,
@@ -102,14 +104,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   size_t off = (size_t)(2 * nw + 1 + K) * 4;
   off = (off + 15) & ~size_t(15);
   T* sA = reinterpret_cast<T*>(sm_raw + off);
-  T* sB = sA + 4 * kTilePts * kBlk;
-  __shared__ int pts[kTilePts];
+  T* sB = sA + 4 * TP * kBlk;
+  __shared__ int pts[TP];
   __shared__ int s_total;
 
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const long long p0 = (long long)blockIdx.x * kTilePts;
-  const int np = (int)min((long long)kTilePts, nq - p0);
-  if (tid < kTilePts) pts[tid] = tid < np ? order[p0 + tid] : -1;
+  const long long p0 = (long long)blockIdx.x * TP;
+  const int np = (int)min((long long)TP, nq - p0);
+  if (tid < TP) pts[tid] = tid < np ? order[p0 + tid] : -1;
   for (int w = tid; w < nw; w += kThreads) bits[w] = 0u;
   __syncthreads();
   // 1. the union of the tile's covering centres
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int tr = tid >> 4, tc = tid & 15;
   const int nblk = (U + kBlk - 1) / kBlk;
-  constexpr int kPlane = kTilePts * kBlk;  // one value plane of a staging array
+  constexpr int kPlane = TP * kBlk;  // one value plane of a staging array
   for (int bi = 0; bi < nblk; ++bi)
     for (int bj = bi; bj < nblk; ++bj) {
       const int a0 = bj * kBlk, b0 = bi * kBlk;  // rows: block bj, columns: block bi
@@ -293,11 +295,43 @@ __global__ void k_dense_fill(const double* __restrict__ Hd, const double* __rest
 }
 
 template <class T>
-size_t tile_smem(int K) {
+size_t tile_smem(int K, int tp) {
   const int nw = (K + 31) >> 5;
   size_t off = (size_t)(2 * nw + 1 + K) * 4;
   off = (off + 15) & ~size_t(15);
-  return off + 2 * 4 * (size_t)kTilePts * kBlk * sizeof(T);
+  return off + 2 * 4 * (size_t)tp * kBlk * sizeof(T);
+}
+
+// points per tile: FF_TSET_TILE = 16, 24 or 32 (for measurements), else the default
+int tile_points() {
+  static const int tp = [] {
+    const char* e = std::getenv("FF_TSET_TILE");
+    const int v = e ? std::atoi(e) : 0;
+    return (v == 16 || v == 24 || v == 32) ? v : kTilePtsDefault;
+  }();
+  return tp;
+}
+
+template <class T, int TP>
+void launch_tiles(ff_ctx* c, const int* order, int K, double* Hd, double* Md) {
+  const long long nq = c->nq;
+  const size_t smem = tile_smem<T>(K, TP);
+  set_max_dyn_smem((const void*)k_tset_tiles<T, TP>, (int)smem);
+  const unsigned tiles = (unsigned)((nq + TP - 1) / TP);
+  (k_tset_tiles<T, TP><<<tiles, kThreads, smem, c->stream>>>(
+       order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<T>(),
+       c->dphi.as<T>(), c->n1, c->wh.as<T>(), c->vol.as<float>(), K, Hd, Md),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+}
+
+template <class T>
+void launch_tiles(ff_ctx* c, const int* order, int K, double* Hd, double* Md) {
+  switch (tile_points()) {
+    case 16: launch_tiles<T, 16>(c, order, K, Hd, Md); break;
+    case 32: launch_tiles<T, 32>(c, order, K, Hd, Md); break;
+    default: launch_tiles<T, 24>(c, order, K, Hd, Md); break;
+  }
 }
 
 }  // namespace
@@ -311,6 +345,7 @@ void tset_assemble(ff_ctx* c) {
   const long long nq = c->nq, n1 = c->n1;
   const int K = (int)c->n;
   const bool f64 = c->prec == FF_PREC_FP64;
+  const bool tdf = !tables_f32(c);  // double-float tables and tile sums
   const int TB = 256;
   // ---- grouping by the nearest covering centre
   int* home = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (nq + 1)));
@@ -335,25 +370,12 @@ void tset_assemble(ff_ctx* c) {
   double* Hd = reinterpret_cast<double*>(c->scratch[2].ensure(2 * sizeof(double) * kk));
   double* Md = Hd + kk;
   FF_CUDA(cudaMemsetAsync(Hd, 0, 2 * sizeof(double) * kk, st));
-  const unsigned tiles = (unsigned)((nq + kTilePts - 1) / kTilePts);
   {
     ProfScope ps(kProfAsmValues);
-    if (f64) {
-      const size_t smem = tile_smem<dfloat>(K);
-      set_max_dyn_smem((const void*)k_tset_tiles<dfloat>, (int)smem);
-      (k_tset_tiles<dfloat><<<tiles, kThreads, smem, st>>>(
-           order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<dfloat>(),
-           c->dphi.as<dfloat>(), n1, c->wh.as<dfloat>(), c->vol.as<float>(), K, Hd, Md),
-       ::ff::note_launch());
-    } else {
-      const size_t smem = tile_smem<float>(K);
-      set_max_dyn_smem((const void*)k_tset_tiles<float>, (int)smem);
-      (k_tset_tiles<float><<<tiles, kThreads, smem, st>>>(
-           order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<float>(),
-           c->dphi.as<float>(), n1, c->wh.as<float>(), c->vol.as<float>(), K, Hd, Md),
-       ::ff::note_launch());
-    }
-    FF_LAUNCH_CHECK();
+    if (tdf)
+      launch_tiles<dfloat>(c, order, K, Hd, Md);
+    else
+      launch_tiles<float>(c, order, K, Hd, Md);
   }
   // ---- CSR
   int* rc = reinterpret_cast<int*>(c->scratch[5].ensure(sizeof(int) * (nq + 1)));

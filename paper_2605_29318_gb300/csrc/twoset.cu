@@ -595,7 +595,7 @@ DevFlags twoset_shape(ff_ctx* c, const float* Q, long long nq, const long long* 
          c->pos.as<float4>(), c->crad.as<double>(), Q, c->qscale, ptr, idx, nq, n1,
          static_cast<double*>(phi), static_cast<double*>(dphi), 1e2, c->flags.as<DevFlags>()),
      ::ff::note_launch());
-  else if (c->prec == FF_PREC_FP64)
+  else if (!tables_f32(c))
     (k_shape_twoset<dfloat><<<ceil_div(nq * 32, T), T, 0, st>>>(
          c->pos.as<float4>(), c->crad.as<double>(), Q, c->qscale, ptr, idx, nq, n1,
          static_cast<dfloat*>(phi), static_cast<dfloat*>(dphi), 1e2, c->flags.as<DevFlags>()),
@@ -816,7 +816,7 @@ void build_twoset(ff_ctx* c, const float* Xq, const float* vq, long long nq, int
   FF_LAUNCH_CHECK();
 
   // ---- 6. shape functions at the quadrature points
-  const size_t es = c->prec == FF_PREC_FP64 ? 8 : 4;
+  const size_t es = tables_f32(c) ? 4 : 8;
   c->phi.ensure(es * std::max(n1, 1LL));
   c->dphi.ensure(3 * es * std::max(n1, 1LL));
   f = twoset_shape(c, Xq, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), n1, c->phi.p,

@@ -146,6 +146,42 @@ def test_skinning_weights_of_a_twoset_cloud(prec):
     ctx.close()
 
 
+def test_fp32_build_in_an_fp64_context():
+    """FP32 build precision (the benchmark spec's plan: FP32 shape functions and
+    assembly sums, FP64 storage and eigensolver): the shape functions within
+    the FP32 tolerance of the oracle's, H_w and M within 1e-4 of their largest
+    entry, and the eigenvalues of the unit cube within 1e-5 of the oracle's
+    dense solve, every residual (against the stored matrices) at 1e-6."""
+    import scipy.sparse as sp
+    from paper_2605_29318_gb300 import binding
+    X, v = synth.cube_grid(16)
+    K, E, nu = 200, 1e5, 0.45
+    ctx = binding.Context(0, "fp64")
+    ctx.set_build_precision("fp32")
+    ctx.rkpm_build_twoset(_dev(X), _dev(v), K, 3.0, 0)
+    _, cen, rad = ctx.twoset()
+    P = X[cen]
+    scale = float(np.float32(rad.max()))
+    optr, oidx, ophi, odphi, _ = twoset.shape_functions(X, P, rad, 3.0, scale=scale)
+    ptr, idx, phi, dphi = ctx.export_rkpm()
+    assert np.array_equal(idx, oidx)
+    assert np.abs(phi - ophi).max() <= TOL_SHAPE["fp32"] * np.abs(ophi).max()
+    ctx.assemble_hessian(None, None, E, nu)
+    aptr, acol, H, M = ctx.export_matrices()
+    OH, OM = twoset.assemble(X.shape[0], K, optr, oidx, ophi, odphi, v, E, nu, dense=True)
+    rows = np.repeat(np.arange(K), np.diff(aptr))
+    assert np.abs(H - OH[rows, acol]).max() <= TOL_MAT["fp32"] * np.abs(OH).max()
+    assert np.abs(M - OM[rows, acol]).max() <= TOL_MAT["fp32"] * np.abs(OM).max()
+    ev, modes, rep, st = ctx.eigenmodes(8, binding.default_opts(tol=1e-6))
+    assert st == 0
+    lam, _ = eigen.eigh_dense(OH, OM, 8)
+    np.testing.assert_allclose(ev[1:], lam[1:], rtol=1e-5)
+    Hs = sp.csr_matrix((H, acol, aptr), shape=(K, K))
+    Ms = sp.csr_matrix((M, acol, aptr), shape=(K, K))
+    assert eigen.residuals(Hs, Ms, ev, modes.double().cpu().numpy())[1:].max() <= 1e-6
+    ctx.close()
+
+
 def test_farthest_points_beyond_shared_memory():
     """More points than the cluster keeps in shared memory: the sampling runs
     from global memory and still matches the oracle exactly."""
@@ -253,3 +289,30 @@ def test_splat_of_a_million_points():
     assert np.abs(W - Wo).max() <= 1e-9 * np.abs(Wo).max()
     ctx.close()
     torch.cuda.synchronize()
+
+
+def test_splat_with_fp32_build():
+    """The benchmark's splat with FP32 build precision: the 63 non-constant
+    eigenvalues within 1e-5 of the oracle's (stored by
+    tests/golden/make_splat_eigenvalues.py), every residual against the stored
+    matrices at 2e-6."""
+    import scipy.sparse as sp
+    from paper_2605_29318_gb300 import binding
+    c = synth.gaussian_mixture(1_000_000)
+    K, k = 1000, 64
+    ctx = binding.Context(0, "fp64")
+    ctx.set_build_precision("fp32")
+    ctx.rkpm_build_twoset(_dev(c.X), _dev(c.v), K, 3.0, 0)
+    ctx.assemble_hessian(_dev(c.E), None, 1.0, float(c.nu))
+    ev, modes, rep, st = ctx.eigenmodes(k, binding.default_opts(tol=1e-6))
+    assert st == 0
+    lam = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden",
+                                  "splat_eigenvalues.txt"))[:, 1]
+    rel = np.abs(ev[1:] - lam[1:k]) / lam[1:k]
+    assert rel.max() <= 1e-5, rel
+    ptr, col, H, M = ctx.export_matrices()
+    Hs = sp.csr_matrix((H, col, ptr), shape=(K, K))
+    Ms = sp.csr_matrix((M, col, ptr), shape=(K, K))
+    C = modes.double().cpu().numpy()
+    assert eigen.residuals(Hs, Ms, ev, C)[1:].max() <= 2e-6
+    ctx.close()
