@@ -147,18 +147,40 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _opts(args):
+# Per-workload defaults of the options a flag leaves unset.  The splat follows
+# its configuration's precision plan: shape functions and tile sums in FP32
+# (the matrices stored in FP64), FP32 preconditioner steps of degree 32 (16
+# iterations instead of 21 at degree 16 on this K = 1,000 pencil); the nodal
+# torus keeps degree 16 and the double-float build of an FP64 context.
+WORKLOAD_DEFAULTS = {
+    "splat": dict(cheb=32, cheb_fp64=64, build_prec="fp32"),
+    "torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64"),
+    "twoset-torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64"),
+    "batch": dict(cheb=16, cheb_fp64=64, build_prec="fp64"),
+}
+
+
+def _opt(args, name, workload=None):
+    v = getattr(args, name, None)
+    return WORKLOAD_DEFAULTS[workload or args.workload][name] if v is None else v
+
+
+def _opts(args, workload=None):
     from paper_2605_29318_gb300 import binding
-    return binding.default_opts(tol=args.tol, cheb_degree=args.cheb, max_iter=args.max_iter,
-                                fp32_phase=args.fp32_phase, cheb_degree_fp64=args.cheb_fp64,
+    return binding.default_opts(tol=args.tol, cheb_degree=_opt(args, "cheb", workload),
+                                max_iter=args.max_iter, fp32_phase=args.fp32_phase,
+                                cheb_degree_fp64=_opt(args, "cheb_fp64", workload),
                                 precond_tc=args.precond_tc, fp32_tol=args.fp32_tol,
                                 precond_compact=args.precond_compact)
 
 
-def _dtype_name(args):
+def _dtype_name(args, workload=None):
     if args.prec == "fp32":
         return "f32+bf16"
-    return "f32+bf16, then f32x2 double-float" if args.fp32_phase else "f64"
+    solve = "f32+bf16, then f32x2 double-float" if args.fp32_phase else "f64"
+    if (workload or args.workload) == "splat" and _opt(args, "build_prec", "splat") == "fp32":
+        return "f32 build (f64 matrices); solve " + solve
+    return solve
 
 
 # ------------------------------------------------------------------ workloads
@@ -170,14 +192,17 @@ def splat_cloud():
 def splat_config(args):
     """The config object of the splat line (identical in both arms)."""
     return {"workload": SPLAT_WORKLOAD, "precision": args.prec,
-            "build_precision": getattr(args, "build_prec", "fp64"), "tol": args.tol,
+            "build_precision": _opt(args, "build_prec", "splat"), "tol": args.tol,
+            "cheb_degree": _opt(args, "cheb", "splat"),
+            "cheb_degree_fp64": _opt(args, "cheb_fp64", "splat"),
             "points": SPLAT["n"], "K": SPLAT["K"], "k": SPLAT["k"], "l2": L2_NOTE,
             "parallelism": "single GPU"}
 
 
 def torus_config(args):
     return {"workload": TORUS_WORKLOAD, "precision": args.prec, "tol": args.tol,
-            "n": 50000, "k": 32, "l2": L2_NOTE, "parallelism": "single GPU"}
+            "cheb_degree": _opt(args, "cheb", "torus"),
+            "cheb_degree_fp64": _opt(args, "cheb_fp64", "torus"), "n": 50000, "k": 32, "l2": L2_NOTE, "parallelism": "single GPU"}
 
 
 def twoset_torus_config(args):
@@ -326,12 +351,12 @@ def run_splat(args, ctx, dev, local):
     v = torch.from_numpy(c.v).to(dev)
     E = torch.from_numpy(np.ascontiguousarray(c.E, np.float32)).to(dev)
     nu = float(c.nu)
-    opts = _opts(args)
+    opts = _opts(args, "splat")
     modes = torch.empty((k, K), dtype=ctx.dtype, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
     if args.prec == "fp64":
-        ctx.set_build_precision(args.build_prec)
+        ctx.set_build_precision(_opt(args, "build_prec", "splat"))
 
     def step():
         ctx.rkpm_build_twoset(X, v, K, trunc, start)
@@ -391,10 +416,10 @@ def splat_line(args, r, peaks):
     # double-float sums of FP64 contexts cost 12 FP32 operations per
     # multiply-add, the FP32 ones 2
     pair_products = r["pair_products"]
-    per_mac = 24 if (args.prec == "fp64" and args.build_prec == "fp64") else 2
+    per_mac = 24 if (args.prec == "fp64" and _opt(args, "build_prec", "splat") == "fp64") else 2
     ops = 4 * pair_products * per_mac
     roof = _roofline("alu", "k_tset_tiles (two-set H_w and M: dense 64 x 64 register tiles of "
-                     "32-point tiles grouped by nearest centre)",
+                     "24-point tiles grouped by nearest centre)",
                      ops, "algorithmic_fp32_ops_per_launch", ms_launch, cnt, peaks,
                      traffic=_traffic("asm_values", "k_tset_tiles"),
                      extra={"pair_products": pair_products,
@@ -430,7 +455,7 @@ def run_torus(args, ctx, dev, local, rank, world):
     X = torch.from_numpy(c.X).to(dev)
     v = torch.from_numpy(c.v).to(dev)
     a = torch.from_numpy(c.a).to(dev)
-    opts = _opts(args)
+    opts = _opts(args, "torus")
     net = binding.Net(local)
     net.set_params(train_warmstart.load_weights())
     modes = torch.empty((32, c.n), dtype=ctx.dtype, device=dev)
@@ -581,7 +606,7 @@ def run_twoset_torus(args, ctx, dev, local):
     K, k = 1000, 32
     X = torch.from_numpy(Xh).to(dev)
     v = torch.from_numpy(vh).to(dev)
-    opts = _opts(args)
+    opts = _opts(args, "twoset-torus")
     modes = torch.empty((k, K), dtype=ctx.dtype, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
@@ -662,7 +687,7 @@ def run_batch(args, dev, local):
     objs = [{"X": torch.from_numpy(c.X).to(dev), "v": torch.from_numpy(c.v).to(dev),
              "a": torch.from_numpy(c.a).to(dev), "E0": c.E, "nu0": c.nu, "k": c.k}
             for c in clouds]
-    opts = _opts(args)
+    opts = _opts(args, "batch")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
 
@@ -825,8 +850,10 @@ def main():
                          "or a 32-object batch")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--cheb", type=int, default=16)
-    ap.add_argument("--cheb-fp64", type=int, default=64)
+    ap.add_argument("--cheb", type=int, default=None,
+                    help="FP32 preconditioner degree (default: 32 for the splat, 16 otherwise)")
+    ap.add_argument("--cheb-fp64", type=int, default=None,
+                    help="double-float phase preconditioner degree (default 64)")
     ap.add_argument("--fp32-phase", type=int, default=1, choices=[0, 1],
                     help="FP64 contexts: iterate in FP32 first, then finish in double-float")
     ap.add_argument("--max-iter", type=int, default=500)
@@ -837,9 +864,9 @@ def main():
     ap.add_argument("--precond-compact", type=int, default=0, choices=[0, 1],
                     help="preconditioner steps on the unconverged columns only, packed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--build-prec", default="fp64", choices=["fp64", "fp32"],
-                    help="splat / two-set: shape functions and assembly sums in double-float "
-                         "(fp64) or FP32 (the matrices stored in FP64 either way)")
+    ap.add_argument("--build-prec", default=None, choices=["fp64", "fp32"],
+                    help="splat: shape functions and assembly sums in double-float (fp64) or "
+                         "FP32 (the matrices stored in FP64 either way; default fp32)")
     ap.add_argument("--no-torus", action="store_true",
                     help="splat workload: leave out the nodal torus beside it")
     args = ap.parse_args()

@@ -207,7 +207,10 @@ typedef struct {
   int precond_spmv_calls;  /* H block products inside the preconditioner */
   double max_residual;     /* largest relative residual over the non-constant modes */
   double seconds;          /* wall time of the call */
-  int warm_start_used;     /* 1 if X0 was used, 0 if the random start was used */
+  int warm_start_used;     /* 1 if X0 was used, 0 if the random start was used, 2 if
+                              X0 was used, did not converge, and the results come
+                              from the random start run after it (the counts and
+                              seconds cover both runs) */
   int fp32_iterations;     /* of the iterations, those run in the FP32 phase */
 } ff_eig_report;
 
@@ -226,14 +229,18 @@ void ff_eig_opts_default(ff_eig_opts* opts);
  *            column-major n x (m + guard) of the context's precision, m the
  *            number of non-constant modes (k - 1, or k with exclude_constant)
  *            (float for FF_PREC_FP32, double for FF_PREC_FP64); NULL = seeded
- *            random start.  A rank-deficient X0 falls back to the random start.
+ *            random start.  A rank-deficient X0 falls back to the random start,
+ *            and so does a start that ends without convergence (not on a
+ *            timeout): the solve is then run again from the random start with
+ *            the same options, so a start block can cost iterations but never
+ *            the answer.
  *   eigvals  host, double[k] eigenvalues (ascending)
  *   modes    device, column-major n x k (leading dimension n) of the context's
  *            precision, in the caller's particle order; may be NULL
  *   rep      host, optional report
  *
  * Returns FF_ERR_NOT_CONVERGED when max_iter is reached or the residual has
- * stopped falling (50 iterations without a new best), FF_ERR_TIMEOUT when the
+ * stopped falling (40 iterations without a new best), FF_ERR_TIMEOUT when the
  * time budget runs out; the outputs then hold the iterate with the smallest
  * largest residual seen. */
 ff_status eigenmodes(ff_ctx* ctx, int k, const ff_eig_opts* opts, const void* X0,

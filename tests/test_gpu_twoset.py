@@ -292,10 +292,14 @@ def test_splat_of_a_million_points():
 
 
 def test_splat_with_fp32_build():
-    """The benchmark's splat with FP32 build precision: the 63 non-constant
-    eigenvalues within 1e-5 of the oracle's (stored by
+    """The benchmark's splat in the benchmark's launch configuration (FP32
+    build precision, FP32 preconditioner degree 32, double-float degree 64):
+    the 63 non-constant eigenvalues within 1e-5 of the oracle's (stored by
     tests/golden/make_splat_eigenvalues.py), every residual against the stored
-    matrices at 2e-6."""
+    matrices at 2e-6, sampled rows of H_w and M against the oracle's FP64 rows
+    at 1e-4 of the row's largest entry (FP32 shape functions and tile sums),
+    and the modes within 1e-3 rad of the exact eigenspace of the stored
+    matrices (LAPACK's dense generalized solve)."""
     import scipy.sparse as sp
     from paper_2605_29318_gb300 import binding
     c = synth.gaussian_mixture(1_000_000)
@@ -303,8 +307,12 @@ def test_splat_with_fp32_build():
     ctx = binding.Context(0, "fp64")
     ctx.set_build_precision("fp32")
     ctx.rkpm_build_twoset(_dev(c.X), _dev(c.v), K, 3.0, 0)
+    _, cen, rad = ctx.twoset()
+    ocen, P, orad = _oracle(c.X, K, 3.0)
+    assert np.array_equal(cen, ocen) and np.array_equal(rad, orad)
     ctx.assemble_hessian(_dev(c.E), None, 1.0, float(c.nu))
-    ev, modes, rep, st = ctx.eigenmodes(k, binding.default_opts(tol=1e-6))
+    ev, modes, rep, st = ctx.eigenmodes(
+        k, binding.default_opts(tol=1e-6, cheb_degree=32, cheb_degree_fp64=64))
     assert st == 0
     lam = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden",
                                   "splat_eigenvalues.txt"))[:, 1]
@@ -315,4 +323,15 @@ def test_splat_with_fp32_build():
     Ms = sp.csr_matrix((M, col, ptr), shape=(K, K))
     C = modes.double().cpu().numpy()
     assert eigen.residuals(Hs, Ms, ev, C)[1:].max() <= 2e-6
+    scale = float(np.float32(orad.max()))
+    for kk, (cols, h, m) in zip([5, 500, 999], twoset.rows([5, 500, 999], c.X, c.v, P, orad, 3.0,
+                                                           c.E, c.nu, scale)):
+        s = slice(ptr[kk], ptr[kk + 1])
+        np.testing.assert_array_equal(col[s], cols)
+        off = col[s] != kk
+        eh = np.abs(H[s][off] - h[off]).max() / np.abs(h).max()
+        em = np.abs(M[s] - m).max() / np.abs(m).max()
+        assert eh <= 1e-4 and em <= 1e-4, (kk, eh, em)
+    _, V = eigen.eigh_dense(Hs, Ms, k)
+    assert eigen.max_principal_angle(Ms, C, V) <= 1e-3
     ctx.close()
