@@ -130,6 +130,78 @@ __device__ void block_cholesky(R* G, int m, int* keep, R drop_rel) {
   }
 }
 
+// The same factorisation with the lower triangle in registers, for m up to
+// kRegCholMax: entry q = tid + kThreads e of the packed lower triangle (rows
+// ascending) lives in thread tid.  Before step j the owners of column j have
+// published it in shared memory (two buffers, alternating), and every thread
+// takes the step's pivot decision itself from the published diagonal, so a
+// step costs one barrier.  The trailing entries lose g_ij g_lj / g_jj (the
+// unscaled column); the owners of column j scale it as they pass it.  keep[j]
+// is written one step late, when nobody reads it any more.
+constexpr int kRegCholE = 9;
+constexpr int kRegCholMax = 135;  // m (m + 1) / 2 <= kRegCholE * kThreads
+template <class R>
+__device__ void reg_cholesky(R* G, int m, int* keep, R drop_rel) {
+  __shared__ R cb[2][kRegCholMax];
+  const int tid = threadIdx.x;
+  const int tot = m * (m + 1) / 2;
+  R g[kRegCholE];
+  int rc[kRegCholE];  // row << 16 | column, or -1
+#pragma unroll
+  for (int e = 0; e < kRegCholE; ++e) {
+    const int q = tid + kThreads * e;
+    rc[e] = -1;
+    g[e] = R(0.0);
+    if (q < tot) {
+      int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+      while (i * (i + 1) / 2 > q) --i;
+      while ((i + 1) * (i + 2) / 2 <= q) ++i;
+      const int l = q - i * (i + 1) / 2;
+      rc[e] = (i << 16) | l;
+      g[e] = G[(size_t)i * m + l];
+      if (l == 0) cb[0][i] = g[e];
+    }
+  }
+  __syncthreads();
+  int kprev = 0;
+  for (int j = 0; j < m; ++j) {
+    const int b = j & 1;
+    const R piv = cb[b][j];
+    const int kj = keep[j] && piv > drop_rel;
+    const R ljj = kj ? sqrt(piv) : R(1.0);
+    const R inv = kj ? R(1.0) / piv : R(0.0);
+    const R rl = R(1.0) / ljj;
+#pragma unroll
+    for (int e = 0; e < kRegCholE; ++e) {
+      if (rc[e] < 0) continue;
+      const int i = rc[e] >> 16, l = rc[e] & 0xffff;
+      if (l == j) {
+        g[e] = i == j ? ljj : (kj ? g[e] * rl : R(0.0));
+      } else if (l > j) {
+        if (kj) g[e] -= cb[b][i] * cb[b][l] * inv;
+        if (l == j + 1) cb[b ^ 1][i] = g[e];
+      }
+    }
+    if (tid == 0 && j > 0) keep[j - 1] = kprev;
+    kprev = kj;
+    __syncthreads();
+  }
+  if (tid == 0 && m > 0) keep[m - 1] = kprev;
+#pragma unroll
+  for (int e = 0; e < kRegCholE; ++e)
+    if (rc[e] >= 0) G[(size_t)(rc[e] >> 16) * m + (rc[e] & 0xffff)] = g[e];
+  __syncthreads();
+}
+
+// the faster factorisation where it fits (blocks of kThreads threads)
+template <class R>
+__device__ void small_cholesky(R* G, int m, int* keep, R drop_rel) {
+  if (m <= kRegCholMax)
+    reg_cholesky(G, m, keep, drop_rel);
+  else
+    block_cholesky(G, m, keep, drop_rel);
+}
+
 // ------------------------------------------------------------------ R(1.) tridiagonalise
 template <class R>
 __global__ void __launch_bounds__(kThreads)
@@ -214,7 +286,7 @@ __global__ void __launch_bounds__(kThreads)
     As[(size_t)j * n + i] = v;
   }
   __syncthreads();
-  block_cholesky(Lw, no, w.keep + o0, drop);
+  small_cholesky(Lw, no, w.keep + o0, drop);
   // A <- T^T A T: O rows by L^-1, then O columns.  A thread's forward
   // substitution reads only the entries of its own column (row) that it wrote
   // itself, so the whole substitution runs without barriers.
@@ -374,156 +446,172 @@ __device__ int sturm(const R* d, const R* e2, int n, R x) {
 
 // ------------------------------------------------------------------ 1b. cluster Householder
 // Householder tridiagonalisation of the transformed n x n matrix (w.As) by a
-// cluster of kCS thread blocks: row r lives in block r % kCS (distributed
-// shared memory), so the O(n^3) work is spread over kCS SMs.  Every block
-// holds column j of the current matrix and forms the same reflector v; each
-// block computes p = tau A v for its rows and publishes it with its share of
-// p^T v and its rows' entries of column j+1 (before the update); after one
-// cluster barrier every block gathers p, forms w = p - K v, updates its rows
-// and forms the updated column j+1 of all rows itself from the published
-// entries -- one cluster barrier per step.  The published buffers alternate
-// between steps, so no barrier guards their reuse.
+// cluster of kCS thread blocks: row r lives in the shared memory of block
+// r % kCS, so the O(n^3) work is spread over kCS SMs.  Every warp of every
+// block holds column j of the current matrix in registers (lane l, entries
+// l + 32 c), forms the reflector v itself (its norm by a warp reduction: the
+// same values everywhere) and
+//   * computes p = tau A v for its own rows, publishing them, its share of
+//     p^T v and its rows' entries of column j+1 (before the update);
+//   * after one cluster barrier gathers what its lanes need from the other
+//     blocks' shared memory: the shares of p^T v (K = tau p^T v / 2), the p
+//     of its lanes' columns (w = p - K v) and their entries of column j+1,
+//     corrected by the rank-2 update: the next step's column;
+//   * updates its own rows, A -= v w^T + w v^T (v and w vanish outside the
+//     trailing block, so the update needs no bounds).
+// One cluster barrier a step and no block barrier; the published buffers
+// alternate between steps, so no barrier guards their reuse.
 constexpr int kCS = 8;
 constexpr int kCT = 256;
+constexpr int kCW = kCT / 32;
 
-template <class R>
-__device__ R cl_block_sum(R v, R* red) {
-  const int lane = threadIdx.x & 31, wdx = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[wdx] = v;
-  __syncthreads();
-  R t = lane < (kCT / 32) ? red[lane] : R(0.0);
-  return warp_sum(t);
+// entry c of a lane's columns l = lane + 32 c, selected without dynamic
+// register indexing
+template <class R, int CL>
+__device__ __forceinline__ R lane_pick(const R (&a)[CL], int c) {
+  R x = R(0.0);
+#pragma unroll
+  for (int q = 0; q < CL; ++q)
+    if (q == c) x = a[q];
+  return x;
 }
 
 template <class R>
+__device__ __forceinline__ R shfl_r(R v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+template <>
+__device__ __forceinline__ dfloat shfl_r<dfloat>(dfloat v, int src) {
+  return dfloat(__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src));
+}
+
+// entry r of the vector held as a[c] at lane r % 32, c = r / 32, in every lane
+template <class R, int CL>
+__device__ __forceinline__ R vec_at(const R (&a)[CL], int r) {
+  return shfl_r(lane_pick<R, CL>(a, r >> 5), r & 31);
+}
+
+template <class R, int CL>
 __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     k_rr_house_cluster(int n, RRWork<R> w) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int kW = kCT / 32;
   const int rpc = (n + kCS - 1) / kCS;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  R* sm = reinterpret_cast<R*>(sm_raw);
-  R* Ar = sm;                      // rpc x n: row rank + kCS * li
-  R* vf = Ar + (size_t)rpc * n;    // n: column j, then v
-  R* wf = vf + n;                  // n: p, then w
-  R* cf = wf + n;                  // n: column j of the current matrix
-  R* pubc = cf + n;                // 2 x rpc: own rows' entries of the next column
-  R* pubp = pubc + 2 * rpc;        // 2 x rpc
-  R* pubs = pubp + 2 * rpc;        // 2
-  __shared__ R red[kW];
+  R* Ar = reinterpret_cast<R*>(sm_raw);  // rpc x n: row rank + kCS * li
+  R* pubc = Ar + (size_t)rpc * n;        // 2 x rpc: own rows' entries of column j+1
+  R* pubp = pubc + 2 * rpc;              // 2 x rpc: own rows' p
+  R* pubk = pubp + 2 * rpc;              // 2 x kCW: the warps' shares of p^T v
   for (int t = tid; t < rpc * n; t += kCT) {
     const int li = t / n, c = t % n, r = rank + kCS * li;
     Ar[t] = r < n ? w.As[(size_t)r * n + c] : R(0.0);
   }
+  R col[CL], v[CL], wv[CL];
+#pragma unroll
+  for (int c = 0; c < CL; ++c) {  // column 0 below the diagonal
+    const int l = lane + 32 * c;
+    col[c] = (l >= 1 && l < n) ? w.As[(size_t)l * n] : R(0.0);
+  }
   __syncthreads();
-  // own rows' entries of column c (rows >= c + 1) into pubc[b], then every
-  // block gathers the column into cf
-  auto publish_col = [&](int c, int b) {
-    for (int li = tid; li < rpc; li += kCT) {
-      const int r = rank + kCS * li;
-      pubc[b * rpc + li] = (r < n && r >= c + 1) ? Ar[(size_t)li * n + c] : R(0.0);
-    }
-  };
-  auto gather_col = [&](int c, int b) {
-    for (int r = c + 1 + tid; r < n; r += kCT) {
-      const R* rem = cl.map_shared_rank(pubc + b * rpc, r % kCS);
-      cf[r] = rem[r / kCS];
-    }
-  };
-  publish_col(0, 0);
-  cl.sync();
-  gather_col(0, 0);
-  __syncthreads();
+  cl.sync();  // every block of the cluster is running before the first remote access
   for (int j = 0; j + 2 < n; ++j) {
     const int buf = j & 1;
-    for (int r = j + 1 + tid; r < n; r += kCT) vf[r] = cf[r];
-    __syncthreads();
-    R part = R(0.0);
-    for (int r = j + 1 + tid; r < n; r += kCT) part += vf[r] * vf[r];
-    const R ss = cl_block_sum(part, red);
-    const R x0 = vf[j + 1];
+    R ss = R(0.0);
+#pragma unroll
+    for (int c = 0; c < CL; ++c) ss += col[c] * col[c];
+    ss = warp_sum(ss);
+    const R x0 = vec_at<R, CL>(col, j + 1);
     const R alpha = sqrt(ss);
-    const int own_j = (j % kCS) == rank;
-    if (!(alpha > Prec<R>::tiny)) {  // nothing to reflect: the next column as it stands
-      if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
-      if (rank == 0 && tid == 0) {
-        w.tau[j] = R(0.0);
-        w.e[j] = x0;
-      }
-      publish_col(j + 1, buf ^ 1);
-      cl.sync();
-      gather_col(j + 1, buf ^ 1);
-      __syncthreads();
-      continue;
-    }
+    const bool refl = alpha > Prec<R>::tiny;
     const R beta = x0 >= R(0.0) ? -alpha : alpha;
-    const R tj = (beta - x0) / beta;
-    const R scale = R(1.0) / (x0 - beta);
-    __syncthreads();
-    for (int r = j + 1 + tid; r < n; r += kCT) {
-      const R v = r == j + 1 ? R(1.0) : vf[r] * scale;
-      vf[r] = v;
-      if (rank == 0) w.ref[(size_t)j * n + r] = v;
+    const R tj = refl ? (beta - x0) / beta : R(0.0);
+    const R scale = refl ? R(1.0) / (x0 - beta) : R(0.0);
+#pragma unroll
+    for (int c = 0; c < CL; ++c) {
+      const int l = lane + 32 * c;
+      v[c] = !refl ? R(0.0) : (l == j + 1 ? R(1.0) : col[c] * scale);
     }
-    if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
-    if (rank == 0 && tid == 0) {
-      w.tau[j] = tj;
-      w.e[j] = beta;
+    if (rank == 0 && wid == 0) {
+#pragma unroll
+      for (int c = 0; c < CL; ++c) {
+        const int l = lane + 32 * c;
+        if (l > j && l < n) w.ref[(size_t)j * n + l] = v[c];
+      }
+      if (lane == 0) {
+        w.tau[j] = tj;
+        w.e[j] = refl ? beta : x0;
+      }
     }
-    __syncthreads();
-    // p = tau A v for own rows r >= j+1, this block's share of p^T v, and the
+    // the diagonal entry, by the warp that updates row j
+    if ((j % kCS) == rank && wid == (j / kCS) % kCW && lane == 0)
+      w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
+    // p = tau A v for own rows r >= j+1, the warp's share of p^T v, and the
     // own rows' entries of column j+1 before the update
     R kp = R(0.0);
-    for (int li = wid; li < rpc; li += kW) {
+    for (int li = wid; li < rpc; li += kCW) {
       const int r = rank + kCS * li;
+      const R* row = Ar + (size_t)li * n;
+      const bool live = r < n && r >= j + 1;
       R acc = R(0.0);
-      if (r < n && r >= j + 1) {
-        const R* row = Ar + (size_t)li * n;
-        for (int l = j + 1 + lane; l < n; l += 32) acc += row[l] * vf[l];
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < CL; ++c) {
+          const int l = lane + 32 * c;
+          if (l < n) acc += row[l] * v[c];
+        }
       }
       acc = warp_sum(acc) * tj;
+      const R vr = live ? vec_at<R, CL>(v, r) : R(0.0);
+      kp += acc * vr;
       if (lane == 0) {
-        pubp[buf * rpc + li] = (r < n && r >= j + 1) ? acc : R(0.0);
-        if (r < n && r >= j + 1) kp += acc * vf[r];
+        pubp[buf * rpc + li] = live ? acc : R(0.0);
+        pubc[buf * rpc + li] = (r < n && r >= j + 2) ? row[j + 1] : R(0.0);
       }
     }
-    publish_col(j + 1, buf ^ 1);
-    const R kpb = cl_block_sum(kp, red);
-    if (tid == 0) pubs[buf] = kpb;
+    if (lane == 0) pubk[buf * kCW + wid] = kp;
     cl.sync();
-    R kq[kCS];  // the blocks' shares, loaded together (remote loads in flight at once)
+    // K from the kCS x kCW shares (two per lane)
+    R kq = R(0.0);
+    for (int q = lane; q < kCS * kCW; q += 32)
+      kq += cl.map_shared_rank(pubk, q / kCW)[buf * kCW + q % kCW];
+    const R K = R(0.5) * tj * warp_sum(kq);
+    // w and the next column for the lane's columns
 #pragma unroll
-    for (int q = 0; q < kCS; ++q) kq[q] = cl.map_shared_rank(pubs, q)[buf];
-    R K = R(0.0);
+    for (int c = 0; c < CL; ++c) {
+      const int l = lane + 32 * c;
+      R pl = R(0.0), cl_ = R(0.0);
+      if (l > j && l < n) {
+        const int owner = l % kCS, ol = l / kCS;
+        pl = cl.map_shared_rank(pubp, owner)[buf * rpc + ol];
+        cl_ = cl.map_shared_rank(pubc, owner)[buf * rpc + ol];
+      }
+      wv[c] = (l > j && l < n) ? pl - K * v[c] : R(0.0);
+      col[c] = cl_;
+    }
+    const R vn = refl ? R(1.0) : R(0.0);  // v_{j+1}
+    const R wn = vec_at<R, CL>(wv, j + 1);
 #pragma unroll
-    for (int q = 0; q < kCS; ++q) K += kq[q];
-    K *= R(0.5) * tj;
-    for (int r = j + 1 + tid; r < n; r += kCT) {
-      const R* rem = cl.map_shared_rank(pubp + buf * rpc, r % kCS);
-      wf[r] = rem[r / kCS] - K * vf[r];
+    for (int c = 0; c < CL; ++c) {
+      const int l = lane + 32 * c;
+      if (l >= j + 2 && l < n) col[c] -= v[c] * wn + wv[c] * vn;
     }
-    __syncthreads();
-    // the updated column j+1 of every row: a_r,j+1 - v_r w_j+1 - w_r v_j+1
-    const R vn = vf[j + 1], wn = wf[j + 1];
-    for (int r = j + 2 + tid; r < n; r += kCT) {
-      const R* rem = cl.map_shared_rank(pubc + (buf ^ 1) * rpc, r % kCS);
-      cf[r] = rem[r / kCS] - (vf[r] * wn + wf[r] * vn);
-    }
-    for (int li = wid; li < rpc; li += kW) {  // A_own -= v w^T + w v^T
+    // A_own -= v w^T + w v^T (rows r >= j+1)
+    for (int li = wid; li < rpc; li += kCW) {
       const int r = rank + kCS * li;
       if (r >= n || r < j + 1) continue;
       R* row = Ar + (size_t)li * n;
-      const R vr = vf[r], wr = wf[r];
-      for (int l = j + 1 + lane; l < n; l += 32) row[l] -= vr * wf[l] + wr * vf[l];
+      const R vr = vec_at<R, CL>(v, r), wr = vec_at<R, CL>(wv, r);
+#pragma unroll
+      for (int c = 0; c < CL; ++c) {
+        const int l = lane + 32 * c;
+        if (l < n) row[l] -= vr * wv[c] + wr * v[c];
+      }
     }
-    __syncthreads();
   }
   // the last 2 x 2 block
+  __syncthreads();
   if (tid == 0) {
     for (int r = (n >= 2 ? n - 2 : 0); r < n; ++r) {
       if (r % kCS != rank) continue;
@@ -538,7 +626,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     }
   }
   __threadfence();
-  cl.sync();
+  cl.sync();  // also: no block leaves while another may still read its buffers
   if (rank == 0)
     for (int i = tid; i < n; i += kCT) w.e2[i] = w.e[i] * w.e[i];
 }
@@ -811,7 +899,7 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
     }
     for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
-    block_cholesky(G, nb, keep_nb, R(0.0));
+    small_cholesky(G, nb, keep_nb, R(0.0));
     for (int i = threadIdx.x; i < n; i += kThreads) {
       R* v = V + (size_t)i * nb;
       for (int s2 = 0; s2 < nb; ++s2) {
@@ -906,7 +994,7 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     R gref = R(0.0);
     for (int s2 = 0; s2 < nb; ++s2) gref = fmax(gref, G[s2 * nb + s2]);
-    block_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
+    small_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
     for (int i = tid; i < n; i += kThreads) {  // Z <- Z L^-T, dropped columns zero
       const R* zt = T1 + (size_t)i * nb;
       R* zr = Z + (size_t)i * nb;
@@ -1074,15 +1162,17 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.U = p; p += n * no;
   w.keep = reinterpret_cast<int*>(p);
   for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
-                         (const void*)k_rr_house_cluster<R>, (const void*)k_rr_invit_sm<R>,
+                         (const void*)k_rr_house_cluster<R, 4>,
+                         (const void*)k_rr_house_cluster<R, 8>,
+                         (const void*)k_rr_house_cluster<R, 16>, (const void*)k_rr_invit_sm<R>,
                          (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
   const size_t tri_bytes = sizeof(R) * n * n;
   const size_t tri2_bytes = sizeof(R) * (n * n + 2 * n * no + no * no);
   const int tri_smem = tri2_bytes <= kMaxDynSmem ? 2 : tri_bytes <= kMaxDynSmem ? 1 : 0;
   const size_t rpc = (n + kCS - 1) / kCS;
-  const size_t cl_bytes = sizeof(R) * (rpc * n + 3 * n + 4 * rpc + 2);
-  const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
+  const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * rpc + 2 * kCW);
+  const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3 && n <= 512;
   const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
   // transform (one block); Householder by the cluster when its rows fit
   (k_rr_tridiag<R><<<1, kThreads, tri_smem == 2 ? tri2_bytes : tri_smem ? tri_bytes : 0, st>>>(
@@ -1090,7 +1180,12 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
-    (k_rr_house_cluster<R><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
+    if (n <= 128)
+      (k_rr_house_cluster<R, 4><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
+    else if (n <= 256)
+      (k_rr_house_cluster<R, 8><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
+    else
+      (k_rr_house_cluster<R, 16><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
   (k_rr_eigvals_mc<R><<<(unsigned)nb, 32 * kEW, (sizeof(R) + sizeof(float)) * 2 * n, st>>>(
