@@ -39,6 +39,7 @@
 // the FP64 residual bar runs it in FP64 or double-float.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
 #include <type_traits>
 
 #include "linalg.cuh"
@@ -130,76 +131,103 @@ __device__ void block_cholesky(R* G, int m, int* keep, R drop_rel) {
   }
 }
 
-// The same factorisation with the lower triangle in registers, for m up to
-// kRegCholMax: entry q = tid + kThreads e of the packed lower triangle (rows
-// ascending) lives in thread tid.  Before step j the owners of column j have
-// published it in shared memory (two buffers, alternating), and every thread
-// takes the step's pivot decision itself from the published diagonal, so a
-// step costs one barrier.  The trailing entries lose g_ij g_lj / g_jj (the
-// unscaled column); the owners of column j scale it as they pass it.  keep[j]
-// is written one step late, when nobody reads it any more.
-constexpr int kRegCholE = 9;
-constexpr int kRegCholMax = 135;  // m (m + 1) / 2 <= kRegCholE * kThreads
 template <class R>
-__device__ void reg_cholesky(R* G, int m, int* keep, R drop_rel) {
-  __shared__ R cb[2][kRegCholMax];
-  const int tid = threadIdx.x;
-  const int tot = m * (m + 1) / 2;
-  R g[kRegCholE];
-  int rc[kRegCholE];  // row << 16 | column, or -1
-#pragma unroll
-  for (int e = 0; e < kRegCholE; ++e) {
-    const int q = tid + kThreads * e;
-    rc[e] = -1;
-    g[e] = R(0.0);
-    if (q < tot) {
-      int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
-      while (i * (i + 1) / 2 > q) --i;
-      while ((i + 1) * (i + 2) / 2 <= q) ++i;
-      const int l = q - i * (i + 1) / 2;
-      rc[e] = (i << 16) | l;
-      g[e] = G[(size_t)i * m + l];
-      if (l == 0) cb[0][i] = g[e];
-    }
-  }
-  __syncthreads();
-  int kprev = 0;
-  for (int j = 0; j < m; ++j) {
-    const int b = j & 1;
-    const R piv = cb[b][j];
-    const int kj = keep[j] && piv > drop_rel;
-    const R ljj = kj ? sqrt(piv) : R(1.0);
-    const R inv = kj ? R(1.0) / piv : R(0.0);
-    const R rl = R(1.0) / ljj;
-#pragma unroll
-    for (int e = 0; e < kRegCholE; ++e) {
-      if (rc[e] < 0) continue;
-      const int i = rc[e] >> 16, l = rc[e] & 0xffff;
-      if (l == j) {
-        g[e] = i == j ? ljj : (kj ? g[e] * rl : R(0.0));
-      } else if (l > j) {
-        if (kj) g[e] -= cb[b][i] * cb[b][l] * inv;
-        if (l == j + 1) cb[b ^ 1][i] = g[e];
-      }
-    }
-    if (tid == 0 && j > 0) keep[j - 1] = kprev;
-    kprev = kj;
-    __syncthreads();
-  }
-  if (tid == 0 && m > 0) keep[m - 1] = kprev;
-#pragma unroll
-  for (int e = 0; e < kRegCholE; ++e)
-    if (rc[e] >= 0) G[(size_t)(rc[e] >> 16) * m + (rc[e] & 0xffff)] = g[e];
-  __syncthreads();
+__device__ __forceinline__ R shfl_xor_r(R v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+template <>
+__device__ __forceinline__ dfloat shfl_xor_r<dfloat>(dfloat v, int o) {
+  return dfloat(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o));
 }
 
-// the faster factorisation where it fits (blocks of kThreads threads)
+// The warp sums of 16 values at once by halving exchanges (16 shuffles
+// instead of 80): lanes 2q and 2q + 1 end with the sum of v[q].
 template <class R>
-__device__ void small_cholesky(R* G, int m, int* keep, R drop_rel) {
-  if (m <= kRegCholMax)
-    reg_cholesky(G, m, keep, drop_rel);
-  else
-    block_cholesky(G, m, keep, drop_rel);
+__device__ __forceinline__ R sum16(R (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+  R a8[8], a4[4], a2[2];
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    a8[k] = (h4 ? v[k + 8] : v[k]) + shfl_xor_r(h4 ? v[k] : v[k + 8], 16);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    a4[k] = (h3 ? a8[k + 4] : a8[k]) + shfl_xor_r(h3 ? a8[k] : a8[k + 4], 8);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    a2[k] = (h2 ? a4[k + 2] : a4[k]) + shfl_xor_r(h2 ? a4[k] : a4[k + 2], 4);
+  R a1 = (h1 ? a2[1] : a2[0]) + shfl_xor_r(h1 ? a2[0] : a2[1], 2);
+  return a1 + shfl_xor_r(a1, 1);
+}
+
+// C = X^T Y over `rows` rows (X: rows x ma, Y: rows x mb, row-major with row
+// strides ldx, ldy), only the entries b <= a when `lower`; C row-major with
+// row stride ldc.  Each warp takes 4 x 4 tiles of C in turn, its lanes
+// splitting the rows, and reduces the tile with sum16.
+template <class R>
+__device__ void blk_gram_tn(const R* X, int ldx, const R* Y, int ldy, int rows, int ma, int mb,
+                            R* C, int ldc, bool lower) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ta = (ma + 3) >> 2, tb = (mb + 3) >> 2;
+  for (int t = wid; t < ta * tb; t += kWarps) {
+    const int ia = t / tb, ib = t - ia * tb;
+    if (lower && ib > ia) continue;
+    R acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = R(0.0);
+    for (int i = lane; i < rows; i += 32) {
+      R xa[4], yb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        xa[r] = 4 * ia + r < ma ? X[(size_t)i * ldx + 4 * ia + r] : R(0.0);
+        yb[r] = 4 * ib + r < mb ? Y[(size_t)i * ldy + 4 * ib + r] : R(0.0);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[4 * r + c] += xa[r] * yb[c];
+    }
+    const R s = sum16(acc);
+    const int q = lane >> 1, a = 4 * ia + (q >> 2), b = 4 * ib + (q & 3);
+    if (!(lane & 1) && a < ma && b < mb && (!lower || b <= a)) C[(size_t)a * ldc + b] = s;
+  }
+}
+
+// C[i][b] = base[i][b] (rows i >= r0; zero above) + sgn sum_a X[i][a] G[a][b]
+// for i < rows, b < mb, a < ma (row strides ldx, ldg, ldc; base shares C's
+// layout; sgn -1 by default), one 4 x 4 tile of C per thread at a time.
+template <class R>
+__device__ void blk_sub_xg(const R* X, int ldx, const R* G, int ldg, int rows, int ma, int mb,
+                           const R* base, int r0, R* C, int ldc, R sgn = R(-1.0)) {
+  const int ta = (rows + 3) >> 2, tb = (mb + 3) >> 2;
+  for (int t = threadIdx.x; t < ta * tb; t += kThreads) {
+    const int ia = t / tb, ib = t - ia * tb;
+    R acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
+    for (int a = 0; a < ma; ++a) {
+      R xr[4], gc[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        xr[r] = 4 * ia + r < rows ? X[(size_t)(4 * ia + r) * ldx + a] : R(0.0);
+        gc[r] = 4 * ib + r < mb ? G[(size_t)a * ldg + 4 * ib + r] : R(0.0);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += xr[r] * gc[c];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = 4 * ia + r, b = 4 * ib + c;
+        if (i < rows && b < mb)
+          C[(size_t)i * ldc + b] = (i >= r0 ? base[(size_t)i * ldc + b] : R(0.0)) + sgn * acc[r][c];
+      }
+  }
 }
 
 // ------------------------------------------------------------------ R(1.) tridiagonalise
@@ -235,77 +263,91 @@ __global__ void __launch_bounds__(kThreads)
     w.dsc[i] = s;
   }
   __syncthreads();
-  for (size_t t = tid; t < nn; t += kThreads) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    As[t] = R(0.5) * ((R)A[t] + (R)A[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j];
-  }
+  // the scaled matrix (rows by warps, columns by lanes), then its symmetric part
+  for (int i = wid; i < n; i += kWarps)
+    for (int j = lane; j < n; j += 32)
+      As[(size_t)i * n + j] = (R)A[(size_t)i * n + j] * w.dsc[i] * w.dsc[j];
+  __syncthreads();
+  for (int i = wid; i < n; i += kWarps)
+    for (int j = lane; j < i; j += 32) {
+      const R v = R(0.5) * (As[(size_t)i * n + j] + As[(size_t)j * n + i]);
+      As[(size_t)i * n + j] = v;
+      As[(size_t)j * n + i] = v;
+    }
   // Second projection of the O block against the rest, in coefficient space.
   // The O columns arrive M-projected against the others once, on the
   // N-vectors; once they are mostly made of the other columns (a converging
   // block) that projection leaves a coupling of order eps / |remainder|.  With
   // C = B_{rest,O} (scaled) and T = [I, -C; 0, I], A <- T^T A T and
   // B_OO <- B_OO - C^T C take it out ("twice is enough"); the rest-rest block
-  // of B is the identity to rounding.
+  // of B is the identity to rounding.  C's rows in O are zero, so the sums
+  // over the rest run over all rows.
   const int o1 = o0 + no;
-  for (int t = tid; t < n * no; t += kThreads) {
-    const int i = t / no, j = o0 + t % no;
-    const bool in_o = i >= o0 && i < o1;
-    Cw[t] = (!in_o && w.keep[i] && w.keep[j])
-                 ? R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j]
-                 : R(0.0);
-  }
-  __syncthreads();
-  for (int t = tid; t < n * no; t += kThreads) {  // U = A_{rest,rest} C
-    const int i = t / no, a = t % no;
-    R acc = R(0.0);
-    if (i < o0 || i >= o1)
-      for (int r = 0; r < n; ++r)
-        if (r < o0 || r >= o1) acc += As[(size_t)i * n + r] * Cw[r * no + a];
-    Uw[t] = acc;
-  }
-  __syncthreads();
-  for (int t = tid; t < no * no; t += kThreads) {
-    const int a = t / no, b = t % no, i = o0 + a, j = o0 + b;
-    R cc = R(0.0), acc = As[(size_t)i * n + j];
-    for (int r = 0; r < n; ++r) {
-      if (r >= o0 && r < o1) continue;
-      const R ca = Cw[r * no + a], cb = Cw[r * no + b];
-      cc += ca * cb;
-      acc += ca * Uw[r * no + b] - ca * As[(size_t)r * n + j] - As[(size_t)i * n + r] * cb;
+  for (int i = wid; i < n; i += kWarps)
+    for (int b = lane; b < no; b += 32) {
+      const int j = o0 + b;
+      const bool in_o = i >= o0 && i < o1;
+      Cw[(size_t)i * no + b] =
+          (!in_o && w.keep[i] && w.keep[j])
+              ? R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j]
+              : R(0.0);
     }
-    const R v = R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j] - cc;
-    Lw[t] = (w.keep[i] && w.keep[j]) ? v : (a == b ? R(1.0) : R(0.0));
-    As[(size_t)i * n + j] = acc;
-  }
   __syncthreads();
-  for (int t = tid; t < n * no; t += kThreads) {
-    const int i = t / no, j = o0 + t % no;
+  R* P2 = w.G;  // no x no scratch (global): C^T A_{.,O}, then C^T C
+  blk_sub_xg(As, n, Cw, no, n, n, no, Cw, n, Uw, no, R(1.0));  // U = A C
+  blk_gram_tn(Cw, no, As + o0, n, n, no, no, P2, no, false);   // C^T A_{.,O}
+  __syncthreads();
+  blk_gram_tn(Cw, no, Uw, no, n, no, no, Lw, no, false);       // C^T U (in L for now)
+  __syncthreads();
+  for (int a = wid; a < no; a += kWarps)  // A_OO += C^T U - C^T A_{.,O} - (C^T A_{.,O})^T
+    for (int b = lane; b < no; b += 32)
+      As[(size_t)(o0 + a) * n + o0 + b] +=
+          Lw[(size_t)a * no + b] - P2[(size_t)a * no + b] - P2[(size_t)b * no + a];
+  __syncthreads();
+  blk_gram_tn(Cw, no, Cw, no, n, no, no, P2, no, false);  // C^T C
+  __syncthreads();
+  for (int a = wid; a < no; a += kWarps)
+    for (int b = lane; b < no; b += 32) {
+      const int i = o0 + a, j = o0 + b;
+      const R v = R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] *
+                      w.dsc[j] -
+                  P2[(size_t)a * no + b];
+      Lw[(size_t)a * no + b] = (w.keep[i] && w.keep[j]) ? v : (a == b ? R(1.0) : R(0.0));
+    }
+
+  __syncthreads();
+  for (int i = wid; i < n; i += kWarps) {  // A_{rest,O} -= U (and its mirror)
     if (i >= o0 && i < o1) continue;
-    const R v = As[(size_t)i * n + j] - Uw[t];
-    As[(size_t)i * n + j] = v;
-    As[(size_t)j * n + i] = v;
+    for (int b = lane; b < no; b += 32) {
+      const int j = o0 + b;
+      const R v = As[(size_t)i * n + j] - Uw[(size_t)i * no + b];
+      As[(size_t)i * n + j] = v;
+      As[(size_t)j * n + i] = v;
+    }
   }
   __syncthreads();
-  small_cholesky(Lw, no, w.keep + o0, drop);
+  block_cholesky(Lw, no, w.keep + o0, drop);
   // A <- T^T A T: O rows by L^-1, then O columns.  A thread's forward
   // substitution reads only the entries of its own column (row) that it wrote
   // itself, so the whole substitution runs without barriers.
-  for (int c = tid; c < n; c += kThreads)
-    for (int a = 0; a < no; ++a) {
-      const int i = o0 + a;
-      R acc = As[(size_t)i * n + c];
-      for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)(o0 + b) * n + c];
-      As[(size_t)i * n + c] = acc / Lw[a * no + a];
-    }
-  __syncthreads();
-  for (int r = tid; r < n; r += kThreads)
-    for (int a = 0; a < no; ++a) {
-      const int i = o0 + a;
-      R acc = As[(size_t)r * n + i];
-      for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)r * n + o0 + b];
-      As[(size_t)r * n + i] = acc / Lw[a * no + a];
-    }
-  __syncthreads();
+  {
+    for (int c = tid; c < n; c += kThreads)
+      for (int a = 0; a < no; ++a) {
+        const int i = o0 + a;
+        R acc = As[(size_t)i * n + c];
+        for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)(o0 + b) * n + c];
+        As[(size_t)i * n + c] = acc / Lw[a * no + a];
+      }
+    __syncthreads();
+    for (int r = tid; r < n; r += kThreads)
+      for (int a = 0; a < no; ++a) {
+        const int i = o0 + a;
+        R acc = As[(size_t)r * n + i];
+        for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)r * n + o0 + b];
+        As[(size_t)r * n + i] = acc / Lw[a * no + a];
+      }
+    __syncthreads();
+  }
   // symmetrise; dropped columns are decoupled with a diagonal just above the
   // spectrum of the kept part (2 ||A_kept||_inf + 1), which keeps them out of
   // the nb lowest without disturbing the scale of the tridiagonal problem
@@ -328,16 +370,19 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
   }
   const R big = R(2.0) * rmax + R(1.0);
-  for (size_t t = tid; t < nn; t += kThreads) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    if (!w.keep[i] || !w.keep[j]) As[t] = (i == j) ? big : R(0.0);
-    else if (i > j) As[t] = R(0.5) * (As[t] + As[(size_t)j * n + i]);
-  }
+  for (int i = wid; i < n; i += kWarps)
+    for (int j = lane; j <= i; j += 32) {
+      R v;
+      if (!w.keep[i] || !w.keep[j])
+        v = (i == j) ? big : R(0.0);
+      else
+        v = i > j ? R(0.5) * (As[(size_t)i * n + j] + As[(size_t)j * n + i]) : As[(size_t)i * n + j];
+      As[(size_t)i * n + j] = v;
+    }
   __syncthreads();
-  for (size_t t = tid; t < nn; t += kThreads) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    if (i < j) As[t] = As[(size_t)j * n + i];
-  }
+  for (int i = wid; i < n; i += kWarps)
+    for (int j = lane; j < n; j += 32)
+      if (i < j) As[(size_t)i * n + j] = As[(size_t)j * n + i];
   __syncthreads();
   if (smem == 2) {  // L and C are read by the later kernels
     for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
@@ -446,172 +491,156 @@ __device__ int sturm(const R* d, const R* e2, int n, R x) {
 
 // ------------------------------------------------------------------ 1b. cluster Householder
 // Householder tridiagonalisation of the transformed n x n matrix (w.As) by a
-// cluster of kCS thread blocks: row r lives in the shared memory of block
-// r % kCS, so the O(n^3) work is spread over kCS SMs.  Every warp of every
-// block holds column j of the current matrix in registers (lane l, entries
-// l + 32 c), forms the reflector v itself (its norm by a warp reduction: the
-// same values everywhere) and
-//   * computes p = tau A v for its own rows, publishing them, its share of
-//     p^T v and its rows' entries of column j+1 (before the update);
-//   * after one cluster barrier gathers what its lanes need from the other
-//     blocks' shared memory: the shares of p^T v (K = tau p^T v / 2), the p
-//     of its lanes' columns (w = p - K v) and their entries of column j+1,
-//     corrected by the rank-2 update: the next step's column;
-//   * updates its own rows, A -= v w^T + w v^T (v and w vanish outside the
-//     trailing block, so the update needs no bounds).
-// One cluster barrier a step and no block barrier; the published buffers
-// alternate between steps, so no barrier guards their reuse.
+// cluster of kCS thread blocks: row r lives in block r % kCS (distributed
+// shared memory), so the O(n^3) work is spread over kCS SMs.  Every block
+// holds column j of the current matrix and forms the same reflector v; each
+// block computes p = tau A v for its rows and publishes it with its share of
+// p^T v and its rows' entries of column j+1 (before the update); after one
+// cluster barrier every block gathers p, forms w = p - K v, updates its rows
+// and forms the updated column j+1 of all rows itself from the published
+// entries -- one cluster barrier per step.  The published buffers alternate
+// between steps, so no barrier guards their reuse.
 constexpr int kCS = 8;
 constexpr int kCT = 256;
-constexpr int kCW = kCT / 32;
 
-// entry c of a lane's columns l = lane + 32 c, selected without dynamic
-// register indexing
-template <class R, int CL>
-__device__ __forceinline__ R lane_pick(const R (&a)[CL], int c) {
-  R x = R(0.0);
-#pragma unroll
-  for (int q = 0; q < CL; ++q)
-    if (q == c) x = a[q];
-  return x;
+template <class R>
+__device__ R cl_block_sum(R v, R* red) {
+  const int lane = threadIdx.x & 31, wdx = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wdx] = v;
+  __syncthreads();
+  R t = lane < (kCT / 32) ? red[lane] : R(0.0);
+  return warp_sum(t);
 }
 
 template <class R>
-__device__ __forceinline__ R shfl_r(R v, int src) {
-  return __shfl_sync(0xffffffffu, v, src);
-}
-template <>
-__device__ __forceinline__ dfloat shfl_r<dfloat>(dfloat v, int src) {
-  return dfloat(__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src));
-}
-
-// entry r of the vector held as a[c] at lane r % 32, c = r / 32, in every lane
-template <class R, int CL>
-__device__ __forceinline__ R vec_at(const R (&a)[CL], int r) {
-  return shfl_r(lane_pick<R, CL>(a, r >> 5), r & 31);
-}
-
-template <class R, int CL>
 __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     k_rr_house_cluster(int n, RRWork<R> w) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int kW = kCT / 32;
   const int rpc = (n + kCS - 1) / kCS;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  R* Ar = reinterpret_cast<R*>(sm_raw);  // rpc x n: row rank + kCS * li
-  R* pubc = Ar + (size_t)rpc * n;        // 2 x rpc: own rows' entries of column j+1
-  R* pubp = pubc + 2 * rpc;              // 2 x rpc: own rows' p
-  R* pubk = pubp + 2 * rpc;              // 2 x kCW: the warps' shares of p^T v
+  R* sm = reinterpret_cast<R*>(sm_raw);
+  R* Ar = sm;                      // rpc x n: row rank + kCS * li
+  R* vf = Ar + (size_t)rpc * n;    // n: column j, then v
+  R* wf = vf + n;                  // n: p, then w
+  R* cf = wf + n;                  // n: column j of the current matrix
+  R* pubc = cf + n;                // 2 x rpc: own rows' entries of the next column
+  R* pubp = pubc + 2 * rpc;        // 2 x rpc
+  R* pubs = pubp + 2 * rpc;        // 2
+  __shared__ R red[kW];
   for (int t = tid; t < rpc * n; t += kCT) {
     const int li = t / n, c = t % n, r = rank + kCS * li;
     Ar[t] = r < n ? w.As[(size_t)r * n + c] : R(0.0);
   }
-  R col[CL], v[CL], wv[CL];
-#pragma unroll
-  for (int c = 0; c < CL; ++c) {  // column 0 below the diagonal
-    const int l = lane + 32 * c;
-    col[c] = (l >= 1 && l < n) ? w.As[(size_t)l * n] : R(0.0);
-  }
   __syncthreads();
-  cl.sync();  // every block of the cluster is running before the first remote access
+  // own rows' entries of column c (rows >= c + 1) into pubc[b], then every
+  // block gathers the column into cf
+  auto publish_col = [&](int c, int b) {
+    for (int li = tid; li < rpc; li += kCT) {
+      const int r = rank + kCS * li;
+      pubc[b * rpc + li] = (r < n && r >= c + 1) ? Ar[(size_t)li * n + c] : R(0.0);
+    }
+  };
+  auto gather_col = [&](int c, int b) {
+    for (int r = c + 1 + tid; r < n; r += kCT) {
+      const R* rem = cl.map_shared_rank(pubc + b * rpc, r % kCS);
+      cf[r] = rem[r / kCS];
+    }
+  };
+  publish_col(0, 0);
+  cl.sync();
+  gather_col(0, 0);
+  __syncthreads();
   for (int j = 0; j + 2 < n; ++j) {
     const int buf = j & 1;
-    R ss = R(0.0);
-#pragma unroll
-    for (int c = 0; c < CL; ++c) ss += col[c] * col[c];
-    ss = warp_sum(ss);
-    const R x0 = vec_at<R, CL>(col, j + 1);
+    for (int r = j + 1 + tid; r < n; r += kCT) vf[r] = cf[r];
+    __syncthreads();
+    R part = R(0.0);
+    for (int r = j + 1 + tid; r < n; r += kCT) part += vf[r] * vf[r];
+    const R ss = cl_block_sum(part, red);
+    const R x0 = vf[j + 1];
     const R alpha = sqrt(ss);
-    const bool refl = alpha > Prec<R>::tiny;
+    const int own_j = (j % kCS) == rank;
+    if (!(alpha > Prec<R>::tiny)) {  // nothing to reflect: the next column as it stands
+      if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
+      if (rank == 0 && tid == 0) {
+        w.tau[j] = R(0.0);
+        w.e[j] = x0;
+      }
+      publish_col(j + 1, buf ^ 1);
+      cl.sync();
+      gather_col(j + 1, buf ^ 1);
+      __syncthreads();
+      continue;
+    }
     const R beta = x0 >= R(0.0) ? -alpha : alpha;
-    const R tj = refl ? (beta - x0) / beta : R(0.0);
-    const R scale = refl ? R(1.0) / (x0 - beta) : R(0.0);
-#pragma unroll
-    for (int c = 0; c < CL; ++c) {
-      const int l = lane + 32 * c;
-      v[c] = !refl ? R(0.0) : (l == j + 1 ? R(1.0) : col[c] * scale);
+    const R tj = (beta - x0) / beta;
+    const R scale = R(1.0) / (x0 - beta);
+    __syncthreads();
+    for (int r = j + 1 + tid; r < n; r += kCT) {
+      const R v = r == j + 1 ? R(1.0) : vf[r] * scale;
+      vf[r] = v;
+      if (rank == 0) w.ref[(size_t)j * n + r] = v;
     }
-    if (rank == 0 && wid == 0) {
-#pragma unroll
-      for (int c = 0; c < CL; ++c) {
-        const int l = lane + 32 * c;
-        if (l > j && l < n) w.ref[(size_t)j * n + l] = v[c];
-      }
-      if (lane == 0) {
-        w.tau[j] = tj;
-        w.e[j] = refl ? beta : x0;
-      }
+    if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
+    if (rank == 0 && tid == 0) {
+      w.tau[j] = tj;
+      w.e[j] = beta;
     }
-    // the diagonal entry, by the warp that updates row j
-    if ((j % kCS) == rank && wid == (j / kCS) % kCW && lane == 0)
-      w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
-    // p = tau A v for own rows r >= j+1, the warp's share of p^T v, and the
+    __syncthreads();
+    // p = tau A v for own rows r >= j+1, this block's share of p^T v, and the
     // own rows' entries of column j+1 before the update
     R kp = R(0.0);
-    for (int li = wid; li < rpc; li += kCW) {
+    for (int li = wid; li < rpc; li += kW) {
       const int r = rank + kCS * li;
-      const R* row = Ar + (size_t)li * n;
-      const bool live = r < n && r >= j + 1;
       R acc = R(0.0);
-      if (live) {
-#pragma unroll
-        for (int c = 0; c < CL; ++c) {
-          const int l = lane + 32 * c;
-          if (l < n) acc += row[l] * v[c];
-        }
+      if (r < n && r >= j + 1) {
+        const R* row = Ar + (size_t)li * n;
+        for (int l = j + 1 + lane; l < n; l += 32) acc += row[l] * vf[l];
       }
       acc = warp_sum(acc) * tj;
-      const R vr = live ? vec_at<R, CL>(v, r) : R(0.0);
-      kp += acc * vr;
       if (lane == 0) {
-        pubp[buf * rpc + li] = live ? acc : R(0.0);
-        pubc[buf * rpc + li] = (r < n && r >= j + 2) ? row[j + 1] : R(0.0);
+        pubp[buf * rpc + li] = (r < n && r >= j + 1) ? acc : R(0.0);
+        if (r < n && r >= j + 1) kp += acc * vf[r];
       }
     }
-    if (lane == 0) pubk[buf * kCW + wid] = kp;
+    publish_col(j + 1, buf ^ 1);
+    const R kpb = cl_block_sum(kp, red);
+    if (tid == 0) pubs[buf] = kpb;
     cl.sync();
-    // K from the kCS x kCW shares (two per lane)
-    R kq = R(0.0);
-    for (int q = lane; q < kCS * kCW; q += 32)
-      kq += cl.map_shared_rank(pubk, q / kCW)[buf * kCW + q % kCW];
-    const R K = R(0.5) * tj * warp_sum(kq);
-    // w and the next column for the lane's columns
+    R kq[kCS];  // the blocks' shares, loaded together (remote loads in flight at once)
 #pragma unroll
-    for (int c = 0; c < CL; ++c) {
-      const int l = lane + 32 * c;
-      R pl = R(0.0), cl_ = R(0.0);
-      if (l > j && l < n) {
-        const int owner = l % kCS, ol = l / kCS;
-        pl = cl.map_shared_rank(pubp, owner)[buf * rpc + ol];
-        cl_ = cl.map_shared_rank(pubc, owner)[buf * rpc + ol];
-      }
-      wv[c] = (l > j && l < n) ? pl - K * v[c] : R(0.0);
-      col[c] = cl_;
-    }
-    const R vn = refl ? R(1.0) : R(0.0);  // v_{j+1}
-    const R wn = vec_at<R, CL>(wv, j + 1);
+    for (int q = 0; q < kCS; ++q) kq[q] = cl.map_shared_rank(pubs, q)[buf];
+    R K = R(0.0);
 #pragma unroll
-    for (int c = 0; c < CL; ++c) {
-      const int l = lane + 32 * c;
-      if (l >= j + 2 && l < n) col[c] -= v[c] * wn + wv[c] * vn;
+    for (int q = 0; q < kCS; ++q) K += kq[q];
+    K *= R(0.5) * tj;
+    for (int r = j + 1 + tid; r < n; r += kCT) {
+      const R* rem = cl.map_shared_rank(pubp + buf * rpc, r % kCS);
+      wf[r] = rem[r / kCS] - K * vf[r];
     }
-    // A_own -= v w^T + w v^T (rows r >= j+1)
-    for (int li = wid; li < rpc; li += kCW) {
+    __syncthreads();
+    // the updated column j+1 of every row: a_r,j+1 - v_r w_j+1 - w_r v_j+1
+    const R vn = vf[j + 1], wn = wf[j + 1];
+    for (int r = j + 2 + tid; r < n; r += kCT) {
+      const R* rem = cl.map_shared_rank(pubc + (buf ^ 1) * rpc, r % kCS);
+      cf[r] = rem[r / kCS] - (vf[r] * wn + wf[r] * vn);
+    }
+    for (int li = wid; li < rpc; li += kW) {  // A_own -= v w^T + w v^T
       const int r = rank + kCS * li;
       if (r >= n || r < j + 1) continue;
       R* row = Ar + (size_t)li * n;
-      const R vr = vec_at<R, CL>(v, r), wr = vec_at<R, CL>(wv, r);
-#pragma unroll
-      for (int c = 0; c < CL; ++c) {
-        const int l = lane + 32 * c;
-        if (l < n) row[l] -= vr * wv[c] + wr * v[c];
-      }
+      const R vr = vf[r], wr = wf[r];
+      for (int l = j + 1 + lane; l < n; l += 32) row[l] -= vr * wf[l] + wr * vf[l];
     }
+    __syncthreads();
   }
   // the last 2 x 2 block
-  __syncthreads();
   if (tid == 0) {
     for (int r = (n >= 2 ? n - 2 : 0); r < n; ++r) {
       if (r % kCS != rank) continue;
@@ -626,7 +655,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     }
   }
   __threadfence();
-  cl.sync();  // also: no block leaves while another may still read its buffers
+  cl.sync();
   if (rank == 0)
     for (int i = tid; i < n; i += kCT) w.e2[i] = w.e[i] * w.e[i];
 }
@@ -890,25 +919,22 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
     __syncthreads();
   }
   for (int pass = 0; pass < 2; ++pass) {
-    for (int t = threadIdx.x; t < nb * nb; t += kThreads) {
-      const int a = t / nb, b = t % nb;
-      R acc = R(0.0);
-      if (b <= a)
-        for (int i = 0; i < n; ++i) acc += V[(size_t)i * nb + a] * V[(size_t)i * nb + b];
-      G[t] = acc;
-    }
+    blk_gram_tn(V, nb, V, nb, n, nb, nb, G, nb, true);
+  
     for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
-    small_cholesky(G, nb, keep_nb, R(0.0));
-    for (int i = threadIdx.x; i < n; i += kThreads) {
-      R* v = V + (size_t)i * nb;
-      for (int s2 = 0; s2 < nb; ++s2) {
-        R acc = v[s2];
-        for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * v[p];
-        v[s2] = acc / G[s2 * nb + s2];
+    block_cholesky(G, nb, keep_nb, R(0.0));
+    {  // V <- V L^-T, a thread per row
+      for (int i = threadIdx.x; i < n; i += kThreads) {
+        R* v = V + (size_t)i * nb;
+        for (int s2 = 0; s2 < nb; ++s2) {
+          R acc = v[s2];
+          for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * v[p];
+          v[s2] = acc / G[s2 * nb + s2];
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (SM)
     for (int t = threadIdx.x; t < n * nb; t += kThreads) w.V[t] = V[t];
@@ -969,58 +995,52 @@ __global__ void __launch_bounds__(kThreads)
     // G = V^T Zp with Zp = V without its X rows, summed over the W and P rows
     // directly: I - V_X^T V_X would cancel catastrophically once the X rows of
     // V are nearly the identity (a converging block)
-    for (int t = tid; t < nb * nb; t += kThreads) {
-      const int a = t / nb, b = t % nb;
-      R acc = R(0.0);
-      for (int i = nx; i < n; ++i) acc += V[(size_t)i * nb + a] * V[(size_t)i * nb + b];
-      G[t] = acc;
-    }
+    blk_gram_tn(V + (size_t)nx * nb, nb, V + (size_t)nx * nb, nb, n - nx, nb, nb, G, nb, false);
+  
     __syncthreads();
-    for (int t = tid; t < n * nb; t += kThreads) {  // Z = Zp - V G
-      const int i = t / nb, b = t % nb;
-      R acc = i < nx ? R(0.0) : V[t];
-      for (int a = 0; a < nb; ++a) acc -= V[(size_t)i * nb + a] * G[a * nb + b];
-      T1[t] = acc;
-    }
+// Z = Zp - V G
+    blk_sub_xg(V, nb, G, nb, n, nb, nb, V, nx, T1, nb);
+  
     __syncthreads();
-    for (int t = tid; t < nb * nb; t += kThreads) {  // G = Z^T Z (lower)
-      const int a = t / nb, b = t % nb;
-      R acc = R(0.0);
-      if (b <= a)
-        for (int i = 0; i < n; ++i) acc += T1[(size_t)i * nb + a] * T1[(size_t)i * nb + b];
-      G[t] = acc;
-    }
+// G = Z^T Z (lower)
+    blk_gram_tn(T1, nb, T1, nb, n, nb, nb, G, nb, true);
+  
     for (int s2 = tid; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
     R gref = R(0.0);
     for (int s2 = 0; s2 < nb; ++s2) gref = fmax(gref, G[s2 * nb + s2]);
-    small_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
-    for (int i = tid; i < n; i += kThreads) {  // Z <- Z L^-T, dropped columns zero
-      const R* zt = T1 + (size_t)i * nb;
-      R* zr = Z + (size_t)i * nb;
-      for (int s2 = 0; s2 < nb; ++s2) {
-        R acc = zt[s2];
-        for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * zr[p];
-        zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : R(0.0);
+    block_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
+    {  // Z <- Z L^-T, dropped columns zero, a thread per row
+      for (int i = tid; i < n; i += kThreads) {
+        const R* zt = T1 + (size_t)i * nb;
+        R* zr = Z + (size_t)i * nb;
+        for (int s2 = 0; s2 < nb; ++s2) {
+          R acc = zt[s2];
+          for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * zr[p];
+          zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : R(0.0);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // back to the coefficients of the original basis: y_O <- L^-T y_O, then
+  // y_rest <- y_rest - C y_O and y <- D y (k_rr_output)
+  {
+    // a thread per column, its back substitution reading only entries it
+    // wrote: no barriers
+    for (int c = tid; c < 2 * nb; c += kThreads) {
+      if (c >= nb && !want_p) continue;
+      R* M_ = c < nb ? V : Z;
+      const int cc = c < nb ? c : c - nb;
+      for (int a = no - 1; a >= 0; --a) {
+        const int i = o0 + a;
+        R acc = M_[(size_t)i * nb + cc];
+        for (int b = a + 1; b < no; ++b) acc -= w.L[b * no + a] * M_[(size_t)(o0 + b) * nb + cc];
+        M_[(size_t)i * nb + cc] = acc / w.L[a * no + a];
       }
     }
     __syncthreads();
   }
-  // back to the coefficients of the original basis: y_O <- L^-T y_O (a
-  // thread per column, its back substitution reading only entries it wrote:
-  // no barriers), then y_rest <- y_rest - C y_O and y <- D y (k_rr_output)
-  for (int c = tid; c < 2 * nb; c += kThreads) {
-    if (c >= nb && !want_p) continue;
-    R* M_ = c < nb ? V : Z;
-    const int cc = c < nb ? c : c - nb;
-    for (int a = no - 1; a >= 0; --a) {
-      const int i = o0 + a;
-      R acc = M_[(size_t)i * nb + cc];
-      for (int b = a + 1; b < no; ++b) acc -= w.L[b * no + a] * M_[(size_t)(o0 + b) * nb + cc];
-      M_[(size_t)i * nb + cc] = acc / w.L[a * no + a];
-    }
-  }
-  __syncthreads();
   if (SM) {
     for (int t = tid; t < n * nb; t += kThreads) w.V[t] = V[t];
     if (want_p)
@@ -1162,17 +1182,15 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.U = p; p += n * no;
   w.keep = reinterpret_cast<int*>(p);
   for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
-                         (const void*)k_rr_house_cluster<R, 4>,
-                         (const void*)k_rr_house_cluster<R, 8>,
-                         (const void*)k_rr_house_cluster<R, 16>, (const void*)k_rr_invit_sm<R>,
+                         (const void*)k_rr_house_cluster<R>, (const void*)k_rr_invit_sm<R>,
                          (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
   const size_t tri_bytes = sizeof(R) * n * n;
   const size_t tri2_bytes = sizeof(R) * (n * n + 2 * n * no + no * no);
   const int tri_smem = tri2_bytes <= kMaxDynSmem ? 2 : tri_bytes <= kMaxDynSmem ? 1 : 0;
   const size_t rpc = (n + kCS - 1) / kCS;
-  const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * rpc + 2 * kCW);
-  const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3 && n <= 512;
+  const size_t cl_bytes = sizeof(R) * (rpc * n + 3 * n + 4 * rpc + 2);
+  const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
   const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
   // transform (one block); Householder by the cluster when its rows fit
   (k_rr_tridiag<R><<<1, kThreads, tri_smem == 2 ? tri2_bytes : tri_smem ? tri_bytes : 0, st>>>(
@@ -1180,12 +1198,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
-    if (n <= 128)
-      (k_rr_house_cluster<R, 4><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
-    else if (n <= 256)
-      (k_rr_house_cluster<R, 8><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
-    else
-      (k_rr_house_cluster<R, 16><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
+    (k_rr_house_cluster<R><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
   (k_rr_eigvals_mc<R><<<(unsigned)nb, 32 * kEW, (sizeof(R) + sizeof(float)) * 2 * n, st>>>(

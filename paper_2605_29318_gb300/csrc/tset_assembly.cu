@@ -19,10 +19,10 @@
 //      densely in shared memory (zeros where a point does not see a centre),
 //      then the 64 x 64 block of sum_t (w_t g_A(t)) g_B(t)^T and
 //      sum_t (v_t phi_A(t)) phi_B(t)^T in register tiles (4 x 4 per thread,
-//      rows 4 tr + r, columns tc + 16 c: broadcast reads of A, conflict-free
-//      reads of B).  The last block of the union is usually narrow; it always
-//      falls on the row side, where the warps whose rows lie past the union
-//      skip the products;
+//      rows 4 tr + r, columns 4 tc + c: one vector read of each of A
+//      (broadcast) and B (conflict-free) per point and value).  The last
+//      block of the union is usually narrow; it always falls on the row side,
+//      where the warps whose rows lie past the union skip the products;
 //   3. each non-zero entry of the upper triangle added into dense K x K FP64
 //      accumulators (atomic adds).
 // The sums inside a tile run in the context's working precision (double-float
@@ -86,35 +86,37 @@ __device__ __forceinline__ int union_rank(const unsigned* bits, const int* wpre,
   return wpre[w] + __popc(bits[w] & ((1u << (c & 31)) - 1u));
 }
 
-// One block per tile.  Shared memory (dynamic): bitmap (nw words), word
-// prefix (nw + 1), union columns (K), then the staging arrays
-// sA[4][TP][kBlk] and sB[4][TP][kBlk] of T.
-template <class T, int TP>
-__global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
-    k_tset_tiles(const int* __restrict__ order, long long nq, const long long* __restrict__ ptr,
-                 const int* __restrict__ idx, const T* __restrict__ phi,
-                 const T* __restrict__ dphi, long long n1, const T* __restrict__ wh,
-                 const float* __restrict__ vol, int K, double* __restrict__ Hd,
-                 double* __restrict__ Md) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int nw = (K + 31) >> 5;
-  unsigned* bits = reinterpret_cast<unsigned*>(sm_raw);
-  int* wpre = reinterpret_cast<int*>(bits + nw);
-  int* ucol = wpre + nw + 1;
-  size_t off = (size_t)(2 * nw + 1 + K) * 4;
-  off = (off + 15) & ~size_t(15);
-  T* sA = reinterpret_cast<T*>(sm_raw + off);
-  T* sB = sA + 4 * TP * kBlk;
-  __shared__ int pts[TP];
-  __shared__ int s_total;
+// four consecutive values of a staging row (16-byte aligned)
+__device__ __forceinline__ void load4(const float* p, float (&x)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  x[0] = q.x;
+  x[1] = q.y;
+  x[2] = q.z;
+  x[3] = q.w;
+}
+__device__ __forceinline__ void load4(const dfloat* p, dfloat (&x)[4]) {
+  const float4 q0 = *reinterpret_cast<const float4*>(p);
+  const float4 q1 = *reinterpret_cast<const float4*>(p + 2);
+  x[0] = dfloat(q0.x, q0.y);
+  x[1] = dfloat(q0.z, q0.w);
+  x[2] = dfloat(q1.x, q1.y);
+  x[3] = dfloat(q1.z, q1.w);
+}
 
+// The tile's points (order[p0 ..]) and the union of their covering centres:
+// the bitmap `bits` over the centres, the exclusive popcount prefix of its
+// words `wpre` and the union's centres `ucol` in ascending order.  Returns the
+// union's size.
+template <int TP>
+__device__ int tile_union(const int* __restrict__ order, long long nq,
+                          const long long* __restrict__ ptr, const int* __restrict__ idx, int nw,
+                          int* pts, unsigned* bits, int* wpre, int* ucol, int* s_total, int& np) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const long long p0 = (long long)blockIdx.x * TP;
-  const int np = (int)min((long long)TP, nq - p0);
+  np = (int)min((long long)TP, nq - p0);
   if (tid < TP) pts[tid] = tid < np ? order[p0 + tid] : -1;
   for (int w = tid; w < nw; w += kThreads) bits[w] = 0u;
   __syncthreads();
-  // 1. the union of the tile's covering centres
   for (int j = wid; j < np; j += kThreads / 32) {
     const int i = pts[j];
     for (long long e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
@@ -139,11 +141,10 @@ __global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
     }
     if (lane == 0) {
       wpre[nw] = run;
-      s_total = run;
+      *s_total = run;
     }
   }
   __syncthreads();
-  const int U = s_total;
   for (int w = tid; w < nw; w += kThreads) {
     unsigned b = bits[w];
     int r = wpre[w];
@@ -154,7 +155,42 @@ __global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
     }
   }
   __syncthreads();
+  return *s_total;
+}
 
+// The upper triangle of one 64 x 64 block's non-zero entries into the dense
+// FP64 accumulators.
+template <class T>
+__device__ __forceinline__ void add_block(const T (&h)[4][4], const T (&m)[4][4], bool live,
+                                          int a0, int b0, int tr, int tc, int U, const int* ucol,
+                                          int K, double* __restrict__ Hd,
+                                          double* __restrict__ Md) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int ur = a0 + 4 * tr + r, uc = b0 + 4 * tc + c;
+      if (!live || ur >= U || uc >= U || ur < uc) continue;
+      const double hv = (double)finish(h[r][c]), mv = (double)finish(m[r][c]);
+      if (hv == 0.0 && mv == 0.0) continue;
+      const long long at = (long long)ucol[uc] * K + ucol[ur];  // upper triangle
+      atomicAdd(&Hd[at], hv);
+      atomicAdd(&Md[at], mv);
+    }
+}
+
+// Every pair of 64-column blocks of the union, each staged on its own: the
+// weighted values of block A = bj and the plain ones of block B = bi <= bj in
+// sA[4][TP][kBlk] and sB[4][TP][kBlk] (zeros where a point does not see a
+// centre), then the block's products and its entries.
+template <class T, int TP>
+__device__ void tile_pairs(const int* pts, int np, int U, const unsigned* bits, const int* wpre,
+                           const int* ucol, const long long* __restrict__ ptr,
+                           const int* __restrict__ idx, const T* __restrict__ phi,
+                           const T* __restrict__ dphi, long long n1, const T* __restrict__ wh,
+                           const float* __restrict__ vol, int K, double* __restrict__ Hd,
+                           double* __restrict__ Md, T* sA, T* sB) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int tr = tid >> 4, tc = tid & 15;
   const int nblk = (U + kBlk - 1) / kBlk;
   constexpr int kPlane = TP * kBlk;  // one value plane of a staging array
@@ -162,7 +198,6 @@ __global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
     for (int bj = bi; bj < nblk; ++bj) {
       const int a0 = bj * kBlk, b0 = bi * kBlk;  // rows: block bj, columns: block bi
       const bool live = 4 * tr < U - a0;         // the thread has a row in the union
-      // 2a. stage the blocks (zeros where a point does not see a centre)
       for (int q = tid; q < 4 * kPlane; q += kThreads) {
         sA[q] = T(0);
         sB[q] = T(0);
@@ -194,7 +229,6 @@ __global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
         }
       }
       __syncthreads();
-      // 2b. the 64 x 64 block: rows 4 tr + r of A, columns tc + 16 c of B
       T h[4][4], m[4][4];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -207,10 +241,8 @@ __global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
 #pragma unroll
         for (int val = 0; val < 4; ++val) {
           T a[4], b[4];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) a[r] = sA[val * kPlane + j * kBlk + 4 * tr + r];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) b[c] = sB[val * kPlane + j * kBlk + tc + 16 * c];
+          load4(sA + val * kPlane + j * kBlk + 4 * tr, a);
+          load4(sB + val * kPlane + j * kBlk + 4 * tc, b);
 #pragma unroll
           for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -222,20 +254,127 @@ __global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
             }
         }
       }
-      // 3. the upper triangle of the non-zero entries into the accumulators
+      add_block(h, m, live, a0, b0, tr, tc, U, ucol, K, Hd, Md);
+      __syncthreads();  // the staging arrays are refilled next
+    }
+}
+
+// One block per tile.  Shared memory (dynamic): bitmap (nw words), word
+// prefix (nw + 1), union columns (K), then the staging arrays
+// sA[4][TP][kBlk] and sB[4][TP][kBlk] of T.
+template <class T, int TP>
+__global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
+    k_tset_tiles(const int* __restrict__ order, long long nq, const long long* __restrict__ ptr,
+                 const int* __restrict__ idx, const T* __restrict__ phi,
+                 const T* __restrict__ dphi, long long n1, const T* __restrict__ wh,
+                 const float* __restrict__ vol, int K, double* __restrict__ Hd,
+                 double* __restrict__ Md) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int nw = (K + 31) >> 5;
+  unsigned* bits = reinterpret_cast<unsigned*>(sm_raw);
+  int* wpre = reinterpret_cast<int*>(bits + nw);
+  int* ucol = wpre + nw + 1;
+  size_t off = (size_t)(2 * nw + 1 + K) * 4;
+  off = (off + 15) & ~size_t(15);
+  T* sA = reinterpret_cast<T*>(sm_raw + off);
+  T* sB = sA + 4 * TP * kBlk;
+  __shared__ int pts[TP];
+  __shared__ int s_total;
+  int np = 0;
+  const int U = tile_union<TP>(order, nq, ptr, idx, nw, pts, bits, wpre, ucol, &s_total, np);
+  tile_pairs<T, TP>(pts, np, U, bits, wpre, ucol, ptr, idx, phi, dphi, n1, wh, vol, K, Hd, Md, sA,
+                    sB);
+}
+
+// FP32 sums: the tile's plain values over the whole union staged once,
+// G[4][TP][Up] (Up = the union rounded up to 64, at most kStageCols), with
+// the points' weights beside them; every pair of 64-column blocks then reads
+// the same read-only staging (the weight applied to the row block's values
+// as they are read, the same rounding as a weighted copy), so the pairs need
+// no barrier between them.  A tile whose union exceeds kStageCols takes the
+// per-pair staging.
+constexpr int kStageCols = 256;
+template <int TP>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tset_tiles_once(const int* __restrict__ order, long long nq,
+                      const long long* __restrict__ ptr, const int* __restrict__ idx,
+                      const float* __restrict__ phi, const float* __restrict__ dphi, long long n1,
+                      const float* __restrict__ wh, const float* __restrict__ vol, int K,
+                      double* __restrict__ Hd, double* __restrict__ Md) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int nw = (K + 31) >> 5;
+  unsigned* bits = reinterpret_cast<unsigned*>(sm_raw);
+  int* wpre = reinterpret_cast<int*>(bits + nw);
+  int* ucol = wpre + nw + 1;
+  size_t off = (size_t)(2 * nw + 1 + K) * 4;
+  off = (off + 15) & ~size_t(15);
+  float* G = reinterpret_cast<float*>(sm_raw + off);
+  __shared__ int pts[TP];
+  __shared__ int s_total;
+  __shared__ float wj[TP], vj[TP];
+  int np = 0;
+  const int U = tile_union<TP>(order, nq, ptr, idx, nw, pts, bits, wpre, ucol, &s_total, np);
+  if (U > kStageCols) {
+    tile_pairs<float, TP>(pts, np, U, bits, wpre, ucol, ptr, idx, phi, dphi, n1, wh, vol, K, Hd,
+                          Md, G, G + 4 * TP * kBlk);
+    return;
+  }
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nblk = (U + kBlk - 1) / kBlk;
+  const int Up = nblk * kBlk;
+  const int plane = TP * Up;
+  for (int q = tid; q < 4 * plane; q += kThreads) G[q] = 0.f;
+  __syncthreads();
+  for (int j = wid; j < np; j += kThreads / 32) {
+    const int i = pts[j];
+    if (lane == 0) {
+      wj[j] = wh[i];
+      vj[j] = vol[i];
+    }
+    for (long long e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+      const int o = j * Up + union_rank(bits, wpre, idx[e]);
+      G[o] = dphi[e];
+      G[plane + o] = dphi[n1 + e];
+      G[2 * plane + o] = dphi[2 * n1 + e];
+      G[3 * plane + o] = phi[e];
+    }
+  }
+  __syncthreads();
+  const int tr = tid >> 4, tc = tid & 15;
+  for (int bi = 0; bi < nblk; ++bi)
+    for (int bj = bi; bj < nblk; ++bj) {
+      const int a0 = bj * kBlk, b0 = bi * kBlk;
+      const bool live = 4 * tr < U - a0;
+      float h[4][4], m[4][4];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const int ur = a0 + 4 * tr + r, uc = b0 + tc + 16 * c;
-          if (!live || ur >= U || uc >= U || ur < uc) continue;
-          const double hv = (double)finish(h[r][c]), mv = (double)finish(m[r][c]);
-          if (hv == 0.0 && mv == 0.0) continue;
-          const long long at = (long long)ucol[uc] * K + ucol[ur];  // upper triangle
-          atomicAdd(&Hd[at], hv);
-          atomicAdd(&Md[at], mv);
+          h[r][c] = 0.f;
+          m[r][c] = 0.f;
         }
-      __syncthreads();  // the staging arrays are refilled next
+      for (int j = 0; j < (live ? np : 0); ++j) {
+        const float wt = wj[j], vt = vj[j];
+#pragma unroll
+        for (int val = 0; val < 4; ++val) {
+          float a[4], b[4];
+          load4(G + val * plane + j * Up + a0 + 4 * tr, a);
+          load4(G + val * plane + j * Up + b0 + 4 * tc, b);
+          const float s = val < 3 ? wt : vt;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float ar = s * a[r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              if (val < 3)
+                h[r][c] = fmaf(ar, b[c], h[r][c]);
+              else
+                m[r][c] = fmaf(ar, b[c], m[r][c]);
+            }
+          }
+        }
+      }
+      add_block(h, m, live, a0, b0, tr, tc, U, ucol, K, Hd, Md);
     }
 }
 
@@ -299,7 +438,10 @@ size_t tile_smem(int K, int tp) {
   const int nw = (K + 31) >> 5;
   size_t off = (size_t)(2 * nw + 1 + K) * 4;
   off = (off + 15) & ~size_t(15);
-  return off + 2 * 4 * (size_t)tp * kBlk * sizeof(T);
+  // FP32: the whole-union staging (which also holds the per-pair arrays)
+  const size_t stage = std::is_same_v<T, float> ? 4 * (size_t)tp * kStageCols
+                                                : 2 * 4 * (size_t)tp * kBlk;
+  return off + stage * sizeof(T);
 }
 
 // points per tile: FF_TSET_TILE = 16, 24 or 32 (for measurements), else the default
@@ -316,12 +458,20 @@ template <class T, int TP>
 void launch_tiles(ff_ctx* c, const int* order, int K, double* Hd, double* Md) {
   const long long nq = c->nq;
   const size_t smem = tile_smem<T>(K, TP);
-  set_max_dyn_smem((const void*)k_tset_tiles<T, TP>, (int)smem);
   const unsigned tiles = (unsigned)((nq + TP - 1) / TP);
-  (k_tset_tiles<T, TP><<<tiles, kThreads, smem, c->stream>>>(
-       order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<T>(),
-       c->dphi.as<T>(), c->n1, c->wh.as<T>(), c->vol.as<float>(), K, Hd, Md),
-   ::ff::note_launch());
+  if constexpr (std::is_same_v<T, float>) {
+    set_max_dyn_smem((const void*)k_tset_tiles_once<TP>, (int)smem);
+    (k_tset_tiles_once<TP><<<tiles, kThreads, smem, c->stream>>>(
+         order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<float>(),
+         c->dphi.as<float>(), c->n1, c->wh.as<float>(), c->vol.as<float>(), K, Hd, Md),
+     ::ff::note_launch());
+  } else {
+    set_max_dyn_smem((const void*)k_tset_tiles<T, TP>, (int)smem);
+    (k_tset_tiles<T, TP><<<tiles, kThreads, smem, c->stream>>>(
+         order, nq, c->nbr_ptr.as<long long>(), c->nbr_idx.as<int>(), c->phi.as<T>(),
+         c->dphi.as<T>(), c->n1, c->wh.as<T>(), c->vol.as<float>(), K, Hd, Md),
+     ::ff::note_launch());
+  }
   FF_LAUNCH_CHECK();
 }
 

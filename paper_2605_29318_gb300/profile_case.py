@@ -11,6 +11,11 @@
         h = 0.012 (228,357 points, K = 1,000): a case of the splat's kernels
         (whole-GPU farthest-point sampling, Gaussian shape functions, dense-tile
         assembly) that holds about 1 GB on the device
+    python -m paper_2605_29318_gb300.profile_case twoset32 [steps]
+        the same with FP32 build precision (the splat benchmark's setting)
+    python -m paper_2605_29318_gb300.profile_case splat32 [steps]
+        the splat step as the benchmark runs it (FP32 build precision, FP32
+        preconditioner degree 32)
 
 Each step is synchronised; the script prints the solver status and iteration
 count.  It only drives the library (nothing is timed here).
@@ -35,7 +40,11 @@ def main(argv):
     dev = "cuda:0"
     ctx = binding.Context(0, "fp64")
     opts = binding.default_opts()
-    if case == "splat":
+    if case in ("splat32", "twoset32"):
+        ctx.set_build_precision("fp32")
+    if case == "splat32":
+        opts = binding.default_opts(cheb_degree=32, cheb_degree_fp64=64)
+    if case in ("splat", "splat32"):
         c = synth.gaussian_mixture(1_000_000)
         X, v = torch.from_numpy(c.X).to(dev), torch.from_numpy(c.v).to(dev)
         E = torch.from_numpy(np.ascontiguousarray(c.E, np.float32)).to(dev)
@@ -55,7 +64,7 @@ def main(argv):
             _, _, rep, st = ctx.eigenmodes(32, opts, check=False)
             torch.cuda.synchronize()
             print("torus step", st, rep["iterations"], flush=True)
-    elif case == "twoset":
+    elif case in ("twoset", "twoset32"):
         Xq, vq = synth.torus_grid(0.012)
         X, v = torch.from_numpy(Xq).to(dev), torch.from_numpy(vq).to(dev)
         for _ in range(steps):
@@ -64,7 +73,7 @@ def main(argv):
             torch.cuda.synchronize()
             print("twoset build", ctx.sizes(), flush=True)
     else:
-        raise SystemExit(f"unknown case {case!r} (splat, torus, twoset)")
+        raise SystemExit(f"unknown case {case!r} (splat, splat32, torus, twoset, twoset32)")
     ctx.close()
 
 
