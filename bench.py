@@ -150,13 +150,16 @@ class Clocks:
 # Per-workload defaults of the options a flag leaves unset.  The splat follows
 # its configuration's precision plan: shape functions and tile sums in FP32
 # (the matrices stored in FP64), FP32 preconditioner steps of degree 32 (16
-# iterations instead of 21 at degree 16 on this K = 1,000 pencil); the nodal
-# torus keeps degree 16 and the double-float build of an FP64 context.
+# iterations instead of 21 at degree 16 on this K = 1,000 pencil; degrees 48
+# to 96 gave no fewer), and the FP32 phase runs to 3e-5 before it hands over
+# (its rounding floor is lower on this small pencil than on the 50k torus);
+# the nodal torus keeps degree 16, the hand-over at 1e-4 and the double-float
+# build of an FP64 context.
 WORKLOAD_DEFAULTS = {
-    "splat": dict(cheb=32, cheb_fp64=64, build_prec="fp32"),
-    "torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64"),
-    "twoset-torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64"),
-    "batch": dict(cheb=16, cheb_fp64=64, build_prec="fp64"),
+    "splat": dict(cheb=32, cheb_fp64=64, build_prec="fp32", fp32_tol=3e-5),
+    "torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64", fp32_tol=1e-4),
+    "twoset-torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64", fp32_tol=1e-4),
+    "batch": dict(cheb=16, cheb_fp64=64, build_prec="fp64", fp32_tol=1e-4),
 }
 
 
@@ -170,7 +173,8 @@ def _opts(args, workload=None):
     return binding.default_opts(tol=args.tol, cheb_degree=_opt(args, "cheb", workload),
                                 max_iter=args.max_iter, fp32_phase=args.fp32_phase,
                                 cheb_degree_fp64=_opt(args, "cheb_fp64", workload),
-                                precond_tc=args.precond_tc, fp32_tol=args.fp32_tol,
+                                precond_tc=args.precond_tc,
+                                fp32_tol=_opt(args, "fp32_tol", workload),
                                 precond_compact=args.precond_compact)
 
 
@@ -195,6 +199,7 @@ def splat_config(args):
             "build_precision": _opt(args, "build_prec", "splat"), "tol": args.tol,
             "cheb_degree": _opt(args, "cheb", "splat"),
             "cheb_degree_fp64": _opt(args, "cheb_fp64", "splat"),
+            "fp32_tol": _opt(args, "fp32_tol", "splat"),
             "points": SPLAT["n"], "K": SPLAT["K"], "k": SPLAT["k"], "l2": L2_NOTE,
             "parallelism": "single GPU"}
 
@@ -416,12 +421,14 @@ def splat_line(args, r, peaks):
     # double-float sums of FP64 contexts cost 12 FP32 operations per
     # multiply-add, the FP32 ones 2
     pair_products = r["pair_products"]
-    per_mac = 24 if (args.prec == "fp64" and _opt(args, "build_prec", "splat") == "fp64") else 2
+    df = args.prec == "fp64" and _opt(args, "build_prec", "splat") == "fp64"
+    per_mac = 24 if df else 2
     ops = 4 * pair_products * per_mac
-    roof = _roofline("alu", "k_tset_tiles (two-set H_w and M: dense 64 x 64 register tiles of "
+    kern = "k_tset_tiles" if df else "k_tset_tiles_once"
+    roof = _roofline("alu", kern + " (two-set H_w and M: dense 64 x 64 register tiles of "
                      "24-point tiles grouped by nearest centre)",
                      ops, "algorithmic_fp32_ops_per_launch", ms_launch, cnt, peaks,
-                     traffic=_traffic("asm_values", "k_tset_tiles"),
+                     traffic=_traffic("asm_values", kern),
                      extra={"pair_products": pair_products,
                             "fp32_ops_per_multiply_add": per_mac // 2 * 2})
     line = {
@@ -857,8 +864,9 @@ def main():
     ap.add_argument("--fp32-phase", type=int, default=1, choices=[0, 1],
                     help="FP64 contexts: iterate in FP32 first, then finish in double-float")
     ap.add_argument("--max-iter", type=int, default=500)
-    ap.add_argument("--fp32-tol", type=float, default=1e-4,
-                    help="residual at which the FP32 phase hands over")
+    ap.add_argument("--fp32-tol", type=float, default=None,
+                    help="residual at which the FP32 phase hands over (default: 3e-5 for the "
+                         "splat, 1e-4 otherwise)")
     ap.add_argument("--precond-tc", type=int, default=1, choices=[0, 1],
                     help="preconditioner steps on tensor cores (BF16 tiles) or on CUDA cores")
     ap.add_argument("--precond-compact", type=int, default=0, choices=[0, 1],

@@ -23,7 +23,8 @@
 //                       division-free Sturm count;
 //   k_rr_invit_sm       their eigenvectors by inverse iteration on the
 //                       tridiagonal (LU with partial pivoting), one block each;
-//   k_rr_cholqr         Cholesky QR (twice) of those vectors;
+//   k_rr_cholqr         Cholesky QR of those vectors (a second pass only when
+//                       the first finds them far from orthogonal);
 //   k_rr_backtransform  the Householder reflectors applied in reverse, one
 //                       warp per vector;
 //   k_rr_momentum       the momentum coefficients Z (the W and P rows of the
@@ -493,26 +494,24 @@ __device__ int sturm(const R* d, const R* e2, int n, R x) {
 // Householder tridiagonalisation of the transformed n x n matrix (w.As) by a
 // cluster of kCS thread blocks: row r lives in block r % kCS (distributed
 // shared memory), so the O(n^3) work is spread over kCS SMs.  Every block
-// holds column j of the current matrix and forms the same reflector v; each
-// block computes p = tau A v for its rows and publishes it with its share of
-// p^T v and its rows' entries of column j+1 (before the update); after one
-// cluster barrier every block gathers p, forms w = p - K v, updates its rows
-// and forms the updated column j+1 of all rows itself from the published
-// entries -- one cluster barrier per step.  The published buffers alternate
-// between steps, so no barrier guards their reuse.
+// holds column j of the current matrix (cf, two buffers); a step
+//   1. forms the reflector in every warp (the norm by a warp reduction over
+//      the block's copy of column j: the same values everywhere, no barrier;
+//      v is formed from column j where it is read);
+//   2. computes p = tau A v for the block's rows (a warp per row, four rows
+//      at a time) and publishes p, the warps' shares of p^T v and the rows'
+//      entries of column j+1 before the update;
+//   3. after one cluster barrier, gathers in one round of remote loads (one
+//      or two per thread) p, the column-j+1 entries and the shares of all
+//      blocks into its own shared memory;
+//   4. after a block barrier, forms K = tau p^T v / 2, w = p - K v, the
+//      updated column j+1 (into the other buffer) and updates its rows
+//      (A -= v w^T + w v^T); a block barrier ends the step.
+// The published buffers alternate between steps, so no barrier guards their
+// reuse.
 constexpr int kCS = 8;
 constexpr int kCT = 256;
-
-template <class R>
-__device__ R cl_block_sum(R v, R* red) {
-  const int lane = threadIdx.x & 31, wdx = threadIdx.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[wdx] = v;
-  __syncthreads();
-  R t = lane < (kCT / 32) ? red[lane] : R(0.0);
-  return warp_sum(t);
-}
+constexpr int kCW = kCT / 32;
 
 template <class R>
 __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
@@ -521,122 +520,104 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int kW = kCT / 32;
   const int rpc = (n + kCS - 1) / kCS;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  R* sm = reinterpret_cast<R*>(sm_raw);
-  R* Ar = sm;                      // rpc x n: row rank + kCS * li
-  R* vf = Ar + (size_t)rpc * n;    // n: column j, then v
-  R* wf = vf + n;                  // n: p, then w
-  R* cf = wf + n;                  // n: column j of the current matrix
-  R* pubc = cf + n;                // 2 x rpc: own rows' entries of the next column
-  R* pubp = pubc + 2 * rpc;        // 2 x rpc
-  R* pubs = pubp + 2 * rpc;        // 2
-  __shared__ R red[kW];
+  R* Ar = reinterpret_cast<R*>(sm_raw);  // rpc x n: row rank + kCS * li
+  R* cf = Ar + (size_t)rpc * n;          // 2 x n: column j (alternating)
+  R* wl = cf + 2 * n;                    // n: the gathered p
+  R* cn = wl + n;                        // n: the gathered entries of column j+1
+  R* kall = cn + n;                      // kCS x kCW: the gathered shares of p^T v
+  R* pubc = kall + kCS * kCW;            // 2 x rpc: own rows' entries of column j+1
+  R* pubp = pubc + 2 * rpc;              // 2 x rpc: own rows' p
+  R* pubk = pubp + 2 * rpc;              // 2 x kCW: the warps' shares of p^T v
   for (int t = tid; t < rpc * n; t += kCT) {
-    const int li = t / n, c = t % n, r = rank + kCS * li;
+    const int li = t / n, c = t - li * n, r = rank + kCS * li;
     Ar[t] = r < n ? w.As[(size_t)r * n + c] : R(0.0);
   }
+  for (int l = tid; l < n; l += kCT) cf[l] = l >= 1 ? w.As[(size_t)l * n] : R(0.0);
   __syncthreads();
-  // own rows' entries of column c (rows >= c + 1) into pubc[b], then every
-  // block gathers the column into cf
-  auto publish_col = [&](int c, int b) {
-    for (int li = tid; li < rpc; li += kCT) {
-      const int r = rank + kCS * li;
-      pubc[b * rpc + li] = (r < n && r >= c + 1) ? Ar[(size_t)li * n + c] : R(0.0);
-    }
-  };
-  auto gather_col = [&](int c, int b) {
-    for (int r = c + 1 + tid; r < n; r += kCT) {
-      const R* rem = cl.map_shared_rank(pubc + b * rpc, r % kCS);
-      cf[r] = rem[r / kCS];
-    }
-  };
-  publish_col(0, 0);
-  cl.sync();
-  gather_col(0, 0);
-  __syncthreads();
+  cl.sync();  // every block of the cluster runs before the first remote access
   for (int j = 0; j + 2 < n; ++j) {
     const int buf = j & 1;
-    for (int r = j + 1 + tid; r < n; r += kCT) vf[r] = cf[r];
-    __syncthreads();
-    R part = R(0.0);
-    for (int r = j + 1 + tid; r < n; r += kCT) part += vf[r] * vf[r];
-    const R ss = cl_block_sum(part, red);
-    const R x0 = vf[j + 1];
+    const R* cur = cf + buf * n;
+    R* nxt = cf + (buf ^ 1) * n;
+    // 1. the reflector, in every warp
+    R ss = R(0.0);
+    for (int l = j + 1 + lane; l < n; l += 32) ss += cur[l] * cur[l];
+    ss = warp_sum(ss);
+    const R x0 = cur[j + 1];
     const R alpha = sqrt(ss);
-    const int own_j = (j % kCS) == rank;
-    if (!(alpha > Prec<R>::tiny)) {  // nothing to reflect: the next column as it stands
-      if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
-      if (rank == 0 && tid == 0) {
-        w.tau[j] = R(0.0);
-        w.e[j] = x0;
-      }
-      publish_col(j + 1, buf ^ 1);
-      cl.sync();
-      gather_col(j + 1, buf ^ 1);
-      __syncthreads();
-      continue;
-    }
+    const bool refl = alpha > Prec<R>::tiny;
     const R beta = x0 >= R(0.0) ? -alpha : alpha;
-    const R tj = (beta - x0) / beta;
-    const R scale = R(1.0) / (x0 - beta);
-    __syncthreads();
-    for (int r = j + 1 + tid; r < n; r += kCT) {
-      const R v = r == j + 1 ? R(1.0) : vf[r] * scale;
-      vf[r] = v;
-      if (rank == 0) w.ref[(size_t)j * n + r] = v;
-    }
-    if (own_j && tid == 0) w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
-    if (rank == 0 && tid == 0) {
-      w.tau[j] = tj;
-      w.e[j] = beta;
-    }
-    __syncthreads();
-    // p = tau A v for own rows r >= j+1, this block's share of p^T v, and the
-    // own rows' entries of column j+1 before the update
-    R kp = R(0.0);
-    for (int li = wid; li < rpc; li += kW) {
-      const int r = rank + kCS * li;
-      R acc = R(0.0);
-      if (r < n && r >= j + 1) {
-        const R* row = Ar + (size_t)li * n;
-        for (int l = j + 1 + lane; l < n; l += 32) acc += row[l] * vf[l];
-      }
-      acc = warp_sum(acc) * tj;
+    const R tj = refl ? (beta - x0) / beta : R(0.0);
+    const R scale = refl ? R(1.0) / (x0 - beta) : R(0.0);
+    const R v1 = refl ? R(1.0) : R(0.0);  // v_{j+1}
+    if (rank == 0 && wid == 0) {
+      for (int l = j + 1 + lane; l < n; l += 32)
+        w.ref[(size_t)j * n + l] = l == j + 1 ? v1 : cur[l] * scale;
       if (lane == 0) {
-        pubp[buf * rpc + li] = (r < n && r >= j + 1) ? acc : R(0.0);
-        if (r < n && r >= j + 1) kp += acc * vf[r];
+        w.tau[j] = tj;
+        w.e[j] = refl ? beta : x0;
       }
     }
-    publish_col(j + 1, buf ^ 1);
-    const R kpb = cl_block_sum(kp, red);
-    if (tid == 0) pubs[buf] = kpb;
+    if ((j % kCS) == rank && wid == (j / kCS) % kCW && lane == 0)
+      w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
+    // 2. p = tau A v for own rows r >= j+1, four rows of a warp at a time
+    R kp = R(0.0);
+    for (int l0 = wid; l0 < rpc; l0 += 4 * kCW) {
+      R acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] = R(0.0);
+        const int li = l0 + q * kCW, r = rank + kCS * li;
+        if (li < rpc && r < n && r >= j + 1) {
+          const R* row = Ar + (size_t)li * n;
+          for (int l = j + 1 + lane; l < n; l += 32)
+            acc[q] += row[l] * (l == j + 1 ? v1 : cur[l] * scale);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]) * tj;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int li = l0 + q * kCW, r = rank + kCS * li;
+        if (li < rpc && r < n && r >= j + 1) {
+          kp += acc[q] * (r == j + 1 ? v1 : cur[r] * scale);
+          if (lane == 0) {
+            pubp[buf * rpc + li] = acc[q];
+            pubc[buf * rpc + li] = Ar[(size_t)li * n + j + 1];
+          }
+        }
+      }
+    }
+    if (lane == 0) pubk[buf * kCW + wid] = kp;
     cl.sync();
-    R kq[kCS];  // the blocks' shares, loaded together (remote loads in flight at once)
-#pragma unroll
-    for (int q = 0; q < kCS; ++q) kq[q] = cl.map_shared_rank(pubs, q)[buf];
-    R K = R(0.0);
-#pragma unroll
-    for (int q = 0; q < kCS; ++q) K += kq[q];
-    K *= R(0.5) * tj;
-    for (int r = j + 1 + tid; r < n; r += kCT) {
-      const R* rem = cl.map_shared_rank(pubp + buf * rpc, r % kCS);
-      wf[r] = rem[r / kCS] - K * vf[r];
+    // 3. one round of remote loads
+    for (int l = j + 1 + tid; l < n; l += kCT) {
+      const int owner = l % kCS, ol = l / kCS;
+      wl[l] = cl.map_shared_rank(pubp, owner)[buf * rpc + ol];
+      cn[l] = cl.map_shared_rank(pubc, owner)[buf * rpc + ol];
     }
+    if (tid < kCS * kCW) kall[tid] = cl.map_shared_rank(pubk, tid / kCW)[buf * kCW + tid % kCW];
     __syncthreads();
-    // the updated column j+1 of every row: a_r,j+1 - v_r w_j+1 - w_r v_j+1
-    const R vn = vf[j + 1], wn = wf[j + 1];
-    for (int r = j + 2 + tid; r < n; r += kCT) {
-      const R* rem = cl.map_shared_rank(pubc + (buf ^ 1) * rpc, r % kCS);
-      cf[r] = rem[r / kCS] - (vf[r] * wn + wf[r] * vn);
+    // 4. K, w, the next column and the update of own rows
+    R kq = R(0.0);
+    for (int q = lane; q < kCS * kCW; q += 32) kq += kall[q];
+    const R K = R(0.5) * tj * warp_sum(kq);
+    const R wn = wl[j + 1] - K * v1;  // w_{j+1}
+    for (int l = j + 2 + tid; l < n; l += kCT) {
+      const R vl = cur[l] * scale, wv = wl[l] - K * vl;
+      nxt[l] = cn[l] - (vl * wn + wv * v1);
     }
-    for (int li = wid; li < rpc; li += kW) {  // A_own -= v w^T + w v^T
+    for (int li = wid; li < rpc; li += kCW) {
       const int r = rank + kCS * li;
       if (r >= n || r < j + 1) continue;
       R* row = Ar + (size_t)li * n;
-      const R vr = vf[r], wr = wf[r];
-      for (int l = j + 1 + lane; l < n; l += 32) row[l] -= vr * wf[l] + wr * vf[l];
+      const R vr = r == j + 1 ? v1 : cur[r] * scale, wr = wl[r] - K * vr;
+      for (int l = j + 1 + lane; l < n; l += 32) {
+        const R vl = l == j + 1 ? v1 : cur[l] * scale;
+        row[l] -= vr * (wl[l] - K * vl) + wr * vl;
+      }
     }
     __syncthreads();
   }
@@ -655,7 +636,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     }
   }
   __threadfence();
-  cl.sync();
+  cl.sync();  // also: no block leaves while another may still read its buffers
   if (rank == 0)
     for (int i = tid; i < n; i += kCT) w.e2[i] = w.e[i] * w.e[i];
 }
@@ -905,7 +886,7 @@ __global__ void k_rr_invit_sm(int n, int nb, RRWork<R> w) {
   for (int i = 0; i < n; ++i) w.V[(size_t)i * nb + s] = z[i];
 }
 
-// ------------------------------------------------------------------ 4a. Cholesky QR (twice) of the tridiagonal eigenvectors
+// ------------------------------------------------------------------ 4a. Cholesky QR of the tridiagonal eigenvectors (twice unless once is enough)
 // SM: V (n x nb) and G staged in shared memory (dynamic), else worked on in
 // the global workspace
 template <class R, bool SM>
@@ -918,11 +899,29 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
     for (int t = threadIdx.x; t < n * nb; t += kThreads) V[t] = w.V[t];
     __syncthreads();
   }
+  __shared__ float s_off[kWarps];
   for (int pass = 0; pass < 2; ++pass) {
     blk_gram_tn(V, nb, V, nb, n, nb, nb, G, nb, true);
-  
     for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
+    // largest off-diagonal of the normalised Gram matrix: at most 1e-3 means
+    // (Gershgorin) a condition number below (1 + nb 1e-3) / (1 - nb 1e-3),
+    // and one pass leaves the vectors orthonormal to a few units of rounding
+    float off = 0.f;
+    if (pass == 0) {
+      for (int t = threadIdx.x; t < nb * nb; t += kThreads) {
+        const int a = t / nb, b = t - a * nb;
+        if (b < a)
+          off = fmaxf(off, fabsf((float)G[(size_t)a * nb + b]) /
+                               sqrtf((float)G[(size_t)a * nb + a] * (float)G[(size_t)b * nb + b]));
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+      if ((threadIdx.x & 31) == 0) s_off[threadIdx.x >> 5] = off;
+      __syncthreads();
+      off = 0.f;
+      for (int q = 0; q < kWarps; ++q) off = fmaxf(off, s_off[q]);
+    }
     block_cholesky(G, nb, keep_nb, R(0.0));
     {  // V <- V L^-T, a thread per row
       for (int i = threadIdx.x; i < n; i += kThreads) {
@@ -935,6 +934,7 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
       }
       __syncthreads();
     }
+    if (pass == 0 && nb * 1e-3f < 0.5f && off <= 1e-3f) break;  // one pass is enough
   }
   if (SM)
     for (int t = threadIdx.x; t < n * nb; t += kThreads) w.V[t] = V[t];
@@ -1189,7 +1189,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   const size_t tri2_bytes = sizeof(R) * (n * n + 2 * n * no + no * no);
   const int tri_smem = tri2_bytes <= kMaxDynSmem ? 2 : tri_bytes <= kMaxDynSmem ? 1 : 0;
   const size_t rpc = (n + kCS - 1) / kCS;
-  const size_t cl_bytes = sizeof(R) * (rpc * n + 3 * n + 4 * rpc + 2);
+  const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * n + kCS * kCW + 4 * rpc + 2 * kCW);
   const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
   const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
   // transform (one block); Householder by the cluster when its rows fit

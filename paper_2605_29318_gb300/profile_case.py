@@ -15,7 +15,7 @@
         the same with FP32 build precision (the splat benchmark's setting)
     python -m paper_2605_29318_gb300.profile_case splat32 [steps]
         the splat step as the benchmark runs it (FP32 build precision, FP32
-        preconditioner degree 32)
+        preconditioner degree 32, hand-over from the FP32 phase at 3e-5)
 
 Each step is synchronised; the script prints the solver status and iteration
 count.  It only drives the library (nothing is timed here).
@@ -43,7 +43,7 @@ def main(argv):
     if case in ("splat32", "twoset32"):
         ctx.set_build_precision("fp32")
     if case == "splat32":
-        opts = binding.default_opts(cheb_degree=32, cheb_degree_fp64=64)
+        opts = binding.default_opts(cheb_degree=32, cheb_degree_fp64=64, fp32_tol=3e-5)
     if case in ("splat", "splat32"):
         c = synth.gaussian_mixture(1_000_000)
         X, v = torch.from_numpy(c.X).to(dev), torch.from_numpy(c.v).to(dev)
