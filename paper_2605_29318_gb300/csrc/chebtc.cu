@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "linalg.cuh"
@@ -28,7 +29,6 @@ namespace ff {
 namespace {
 
 constexpr int kTcRows = 16;            // rows per block (the M of the MMA)
-constexpr int kWB = 4;                 // warps per block of the step kernel
 constexpr int kTcMaxWords = 8192;      // bitmap words: column spans up to 262144
 constexpr unsigned kFullMask = 0xffffffffu;
 
@@ -176,22 +176,30 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint4& a, unsigned
       : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
-// One block of kWB warps per 16-row block; warp w takes the block's k-steps
-// w, w + kWB, ...: three staging buffers per warp keep the union rows of two
+// One block of WB warps per 16-row block; warp w takes the block's k-steps
+// w, w + WB, ...: three staging buffers per warp keep the union rows of two
 // later steps in flight while a step is multiplied (their union columns and
 // A fragments loaded earlier still).  The warps' partial 16 x m products are
 // summed through the same shared memory and each warp finishes a share of the
 // column tiles: res -= D^-1 (H d), d' = c1 d + c2 res (BF16), x += d'.
-template <int NT>
-__global__ void __launch_bounds__(32 * kWB)
+// WB = 4 where the row blocks fill the GPU; WB = 16 where they are few (a
+// K x K pencil of a two-set cloud: 63 row blocks for K = 1,000), so that each
+// warp's chain of k-steps is four times shorter.
+template <int WB>
+constexpr size_t tc_step_smem(int NT) {
+  return std::max<size_t>((size_t)WB * 3 * kTcRows * 8 * NT * 2, (size_t)WB * 32 * 4 * NT * 4);
+}
+
+template <int NT, int WB>
+__global__ void __launch_bounds__(32 * WB)
     k_cheb_step_tc(const int* __restrict__ kofs, const int* __restrict__ ucol,
                    const uint4* __restrict__ tile, const float* __restrict__ hs,
                    const float* __restrict__ hdiag, int n, const __nv_bfloat16* __restrict__ din,
                    __nv_bfloat16* __restrict__ dout, float* __restrict__ x,
                    float* __restrict__ res, float c1, float c2) {
+  constexpr int kWB = WB;
   constexpr int m = 8 * NT, PIECES = kTcRows * NT, ITERS = (PIECES + 31) / 32, NB = 3;
-  constexpr int kStage = kWB * NB * kTcRows * m * 2, kRed = kWB * 32 * 4 * NT * 4;
-  __shared__ __align__(16) unsigned char smem[kStage > kRed ? kStage : kRed];
+  extern __shared__ __align__(16) unsigned char smem[];
   const int b = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem) + w * NB * kTcRows * m;
   const int s0 = kofs[b], ns = kofs[b + 1] - s0;
@@ -359,12 +367,28 @@ bool cheb_step_tc(cudaStream_t st, const ff_ctx* c, int m, const void* din, void
   const int nblk = (int)((c->n + kTcRows - 1) / kTcRows);
   const auto* bi = static_cast<const __nv_bfloat16*>(din);
   auto* bo = static_cast<__nv_bfloat16*>(dout);
-#define FF_TC(NT)                                                                              \
-  (k_cheb_step_tc<NT><<<nblk, 32 * kWB, 0, st>>>(c->tc_kofs.as<int>(), c->tc_ucol.as<int>(),        \
-                                             reinterpret_cast<const uint4*>(c->tc_tile.p),     \
-                                             c->tc_hs.as<float>(), c->hdiag_f32.as<float>(),   \
-                                             (int)c->n, bi, bo, x, res, c1, c2),               \
-   ::ff::note_launch())
+  const bool few = nblk < 2 * sm_count();
+  auto go = [&](auto nt) {
+    constexpr int NT = decltype(nt)::value;
+    if (few) {
+      const size_t sm = tc_step_smem<16>(NT);
+      set_max_dyn_smem((const void*)k_cheb_step_tc<NT, 16>, (int)sm);
+      (k_cheb_step_tc<NT, 16><<<nblk, 32 * 16, sm, st>>>(
+           c->tc_kofs.as<int>(), c->tc_ucol.as<int>(),
+           reinterpret_cast<const uint4*>(c->tc_tile.p), c->tc_hs.as<float>(),
+           c->hdiag_f32.as<float>(), (int)c->n, bi, bo, x, res, c1, c2),
+       ::ff::note_launch());
+    } else {
+      const size_t sm = tc_step_smem<4>(NT);
+      set_max_dyn_smem((const void*)k_cheb_step_tc<NT, 4>, (int)sm);
+      (k_cheb_step_tc<NT, 4><<<nblk, 32 * 4, sm, st>>>(
+           c->tc_kofs.as<int>(), c->tc_ucol.as<int>(),
+           reinterpret_cast<const uint4*>(c->tc_tile.p), c->tc_hs.as<float>(),
+           c->hdiag_f32.as<float>(), (int)c->n, bi, bo, x, res, c1, c2),
+       ::ff::note_launch());
+    }
+  };
+#define FF_TC(NT) go(std::integral_constant<int, NT>{})
   switch (m / 8) {
     case 1: FF_TC(1); break;
     case 2: FF_TC(2); break;

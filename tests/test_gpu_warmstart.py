@@ -166,6 +166,30 @@ def test_warmstart_block_layout_and_solve(prec):
     net.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_unconverged_start_block_falls_back_to_the_random_start(prec):
+    """A start block that ends without convergence is run again from the
+    seeded random start: with max_iter too small for either start, the call
+    reports warm_start_used = 2, counts the iterations of both runs, and
+    returns exactly what the plain call returns (same seed, same options)."""
+    import torch
+    from paper_2605_29318_gb300 import binding
+    c = synth.warmstart_shape(20004, nmin=3000, nmax=4000)
+    ctx = _ctx(c, prec)
+    ctx.assemble_hessian(None, None, c.E, c.nu)
+    o = binding.default_opts(tol=1e-6, seed=3, max_iter=2)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    X0 = torch.randn((11 + o.guard, c.n), generator=g, dtype=ctx.dtype).cuda()
+    ev_w, m_w, rep_w, st_w = ctx.eigenmodes(12, o, X0=X0, check=False)
+    ev_p, m_p, rep_p, st_p = ctx.eigenmodes(12, o, check=False)
+    assert st_w == st_p == 5
+    assert rep_w["warm_start_used"] == 2 and rep_p["warm_start_used"] == 0
+    assert rep_w["iterations"] > rep_p["iterations"]
+    np.testing.assert_array_equal(ev_w, ev_p)
+    assert torch.equal(m_w, m_p)
+    ctx.close()
+
+
 def test_trained_network_captures_heldout_modes():
     """What the trained network gains over the method without it: on held-out
     shapes (seeds 20000+) the span of its predicted block holds most of the
