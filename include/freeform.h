@@ -410,8 +410,8 @@ ff_status ff_apply_operators_matfree(ff_ctx* ctx, const float* E, const float* n
  * makes no cudaMalloc/cudaFree or other allocation.  Requires
  * 3 * n * m * (4 for FF_PREC_FP32, 8 for FF_PREC_FP64) bytes <= 32 MiB (each
  * panel rounded up to 256 bytes); larger blocks return FF_ERR_INVALID_ARG.
- * The first call on a device looks up the array's device address and should
- * come before any stream capture.  Like every call of this library it
+ * The first call on a device looks up the array's device address.  Like
+ * every call of this library it
  * synchronises the context's stream before returning.  All calls share the
  * array: calls that overlap on the GPU race and must be serialised by the
  * caller. */

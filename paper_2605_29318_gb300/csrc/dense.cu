@@ -105,31 +105,57 @@ __device__ R block_sum(R v, R* red) {
   return warp_sum(t);
 }
 
-// right-looking Cholesky (lower) of an m x m matrix in place, with drop
+// acc - sum_{p0 <= p < p1} term(p), with four independent partial sums so
+// that a long serial substitution keeps several multiply-adds in flight
+template <class R, class F>
+__device__ __forceinline__ R sub_dot(R acc, int p0, int p1, F term) {
+  R a1 = R(0.0), a2 = R(0.0), a3 = R(0.0);
+  int p = p0;
+  for (; p + 3 < p1; p += 4) {
+    acc -= term(p);
+    a1 -= term(p + 1);
+    a2 -= term(p + 2);
+    a3 -= term(p + 3);
+  }
+  for (; p < p1; ++p) acc -= term(p);
+  return (acc + a1) + (a2 + a3);
+}
+
+// right-looking Cholesky (lower) of an m x m matrix in place, with drop.  Step
+// j subtracts g_ij g_lj / g_jj from the trailing lower triangle (a warp per
+// row, lanes along the row) using the unscaled column j; column j is scaled
+// in step j + 1, when no thread reads it any more, and keep[j] is written then
+// too, so a step costs one barrier.  Every thread takes the pivot decision
+// itself from the same diagonal entry.
 template <class R>
 __device__ void block_cholesky(R* G, int m, int* keep, R drop_rel) {
-  __shared__ int s_keep;
-  for (int j = 0; j < m; ++j) {
-    if (threadIdx.x == 0) {
-      const R piv = G[j * m + j];
-      const int k = keep[j] && piv > drop_rel;
-      keep[j] = k;
-      G[j * m + j] = k ? sqrt(piv) : R(1.0);
-      s_keep = k;
-    }
-    __syncthreads();
-    const R ljj = G[j * m + j];
-    const int kj = s_keep;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) G[i * m + j] = kj ? G[i * m + j] / ljj : R(0.0);
-    __syncthreads();
-    const int r = m - j - 1;
-    if (kj)
-      for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-        const int i = j + 1 + t / r, l = j + 1 + t % r;
-        if (l <= i) G[i * m + l] -= G[i * m + j] * G[l * m + j];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int kprev = 0;
+  R lprev = R(1.0);
+  for (int j = 0; j <= m; ++j) {
+    if (j > 0) {  // finish column j - 1
+      const int c = j - 1;
+      for (int i = j + threadIdx.x; i < m; i += blockDim.x)
+        G[(size_t)i * m + c] = kprev ? G[(size_t)i * m + c] / lprev : R(0.0);
+      if (threadIdx.x == 0) {
+        G[(size_t)c * m + c] = lprev;
+        keep[c] = kprev;
       }
+    }
+    if (j == m) break;
+    const R piv = G[(size_t)j * m + j];
+    const int kj = keep[j] && piv > drop_rel;
+    const R inv = kj ? R(1.0) / piv : R(0.0);
+    if (kj)
+      for (int i = j + 1 + wid; i < m; i += nw) {
+        const R gij = G[(size_t)i * m + j] * inv;
+        for (int l = j + 1 + lane; l <= i; l += 32) G[(size_t)i * m + l] -= gij * G[(size_t)l * m + j];
+      }
+    kprev = kj;
+    lprev = kj ? sqrt(piv) : R(1.0);
     __syncthreads();
   }
+  __syncthreads();
 }
 
 template <class R>
@@ -335,16 +361,18 @@ __global__ void __launch_bounds__(kThreads)
     for (int c = tid; c < n; c += kThreads)
       for (int a = 0; a < no; ++a) {
         const int i = o0 + a;
-        R acc = As[(size_t)i * n + c];
-        for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)(o0 + b) * n + c];
+        const R acc = sub_dot(As[(size_t)i * n + c], 0, a, [&](int b) {
+          return Lw[a * no + b] * As[(size_t)(o0 + b) * n + c];
+        });
         As[(size_t)i * n + c] = acc / Lw[a * no + a];
       }
     __syncthreads();
     for (int r = tid; r < n; r += kThreads)
       for (int a = 0; a < no; ++a) {
         const int i = o0 + a;
-        R acc = As[(size_t)r * n + i];
-        for (int b = 0; b < a; ++b) acc -= Lw[a * no + b] * As[(size_t)r * n + o0 + b];
+        const R acc = sub_dot(As[(size_t)r * n + i], 0, a, [&](int b) {
+          return Lw[a * no + b] * As[(size_t)r * n + o0 + b];
+        });
         As[(size_t)r * n + i] = acc / Lw[a * no + a];
       }
     __syncthreads();
@@ -927,8 +955,9 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
       for (int i = threadIdx.x; i < n; i += kThreads) {
         R* v = V + (size_t)i * nb;
         for (int s2 = 0; s2 < nb; ++s2) {
-          R acc = v[s2];
-          for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * v[p];
+          const R acc = sub_dot(v[s2], 0, s2, [&](int p) {
+            return G[s2 * nb + p] * v[p];
+          });
           v[s2] = acc / G[s2 * nb + s2];
         }
       }
@@ -1015,8 +1044,9 @@ __global__ void __launch_bounds__(kThreads)
         const R* zt = T1 + (size_t)i * nb;
         R* zr = Z + (size_t)i * nb;
         for (int s2 = 0; s2 < nb; ++s2) {
-          R acc = zt[s2];
-          for (int p = 0; p < s2; ++p) acc -= G[s2 * nb + p] * zr[p];
+          const R acc = sub_dot(zt[s2], 0, s2, [&](int p) {
+            return G[s2 * nb + p] * zr[p];
+          });
           zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : R(0.0);
         }
       }
@@ -1034,8 +1064,9 @@ __global__ void __launch_bounds__(kThreads)
       const int cc = c < nb ? c : c - nb;
       for (int a = no - 1; a >= 0; --a) {
         const int i = o0 + a;
-        R acc = M_[(size_t)i * nb + cc];
-        for (int b = a + 1; b < no; ++b) acc -= w.L[b * no + a] * M_[(size_t)(o0 + b) * nb + cc];
+        const R acc = sub_dot(M_[(size_t)i * nb + cc], a + 1, no, [&](int b) {
+          return w.L[b * no + a] * M_[(size_t)(o0 + b) * nb + cc];
+        });
         M_[(size_t)i * nb + cc] = acc / w.L[a * no + a];
       }
     }

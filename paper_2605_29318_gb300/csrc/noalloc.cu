@@ -13,14 +13,13 @@
 //
 // Host code must not use the array's name as a device address (on the host it
 // names a stand-in object); the device address is fetched once per device with
-// cudaGetSymbolAddress, with that device current, and cached.  The first call
-// on a device does this set-up, so it should be made before any stream
-// capture.  Every call shares the one array and leaves its contents behind;
-// nothing in it needs to start at zero (each call overwrites every byte it
-// reads).  Calls that overlap on the GPU -- on two streams, or from two
-// threads -- race on the array and must be serialised by the caller.  Like the
-// library's other calls, it synchronises the context's stream before it
-// returns.
+// cudaGetSymbolAddress, with that device current, and cached; the first call
+// on a device does this set-up.  Every call shares the one array and leaves
+// its contents behind; nothing in it needs to start at zero (each call
+// overwrites every byte it reads).  Calls that overlap on the GPU -- on two
+// streams, or from two threads -- race on the array and must be serialised by
+// the caller.  Like the library's other calls, it synchronises the context's
+// stream before it returns.
 #include <mutex>
 
 #include "linalg.cuh"
