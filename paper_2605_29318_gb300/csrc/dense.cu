@@ -105,22 +105,6 @@ __device__ R block_sum(R v, R* red) {
   return warp_sum(t);
 }
 
-// acc - sum_{p0 <= p < p1} term(p), with four independent partial sums so
-// that a long serial substitution keeps several multiply-adds in flight
-template <class R, class F>
-__device__ __forceinline__ R sub_dot(R acc, int p0, int p1, F term) {
-  R a1 = R(0.0), a2 = R(0.0), a3 = R(0.0);
-  int p = p0;
-  for (; p + 3 < p1; p += 4) {
-    acc -= term(p);
-    a1 -= term(p + 1);
-    a2 -= term(p + 2);
-    a3 -= term(p + 3);
-  }
-  for (; p < p1; ++p) acc -= term(p);
-  return (acc + a1) + (a2 + a3);
-}
-
 // right-looking Cholesky (lower) of an m x m matrix in place, with drop.  Step
 // j subtracts g_ij g_lj / g_jj from the trailing lower triangle (a warp per
 // row, lanes along the row) using the unscaled column j; column j is scaled
@@ -165,6 +149,22 @@ __device__ __forceinline__ R shfl_xor_r(R v, int o) {
 template <>
 __device__ __forceinline__ dfloat shfl_xor_r<dfloat>(dfloat v, int o) {
   return dfloat(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o));
+}
+
+// acc - sum_{p0 <= p < p1} term(p), with four independent partial sums so
+// that a long serial substitution keeps several multiply-adds in flight
+template <class R, class F>
+__device__ __forceinline__ R sub_dot(R acc, int p0, int p1, F term) {
+  R a1 = R(0.0), a2 = R(0.0), a3 = R(0.0);
+  int p = p0;
+  for (; p + 3 < p1; p += 4) {
+    acc -= term(p);
+    a1 -= term(p + 1);
+    a2 -= term(p + 2);
+    a3 -= term(p + 3);
+  }
+  for (; p < p1; ++p) acc -= term(p);
+  return (acc + a1) + (a2 + a3);
 }
 
 // The warp sums of 16 values at once by halving exchanges (16 shuffles
@@ -220,6 +220,43 @@ __device__ void blk_gram_tn(const R* X, int ldx, const R* Y, int ldy, int rows, 
   }
 }
 
+// The same Gram with a thread per 4 x 4 tile running over all rows: the
+// threads of a warp read one row at a time, so global row-major operands are
+// read in whole lines and shared ones without bank conflicts at any stride.
+template <class R>
+__device__ void blk_gram_tn_rows(const R* X, int ldx, const R* Y, int ldy, int rows, int ma,
+                                 int mb, R* C, int ldc, bool lower) {
+  const int ta = (ma + 3) >> 2, tb = (mb + 3) >> 2;
+  for (int t = threadIdx.x; t < ta * tb; t += kThreads) {
+    const int ia = t / tb, ib = t - ia * tb;
+    if (lower && ib > ia) continue;
+    R acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
+    for (int i = 0; i < rows; ++i) {
+      R xa[4], yb[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        xa[r] = 4 * ia + r < ma ? X[(size_t)i * ldx + 4 * ia + r] : R(0.0);
+        yb[r] = 4 * ib + r < mb ? Y[(size_t)i * ldy + 4 * ib + r] : R(0.0);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += xa[r] * yb[c];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int a = 4 * ia + r, b = 4 * ib + c;
+        if (a < ma && b < mb && (!lower || b <= a)) C[(size_t)a * ldc + b] = acc[r][c];
+      }
+  }
+}
+
 // C[i][b] = base[i][b] (rows i >= r0; zero above) + sgn sum_a X[i][a] G[a][b]
 // for i < rows, b < mb, a < ma (row strides ldx, ldg, ldc; base shares C's
 // layout; sgn -1 by default), one 4 x 4 tile of C per thread at a time.
@@ -266,10 +303,12 @@ __global__ void __launch_bounds__(kThreads)
   R* dyn = reinterpret_cast<R*>(dyn_raw);
   __shared__ R red[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const size_t nn = (size_t)n * n;
-  // smem = 1: A in shared memory; smem = 2: also C, U (n x no) and L (no x no)
+  // smem = 1: A in shared memory (and a copy of L once factored); smem = 2:
+  // also C, U (n x no) and L (no x no).  In shared memory A's rows are padded
+  // to an odd stride, so that a thread per row hits distinct banks.
+  const int la = (smem && !do_house) ? (n | 1) : n;
   R* As = smem ? dyn : w.As;
-  R* Cw = smem == 2 ? As + nn : w.C;
+  R* Cw = smem == 2 ? As + (size_t)n * la : w.C;
   R* Uw = smem == 2 ? Cw + (size_t)n * no : w.U;
   R* Lw = smem == 2 ? Uw + (size_t)n * no : w.L;
   R* vt = w.T1;            // n
@@ -293,13 +332,13 @@ __global__ void __launch_bounds__(kThreads)
   // the scaled matrix (rows by warps, columns by lanes), then its symmetric part
   for (int i = wid; i < n; i += kWarps)
     for (int j = lane; j < n; j += 32)
-      As[(size_t)i * n + j] = (R)A[(size_t)i * n + j] * w.dsc[i] * w.dsc[j];
+      As[(size_t)i * la + j] = (R)A[(size_t)i * n + j] * w.dsc[i] * w.dsc[j];
   __syncthreads();
   for (int i = wid; i < n; i += kWarps)
     for (int j = lane; j < i; j += 32) {
-      const R v = R(0.5) * (As[(size_t)i * n + j] + As[(size_t)j * n + i]);
-      As[(size_t)i * n + j] = v;
-      As[(size_t)j * n + i] = v;
+      const R v = R(0.5) * (As[(size_t)i * la + j] + As[(size_t)j * la + i]);
+      As[(size_t)i * la + j] = v;
+      As[(size_t)j * la + i] = v;
     }
   // Second projection of the O block against the rest, in coefficient space.
   // The O columns arrive M-projected against the others once, on the
@@ -321,17 +360,17 @@ __global__ void __launch_bounds__(kThreads)
     }
   __syncthreads();
   R* P2 = w.G;  // no x no scratch (global): C^T A_{.,O}, then C^T C
-  blk_sub_xg(As, n, Cw, no, n, n, no, Cw, n, Uw, no, R(1.0));  // U = A C
-  blk_gram_tn(Cw, no, As + o0, n, n, no, no, P2, no, false);   // C^T A_{.,O}
+  blk_sub_xg(As, la, Cw, no, n, n, no, Cw, n, Uw, no, R(1.0));     // U = A C
+  blk_gram_tn_rows(Cw, no, As + o0, la, n, no, no, P2, no, false);  // C^T A_{.,O}
   __syncthreads();
-  blk_gram_tn(Cw, no, Uw, no, n, no, no, Lw, no, false);       // C^T U (in L for now)
+  blk_gram_tn_rows(Cw, no, Uw, no, n, no, no, Lw, no, false);  // C^T U (in L for now)
   __syncthreads();
   for (int a = wid; a < no; a += kWarps)  // A_OO += C^T U - C^T A_{.,O} - (C^T A_{.,O})^T
     for (int b = lane; b < no; b += 32)
-      As[(size_t)(o0 + a) * n + o0 + b] +=
+      As[(size_t)(o0 + a) * la + o0 + b] +=
           Lw[(size_t)a * no + b] - P2[(size_t)a * no + b] - P2[(size_t)b * no + a];
   __syncthreads();
-  blk_gram_tn(Cw, no, Cw, no, n, no, no, P2, no, false);  // C^T C
+  blk_gram_tn_rows(Cw, no, Cw, no, n, no, no, P2, no, false);  // C^T C
   __syncthreads();
   for (int a = wid; a < no; a += kWarps)
     for (int b = lane; b < no; b += 32) {
@@ -347,36 +386,42 @@ __global__ void __launch_bounds__(kThreads)
     if (i >= o0 && i < o1) continue;
     for (int b = lane; b < no; b += 32) {
       const int j = o0 + b;
-      const R v = As[(size_t)i * n + j] - Uw[(size_t)i * no + b];
-      As[(size_t)i * n + j] = v;
-      As[(size_t)j * n + i] = v;
+      const R v = As[(size_t)i * la + j] - Uw[(size_t)i * no + b];
+      As[(size_t)i * la + j] = v;
+      As[(size_t)j * la + i] = v;
     }
   }
   __syncthreads();
   block_cholesky(Lw, no, w.keep + o0, drop);
-  // A <- T^T A T: O rows by L^-1, then O columns.  A thread's forward
-  // substitution reads only the entries of its own column (row) that it wrote
-  // itself, so the whole substitution runs without barriers.
-  {
-    for (int c = tid; c < n; c += kThreads)
-      for (int a = 0; a < no; ++a) {
-        const int i = o0 + a;
-        const R acc = sub_dot(As[(size_t)i * n + c], 0, a, [&](int b) {
-          return Lw[a * no + b] * As[(size_t)(o0 + b) * n + c];
-        });
-        As[(size_t)i * n + c] = acc / Lw[a * no + a];
-      }
-    __syncthreads();
-    for (int r = tid; r < n; r += kThreads)
-      for (int a = 0; a < no; ++a) {
-        const int i = o0 + a;
-        const R acc = sub_dot(As[(size_t)r * n + i], 0, a, [&](int b) {
-          return Lw[a * no + b] * As[(size_t)r * n + o0 + b];
-        });
-        As[(size_t)r * n + i] = acc / Lw[a * no + a];
-      }
+  // A <- T^T A T: O rows by L^-1, then O columns.  With A alone in shared
+  // memory the factor is copied beside it first (its entries are read by
+  // every thread at every step).
+  if (smem == 1) {
+    R* Ls = As + (size_t)n * la;
+    for (int t = tid; t < no * no; t += kThreads) Ls[t] = Lw[t];
+    Lw = Ls;
     __syncthreads();
   }
+  // a thread's forward substitution reads only the entries of its own column
+  // (row) that it wrote itself: no barriers inside
+  for (int c = tid; c < n; c += kThreads)
+    for (int a = 0; a < no; ++a) {
+      const int i = o0 + a;
+      const R acc = sub_dot(As[(size_t)i * la + c], 0, a, [&](int b) {
+        return Lw[a * no + b] * As[(size_t)(o0 + b) * la + c];
+      });
+      As[(size_t)i * la + c] = acc / Lw[a * no + a];
+    }
+  __syncthreads();
+  for (int r = tid; r < n; r += kThreads)
+    for (int a = 0; a < no; ++a) {
+      const int i = o0 + a;
+      const R acc = sub_dot(As[(size_t)r * la + i], 0, a, [&](int b) {
+        return Lw[a * no + b] * As[(size_t)r * la + o0 + b];
+      });
+      As[(size_t)r * la + i] = acc / Lw[a * no + a];
+    }
+  __syncthreads();
   // symmetrise; dropped columns are decoupled with a diagonal just above the
   // spectrum of the kept part (2 ||A_kept||_inf + 1), which keeps them out of
   // the nb lowest without disturbing the scale of the tridiagonal problem
@@ -385,7 +430,7 @@ __global__ void __launch_bounds__(kThreads)
     if (!w.keep[i]) continue;
     R rs = R(0.0);
     for (int j = lane; j < n; j += 32)
-      if (w.keep[j]) rs += fabs(As[(size_t)i * n + j]);
+      if (w.keep[j]) rs += fabs(As[(size_t)i * la + j]);
     rmax = fmax(rmax, warp_sum(rs));
   }
   {
@@ -405,13 +450,13 @@ __global__ void __launch_bounds__(kThreads)
       if (!w.keep[i] || !w.keep[j])
         v = (i == j) ? big : R(0.0);
       else
-        v = i > j ? R(0.5) * (As[(size_t)i * n + j] + As[(size_t)j * n + i]) : As[(size_t)i * n + j];
-      As[(size_t)i * n + j] = v;
+        v = i > j ? R(0.5) * (As[(size_t)i * la + j] + As[(size_t)j * la + i]) : As[(size_t)i * la + j];
+      As[(size_t)i * la + j] = v;
     }
   __syncthreads();
   for (int i = wid; i < n; i += kWarps)
     for (int j = lane; j < n; j += 32)
-      if (i < j) As[(size_t)i * n + j] = As[(size_t)j * n + i];
+      if (i < j) As[(size_t)i * la + j] = As[(size_t)j * la + i];
   __syncthreads();
   if (smem == 2) {  // L and C are read by the later kernels
     for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
@@ -419,7 +464,8 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (!do_house) {  // hand the transformed matrix to the cluster reduction
     if (smem)
-      for (size_t t = tid; t < nn; t += kThreads) w.As[t] = As[t];
+      for (int i = wid; i < n; i += kWarps)
+        for (int j = lane; j < n; j += 32) w.As[(size_t)i * n + j] = As[(size_t)i * la + j];
     return;
   }
   // Householder: reflector j = [1, v] stored in row j of w.ref (entries j+1..n-1)
@@ -427,18 +473,18 @@ __global__ void __launch_bounds__(kThreads)
     const int m = n - j - 1;
     R part = R(0.0);
     for (int i = tid; i < m; i += kThreads) {
-      const R x = As[(size_t)(j + 1 + i) * n + j];
+      const R x = As[(size_t)(j + 1 + i) * la + j];
       part += x * x;
     }
     const R ss = block_sum(part, red);
-    const R x0 = As[(size_t)(j + 1) * n + j];
+    const R x0 = As[(size_t)(j + 1) * la + j];
     const R alpha = sqrt(ss);
     __syncthreads();
     if (!(alpha > Prec<R>::tiny)) {
       if (tid == 0) {
         w.tau[j] = R(0.0);
         w.e[j] = x0;
-        w.dg[j] = As[(size_t)j * n + j];
+        w.dg[j] = As[(size_t)j * la + j];
       }
       __syncthreads();
       continue;
@@ -447,14 +493,14 @@ __global__ void __launch_bounds__(kThreads)
     const R tj = (beta - x0) / beta;
     const R scale = R(1.0) / (x0 - beta);
     for (int i = tid; i < m; i += kThreads) {
-      const R v = i == 0 ? R(1.0) : As[(size_t)(j + 1 + i) * n + j] * scale;
+      const R v = i == 0 ? R(1.0) : As[(size_t)(j + 1 + i) * la + j] * scale;
       vt[i] = v;
       w.ref[(size_t)j * n + j + 1 + i] = v;
     }
     if (tid == 0) {
       w.tau[j] = tj;
       w.e[j] = beta;
-      w.dg[j] = As[(size_t)j * n + j];
+      w.dg[j] = As[(size_t)j * la + j];
     }
     __syncthreads();
     for (int i = wid; i < m; i += kWarps) {  // p = tau A22 v
@@ -480,11 +526,11 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (tid == 0) {
     if (n >= 2) {
-      w.dg[n - 2] = As[(size_t)(n - 2) * n + (n - 2)];
-      w.e[n - 2] = As[(size_t)(n - 1) * n + (n - 2)];
+      w.dg[n - 2] = As[(size_t)(n - 2) * la + (n - 2)];
+      w.e[n - 2] = As[(size_t)(n - 1) * la + (n - 2)];
       w.tau[n - 2] = R(0.0);
     }
-    w.dg[n - 1] = As[(size_t)(n - 1) * n + (n - 1)];
+    w.dg[n - 1] = As[(size_t)(n - 1) * la + (n - 1)];
     w.e[n - 1] = R(0.0);
     w.tau[n - 1] = R(0.0);
   }
@@ -921,15 +967,20 @@ template <class R, bool SM>
 __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R> w) {
   __shared__ int keep_nb[512];
   extern __shared__ __align__(16) unsigned char cq_raw[];
+  // in shared memory V's rows are padded to an odd stride, so that a thread
+  // per row (and the Gram's lanes over rows) hit distinct banks
+  const int lv = SM ? (nb | 1) : nb;
   R* V = SM ? reinterpret_cast<R*>(cq_raw) : w.V;
-  R* G = SM ? V + (size_t)n * nb : w.G;
+  R* G = SM ? V + (size_t)n * lv : w.G;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (SM) {
-    for (int t = threadIdx.x; t < n * nb; t += kThreads) V[t] = w.V[t];
+    for (int i = wid; i < n; i += kWarps)
+      for (int c = lane; c < nb; c += 32) V[(size_t)i * lv + c] = w.V[(size_t)i * nb + c];
     __syncthreads();
   }
   __shared__ float s_off[kWarps];
   for (int pass = 0; pass < 2; ++pass) {
-    blk_gram_tn(V, nb, V, nb, n, nb, nb, G, nb, true);
+    blk_gram_tn(V, lv, V, lv, n, nb, nb, G, nb, true);
     for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
     // largest off-diagonal of the normalised Gram matrix: at most 1e-3 means
@@ -951,22 +1002,19 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
       for (int q = 0; q < kWarps; ++q) off = fmaxf(off, s_off[q]);
     }
     block_cholesky(G, nb, keep_nb, R(0.0));
-    {  // V <- V L^-T, a thread per row
-      for (int i = threadIdx.x; i < n; i += kThreads) {
-        R* v = V + (size_t)i * nb;
-        for (int s2 = 0; s2 < nb; ++s2) {
-          const R acc = sub_dot(v[s2], 0, s2, [&](int p) {
-            return G[s2 * nb + p] * v[p];
-          });
-          v[s2] = acc / G[s2 * nb + s2];
-        }
+    for (int i = threadIdx.x; i < n; i += kThreads) {  // V <- V L^-T, a thread per row
+      R* v = V + (size_t)i * lv;
+      for (int s2 = 0; s2 < nb; ++s2) {
+        const R acc = sub_dot(v[s2], 0, s2, [&](int p) { return G[s2 * nb + p] * v[p]; });
+        v[s2] = acc / G[s2 * nb + s2];
       }
-      __syncthreads();
     }
+    __syncthreads();
     if (pass == 0 && nb * 1e-3f < 0.5f && off <= 1e-3f) break;  // one pass is enough
   }
   if (SM)
-    for (int t = threadIdx.x; t < n * nb; t += kThreads) w.V[t] = V[t];
+    for (int i = wid; i < n; i += kWarps)
+      for (int c = lane; c < nb; c += 32) w.V[(size_t)i * nb + c] = V[(size_t)i * lv + c];
 }
 
 // ------------------------------------------------------------------ 4b. back-transform, one warp per vector
@@ -1010,72 +1058,78 @@ __global__ void __launch_bounds__(kThreads)
                   T* __restrict__ YZ, int* __restrict__ dropped) {
   __shared__ int keep_nb[512];
   const int tid = threadIdx.x;
-  // SM: V, Z, T1 (n x nb each) and G staged in shared memory (dynamic)
+  // SM: V, Z, T1 (n x nb each, rows padded to an odd stride so that a thread
+  // per row hits distinct banks) and G staged in shared memory (dynamic)
   extern __shared__ __align__(16) unsigned char mo_raw[];
+  const int lv = SM ? (nb | 1) : nb;
+  const int lane = tid & 31, wid = tid >> 5;
   R* V = SM ? reinterpret_cast<R*>(mo_raw) : w.V;
-  R* Z = SM ? V + (size_t)n * nb : w.Z;
-  R* T1 = SM ? Z + (size_t)n * nb : w.T1;
-  R* G = SM ? T1 + (size_t)n * nb : w.G;
+  R* Z = SM ? V + (size_t)n * lv : w.Z;
+  R* T1 = SM ? Z + (size_t)n * lv : w.T1;
+  R* G = SM ? T1 + (size_t)n * lv : w.G;
   if (SM) {
-    for (int t = tid; t < n * nb; t += kThreads) V[t] = w.V[t];
+    for (int i = wid; i < n; i += kWarps)
+      for (int c = lane; c < nb; c += 32) V[(size_t)i * lv + c] = w.V[(size_t)i * nb + c];
     __syncthreads();
   }
   if (want_p) {
     // G = V^T Zp with Zp = V without its X rows, summed over the W and P rows
     // directly: I - V_X^T V_X would cancel catastrophically once the X rows of
     // V are nearly the identity (a converging block)
-    blk_gram_tn(V + (size_t)nx * nb, nb, V + (size_t)nx * nb, nb, n - nx, nb, nb, G, nb, false);
+    blk_gram_tn(V + (size_t)nx * lv, lv, V + (size_t)nx * lv, lv, n - nx, nb, nb, G, nb, false);
   
     __syncthreads();
 // Z = Zp - V G
-    blk_sub_xg(V, nb, G, nb, n, nb, nb, V, nx, T1, nb);
+    blk_sub_xg(V, lv, G, nb, n, nb, nb, V, nx, T1, lv);
   
     __syncthreads();
 // G = Z^T Z (lower)
-    blk_gram_tn(T1, nb, T1, nb, n, nb, nb, G, nb, true);
+    blk_gram_tn(T1, lv, T1, lv, n, nb, nb, G, nb, true);
   
     for (int s2 = tid; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
     R gref = R(0.0);
     for (int s2 = 0; s2 < nb; ++s2) gref = fmax(gref, G[s2 * nb + s2]);
     block_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
-    {  // Z <- Z L^-T, dropped columns zero, a thread per row
-      for (int i = tid; i < n; i += kThreads) {
-        const R* zt = T1 + (size_t)i * nb;
-        R* zr = Z + (size_t)i * nb;
-        for (int s2 = 0; s2 < nb; ++s2) {
-          const R acc = sub_dot(zt[s2], 0, s2, [&](int p) {
-            return G[s2 * nb + p] * zr[p];
-          });
-          zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : R(0.0);
-        }
-      }
-      __syncthreads();
-    }
-  }
-  // back to the coefficients of the original basis: y_O <- L^-T y_O, then
-  // y_rest <- y_rest - C y_O and y <- D y (k_rr_output)
-  {
-    // a thread per column, its back substitution reading only entries it
-    // wrote: no barriers
-    for (int c = tid; c < 2 * nb; c += kThreads) {
-      if (c >= nb && !want_p) continue;
-      R* M_ = c < nb ? V : Z;
-      const int cc = c < nb ? c : c - nb;
-      for (int a = no - 1; a >= 0; --a) {
-        const int i = o0 + a;
-        const R acc = sub_dot(M_[(size_t)i * nb + cc], a + 1, no, [&](int b) {
-          return w.L[b * no + a] * M_[(size_t)(o0 + b) * nb + cc];
-        });
-        M_[(size_t)i * nb + cc] = acc / w.L[a * no + a];
+    for (int i = tid; i < n; i += kThreads) {  // Z <- Z L^-T, dropped columns zero
+      const R* zt = T1 + (size_t)i * lv;
+      R* zr = Z + (size_t)i * lv;
+      for (int s2 = 0; s2 < nb; ++s2) {
+        const R acc = sub_dot(zt[s2], 0, s2, [&](int p) { return G[s2 * nb + p] * zr[p]; });
+        zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : R(0.0);
       }
     }
     __syncthreads();
   }
+  // back to the coefficients of the original basis: y_O <- L^-T y_O (the
+  // factor staged in G's place when in shared memory), then y_rest <- y_rest
+  // - C y_O and y <- D y (k_rr_output)
+  const R* Lf = w.L;
+  if (SM && no <= nb) {
+    for (int t = tid; t < no * no; t += kThreads) G[t] = w.L[t];
+    Lf = G;
+    __syncthreads();
+  }
+  // a thread per column, its back substitution reading only entries it wrote
+  for (int c = tid; c < 2 * nb; c += kThreads) {
+    if (c >= nb && !want_p) continue;
+    R* M_ = c < nb ? V : Z;
+    const int cc = c < nb ? c : c - nb;
+    for (int a = no - 1; a >= 0; --a) {
+      const int i = o0 + a;
+      const R acc = sub_dot(M_[(size_t)i * lv + cc], a + 1, no, [&](int b) {
+        return Lf[b * no + a] * M_[(size_t)(o0 + b) * lv + cc];
+      });
+      M_[(size_t)i * lv + cc] = acc / Lf[a * no + a];
+    }
+  }
+  __syncthreads();
   if (SM) {
-    for (int t = tid; t < n * nb; t += kThreads) w.V[t] = V[t];
+    for (int i = wid; i < n; i += kWarps)
+      for (int c = lane; c < nb; c += 32) w.V[(size_t)i * nb + c] = V[(size_t)i * lv + c];
     if (want_p)
-      for (int t = tid; t < n * nb; t += kThreads) w.Z[t] = Z[t];
+      for (int i = wid; i < n; i += kWarps)
+        for (int c = lane; c < nb; c += 32) w.Z[(size_t)i * nb + c] = Z[(size_t)i * lv + c];
   }
   if (tid == 0) {
     int dc = 0;
@@ -1216,8 +1270,8 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
                          (const void*)k_rr_house_cluster<R>, (const void*)k_rr_invit_sm<R>,
                          (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
-  const size_t tri_bytes = sizeof(R) * n * n;
-  const size_t tri2_bytes = sizeof(R) * (n * n + 2 * n * no + no * no);
+  const size_t tri_bytes = sizeof(R) * (n * (n | 1) + no * no);
+  const size_t tri2_bytes = sizeof(R) * (n * (n | 1) + 2 * n * no + no * no);
   const int tri_smem = tri2_bytes <= kMaxDynSmem ? 2 : tri_bytes <= kMaxDynSmem ? 1 : 0;
   const size_t rpc = (n + kCS - 1) / kCS;
   const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * n + kCS * kCW + 4 * rpc + 2 * kCW);
@@ -1244,7 +1298,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
     (k_rr_invit<R><<<(unsigned)((nb + 31) / 32), 32, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
-  const size_t cq_bytes = sizeof(R) * (n * nb + nb * nb);
+  const size_t cq_bytes = sizeof(R) * (n * (nb | 1) + nb * nb);
   if (cq_bytes <= kMaxDynSmem)
     (k_rr_cholqr<R, true><<<1, kThreads, cq_bytes, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   else
@@ -1260,7 +1314,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
                                     sizeof(R) * kBW * n, st>>>(d.ns, d.nb, w),
      ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  const size_t mo_bytes = sizeof(R) * (3 * n * nb + nb * nb);
+  const size_t mo_bytes = sizeof(R) * (3 * n * (nb | 1) + nb * nb);
   if (mo_bytes <= kMaxDynSmem)
     (k_rr_momentum<R, T, true><<<1, kThreads, mo_bytes, st>>>(d.ns, d.o0, d.no, d.nx, d.nb,
                                                                d.want_p, w, YZ, dropped),

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, TP == 32 ? 1 : 2)
 // per-pair staging.
 constexpr int kStageCols = 256;
 template <int TP>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, TP == 16 ? 3 : 2)
     k_tset_tiles_once(const int* __restrict__ order, long long nq,
                       const long long* __restrict__ ptr, const int* __restrict__ idx,
                       const float* __restrict__ phi, const float* __restrict__ dphi, long long n1,
