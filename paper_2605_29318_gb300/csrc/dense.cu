@@ -392,16 +392,19 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   __syncthreads();
-  block_cholesky(Lw, no, w.keep + o0, drop);
-  // A <- T^T A T: O rows by L^-1, then O columns.  With A alone in shared
-  // memory the factor is copied beside it first (its entries are read by
-  // every thread at every step).
+  // With A alone in shared memory, B_OO - C^T C is copied beside it and
+  // factored there (the factorisation and the substitutions below read it
+  // every step); the factor goes back to the workspace for the later kernels.
   if (smem == 1) {
     R* Ls = As + (size_t)n * la;
     for (int t = tid; t < no * no; t += kThreads) Ls[t] = Lw[t];
     Lw = Ls;
     __syncthreads();
   }
+  block_cholesky(Lw, no, w.keep + o0, drop);
+  if (smem == 1)
+    for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
+  // A <- T^T A T: O rows by L^-1, then O columns
   // a thread's forward substitution reads only the entries of its own column
   // (row) that it wrote itself: no barriers inside
   for (int c = tid; c < n; c += kThreads)
