@@ -156,10 +156,10 @@ class Clocks:
 # the nodal torus keeps degree 16, the hand-over at 1e-4 and the double-float
 # build of an FP64 context.
 WORKLOAD_DEFAULTS = {
-    "splat": dict(cheb=32, cheb_fp64=64, build_prec="fp32", fp32_tol=3e-5),
-    "torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64", fp32_tol=1e-4),
-    "twoset-torus": dict(cheb=16, cheb_fp64=64, build_prec="fp64", fp32_tol=1e-4),
-    "batch": dict(cheb=16, cheb_fp64=64, build_prec="fp64", fp32_tol=1e-4),
+    "splat": dict(cheb=32, cheb_fp64=48, build_prec="fp32", fp32_tol=3e-5),
+    "torus": dict(cheb=16, cheb_fp64=48, build_prec="fp64", fp32_tol=1e-4),
+    "twoset-torus": dict(cheb=16, cheb_fp64=48, build_prec="fp64", fp32_tol=1e-4),
+    "batch": dict(cheb=16, cheb_fp64=48, build_prec="fp64", fp32_tol=1e-4),
 }
 
 
@@ -860,7 +860,7 @@ def main():
     ap.add_argument("--cheb", type=int, default=None,
                     help="FP32 preconditioner degree (default: 32 for the splat, 16 otherwise)")
     ap.add_argument("--cheb-fp64", type=int, default=None,
-                    help="double-float phase preconditioner degree (default 64)")
+                    help="double-float phase preconditioner degree (default 48)")
     ap.add_argument("--fp32-phase", type=int, default=1, choices=[0, 1],
                     help="FP64 contexts: iterate in FP32 first, then finish in double-float")
     ap.add_argument("--max-iter", type=int, default=500)

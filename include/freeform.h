@@ -189,7 +189,7 @@ typedef struct {
                            0 = FP64 blocks and Rayleigh-Ritz throughout (1) */
   double fp32_tol;      /* residual at which the FP32 phase hands over (1e-4) */
   int cheb_degree_fp64; /* Chebyshev degree of the second phase that follows an FP32 phase;
-                           0 = cheb_degree (64) */
+                           0 = cheb_degree (48) */
   int precond_tc;       /* 1: the preconditioner's H products on tensor cores, with H in
                            BF16 dense tiles of 16-row blocks (block widths 8..120 in steps
                            of 8); 0: sparse FP32 H on CUDA cores (1) */

@@ -194,7 +194,7 @@ void ff_eig_opts_default(ff_eig_opts* o) {
   o->verbose = 0;
   o->fp32_phase = 1;
   o->fp32_tol = 1e-4;
-  o->cheb_degree_fp64 = 64;
+  o->cheb_degree_fp64 = 48;
   o->precond_tc = 1;
   o->precond_compact = 0;
 }

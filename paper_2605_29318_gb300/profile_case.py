@@ -43,7 +43,7 @@ def main(argv):
     if case in ("splat32", "twoset32"):
         ctx.set_build_precision("fp32")
     if case == "splat32":
-        opts = binding.default_opts(cheb_degree=32, cheb_degree_fp64=64, fp32_tol=3e-5)
+        opts = binding.default_opts(cheb_degree=32, cheb_degree_fp64=48, fp32_tol=3e-5)
     if case in ("splat", "splat32"):
         c = synth.gaussian_mixture(1_000_000)
         X, v = torch.from_numpy(c.X).to(dev), torch.from_numpy(c.v).to(dev)

@@ -65,7 +65,7 @@ def test_default_options_without_gpu(lib):
     from paper_2605_29318_gb300 import binding
     o = binding.default_opts()
     assert o.tol == 1e-6 and o.max_iter == 500 and o.cheb_degree == 16 and o.guard == 8
-    assert o.fp32_phase == 1 and o.fp32_tol == 1e-4 and o.cheb_degree_fp64 == 64
+    assert o.fp32_phase == 1 and o.fp32_tol == 1e-4 and o.cheb_degree_fp64 == 48
     assert o.precond_tc == 1 and o.precond_compact == 0
 
 
