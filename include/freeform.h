@@ -139,8 +139,8 @@ ff_status rkpm_build_twoset(ff_ctx* ctx, const float* points, const float* volum
  * default): shape functions, material weights and the assembly's sums in
  * double-float (~2^-47).  FF_PREC_FP32: the shape functions in FP32 (the FP64
  * redo for ill-conditioned moment matrices kept) and the sums within a tile of
- * 24 points in FP32, across tiles in FP64 -- the benchmark spec's precision plan
- * (assembly in FP32; FP64 for the eigensolver's dense steps): H_w and M are
+ * 24 points in FP32, across tiles in FP64 -- assembly in FP32 with FP64-grade
+ * dense steps in the eigensolver: H_w and M are
  * still stored in FP64, with about FP32 accuracy (~1e-7 of their entries),
  * and eigenmodes runs as in any FP64 context, its residuals measured against
  * those stored matrices.  FP32 contexts always build in FP32.

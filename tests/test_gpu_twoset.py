@@ -147,7 +147,7 @@ def test_skinning_weights_of_a_twoset_cloud(prec):
 
 
 def test_fp32_build_in_an_fp64_context():
-    """FP32 build precision (the benchmark spec's plan: FP32 shape functions and
+    """FP32 build precision (the splat benchmark's plan: FP32 shape functions and
     assembly sums, FP64 storage and eigensolver): the shape functions within
     the FP32 tolerance of the oracle's, H_w and M within 1e-4 of their largest
     entry, and the eigenvalues of the unit cube within 1e-5 of the oracle's
