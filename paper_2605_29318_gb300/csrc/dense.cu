@@ -8,10 +8,14 @@
 // chain of launches that hand their results over in a global workspace.
 // GB300 runs FP64 at a small fraction of its FP32 rate on each SM, so every
 // stage that can be spread over SMs is:
-//   k_rr_tridiag        (one block) scale the O block by diag(B_OO)^-1/2,
-//                       Cholesky B_OO = L L^T with drop (dependent or empty
-//                       columns leave the basis, as do columns outside O whose
-//                       B_ii is not ~1: empty momentum directions),
+//   k_rr_proj_c, k_rr_proj_v, k_rr_proj_oo
+//                       (many blocks) scale the O block by diag(B_OO)^-1/2
+//                       (columns outside O whose B_ii is not ~1, empty
+//                       momentum directions, leave the basis) and project the
+//                       O block against the rest once more in coefficient
+//                       space;
+//   k_rr_tridiag        (one block) Cholesky B_OO = L L^T with drop
+//                       (dependent or empty columns leave the basis),
 //                       A <- T^T A T with T = blockdiag(I, L^-T, I); for bases
 //                       too large for the cluster it also tridiagonalises;
 //   k_rr_house_cluster  Householder tridiagonalisation of A by an 8-block
@@ -294,42 +298,154 @@ __device__ void blk_sub_xg(const R* X, int ldx, const R* G, int ldg, int rows, i
   }
 }
 
+// ------------------------------------------------------------------ R(0.) coefficient-space projection
+// The scaling of basis column i: O columns by B_ii^-1/2 (kept when B_ii is
+// positive and finite), the others by 1 (kept when B_ii ~ 1; an empty
+// momentum direction leaves the basis).
+template <class R>
+__device__ __forceinline__ int rr_scale(const double* __restrict__ B, int n, int o0, int no, int i,
+                                        R& s) {
+  const R bii = (R)B[(size_t)i * n + i];
+  int k;
+  if (i >= o0 && i < o0 + no) {
+    k = bii > Prec<R>::tiny && isfinite(bii);
+    s = k ? R(1.0) / sqrt(bii) : R(0.0);
+  } else {
+    k = bii > R(0.25) && bii < R(4.0);
+    s = k ? R(1.0) : R(0.0);
+  }
+  return k;
+}
+
+// Second projection of the O block against the rest, in coefficient space.
+// The O columns arrive M-projected against the others once, on the
+// N-vectors; once they are mostly made of the other columns (a converging
+// block) that projection leaves a coupling of order eps / |remainder|.  With
+// the scaled matrices, C = B_{rest,O} and T = [I, -C; 0, I] (C's rows in O
+// are zero), T^T A T and T^T B T differ from A and B only in
+//   A_{rest,O} <- V = A_{rest,O} - A_{rest,rest} C,
+//   A_OO       <- A_OO - C^T V - (C^T A_{rest,O})^T,
+//   B_OO       <- B_OO - C^T C,
+// and the rest-rest block of B is the identity to rounding ("twice is
+// enough").  Three launches spread this over the SMs: the scaling and C, the
+// rows of V (a block per kPR rows), the O x O blocks (a block per row).
+constexpr int kPR = 8;
+constexpr int kPT = 256;
+
+template <class R>
+__global__ void __launch_bounds__(kPT)
+    k_rr_proj_c(const double* __restrict__ B, int n, int o0, int no, RRWork<R> w) {
+  const long long t = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (t < n) {
+    R s;
+    w.keep[t] = rr_scale(B, n, o0, no, (int)t, s);
+    w.dsc[t] = s;
+    return;
+  }
+  const long long u = t - n;
+  if (u >= (long long)n * no) return;
+  const int i = (int)(u / no), b = (int)(u - (long long)i * no), j = o0 + b;
+  R c = R(0.0);
+  if (!(i >= o0 && i < o0 + no)) {
+    R si, sj;
+    const int ki = rr_scale(B, n, o0, no, i, si), kj = rr_scale(B, n, o0, no, j, sj);
+    if (ki && kj) c = R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * si * sj;
+  }
+  w.C[u] = c;
+}
+
+// the scaled symmetric A: A_ij d_i d_j and A_ji d_j d_i averaged
+template <class R>
+__device__ __forceinline__ R rr_asym(const double* __restrict__ A, int n, const R* dsc, int i,
+                                     int j) {
+  const R di = dsc[i], dj = dsc[j];
+  return R(0.5) * ((R)A[(size_t)i * n + j] * di * dj + (R)A[(size_t)j * n + i] * dj * di);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kPT)
+    k_rr_proj_v(const double* __restrict__ A, int n, int o0, int no, RRWork<R> w) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* at = reinterpret_cast<R*>(dyn_raw);  // kPR x n: the block's rows of the scaled A
+  const int i0 = blockIdx.x * kPR, o1 = o0 + no;
+  for (int t = threadIdx.x; t < kPR * n; t += kPT) {
+    const int k = t / kPR, q = t - k * kPR, i = i0 + q;
+    at[(size_t)q * n + k] = i < n ? rr_asym(A, n, w.dsc, i, k) : R(0.0);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kPR * no; t += kPT) {
+    const int q = t / no, b = t - q * no, i = i0 + q;
+    if (i >= n || (i >= o0 && i < o1)) continue;
+    const R* ar = at + (size_t)q * n;
+    const R* cb = w.C + b;
+    R s[4] = {R(0.0), R(0.0), R(0.0), R(0.0)};
+    for (int seg = 0; seg < 2; ++seg) {
+      const int k0 = seg ? o1 : 0, k1 = seg ? n : o0;
+      int k = k0;
+      for (; k + 4 <= k1; k += 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s[r] += ar[k + r] * cb[(size_t)(k + r) * no];
+      }
+      for (; k < k1; ++k) s[0] += ar[k] * cb[(size_t)k * no];
+    }
+    w.U[(size_t)i * no + b] = ar[o0 + b] - ((s[0] + s[1]) + (s[2] + s[3]));
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(128)
+    k_rr_proj_oo(const double* __restrict__ A, const double* __restrict__ B, int n, int o0, int no,
+                 RRWork<R> w) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* ca = reinterpret_cast<R*>(dyn_raw);  // n: column a of C
+  R* aa = ca + n;                         // n: column o0 + a of the scaled A
+  const int a = blockIdx.x, ia = o0 + a, o1 = o0 + no;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    ca[k] = w.C[(size_t)k * no + a];
+    aa[k] = rr_asym(A, n, w.dsc, k, ia);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < no; b += blockDim.x) {
+    const int ib = o0 + b;
+    R sa[2] = {R(0.0), R(0.0)}, sb[2] = {R(0.0), R(0.0)};
+    for (int seg = 0; seg < 2; ++seg) {
+      const int k0 = seg ? o1 : 0, k1 = seg ? n : o0;
+      for (int k = k0; k < k1; ++k) {
+        const R cb = w.C[(size_t)k * no + b];
+        sa[k & 1] += ca[k] * w.U[(size_t)k * no + b] + cb * aa[k];
+        sb[k & 1] += ca[k] * cb;
+      }
+    }
+    w.G[(size_t)a * no + b] = rr_asym(A, n, w.dsc, ia, ib) - (sa[0] + sa[1]);
+    const R bv = R(0.5) * ((R)B[(size_t)ia * n + ib] + (R)B[(size_t)ib * n + ia]) * w.dsc[ia] *
+                     w.dsc[ib] -
+                 (sb[0] + sb[1]);
+    w.L[(size_t)a * no + b] = (w.keep[ia] && w.keep[ib]) ? bv : (a == b ? R(1.0) : R(0.0));
+  }
+}
+
 // ------------------------------------------------------------------ R(1.) tridiagonalise
 template <class R>
 __global__ void __launch_bounds__(kThreads)
     k_rr_tridiag(const double* __restrict__ A, const double* __restrict__ B, int n, int o0, int no,
-                 RRWork<R> w, int smem, int do_house, R drop) {
+                 RRWork<R> w, int smem, int lsm, int do_house, R drop) {
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   R* dyn = reinterpret_cast<R*>(dyn_raw);
   __shared__ R red[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  // smem = 1: A in shared memory (and a copy of L once factored); smem = 2:
-  // also C, U (n x no) and L (no x no).  In shared memory A's rows are padded
-  // to an odd stride, so that a thread per row hits distinct banks.
+  // smem = 1: A in shared memory (rows padded to an odd stride, so that a
+  // thread per row hits distinct banks); lsm = 1: a copy of B_OO - C^T C in
+  // shared memory, factored there (the factorisation and the substitutions
+  // read it every step), after A when A is there too.
   const int la = (smem && !do_house) ? (n | 1) : n;
   R* As = smem ? dyn : w.As;
-  R* Cw = smem == 2 ? As + (size_t)n * la : w.C;
-  R* Uw = smem == 2 ? Cw + (size_t)n * no : w.U;
-  R* Lw = smem == 2 ? Uw + (size_t)n * no : w.L;
+  R* Lw = w.L;
   R* vt = w.T1;            // n
   R* pw = w.T1 + n;        // n
-  // scaling: O columns by diag(B)^-1/2; other columns must have B_ii ~ 1
-  for (int i = tid; i < n; i += kThreads) {
-    const R bii = (R)B[(size_t)i * n + i];
-    R s = R(1.0);
-    int k = 1;
-    if (i >= o0 && i < o0 + no) {
-      k = bii > Prec<R>::tiny && isfinite(bii);
-      s = k ? R(1.0) / sqrt(bii) : R(0.0);
-    } else if (!(bii > R(0.25) && bii < R(4.0))) {
-      k = 0;
-      s = R(0.0);
-    }
-    w.keep[i] = k;
-    w.dsc[i] = s;
-  }
-  __syncthreads();
-  // the scaled matrix (rows by warps, columns by lanes), then its symmetric part
+  const int o1 = o0 + no;
+  // the scaled matrix (rows by warps, columns by lanes) and its symmetric
+  // part; then the projected blocks (scaling, keep flags, V, the O x O
+  // blocks of A and B come from the projection launches)
   for (int i = wid; i < n; i += kWarps)
     for (int j = lane; j < n; j += 32)
       As[(size_t)i * la + j] = (R)A[(size_t)i * n + j] * w.dsc[i] * w.dsc[j];
@@ -340,69 +456,27 @@ __global__ void __launch_bounds__(kThreads)
       As[(size_t)i * la + j] = v;
       As[(size_t)j * la + i] = v;
     }
-  // Second projection of the O block against the rest, in coefficient space.
-  // The O columns arrive M-projected against the others once, on the
-  // N-vectors; once they are mostly made of the other columns (a converging
-  // block) that projection leaves a coupling of order eps / |remainder|.  With
-  // C = B_{rest,O} (scaled) and T = [I, -C; 0, I], A <- T^T A T and
-  // B_OO <- B_OO - C^T C take it out ("twice is enough"); the rest-rest block
-  // of B is the identity to rounding.  C's rows in O are zero, so the sums
-  // over the rest run over all rows.
-  const int o1 = o0 + no;
-  for (int i = wid; i < n; i += kWarps)
-    for (int b = lane; b < no; b += 32) {
-      const int j = o0 + b;
-      const bool in_o = i >= o0 && i < o1;
-      Cw[(size_t)i * no + b] =
-          (!in_o && w.keep[i] && w.keep[j])
-              ? R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] * w.dsc[j]
-              : R(0.0);
-    }
   __syncthreads();
-  R* P2 = w.G;  // no x no scratch (global): C^T A_{.,O}, then C^T C
-  blk_sub_xg(As, la, Cw, no, n, n, no, Cw, n, Uw, no, R(1.0));     // U = A C
-  blk_gram_tn_rows(Cw, no, As + o0, la, n, no, no, P2, no, false);  // C^T A_{.,O}
-  __syncthreads();
-  blk_gram_tn_rows(Cw, no, Uw, no, n, no, no, Lw, no, false);  // C^T U (in L for now)
-  __syncthreads();
-  for (int a = wid; a < no; a += kWarps)  // A_OO += C^T U - C^T A_{.,O} - (C^T A_{.,O})^T
-    for (int b = lane; b < no; b += 32)
-      As[(size_t)(o0 + a) * la + o0 + b] +=
-          Lw[(size_t)a * no + b] - P2[(size_t)a * no + b] - P2[(size_t)b * no + a];
-  __syncthreads();
-  blk_gram_tn_rows(Cw, no, Cw, no, n, no, no, P2, no, false);  // C^T C
-  __syncthreads();
-  for (int a = wid; a < no; a += kWarps)
-    for (int b = lane; b < no; b += 32) {
-      const int i = o0 + a, j = o0 + b;
-      const R v = R(0.5) * ((R)B[(size_t)i * n + j] + (R)B[(size_t)j * n + i]) * w.dsc[i] *
-                      w.dsc[j] -
-                  P2[(size_t)a * no + b];
-      Lw[(size_t)a * no + b] = (w.keep[i] && w.keep[j]) ? v : (a == b ? R(1.0) : R(0.0));
-    }
-
-  __syncthreads();
-  for (int i = wid; i < n; i += kWarps) {  // A_{rest,O} -= U (and its mirror)
-    if (i >= o0 && i < o1) continue;
-    for (int b = lane; b < no; b += 32) {
-      const int j = o0 + b;
-      const R v = As[(size_t)i * la + j] - Uw[(size_t)i * no + b];
-      As[(size_t)i * la + j] = v;
-      As[(size_t)j * la + i] = v;
+  for (int i = wid; i < n; i += kWarps) {
+    if (i >= o0 && i < o1) {
+      for (int b = lane; b < no; b += 32)
+        As[(size_t)i * la + o0 + b] = w.G[(size_t)(i - o0) * no + b];
+    } else {
+      for (int b = lane; b < no; b += 32) {
+        const R v = w.U[(size_t)i * no + b];
+        As[(size_t)i * la + o0 + b] = v;
+        As[(size_t)(o0 + b) * la + i] = v;
+      }
     }
   }
-  __syncthreads();
-  // With A alone in shared memory, B_OO - C^T C is copied beside it and
-  // factored there (the factorisation and the substitutions below read it
-  // every step); the factor goes back to the workspace for the later kernels.
-  if (smem == 1) {
-    R* Ls = As + (size_t)n * la;
+  if (lsm) {
+    R* Ls = dyn + (smem ? (size_t)n * la : 0);
     for (int t = tid; t < no * no; t += kThreads) Ls[t] = Lw[t];
     Lw = Ls;
-    __syncthreads();
   }
+  __syncthreads();
   block_cholesky(Lw, no, w.keep + o0, drop);
-  if (smem == 1)
+  if (lsm)
     for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
   // A <- T^T A T: O rows by L^-1, then O columns
   // a thread's forward substitution reads only the entries of its own column
@@ -461,10 +535,6 @@ __global__ void __launch_bounds__(kThreads)
     for (int j = lane; j < n; j += 32)
       if (i < j) As[(size_t)i * la + j] = As[(size_t)j * la + i];
   __syncthreads();
-  if (smem == 2) {  // L and C are read by the later kernels
-    for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
-    for (int t = tid; t < n * no; t += kThreads) w.C[t] = Cw[t];
-  }
   if (!do_house) {  // hand the transformed matrix to the cluster reduction
     if (smem)
       for (int i = wid; i < n; i += kWarps)
@@ -1271,18 +1341,33 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.keep = reinterpret_cast<int*>(p);
   for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
                          (const void*)k_rr_house_cluster<R>, (const void*)k_rr_invit_sm<R>,
-                         (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>})
+                         (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>,
+                         (const void*)k_rr_proj_v<R>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
-  const size_t tri_bytes = sizeof(R) * (n * (n | 1) + no * no);
-  const size_t tri2_bytes = sizeof(R) * (n * (n | 1) + 2 * n * no + no * no);
-  const int tri_smem = tri2_bytes <= kMaxDynSmem ? 2 : tri_bytes <= kMaxDynSmem ? 1 : 0;
+  const size_t a_bytes = sizeof(R) * n * (n | 1), l_bytes = sizeof(R) * no * no;
+  const int tri_smem = a_bytes + l_bytes <= kMaxDynSmem ? 1 : 0;
+  const int tri_lsm = l_bytes <= kMaxDynSmem ? 1 : 0;
+  const size_t tri_bytes = (tri_smem ? a_bytes : 0) + (tri_lsm ? l_bytes : 0);
   const size_t rpc = (n + kCS - 1) / kCS;
   const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * n + kCS * kCW + 4 * rpc + 2 * kCW);
   const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
   const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
-  // transform (one block); Householder by the cluster when its rows fit
-  (k_rr_tridiag<R><<<1, kThreads, tri_smem == 2 ? tri2_bytes : tri_smem ? tri_bytes : 0, st>>>(
-       A, B, d.ns, d.o0, d.no, w, tri_smem, use_cluster ? 0 : 1, drop),
+  // scaling and projection (many blocks), transform (one block); Householder
+  // by the cluster when its rows fit
+  (k_rr_proj_c<R><<<(unsigned)((n * no + n + kPT - 1) / kPT), kPT, 0, st>>>(B, d.ns, d.o0, d.no, w),
+   ::ff::note_launch());
+  FF_LAUNCH_CHECK();
+  if (no > 0) {
+    (k_rr_proj_v<R><<<(unsigned)((n + kPR - 1) / kPR), kPT, sizeof(R) * kPR * n, st>>>(
+         A, d.ns, d.o0, d.no, w),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    (k_rr_proj_oo<R><<<(unsigned)no, 128, sizeof(R) * 2 * n, st>>>(A, B, d.ns, d.o0, d.no, w),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
+  (k_rr_tridiag<R><<<1, kThreads, tri_bytes, st>>>(A, B, d.ns, d.o0, d.no, w, tri_smem, tri_lsm,
+                                                   use_cluster ? 0 : 1, drop),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
