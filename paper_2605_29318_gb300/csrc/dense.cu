@@ -109,41 +109,280 @@ __device__ R block_sum(R v, R* red) {
   return warp_sum(t);
 }
 
-// right-looking Cholesky (lower) of an m x m matrix in place, with drop.  Step
-// j subtracts g_ij g_lj / g_jj from the trailing lower triangle (a warp per
-// row, lanes along the row) using the unscaled column j; column j is scaled
-// in step j + 1, when no thread reads it any more, and keep[j] is written then
-// too, so a step costs one barrier.  Every thread takes the pivot decision
-// itself from the same diagonal entry.
+// Blocked one-block dense factorisation and solves, in panels of kPB columns:
+// each panel's few columns are done by short substitutions, and what they
+// change in the rest of the matrix is applied as one product in 4 x 4
+// register tiles over all threads (4 x 4 for 4-byte types: 16 multiply-adds
+// per 8 shared loads; 2 x 4 for 8-byte ones, which would spill), so
+// that the serial part is kPB steps long and the bulk runs at full width.
+constexpr int kPB = 8;
+
+// Cholesky (lower, row-major m x m) of G in place, with drop: column j is
+// kept when keep[j] and its updated pivot g_jj > drop_rel, else it leaves (a
+// zero column with l_jj = 1, keep[j] = 0, updating nothing).  L^T is mirrored
+// into the upper triangle (g_kj = l_jk for k > j), where the solves below read
+// it by rows.  With X (m rows of nx entries, stride ldx) the same elimination
+// is applied to X's rows, which leaves L^-1 X in X (a dropped column's row is
+// left as it is).  Per panel: the kPB x kPB diagonal block by warp 0, the
+// panel's rows below and the panel's rows of X by a thread per row / column
+// (substitutions of at most kPB steps), then the trailing lower triangle and
+// X's rows below in register tiles; three barriers a panel.
 template <class R>
-__device__ void block_cholesky(R* G, int m, int* keep, R drop_rel) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int kprev = 0;
-  R lprev = R(1.0);
-  for (int j = 0; j <= m; ++j) {
-    if (j > 0) {  // finish column j - 1
-      const int c = j - 1;
-      for (int i = j + threadIdx.x; i < m; i += blockDim.x)
-        G[(size_t)i * m + c] = kprev ? G[(size_t)i * m + c] / lprev : R(0.0);
-      if (threadIdx.x == 0) {
-        G[(size_t)c * m + c] = lprev;
-        keep[c] = kprev;
+__device__ void block_cholesky(R* G, int m, int* keep, R drop_rel, R* X = nullptr, int ldx = 0,
+                               int nx = 0) {
+  constexpr int TR = sizeof(R) > 4 ? 2 : 4;  // tile rows: 8-byte types would spill at 4
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int j0 = 0; j0 < m; j0 += kPB) {
+    const int jb = min(kPB, m - j0);
+    R* D = G + (size_t)j0 * m + j0;  // the diagonal block, D[i m + k]
+    if (tid < 32) {
+      for (int j = 0; j < jb; ++j) {
+        const R piv = D[(size_t)j * m + j];
+        const int kj = keep[j0 + j] && piv > drop_rel;
+        const R l = kj ? sqrt(piv) : R(1.0);
+        __syncwarp();
+        if (lane > j && lane < jb) {
+          const R v = kj ? D[(size_t)lane * m + j] / l : R(0.0);
+          D[(size_t)lane * m + j] = v;
+          D[(size_t)j * m + lane] = v;
+        }
+        if (lane == 0) {
+          D[(size_t)j * m + j] = l;
+          keep[j0 + j] = kj;
+        }
+        __syncwarp();
+        for (int e = lane; e < kPB * kPB; e += 32) {
+          const int i = e / kPB, k = e - i * kPB;
+          if (k > j && k <= i && i < jb)
+            D[(size_t)i * m + k] -= D[(size_t)i * m + j] * D[(size_t)k * m + j];
+        }
+        __syncwarp();
       }
     }
-    if (j == m) break;
-    const R piv = G[(size_t)j * m + j];
-    const int kj = keep[j] && piv > drop_rel;
-    const R inv = kj ? R(1.0) / piv : R(0.0);
-    if (kj)
-      for (int i = j + 1 + wid; i < m; i += nw) {
-        const R gij = G[(size_t)i * m + j] * inv;
-        for (int l = j + 1 + lane; l <= i; l += 32) G[(size_t)i * m + l] -= gij * G[(size_t)l * m + j];
+    __syncthreads();
+    const int r0 = j0 + jb, nr = m - r0;
+    // the panel's rows below: l_ij = (g_ij - sum_{p<j} l_ip l_jp) / l_jj
+    for (int i = r0 + tid; i < m; i += blockDim.x) {
+      R* gi = G + (size_t)i * m + j0;
+      R v[kPB];
+#pragma unroll
+      for (int j = 0; j < kPB; ++j) {
+        if (j < jb) {
+          R acc = gi[j];
+#pragma unroll
+          for (int p = 0; p < j; ++p) acc -= v[p] * D[(size_t)j * m + p];
+          v[j] = keep[j0 + j] ? acc / D[(size_t)j * m + j] : R(0.0);
+          gi[j] = v[j];
+          G[(size_t)(j0 + j) * m + i] = v[j];
+        }
       }
-    kprev = kj;
-    lprev = kj ? sqrt(piv) : R(1.0);
+    }
+    // the panel's rows of X: y_j = (x_j - sum_{p<j} l_jp y_p) / l_jj
+    if (X)
+      for (int c = tid; c < nx; c += blockDim.x) {
+        R v[kPB];
+#pragma unroll
+        for (int j = 0; j < kPB; ++j) {
+          if (j < jb) {
+            R acc = X[(size_t)(j0 + j) * ldx + c];
+#pragma unroll
+            for (int p = 0; p < j; ++p) acc -= D[(size_t)j * m + p] * v[p];
+            v[j] = acc / D[(size_t)j * m + j];
+            X[(size_t)(j0 + j) * ldx + c] = v[j];
+          }
+        }
+      }
+    __syncthreads();
+    if (nr > 0) {
+      // trailing lower triangle: g_ik -= sum_j l_ij l_kj (k <= i), 4 x 4 tiles
+      const int ta = (nr + TR - 1) / TR, tt = (nr + 3) >> 2;
+      for (int t = tid; t < ta * tt; t += blockDim.x) {
+        const int ia = t / tt, ib = t - ia * tt;
+        if (4 * ib > TR * ia + TR - 1) continue;  // above the diagonal
+        R acc[TR][4];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
+        for (int j = 0; j < jb; ++j) {
+          R la[TR], lb[4];
+          const R* up = G + (size_t)(j0 + j) * m + r0;  // row j of L^T
+#pragma unroll
+          for (int r = 0; r < TR; ++r) la[r] = TR * ia + r < nr ? up[TR * ia + r] : R(0.0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) lb[c] = 4 * ib + c < nr ? up[4 * ib + c] : R(0.0);
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] += la[r] * lb[c];
+        }
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = TR * ia + r, k = 4 * ib + c;
+            if (i < nr && k <= i) G[(size_t)(r0 + i) * m + r0 + k] -= acc[r][c];
+          }
+      }
+      // X's rows below: x_i -= sum_j l_ij y_j, 4 x 4 tiles over (i, c)
+      if (X) {
+        const int tc = (nx + 3) >> 2;
+        for (int t = tid; t < ta * tc; t += blockDim.x) {
+          const int ia = t / tc, ib = t - ia * tc;
+          R acc[TR][4];
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
+          for (int j = 0; j < jb; ++j) {
+            R la[TR], yb[4];
+            const R* up = G + (size_t)(j0 + j) * m + r0;
+            const R* yj = X + (size_t)(j0 + j) * ldx;
+#pragma unroll
+            for (int r = 0; r < TR; ++r) la[r] = TR * ia + r < nr ? up[TR * ia + r] : R(0.0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) yb[c] = 4 * ib + c < nx ? yj[4 * ib + c] : R(0.0);
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[r][c] += la[r] * yb[c];
+          }
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int i = TR * ia + r, cc = 4 * ib + c;
+              if (i < nr && cc < nx) X[(size_t)(r0 + i) * ldx + cc] -= acc[r][c];
+            }
+        }
+      }
+    }
     __syncthreads();
   }
-  __syncthreads();
+}
+
+// X <- X L^-T for `rows` rows of X (m entries each, stride ldx): every row is
+// a forward substitution along the row.  L is lower (row-major, m x m) with
+// L^T mirrored into its upper triangle, as block_cholesky leaves it.  Per
+// panel: its columns by a thread per row, then the later columns in 4 x 4
+// register tiles (x_k -= sum_j x_j l_kj, l_kj read from the mirror).
+template <class R>
+__device__ void block_trsm_rt(const R* L, int m, R* X, int ldx, int rows) {
+  constexpr int TR = sizeof(R) > 4 ? 2 : 4;
+  const int tid = threadIdx.x;
+  for (int j0 = 0; j0 < m; j0 += kPB) {
+    const int jb = min(kPB, m - j0);
+    const R* D = L + (size_t)j0 * m + j0;
+    for (int a = tid; a < rows; a += blockDim.x) {
+      R* x = X + (size_t)a * ldx + j0;
+      R v[kPB];
+#pragma unroll
+      for (int j = 0; j < kPB; ++j) {
+        if (j < jb) {
+          R acc = x[j];
+#pragma unroll
+          for (int p = 0; p < j; ++p) acc -= v[p] * D[(size_t)j * m + p];
+          v[j] = acc / D[(size_t)j * m + j];
+          x[j] = v[j];
+        }
+      }
+    }
+    __syncthreads();
+    const int k0 = j0 + jb, nk = m - k0;
+    if (nk > 0) {
+      const int ta = (rows + TR - 1) / TR, tb = (nk + 3) >> 2;
+      for (int t = tid; t < ta * tb; t += blockDim.x) {
+        const int ia = t / tb, ib = t - ia * tb;
+        R acc[TR][4];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
+        for (int j = 0; j < jb; ++j) {
+          R xa[TR], lb[4];
+          const R* up = L + (size_t)(j0 + j) * m + k0;
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+            xa[r] = TR * ia + r < rows ? X[(size_t)(TR * ia + r) * ldx + j0 + j] : R(0.0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) lb[c] = 4 * ib + c < nk ? up[4 * ib + c] : R(0.0);
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] += xa[r] * lb[c];
+        }
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int a = TR * ia + r, k = 4 * ib + c;
+            if (a < rows && k < nk) X[(size_t)a * ldx + k0 + k] -= acc[r][c];
+          }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// X <- L^-T X for the m rows of X (nc entries each, stride ldx; L lower,
+// row-major m x m): a backward substitution down every column.  Per panel,
+// from the last: its rows by a thread per column, then the earlier rows in
+// 4 x 4 register tiles (x_b -= sum_j l_jb x_j, l_jb read along row j of L).
+template <class R>
+__device__ void block_trsm_lt(const R* L, int m, R* X, int ldx, int nc) {
+  constexpr int TR = sizeof(R) > 4 ? 2 : 4;
+  const int tid = threadIdx.x;
+  for (int j1 = m; j1 > 0; j1 -= kPB) {
+    const int j0 = max(0, j1 - kPB), jb = j1 - j0;
+    for (int c = tid; c < nc; c += blockDim.x) {
+      R v[kPB];
+#pragma unroll
+      for (int jj = kPB - 1; jj >= 0; --jj) {
+        if (jj < jb) {
+          const int j = j0 + jj;
+          R acc = X[(size_t)j * ldx + c];
+#pragma unroll
+          for (int p = jj + 1; p < kPB; ++p)
+            if (p < jb) acc -= L[(size_t)(j0 + p) * m + j] * v[p];
+          v[jj] = acc / L[(size_t)j * m + j];
+          X[(size_t)j * ldx + c] = v[jj];
+        }
+      }
+    }
+    __syncthreads();
+    if (j0 > 0) {
+      const int ta = (j0 + TR - 1) / TR, tb = (nc + 3) >> 2;
+      for (int t = tid; t < ta * tb; t += blockDim.x) {
+        const int ia = t / tb, ib = t - ia * tb;
+        R acc[TR][4];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
+        for (int j = 0; j < jb; ++j) {
+          R la[TR], xb[4];
+          const R* lj = L + (size_t)(j0 + j) * m;
+          const R* xj = X + (size_t)(j0 + j) * ldx;
+#pragma unroll
+          for (int r = 0; r < TR; ++r) la[r] = TR * ia + r < j0 ? lj[TR * ia + r] : R(0.0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) xb[c] = 4 * ib + c < nc ? xj[4 * ib + c] : R(0.0);
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[r][c] += la[r] * xb[c];
+        }
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int b = TR * ia + r, cc = 4 * ib + c;
+            if (b < j0 && cc < nc) X[(size_t)b * ldx + cc] -= acc[r][c];
+          }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 template <class R>
@@ -428,7 +667,7 @@ __global__ void __launch_bounds__(128)
 template <class R>
 __global__ void __launch_bounds__(kThreads)
     k_rr_tridiag(const double* __restrict__ A, const double* __restrict__ B, int n, int o0, int no,
-                 RRWork<R> w, int smem, int lsm, int do_house, R drop) {
+                 RRWork<R> w, int smem, int lsm, int xsm, int do_house, R drop) {
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   R* dyn = reinterpret_cast<R*>(dyn_raw);
   __shared__ R red[kWarps];
@@ -436,7 +675,8 @@ __global__ void __launch_bounds__(kThreads)
   // smem = 1: A in shared memory (rows padded to an odd stride, so that a
   // thread per row hits distinct banks); lsm = 1: a copy of B_OO - C^T C in
   // shared memory, factored there (the factorisation and the substitutions
-  // read it every step), after A when A is there too.
+  // read it every step), after A when A is there too; xsm = 1 (A in global
+  // memory): A's O rows staged after it while they are transformed.
   const int la = (smem && !do_house) ? (n | 1) : n;
   R* As = smem ? dyn : w.As;
   R* Lw = w.L;
@@ -474,30 +714,33 @@ __global__ void __launch_bounds__(kThreads)
     for (int t = tid; t < no * no; t += kThreads) Ls[t] = Lw[t];
     Lw = Ls;
   }
+  __shared__ int keep_o[1024];  // the O columns' keep flags while factoring
+  for (int a = tid; a < no; a += kThreads) keep_o[a] = w.keep[o0 + a];
   __syncthreads();
-  block_cholesky(Lw, no, w.keep + o0, drop);
+  // A <- T^T A T.  The elimination that factors B_OO - C^T C applies L^-1
+  // to A's O rows on the way (Y = L^-1 A_{O,.}); the rest-O blocks are then
+  // Y's transposes and the O x O block is Y_OO L^-T.
+  R* X = As + (size_t)o0 * la;
+  int ldx = la;
+  if (xsm) {
+    ldx = n | 1;
+    X = dyn + (size_t)no * no;
+    for (int a = wid; a < no; a += kWarps)
+      for (int c = lane; c < n; c += 32) X[(size_t)a * ldx + c] = As[(size_t)(o0 + a) * la + c];
+    __syncthreads();
+  }
+  block_cholesky(Lw, no, keep_o, drop, X, ldx, n);
+  for (int a = tid; a < no; a += kThreads) w.keep[o0 + a] = keep_o[a];
   if (lsm)
     for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
-  // A <- T^T A T: O rows by L^-1, then O columns
-  // a thread's forward substitution reads only the entries of its own column
-  // (row) that it wrote itself: no barriers inside
-  for (int c = tid; c < n; c += kThreads)
-    for (int a = 0; a < no; ++a) {
-      const int i = o0 + a;
-      const R acc = sub_dot(As[(size_t)i * la + c], 0, a, [&](int b) {
-        return Lw[a * no + b] * As[(size_t)(o0 + b) * la + c];
-      });
-      As[(size_t)i * la + c] = acc / Lw[a * no + a];
-    }
-  __syncthreads();
-  for (int r = tid; r < n; r += kThreads)
-    for (int a = 0; a < no; ++a) {
-      const int i = o0 + a;
-      const R acc = sub_dot(As[(size_t)r * la + i], 0, a, [&](int b) {
-        return Lw[a * no + b] * As[(size_t)r * la + o0 + b];
-      });
-      As[(size_t)r * la + i] = acc / Lw[a * no + a];
-    }
+  block_trsm_rt(Lw, no, X + o0, ldx, no);  // Y_OO <- Y_OO L^-T
+  if (xsm)
+    for (int a = wid; a < no; a += kWarps)
+      for (int c = lane; c < n; c += 32) As[(size_t)(o0 + a) * la + c] = X[(size_t)a * ldx + c];
+  for (int i = wid; i < n; i += kWarps) {
+    if (i >= o0 && i < o1) continue;
+    for (int b = lane; b < no; b += 32) As[(size_t)i * la + o0 + b] = X[(size_t)b * ldx + i];
+  }
   __syncthreads();
   // symmetrise; dropped columns are decoupled with a diagonal just above the
   // spectrum of the kept part (2 ||A_kept||_inf + 1), which keeps them out of
@@ -1075,14 +1318,7 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
       for (int q = 0; q < kWarps; ++q) off = fmaxf(off, s_off[q]);
     }
     block_cholesky(G, nb, keep_nb, R(0.0));
-    for (int i = threadIdx.x; i < n; i += kThreads) {  // V <- V L^-T, a thread per row
-      R* v = V + (size_t)i * lv;
-      for (int s2 = 0; s2 < nb; ++s2) {
-        const R acc = sub_dot(v[s2], 0, s2, [&](int p) { return G[s2 * nb + p] * v[p]; });
-        v[s2] = acc / G[s2 * nb + s2];
-      }
-    }
-    __syncthreads();
+    block_trsm_rt(G, nb, V, lv, n);  // V <- V L^-T
     if (pass == 0 && nb * 1e-3f < 0.5f && off <= 1e-3f) break;  // one pass is enough
   }
   if (SM)
@@ -1164,14 +1400,10 @@ __global__ void __launch_bounds__(kThreads)
     R gref = R(0.0);
     for (int s2 = 0; s2 < nb; ++s2) gref = fmax(gref, G[s2 * nb + s2]);
     block_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
-    for (int i = tid; i < n; i += kThreads) {  // Z <- Z L^-T, dropped columns zero
-      const R* zt = T1 + (size_t)i * lv;
-      R* zr = Z + (size_t)i * lv;
-      for (int s2 = 0; s2 < nb; ++s2) {
-        const R acc = sub_dot(zt[s2], 0, s2, [&](int p) { return G[s2 * nb + p] * zr[p]; });
-        zr[s2] = keep_nb[s2] ? acc / G[s2 * nb + s2] : R(0.0);
-      }
-    }
+    block_trsm_rt(G, nb, T1, lv, n);  // Z <- Z L^-T, dropped columns zero
+    for (int i = wid; i < n; i += kWarps)
+      for (int c = lane; c < nb; c += 32)
+        Z[(size_t)i * lv + c] = keep_nb[c] ? T1[(size_t)i * lv + c] : R(0.0);
     __syncthreads();
   }
   // back to the coefficients of the original basis: y_O <- L^-T y_O (the
@@ -1183,20 +1415,8 @@ __global__ void __launch_bounds__(kThreads)
     Lf = G;
     __syncthreads();
   }
-  // a thread per column, its back substitution reading only entries it wrote
-  for (int c = tid; c < 2 * nb; c += kThreads) {
-    if (c >= nb && !want_p) continue;
-    R* M_ = c < nb ? V : Z;
-    const int cc = c < nb ? c : c - nb;
-    for (int a = no - 1; a >= 0; --a) {
-      const int i = o0 + a;
-      const R acc = sub_dot(M_[(size_t)i * lv + cc], a + 1, no, [&](int b) {
-        return Lf[b * no + a] * M_[(size_t)(o0 + b) * lv + cc];
-      });
-      M_[(size_t)i * lv + cc] = acc / Lf[a * no + a];
-    }
-  }
-  __syncthreads();
+  block_trsm_lt(Lf, no, V + (size_t)o0 * lv, lv, nb);
+  if (want_p) block_trsm_lt(Lf, no, Z + (size_t)o0 * lv, lv, nb);
   if (SM) {
     for (int i = wid; i < n; i += kWarps)
       for (int c = lane; c < nb; c += 32) w.V[(size_t)i * nb + c] = V[(size_t)i * lv + c];
@@ -1345,9 +1565,12 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
                          (const void*)k_rr_proj_v<R>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
   const size_t a_bytes = sizeof(R) * n * (n | 1), l_bytes = sizeof(R) * no * no;
+  const size_t x_bytes = sizeof(R) * no * (n | 1);
   const int tri_smem = a_bytes + l_bytes <= kMaxDynSmem ? 1 : 0;
   const int tri_lsm = l_bytes <= kMaxDynSmem ? 1 : 0;
-  const size_t tri_bytes = (tri_smem ? a_bytes : 0) + (tri_lsm ? l_bytes : 0);
+  const int tri_xsm = !tri_smem && l_bytes + x_bytes <= kMaxDynSmem ? 1 : 0;
+  const size_t tri_bytes =
+      (tri_smem ? a_bytes : 0) + (tri_lsm ? l_bytes : 0) + (tri_xsm ? x_bytes : 0);
   const size_t rpc = (n + kCS - 1) / kCS;
   const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * n + kCS * kCW + 4 * rpc + 2 * kCW);
   const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
@@ -1367,7 +1590,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
     FF_LAUNCH_CHECK();
   }
   (k_rr_tridiag<R><<<1, kThreads, tri_bytes, st>>>(A, B, d.ns, d.o0, d.no, w, tri_smem, tri_lsm,
-                                                   use_cluster ? 0 : 1, drop),
+                                                   tri_xsm, use_cluster ? 0 : 1, drop),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
