@@ -882,8 +882,8 @@ __device__ int sturm(const R* d, const R* e2, int n, R x) {
 
 // ------------------------------------------------------------------ 1b. cluster Householder
 // Householder tridiagonalisation of the transformed n x n matrix (w.As) by a
-// cluster of kCS thread blocks: row r lives in block r % kCS (distributed
-// shared memory), so the O(n^3) work is spread over kCS SMs.  Every block
+// cluster of CS thread blocks: row r lives in block r % CS (distributed
+// shared memory), so the O(n^3) work is spread over CS SMs.  Every block
 // holds column j of the current matrix (cf, two buffers); a step
 //   1. forms the reflector in every warp (the norm by a warp reduction over
 //      the block's copy of column j: the same values everywhere, no barrier;
@@ -891,37 +891,38 @@ __device__ int sturm(const R* d, const R* e2, int n, R x) {
 //   2. computes p = tau A v for the block's rows (a warp per row, four rows
 //      at a time) and publishes p, the warps' shares of p^T v and the rows'
 //      entries of column j+1 before the update;
-//   3. after one cluster barrier, gathers in one round of remote loads (one
-//      or two per thread) p, the column-j+1 entries and the shares of all
+//   3. after one cluster barrier, gathers in one round of remote loads (at
+//      most one or two per thread) p, the column-j+1 entries and the shares of all
 //      blocks into its own shared memory;
 //   4. after a block barrier, forms K = tau p^T v / 2, w = p - K v, the
 //      updated column j+1 (into the other buffer) and updates its rows
 //      (A -= v w^T + w v^T); a block barrier ends the step.
 // The published buffers alternate between steps, so no barrier guards their
 // reuse.
-constexpr int kCS = 8;
-constexpr int kCT = 256;
+// The cluster has 16 blocks where the GPU can place such clusters (a
+// non-portable size; 8 otherwise) of 512 threads: on n = 216 in FP32 that
+// measured 560 us a call against 627 us for 8 blocks of 256 threads.
+constexpr int kCT = 512;
 constexpr int kCW = kCT / 32;
 
-template <class R>
-__global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
-    k_rr_house_cluster(int n, RRWork<R> w) {
+template <class R, int CS>
+__global__ void __launch_bounds__(kCT) k_rr_house_cluster(int n, RRWork<R> w) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int rpc = (n + kCS - 1) / kCS;
+  const int rpc = (n + CS - 1) / CS;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  R* Ar = reinterpret_cast<R*>(sm_raw);  // rpc x n: row rank + kCS * li
+  R* Ar = reinterpret_cast<R*>(sm_raw);  // rpc x n: row rank + CS * li
   R* cf = Ar + (size_t)rpc * n;          // 2 x n: column j (alternating)
   R* wl = cf + 2 * n;                    // n: the gathered p
   R* cn = wl + n;                        // n: the gathered entries of column j+1
-  R* kall = cn + n;                      // kCS x kCW: the gathered shares of p^T v
-  R* pubc = kall + kCS * kCW;            // 2 x rpc: own rows' entries of column j+1
+  R* kall = cn + n;                      // CS x kCW: the gathered shares of p^T v
+  R* pubc = kall + CS * kCW;            // 2 x rpc: own rows' entries of column j+1
   R* pubp = pubc + 2 * rpc;              // 2 x rpc: own rows' p
   R* pubk = pubp + 2 * rpc;              // 2 x kCW: the warps' shares of p^T v
   for (int t = tid; t < rpc * n; t += kCT) {
-    const int li = t / n, c = t - li * n, r = rank + kCS * li;
+    const int li = t / n, c = t - li * n, r = rank + CS * li;
     Ar[t] = r < n ? w.As[(size_t)r * n + c] : R(0.0);
   }
   for (int l = tid; l < n; l += kCT) cf[l] = l >= 1 ? w.As[(size_t)l * n] : R(0.0);
@@ -950,8 +951,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
         w.e[j] = refl ? beta : x0;
       }
     }
-    if ((j % kCS) == rank && wid == (j / kCS) % kCW && lane == 0)
-      w.dg[j] = Ar[(size_t)(j / kCS) * n + j];
+    if ((j % CS) == rank && wid == (j / CS) % kCW && lane == 0)
+      w.dg[j] = Ar[(size_t)(j / CS) * n + j];
     // 2. p = tau A v for own rows r >= j+1, four rows of a warp at a time
     R kp = R(0.0);
     for (int l0 = wid; l0 < rpc; l0 += 4 * kCW) {
@@ -959,7 +960,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc[q] = R(0.0);
-        const int li = l0 + q * kCW, r = rank + kCS * li;
+        const int li = l0 + q * kCW, r = rank + CS * li;
         if (li < rpc && r < n && r >= j + 1) {
           const R* row = Ar + (size_t)li * n;
           for (int l = j + 1 + lane; l < n; l += 32)
@@ -970,7 +971,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
       for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]) * tj;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int li = l0 + q * kCW, r = rank + kCS * li;
+        const int li = l0 + q * kCW, r = rank + CS * li;
         if (li < rpc && r < n && r >= j + 1) {
           kp += acc[q] * (r == j + 1 ? v1 : cur[r] * scale);
           if (lane == 0) {
@@ -984,15 +985,15 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
     cl.sync();
     // 3. one round of remote loads
     for (int l = j + 1 + tid; l < n; l += kCT) {
-      const int owner = l % kCS, ol = l / kCS;
+      const int owner = l % CS, ol = l / CS;
       wl[l] = cl.map_shared_rank(pubp, owner)[buf * rpc + ol];
       cn[l] = cl.map_shared_rank(pubc, owner)[buf * rpc + ol];
     }
-    if (tid < kCS * kCW) kall[tid] = cl.map_shared_rank(pubk, tid / kCW)[buf * kCW + tid % kCW];
+    if (tid < CS * kCW) kall[tid] = cl.map_shared_rank(pubk, tid / kCW)[buf * kCW + tid % kCW];
     __syncthreads();
     // 4. K, w, the next column and the update of own rows
     R kq = R(0.0);
-    for (int q = lane; q < kCS * kCW; q += 32) kq += kall[q];
+    for (int q = lane; q < CS * kCW; q += 32) kq += kall[q];
     const R K = R(0.5) * tj * warp_sum(kq);
     const R wn = wl[j + 1] - K * v1;  // w_{j+1}
     for (int l = j + 2 + tid; l < n; l += kCT) {
@@ -1000,7 +1001,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
       nxt[l] = cn[l] - (vl * wn + wv * v1);
     }
     for (int li = wid; li < rpc; li += kCW) {
-      const int r = rank + kCS * li;
+      const int r = rank + CS * li;
       if (r >= n || r < j + 1) continue;
       R* row = Ar + (size_t)li * n;
       const R vr = r == j + 1 ? v1 : cur[r] * scale, wr = wl[r] - K * vr;
@@ -1014,8 +1015,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCT)
   // the last 2 x 2 block
   if (tid == 0) {
     for (int r = (n >= 2 ? n - 2 : 0); r < n; ++r) {
-      if (r % kCS != rank) continue;
-      const R* row = Ar + (size_t)(r / kCS) * n;
+      if (r % CS != rank) continue;
+      const R* row = Ar + (size_t)(r / CS) * n;
       w.dg[r] = row[r];
       if (r == n - 1 && n >= 2) w.e[n - 2] = row[n - 2];
     }
@@ -1532,6 +1533,59 @@ __global__ void k_rr_invit(int n, int nb, RRWork<R> w) {
   for (int i = 0; i < n; ++i) w.V[(size_t)i * nb + s] = z[i];
 }
 
+// the cluster size of the Householder: 16 when the device can place a
+// cluster of 16 such blocks (with the largest shared memory a call may ask
+// for), else the portable 8; decided once per precision
+template <class R>
+int house_cluster_size() {
+  static const int cs = [] {
+    const void* k16 = (const void*)k_rr_house_cluster<R, 16>;
+    if (cudaFuncSetAttribute(k16, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 8;
+    }
+    set_max_dyn_smem(k16, (int)kMaxDynSmem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kCT);
+    cfg.dynamicSmemBytes = kMaxDynSmem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_rr_house_cluster<R, 16>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 8;
+    }
+    return clusters >= 1 ? 16 : 8;
+  }();
+  return cs;
+}
+
+template <class R, int CS>
+void launch_house(int n, RRWork<R> w, size_t bytes, cudaStream_t st) {
+  set_max_dyn_smem((const void*)k_rr_house_cluster<R, CS>, (int)kMaxDynSmem);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CS);
+  cfg.blockDim = dim3(kCT);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  FF_CUDA(cudaLaunchKernelEx(&cfg, k_rr_house_cluster<R, CS>, n, w));
+  ::ff::note_launch();
+}
+
 // one Rayleigh-Ritz step in working precision R, output in T
 template <class R, class T>
 void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, double* theta,
@@ -1560,7 +1614,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.U = p; p += n * no;
   w.keep = reinterpret_cast<int*>(p);
   for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
-                         (const void*)k_rr_house_cluster<R>, (const void*)k_rr_invit_sm<R>,
+                         (const void*)k_rr_invit_sm<R>,
                          (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>,
                          (const void*)k_rr_proj_v<R>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
@@ -1571,8 +1625,9 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   const int tri_xsm = !tri_smem && l_bytes + x_bytes <= kMaxDynSmem ? 1 : 0;
   const size_t tri_bytes =
       (tri_smem ? a_bytes : 0) + (tri_lsm ? l_bytes : 0) + (tri_xsm ? x_bytes : 0);
-  const size_t rpc = (n + kCS - 1) / kCS;
-  const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * n + kCS * kCW + 4 * rpc + 2 * kCW);
+  const int cs = house_cluster_size<R>();
+  const size_t rpc = (n + cs - 1) / cs;
+  const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * n + cs * kCW + 4 * rpc + 2 * kCW);
   const bool use_cluster = cl_bytes <= kMaxDynSmem && n >= 3;
   const R drop = (R)std::max(d.drop, (double)Prec<R>::drop);
   // scaling and projection (many blocks), transform (one block); Householder
@@ -1594,8 +1649,10 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
-    (k_rr_house_cluster<R><<<kCS, kCT, cl_bytes, st>>>(d.ns, w), ::ff::note_launch());
-    FF_LAUNCH_CHECK();
+    if (cs == 16)
+      launch_house<R, 16>(d.ns, w, cl_bytes, st);
+    else
+      launch_house<R, 8>(d.ns, w, cl_bytes, st);
   }
   (k_rr_eigvals_mc<R><<<(unsigned)nb, 32 * kEW, (sizeof(R) + sizeof(float)) * 2 * n, st>>>(
        d.ns, d.nb, w, theta),
