@@ -29,8 +29,9 @@
 //                       tridiagonal (LU with partial pivoting), one block each;
 //   k_rr_cholqr         Cholesky QR of those vectors (a second pass only when
 //                       the first finds them far from orthogonal);
-//   k_rr_backtransform  the Householder reflectors applied in reverse, one
-//                       warp per vector;
+//   k_rr_wy_t, k_rr_backtransform
+//                       the Householder reflectors applied in reverse, in
+//                       groups of eight in compact WY form;
 //   k_rr_momentum       the momentum coefficients Z (the W and P rows of the
 //                       Ritz vectors, orthogonalised against them and
 //                       orthonormalised -- the next P = S Z is then
@@ -1327,38 +1328,111 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
       for (int c = lane; c < nb; c += 32) w.V[(size_t)i * nb + c] = V[(size_t)i * lv + c];
 }
 
-// ------------------------------------------------------------------ 4b. back-transform, one warp per vector
-// kBW vectors (warps) per block; SM: the reflectors and tau staged in shared
-// memory once per block (the reflector loop is a dependent chain per vector)
+// ------------------------------------------------------------------ 4b. back-transform, blocked
+// The reflectors are applied in groups of kWY in compact WY form: H_j0 ...
+// H_{j0+b-1} = I - V T V^T with V the group's vectors (v_j zero above row
+// j + 1) and T upper triangular, T_ii = tau_i and T_{0:i,i} = -tau_i
+// T_{0:i,0:i} V_{:,0:i}^T v_i.  k_rr_wy_t builds T for every group (a block
+// per group: the V^T V products by warps, the recurrence by one thread);
+// k_rr_backtransform applies the groups, last first, to kBW vectors per
+// block: W = V^T Z, W <- T W, Z -= V W, each a product over the block's
+// threads, so a group costs four block barriers instead of kWY dependent
+// warp reductions per vector.
+constexpr int kWY = 8;
 constexpr int kBW = 8;
-template <class R, bool SM>
-__global__ void __launch_bounds__(32 * kBW) k_rr_backtransform(int n, int nb, RRWork<R> w) {
+
+template <class R>
+__global__ void __launch_bounds__(256) k_rr_wy_t(int n, RRWork<R> w, R* __restrict__ T) {
+  __shared__ R dd[kWY * kWY];
+  const int g = blockIdx.x, j0 = g * kWY, b = min(kWY, n - 2 - j0);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = wid; q < kWY * kWY; q += 8) {
+    const int k = q / kWY, i = q - k * kWY;
+    if (!(k < i && i < b)) continue;
+    if (w.tau[j0 + k] == R(0.0) || w.tau[j0 + i] == R(0.0)) {  // H = I: v need not be set
+      if (lane == 0) dd[q] = R(0.0);
+      continue;
+    }
+    const R* vk = w.ref + (size_t)(j0 + k) * n;
+    const R* vi = w.ref + (size_t)(j0 + i) * n;
+    R acc = R(0.0);
+    for (int l = j0 + i + 1 + lane; l < n; l += 32) acc += vk[l] * vi[l];
+    acc = warp_sum(acc);
+    if (lane == 0) dd[q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R t[kWY * kWY];
+#pragma unroll
+    for (int q = 0; q < kWY * kWY; ++q) t[q] = R(0.0);
+    for (int i = 0; i < b; ++i) {
+      const R ti = w.tau[j0 + i];
+      for (int k = 0; k < i; ++k) {
+        R s = R(0.0);
+        for (int m = k; m < i; ++m) s += t[k * kWY + m] * dd[m * kWY + i];
+        t[k * kWY + i] = -ti * s;
+      }
+      t[i * kWY + i] = ti;
+    }
+    for (int q = 0; q < kWY * kWY; ++q) T[(size_t)g * kWY * kWY + q] = t[q];
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(32 * kBW) k_rr_backtransform(int n, int nb, RRWork<R> w,
+                                                               const R* __restrict__ T) {
   extern __shared__ __align__(16) unsigned char z_raw[];
-  R* zall = reinterpret_cast<R*>(z_raw);               // kBW x n
-  R* ref = SM ? zall + (size_t)kBW * n : w.ref;       // n x n
-  R* tau = SM ? ref + (size_t)n * n : w.tau;          // n
-  const int wv = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * kBW + wv;
-  if (SM) {
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) ref[t] = w.ref[t];
-    for (int t = threadIdx.x; t < n; t += blockDim.x) tau[t] = w.tau[t];
+  R* Z = reinterpret_cast<R*>(z_raw);  // n x kBW: the block's vectors, row-major
+  R* V = Z + (size_t)n * kBW;          // kWY x n: the group's reflectors
+  __shared__ R W[kWY * kBW], W2[kWY * kBW];
+  const int tid = threadIdx.x, s0 = blockIdx.x * kBW;
+  const int ns = min(kBW, nb - s0);
+  for (int t = tid; t < n * kBW; t += blockDim.x) {
+    const int i = t / kBW, s = t - i * kBW;
+    Z[t] = s < ns ? w.V[(size_t)i * nb + s0 + s] : R(0.0);
+  }
+  const int ng = n > 2 ? (n - 2 + kWY - 1) / kWY : 0;
+  for (int g = ng - 1; g >= 0; --g) {
+    const int j0 = g * kWY, b = min(kWY, n - 2 - j0);
+    for (int t = tid; t < kWY * n; t += blockDim.x) {
+      const int k = t / n, l = t - k * n;
+      V[t] = (k < b && l >= j0 + k + 1 && !(w.tau[j0 + k] == R(0.0)))
+                 ? w.ref[(size_t)(j0 + k) * n + l]
+                 : R(0.0);
+    }
+    __syncthreads();
+    // W = V^T Z: four threads per entry over rows l = p mod 4
+    {
+      const int o = tid >> 2, p = tid & 3, k = o / kBW, s = o - k * kBW;
+      R acc = R(0.0);
+      if (k < b)
+        for (int l = j0 + k + 1 + p; l < n; l += 4) acc += V[(size_t)k * n + l] * Z[(size_t)l * kBW + s];
+      acc += shfl_xor_r(acc, 1);
+      acc += shfl_xor_r(acc, 2);
+      if (p == 0) W[o] = acc;
+    }
+    __syncthreads();
+    if (tid < kWY * kBW) {  // W <- T W
+      const int k = tid / kBW, s = tid - k * kBW;
+      const R* tg = T + (size_t)g * kWY * kWY;
+      R acc = R(0.0);
+      for (int m = k; m < b; ++m) acc += tg[k * kWY + m] * W[m * kBW + s];
+      W2[tid] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < (n - j0 - 1) * kBW; t += blockDim.x) {  // Z -= V W
+      const int l = j0 + 1 + t / kBW, s = t % kBW;
+      R acc = R(0.0);
+#pragma unroll
+      for (int k = 0; k < kWY; ++k) acc += V[(size_t)k * n + l] * W2[k * kBW + s];
+      Z[(size_t)l * kBW + s] -= acc;
+    }
     __syncthreads();
   }
-  if (s >= nb) return;
-  R* z = zall + (size_t)wv * n;
-  for (int i = lane; i < n; i += 32) z[i] = w.V[(size_t)i * nb + s];
-  __syncwarp();
-  for (int j = n - 3; j >= 0; --j) {
-    const R tj = tau[j];
-    if (tj == R(0.0)) continue;
-    const R* v = ref + (size_t)j * n;
-    R acc = R(0.0);
-    for (int i = j + 1 + lane; i < n; i += 32) acc += v[i] * z[i];
-    acc = warp_sum(acc) * tj;
-    for (int i = j + 1 + lane; i < n; i += 32) z[i] -= acc * v[i];
-    __syncwarp();
+  for (int t = tid; t < n * kBW; t += blockDim.x) {
+    const int i = t / kBW, s = t - i * kBW;
+    if (s < ns) w.V[(size_t)i * nb + s0 + s] = Z[t];
   }
-  for (int i = lane; i < n; i += 32) w.V[(size_t)i * nb + s] = z[i];
 }
 
 // ------------------------------------------------------------------ 4c. momentum and mapping back
@@ -1615,7 +1689,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.keep = reinterpret_cast<int*>(p);
   for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
                          (const void*)k_rr_invit_sm<R>,
-                         (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R, true>,
+                         (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R>,
                          (const void*)k_rr_proj_v<R>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
   const size_t a_bytes = sizeof(R) * n * (n | 1), l_bytes = sizeof(R) * no * no;
@@ -1672,15 +1746,14 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   else
     (k_rr_cholqr<R, false><<<1, kThreads, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  const size_t bt_bytes = sizeof(R) * (kBW * n + n * n + n);
-  if (bt_bytes <= kMaxDynSmem)
-    (k_rr_backtransform<R, true><<<(unsigned)((nb + kBW - 1) / kBW), 32 * kBW, bt_bytes, st>>>(
-         d.ns, d.nb, w),
-     ::ff::note_launch());
-  else
-    (k_rr_backtransform<R, false><<<(unsigned)((nb + kBW - 1) / kBW), 32 * kBW,
-                                    sizeof(R) * kBW * n, st>>>(d.ns, d.nb, w),
-     ::ff::note_launch());
+  const int ngr = n > 2 ? (int)((n - 2 + kWY - 1) / kWY) : 0;
+  if (ngr > 0) {
+    (k_rr_wy_t<R><<<(unsigned)ngr, 256, 0, st>>>(d.ns, w, w.scr), ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
+  (k_rr_backtransform<R><<<(unsigned)((nb + kBW - 1) / kBW), 32 * kBW,
+                           sizeof(R) * n * (kBW + kWY), st>>>(d.ns, d.nb, w, w.scr),
+   ::ff::note_launch());
   FF_LAUNCH_CHECK();
   const size_t mo_bytes = sizeof(R) * (3 * n * (nb | 1) + nb * nb);
   if (mo_bytes <= kMaxDynSmem)
