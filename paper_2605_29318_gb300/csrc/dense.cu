@@ -1278,11 +1278,69 @@ __global__ void k_rr_invit_sm(int n, int nb, RRWork<R> w) {
   for (int i = 0; i < n; ++i) w.V[(size_t)i * nb + s] = z[i];
 }
 
+// ------------------------------------------------------------------ small dense products over many blocks
+// The Gram matrices and the product of the momentum step and the first Gram
+// of Cholesky QR, spread over the SMs (on one SM in double-float they cost
+// several hundred thousand cycles): G = X_{r0:r1}^T Y_{r0:r1} (lower: only
+// the lower triangle) with a warp per 4 x 4 tile of G, lanes over rows; and
+// T = Zp - V G (Zp = V with rows below r0 zero) with a thread per 4 entries.
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_rr_gram_mb(const R* __restrict__ X, int ldx, const R* __restrict__ Y, int ldy, int r0,
+                 int r1, int ma, int mb, R* __restrict__ G, int ldg, int lower) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int ta = (ma + 3) >> 2, tb = (mb + 3) >> 2;
+  if (t >= ta * tb) return;
+  const int ia = t / tb, ib = t - ia * tb;
+  if (lower && ib > ia) return;
+  R acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = R(0.0);
+  for (int i = r0 + lane; i < r1; i += 32) {
+    R xa[4], yb[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      xa[r] = 4 * ia + r < ma ? X[(size_t)i * ldx + 4 * ia + r] : R(0.0);
+      yb[r] = 4 * ib + r < mb ? Y[(size_t)i * ldy + 4 * ib + r] : R(0.0);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[4 * r + c] += xa[r] * yb[c];
+  }
+  const R sm = sum16(acc);
+  const int q = lane >> 1, a = 4 * ia + (q >> 2), b = 4 * ib + (q & 3);
+  if (!(lane & 1) && a < ma && b < mb && (!lower || b <= a)) G[(size_t)a * ldg + b] = sm;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_rr_zp_mb(const R* __restrict__ V, const R* __restrict__ G, int n, int nb, int r0,
+               R* __restrict__ T) {
+  const int tq = (nb + 3) >> 2;
+  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (t >= (long long)n * tq) return;
+  const int i = (int)(t / tq), c0 = 4 * (int)(t - (long long)i * tq);
+  const R* vi = V + (size_t)i * nb;
+  R acc[4] = {R(0.0), R(0.0), R(0.0), R(0.0)};
+  for (int a = 0; a < nb; ++a) {
+    const R va = vi[a];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c0 + c < nb) acc[c] += va * G[(size_t)a * nb + c0 + c];
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    if (c0 + c < nb) T[(size_t)i * nb + c0 + c] = (i >= r0 ? vi[c0 + c] : R(0.0)) - acc[c];
+}
+
 // ------------------------------------------------------------------ 4a. Cholesky QR of the tridiagonal eigenvectors (twice unless once is enough)
 // SM: V (n x nb) and G staged in shared memory (dynamic), else worked on in
 // the global workspace
 template <class R, bool SM>
 __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R> w) {
+  // the first pass's Gram (lower triangle) arrives in w.G from k_rr_gram_mb
   __shared__ int keep_nb[512];
   extern __shared__ __align__(16) unsigned char cq_raw[];
   // in shared memory V's rows are padded to an odd stride, so that a thread
@@ -1298,7 +1356,10 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
   }
   __shared__ float s_off[kWarps];
   for (int pass = 0; pass < 2; ++pass) {
-    blk_gram_tn(V, lv, V, lv, n, nb, nb, G, nb, true);
+    if (pass > 0)
+      blk_gram_tn(V, lv, V, lv, n, nb, nb, G, nb, true);
+    else if (SM)
+      for (int t = threadIdx.x; t < nb * nb; t += kThreads) G[t] = w.G[t];
     for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
     // largest off-diagonal of the normalised Gram matrix: at most 1e-3 means
@@ -1457,19 +1518,15 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
   }
   if (want_p) {
-    // G = V^T Zp with Zp = V without its X rows, summed over the W and P rows
-    // directly: I - V_X^T V_X would cancel catastrophically once the X rows of
-    // V are nearly the identity (a converging block)
-    blk_gram_tn(V + (size_t)nx * lv, lv, V + (size_t)nx * lv, lv, n - nx, nb, nb, G, nb, false);
-  
-    __syncthreads();
-// Z = Zp - V G
-    blk_sub_xg(V, lv, G, nb, n, nb, nb, V, nx, T1, lv);
-  
-    __syncthreads();
-// G = Z^T Z (lower)
-    blk_gram_tn(T1, lv, T1, lv, n, nb, nb, G, nb, true);
-  
+    // from the multi-block launches: Z = Zp - V G in w.T1 and Z^T Z (lower)
+    // in w.G, where G = V^T Zp and Zp = V without its X rows (summed over
+    // the W and P rows directly: I - V_X^T V_X would cancel catastrophically
+    // once the X rows of V are nearly the identity, a converging block)
+    if (SM) {
+      for (int i = wid; i < n; i += kWarps)
+        for (int c = lane; c < nb; c += 32) T1[(size_t)i * lv + c] = w.T1[(size_t)i * nb + c];
+      for (int t = tid; t < nb * nb; t += kThreads) G[t] = w.G[t];
+    }
     for (int s2 = tid; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
     R gref = R(0.0);
@@ -1740,6 +1797,16 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
     (k_rr_invit<R><<<(unsigned)((nb + 31) / 32), 32, 0, st>>>(d.ns, d.nb, w), ::ff::note_launch());
   }
   FF_LAUNCH_CHECK();
+  // G = X_{r0:r1}^T Y_{r0:r1} over many blocks (a warp per 4 x 4 tile)
+  auto gram_mb = [&](const R* X, const R* Y, int r0, int r1, R* G, int lower) {
+    const int tiles = (int)(((nb + 3) / 4) * ((nb + 3) / 4));
+    (k_rr_gram_mb<R><<<(unsigned)((tiles + 7) / 8), 256, 0, st>>>(X, (int)nb, Y, (int)nb, r0, r1,
+                                                                  (int)nb, (int)nb, G, (int)nb,
+                                                                  lower),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  };
+  gram_mb(w.V, w.V, 0, (int)n, w.G, 1);  // Cholesky QR's first Gram
   const size_t cq_bytes = sizeof(R) * (n * (nb | 1) + nb * nb);
   if (cq_bytes <= kMaxDynSmem)
     (k_rr_cholqr<R, true><<<1, kThreads, cq_bytes, st>>>(d.ns, d.nb, w), ::ff::note_launch());
@@ -1755,6 +1822,15 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
                            sizeof(R) * n * (kBW + kWY), st>>>(d.ns, d.nb, w, w.scr),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
+  if (d.want_p) {  // the momentum step's Grams and Z = Zp - V G over many blocks
+    gram_mb(w.V, w.V, d.nx, (int)n, w.G, 0);
+    const long long zt = (long long)n * ((nb + 3) / 4);
+    (k_rr_zp_mb<R><<<(unsigned)((zt + 255) / 256), 256, 0, st>>>(w.V, w.G, (int)n, (int)nb, d.nx,
+                                                                 w.T1),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    gram_mb(w.T1, w.T1, 0, (int)n, w.G, 1);
+  }
   const size_t mo_bytes = sizeof(R) * (3 * n * (nb | 1) + nb * nb);
   if (mo_bytes <= kMaxDynSmem)
     (k_rr_momentum<R, T, true><<<1, kThreads, mo_bytes, st>>>(d.ns, d.o0, d.no, d.nx, d.nb,
