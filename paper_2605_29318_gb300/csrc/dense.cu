@@ -14,9 +14,13 @@
 //                       momentum directions, leave the basis) and project the
 //                       O block against the rest once more in coefficient
 //                       space;
-//   k_rr_tridiag        (one block) Cholesky B_OO = L L^T with drop
-//                       (dependent or empty columns leave the basis),
-//                       A <- T^T A T with T = blockdiag(I, L^-T, I); for bases
+//   k_rr_chol, k_rr_ysolve, k_rr_zsolve
+//                       Cholesky B_OO = L L^T with drop (dependent or empty
+//                       columns leave the basis; one block), then the two
+//                       triangular solves of A <- T^T A T with
+//                       T = blockdiag(I, L^-T, I) (many blocks);
+//   k_rr_tridiag        (one block) the transformed matrix assembled,
+//                       symmetrised, dropped columns decoupled; for bases
 //                       too large for the cluster it also tridiagonalises;
 //   k_rr_house_cluster  Householder tridiagonalisation of A by an 8-block
 //                       thread-block cluster, rows spread over the blocks'
@@ -664,29 +668,98 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// ------------------------------------------------------------------ R(0.5) factor and solves of the transform
+// A <- T^T A T with T = blockdiag(I, L^-T, I), L L^T = B_OO - C^T C: with
+// Y = L^-1 A_{O,.} (A's O rows after the projection), the rest-O blocks are
+// Y's transposes and the O x O block is Y_OO L^-T.  The factor takes one
+// block; each column of Y is a forward substitution of its own, and so is
+// each row of Y_OO L^-T, so both solves are spread over blocks of kYC
+// columns (rows), each with its own copy of L.
+constexpr int kYC = 32;
+
+template <class R>
+__global__ void __launch_bounds__(kThreads)
+    k_rr_chol(int o0, int no, RRWork<R> w, int lsm, R drop) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* Ls = lsm ? reinterpret_cast<R*>(dyn_raw) : w.L;
+  __shared__ int keep_o[1024];
+  if (lsm)
+    for (int t = threadIdx.x; t < no * no; t += kThreads) Ls[t] = w.L[t];
+  for (int a = threadIdx.x; a < no; a += kThreads) keep_o[a] = w.keep[o0 + a];
+  __syncthreads();
+  block_cholesky(Ls, no, keep_o, drop);
+  for (int a = threadIdx.x; a < no; a += kThreads) w.keep[o0 + a] = keep_o[a];
+  if (lsm)
+    for (int t = threadIdx.x; t < no * no; t += kThreads) w.L[t] = Ls[t];
+}
+
+// Y (no x n, row-major, in Yg) = L^-1 A_{O,.}: a block per cb columns, each
+// column staged as a row of Xt and solved as x L^-T
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_rr_ysolve(int n, int o0, int no, RRWork<R> w, R* __restrict__ Yg, int cb, int lsm) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* dyn = reinterpret_cast<R*>(dyn_raw);
+  const R* L = lsm ? dyn : w.L;
+  R* Xt = dyn + (lsm ? (size_t)no * no : 0);
+  const int lx = no | 1, c0 = blockIdx.x * cb, nc = min(cb, n - c0);
+  if (lsm)
+    for (int t = threadIdx.x; t < no * no; t += blockDim.x) dyn[t] = w.L[t];
+  for (int t = threadIdx.x; t < nc * no; t += blockDim.x) {
+    const int c = t / no, a = t - c * no, col = c0 + c;
+    Xt[(size_t)c * lx + a] = (col >= o0 && col < o0 + no) ? w.G[(size_t)a * no + (col - o0)]
+                                                          : w.U[(size_t)col * no + a];
+  }
+  __syncthreads();
+  block_trsm_rt(L, no, Xt, lx, nc);
+  for (int t = threadIdx.x; t < nc * no; t += blockDim.x) {
+    const int a = t / nc, c = t - a * nc;
+    Yg[(size_t)a * n + c0 + c] = Xt[(size_t)c * lx + a];
+  }
+}
+
+// Y_OO <- Y_OO L^-T in place in Yg: a block per cb rows
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_rr_zsolve(int n, int o0, int no, RRWork<R> w, R* __restrict__ Yg, int cb, int lsm) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* dyn = reinterpret_cast<R*>(dyn_raw);
+  const R* L = lsm ? dyn : w.L;
+  R* Xs = dyn + (lsm ? (size_t)no * no : 0);
+  const int lx = no | 1, a0 = blockIdx.x * cb, nr = min(cb, no - a0);
+  if (lsm)
+    for (int t = threadIdx.x; t < no * no; t += blockDim.x) dyn[t] = w.L[t];
+  for (int t = threadIdx.x; t < nr * no; t += blockDim.x) {
+    const int r = t / no, b = t - r * no;
+    Xs[(size_t)r * lx + b] = Yg[(size_t)(a0 + r) * n + o0 + b];
+  }
+  __syncthreads();
+  block_trsm_rt(L, no, Xs, lx, nr);
+  for (int t = threadIdx.x; t < nr * no; t += blockDim.x) {
+    const int r = t / no, b = t - r * no;
+    Yg[(size_t)(a0 + r) * n + o0 + b] = Xs[(size_t)r * lx + b];
+  }
+}
+
 // ------------------------------------------------------------------ R(1.) tridiagonalise
 template <class R>
 __global__ void __launch_bounds__(kThreads)
     k_rr_tridiag(const double* __restrict__ A, const double* __restrict__ B, int n, int o0, int no,
-                 RRWork<R> w, int smem, int lsm, int xsm, int do_house, R drop) {
+                 RRWork<R> w, int smem, int do_house, const R* __restrict__ Yg) {
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   R* dyn = reinterpret_cast<R*>(dyn_raw);
   __shared__ R red[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // smem = 1: A in shared memory (rows padded to an odd stride, so that a
-  // thread per row hits distinct banks); lsm = 1: a copy of B_OO - C^T C in
-  // shared memory, factored there (the factorisation and the substitutions
-  // read it every step), after A when A is there too; xsm = 1 (A in global
-  // memory): A's O rows staged after it while they are transformed.
+  // thread per row hits distinct banks)
   const int la = (smem && !do_house) ? (n | 1) : n;
   R* As = smem ? dyn : w.As;
-  R* Lw = w.L;
-  R* vt = w.T1;            // n
+  R* vt = w.T1;            // n (after Yg has been read)
   R* pw = w.T1 + n;        // n
   const int o1 = o0 + no;
   // the scaled matrix (rows by warps, columns by lanes) and its symmetric
-  // part; then the projected blocks (scaling, keep flags, V, the O x O
-  // blocks of A and B come from the projection launches)
+  // part; then A's O rows and the rest-O blocks from Y (no x n in Yg, its
+  // O x O block already times L^-T), which the solve launches left there
   for (int i = wid; i < n; i += kWarps)
     for (int j = lane; j < n; j += 32)
       As[(size_t)i * la + j] = (R)A[(size_t)i * n + j] * w.dsc[i] * w.dsc[j];
@@ -700,47 +773,10 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   for (int i = wid; i < n; i += kWarps) {
     if (i >= o0 && i < o1) {
-      for (int b = lane; b < no; b += 32)
-        As[(size_t)i * la + o0 + b] = w.G[(size_t)(i - o0) * no + b];
+      for (int c = lane; c < n; c += 32) As[(size_t)i * la + c] = Yg[(size_t)(i - o0) * n + c];
     } else {
-      for (int b = lane; b < no; b += 32) {
-        const R v = w.U[(size_t)i * no + b];
-        As[(size_t)i * la + o0 + b] = v;
-        As[(size_t)(o0 + b) * la + i] = v;
-      }
+      for (int b = lane; b < no; b += 32) As[(size_t)i * la + o0 + b] = Yg[(size_t)b * n + i];
     }
-  }
-  if (lsm) {
-    R* Ls = dyn + (smem ? (size_t)n * la : 0);
-    for (int t = tid; t < no * no; t += kThreads) Ls[t] = Lw[t];
-    Lw = Ls;
-  }
-  __shared__ int keep_o[1024];  // the O columns' keep flags while factoring
-  for (int a = tid; a < no; a += kThreads) keep_o[a] = w.keep[o0 + a];
-  __syncthreads();
-  // A <- T^T A T.  The elimination that factors B_OO - C^T C applies L^-1
-  // to A's O rows on the way (Y = L^-1 A_{O,.}); the rest-O blocks are then
-  // Y's transposes and the O x O block is Y_OO L^-T.
-  R* X = As + (size_t)o0 * la;
-  int ldx = la;
-  if (xsm) {
-    ldx = n | 1;
-    X = dyn + (size_t)no * no;
-    for (int a = wid; a < no; a += kWarps)
-      for (int c = lane; c < n; c += 32) X[(size_t)a * ldx + c] = As[(size_t)(o0 + a) * la + c];
-    __syncthreads();
-  }
-  block_cholesky(Lw, no, keep_o, drop, X, ldx, n);
-  for (int a = tid; a < no; a += kThreads) w.keep[o0 + a] = keep_o[a];
-  if (lsm)
-    for (int t = tid; t < no * no; t += kThreads) w.L[t] = Lw[t];
-  block_trsm_rt(Lw, no, X + o0, ldx, no);  // Y_OO <- Y_OO L^-T
-  if (xsm)
-    for (int a = wid; a < no; a += kWarps)
-      for (int c = lane; c < n; c += 32) As[(size_t)(o0 + a) * la + c] = X[(size_t)a * ldx + c];
-  for (int i = wid; i < n; i += kWarps) {
-    if (i >= o0 && i < o1) continue;
-    for (int b = lane; b < no; b += 32) As[(size_t)i * la + o0 + b] = X[(size_t)b * ldx + i];
   }
   __syncthreads();
   // symmetrise; dropped columns are decoupled with a diagonal just above the
@@ -1249,6 +1285,9 @@ __global__ void k_rr_invit_sm(int n, int nb, RRWork<R> w) {
   u[n - 1] = fabs(a_i) < pivmin ? (a_i < R(0.0) ? -pivmin : pivmin) : a_i;
   u1[n - 1] = R(0.0);
   u2[n - 1] = R(0.0);
+  // the pivots' reciprocals, once: the substitutions below then multiply
+  // (independent divisions here instead of one on every step of the chain)
+  for (int i = 0; i < n; ++i) u[i] = R(1.0) / u[i];
   unsigned int h = 2166136261u ^ (unsigned)s * 16777619u;
   for (int i = 0; i < n; ++i) {
     h = h * 1664525u + 1013904223u;
@@ -1268,7 +1307,7 @@ __global__ void k_rr_invit_sm(int n, int nb, RRWork<R> w) {
       R t = z[i];
       if (i + 1 < n) t -= u1[i] * z[i + 1];
       if (i + 2 < n) t -= u2[i] * z[i + 2];
-      z[i] = t / u[i];
+      z[i] = t * u[i];
     }
     R nrm = R(0.0);
     for (int i = 0; i < n; ++i) nrm = fmax(nrm, fabs(z[i]));
@@ -1635,6 +1674,9 @@ __global__ void k_rr_invit(int n, int nb, RRWork<R> w) {
   u[n - 1] = fabs(a_i) < pivmin ? (a_i < R(0.0) ? -pivmin : pivmin) : a_i;
   u1[n - 1] = R(0.0);
   u2[n - 1] = R(0.0);
+  // the pivots' reciprocals, once: the substitutions below then multiply
+  // (independent divisions here instead of one on every step of the chain)
+  for (int i = 0; i < n; ++i) u[i] = R(1.0) / u[i];
   unsigned int h = 2166136261u ^ (unsigned)s * 16777619u;  // deterministic start vector
   for (int i = 0; i < n; ++i) {
     h = h * 1664525u + 1013904223u;
@@ -1654,7 +1696,7 @@ __global__ void k_rr_invit(int n, int nb, RRWork<R> w) {
       R t = z[i];
       if (i + 1 < n) t -= u1[i] * z[i + 1];
       if (i + 2 < n) t -= u2[i] * z[i + 2];
-      z[i] = t / u[i];
+      z[i] = t * u[i];
     }
     R nrm = R(0.0);
     for (int i = 0; i < n; ++i) nrm = fmax(nrm, fabs(z[i]));
@@ -1747,15 +1789,19 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
                          (const void*)k_rr_invit_sm<R>,
                          (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R>,
-                         (const void*)k_rr_proj_v<R>})
+                         (const void*)k_rr_proj_v<R>, (const void*)k_rr_chol<R>,
+                         (const void*)k_rr_ysolve<R>, (const void*)k_rr_zsolve<R>})
     set_max_dyn_smem(fn, (int)kMaxDynSmem);
   const size_t a_bytes = sizeof(R) * n * (n | 1), l_bytes = sizeof(R) * no * no;
-  const size_t x_bytes = sizeof(R) * no * (n | 1);
-  const int tri_smem = a_bytes + l_bytes <= kMaxDynSmem ? 1 : 0;
-  const int tri_lsm = l_bytes <= kMaxDynSmem ? 1 : 0;
-  const int tri_xsm = !tri_smem && l_bytes + x_bytes <= kMaxDynSmem ? 1 : 0;
-  const size_t tri_bytes =
-      (tri_smem ? a_bytes : 0) + (tri_lsm ? l_bytes : 0) + (tri_xsm ? x_bytes : 0);
+  const int tri_smem = a_bytes <= kMaxDynSmem ? 1 : 0;
+  const int ch_lsm = l_bytes <= kMaxDynSmem ? 1 : 0;
+  // the solves: L in shared memory when a few staged rows fit beside it
+  const size_t lx_bytes = sizeof(R) * (no | 1);
+  const int sv_lsm = l_bytes + 8 * lx_bytes <= kMaxDynSmem ? 1 : 0;
+  int cb = kYC;
+  while (cb > 1 && (sv_lsm ? l_bytes : 0) + cb * lx_bytes > kMaxDynSmem) cb >>= 1;
+  const size_t sv_bytes = (sv_lsm ? l_bytes : 0) + cb * lx_bytes;
+  R* Yg = w.T1;  // Y = L^-1 A_{O,.}, no x n
   const int cs = house_cluster_size<R>();
   const size_t rpc = (n + cs - 1) / cs;
   const size_t cl_bytes = sizeof(R) * (rpc * n + 4 * n + cs * kCW + 4 * rpc + 2 * kCW);
@@ -1775,8 +1821,21 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
   }
-  (k_rr_tridiag<R><<<1, kThreads, tri_bytes, st>>>(A, B, d.ns, d.o0, d.no, w, tri_smem, tri_lsm,
-                                                   tri_xsm, use_cluster ? 0 : 1, drop),
+  if (no > 0) {
+    (k_rr_chol<R><<<1, kThreads, ch_lsm ? l_bytes : 0, st>>>(d.o0, d.no, w, ch_lsm, drop),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    (k_rr_ysolve<R><<<(unsigned)((n + cb - 1) / cb), 256, sv_bytes, st>>>(d.ns, d.o0, d.no, w, Yg,
+                                                                         cb, sv_lsm),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+    (k_rr_zsolve<R><<<(unsigned)((no + cb - 1) / cb), 256, sv_bytes, st>>>(d.ns, d.o0, d.no, w,
+                                                                          Yg, cb, sv_lsm),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
+  (k_rr_tridiag<R><<<1, kThreads, tri_smem ? a_bytes : 0, st>>>(A, B, d.ns, d.o0, d.no, w,
+                                                                tri_smem, use_cluster ? 0 : 1, Yg),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
   if (use_cluster) {
