@@ -36,11 +36,13 @@
 //   k_rr_wy_t, k_rr_backtransform
 //                       the Householder reflectors applied in reverse, in
 //                       groups of eight in compact WY form;
-//   k_rr_momentum       the momentum coefficients Z (the W and P rows of the
+//   k_rr_gram_mb, k_rr_zp_mb, k_rr_mchol, k_rr_rsolve, k_rr_bsolve
+//                       the momentum coefficients Z (the W and P rows of the
 //                       Ritz vectors, orthogonalised against them and
 //                       orthonormalised -- the next P = S Z is then
 //                       M-orthonormal and M-orthogonal to the next X), and the
-//                       O rows mapped back through L^-T and the scaling.
+//                       O rows mapped back through L^-T;
+//   k_rr_output         the projection undone and the scaling.
 // Output YZ = [Y | Z] (n x 2 nb, row-major, context precision) and the Ritz
 // values theta (nb).  Instantiated in FP64 (FP64 blocks), in double-float
 // (the double-float phase of the mixed solve) and in FP32 (the FP32 phase):
@@ -92,7 +94,8 @@ __device__ __forceinline__ dfloat scalbn_r(dfloat x, int e) {
 template <class R>
 struct RRWork {
   R *As, *ref, *L, *dsc, *dg, *e, *e2, *tau, *lam, *V, *Z, *G, *T1, *scr, *C, *U;
-  int* keep;
+  int* keep;   // n: basis columns kept
+  int* keepz;  // nb: momentum columns kept
 };
 
 template <class R>
@@ -399,22 +402,6 @@ __device__ __forceinline__ dfloat shfl_xor_r<dfloat>(dfloat v, int o) {
   return dfloat(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o));
 }
 
-// acc - sum_{p0 <= p < p1} term(p), with four independent partial sums so
-// that a long serial substitution keeps several multiply-adds in flight
-template <class R, class F>
-__device__ __forceinline__ R sub_dot(R acc, int p0, int p1, F term) {
-  R a1 = R(0.0), a2 = R(0.0), a3 = R(0.0);
-  int p = p0;
-  for (; p + 3 < p1; p += 4) {
-    acc -= term(p);
-    a1 -= term(p + 1);
-    a2 -= term(p + 2);
-    a3 -= term(p + 3);
-  }
-  for (; p < p1; ++p) acc -= term(p);
-  return (acc + a1) + (a2 + a3);
-}
-
 // The warp sums of 16 values at once by halving exchanges (16 shuffles
 // instead of 80): lanes 2q and 2q + 1 end with the sum of v[q].
 template <class R>
@@ -465,80 +452,6 @@ __device__ void blk_gram_tn(const R* X, int ldx, const R* Y, int ldy, int rows, 
     const R s = sum16(acc);
     const int q = lane >> 1, a = 4 * ia + (q >> 2), b = 4 * ib + (q & 3);
     if (!(lane & 1) && a < ma && b < mb && (!lower || b <= a)) C[(size_t)a * ldc + b] = s;
-  }
-}
-
-// The same Gram with a thread per 4 x 4 tile running over all rows: the
-// threads of a warp read one row at a time, so global row-major operands are
-// read in whole lines and shared ones without bank conflicts at any stride.
-template <class R>
-__device__ void blk_gram_tn_rows(const R* X, int ldx, const R* Y, int ldy, int rows, int ma,
-                                 int mb, R* C, int ldc, bool lower) {
-  const int ta = (ma + 3) >> 2, tb = (mb + 3) >> 2;
-  for (int t = threadIdx.x; t < ta * tb; t += kThreads) {
-    const int ia = t / tb, ib = t - ia * tb;
-    if (lower && ib > ia) continue;
-    R acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
-    for (int i = 0; i < rows; ++i) {
-      R xa[4], yb[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        xa[r] = 4 * ia + r < ma ? X[(size_t)i * ldx + 4 * ia + r] : R(0.0);
-        yb[r] = 4 * ib + r < mb ? Y[(size_t)i * ldy + 4 * ib + r] : R(0.0);
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] += xa[r] * yb[c];
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int a = 4 * ia + r, b = 4 * ib + c;
-        if (a < ma && b < mb && (!lower || b <= a)) C[(size_t)a * ldc + b] = acc[r][c];
-      }
-  }
-}
-
-// C[i][b] = base[i][b] (rows i >= r0; zero above) + sgn sum_a X[i][a] G[a][b]
-// for i < rows, b < mb, a < ma (row strides ldx, ldg, ldc; base shares C's
-// layout; sgn -1 by default), one 4 x 4 tile of C per thread at a time.
-template <class R>
-__device__ void blk_sub_xg(const R* X, int ldx, const R* G, int ldg, int rows, int ma, int mb,
-                           const R* base, int r0, R* C, int ldc, R sgn = R(-1.0)) {
-  const int ta = (rows + 3) >> 2, tb = (mb + 3) >> 2;
-  for (int t = threadIdx.x; t < ta * tb; t += kThreads) {
-    const int ia = t / tb, ib = t - ia * tb;
-    R acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = R(0.0);
-    for (int a = 0; a < ma; ++a) {
-      R xr[4], gc[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        xr[r] = 4 * ia + r < rows ? X[(size_t)(4 * ia + r) * ldx + a] : R(0.0);
-        gc[r] = 4 * ib + r < mb ? G[(size_t)a * ldg + 4 * ib + r] : R(0.0);
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] += xr[r] * gc[c];
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = 4 * ia + r, b = 4 * ib + c;
-        if (i < rows && b < mb)
-          C[(size_t)i * ldc + b] = (i >= r0 ? base[(size_t)i * ldc + b] : R(0.0)) + sgn * acc[r][c];
-      }
   }
 }
 
@@ -1536,69 +1449,94 @@ __global__ void __launch_bounds__(32 * kBW) k_rr_backtransform(int n, int nb, RR
 }
 
 // ------------------------------------------------------------------ 4c. momentum and mapping back
-template <class R, class T, bool SM>
+// The momentum coefficients Z (the W and P rows of the Ritz vectors,
+// orthogonalised against them and orthonormalised -- the next P = S Z is
+// then M-orthonormal and M-orthogonal to the next X), from the multi-block
+// launches' Z = Zp - V G (w.T1) and Z^T Z (w.G): the factor of Z^T Z with
+// drop in one block (k_rr_mchol, which also counts the basis columns the
+// step dropped), Z <- Z L^-T with dropped columns zero over blocks of rows
+// (k_rr_rsolve), and the O rows of V and Z mapped back through the
+// transform's factor, y_O <- L^-T y_O, over blocks of columns (k_rr_bsolve);
+// then y_rest <- y_rest - C y_O and y <- D y (k_rr_output).
+template <class R>
 __global__ void __launch_bounds__(kThreads)
-    k_rr_momentum(int n, int o0, int no, int nx, int nb, int want_p, RRWork<R> w,
-                  T* __restrict__ YZ, int* __restrict__ dropped) {
+    k_rr_mchol(int n, int nb, int want_p, RRWork<R> w, int* __restrict__ dropped, int lsm) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* G = lsm ? reinterpret_cast<R*>(dyn_raw) : w.G;
   __shared__ int keep_nb[512];
   const int tid = threadIdx.x;
-  // SM: V, Z, T1 (n x nb each, rows padded to an odd stride so that a thread
-  // per row hits distinct banks) and G staged in shared memory (dynamic)
-  extern __shared__ __align__(16) unsigned char mo_raw[];
-  const int lv = SM ? (nb | 1) : nb;
-  const int lane = tid & 31, wid = tid >> 5;
-  R* V = SM ? reinterpret_cast<R*>(mo_raw) : w.V;
-  R* Z = SM ? V + (size_t)n * lv : w.Z;
-  R* T1 = SM ? Z + (size_t)n * lv : w.T1;
-  R* G = SM ? T1 + (size_t)n * lv : w.G;
-  if (SM) {
-    for (int i = wid; i < n; i += kWarps)
-      for (int c = lane; c < nb; c += 32) V[(size_t)i * lv + c] = w.V[(size_t)i * nb + c];
-    __syncthreads();
-  }
   if (want_p) {
-    // from the multi-block launches: Z = Zp - V G in w.T1 and Z^T Z (lower)
-    // in w.G, where G = V^T Zp and Zp = V without its X rows (summed over
-    // the W and P rows directly: I - V_X^T V_X would cancel catastrophically
-    // once the X rows of V are nearly the identity, a converging block)
-    if (SM) {
-      for (int i = wid; i < n; i += kWarps)
-        for (int c = lane; c < nb; c += 32) T1[(size_t)i * lv + c] = w.T1[(size_t)i * nb + c];
+    if (lsm)
       for (int t = tid; t < nb * nb; t += kThreads) G[t] = w.G[t];
-    }
     for (int s2 = tid; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
     __syncthreads();
     R gref = R(0.0);
     for (int s2 = 0; s2 < nb; ++s2) gref = fmax(gref, G[s2 * nb + s2]);
     block_cholesky(G, nb, keep_nb, Prec<R>::drop * fmax(gref, Prec<R>::tiny));
-    block_trsm_rt(G, nb, T1, lv, n);  // Z <- Z L^-T, dropped columns zero
-    for (int i = wid; i < n; i += kWarps)
-      for (int c = lane; c < nb; c += 32)
-        Z[(size_t)i * lv + c] = keep_nb[c] ? T1[(size_t)i * lv + c] : R(0.0);
-    __syncthreads();
-  }
-  // back to the coefficients of the original basis: y_O <- L^-T y_O (the
-  // factor staged in G's place when in shared memory), then y_rest <- y_rest
-  // - C y_O and y <- D y (k_rr_output)
-  const R* Lf = w.L;
-  if (SM && no <= nb) {
-    for (int t = tid; t < no * no; t += kThreads) G[t] = w.L[t];
-    Lf = G;
-    __syncthreads();
-  }
-  block_trsm_lt(Lf, no, V + (size_t)o0 * lv, lv, nb);
-  if (want_p) block_trsm_lt(Lf, no, Z + (size_t)o0 * lv, lv, nb);
-  if (SM) {
-    for (int i = wid; i < n; i += kWarps)
-      for (int c = lane; c < nb; c += 32) w.V[(size_t)i * nb + c] = V[(size_t)i * lv + c];
-    if (want_p)
-      for (int i = wid; i < n; i += kWarps)
-        for (int c = lane; c < nb; c += 32) w.Z[(size_t)i * nb + c] = Z[(size_t)i * lv + c];
+    for (int s2 = tid; s2 < nb; s2 += kThreads) w.keepz[s2] = keep_nb[s2];
+    if (lsm)
+      for (int t = tid; t < nb * nb; t += kThreads) w.G[t] = G[t];
   }
   if (tid == 0) {
     int dc = 0;
     for (int a = 0; a < n; ++a) dc += !w.keep[a];
     *dropped = dc;
+  }
+}
+
+// Xout <- Xin L^-T for `rows` rows (m entries each; L as block_cholesky
+// leaves it, ld m), entries of columns with mask[c] == 0 set to zero: a
+// block per cb rows
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_rr_rsolve(const R* __restrict__ Lg, int m, const R* __restrict__ Xin, int ldin,
+                R* __restrict__ Xout, int ldout, int rows, const int* __restrict__ mask, int cb,
+                int lsm) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* dyn = reinterpret_cast<R*>(dyn_raw);
+  const R* L = lsm ? dyn : Lg;
+  R* Xs = dyn + (lsm ? (size_t)m * m : 0);
+  const int lx = m | 1, r0 = blockIdx.x * cb, nr = min(cb, rows - r0);
+  if (lsm)
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) dyn[t] = Lg[t];
+  for (int t = threadIdx.x; t < nr * m; t += blockDim.x) {
+    const int r = t / m, c = t - r * m;
+    Xs[(size_t)r * lx + c] = Xin[(size_t)(r0 + r) * ldin + c];
+  }
+  __syncthreads();
+  block_trsm_rt(L, m, Xs, lx, nr);
+  for (int t = threadIdx.x; t < nr * m; t += blockDim.x) {
+    const int r = t / m, c = t - r * m;
+    Xout[(size_t)(r0 + r) * ldout + c] = (mask && !mask[c]) ? R(0.0) : Xs[(size_t)r * lx + c];
+  }
+}
+
+// the O rows of V (columns 0..nb-1) and Z (columns nb..ncol-1): y_O <-
+// L^-T y_O, a block per cb columns
+template <class R>
+__global__ void __launch_bounds__(256)
+    k_rr_bsolve(const R* __restrict__ Lg, int no, int o0, R* __restrict__ V, R* __restrict__ Z,
+                int nb, int ncol, int cb, int lsm) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* dyn = reinterpret_cast<R*>(dyn_raw);
+  const R* L = lsm ? dyn : Lg;
+  R* Xs = dyn + (lsm ? (size_t)no * no : 0);  // no x cb
+  const int c0 = blockIdx.x * cb, nc = min(cb, ncol - c0);
+  if (lsm)
+    for (int t = threadIdx.x; t < no * no; t += blockDim.x) dyn[t] = Lg[t];
+  for (int t = threadIdx.x; t < no * nc; t += blockDim.x) {
+    const int a = t / nc, c = t - a * nc, col = c0 + c;
+    Xs[(size_t)a * cb + c] =
+        col < nb ? V[(size_t)(o0 + a) * nb + col] : Z[(size_t)(o0 + a) * nb + col - nb];
+  }
+  __syncthreads();
+  block_trsm_lt(L, no, Xs, cb, nc);
+  for (int t = threadIdx.x; t < no * nc; t += blockDim.x) {
+    const int a = t / nc, c = t - a * nc, col = c0 + c;
+    if (col < nb)
+      V[(size_t)(o0 + a) * nb + col] = Xs[(size_t)a * cb + c];
+    else
+      Z[(size_t)(o0 + a) * nb + col - nb] = Xs[(size_t)a * cb + c];
   }
 }
 
@@ -1767,7 +1705,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   const size_t t1 = std::max(n * nb, 2 * n);
   const size_t total =
       2 * n * n + no * no + 5 * n + nb + 2 * n * nb + nb * nb + t1 + 6 * n * nb + 2 * n * no;
-  R* p = reinterpret_cast<R*>(work.ensure(sizeof(R) * total + sizeof(int) * n + 256));
+  R* p = reinterpret_cast<R*>(work.ensure(sizeof(R) * total + sizeof(int) * (n + nb) + 256));
   RRWork<R> w;
   w.As = p; p += n * n;
   w.ref = p; p += n * n;
@@ -1786,7 +1724,9 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.C = p; p += n * no;
   w.U = p; p += n * no;
   w.keep = reinterpret_cast<int*>(p);
-  for (const void* fn : {(const void*)k_rr_momentum<R, T, true>, (const void*)k_rr_tridiag<R>,
+  w.keepz = w.keep + n;
+  for (const void* fn : {(const void*)k_rr_mchol<R>, (const void*)k_rr_rsolve<R>,
+                         (const void*)k_rr_bsolve<R>, (const void*)k_rr_tridiag<R>,
                          (const void*)k_rr_invit_sm<R>,
                          (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R>,
                          (const void*)k_rr_proj_v<R>, (const void*)k_rr_chol<R>,
@@ -1890,16 +1830,36 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
     FF_LAUNCH_CHECK();
     gram_mb(w.T1, w.T1, 0, (int)n, w.G, 1);
   }
-  const size_t mo_bytes = sizeof(R) * (3 * n * (nb | 1) + nb * nb);
-  if (mo_bytes <= kMaxDynSmem)
-    (k_rr_momentum<R, T, true><<<1, kThreads, mo_bytes, st>>>(d.ns, d.o0, d.no, d.nx, d.nb,
-                                                               d.want_p, w, YZ, dropped),
-     ::ff::note_launch());
-  else
-    (k_rr_momentum<R, T, false><<<1, kThreads, 0, st>>>(d.ns, d.o0, d.no, d.nx, d.nb, d.want_p,
-                                                         w, YZ, dropped),
-     ::ff::note_launch());
+  // the momentum factor (one block), Z L^-T (blocks of rows), the O rows
+  // mapped back (blocks of columns)
+  const size_t g_bytes = sizeof(R) * nb * nb;
+  const int mc_lsm = g_bytes <= kMaxDynSmem ? 1 : 0;
+  (k_rr_mchol<R><<<1, kThreads, mc_lsm ? g_bytes : 0, st>>>((int)n, (int)nb, d.want_p, w, dropped,
+                                                            mc_lsm),
+   ::ff::note_launch());
   FF_LAUNCH_CHECK();
+  if (d.want_p) {
+    const size_t lz = sizeof(R) * (nb | 1);
+    const int rs_lsm = g_bytes + 8 * lz <= kMaxDynSmem ? 1 : 0;
+    int rcb = kYC;
+    while (rcb > 1 && (rs_lsm ? g_bytes : 0) + rcb * lz > kMaxDynSmem) rcb >>= 1;
+    (k_rr_rsolve<R><<<(unsigned)((n + rcb - 1) / rcb), 256, (rs_lsm ? g_bytes : 0) + rcb * lz,
+                      st>>>(w.G, (int)nb, w.T1, (int)nb, w.Z, (int)nb, (int)n, w.keepz, rcb,
+                            rs_lsm),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
+  if (no > 0) {
+    const int ncol = d.want_p ? 2 * (int)nb : (int)nb;
+    const size_t lc = sizeof(R) * no;
+    const int bs_lsm = l_bytes + 8 * lc <= kMaxDynSmem ? 1 : 0;
+    int bcb = kYC;
+    while (bcb > 1 && (bs_lsm ? l_bytes : 0) + bcb * lc > kMaxDynSmem) bcb >>= 1;
+    (k_rr_bsolve<R><<<(unsigned)((ncol + bcb - 1) / bcb), 256, (bs_lsm ? l_bytes : 0) + bcb * lc,
+                      st>>>(w.L, d.no, d.o0, w.V, w.Z, (int)nb, ncol, bcb, bs_lsm),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
   (k_rr_output<R, T><<<(unsigned)n, 128, 0, st>>>(d.ns, d.o0, d.no, d.nb, d.want_p, w, YZ),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
