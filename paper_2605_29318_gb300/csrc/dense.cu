@@ -31,8 +31,11 @@
 //                       division-free Sturm count;
 //   k_rr_invit_sm       their eigenvectors by inverse iteration on the
 //                       tridiagonal (LU with partial pivoting), one block each;
-//   k_rr_cholqr         Cholesky QR of those vectors (a second pass only when
-//                       the first finds them far from orthogonal);
+//   k_rr_gram_mb, k_rr_cqchol, k_rr_rsolve, k_rr_cholqr
+//                       Cholesky QR of those vectors (the Gram and V L^-T
+//                       over many blocks, the factor in one; a second pass,
+//                       in one block, only when the first finds them far
+//                       from orthogonal);
 //   k_rr_wy_t, k_rr_backtransform
 //                       the Householder reflectors applied in reverse, in
 //                       groups of eight in compact WY form;
@@ -96,6 +99,7 @@ struct RRWork {
   R *As, *ref, *L, *dsc, *dg, *e, *e2, *tau, *lam, *V, *Z, *G, *T1, *scr, *C, *U;
   int* keep;   // n: basis columns kept
   int* keepz;  // nb: momentum columns kept
+  int* flag;   // 1: Cholesky QR's second pass is needed
 };
 
 template <class R>
@@ -1288,11 +1292,46 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ 4a. Cholesky QR of the tridiagonal eigenvectors (twice unless once is enough)
-// SM: V (n x nb) and G staged in shared memory (dynamic), else worked on in
-// the global workspace
+// First pass: the Gram V^T V over many blocks (k_rr_gram_mb), its factor in
+// one block (k_rr_cqchol, which also decides whether a second pass is
+// needed), V <- V L^-T over blocks of rows (k_rr_rsolve); the second pass,
+// when needed, in one block (k_rr_cholqr, which returns at once otherwise).
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_rr_cqchol(int nb, RRWork<R> w, int lsm) {
+  extern __shared__ __align__(16) unsigned char dyn_raw[];
+  R* G = lsm ? reinterpret_cast<R*>(dyn_raw) : w.G;
+  __shared__ int keep_nb[512];
+  __shared__ float s_off[kWarps];
+  if (lsm)
+    for (int t = threadIdx.x; t < nb * nb; t += kThreads) G[t] = w.G[t];
+  for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
+  __syncthreads();
+  // largest off-diagonal of the normalised Gram matrix: at most 1e-3 means
+  // (Gershgorin) a condition number below (1 + nb 1e-3) / (1 - nb 1e-3),
+  // and one pass leaves the vectors orthonormal to a few units of rounding
+  float off = 0.f;
+  for (int t = threadIdx.x; t < nb * nb; t += kThreads) {
+    const int a = t / nb, b = t - a * nb;
+    if (b < a)
+      off = fmaxf(off, fabsf((float)G[(size_t)a * nb + b]) /
+                           sqrtf((float)G[(size_t)a * nb + a] * (float)G[(size_t)b * nb + b]));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+  if ((threadIdx.x & 31) == 0) s_off[threadIdx.x >> 5] = off;
+  __syncthreads();
+  off = 0.f;
+  for (int q = 0; q < kWarps; ++q) off = fmaxf(off, s_off[q]);
+  block_cholesky(G, nb, keep_nb, R(0.0));
+  if (threadIdx.x == 0) *w.flag = !(nb * 1e-3f < 0.5f && off <= 1e-3f);
+  if (lsm)
+    for (int t = threadIdx.x; t < nb * nb; t += kThreads) w.G[t] = G[t];
+}
+// The second pass.  SM: V (n x nb) and G staged in shared memory (dynamic),
+// else worked on in the global workspace
 template <class R, bool SM>
 __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R> w) {
-  // the first pass's Gram (lower triangle) arrives in w.G from k_rr_gram_mb
+  if (!*w.flag) return;  // one pass was enough
   __shared__ int keep_nb[512];
   extern __shared__ __align__(16) unsigned char cq_raw[];
   // in shared memory V's rows are padded to an odd stride, so that a thread
@@ -1306,36 +1345,11 @@ __global__ void __launch_bounds__(kThreads) k_rr_cholqr(int n, int nb, RRWork<R>
       for (int c = lane; c < nb; c += 32) V[(size_t)i * lv + c] = w.V[(size_t)i * nb + c];
     __syncthreads();
   }
-  __shared__ float s_off[kWarps];
-  for (int pass = 0; pass < 2; ++pass) {
-    if (pass > 0)
-      blk_gram_tn(V, lv, V, lv, n, nb, nb, G, nb, true);
-    else if (SM)
-      for (int t = threadIdx.x; t < nb * nb; t += kThreads) G[t] = w.G[t];
-    for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
-    __syncthreads();
-    // largest off-diagonal of the normalised Gram matrix: at most 1e-3 means
-    // (Gershgorin) a condition number below (1 + nb 1e-3) / (1 - nb 1e-3),
-    // and one pass leaves the vectors orthonormal to a few units of rounding
-    float off = 0.f;
-    if (pass == 0) {
-      for (int t = threadIdx.x; t < nb * nb; t += kThreads) {
-        const int a = t / nb, b = t - a * nb;
-        if (b < a)
-          off = fmaxf(off, fabsf((float)G[(size_t)a * nb + b]) /
-                               sqrtf((float)G[(size_t)a * nb + a] * (float)G[(size_t)b * nb + b]));
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
-      if ((threadIdx.x & 31) == 0) s_off[threadIdx.x >> 5] = off;
-      __syncthreads();
-      off = 0.f;
-      for (int q = 0; q < kWarps; ++q) off = fmaxf(off, s_off[q]);
-    }
-    block_cholesky(G, nb, keep_nb, R(0.0));
-    block_trsm_rt(G, nb, V, lv, n);  // V <- V L^-T
-    if (pass == 0 && nb * 1e-3f < 0.5f && off <= 1e-3f) break;  // one pass is enough
-  }
+  blk_gram_tn(V, lv, V, lv, n, nb, nb, G, nb, true);
+  for (int s2 = threadIdx.x; s2 < nb; s2 += kThreads) keep_nb[s2] = 1;
+  __syncthreads();
+  block_cholesky(G, nb, keep_nb, R(0.0));
+  block_trsm_rt(G, nb, V, lv, n);  // V <- V L^-T
   if (SM)
     for (int i = wid; i < n; i += kWarps)
       for (int c = lane; c < nb; c += 32) w.V[(size_t)i * nb + c] = V[(size_t)i * lv + c];
@@ -1486,12 +1500,11 @@ __global__ void __launch_bounds__(kThreads)
 
 // Xout <- Xin L^-T for `rows` rows (m entries each; L as block_cholesky
 // leaves it, ld m), entries of columns with mask[c] == 0 set to zero: a
-// block per cb rows
+// block per cb rows (Xout may be Xin: a block writes only the rows it read)
 template <class R>
 __global__ void __launch_bounds__(256)
-    k_rr_rsolve(const R* __restrict__ Lg, int m, const R* __restrict__ Xin, int ldin,
-                R* __restrict__ Xout, int ldout, int rows, const int* __restrict__ mask, int cb,
-                int lsm) {
+    k_rr_rsolve(const R* __restrict__ Lg, int m, const R* Xin, int ldin, R* Xout, int ldout,
+                int rows, const int* __restrict__ mask, int cb, int lsm) {
   extern __shared__ __align__(16) unsigned char dyn_raw[];
   R* dyn = reinterpret_cast<R*>(dyn_raw);
   const R* L = lsm ? dyn : Lg;
@@ -1705,7 +1718,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   const size_t t1 = std::max(n * nb, 2 * n);
   const size_t total =
       2 * n * n + no * no + 5 * n + nb + 2 * n * nb + nb * nb + t1 + 6 * n * nb + 2 * n * no;
-  R* p = reinterpret_cast<R*>(work.ensure(sizeof(R) * total + sizeof(int) * (n + nb) + 256));
+  R* p = reinterpret_cast<R*>(work.ensure(sizeof(R) * total + sizeof(int) * (n + nb + 1) + 256));
   RRWork<R> w;
   w.As = p; p += n * n;
   w.ref = p; p += n * n;
@@ -1725,7 +1738,9 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
   w.U = p; p += n * no;
   w.keep = reinterpret_cast<int*>(p);
   w.keepz = w.keep + n;
+  w.flag = w.keepz + nb;
   for (const void* fn : {(const void*)k_rr_mchol<R>, (const void*)k_rr_rsolve<R>,
+                         (const void*)k_rr_cqchol<R>,
                          (const void*)k_rr_bsolve<R>, (const void*)k_rr_tridiag<R>,
                          (const void*)k_rr_invit_sm<R>,
                          (const void*)k_rr_cholqr<R, true>, (const void*)k_rr_backtransform<R>,
@@ -1805,7 +1820,26 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
      ::ff::note_launch());
     FF_LAUNCH_CHECK();
   };
+  // X <- X L^-T (L: m x m as block_cholesky leaves it) over blocks of rows,
+  // columns with mask[c] == 0 set to zero
+  auto rsolve = [&](const R* Lg, int m, const R* Xin, R* Xout, int rows, const int* mask) {
+    const size_t lb = sizeof(R) * m * m, lz = sizeof(R) * (m | 1);
+    const int lsm = lb + 8 * lz <= kMaxDynSmem ? 1 : 0;
+    int rcb = kYC;
+    while (rcb > 1 && (lsm ? lb : 0) + rcb * lz > kMaxDynSmem) rcb >>= 1;
+    (k_rr_rsolve<R><<<(unsigned)((rows + rcb - 1) / rcb), 256, (lsm ? lb : 0) + rcb * lz, st>>>(
+         Lg, m, Xin, m, Xout, m, rows, mask, rcb, lsm),
+     ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  };
   gram_mb(w.V, w.V, 0, (int)n, w.G, 1);  // Cholesky QR's first Gram
+  {
+    const size_t gq = sizeof(R) * nb * nb;
+    const int lsm = gq <= kMaxDynSmem ? 1 : 0;
+    (k_rr_cqchol<R><<<1, kThreads, lsm ? gq : 0, st>>>((int)nb, w, lsm), ::ff::note_launch());
+    FF_LAUNCH_CHECK();
+  }
+  rsolve(w.G, (int)nb, w.V, w.V, (int)n, nullptr);
   const size_t cq_bytes = sizeof(R) * (n * (nb | 1) + nb * nb);
   if (cq_bytes <= kMaxDynSmem)
     (k_rr_cholqr<R, true><<<1, kThreads, cq_bytes, st>>>(d.ns, d.nb, w), ::ff::note_launch());
@@ -1838,17 +1872,7 @@ void rr_run(cudaStream_t st, const double* A, const double* B, RRDims d, T* YZ, 
                                                             mc_lsm),
    ::ff::note_launch());
   FF_LAUNCH_CHECK();
-  if (d.want_p) {
-    const size_t lz = sizeof(R) * (nb | 1);
-    const int rs_lsm = g_bytes + 8 * lz <= kMaxDynSmem ? 1 : 0;
-    int rcb = kYC;
-    while (rcb > 1 && (rs_lsm ? g_bytes : 0) + rcb * lz > kMaxDynSmem) rcb >>= 1;
-    (k_rr_rsolve<R><<<(unsigned)((n + rcb - 1) / rcb), 256, (rs_lsm ? g_bytes : 0) + rcb * lz,
-                      st>>>(w.G, (int)nb, w.T1, (int)nb, w.Z, (int)nb, (int)n, w.keepz, rcb,
-                            rs_lsm),
-     ::ff::note_launch());
-    FF_LAUNCH_CHECK();
-  }
+  if (d.want_p) rsolve(w.G, (int)nb, w.T1, w.Z, (int)n, w.keepz);
   if (no > 0) {
     const int ncol = d.want_p ? 2 * (int)nb : (int)nb;
     const size_t lc = sizeof(R) * no;
