@@ -901,6 +901,105 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same product for pencils with few rows and long ones (the two-set
+// pencils: ~1,000 rows of a few hundred nonzeros): one warp per row leaves
+// most of the GPU idle behind long serial chains, so a block of kSW warps
+// shares each row (group q of the block takes nonzeros q, q + Q, ...), the
+// warps' partial sums added in shared memory in a fixed order.
+constexpr int kSW = 8;
+__global__ void __launch_bounds__(32 * kSW)
+    k_spmm_hm_df_split(const long long* __restrict__ ptr, const int* __restrict__ col,
+                       const float4* __restrict__ val, int n, const dfloat* __restrict__ X,
+                       int ldx, dfloat* __restrict__ YH, dfloat* __restrict__ YM, int ldy, int m) {
+  __shared__ dfloat part[kSW][32][9];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = m / 4, P = 32 / G;
+  const int g = lane / G, cv = (lane % G) * 4;
+  const bool act = g < P;
+  const int Q = kSW * P;  // groups per row
+  for (int k = blockIdx.x; k < n; k += gridDim.x) {
+    const long long s = ptr[k];
+    const int cnt = (int)(ptr[k + 1] - s);
+    const int* cr = col + s;
+    const float4* vr = val + s;
+    dfloat ah[4], am[4], hs(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ah[u] = am[u] = dfloat(0);
+    for (int e = act ? wid * P + g : cnt; e < cnt; e += Q) {
+      const int l0 = __ldg(cr + e);
+      const float4 v0 = __ldg(vr + e);
+      const float4* p0 = reinterpret_cast<const float4*>(X + (long long)l0 * ldx + cv);
+      const float4 a0 = __ldg(p0), b0 = __ldg(p0 + 1);
+      const dfloat x0[4] = {dfloat(a0.x, a0.y), dfloat(a0.z, a0.w), dfloat(b0.x, b0.y),
+                            dfloat(b0.z, b0.w)};
+      const dfloat h0(v0.x, v0.y), m0(v0.z, v0.w);
+      df_acc(hs, h0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        df_mac(ah[u], h0, x0[u]);
+        df_mac(am[u], m0, x0[u]);
+      }
+    }
+    for (int q = 1; q < P; ++q) {  // the warp's groups onto group 0
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const dfloat th = __shfl_down_sync(kFull, ah[u], q * G);
+        const dfloat tm = __shfl_down_sync(kFull, am[u], q * G);
+        if (g == 0) {
+          df_acc(ah[u], th);
+          df_acc(am[u], tm);
+        }
+      }
+      const dfloat ts = __shfl_down_sync(kFull, hs, q * G);
+      if (g == 0) df_acc(hs, ts);
+    }
+    if (g == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        part[wid][lane][u] = ah[u];
+        part[wid][lane][4 + u] = am[u];
+      }
+      part[wid][lane][8] = hs;
+    }
+    __syncthreads();
+    if (wid == 0 && g == 0) {
+      for (int w = 1; w < kSW; ++w) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          df_acc(ah[u], part[w][lane][u]);
+          df_acc(am[u], part[w][lane][4 + u]);
+        }
+        df_acc(hs, part[w][lane][8]);
+      }
+      const long long o = (long long)k * ldy + cv;
+      if (YH) {
+        const float4* pk = reinterpret_cast<const float4*>(X + (long long)k * ldx + cv);
+        const float4 xa = pk[0], xb = pk[1];
+        const dfloat xk[4] = {dfloat(xa.x, xa.y), dfloat(xa.z, xa.w), dfloat(xb.x, xb.y),
+                              dfloat(xb.z, xb.w)};
+        dfloat r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          df_mac(ah[u], -hs, xk[u]);
+          r[u] = df_norm(ah[u]);
+        }
+        float4* out = reinterpret_cast<float4*>(YH + o);
+        out[0] = make_float4(r[0].h, r[0].l, r[1].h, r[1].l);
+        out[1] = make_float4(r[2].h, r[2].l, r[3].h, r[3].l);
+      }
+      if (YM) {
+        dfloat r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r[u] = df_norm(am[u]);
+        float4* out = reinterpret_cast<float4*>(YM + o);
+        out[0] = make_float4(r[0].h, r[0].l, r[1].h, r[1].l);
+        out[1] = make_float4(r[2].h, r[2].l, r[3].h, r[3].l);
+      }
+    }
+    __syncthreads();  // part is rewritten for the next row
+  }
+}
+
 template <class T>
 void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T* val, long long n,
                  const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
@@ -914,7 +1013,11 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
                        reinterpret_cast<uintptr_t>(val) % 16 == 0 &&
                        (!YH || reinterpret_cast<uintptr_t>(YH) % 16 == 0) &&
                        (!YM || reinterpret_cast<uintptr_t>(YM) % 16 == 0);
-    if (df_ok)
+    if (df_ok && n > 0 && n < (long long)sm_count() * 16)  // few rows: a block per row
+      (k_spmm_hm_df_split<<<(unsigned)n, 32 * kSW, 0, st>>>(
+           ptr, col, reinterpret_cast<const float4*>(val), (int)n, X, ldx, YH, YM, ldy, m),
+       ::ff::note_launch());
+    else if (df_ok)
       (k_spmm_hm_df<<<(unsigned)blocks, T_, 0, st>>>(ptr, col, reinterpret_cast<const float4*>(val),
                                                      (int)n, X, ldx, YH, YM, ldy, m),
        ::ff::note_launch());
