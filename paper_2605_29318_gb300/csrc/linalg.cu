@@ -1000,6 +1000,77 @@ __global__ void __launch_bounds__(32 * kSW)
   }
 }
 
+// k_spmm_hm_vec for pencils with few rows and long ones: a block of kSW
+// warps per row, the warps' partial sums added in shared memory in a fixed
+// order (see k_spmm_hm_df_split)
+template <class T>
+__global__ void __launch_bounds__(32 * kSW)
+    k_spmm_hm_vec_split(const long long* __restrict__ ptr, const int* __restrict__ col,
+                        const T* __restrict__ val, long long n, const T* __restrict__ X, int ldx,
+                        T* __restrict__ YH, T* __restrict__ YM, int ldy, int m) {
+  constexpr int VEC = Vec16<T>::n;
+  __shared__ T part[kSW][32][2 * VEC];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = m / VEC, P = 32 / G;
+  const int g = lane / G, cv = (lane % G) * VEC;
+  const bool act = g < P;
+  const int Q = kSW * P;
+  using T2 = typename std::conditional<std::is_same_v<T, float>, float2, double2>::type;
+  for (long long k = blockIdx.x; k < n; k += gridDim.x) {
+    const long long s = ptr[k];
+    const int cnt = (int)(ptr[k + 1] - s);
+    const int* cr = col + s;
+    const T2* vr = reinterpret_cast<const T2*>(val) + s;
+    T xk[VEC], ah[VEC], am[VEC];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) ah[u] = am[u] = T(0);
+    if (act) vload(X + k * ldx + cv, xk);
+    else
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) xk[u] = T(0);
+    for (int e = act ? wid * P + g : cnt; e < cnt; e += Q) {
+      const int l = __ldg(cr + e);
+      const T2 hm = vr[e];
+      T xl[VEC];
+      vload(X + (long long)l * ldx + cv, xl);
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        ah[u] += hm.x * (xl[u] - xk[u]);
+        am[u] += hm.y * xl[u];
+      }
+    }
+    for (int q = 1; q < P; ++q) {
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        const T th = __shfl_down_sync(kFull, ah[u], q * G);
+        const T tm = __shfl_down_sync(kFull, am[u], q * G);
+        if (g == 0) {
+          ah[u] += th;
+          am[u] += tm;
+        }
+      }
+    }
+    if (g == 0)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        part[wid][lane][u] = ah[u];
+        part[wid][lane][VEC + u] = am[u];
+      }
+    __syncthreads();
+    if (wid == 0 && g == 0) {
+      for (int w = 1; w < kSW; ++w)
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          ah[u] += part[w][lane][u];
+          am[u] += part[w][lane][VEC + u];
+        }
+      if (YH) vstore(YH + k * ldy + cv, ah);
+      if (YM) vstore(YM + k * ldy + cv, am);
+    }
+    __syncthreads();  // part is rewritten for the next row
+  }
+}
+
 template <class T>
 void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T* val, long long n,
                  const T* X, int ldx, T* YH, T* YM, int ldy, int m) {
@@ -1040,7 +1111,11 @@ void spmm_hm_raw(cudaStream_t st, const long long* ptr, const int* col, const T*
         return;
       }
     }
-    if (vec_ok && std::is_same_v<T, float> && m == 40)  // the solver's 40-column blocks
+    if (vec_ok && std::is_same_v<T, float> && n > 0 && n < (long long)sm_count() * 16)
+      (k_spmm_hm_vec_split<T><<<(unsigned)n, 32 * kSW, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM,
+                                                                 ldy, m),
+       ::ff::note_launch());  // few rows: a block per row
+    else if (vec_ok && std::is_same_v<T, float> && m == 40)  // the solver's 40-column blocks
       (k_spmm_hm_vec<T, 10><<<(unsigned)blocks, T_, 0, st>>>(ptr, col, val, n, X, ldx, YH, YM,
                                                               ldy, m),
        ::ff::note_launch());
