@@ -50,6 +50,7 @@ import argparse
 import json
 import os
 import statistics
+import atexit
 import subprocess
 import sys
 import time
@@ -98,7 +99,11 @@ def _traffic(cls, kernel):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region.
+
+    Started before the warm-up steps (enter() returns at once when already
+    started), so that nvidia-smi's own start-up overlaps untimed work; the
+    samples then cover the warm-up and the timed steps."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -108,14 +113,21 @@ class Clocks:
         self.proc = None
 
     def __enter__(self):
+        if self.proc:
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            atexit.register(self._kill)  # never left sampling if a step raises
         except Exception:
             self.proc = None
         return self
+
+    def _kill(self):
+        if self.proc and self.proc.poll() is None:
+            self.proc.kill()
 
     def __exit__(self, *a):
         self.out = ""
@@ -368,13 +380,14 @@ def run_splat(args, ctx, dev, local):
         ctx.assemble_hessian(E, None, 1.0, nu)
         return ctx.eigenmodes(k, opts, modes_out=modes, check=False)
 
+    clk = Clocks(local).__enter__()
     for _ in range(args.warmup):
         _timed(step, st, flush)
     roof_cls = "asm_values"
     ctx.profile(True, classes=[roof_cls])
     launches0 = binding.launch_count()
     times, reps = [], []
-    with Clocks(local) as clk:
+    with clk:
         for _ in range(args.steps):
             t, (_, _, rep, status) = _timed(step, st, flush)
             times.append(t)
@@ -475,12 +488,13 @@ def run_torus(args, ctx, dev, local, rank, world):
         X0 = ctx.warmstart_block(net, 32, opts) if warm else None
         return ctx.eigenmodes(32, opts, X0=X0, modes_out=modes, check=False)
 
+    clk = Clocks(local).__enter__()
     for _ in range(args.warmup):
         _timed(step, st, flush)
     ctx.profile(True, classes=["precond"])
     launches0 = binding.launch_count()
     times, reps = [], []
-    with Clocks(local) as clk:
+    with clk:
         for _ in range(args.steps):
             t, (_, _, rep, status) = _timed(step, st, flush)
             times.append(t)
@@ -623,11 +637,12 @@ def run_twoset_torus(args, ctx, dev, local):
         ctx.assemble_hessian(None, None, 1e6, 0.4)
         return ctx.eigenmodes(k, opts, modes_out=modes, check=False)
 
+    clk = Clocks(local).__enter__()
     for _ in range(args.warmup):
         _timed(step, st, flush)
     launches0 = binding.launch_count()
     times = []
-    with Clocks(local) as clk:
+    with clk:
         for _ in range(args.steps):
             t, (_, _, rep, status) = _timed(step, st, flush)
             times.append(t)
@@ -701,11 +716,12 @@ def run_batch(args, dev, local):
     def step():
         return binding.eigenmodes_batched(objs, args.prec, opts, device=local)
 
+    clk = Clocks(local).__enter__()
     for _ in range(args.warmup):
         _timed(step, st, flush)
     launches0 = binding.launch_count()
     times = []
-    with Clocks(local) as clk:
+    with clk:
         for _ in range(args.steps):
             t, (status, res) = _timed(step, st, flush)
             times.append(t)
