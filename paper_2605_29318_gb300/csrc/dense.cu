@@ -66,29 +66,24 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr size_t kMaxDynSmem = 220 * 1024;  // opt-in limit less room for static shared memory
 // working-precision constants: unit roundoff, smallest magnitude kept apart
-// from zero, default Cholesky drop, and the exponent at which the Sturm
-// recurrence rescales
+// from zero, default Cholesky drop
 template <class R>
 struct Prec;
 template <>
 struct Prec<double> {
-  static constexpr double eps = 1.1e-16, tiny = 1e-290, drop = 1e-13, hi = 0x1p+600, lo = 0x1p-600;
+  static constexpr double eps = 1.1e-16, tiny = 1e-290, drop = 1e-13;
 };
 template <>
 struct Prec<float> {
-  static constexpr float eps = 6e-8f, tiny = 1e-30f, drop = 1e-6f, hi = 0x1p+60f, lo = 0x1p-60f;
+  static constexpr float eps = 6e-8f, tiny = 1e-30f, drop = 1e-6f;
 };
 // double-float: ~2^-47 unit roundoff at the FP32 exponent range
 template <>
 struct Prec<dfloat> {
-  static constexpr dfloat eps = dfloat(1.5e-14), tiny = dfloat(1e-30), drop = dfloat(1e-12),
-                          hi = dfloat(0x1p+60), lo = dfloat(0x1p-60);
+  static constexpr dfloat eps = dfloat(1.5e-14), tiny = dfloat(1e-30), drop = dfloat(1e-12);
 };
-__device__ __forceinline__ int ilogb_r(double x) { return ilogb(x); }
-__device__ __forceinline__ int ilogb_r(float x) { return ilogbf(x); }
 __device__ __forceinline__ double scalbn_r(double x, int e) { return scalbn(x, e); }
 __device__ __forceinline__ float scalbn_r(float x, int e) { return scalbnf(x, e); }
-__device__ __forceinline__ int ilogb_r(dfloat x) { return ilogbf(x.h); }
 __device__ __forceinline__ dfloat scalbn_r(dfloat x, int e) {
   return dfloat(scalbnf(x.h, e), scalbnf(x.l, e));
 }
@@ -808,32 +803,6 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = tid; i < n; i += kThreads) w.e2[i] = w.e[i] * w.e[i];
 }
 
-// ------------------------------------------------------------------ R(2.) eigenvalues
-// Division-free Sturm count in FP64: sign changes along the leading principal
-// minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{-1} = 1), rescaled by
-// exact powers of two to stay in range.  A zero minor takes the sign opposite
-// to its predecessor.
-template <class R>
-__device__ int sturm(const R* d, const R* e2, int n, R x) {
-  R pm = R(1.0), p = d[0] - x;
-  if (p == R(0.0)) p = -Prec<R>::tiny;
-  int c = p < R(0.0);
-  for (int i = 1; i < n; ++i) {
-    R q = fma(d[i] - x, p, -e2[i - 1] * pm);
-    if (q == R(0.0)) q = p > R(0.0) ? -Prec<R>::tiny : Prec<R>::tiny;
-    c += (q < R(0.0)) != (p < R(0.0));
-    pm = p;
-    p = q;
-    const R ap = fabs(p);
-    if (ap > Prec<R>::hi || ap < Prec<R>::lo) {
-      const int ex = ilogb_r(p);
-      p = scalbn_r(p, -ex);
-      pm = scalbn_r(pm, -ex);
-    }
-  }
-  return c;
-}
-
 // ------------------------------------------------------------------ 1b. cluster Householder
 // Householder tridiagonalisation of the transformed n x n matrix (w.As) by a
 // cluster of CS thread blocks: row r lives in block r % CS (distributed
@@ -989,7 +958,10 @@ __global__ void __launch_bounds__(kCT) k_rr_house_cluster(int n, RRWork<R> w) {
 // ------------------------------------------------------------------ 2b. eigenvalues, one block each
 // FP64 multisection with the division-free Sturm count: one warp per
 // eigenvalue, 32 probes per round (a 33-fold shrink of the bracket per round).
-// Sturm count with the sign and range tests on the bit patterns (integer
+// The count is the number of sign changes along the leading principal minors
+// p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (p_{-1} = 1), rescaled by exact
+// powers of two to stay in range, a zero minor taking the sign opposite to
+// its predecessor; the sign and range tests run on the bit patterns (integer
 // instructions): per step three floating-point instructions, which matters in
 // FP64 on GB300 (64 cycles per FP64 warp instruction).
 __device__ __forceinline__ long long bits(double v) { return __double_as_longlong(v); }
